@@ -1,0 +1,184 @@
+"""FP64 CPU oracle of the GaussianPile slice projection operator (arXiv 2603.20611).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The product library (``paper_2603_20611_b300``) never imports it and
+shares no code with it: the arithmetic lives in ``oracle.c`` (plain C, double
+precision, OpenMP), built here with gcc into ``liboracle.so`` and called through
+ctypes.
+
+Functions follow the paper's route (Eq. 6-10 forward, Sec. S2 chain for the
+backward, Eq. 12 for the voxelizer); see the header of ``oracle.c`` for the
+conventions and the per-step citations.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_HDR = os.path.join(_HERE, "oracle.h")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, -O2, OpenMP, IEEE double)."""
+    newest_src = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= newest_src):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+           "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Set(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64),
+                ("mu", ctypes.c_void_p),
+                ("scale", ctypes.c_void_p),
+                ("quat", ctypes.c_void_p),
+                ("alpha", ctypes.c_void_p),
+                ("scale_mod", ctypes.c_double)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        I64 = ctypes.c_int64
+        D = ctypes.c_double
+        SP = ctypes.POINTER(_Set)
+        lib.orc_render.argtypes = [SP, I, P, I, I, D, I, P]
+        lib.orc_render_points.argtypes = [SP, I, P, D, I, I64, P, P, P, P]
+        lib.orc_render_backward.argtypes = [SP, I, P, I, I, D, I, P, P, P, P, P]
+        lib.orc_voxelize.argtypes = [SP, I, I, I, P]
+        lib.orc_voxelize_points.argtypes = [SP, I64, P, P, P, P]
+        lib.orc_voxelize_backward.argtypes = [SP, I, I, I, P, P, P, P, P]
+        lib.orc_mse.argtypes = [I64, P, P, P]
+        lib.orc_mse.restype = D
+        lib.orc_num_threads.restype = I
+        for f in ("orc_render", "orc_render_points", "orc_render_backward",
+                  "orc_voxelize", "orc_voxelize_points", "orc_voxelize_backward"):
+            getattr(lib, f).restype = I
+        _lib = lib
+    return _lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class _GaussianSet:
+    """Keeps fp64 copies alive while the C code reads them."""
+
+    def __init__(self, mu, scale, quat, alpha, scale_mod=1.0):
+        self.mu = _f64(mu, (-1, 3))
+        self.scale = _f64(scale, (-1, 3))
+        self.quat = _f64(quat, (-1, 4))
+        self.alpha = _f64(alpha, (-1,))
+        n = self.alpha.shape[0]
+        assert self.mu.shape[0] == n and self.scale.shape[0] == n and self.quat.shape[0] == n
+        self.n = n
+        self.c = _Set(n, _ptr(self.mu).value, _ptr(self.scale).value,
+                      _ptr(self.quat).value, _ptr(self.alpha).value, float(scale_mod))
+
+
+def _check(rc, name):
+    if rc != 0:
+        raise ValueError(f"{name} rejected its arguments (status {rc})")
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def render(mu, scale, quat, alpha, z, H, W, sigma_z, axis=2, scale_mod=1.0):
+    """Slice stack [S, H, W] by brute force over every Gaussian (Eq. 6-10)."""
+    g = _GaussianSet(mu, scale, quat, alpha, scale_mod)
+    z = _f64(z, (-1,))
+    out = np.zeros((z.shape[0], H, W), np.float64)
+    _check(_load().orc_render(ctypes.byref(g.c), z.shape[0], _ptr(z), H, W,
+                              float(sigma_z), axis, _ptr(out)), "orc_render")
+    return out
+
+
+def render_points(mu, scale, quat, alpha, z, sigma_z, pt_slice, pt_x, pt_y, axis=2,
+                  scale_mod=1.0):
+    """Eq. 10 at sample points (slice index, camera x, camera y)."""
+    g = _GaussianSet(mu, scale, quat, alpha, scale_mod)
+    z = _f64(z, (-1,))
+    ps = np.ascontiguousarray(np.asarray(pt_slice, dtype=np.int32).reshape(-1))
+    px = _f64(pt_x, (-1,))
+    py = _f64(pt_y, (-1,))
+    out = np.zeros(ps.shape[0], np.float64)
+    _check(_load().orc_render_points(ctypes.byref(g.c), z.shape[0], _ptr(z), float(sigma_z),
+                                     axis, ps.shape[0], _ptr(ps), _ptr(px), _ptr(py),
+                                     _ptr(out)), "orc_render_points")
+    return out
+
+
+def render_backward(mu, scale, quat, alpha, z, H, W, sigma_z, dL_dI, axis=2, scale_mod=1.0):
+    """(dL/dmu [n,3], dL/dscale [n,3], dL/dquat [n,4], dL/dalpha [n]) for a given dL/dI."""
+    g = _GaussianSet(mu, scale, quat, alpha, scale_mod)
+    z = _f64(z, (-1,))
+    G = _f64(dL_dI, (z.shape[0], H, W))
+    n = g.n
+    dmu = np.zeros((n, 3)); ds = np.zeros((n, 3)); dq = np.zeros((n, 4)); da = np.zeros(n)
+    _check(_load().orc_render_backward(ctypes.byref(g.c), z.shape[0], _ptr(z), H, W,
+                                       float(sigma_z), axis, _ptr(G), _ptr(dmu), _ptr(ds),
+                                       _ptr(dq), _ptr(da)), "orc_render_backward")
+    return dmu, ds, dq, da
+
+
+def voxelize(mu, scale, quat, alpha, X, Y, Z, scale_mod=1.0):
+    """Volume [Z, Y, X] of Eq. 12 by brute force."""
+    g = _GaussianSet(mu, scale, quat, alpha, scale_mod)
+    out = np.zeros((Z, Y, X), np.float64)
+    _check(_load().orc_voxelize(ctypes.byref(g.c), X, Y, Z, _ptr(out)), "orc_voxelize")
+    return out
+
+
+def voxelize_points(mu, scale, quat, alpha, px, py, pz, scale_mod=1.0):
+    g = _GaussianSet(mu, scale, quat, alpha, scale_mod)
+    px = _f64(px, (-1,)); py = _f64(py, (-1,)); pz = _f64(pz, (-1,))
+    out = np.zeros(px.shape[0], np.float64)
+    _check(_load().orc_voxelize_points(ctypes.byref(g.c), px.shape[0], _ptr(px), _ptr(py),
+                                       _ptr(pz), _ptr(out)), "orc_voxelize_points")
+    return out
+
+
+def voxelize_backward(mu, scale, quat, alpha, X, Y, Z, dL_dV, scale_mod=1.0):
+    g = _GaussianSet(mu, scale, quat, alpha, scale_mod)
+    G = _f64(dL_dV, (Z, Y, X))
+    n = g.n
+    dmu = np.zeros((n, 3)); ds = np.zeros((n, 3)); dq = np.zeros((n, 4)); da = np.zeros(n)
+    _check(_load().orc_voxelize_backward(ctypes.byref(g.c), X, Y, Z, _ptr(G), _ptr(dmu),
+                                         _ptr(ds), _ptr(dq), _ptr(da)),
+           "orc_voxelize_backward")
+    return dmu, ds, dq, da
+
+
+def mse(I, T):
+    """(L, dL/dI) of the mean squared error."""
+    I = _f64(I); T = _f64(T, I.shape)
+    g = np.zeros_like(I)
+    L = _load().orc_mse(I.size, _ptr(I), _ptr(T), _ptr(g))
+    return float(L), g
