@@ -1,0 +1,176 @@
+/*
+ * gp.h -- C ABI of the B300 (sm_103a) slice projection operator of GaussianPile
+ * (arXiv 2603.20611): the finite-thickness Focus-Gaussian slice renderer, its
+ * hand-written backward, the differentiable voxelizer, a batched launch and a
+ * serving loop.
+ *
+ * The operator (Sec. 4.2, Eq. 6-10; Sec. S1).  For a slice plane at position
+ * z_s along the slice axis, every 3-D Gaussian (mean mu, scale s, rotation
+ * quaternion q, intensity alpha) with covariance Sigma = R S S^T R^T is weighted
+ * by the Gaussian axial sensitivity h(t) = exp(-t^2 / 2 sigma_z^2) (Eq. 3) and
+ * contributes, at pixel p of the slice,
+ *      a~ exp(-1/2 d^T Sigma_2d^-1 d),   d = p - mu_2d,
+ * with Sigma_2d, mu_2d the in-plane block of the Focus Gaussian (Eq. 6, 8) and
+ * a~ = alpha opacity_r / sqrt(det Sigma_2d) (Eq. 7, 9).  Contributions add up
+ * without occlusion (Eq. 10).  In closed form, with v = Sigma_cc + sigma_z^2
+ * (c the slice axis, p the in-plane axes), delta = mu_c - z_s:
+ *      Sigma_2d  = Sigma_pp - Sigma_pc Sigma_cp / v      (slice-invariant)
+ *      mu_2d     = mu_p - Sigma_pc delta / v
+ *      opacity_r = exp(-delta^2 / 2v).
+ *
+ * Conventions.
+ *   - Gaussian parameters are fp32 structure-of-arrays in DEVICE memory, owned
+ *     by the caller and never freed or written by the library: mu[3n],
+ *     scale[3n] (linear, > 0), quat[4n] = (w, x, y, z) (normalised inside;
+ *     16-byte aligned), alpha[n] (linear).  The covariance uses
+ *     S = diag(scale_mod * s) (Sec. S1).
+ *   - Slice axis `axis` = 2 (planes z = z_s; image columns x, rows y),
+ *     1 (planes y = z_s; columns x, rows z) or 0 (planes x = z_s; columns y,
+ *     rows z).  Pixel (ix, iy) sits at (ix + 0.5, iy + 0.5) in the plane;
+ *     voxel (ix, iy, iz) at (ix + .5, iy + .5, iz + .5).
+ *   - Images are [S][H][W] fp32 row-major, volumes [Z][Y][X] fp32.
+ *   - Every call is asynchronous on the caller's CUDA stream (`stream` is a
+ *     cudaStream_t, NULL = the legacy default stream), except where noted.
+ *     Plain render / backward / voxelize calls read back one pair count (a
+ *     short stream synchronisation) to size their sort buffers.
+ *   - Contributions are culled where they are provably below eps relative to
+ *     their Gaussian: slices with opacity_r < eps are skipped, and only screen
+ *     tiles that the ellipse d^T Sigma_2d^-1 d <= 2 ln(1/eps) touches are
+ *     visited (the culling the paper leaves at "a small threshold", Sec. 4.2).
+ *     Inside a visited tile every pixel is evaluated.
+ *   - Errors never abort: each call returns a gp_status, and gp_last_error()
+ *     gives a message.  Argument errors are detected before any launch.
+ */
+#ifndef GP_H
+#define GP_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GP_API __attribute__((visibility("default")))
+#else
+#define GP_API
+#endif
+
+typedef int gp_status;
+#define GP_OK 0
+#define GP_PENDING 1          /* gp_serve_poll: request not finished yet */
+#define GP_ERR_ARG (-1)       /* invalid argument (null pointer, bad size, ...) */
+#define GP_ERR_OOM (-2)       /* device allocation failed or over the workspace limit */
+#define GP_ERR_CUDA (-3)      /* a CUDA runtime call failed */
+#define GP_ERR_TIMEOUT (-4)   /* a bounded wait ran out */
+#define GP_ERR_OVERFLOW (-5)  /* a preplanned buffer was too small; re-plan */
+#define GP_ERR_STATE (-6)     /* call not valid in the object's current state */
+
+typedef struct gp_ctx gp_ctx;
+
+/* Exponential used by the rasterisers. */
+#define GP_EXP_POLY 0  /* project-written exp2: range reduction + degree-6 polynomial on
+                          the FP32 pipe (no ex2.approx); the default */
+#define GP_EXP_HW 1    /* the SFU ex2.approx instruction (benchmarked alternative) */
+
+typedef struct {
+  float eps;              /* culling bound: truncated mass per pair <= eps (default 1e-6) */
+  int deterministic;      /* 1: backward reduces per-pair partials in a fixed order
+                             (bitwise repeatable); 0: warp-reduced atomics (default 0) */
+  int exp_mode;           /* GP_EXP_POLY (default) or GP_EXP_HW */
+  int tile;               /* screen tile side in pixels: 16 (default) or 8 */
+  int fwd_px;             /* pixels per thread in the forward rasteriser (0 = default) */
+  int bwd_px;             /* pixels per thread in the backward rasteriser (0 = default) */
+  int64_t workspace_limit;/* max device bytes of library scratch, 0 = no limit */
+} gp_config;
+
+/* Fills *cfg with the defaults above.  Returns GP_ERR_ARG if cfg is NULL. */
+GP_API gp_status gp_config_default(gp_config* cfg);
+
+/* Creates a context on CUDA device `device` (it becomes current on the calling
+ * thread).  cfg may be NULL for defaults; GP_ERR_ARG for an invalid cfg.  The
+ * context owns a grow-only device workspace pool (freed by gp_destroy).  A
+ * context is not thread-safe: use one per host thread, or serialise calls. */
+GP_API gp_status gp_create(gp_ctx** out, int device, const gp_config* cfg);
+
+/* Frees the context and its workspace (after synchronising the device). */
+GP_API gp_status gp_destroy(gp_ctx* ctx);
+
+/* Message of the last error on ctx (static string if ctx is NULL).  Valid until
+ * the next call on ctx. */
+GP_API const char* gp_last_error(gp_ctx* ctx);
+
+/* Library scratch currently held by ctx, in bytes. */
+GP_API int64_t gp_workspace_bytes(gp_ctx* ctx);
+
+/* Gaussian set: caller-owned device pointers (see conventions). n may be 0. */
+typedef struct {
+  const float* mu;
+  const float* scale;
+  const float* quat;
+  const float* alpha;
+  int64_t n;
+  float scale_mod;       /* Sec. S1 "mod"; 1 for the plain S = diag(s) */
+} gp_set;
+
+/* Forward (Eq. 10): renders S slices at plane positions z[S] (HOST array) into
+ * out (DEVICE, [S][H][W], fully overwritten).  sigma_z in (0, inf).
+ * Returns GP_ERR_ARG for S < 0, H or W <= 0, bad sigma_z or axis, null
+ * pointers, non-finite z, or S*H*W > 2^31; GP_ERR_OVERFLOW for more than 2^31
+ * (Gaussian, slice, tile) pairs in one call. */
+GP_API gp_status gp_render_slices(gp_ctx* ctx, const gp_set* set, const float* z, int S, int H,
+                           int W, float sigma_z, int axis, float* out, void* stream);
+
+/* Backward of gp_render_slices (Sec. 4.3; the chain of Sec. S2 re-derived in
+ * closed form): given dL/dI (DEVICE, [S][H][W]), writes dL/dmu [3n],
+ * dL/dscale [3n], dL/dquat [4n] (through the quaternion normalisation, 16-byte
+ * aligned) and dL/dalpha [n] (DEVICE, overwritten).  Per-tile Gaussian lists
+ * are recomputed, no per-pixel state is stored. */
+GP_API gp_status gp_render_backward(gp_ctx* ctx, const gp_set* set, const float* z, int S, int H,
+                             int W, float sigma_z, int axis, const float* dL_dI,
+                             float* d_mu, float* d_scale, float* d_quat, float* d_alpha,
+                             void* stream);
+
+/* Mean squared error of a rendered stack against target slices (the loss the
+ * operator is driven with here; the paper's L1 + D-SSIM of Eq. 11 is not
+ * built).  I: [S][H][W] DEVICE.  T: DEVICE target stack of at least
+ * max(t_index)+1 slices of H*W.  t_index: HOST array of S slice indices into T,
+ * or NULL for T[s] = slice s.  Writes dL/dI = 2 (I - T) / (S H W) (DEVICE) and,
+ * if loss != NULL, L = mean (I - T)^2 into loss[0] (DEVICE, fp32). */
+GP_API gp_status gp_mse_grad(gp_ctx* ctx, const float* I, const float* T, const int* t_index,
+                      int S, int H, int W, float* dL_dI, float* loss, void* stream);
+
+/* Differentiable voxelizer (Sec. 4.3 "Differentiable Voxelization", Eq. 12):
+ * V(x) = sum_i alpha_i exp(-1/2 (x - mu_i)^T Sigma_i^-1 (x - mu_i)) on the
+ * X x Y x Z voxel grid, written to vol (DEVICE, [Z][Y][X], overwritten).
+ * Binned to 8^3 voxel tiles; each Gaussian visits the tiles inside the bounding
+ * box of its ellipsoid (x - mu)^T Sigma^-1 (x - mu) <= 2 ln(1/eps). */
+GP_API gp_status gp_voxelize(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, float* vol,
+                      void* stream);
+
+/* Backward of gp_voxelize given dL/dV (DEVICE [Z][Y][X]); gradients as in
+ * gp_render_backward (overwritten). */
+GP_API gp_status gp_voxelize_backward(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z,
+                               const float* dL_dV, float* d_mu, float* d_scale,
+                               float* d_quat, float* d_alpha, void* stream);
+
+/* Diagnostics of the last gp_render_slices / gp_render_backward / gp_voxelize
+ * on ctx: number of (Gaussian, slice, tile) pairs binned and of pixel
+ * evaluations issued (pairs x tile pixels). */
+GP_API gp_status gp_last_counts(gp_ctx* ctx, int64_t* pairs, int64_t* issued_evals);
+
+/* Number of Gaussian-pixel evaluations inside the culling ellipse
+ * (d^T Sigma_2d^-1 d <= 2 ln(1/eps), opacity_r >= eps) of a render call with
+ * these arguments: the algorithmic work of Eq. 10.  Synchronous. */
+GP_API gp_status gp_count_evals(gp_ctx* ctx, const gp_set* set, const float* z, int S, int H,
+                         int W, float sigma_z, int axis, int64_t* evals);
+
+/* Test hook for the rasterisers' exponential: y[i] = 2^x[i] for n DEVICE floats
+ * with the given mode (GP_EXP_POLY or GP_EXP_HW).  Inputs below -125 clamp. */
+GP_API gp_status gp_exp2_eval(gp_ctx* ctx, const float* x, float* y, int64_t n, int mode,
+                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,286 @@
+"""Thin ctypes binding of ``libgaussianpile.so`` (the C ABI in ``include/gp.h``).
+
+Argument marshalling only: every function below checks tensor placement and
+layout, passes raw device pointers and the current CUDA stream to the C entry
+point of the same name, and raises ``GPError`` on a non-zero status.  There is
+no fallback: if the shared library is missing the import fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgaussianpile.so")
+
+GP_OK = 0
+GP_PENDING = 1
+GP_ERR_ARG = -1
+GP_ERR_OOM = -2
+GP_ERR_CUDA = -3
+GP_ERR_TIMEOUT = -4
+GP_ERR_OVERFLOW = -5
+GP_ERR_STATE = -6
+GP_EXP_POLY = 0
+GP_EXP_HW = 1
+
+# Every symbol include/gp.h declares (checked by the CPU ABI test).
+EXPORTS = (
+    "gp_config_default", "gp_create", "gp_destroy", "gp_last_error", "gp_workspace_bytes",
+    "gp_render_slices", "gp_render_backward", "gp_mse_grad", "gp_voxelize", "gp_voxelize_backward",
+    "gp_last_counts", "gp_count_evals", "gp_exp2_eval",
+)
+
+
+class GPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class gp_config(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_float), ("deterministic", ctypes.c_int), ("exp_mode", ctypes.c_int),
+                ("tile", ctypes.c_int), ("fwd_px", ctypes.c_int), ("bwd_px", ctypes.c_int),
+                ("workspace_limit", ctypes.c_int64)]
+
+
+class gp_set(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("quat", ctypes.c_void_p),
+                ("alpha", ctypes.c_void_p), ("n", ctypes.c_int64), ("scale_mod", ctypes.c_float)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2603_20611_b300.build` "
+                          "(the operator has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, I64, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float
+    CP, SP = ctypes.POINTER(gp_config), ctypes.POINTER(gp_set)
+    sig = {
+        "gp_config_default": [CP],
+        "gp_create": [ctypes.POINTER(P), I, CP],
+        "gp_destroy": [P],
+        "gp_last_error": [P],
+        "gp_workspace_bytes": [P],
+        "gp_render_slices": [P, SP, P, I, I, I, F, I, P, P],
+        "gp_render_backward": [P, SP, P, I, I, I, F, I, P, P, P, P, P, P],
+        "gp_mse_grad": [P, P, P, P, I, I, I, P, P, P],
+        "gp_voxelize": [P, SP, I, I, I, P, P],
+        "gp_voxelize_backward": [P, SP, I, I, I, P, P, P, P, P, P],
+        "gp_last_counts": [P, ctypes.POINTER(I64), ctypes.POINTER(I64)],
+        "gp_count_evals": [P, SP, P, I, I, I, F, I, ctypes.POINTER(I64)],
+        "gp_exp2_eval": [P, P, P, I64, I, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = I
+    lib.gp_last_error.restype = ctypes.c_char_p
+    lib.gp_workspace_bytes.restype = I64
+    return lib
+
+
+lib = _load()
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, name, dtype=torch.float32, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(-1))
+
+
+class Context:
+    """Owns a gp_ctx (device workspace pool) on one CUDA device."""
+
+    def __init__(self, device=0, eps=1e-6, deterministic=False, exp_mode=GP_EXP_POLY, tile=16,
+                 fwd_px=0, bwd_px=0, workspace_limit=0):
+        cfg = gp_config()
+        lib.gp_config_default(ctypes.byref(cfg))
+        cfg.eps, cfg.deterministic, cfg.exp_mode = float(eps), int(bool(deterministic)), int(exp_mode)
+        cfg.tile, cfg.fwd_px, cfg.bwd_px = int(tile), int(fwd_px), int(bwd_px)
+        cfg.workspace_limit = int(workspace_limit)
+        self.device = int(device)
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        st = lib.gp_create(ctypes.byref(h), self.device, ctypes.byref(cfg))
+        if st != GP_OK:
+            raise GPError(st, "gp_create failed")
+        self.h = h
+
+    def check(self, st, what):
+        if st != GP_OK:
+            msg = lib.gp_last_error(self.h).decode(errors="replace")
+            raise GPError(st, f"{what}: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.gp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self):
+        return int(lib.gp_workspace_bytes(self.h))
+
+    def last_counts(self):
+        p, e = ctypes.c_int64(), ctypes.c_int64()
+        self.check(lib.gp_last_counts(self.h, ctypes.byref(p), ctypes.byref(e)), "gp_last_counts")
+        return int(p.value), int(e.value)
+
+
+class GaussianSet:
+    """Device tensors of one Gaussian set (Sec. S1: G = (mu, s, q, alpha))."""
+
+    def __init__(self, mu, scale, quat, alpha, scale_mod=1.0):
+        self.mu, self.scale, self.quat, self.alpha = mu, scale, quat, alpha
+        self.scale_mod = float(scale_mod)
+
+    @property
+    def n(self):
+        return int(self.alpha.shape[0])
+
+    @classmethod
+    def from_numpy(cls, g, device="cuda", scale_mod=1.0):
+        f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
+        return cls(f(g.mu), f(g.scale), f(g.quat), f(g.alpha), scale_mod)
+
+    def c(self):
+        n = self.n
+        return gp_set(_dev(self.mu, "mu", shape=(n, 3)).value, _dev(self.scale, "scale", shape=(n, 3)).value,
+                      _dev(self.quat, "quat", shape=(n, 4)).value, _dev(self.alpha, "alpha", shape=(n,)).value,
+                      n, self.scale_mod)
+
+
+def _grads_like(gs, grads):
+    n = gs.n
+    if grads is None:
+        dev = gs.alpha.device
+        grads = (torch.empty(n, 3, device=dev), torch.empty(n, 3, device=dev), torch.empty(n, 4, device=dev),
+                 torch.empty(n, device=dev))
+    return grads
+
+
+def gp_render_slices(ctx, gs, z, H, W, sigma_z, axis=2, out=None, stream=None):
+    z = _host_f32(z)
+    S = z.shape[0]
+    if out is None:
+        out = torch.empty(S, H, W, device=gs.alpha.device)
+    st = lib.gp_render_slices(ctx.h, ctypes.byref(gs.c()), z.ctypes.data_as(ctypes.c_void_p), S, H, W,
+                              float(sigma_z), axis, _dev(out, "out", shape=(S, H, W)), _stream(stream))
+    ctx.check(st, "gp_render_slices")
+    return out
+
+
+def gp_render_backward(ctx, gs, z, H, W, sigma_z, dL_dI, axis=2, grads=None, stream=None):
+    z = _host_f32(z)
+    S = z.shape[0]
+    d_mu, d_s, d_q, d_a = _grads_like(gs, grads)
+    st = lib.gp_render_backward(ctx.h, ctypes.byref(gs.c()), z.ctypes.data_as(ctypes.c_void_p), S, H, W,
+                                float(sigma_z), axis, _dev(dL_dI, "dL_dI", shape=(S, H, W)),
+                                _dev(d_mu, "d_mu"), _dev(d_s, "d_scale"), _dev(d_q, "d_quat"),
+                                _dev(d_a, "d_alpha"), _stream(stream))
+    ctx.check(st, "gp_render_backward")
+    return d_mu, d_s, d_q, d_a
+
+
+def gp_mse_grad(ctx, I, T, t_index=None, dL_dI=None, loss=None, stream=None):
+    S, H, W = I.shape
+    if dL_dI is None:
+        dL_dI = torch.empty_like(I)
+    tid = None
+    if t_index is not None:
+        tid = np.ascontiguousarray(np.asarray(t_index, np.int32).reshape(-1))
+        if tid.shape[0] != S:
+            raise ValueError("t_index needs one entry per slice")
+        if T.dim() != 3 or T.shape[1:] != I.shape[1:] or int(tid.max(initial=0)) >= T.shape[0]:
+            raise ValueError("target stack too small for t_index")
+    elif tuple(T.shape) != tuple(I.shape):
+        raise ValueError("T must match I when t_index is None")
+    st = lib.gp_mse_grad(ctx.h, _dev(I, "I"), _dev(T, "T"),
+                         None if tid is None else tid.ctypes.data_as(ctypes.c_void_p), S, H, W,
+                         _dev(dL_dI, "dL_dI", shape=(S, H, W)),
+                         None if loss is None else _dev(loss, "loss", shape=(1,)), _stream(stream))
+    ctx.check(st, "gp_mse_grad")
+    return dL_dI, loss
+
+
+def gp_voxelize(ctx, gs, X, Y, Z, vol=None, stream=None):
+    if vol is None:
+        vol = torch.empty(Z, Y, X, device=gs.alpha.device)
+    st = lib.gp_voxelize(ctx.h, ctypes.byref(gs.c()), X, Y, Z, _dev(vol, "vol", shape=(Z, Y, X)),
+                         _stream(stream))
+    ctx.check(st, "gp_voxelize")
+    return vol
+
+
+def gp_voxelize_backward(ctx, gs, X, Y, Z, dL_dV, grads=None, stream=None):
+    d_mu, d_s, d_q, d_a = _grads_like(gs, grads)
+    st = lib.gp_voxelize_backward(ctx.h, ctypes.byref(gs.c()), X, Y, Z, _dev(dL_dV, "dL_dV", shape=(Z, Y, X)),
+                                  _dev(d_mu, "d_mu"), _dev(d_s, "d_scale"), _dev(d_q, "d_quat"),
+                                  _dev(d_a, "d_alpha"), _stream(stream))
+    ctx.check(st, "gp_voxelize_backward")
+    return d_mu, d_s, d_q, d_a
+
+
+def gp_count_evals(ctx, gs, z, H, W, sigma_z, axis=2):
+    z = _host_f32(z)
+    out = ctypes.c_int64()
+    st = lib.gp_count_evals(ctx.h, ctypes.byref(gs.c()), z.ctypes.data_as(ctypes.c_void_p), z.shape[0], H, W,
+                            float(sigma_z), axis, ctypes.byref(out))
+    ctx.check(st, "gp_count_evals")
+    return int(out.value)
+
+
+def gp_exp2_eval(ctx, x, mode=GP_EXP_POLY, y=None, stream=None):
+    if y is None:
+        y = torch.empty_like(x)
+    st = lib.gp_exp2_eval(ctx.h, _dev(x, "x"), _dev(y, "y", shape=x.shape), x.numel(), int(mode), _stream(stream))
+    ctx.check(st, "gp_exp2_eval")
+    return y
+
+
+class SliceRender(torch.autograd.Function):
+    """Differentiable slice projection: forward gp_render_slices, backward
+    gp_render_backward (per-tile lists rebuilt, no per-pixel state kept)."""
+
+    @staticmethod
+    def forward(fctx, ctx, z, H, W, sigma_z, axis, scale_mod, mu, scale, quat, alpha):
+        gs = GaussianSet(mu.contiguous(), scale.contiguous(), quat.contiguous(), alpha.contiguous(), scale_mod)
+        fctx.meta = (ctx, _host_f32(z).copy(), H, W, sigma_z, axis, scale_mod)
+        fctx.save_for_backward(gs.mu, gs.scale, gs.quat, gs.alpha)
+        return gp_render_slices(ctx, gs, z, H, W, sigma_z, axis)
+
+    @staticmethod
+    def backward(fctx, g):
+        ctx, z, H, W, sigma_z, axis, scale_mod = fctx.meta
+        mu, scale, quat, alpha = fctx.saved_tensors
+        gs = GaussianSet(mu, scale, quat, alpha, scale_mod)
+        dm, ds, dq, da = gp_render_backward(ctx, gs, z, H, W, sigma_z, g.contiguous(), axis)
+        return None, None, None, None, None, None, None, dm, ds, dq, da
+
+
+def render(ctx, mu, scale, quat, alpha, z, H, W, sigma_z, axis=2, scale_mod=1.0):
+    """Autograd-aware slice stack [S, H, W]."""
+    return SliceRender.apply(ctx, z, H, W, sigma_z, axis, scale_mod, mu, scale, quat, alpha)

@@ -1,0 +1,188 @@
+// gp_common.cuh -- shared device helpers of the sm_103a slice projection library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gp.h"
+
+namespace gp {
+
+// log2(e) as an fp32 literal of the mathematical constant.
+constexpr float kLog2e = 1.4426950408889634f;
+
+// ---------------------------------------------------------------- exp2
+// 2^x = 2^n 2^f, n = round(x), f = x - n in [-1/2, 1/2]; 2^f by a degree-6
+// polynomial with p(0) = 1 fitted for minimal relative error on [-1/2, 1/2]
+// (Remez exchange; coefficients derived by csrc/exp2_poly.py, max relative
+// error 1.9 ulp of 2^-24 with plain fp32 Horner).  n is recovered with the
+// round-to-nearest trick (x + 1.5*2^23 leaves n in the low mantissa bits) and
+// inserted into the exponent with an integer shift-add.  Valid for
+// x in [-125, 0.5]; callers clamp below.
+#define GP_EXP2_C1 0.6931472420692444f
+#define GP_EXP2_C2 0.24022652208805084f
+#define GP_EXP2_C3 0.055503103882074356f
+#define GP_EXP2_C4 0.009617692790925503f
+#define GP_EXP2_C5 0.0013406643411144614f
+#define GP_EXP2_C6 0.00015594677824992687f
+
+__device__ __forceinline__ float exp2_poly(float x) {
+  const float kShift = 12582912.0f;  // 1.5 * 2^23
+  float t = __fadd_rn(x, kShift);
+  float n = __fsub_rn(t, kShift);
+  float f = __fsub_rn(x, n);
+  float p = GP_EXP2_C6;
+  p = fmaf(p, f, GP_EXP2_C5);
+  p = fmaf(p, f, GP_EXP2_C4);
+  p = fmaf(p, f, GP_EXP2_C3);
+  p = fmaf(p, f, GP_EXP2_C2);
+  p = fmaf(p, f, GP_EXP2_C1);
+  p = fmaf(p, f, 1.0f);
+  return __int_as_float(__float_as_int(p) + (__float_as_int(t) << 23));
+}
+
+// The SFU instruction, as a benchmarked alternative (GP_EXP_HW).
+__device__ __forceinline__ float exp2_hw(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <int MODE>
+__device__ __forceinline__ float exp2_sel(float x) {
+  if constexpr (MODE == GP_EXP_HW) return exp2_hw(x);
+  else return exp2_poly(x);
+}
+
+constexpr float kExpFloor = -125.0f;  // 2^-125 ~ 2.4e-38: below fp32 resolution of any sum
+
+// ---------------------------------------------------------------- records
+// Per-Gaussian slice-invariant record of the slice renderer (camera frame of the
+// slice axis), 64 bytes:
+//   r0 = (mu_x, mu_y, mu_z, 1/v)         v = Sigma_zz + sigma_z^2
+//   r1 = (a_x, a_y, A, zr)                a = Sigma_{xy,z}/v, A = alpha/sqrt(det Sigma_2d),
+//                                         zr = axial half range sqrt(2 v ln(1/eps))
+//   r2 = (C00, C01, C11, rx)              C = Sigma_2d^-1, rx = k sqrt(Sigma_2d,xx)
+//   r3 = (ry, valid, 0, 0)                ry = k sqrt(Sigma_2d,yy)
+struct __align__(16) SliceRec {
+  float4 r0, r1, r2, r3;
+};
+
+// Per-Gaussian record of the voxelizer (world frame), 64 bytes:
+//   r0 = (mu_x, mu_y, mu_z, alpha)
+//   r1 = (K00, K01, K02, K11)             K = Sigma^-1
+//   r2 = (K12, K22, hx, hy)               h = k sqrt(diag Sigma): bounding box
+//   r3 = (hz, valid, 0, 0)
+struct __align__(16) VoxRec {
+  float4 r0, r1, r2, r3;
+};
+
+// ------------------------------------------------------------ rotations
+// Rotation matrix of q/|q|, q = (w, x, y, z).
+__device__ __forceinline__ void quat_rot(float4 q, float R[3][3], float qn[4], float& qnorm) {
+  qnorm = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+  float inv = 1.0f / qnorm;
+  float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+  qn[0] = w; qn[1] = x; qn[2] = y; qn[3] = z;
+  float xx = x * x, yy = y * y, zz = z * z;
+  float xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y, wz = w * z;
+  R[0][0] = 1.f - 2.f * (yy + zz); R[0][1] = 2.f * (xy - wz);       R[0][2] = 2.f * (xz + wy);
+  R[1][0] = 2.f * (xy + wz);       R[1][1] = 1.f - 2.f * (xx + zz); R[1][2] = 2.f * (yz - wx);
+  R[2][0] = 2.f * (xz - wy);       R[2][1] = 2.f * (yz + wx);       R[2][2] = 1.f - 2.f * (xx + yy);
+}
+
+// World covariance Sigma = (R D)(R D)^T, D = diag(d); returns the 6 unique entries
+// (xx, xy, xz, yy, yz, zz) and M = R D.
+__device__ __forceinline__ void covariance(const float R[3][3], const float d[3], float M[3][3],
+                                           float S6[6]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M[r][c] = R[r][c] * d[c];
+  auto dot = [&](int a, int b) { return M[a][0] * M[b][0] + M[a][1] * M[b][1] + M[a][2] * M[b][2]; };
+  S6[0] = dot(0, 0); S6[1] = dot(0, 1); S6[2] = dot(0, 2);
+  S6[3] = dot(1, 1); S6[4] = dot(1, 2); S6[5] = dot(2, 2);
+}
+
+// Backward of Sigma = M M^T, M = R diag(dd), dd = mod * s, R = R(q/|q|), given
+// the symmetric gradient Gw = dL/dSigma.  Adds dL/ds into gs[3] and writes
+// dL/dq (through the normalisation q/|q|) into gq[4].
+__device__ __forceinline__ void scale_quat_backward(const float R[3][3], const float M[3][3],
+                                                    const float dd[3], const float qn[4], float qnorm,
+                                                    float mod, const float Gw[3][3], float gs[3],
+                                                    float gq[4]) {
+  // dL/dM = 2 Gw M, then M = R D: dL/dR = dL/dM D, dL/dD_c = sum_r R_rc dL/dM_rc
+  float gR[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float gm = 2.0f * (Gw[r][0] * M[0][c] + Gw[r][1] * M[1][c] + Gw[r][2] * M[2][c]);
+      gR[r][c] = gm * dd[c];
+      gs[c] += mod * R[r][c] * gm;
+    }
+  // dR/d(w, x, y, z) of the unit-quaternion rotation, contracted with gR
+  const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+  float gw = 2.f * (z * (gR[1][0] - gR[0][1]) + y * (gR[0][2] - gR[2][0]) + x * (gR[2][1] - gR[1][2]));
+  float gx = 2.f * (y * (gR[0][1] + gR[1][0]) + z * (gR[0][2] + gR[2][0]) + w * (gR[2][1] - gR[1][2])) -
+             4.f * x * (gR[1][1] + gR[2][2]);
+  float gy = 2.f * (x * (gR[0][1] + gR[1][0]) + w * (gR[0][2] - gR[2][0]) + z * (gR[1][2] + gR[2][1])) -
+             4.f * y * (gR[0][0] + gR[2][2]);
+  float gz = 2.f * (w * (gR[1][0] - gR[0][1]) + x * (gR[0][2] + gR[2][0]) + y * (gR[1][2] + gR[2][1])) -
+             4.f * z * (gR[0][0] + gR[1][1]);
+  // q_n = q / |q|: dL/dq = (g - q_n (q_n . g)) / |q|
+  float dot = gw * w + gx * x + gy * y + gz * z;
+  float iq = 1.0f / qnorm;
+  gq[0] = (gw - w * dot) * iq;
+  gq[1] = (gx - x * dot) * iq;
+  gq[2] = (gy - y * dot) * iq;
+  gq[3] = (gz - z * dot) * iq;
+}
+
+// Camera axis permutation: camera coordinate j is world coordinate perm(axis, j).
+//   axis 2: (x, y, z); axis 1: (x, z, y); axis 0: (y, z, x).
+__host__ __device__ __forceinline__ int axis_perm(int axis, int j) {
+  return axis == 2 ? j : (axis == 1 ? (j == 0 ? 0 : (j == 1 ? 2 : 1)) : (j == 0 ? 1 : (j == 1 ? 2 : 0)));
+}
+
+__host__ __device__ __forceinline__ int sym_index(int a, int b) {
+  // index into (xx, xy, xz, yy, yz, zz)
+  int lo = a < b ? a : b, hi = a < b ? b : a;
+  return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+}
+
+// --------------------------------------------------- ellipse vs rectangle
+// Minimum over the rectangle [x0, x1] x [y0, y1] of q(p) = (p-m)^T C (p-m),
+// C = [[c00, c01], [c01, c11]] positive definite, compared with k2.  Written with
+// explicit rounding intrinsics so that the pair count and the pair emission (two
+// kernels) take bit-identical decisions.
+__device__ __forceinline__ float qform(float c00, float c01, float c11, float dx, float dy) {
+  float t = __fmaf_rn(c01, __fmul_rn(2.0f, dy), __fmul_rn(c00, dx));
+  return __fmaf_rn(t, dx, __fmul_rn(__fmul_rn(c11, dy), dy));
+}
+
+// Minimum of q along one edge: the fixed coordinate offset is dfix, the free one
+// runs over [dlo, dhi]; the free-coordinate minimiser is -c01 dfix / c_var.
+__device__ __forceinline__ float edge_min(float c_fixed, float c01, float c_var, float dfix,
+                                          float dlo, float dhi, bool fixed_is_x) {
+  float dstar = __fdiv_rn(-__fmul_rn(c01, dfix), c_var);
+  dstar = fminf(fmaxf(dstar, dlo), dhi);
+  return fixed_is_x ? qform(c_fixed, c01, c_var, dfix, dstar) : qform(c_var, c01, c_fixed, dstar, dfix);
+}
+
+__device__ __forceinline__ bool ellipse_hits_rect(float mx, float my, float c00, float c01,
+                                                  float c11, float k2, float x0, float x1,
+                                                  float y0, float y1) {
+  if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
+  float dxl = __fsub_rn(x0, mx), dxh = __fsub_rn(x1, mx);
+  float dyl = __fsub_rn(y0, my), dyh = __fsub_rn(y1, my);
+  float m = edge_min(c00, c01, c11, dxl, dyl, dyh, true);
+  m = fminf(m, edge_min(c00, c01, c11, dxh, dyl, dyh, true));
+  m = fminf(m, edge_min(c11, c01, c00, dyl, dxl, dxh, false));
+  m = fminf(m, edge_min(c11, c01, c00, dyh, dxl, dxh, false));
+  return m <= k2;
+}
+
+// ------------------------------------------------------------ misc
+__host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace gp

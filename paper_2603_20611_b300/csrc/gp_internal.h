@@ -1,0 +1,70 @@
+// gp_internal.h -- host-side internals shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gp.h"
+
+namespace gp {
+
+// ------------------------------------------------------------- primitives
+int64_t scan_temp_bytes(int64_t n);
+template <typename T>
+cudaError_t exclusive_scan(const T* in, T* out, int64_t n, unsigned long long* total, void* temp,
+                           cudaStream_t st);
+int64_t radix_temp_bytes(int64_t cap);
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                             const unsigned long long* n_dev, uint32_t cap, int bits, void* temp,
+                             cudaStream_t st, bool* result_in_alt);
+
+// --------------------------------------------------------------- workspace
+// A grow-only device buffer.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct Ctx;
+
+// Ensures buf holds at least `bytes`; grows by 1.25x.  Returns GP_OK or GP_ERR_OOM.
+gp_status ws_reserve(Ctx* c, DevBuf& buf, size_t bytes);
+void ws_release(Ctx* c, DevBuf& buf);
+
+// Buffers of one binned render (slice renderer or voxelizer).
+struct BinBufs {
+  DevBuf rec;        // per-Gaussian record (64 B)
+  DevBuf counts;     // per-Gaussian pair count (uint64)
+  DevBuf offsets;    // exclusive scan of counts (uint64)
+  DevBuf total;      // pair total (uint64) + spare slots
+  DevBuf keys, vals, keys_alt, vals_alt;  // uint32
+  DevBuf emit_gid;   // emission index -> Gaussian id (uint32)
+  DevBuf ranges;     // per (slice, tile): [start, end) (uint2)
+  DevBuf scan_tmp, sort_tmp;
+  DevBuf zs, zorder, zorig;  // sorted plane positions, their slice indices, positions by index
+  DevBuf accum;      // backward: per-Gaussian accumulators
+  DevBuf partial;    // backward, deterministic mode: per-pair partials
+  DevBuf loss_tmp;
+};
+
+struct Ctx {
+  int device = 0;
+  gp_config cfg{};
+  std::string err;
+  int64_t ws_bytes = 0;
+  BinBufs b;
+  unsigned long long* h_total = nullptr;  // pinned readback slot
+  int64_t last_pairs = 0, last_issued = 0;
+  int sm_count = 148;
+};
+
+gp_status set_err(Ctx* c, gp_status st, const std::string& msg);
+gp_status cuda_err(Ctx* c, cudaError_t e, const char* where);
+
+}  // namespace gp
+
+struct gp_ctx {
+  gp::Ctx impl;
+};

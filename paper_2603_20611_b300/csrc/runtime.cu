@@ -1,0 +1,501 @@
+// runtime.cu -- C ABI of the slice projection library: context, workspace pool,
+// argument checking and the host sequencing of the render / backward /
+// voxelize pipelines.  Every arithmetic step runs in the kernels of slice.cu,
+// voxel.cu and sort.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "gp_internal.h"
+#include "slice.cuh"
+#include "voxel.cuh"
+
+namespace gp {
+
+gp_status set_err(Ctx* c, gp_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+gp_status cuda_err(Ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return GP_OK;
+  cudaGetLastError();  // clear the (non-sticky) error so the context stays usable
+  if (e == cudaErrorMemoryAllocation) return set_err(c, GP_ERR_OOM, std::string(where) + ": out of device memory");
+  return set_err(c, GP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+gp_status ws_reserve(Ctx* c, DevBuf& buf, size_t bytes) {
+  if (bytes <= buf.bytes) return GP_OK;
+  size_t want = std::max(bytes, (size_t)(buf.bytes * 1.25));
+  want = (want + 255) & ~(size_t)255;
+  int64_t limit = c->cfg.workspace_limit;
+  if (limit > 0 && c->ws_bytes - (int64_t)buf.bytes + (int64_t)want > limit) {
+    want = (bytes + 255) & ~(size_t)255;
+    if (c->ws_bytes - (int64_t)buf.bytes + (int64_t)want > limit)
+      return set_err(c, GP_ERR_OOM, "workspace limit exceeded (" + std::to_string(limit) + " bytes)");
+  }
+  if (buf.ptr) {
+    cudaError_t e = cudaFree(buf.ptr);
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaFree");
+    c->ws_bytes -= (int64_t)buf.bytes;
+    buf.ptr = nullptr;
+    buf.bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&buf.ptr, want);
+  if (e != cudaSuccess) {
+    buf.ptr = nullptr;
+    cudaGetLastError();
+    return set_err(c, GP_ERR_OOM, "cudaMalloc of " + std::to_string(want) + " bytes failed");
+  }
+  buf.bytes = want;
+  c->ws_bytes += (int64_t)want;
+  return GP_OK;
+}
+
+void ws_release(Ctx* c, DevBuf& buf) {
+  if (buf.ptr) {
+    cudaFree(buf.ptr);
+    c->ws_bytes -= (int64_t)buf.bytes;
+  }
+  buf.ptr = nullptr;
+  buf.bytes = 0;
+}
+
+#define GP_TRY(x)               \
+  do {                          \
+    gp_status _s = (x);         \
+    if (_s != GP_OK) return _s; \
+  } while (0)
+#define GP_CUDA(c, x, where)                               \
+  do {                                                     \
+    cudaError_t _e = (x);                                  \
+    if (_e != cudaSuccess) return cuda_err(c, _e, where);  \
+  } while (0)
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static gp_status check_set(Ctx* c, const gp_set* s) {
+  if (!s) return set_err(c, GP_ERR_ARG, "set is NULL");
+  if (s->n < 0 || s->n > (int64_t)INT32_MAX - 1) return set_err(c, GP_ERR_ARG, "set size out of range");
+  if (s->n > 0 && (!s->mu || !s->scale || !s->quat || !s->alpha))
+    return set_err(c, GP_ERR_ARG, "set has a NULL parameter pointer");
+  if (s->n > 0 && !aligned16(s->quat)) return set_err(c, GP_ERR_ARG, "quat must be 16-byte aligned");
+  if (!(s->scale_mod > 0.0f) || !isfinite(s->scale_mod)) return set_err(c, GP_ERR_ARG, "scale_mod must be > 0");
+  return GP_OK;
+}
+
+static int tile_of(const Ctx* c) { return c->cfg.tile == 8 ? 8 : 16; }
+static int fwd_px(const Ctx* c) { return c->cfg.fwd_px > 0 ? c->cfg.fwd_px : 1; }
+static int bwd_px(const Ctx* c) { return c->cfg.bwd_px > 0 ? c->cfg.bwd_px : (c->cfg.tile == 8 ? 2 : 4); }
+
+// Sorts the sorted keys' pairs after emission; shared tail of both binnings.
+static gp_status sort_and_range(Ctx* c, uint32_t P, int64_t nkeys, cudaStream_t st, const uint32_t** sorted_vals) {
+  BinBufs& b = c->b;
+  int bits = 1;
+  while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)nkeys) ++bits;
+  bool in_alt = false;
+  GP_CUDA(c, radix_sort_pairs((uint32_t*)b.keys.ptr, (uint32_t*)b.vals.ptr, (uint32_t*)b.keys_alt.ptr,
+                              (uint32_t*)b.vals_alt.ptr, (const unsigned long long*)b.total.ptr, P, bits,
+                              b.sort_tmp.ptr, st, &in_alt),
+          "radix sort");
+  const uint32_t* sk = (const uint32_t*)(in_alt ? b.keys_alt.ptr : b.keys.ptr);
+  *sorted_vals = (const uint32_t*)(in_alt ? b.vals_alt.ptr : b.vals.ptr);
+  launch_ranges(sk, (const unsigned long long*)b.total.ptr, P, (uint2*)b.ranges.ptr, st);
+  return GP_OK;
+}
+
+static gp_status reserve_pairs(Ctx* c, uint32_t P) {
+  BinBufs& b = c->b;
+  GP_TRY(ws_reserve(c, b.keys, (size_t)P * 4));
+  GP_TRY(ws_reserve(c, b.vals, (size_t)P * 4));
+  GP_TRY(ws_reserve(c, b.keys_alt, (size_t)P * 4));
+  GP_TRY(ws_reserve(c, b.vals_alt, (size_t)P * 4));
+  GP_TRY(ws_reserve(c, b.emit_gid, (size_t)P * 4));
+  GP_TRY(ws_reserve(c, b.sort_tmp, (size_t)radix_temp_bytes(P)));
+  return GP_OK;
+}
+
+// Scan of the per-Gaussian counts and the one host readback of the total.
+static gp_status scan_counts(Ctx* c, int n, cudaStream_t st, uint32_t* P) {
+  BinBufs& b = c->b;
+  GP_CUDA(c, exclusive_scan<unsigned long long>((unsigned long long*)b.counts.ptr, (unsigned long long*)b.offsets.ptr,
+                                                n, (unsigned long long*)b.total.ptr, b.scan_tmp.ptr, st),
+          "pair scan");
+  GP_CUDA(c, cudaMemcpyAsync(c->h_total, b.total.ptr, 8, cudaMemcpyDeviceToHost, st), "pair count readback");
+  GP_CUDA(c, cudaStreamSynchronize(st), "pair count readback");
+  unsigned long long tot = *c->h_total;
+  if (tot >= (unsigned long long)INT32_MAX)
+    return set_err(c, GP_ERR_OVERFLOW, "more than 2^31 binned pairs in one call; split the call");
+  *P = (uint32_t)tot;
+  return GP_OK;
+}
+
+// Bins the set's (Gaussian, slice, tile) pairs of a slice stack: K-pre, scan,
+// one count readback, K-emit, radix sort, K-range.  On return the context's
+// buffers hold the records, the sorted emission indices and the tile ranges,
+// and *a describes the launch.
+static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, int H, int W, float sigma_z,
+                            int axis, cudaStream_t st, SliceArgs* a, uint32_t* pairs_out,
+                            const uint32_t** sorted_vals) {
+  if (S < 0 || H <= 0 || W <= 0) return set_err(c, GP_ERR_ARG, "need S >= 0, H > 0, W > 0");
+  if (S > 0 && !z) return set_err(c, GP_ERR_ARG, "z is NULL");
+  if (!(sigma_z > 0.0f) || !isfinite(sigma_z)) return set_err(c, GP_ERR_ARG, "sigma_z must be in (0, inf)");
+  if (axis < 0 || axis > 2) return set_err(c, GP_ERR_ARG, "axis must be 0, 1 or 2");
+  if ((int64_t)S * H * W > (int64_t)INT32_MAX) return set_err(c, GP_ERR_ARG, "S*H*W exceeds 2^31");
+  for (int s = 0; s < S; ++s)
+    if (!isfinite(z[s])) return set_err(c, GP_ERR_ARG, "z contains a non-finite value");
+  const int tile = tile_of(c);
+  const int TX = ceil_div(W, tile), TY = ceil_div(H, tile);
+  const int64_t nkeys = (int64_t)S * TX * TY;
+  BinBufs& b = c->b;
+  const int n = (int)set->n;
+  // slice positions: sorted copy + order (host), uploaded once per call
+  std::vector<int> order(S);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return z[i] < z[j]; });
+  std::vector<float> zs(S);
+  for (int j = 0; j < S; ++j) zs[j] = z[order[j]];
+  GP_TRY(ws_reserve(c, b.zs, (size_t)std::max(S, 1) * 4));
+  GP_TRY(ws_reserve(c, b.zorder, (size_t)std::max(S, 1) * 4));
+  GP_TRY(ws_reserve(c, b.zorig, (size_t)std::max(S, 1) * 4));
+  if (S > 0) {
+    GP_CUDA(c, cudaMemcpyAsync(b.zs.ptr, zs.data(), S * 4, cudaMemcpyHostToDevice, st), "upload z");
+    GP_CUDA(c, cudaMemcpyAsync(b.zorder.ptr, order.data(), S * 4, cudaMemcpyHostToDevice, st), "upload z");
+    GP_CUDA(c, cudaMemcpyAsync(b.zorig.ptr, z, S * 4, cudaMemcpyHostToDevice, st), "upload z");
+  }
+  SliceArgs& A = *a;
+  A.mu = set->mu; A.scale = set->scale; A.quat = set->quat; A.alpha = set->alpha;
+  A.n = n; A.mod = set->scale_mod; A.axis = axis; A.sigma2 = sigma_z * sigma_z;
+  A.k2 = 2.0f * logf(1.0f / c->cfg.eps);
+  A.zs = (const float*)b.zs.ptr; A.zorder = (const int*)b.zorder.ptr; A.zorig = (const float*)b.zorig.ptr;
+  A.S = S; A.H = H; A.W = W; A.tile = tile; A.TX = TX; A.TY = TY;
+  GP_TRY(ws_reserve(c, b.rec, (size_t)std::max(n, 1) * sizeof(SliceRec)));
+  GP_TRY(ws_reserve(c, b.counts, (size_t)std::max(n, 1) * 8));
+  GP_TRY(ws_reserve(c, b.offsets, (size_t)std::max(n, 1) * 8));
+  GP_TRY(ws_reserve(c, b.total, 64));
+  GP_TRY(ws_reserve(c, b.scan_tmp, (size_t)scan_temp_bytes(std::max(n, 1))));
+  GP_TRY(ws_reserve(c, b.ranges, (size_t)std::max<int64_t>(nkeys, 1) * 8));
+  GP_CUDA(c, cudaMemsetAsync(b.ranges.ptr, 0, (size_t)std::max<int64_t>(nkeys, 1) * 8, st), "memset ranges");
+  uint32_t P = 0;
+  if (n > 0 && S > 0) {
+    launch_slice_pre(A, (SliceRec*)b.rec.ptr, (unsigned long long*)b.counts.ptr, st);
+    GP_TRY(scan_counts(c, n, st, &P));
+  } else if (n > 0) {
+    GP_CUDA(c, cudaMemsetAsync(b.counts.ptr, 0, (size_t)n * 8, st), "clear counts");
+    GP_CUDA(c, cudaMemsetAsync(b.offsets.ptr, 0, (size_t)n * 8, st), "clear offsets");
+  }
+  *sorted_vals = nullptr;
+  if (P > 0) {
+    GP_TRY(reserve_pairs(c, P));
+    launch_slice_emit(A, (const SliceRec*)b.rec.ptr, (const unsigned long long*)b.offsets.ptr,
+                      (uint32_t*)b.keys.ptr, (uint32_t*)b.vals.ptr, (uint32_t*)b.emit_gid.ptr, st);
+    GP_TRY(sort_and_range(c, P, nkeys, st, sorted_vals));
+  }
+  *pairs_out = P;
+  c->last_pairs = P;
+  c->last_issued = (int64_t)P * tile * tile;
+  return cuda_err(c, cudaGetLastError(), "binning kernels");
+}
+
+// Bins the voxelizer's (Gaussian, 8^3 tile) pairs: K-vpre, scan, count
+// readback, K-vemit, radix sort, K-range.
+static gp_status bin_voxels(Ctx* c, const gp_set* set, int X, int Y, int Z, cudaStream_t st, VoxArgs* a,
+                            uint32_t* pairs_out, const uint32_t** sorted_vals) {
+  if (X <= 0 || Y <= 0 || Z <= 0) return set_err(c, GP_ERR_ARG, "need X, Y, Z > 0");
+  if ((int64_t)X * Y * Z > (int64_t)INT32_MAX * 4) return set_err(c, GP_ERR_ARG, "volume too large");
+  const int TX = ceil_div(X, VOX_TILE), TY = ceil_div(Y, VOX_TILE), TZ = ceil_div(Z, VOX_TILE);
+  const int64_t nkeys = (int64_t)TX * TY * TZ;
+  BinBufs& b = c->b;
+  const int n = (int)set->n;
+  VoxArgs& A = *a;
+  A.mu = set->mu; A.scale = set->scale; A.quat = set->quat; A.alpha = set->alpha;
+  A.n = n; A.mod = set->scale_mod; A.k2 = 2.0f * logf(1.0f / c->cfg.eps);
+  A.X = X; A.Y = Y; A.Z = Z; A.TX = TX; A.TY = TY; A.TZ = TZ;
+  GP_TRY(ws_reserve(c, b.rec, (size_t)std::max(n, 1) * sizeof(VoxRec)));
+  GP_TRY(ws_reserve(c, b.counts, (size_t)std::max(n, 1) * 8));
+  GP_TRY(ws_reserve(c, b.offsets, (size_t)std::max(n, 1) * 8));
+  GP_TRY(ws_reserve(c, b.total, 64));
+  GP_TRY(ws_reserve(c, b.scan_tmp, (size_t)scan_temp_bytes(std::max(n, 1))));
+  GP_TRY(ws_reserve(c, b.ranges, (size_t)nkeys * 8));
+  GP_CUDA(c, cudaMemsetAsync(b.ranges.ptr, 0, (size_t)nkeys * 8, st), "memset ranges");
+  uint32_t P = 0;
+  if (n > 0) {
+    launch_vox_pre(A, (VoxRec*)b.rec.ptr, (unsigned long long*)b.counts.ptr, st);
+    GP_TRY(scan_counts(c, n, st, &P));
+  }
+  *sorted_vals = nullptr;
+  if (P > 0) {
+    GP_TRY(reserve_pairs(c, P));
+    launch_vox_emit(A, (const VoxRec*)b.rec.ptr, (const unsigned long long*)b.offsets.ptr, (uint32_t*)b.keys.ptr,
+                    (uint32_t*)b.vals.ptr, (uint32_t*)b.emit_gid.ptr, st);
+    GP_TRY(sort_and_range(c, P, nkeys, st, sorted_vals));
+  }
+  *pairs_out = P;
+  c->last_pairs = P;
+  c->last_issued = (int64_t)P * VOX_TILE * VOX_TILE * VOX_TILE;
+  return cuda_err(c, cudaGetLastError(), "voxel binning kernels");
+}
+
+static gp_status check_grads(Ctx* c, int64_t n, float* d_mu, float* d_scale, float* d_quat, float* d_alpha) {
+  if (n > 0 && (!d_mu || !d_scale || !d_quat || !d_alpha)) return set_err(c, GP_ERR_ARG, "gradient pointer is NULL");
+  if (n > 0 && !aligned16(d_quat)) return set_err(c, GP_ERR_ARG, "d_quat must be 16-byte aligned");
+  return GP_OK;
+}
+
+}  // namespace gp
+
+using namespace gp;
+
+extern "C" {
+
+gp_status gp_config_default(gp_config* cfg) {
+  if (!cfg) return GP_ERR_ARG;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->eps = 1e-6f;
+  cfg->deterministic = 0;
+  cfg->exp_mode = GP_EXP_POLY;
+  cfg->tile = 16;
+  cfg->fwd_px = 0;
+  cfg->bwd_px = 0;
+  cfg->workspace_limit = 0;
+  return GP_OK;
+}
+
+gp_status gp_create(gp_ctx** out, int device, const gp_config* cfg) {
+  if (!out) return GP_ERR_ARG;
+  *out = nullptr;
+  gp_config c;
+  gp_config_default(&c);
+  if (cfg) {
+    c = *cfg;
+    if (!(c.eps > 0.0f && c.eps < 1.0f)) return GP_ERR_ARG;
+    if (c.tile != 8 && c.tile != 16) return GP_ERR_ARG;
+    if (c.exp_mode != GP_EXP_POLY && c.exp_mode != GP_EXP_HW) return GP_ERR_ARG;
+    if (c.workspace_limit < 0) return GP_ERR_ARG;
+    if (c.fwd_px < 0 || (c.fwd_px > 0 && !fwd_px_supported(c.tile, c.fwd_px))) return GP_ERR_ARG;
+    if (c.bwd_px < 0 || (c.bwd_px > 0 && !bwd_px_supported(c.tile, c.bwd_px))) return GP_ERR_ARG;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return GP_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return GP_ERR_CUDA;
+  gp_ctx* ctx = new (std::nothrow) gp_ctx();
+  if (!ctx) return GP_ERR_OOM;
+  ctx->impl.device = device;
+  ctx->impl.cfg = c;
+  if (cudaMallocHost(&ctx->impl.h_total, 64) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return GP_ERR_OOM;
+  }
+  cudaDeviceGetAttribute(&ctx->impl.sm_count, cudaDevAttrMultiProcessorCount, device);
+  *out = ctx;
+  return GP_OK;
+}
+
+gp_status gp_destroy(gp_ctx* ctx) {
+  if (!ctx) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  BinBufs& b = c->b;
+  DevBuf* all[] = {&b.rec, &b.counts, &b.offsets, &b.total, &b.keys, &b.vals, &b.keys_alt, &b.vals_alt,
+                   &b.emit_gid, &b.ranges, &b.scan_tmp, &b.sort_tmp, &b.zs, &b.zorder, &b.zorig,
+                   &b.accum, &b.partial, &b.loss_tmp};
+  for (DevBuf* d : all) ws_release(c, *d);
+  if (c->h_total) cudaFreeHost(c->h_total);
+  delete ctx;
+  return GP_OK;
+}
+
+const char* gp_last_error(gp_ctx* ctx) {
+  if (!ctx) return "no context";
+  return ctx->impl.err.c_str();
+}
+
+int64_t gp_workspace_bytes(gp_ctx* ctx) { return ctx ? ctx->impl.ws_bytes : 0; }
+
+gp_status gp_last_counts(gp_ctx* ctx, int64_t* pairs, int64_t* issued) {
+  if (!ctx) return GP_ERR_ARG;
+  if (pairs) *pairs = ctx->impl.last_pairs;
+  if (issued) *issued = ctx->impl.last_issued;
+  return GP_OK;
+}
+
+gp_status gp_render_slices(gp_ctx* ctx, const gp_set* set, const float* z, int S, int H, int W,
+                           float sigma_z, int axis, float* out, void* stream) {
+  if (!ctx) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+  GP_TRY(check_set(c, set));
+  if (!out && S > 0) return set_err(c, GP_ERR_ARG, "out is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  SliceArgs a;
+  uint32_t P = 0;
+  const uint32_t* vals = nullptr;
+  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, axis, st, &a, &P, &vals));
+  if (S == 0) return GP_OK;
+  if (P == 0) {
+    GP_CUDA(c, cudaMemsetAsync(out, 0, (size_t)S * H * W * 4, st), "clear out");
+    return GP_OK;
+  }
+  GP_CUDA(c, launch_raster_fwd(a, fwd_px(c), c->cfg.exp_mode, (const SliceRec*)c->b.rec.ptr, vals,
+                               (const uint32_t*)c->b.emit_gid.ptr, (const uint2*)c->b.ranges.ptr, out, st),
+          "raster forward");
+  return GP_OK;
+}
+
+gp_status gp_render_backward(gp_ctx* ctx, const gp_set* set, const float* z, int S, int H, int W,
+                             float sigma_z, int axis, const float* dL_dI, float* d_mu, float* d_scale,
+                             float* d_quat, float* d_alpha, void* stream) {
+  if (!ctx) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+  GP_TRY(check_set(c, set));
+  const int n = (int)set->n;
+  GP_TRY(check_grads(c, n, d_mu, d_scale, d_quat, d_alpha));
+  if (S > 0 && !dL_dI) return set_err(c, GP_ERR_ARG, "dL_dI is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  SliceArgs a;
+  uint32_t P = 0;
+  const uint32_t* vals = nullptr;
+  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, axis, st, &a, &P, &vals));
+  if (n == 0) return GP_OK;
+  BinBufs& b = c->b;
+  GP_TRY(ws_reserve(c, b.accum, (size_t)n * 10 * 4));
+  const bool det = c->cfg.deterministic != 0;
+  if (det) {
+    GP_TRY(ws_reserve(c, b.partial, (size_t)std::max<uint32_t>(P, 1) * 32));
+  } else {
+    GP_CUDA(c, cudaMemsetAsync(b.accum.ptr, 0, (size_t)n * 10 * 4, st), "clear accumulators");
+  }
+  if (P > 0) {
+    GP_CUDA(c, launch_raster_bwd(a, bwd_px(c), c->cfg.exp_mode, det, (const SliceRec*)b.rec.ptr, vals,
+                                 (const uint32_t*)b.emit_gid.ptr, (const uint2*)b.ranges.ptr, dL_dI,
+                                 (float*)b.accum.ptr, (float4*)b.partial.ptr, st),
+            "raster backward");
+  }
+  if (det)
+    launch_det_reduce(n, (const unsigned long long*)b.offsets.ptr, (const unsigned long long*)b.counts.ptr,
+                      (const float4*)b.partial.ptr, (float*)b.accum.ptr, st);
+  launch_slice_bwd_pre(a, (const float*)b.accum.ptr, d_mu, d_scale, d_quat, d_alpha, st);
+  return cuda_err(c, cudaGetLastError(), "backward kernels");
+}
+
+gp_status gp_mse_grad(gp_ctx* ctx, const float* I, const float* T, const int* t_index, int S, int H, int W,
+                      float* dL_dI, float* loss, void* stream) {
+  if (!ctx) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+  if (S < 0 || H <= 0 || W <= 0) return set_err(c, GP_ERR_ARG, "need S >= 0, H > 0, W > 0");
+  if (S == 0) return GP_OK;
+  if (!I || !T || !dL_dI) return set_err(c, GP_ERR_ARG, "NULL image pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  const int64_t HW = (int64_t)H * W;
+  BinBufs& b = c->b;
+  const size_t tmp_bytes = ((size_t)mse_tmp_floats(S, HW) * 4 + 255) & ~(size_t)255;
+  GP_TRY(ws_reserve(c, b.loss_tmp, tmp_bytes + (size_t)S * 4));
+  const int* tid = nullptr;
+  if (t_index) {
+    for (int s = 0; s < S; ++s)
+      if (t_index[s] < 0) return set_err(c, GP_ERR_ARG, "negative target slice index");
+    int* dst = (int*)((char*)b.loss_tmp.ptr + tmp_bytes);
+    GP_CUDA(c, cudaMemcpyAsync(dst, t_index, (size_t)S * 4, cudaMemcpyHostToDevice, st), "upload t_index");
+    tid = dst;
+  }
+  launch_mse(I, T, tid, S, HW, dL_dI, loss, (float*)b.loss_tmp.ptr, st);
+  return cuda_err(c, cudaGetLastError(), "mse");
+}
+
+gp_status gp_count_evals(gp_ctx* ctx, const gp_set* set, const float* z, int S, int H, int W, float sigma_z,
+                         int axis, int64_t* evals) {
+  if (!ctx || !evals) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+  GP_TRY(check_set(c, set));
+  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  cudaStream_t st = 0;
+  SliceArgs a;
+  uint32_t P = 0;
+  const uint32_t* vals = nullptr;
+  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, axis, st, &a, &P, &vals));
+  unsigned long long* d = (unsigned long long*)c->b.total.ptr + 1;
+  GP_CUDA(c, cudaMemsetAsync(d, 0, 8, st), "count");
+  if (set->n > 0 && S > 0) launch_count_evals(a, (const SliceRec*)c->b.rec.ptr, d, st);
+  GP_CUDA(c, cudaMemcpyAsync(c->h_total, d, 8, cudaMemcpyDeviceToHost, st), "count readback");
+  GP_CUDA(c, cudaStreamSynchronize(st), "count readback");
+  *evals = (int64_t)*c->h_total;
+  return GP_OK;
+}
+
+gp_status gp_exp2_eval(gp_ctx* ctx, const float* x, float* y, int64_t n, int mode, void* stream) {
+  if (!ctx) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+  if (n < 0 || (n > 0 && (!x || !y))) return set_err(c, GP_ERR_ARG, "bad exp2 arguments");
+  if (mode != GP_EXP_POLY && mode != GP_EXP_HW) return set_err(c, GP_ERR_ARG, "bad exp mode");
+  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  launch_exp2_eval(x, y, n, mode, (cudaStream_t)stream);
+  return cuda_err(c, cudaGetLastError(), "exp2 eval");
+}
+
+gp_status gp_voxelize(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, float* vol, void* stream) {
+  if (!ctx) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+  GP_TRY(check_set(c, set));
+  if (!vol) return set_err(c, GP_ERR_ARG, "vol is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  VoxArgs a;
+  uint32_t P = 0;
+  const uint32_t* vals = nullptr;
+  GP_TRY(bin_voxels(c, set, X, Y, Z, st, &a, &P, &vals));
+  if (P == 0) {
+    GP_CUDA(c, cudaMemsetAsync(vol, 0, (size_t)X * Y * Z * 4, st), "clear vol");
+    return GP_OK;
+  }
+  GP_CUDA(c, launch_vox_fwd(a, (const VoxRec*)c->b.rec.ptr, vals, (const uint32_t*)c->b.emit_gid.ptr,
+                            (const uint2*)c->b.ranges.ptr, vol, st),
+          "voxelize forward");
+  return GP_OK;
+}
+
+gp_status gp_voxelize_backward(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, const float* dL_dV,
+                               float* d_mu, float* d_scale, float* d_quat, float* d_alpha, void* stream) {
+  if (!ctx) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+  GP_TRY(check_set(c, set));
+  const int n = (int)set->n;
+  GP_TRY(check_grads(c, n, d_mu, d_scale, d_quat, d_alpha));
+  if (!dL_dV) return set_err(c, GP_ERR_ARG, "dL_dV is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  VoxArgs a;
+  uint32_t P = 0;
+  const uint32_t* vals = nullptr;
+  GP_TRY(bin_voxels(c, set, X, Y, Z, st, &a, &P, &vals));
+  if (n == 0) return GP_OK;
+  BinBufs& b = c->b;
+  GP_TRY(ws_reserve(c, b.accum, (size_t)n * 10 * 4));
+  const bool det = c->cfg.deterministic != 0;
+  if (det) GP_TRY(ws_reserve(c, b.partial, (size_t)std::max<uint32_t>(P, 1) * 48));
+  else GP_CUDA(c, cudaMemsetAsync(b.accum.ptr, 0, (size_t)n * 10 * 4, st), "clear accumulators");
+  if (P > 0)
+    GP_CUDA(c, launch_vox_bwd(a, det, (const VoxRec*)b.rec.ptr, vals, (const uint32_t*)b.emit_gid.ptr,
+                              (const uint2*)b.ranges.ptr, dL_dV, (float*)b.accum.ptr, (float4*)b.partial.ptr, st),
+            "voxelize backward");
+  if (det)
+    launch_vox_det_reduce(n, (const unsigned long long*)b.offsets.ptr, (const unsigned long long*)b.counts.ptr,
+                          (const float4*)b.partial.ptr, (float*)b.accum.ptr, st);
+  launch_vox_bwd_pre(a, (const float*)b.accum.ptr, d_mu, d_scale, d_quat, d_alpha, st);
+  return cuda_err(c, cudaGetLastError(), "voxelize backward kernels");
+}
+
+}  // extern "C"

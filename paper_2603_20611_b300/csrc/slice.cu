@@ -1,0 +1,696 @@
+// slice.cu -- sm_103a kernels of the finite-thickness slice projection operator
+// (GaussianPile, arXiv 2603.20611, Sec. 4.2 Eq. 6-10 forward, Sec. 4.3 backward).
+//
+// Closed form used on the device.  For slice axis c with in-plane axes p and a
+// plane at z_s, the paper's inverse-covariance update (Eq. 6), opacity
+// modulation (Eq. 7) and marginal (Eq. 8) reduce, by the Sherman-Morrison
+// identity, to
+//     v = Sigma_cc + sigma_z^2,  a = Sigma_pc / v,
+//     Sigma_2d = Sigma_pp - Sigma_pc Sigma_cp / v,                 (slice-invariant)
+//     mu_2d = mu_p - a delta,  opacity_r = exp(-delta^2 / 2v),     delta = mu_c - z_s,
+// and a~ = alpha opacity_r / sqrt(det Sigma_2d) (Eq. 9).  So one 64-byte record
+// per Gaussian (K-pre) serves every slice; per (Gaussian, slice) only mu_2d and
+// a~ change, and each Gaussian touches a contiguous run of planes
+// |delta| <= sqrt(2 v ln(1/eps)).
+//
+// Pipeline of one render:
+//   K-pre     per Gaussian: record + number of (slice, tile) pairs it touches
+//   scan      exclusive scan of the counts (sort.cu)
+//   K-emit    keys (slice * T + tile) with emission indices as values
+//   sort      stable radix sort on the live key bits (sort.cu)
+//   K-range   [start, end) of every (slice, tile)
+//   K-fwd     one CTA per (slice, tile): stage the tile's Gaussians in shared
+//             memory with 16-byte loads, every thread accumulates PX pixels of
+//             a row (Eq. 10)
+// Backward (no per-pixel state is stored; lists are rebuilt):
+//   K-bwd     per (slice, tile): recompute each exponential, form six pixel
+//             moments per Gaussian, warp-shuffle reduce them, combine the warps
+//             in a fixed order, then either atomically fold them into ten
+//             per-Gaussian accumulators or write per-pair partials
+//   K-det     (deterministic mode) ordered per-Gaussian reduction of partials
+//   K-bwd-pre accumulators -> dL/d(mu, scale, quat, alpha) in closed form
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "gp_common.cuh"
+#include "slice.cuh"
+
+namespace gp {
+
+constexpr int PRE_THREADS = 256;
+
+// ------------------------------------------------------------ K-pre
+__device__ __forceinline__ int lower_bound_f(const float* __restrict__ v, int n, float x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (v[m] < x) lo = m + 1; else hi = m;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int upper_bound_f(const float* __restrict__ v, int n, float x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (v[m] <= x) lo = m + 1; else hi = m;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int clamp_tile(float t, int nt) {
+  // t is a (possibly huge) tile coordinate; clamp in float first
+  t = fminf(fmaxf(t, -1.0f), (float)nt);
+  return (int)floorf(t);
+}
+
+// Visits every (sorted slice position j, tile) pair of one Gaussian: planes with
+// |mu_z - z_s| <= zr, tiles whose pixel-centre rectangle the ellipse
+// d^T C d <= k2 around mu_2d touches.  Arithmetic uses explicit rounding so every
+// caller takes identical decisions.
+template <class F>
+__device__ __forceinline__ void for_each_pair(const SliceArgs& a, const SliceRec& r, F&& f) {
+  if (r.r3.y == 0.0f) return;
+  const float mz = r.r0.z, zr = r.r1.w;
+  const int lo = lower_bound_f(a.zs, a.S, __fsub_rn(mz, zr));
+  const int hi = upper_bound_f(a.zs, a.S, __fadd_rn(mz, zr));
+  const float rx = r.r2.w, ry = r.r3.x;
+  const float inv_tile = 1.0f / (float)a.tile;
+  for (int j = lo; j < hi; ++j) {
+    float d = __fsub_rn(mz, a.zs[j]);
+    float mx = __fsub_rn(r.r0.x, __fmul_rn(r.r1.x, d));
+    float my = __fsub_rn(r.r0.y, __fmul_rn(r.r1.y, d));
+    int tx0 = max(0, clamp_tile(__fmul_rn(__fsub_rn(__fsub_rn(mx, rx), 0.5f), inv_tile), a.TX));
+    int tx1 = min(a.TX - 1, clamp_tile(__fmul_rn(__fsub_rn(__fadd_rn(mx, rx), 0.5f), inv_tile), a.TX));
+    int ty0 = max(0, clamp_tile(__fmul_rn(__fsub_rn(__fsub_rn(my, ry), 0.5f), inv_tile), a.TY));
+    int ty1 = min(a.TY - 1, clamp_tile(__fmul_rn(__fsub_rn(__fadd_rn(my, ry), 0.5f), inv_tile), a.TY));
+    for (int ty = ty0; ty <= ty1; ++ty) {
+      float y0 = (float)(ty * a.tile) + 0.5f;
+      float y1 = (float)(min((ty + 1) * a.tile, a.H)) - 0.5f;
+      for (int tx = tx0; tx <= tx1; ++tx) {
+        float x0 = (float)(tx * a.tile) + 0.5f;
+        float x1 = (float)(min((tx + 1) * a.tile, a.W)) - 0.5f;
+        if (ellipse_hits_rect(mx, my, r.r2.x, r.r2.y, r.r2.z, a.k2, x0, x1, y0, y1)) f(j, ty * a.TX + tx);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(PRE_THREADS) k_slice_pre(SliceArgs a, SliceRec* __restrict__ rec,
+                                                           unsigned long long* __restrict__ counts) {
+  int i = blockIdx.x * PRE_THREADS + threadIdx.x;
+  if (i >= a.n) return;
+  float4 q = reinterpret_cast<const float4*>(a.quat)[i];
+  float R[3][3], qn[4], qnorm;
+  quat_rot(q, R, qn, qnorm);
+  float d3[3] = {a.mod * a.scale[3 * i], a.mod * a.scale[3 * i + 1], a.mod * a.scale[3 * i + 2]};
+  float M[3][3], Sw[6];
+  covariance(R, d3, M, Sw);
+  // camera frame (axis permutation): Sc[u][w] = Sigma[perm u][perm w]
+  const int p0 = axis_perm(a.axis, 0), p1 = axis_perm(a.axis, 1), p2 = axis_perm(a.axis, 2);
+  float cxx = Sw[sym_index(p0, p0)], cxy = Sw[sym_index(p0, p1)], cxz = Sw[sym_index(p0, p2)];
+  float cyy = Sw[sym_index(p1, p1)], cyz = Sw[sym_index(p1, p2)], czz = Sw[sym_index(p2, p2)];
+  float mux = a.mu[3 * i + p0], muy = a.mu[3 * i + p1], muz = a.mu[3 * i + p2];
+  float v = czz + a.sigma2;
+  float iv = 1.0f / v;
+  float ax = cxz * iv, ay = cyz * iv;
+  float sxx = cxx - cxz * ax, sxy = cxy - cxz * ay, syy = cyy - cyz * ay;
+  float det = sxx * syy - sxy * sxy;
+  bool valid = det > 1e-30f && isfinite(det) && isfinite(v) && isfinite(mux) && isfinite(muy) &&
+               isfinite(muz) && qnorm > 0.0f && isfinite(a.alpha[i]);
+  float idet = 1.0f / det;
+  SliceRec r;
+  r.r0 = make_float4(mux, muy, muz, iv);
+  r.r1 = make_float4(ax, ay, a.alpha[i] / sqrtf(det), sqrtf(a.k2 * v));
+  r.r2 = make_float4(syy * idet, -sxy * idet, sxx * idet, sqrtf(a.k2 * sxx));
+  r.r3 = make_float4(sqrtf(a.k2 * syy), valid ? 1.0f : 0.0f, 0.0f, 0.0f);
+  rec[i] = r;
+  unsigned long long cnt = 0;
+  for_each_pair(a, r, [&](int, int) { ++cnt; });
+  counts[i] = cnt;
+}
+
+void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
+  if (a.n <= 0) return;
+  k_slice_pre<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, counts);
+}
+
+// ------------------------------------------------------------ K-emit
+__global__ void __launch_bounds__(PRE_THREADS) k_slice_emit(SliceArgs a, const SliceRec* __restrict__ rec,
+                                                            const unsigned long long* __restrict__ offsets,
+                                                            uint32_t* __restrict__ keys,
+                                                            uint32_t* __restrict__ vals,
+                                                            uint32_t* __restrict__ emit_gid) {
+  int i = blockIdx.x * PRE_THREADS + threadIdx.x;
+  if (i >= a.n) return;
+  SliceRec r = rec[i];
+  uint32_t e = (uint32_t)offsets[i];
+  const uint32_t T = (uint32_t)(a.TX * a.TY);
+  for_each_pair(a, r, [&](int j, int tile) {
+    uint32_t s = (uint32_t)a.zorder[j];
+    keys[e] = s * T + (uint32_t)tile;
+    vals[e] = e;
+    emit_gid[e] = (uint32_t)i;
+    ++e;
+  });
+}
+
+void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* offsets,
+                       uint32_t* keys, uint32_t* vals, uint32_t* emit_gid, cudaStream_t st) {
+  if (a.n <= 0) return;
+  k_slice_emit<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, offsets, keys, vals, emit_gid);
+}
+
+// ------------------------------------------------------------ K-range
+__global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long long* __restrict__ n_dev,
+                         uint32_t cap, uint2* __restrict__ ranges) {
+  unsigned long long nn = *n_dev;
+  uint32_t n = nn < cap ? (uint32_t)nn : cap;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t k = keys[i];
+    if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
+    if (i + 1 == n || keys[i + 1] != k) ranges[k].y = i + 1;
+  }
+}
+
+void launch_ranges(const uint32_t* keys, const unsigned long long* n_dev, uint32_t cap, uint2* ranges,
+                   cudaStream_t st) {
+  if (cap == 0) return;
+  int blocks = (int)std::min<int64_t>(((int64_t)cap + 255) / 256, 148 * 16);
+  k_ranges<<<blocks, 256, 0, st>>>(keys, n_dev, cap, ranges);
+}
+
+// ------------------------------------------------------------ K-fwd
+constexpr int FWD_CHUNK = 256;
+
+// Per-(tile, slice) staging of one Gaussian: mu_2d relative to the tile origin
+// (exact subtraction of the integer origin keeps pixel offsets accurate to a
+// few 1e-7 px even 1000 px from the origin), a~, and the conic pre-scaled so
+// that the exponent is already in base 2: e = c0 dx^2 + c1 dx dy + c2 dy^2.
+//   s0 = (mu_2d,x - x0, mu_2d,y - y0, a~, C01),  s1 = (c0, c1, c2, C00)
+template <int EXPM>
+__device__ __forceinline__ void stage_gaussian(const SliceRec* __restrict__ rec, uint32_t g, float zsv,
+                                               float x0, float y0, float4& s0, float4& s1, float& d,
+                                               float& w, float& c11) {
+  const float4* rp = reinterpret_cast<const float4*>(rec + g);
+  float4 r0 = __ldg(rp), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2);
+  d = r0.z - zsv;
+  w = exp2_sel<EXPM>(fmaxf(-0.5f * kLog2e * d * d * r0.w, kExpFloor));
+  float mxr = (r0.x - x0) - r1.x * d;
+  float myr = (r0.y - y0) - r1.y * d;
+  s0 = make_float4(mxr, myr, r1.z * w, r2.y);
+  s1 = make_float4(-0.5f * kLog2e * r2.x, -kLog2e * r2.y, -0.5f * kLog2e * r2.z, r2.x);
+  c11 = r2.z;
+}
+
+template <int TILE, int PX, int EXPM>
+__global__ void __launch_bounds__(TILE* TILE / PX) k_raster_fwd(SliceArgs a, const SliceRec* __restrict__ rec,
+                                                               const uint32_t* __restrict__ vals,
+                                                               const uint32_t* __restrict__ emit_gid,
+                                                               const uint2* __restrict__ ranges,
+                                                               float* __restrict__ out) {
+  constexpr int NT = TILE * TILE / PX;
+  constexpr int SEGS = TILE / PX;
+  __shared__ float4 s0[FWD_CHUNK], s1[FWD_CHUNK];
+  const int T = a.TX * a.TY;
+  const int tile_id = blockIdx.x;
+  const int s = tile_id / T, t = tile_id - s * T;
+  const int ty = t / a.TX, tx = t - ty * a.TX;
+  const uint2 rg = ranges[tile_id];
+  const int row = threadIdx.x / SEGS, seg = threadIdx.x - row * SEGS;
+  const float pyr = (float)row + 0.5f;
+  const float px0 = (float)(seg * PX) + 0.5f;
+  const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
+  const float zsv = a.zorig[s];
+  float acc[PX];
+#pragma unroll
+  for (int p = 0; p < PX; ++p) acc[p] = 0.0f;
+  for (uint32_t base = rg.x; base < rg.y; base += FWD_CHUNK) {
+    const int cnt = (int)min((uint32_t)FWD_CHUNK, rg.y - base);
+    for (int j = threadIdx.x; j < cnt; j += NT) {
+      uint32_t g = emit_gid[vals[base + j]];
+      float d, w, c11;
+      float4 a0, a1;
+      stage_gaussian<EXPM>(rec, g, zsv, x0, y0, a0, a1, d, w, c11);
+      s0[j] = a0;
+      s1[j] = a1;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int j = 0; j < cnt; ++j) {
+      const float4 g0 = s0[j], g1 = s1[j];
+      const float dy = pyr - g0.y;
+      const float u = g1.y * dy;
+      const float wy = g1.z * dy * dy;
+#pragma unroll
+      for (int p = 0; p < PX; ++p) {
+        float dx = (px0 + (float)p) - g0.x;
+        float e = fmaf(dx, fmaf(g1.x, dx, u), wy);
+        e = fmaxf(e, kExpFloor);
+        acc[p] = fmaf(g0.z, exp2_sel<EXPM>(e), acc[p]);
+      }
+    }
+    __syncthreads();
+  }
+  const int py = ty * TILE + row;
+  if (py < a.H) {
+    float* o = out + ((int64_t)s * a.H + py) * a.W + tx * TILE + seg * PX;
+#pragma unroll
+    for (int p = 0; p < PX; ++p)
+      if (tx * TILE + seg * PX + p < a.W) o[p] = acc[p];
+  }
+}
+
+template <int TILE, int PX>
+static cudaError_t fwd_dispatch(const SliceArgs& a, int exp_mode, const SliceRec* rec, const uint32_t* vals,
+                                const uint32_t* emit_gid, const uint2* ranges, float* out, cudaStream_t st) {
+  int64_t tiles = (int64_t)a.S * a.TX * a.TY;
+  if (tiles == 0) return cudaSuccess;
+  constexpr int NT = TILE * TILE / PX;
+  if (exp_mode == GP_EXP_HW)
+    k_raster_fwd<TILE, PX, GP_EXP_HW><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, out);
+  else
+    k_raster_fwd<TILE, PX, GP_EXP_POLY><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, out);
+  return cudaGetLastError();
+}
+
+bool fwd_px_supported(int tile, int px) {
+  return tile == 16 ? (px == 1 || px == 2 || px == 4) : (tile == 8 ? (px == 1 || px == 2) : false);
+}
+
+cudaError_t launch_raster_fwd(const SliceArgs& a, int px, int exp_mode, const SliceRec* rec,
+                              const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
+                              float* out, cudaStream_t st) {
+  if (a.tile == 16) {
+    switch (px) {
+      case 1: return fwd_dispatch<16, 1>(a, exp_mode, rec, vals, emit_gid, ranges, out, st);
+      case 2: return fwd_dispatch<16, 2>(a, exp_mode, rec, vals, emit_gid, ranges, out, st);
+      case 4: return fwd_dispatch<16, 4>(a, exp_mode, rec, vals, emit_gid, ranges, out, st);
+      default: return cudaErrorInvalidValue;
+    }
+  } else if (a.tile == 8) {
+    switch (px) {
+      case 1: return fwd_dispatch<8, 1>(a, exp_mode, rec, vals, emit_gid, ranges, out, st);
+      case 2: return fwd_dispatch<8, 2>(a, exp_mode, rec, vals, emit_gid, ranges, out, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------ K-bwd
+// Accumulator layout, 10 floats per Gaussian (sums over its slices s):
+//   0,1  S1 = sum dL/dmu_2d            2,3  S2 = sum delta dL/dmu_2d
+//   4    T0 = sum dL/da~ w             5    T1 = sum dL/da~ w delta
+//   6    T2 = sum dL/da~ w delta^2     7..9 sum dL/dC (C00, C01 as one symmetric
+//                                           parameter, C11), C = Sigma_2d^-1
+// with w = opacity_r of the slice.
+constexpr int ACC = 10;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int TILE, int PX, int EXPM, bool DET>
+__global__ void __launch_bounds__(TILE* TILE / PX) k_raster_bwd(
+    SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges,
+    const float* __restrict__ dL_dI, float* __restrict__ accum, float4* __restrict__ partial) {
+  constexpr int NT = TILE * TILE / PX;
+  constexpr int SEGS = TILE / PX;
+  constexpr int NW = NT / 32;
+  constexpr int CH = (NW >= 8) ? 64 : (NW >= 4 ? 128 : 256);
+  __shared__ float4 s0[CH], s1[CH];
+  __shared__ float4 s2[CH];            // (delta, w, C11, 0)
+  __shared__ uint32_t sg[CH];          // Gaussian id
+  __shared__ float sp[NW][6][CH];      // per-warp moments
+  const int T = a.TX * a.TY;
+  const int tile_id = blockIdx.x;
+  const int s = tile_id / T, t = tile_id - s * T;
+  const int ty = t / a.TX, tx = t - ty * a.TX;
+  const uint2 rg = ranges[tile_id];
+  if (rg.y <= rg.x) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = threadIdx.x / SEGS, seg = threadIdx.x - row * SEGS;
+  const float pyr = (float)row + 0.5f;
+  const float px0 = (float)(seg * PX) + 0.5f;
+  const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
+  const float zsv = a.zorig[s];
+  float G[PX];
+  {
+    const int py = ty * TILE + row;
+#pragma unroll
+    for (int p = 0; p < PX; ++p) {
+      const int px = tx * TILE + seg * PX + p;
+      G[p] = (py < a.H && px < a.W) ? dL_dI[((int64_t)s * a.H + py) * a.W + px] : 0.0f;
+    }
+  }
+  for (uint32_t base = rg.x; base < rg.y; base += CH) {
+    const int cnt = (int)min((uint32_t)CH, rg.y - base);
+    for (int j = threadIdx.x; j < cnt; j += NT) {
+      uint32_t g = emit_gid[vals[base + j]];
+      float d, w, c11;
+      float4 a0, a1;
+      stage_gaussian<EXPM>(rec, g, zsv, x0, y0, a0, a1, d, w, c11);
+      s0[j] = a0;
+      s1[j] = a1;
+      s2[j] = make_float4(d, w, c11, 0.0f);
+      sg[j] = g;
+    }
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+      const float4 g0 = s0[j], g1 = s1[j];
+      const float dy = pyr - g0.y;
+      const float u = g1.y * dy;
+      const float wy = g1.z * dy * dy;
+      float m0 = 0.f, mx = 0.f, mxx = 0.f;
+#pragma unroll
+      for (int p = 0; p < PX; ++p) {
+        float dx = (px0 + (float)p) - g0.x;
+        float e = fmaf(dx, fmaf(g1.x, dx, u), wy);
+        e = fmaxf(e, kExpFloor);
+        float gE = G[p] * exp2_sel<EXPM>(e);
+        m0 += gE;
+        float tdx = gE * dx;
+        mx += tdx;
+        mxx = fmaf(tdx, dx, mxx);
+      }
+      // row moments -> the six moments of this lane
+      float v0 = m0, v1 = mx, v2 = m0 * dy, v3 = mxx, v4 = mx * dy, v5 = v2 * dy;
+      v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
+      v3 = warp_sum(v3); v4 = warp_sum(v4); v5 = warp_sum(v5);
+      if (lane == 0) {
+        sp[warp][0][j] = v0; sp[warp][1][j] = v1; sp[warp][2][j] = v2;
+        sp[warp][3][j] = v3; sp[warp][4][j] = v4; sp[warp][5][j] = v5;
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += NT) {
+      float m[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        float acc = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) acc += sp[w][k][j];
+        m[k] = acc;
+      }
+      const float4 g0 = s0[j], g1 = s1[j];
+      const float4 dw = s2[j];
+      const float at = g0.z;  // a~
+      const float C01 = g0.w, C00 = g1.w, C11 = dw.z;
+      // pixel moments: m0 = sum G E, m1 = sum G E dx, m2 = sum G E dy,
+      //                m3 = sum G E dx^2, m4 = sum G E dx dy, m5 = sum G E dy^2
+      // dE/dmu_2d = E C d, dE/dC00 = -E dx^2 / 2, dE/dC01 = -E dx dy, dE/dC11 = -E dy^2 / 2
+      const float g_at = m[0];
+      const float gmx = at * (C00 * m[1] + C01 * m[2]);
+      const float gmy = at * (C01 * m[1] + C11 * m[2]);
+      const float gc00 = -0.5f * at * m[3];
+      const float gc01 = -at * m[4];
+      const float gc11 = -0.5f * at * m[5];
+      if constexpr (DET) {
+        uint32_t e = vals[base + j];
+        partial[2 * (size_t)e] = make_float4(g_at, gmx, gmy, gc00);
+        partial[2 * (size_t)e + 1] = make_float4(gc01, gc11, dw.x, dw.y);
+      } else {
+        float* A = accum + (size_t)sg[j] * ACC;
+        const float d = dw.x, w = dw.y;
+        const float gw = g_at * w;
+        atomicAdd(A + 0, gmx);
+        atomicAdd(A + 1, gmy);
+        atomicAdd(A + 2, d * gmx);
+        atomicAdd(A + 3, d * gmy);
+        atomicAdd(A + 4, gw);
+        atomicAdd(A + 5, gw * d);
+        atomicAdd(A + 6, gw * d * d);
+        atomicAdd(A + 7, gc00);
+        atomicAdd(A + 8, gc01);
+        atomicAdd(A + 9, gc11);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int TILE, int PX>
+static cudaError_t bwd_dispatch(const SliceArgs& a, int exp_mode, bool det, const SliceRec* rec,
+                                const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
+                                const float* dL_dI, float* accum, float4* partial, cudaStream_t st) {
+  int64_t tiles = (int64_t)a.S * a.TX * a.TY;
+  if (tiles == 0) return cudaSuccess;
+  constexpr int NT = TILE * TILE / PX;
+  unsigned g = (unsigned)tiles;
+  if (exp_mode == GP_EXP_HW) {
+    if (det) k_raster_bwd<TILE, PX, GP_EXP_HW, true><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, dL_dI, accum, partial);
+    else k_raster_bwd<TILE, PX, GP_EXP_HW, false><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, dL_dI, accum, partial);
+  } else {
+    if (det) k_raster_bwd<TILE, PX, GP_EXP_POLY, true><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, dL_dI, accum, partial);
+    else k_raster_bwd<TILE, PX, GP_EXP_POLY, false><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, dL_dI, accum, partial);
+  }
+  return cudaGetLastError();
+}
+
+bool bwd_px_supported(int tile, int px) {
+  return tile == 16 ? (px == 2 || px == 4 || px == 8) : (tile == 8 ? px == 2 : false);
+}
+
+cudaError_t launch_raster_bwd(const SliceArgs& a, int px, int exp_mode, bool det, const SliceRec* rec,
+                              const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
+                              const float* dL_dI, float* accum, float4* partial, cudaStream_t st) {
+  if (a.tile == 16) {
+    switch (px) {
+      case 2: return bwd_dispatch<16, 2>(a, exp_mode, det, rec, vals, emit_gid, ranges, dL_dI, accum, partial, st);
+      case 4: return bwd_dispatch<16, 4>(a, exp_mode, det, rec, vals, emit_gid, ranges, dL_dI, accum, partial, st);
+      case 8: return bwd_dispatch<16, 8>(a, exp_mode, det, rec, vals, emit_gid, ranges, dL_dI, accum, partial, st);
+      default: return cudaErrorInvalidValue;
+    }
+  } else if (a.tile == 8) {
+    switch (px) {
+      case 2: return bwd_dispatch<8, 2>(a, exp_mode, det, rec, vals, emit_gid, ranges, dL_dI, accum, partial, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------ K-det
+__global__ void k_det_reduce(int n, const unsigned long long* __restrict__ offsets,
+                             const unsigned long long* __restrict__ counts,
+                             const float4* __restrict__ partial, float* __restrict__ accum) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float A[ACC];
+#pragma unroll
+  for (int k = 0; k < ACC; ++k) A[k] = 0.f;
+  unsigned long long e0 = offsets[i], e1 = e0 + counts[i];
+  for (unsigned long long e = e0; e < e1; ++e) {
+    float4 p0 = partial[2 * e], p1 = partial[2 * e + 1];
+    const float g_at = p0.x, gmx = p0.y, gmy = p0.z, gc00 = p0.w, gc01 = p1.x, gc11 = p1.y;
+    const float d = p1.z, w = p1.w, gw = g_at * w;
+    A[0] += gmx; A[1] += gmy; A[2] += d * gmx; A[3] += d * gmy;
+    A[4] += gw; A[5] += gw * d; A[6] += gw * d * d;
+    A[7] += gc00; A[8] += gc01; A[9] += gc11;
+  }
+#pragma unroll
+  for (int k = 0; k < ACC; ++k) accum[(size_t)i * ACC + k] = A[k];
+}
+
+void launch_det_reduce(int n, const unsigned long long* offsets, const unsigned long long* counts,
+                       const float4* partial, float* accum, cudaStream_t st) {
+  if (n <= 0) return;
+  k_det_reduce<<<ceil_div(n, 256), 256, 0, st>>>(n, offsets, counts, partial, accum);
+}
+
+// ------------------------------------------------------------ K-bwd-pre
+// Closed-form chain from the ten accumulators to the parameters:
+//   dL/dmu_p = S1,  dL/da = -S2,  dL/dmu_c = -a.S1 - A T1 / v,
+//   dL/dA = T0 (dL/dalpha = T0 / sqrt(det)),  dL/ddet = -T0 A / (2 det),
+//   dL/dv |_w = A T2 / (2 v^2),
+//   dL/dSigma_2d = -C Gc C + dL/ddet det C   (Gc = symmetric dL/dC),
+//   Sigma_2d = Sigma_pp - b b^T / v, a = b / v, v = Sigma_cc + sigma_z^2, b = Sigma_pc,
+//   Sigma = M M^T, M = R diag(mod s), R = R(q/|q|).
+__global__ void __launch_bounds__(PRE_THREADS) k_slice_bwd_pre(SliceArgs a, const float* __restrict__ accum,
+                                                               float* __restrict__ d_mu,
+                                                               float* __restrict__ d_scale,
+                                                               float* __restrict__ d_quat,
+                                                               float* __restrict__ d_alpha) {
+  int i = blockIdx.x * PRE_THREADS + threadIdx.x;
+  if (i >= a.n) return;
+  float acc[ACC];
+#pragma unroll
+  for (int k = 0; k < ACC; ++k) acc[k] = accum[(size_t)i * ACC + k];
+  float4 q = reinterpret_cast<const float4*>(a.quat)[i];
+  float R[3][3], qn[4], qnorm;
+  quat_rot(q, R, qn, qnorm);
+  float dd[3] = {a.mod * a.scale[3 * i], a.mod * a.scale[3 * i + 1], a.mod * a.scale[3 * i + 2]};
+  float M[3][3], Sw[6];
+  covariance(R, dd, M, Sw);
+  const int p[3] = {axis_perm(a.axis, 0), axis_perm(a.axis, 1), axis_perm(a.axis, 2)};
+  float cxx = Sw[sym_index(p[0], p[0])], cxy = Sw[sym_index(p[0], p[1])], cxz = Sw[sym_index(p[0], p[2])];
+  float cyy = Sw[sym_index(p[1], p[1])], cyz = Sw[sym_index(p[1], p[2])], czz = Sw[sym_index(p[2], p[2])];
+  float v = czz + a.sigma2, iv = 1.0f / v;
+  float ax = cxz * iv, ay = cyz * iv;
+  float sxx = cxx - cxz * ax, sxy = cxy - cxz * ay, syy = cyy - cyz * ay;
+  float det = sxx * syy - sxy * sxy;
+  bool valid = det > 1e-30f && isfinite(det) && qnorm > 0.0f;
+  float gmu[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, galpha = 0.f;
+  if (valid) {
+    float idet = 1.0f / det, sq = sqrtf(det);
+    float A = a.alpha[i] / sq;
+    float C00 = syy * idet, C01 = -sxy * idet, C11 = sxx * idet;
+    const float S1x = acc[0], S1y = acc[1], S2x = acc[2], S2y = acc[3];
+    const float T0 = acc[4], T1 = acc[5], T2 = acc[6];
+    const float G00 = acc[7], G01 = 0.5f * acc[8], G11 = acc[9];
+    galpha = T0 / sq;
+    float gdet = -0.5f * T0 * A * idet;
+    // dL/dSigma_2d = -C Gc C + gdet det C  (symmetric)
+    float CG00 = C00 * G00 + C01 * G01, CG01 = C00 * G01 + C01 * G11;
+    float CG10 = C01 * G00 + C11 * G01, CG11 = C01 * G01 + C11 * G11;
+    float H00 = -(CG00 * C00 + CG01 * C01) + gdet * det * C00;
+    float H01 = -(CG00 * C01 + CG01 * C11) + gdet * det * C01;
+    float H11 = -(CG10 * C01 + CG11 * C11) + gdet * det * C11;
+    float gax = -S2x, gay = -S2y;
+    float Hbx = H00 * cxz + H01 * cyz, Hby = H01 * cxz + H11 * cyz;
+    float gv = A * T2 * iv * iv * 0.5f + (cxz * Hbx + cyz * Hby) * iv * iv - (gax * cxz + gay * cyz) * iv * iv;
+    float gbx = -2.0f * Hbx * iv + gax * iv, gby = -2.0f * Hby * iv + gay * iv;
+    float gmc[3] = {S1x, S1y, -(ax * S1x + ay * S1y) - A * iv * T1};
+    // camera-frame symmetric gradient -> world (inverse axis permutation)
+    float Gc[3][3] = {{H00, H01, 0.5f * gbx}, {H01, H11, 0.5f * gby}, {0.5f * gbx, 0.5f * gby, gv}};
+    float Gw[3][3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      gmu[p[u]] = gmc[u];
+#pragma unroll
+      for (int w = 0; w < 3; ++w) Gw[p[u]][p[w]] = Gc[u][w];
+    }
+    scale_quat_backward(R, M, dd, qn, qnorm, a.mod, Gw, gs, gq);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    d_mu[3 * i + k] = gmu[k];
+    d_scale[3 * i + k] = gs[k];
+  }
+  reinterpret_cast<float4*>(d_quat)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+  d_alpha[i] = galpha;
+}
+
+void launch_slice_bwd_pre(const SliceArgs& a, const float* accum, float* d_mu, float* d_scale,
+                          float* d_quat, float* d_alpha, cudaStream_t st) {
+  if (a.n <= 0) return;
+  k_slice_bwd_pre<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, accum, d_mu, d_scale, d_quat,
+                                                                      d_alpha);
+}
+
+// ------------------------------------------------------------ K-loss
+constexpr int MSE_THREADS = 256;
+constexpr int MSE_ITEMS = 8;
+
+__global__ void __launch_bounds__(MSE_THREADS) k_mse(const float* __restrict__ I, const float* __restrict__ T,
+                                                     const int* __restrict__ t_index, int64_t HW, int bpsl,
+                                                     float scale, float* __restrict__ g,
+                                                     float* __restrict__ part) {
+  __shared__ float sw[MSE_THREADS / 32];
+  const int s = blockIdx.x / bpsl, b = blockIdx.x - s * bpsl;
+  const int64_t ts = t_index ? (int64_t)t_index[s] : (int64_t)s;
+  const float* Is = I + (int64_t)s * HW;
+  const float* Ts = T + ts * HW;
+  float* gs = g + (int64_t)s * HW;
+  float acc = 0.f;
+  for (int64_t i = (int64_t)b * MSE_THREADS + threadIdx.x; i < HW; i += (int64_t)bpsl * MSE_THREADS) {
+    float r = Is[i] - Ts[i];
+    gs[i] = 2.0f * r * scale;
+    acc = fmaf(r, r, acc);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < MSE_THREADS / 32; ++w) t += sw[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_mse_final(const float* __restrict__ part, int nb, float scale, float* __restrict__ loss) {
+  __shared__ float sw[32];
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += part[i];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += sw[w];
+    *loss = t * scale;
+  }
+}
+
+static int mse_blocks_per_slice(int64_t HW) {
+  int64_t b = (HW + (int64_t)MSE_THREADS * MSE_ITEMS - 1) / ((int64_t)MSE_THREADS * MSE_ITEMS);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 4096));
+}
+
+int mse_tmp_floats(int S, int64_t HW) { return S * mse_blocks_per_slice(HW); }
+
+void launch_mse(const float* I, const float* T, const int* t_index, int S, int64_t HW, float* dL_dI,
+                float* loss, float* tmp, cudaStream_t st) {
+  if (S <= 0 || HW <= 0) return;
+  int bpsl = mse_blocks_per_slice(HW);
+  float scale = 1.0f / ((float)S * (float)HW);
+  k_mse<<<S * bpsl, MSE_THREADS, 0, st>>>(I, T, t_index, HW, bpsl, scale, dL_dI, tmp);
+  if (loss) k_mse_final<<<1, 1024, 0, st>>>(tmp, S * bpsl, scale, loss);
+}
+
+// ------------------------------------------------------------ counting
+// Pixels of one (Gaussian, slice, tile) inside d^T C d <= k2: per row, the
+// interval of dx solving the quadratic, intersected with the tile.
+__global__ void __launch_bounds__(PRE_THREADS) k_count_evals(SliceArgs a, const SliceRec* __restrict__ rec,
+                                                             unsigned long long* __restrict__ out) {
+  int i = blockIdx.x * PRE_THREADS + threadIdx.x;
+  unsigned long long cnt = 0;
+  if (i < a.n) {
+    SliceRec r = rec[i];
+    const float c00 = r.r2.x, c01 = r.r2.y, c11 = r.r2.z;
+    for_each_pair(a, r, [&](int j, int tile) {
+      float d = r.r0.z - a.zs[j];
+      float mx = r.r0.x - r.r1.x * d, my = r.r0.y - r.r1.y * d;
+      int ty = tile / a.TX, tx = tile - ty * a.TX;
+      int xa = tx * a.tile, xb = min((tx + 1) * a.tile, a.W);
+      for (int y = ty * a.tile; y < min((ty + 1) * a.tile, a.H); ++y) {
+        float dy = (float)y + 0.5f - my;
+        float disc = c01 * c01 * dy * dy - c00 * (c11 * dy * dy - a.k2);
+        if (disc < 0.f) continue;
+        float sq = sqrtf(disc);
+        float lo = mx + (-c01 * dy - sq) / c00, hi = mx + (-c01 * dy + sq) / c00;
+        // pixels x with x + 0.5 in [lo, hi]
+        int x0 = max(xa, (int)ceilf(lo - 0.5f)), x1 = min(xb - 1, (int)floorf(hi - 0.5f));
+        if (x1 >= x0) cnt += (unsigned long long)(x1 - x0 + 1);
+      }
+    });
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+}
+
+void launch_count_evals(const SliceArgs& a, const SliceRec* rec, unsigned long long* out, cudaStream_t st) {
+  if (a.n <= 0) return;
+  k_count_evals<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, out);
+}
+
+__global__ void k_exp2_eval(const float* __restrict__ x, float* __restrict__ y, int64_t n, int mode) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float v = fmaxf(x[i], kExpFloor);
+  y[i] = mode == GP_EXP_HW ? exp2_hw(v) : exp2_poly(v);
+}
+
+void launch_exp2_eval(const float* x, float* y, int64_t n, int mode, cudaStream_t st) {
+  if (n <= 0) return;
+  k_exp2_eval<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n, mode);
+}
+
+}  // namespace gp

@@ -1,0 +1,65 @@
+// slice.cuh -- launch interface of the slice-renderer kernels (slice.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gp_common.cuh"
+
+namespace gp {
+
+// Arguments shared by every slice-renderer kernel.
+struct SliceArgs {
+  const float* mu;
+  const float* scale;
+  const float* quat;
+  const float* alpha;
+  int n;
+  float mod;
+  int axis;
+  float sigma2;   // sigma_z^2
+  float k2;       // 2 ln(1/eps): squared Mahalanobis culling radius
+  const float* zs;      // [S] plane positions sorted ascending
+  const int* zorder;    // [S] slice index of sorted position j
+  const float* zorig;   // [S] plane position of slice index s
+  int S, H, W;
+  int tile, TX, TY;     // tile side and tile grid (TX * TY tiles per slice)
+};
+
+// K-pre: records + per-Gaussian pair counts.
+void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st);
+// K-emit: (slice, tile) keys, identity values, emission -> Gaussian id.
+void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* offsets,
+                       uint32_t* keys, uint32_t* vals, uint32_t* emit_gid, cudaStream_t st);
+// K-range: [start, end) of each key in the sorted key list; ranges must be zeroed.
+void launch_ranges(const uint32_t* keys, const unsigned long long* n_dev, uint32_t cap, uint2* ranges,
+                   cudaStream_t st);
+// K-fwd.
+cudaError_t launch_raster_fwd(const SliceArgs& a, int px, int exp_mode, const SliceRec* rec,
+                              const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
+                              float* out, cudaStream_t st);
+// K-bwd-raster; atomic mode adds into accum [n][10] (zeroed), deterministic mode
+// writes per-pair partials [pairs][8].
+cudaError_t launch_raster_bwd(const SliceArgs& a, int px, int exp_mode, bool deterministic,
+                              const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
+                              const uint2* ranges, const float* dL_dI, float* accum, float4* partial,
+                              cudaStream_t st);
+// K-det: per-Gaussian ordered reduction of partials into accum.
+void launch_det_reduce(int n, const unsigned long long* offsets, const unsigned long long* counts,
+                       const float4* partial, float* accum, cudaStream_t st);
+// K-bwd-pre: accumulators -> parameter gradients.
+void launch_slice_bwd_pre(const SliceArgs& a, const float* accum, float* d_mu, float* d_scale,
+                          float* d_quat, float* d_alpha, cudaStream_t st);
+// K-loss.
+void launch_mse(const float* I, const float* T, const int* t_index, int S, int64_t HW, float* dL_dI,
+                float* loss, float* tmp, cudaStream_t st);
+int mse_tmp_floats(int S, int64_t HW);
+// Algorithmic evaluation count (pixels inside the culling ellipse), added into *out.
+void launch_count_evals(const SliceArgs& a, const SliceRec* rec, unsigned long long* out,
+                        cudaStream_t st);
+void launch_exp2_eval(const float* x, float* y, int64_t n, int mode, cudaStream_t st);
+
+// Supported pixels-per-thread of the rasterisers for a tile side.
+bool fwd_px_supported(int tile, int px);
+bool bwd_px_supported(int tile, int px);
+
+}  // namespace gp

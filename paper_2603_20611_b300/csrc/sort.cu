@@ -1,0 +1,253 @@
+// sort.cu -- device-wide exclusive scan and a stable LSD radix sort of 32-bit
+// (slice, tile) keys with 32-bit values, written for sm_103a.
+//
+// The renderer's binning (the "binned to screen tiles" step of the operator)
+// needs the Gaussians of every (slice, tile) contiguous and, inside a tile, in
+// ascending emission (= Gaussian id) order so that sums are reproducible.  Keys
+// are emitted in that order, so a STABLE sort on the key alone suffices.
+//
+// Radix sort, per 8-bit digit pass:
+//   1. k_radix_hist     per 4096-key tile: 256-bin histogram (shared atomics),
+//                       stored digit-major hist[d * nb + b];
+//   2. exclusive scan   of hist -> global scatter base of (digit, tile);
+//   3. k_radix_scatter  per tile, 16 rounds of 256 keys in input order: warp
+//                       match_any gives each key its rank among equal digits in
+//                       its warp, a per-digit prefix over the 8 warps gives the
+//                       rank in the round, and a running per-digit count the rank
+//                       in the tile -> stable positions.
+// Only ceil(bits / 8) passes run; bits is the number of live key bits.
+// Counts are read from device memory (n_dev) with a host-side capacity bound on
+// the grid, so the same launches serve a preplanned (graph-captured) binning.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gp_internal.h"
+
+namespace gp {
+
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Exclusive scan of the block's per-thread values; returns the thread's prefix
+// and writes the block total to *total.
+template <typename T, int NT>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* smem_warp, T* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T inc = warp_inclusive_scan(v);
+  if (lane == 31) smem_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < NT / 32 ? smem_warp[lane] : T(0);
+    T wi = warp_inclusive_scan(w);
+    if (lane < NT / 32) smem_warp[lane] = wi - w;
+    if (lane == NT / 32 - 1) smem_warp[NT / 32] = wi;
+  }
+  __syncthreads();
+  T r = smem_warp[warp] + inc - v;
+  *total = smem_warp[NT / 32];
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const T* __restrict__ in, int64_t n,
+                                                               unsigned long long* __restrict__ part) {
+  __shared__ unsigned long long sw[SCAN_THREADS / 32 + 1];
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  unsigned long long s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int64_t i = base + (int64_t)k * SCAN_THREADS + threadIdx.x;
+    if (i < n) s += (unsigned long long)in[i];
+  }
+  unsigned long long tot;
+  block_exclusive_scan<unsigned long long, SCAN_THREADS>(s, sw, &tot);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// One block scans the per-tile partials (exclusive) and writes the grand total.
+__global__ void __launch_bounds__(1024) k_scan_partials(unsigned long long* __restrict__ part, int nb,
+                                                        unsigned long long* __restrict__ total) {
+  __shared__ unsigned long long sw[1024 / 32 + 1];
+  unsigned long long carry = 0;
+  for (int base = 0; base < nb; base += 1024) {
+    int i = base + threadIdx.x;
+    unsigned long long v = i < nb ? part[i] : 0ull;
+    unsigned long long tot;
+    unsigned long long ex = block_exclusive_scan<unsigned long long, 1024>(v, sw, &tot);
+    if (i < nb) part[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const T* __restrict__ in, T* __restrict__ out,
+                                                             int64_t n,
+                                                             const unsigned long long* __restrict__ part) {
+  __shared__ unsigned long long sw[SCAN_THREADS / 32 + 1];
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  T v[SCAN_ITEMS];
+  unsigned long long s = 0;
+  // blocked arrangement: thread t owns SCAN_ITEMS consecutive items
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int64_t i = base + k;
+    v[k] = i < n ? in[i] : T(0);
+    s += (unsigned long long)v[k];
+  }
+  unsigned long long tot;
+  unsigned long long ex = block_exclusive_scan<unsigned long long, SCAN_THREADS>(s, sw, &tot);
+  unsigned long long run = part[blockIdx.x] + ex;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int64_t i = base + k;
+    if (i < n) out[i] = (T)run;
+    run += (unsigned long long)v[k];
+  }
+}
+
+int64_t scan_temp_bytes(int64_t n) {
+  int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  return (nb + 1) * (int64_t)sizeof(unsigned long long);
+}
+
+template <typename T>
+cudaError_t exclusive_scan(const T* in, T* out, int64_t n, unsigned long long* total, void* temp,
+                           cudaStream_t st) {
+  int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  unsigned long long* part = (unsigned long long*)temp;
+  if (nb == 0) {
+    if (total) return cudaMemsetAsync(total, 0, sizeof(unsigned long long), st);
+    return cudaSuccess;
+  }
+  k_scan_reduce<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, part);
+  k_scan_partials<<<1, 1024, 0, st>>>(part, (int)nb, total);
+  k_scan_down<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, part);
+  return cudaGetLastError();
+}
+
+template cudaError_t exclusive_scan<uint32_t>(const uint32_t*, uint32_t*, int64_t, unsigned long long*,
+                                              void*, cudaStream_t);
+template cudaError_t exclusive_scan<unsigned long long>(const unsigned long long*, unsigned long long*,
+                                                        int64_t, unsigned long long*, void*, cudaStream_t);
+
+// ---------------------------------------------------------------- radix sort
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+constexpr int RS_BINS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+__device__ __forceinline__ uint32_t load_count(const unsigned long long* n_dev, uint32_t cap) {
+  unsigned long long n = *n_dev;
+  return n < cap ? (uint32_t)n : cap;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                            const unsigned long long* __restrict__ n_dev,
+                                                            uint32_t cap, int shift,
+                                                            uint32_t* __restrict__ hist, int nb) {
+  __shared__ uint32_t cnt[RS_BINS];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t n = load_count(n_dev, cap);
+  uint32_t base = blockIdx.x * RS_TILE;
+  if (base < n) {
+#pragma unroll 4
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+      uint32_t i = base + r * RS_THREADS + threadIdx.x;
+      if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 0xffu], 1u);
+    }
+  }
+  __syncthreads();
+  hist[(size_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, const unsigned long long* __restrict__ n_dev, uint32_t cap, int shift,
+    const uint32_t* __restrict__ hist, int nb) {
+  __shared__ uint32_t base_d[RS_BINS];
+  __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  uint32_t n = load_count(n_dev, cap);
+  uint32_t tile0 = blockIdx.x * RS_TILE;
+  if (tile0 >= n) return;  // uniform across the block
+  base_d[t] = hist[(size_t)t * nb + blockIdx.x];
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    uint32_t round0 = tile0 + r * RS_THREADS;
+    if (round0 >= n) break;  // uniform
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) wcnt[w][t] = 0;
+    __syncthreads();
+    uint32_t i = round0 + t;
+    bool valid = i < n;
+    uint32_t key = valid ? kin[i] : 0u;
+    uint32_t val = valid ? vin[i] : 0u;
+    uint32_t d = valid ? ((key >> shift) & 0xffu) : (RS_BINS + lane);
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    // thread t owns digit t: exclusive prefix over warps, and the round total
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) {
+      uint32_t c = wcnt[w][t];
+      wcnt[w][t] = run;
+      run += c;
+    }
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = base_d[d] + wcnt[warp][d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    base_d[t] += run;
+  }
+}
+
+int64_t radix_temp_bytes(int64_t cap) {
+  int64_t nb = (cap + RS_TILE - 1) / RS_TILE;
+  int64_t hist = (int64_t)RS_BINS * nb;
+  return ((hist * 4 + 255) / 256) * 256 + scan_temp_bytes(hist) + 64;
+}
+
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                             const unsigned long long* n_dev, uint32_t cap, int bits, void* temp,
+                             cudaStream_t st, bool* result_in_alt) {
+  *result_in_alt = false;
+  if (cap == 0 || bits <= 0) return cudaSuccess;
+  int nb = (int)((cap + RS_TILE - 1) / RS_TILE);
+  uint32_t* hist = (uint32_t*)temp;
+  int64_t nh = (int64_t)RS_BINS * nb;
+  void* stemp = (char*)temp + ((nh * 4 + 255) / 256) * 256;
+  uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_radix_hist<<<nb, RS_THREADS, 0, st>>>(ki, n_dev, cap, shift, hist, nb);
+    cudaError_t e = exclusive_scan<uint32_t>(hist, hist, nh, nullptr, stemp, st);
+    if (e != cudaSuccess) return e;
+    k_radix_scatter<<<nb, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, hist, nb);
+    uint32_t* tk = ki; ki = ko; ko = tk;
+    uint32_t* tv = vi; vi = vo; vo = tv;
+    *result_in_alt = !*result_in_alt;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gp
