@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Benchmark of the slice projection operator on the microscopy-shaped fit step.
+
+Workload (one step = the whole hot path): 500k Gaussians in a 1024 x 1024 x 256
+light-sheet-shaped volume (z-scale 3x the xy-scale, log-normal intensities),
+sigma_z = 3; each step renders a random batch of 16 of the 256 slices
+(K-pre, pair binning, radix sort, K-range, K-fwd), takes the MSE against the
+same slices of a seeded 256-slice target stack (K-loss), and runs the backward
+(re-binning, K-bwd, K-bwd-pre) to gradients of all 11 parameters per Gaussian.
+Inputs are synthetic (seeded); the target stack is rendered once, untimed,
+from a second seeded set of the same distribution.
+
+Metric: Gaussian-pixel evaluations per second, forward + backward, counting
+ALGORITHMIC evaluations (pixels inside each pair's culling ellipse,
+d^T Sigma_2d^-1 d <= 2 ln(1/eps), on slices with opacity_r >= eps), twice per
+step (forward and backward).  Also reported: slices/s, per-phase times, the
+roofline of the dominant kernel, an end-to-end figure through host buffers,
+and the FP64 oracle timed on host cores on a bounded sample.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Gaussian-pixel evals/s"
+UNIT = "evals/s"
+WORKLOAD = {"workload": "microscopy fit step: 500k Gaussians, 1024x1024x256 volume, sigma_z=3, "
+                        "random batch of 16 slices per step, fwd + MSE + bwd",
+            "n_gaussians": 500_000, "slice_hw": [1024, 1024], "n_planes": 256, "slices_per_step": 16,
+            "sigma_z": 3.0, "eps": 1e-6, "l2": "flushed between steps (256 MiB write)"}
+N, H, W, DEPTH, S, SIGMA = 500_000, 1024, 1024, 256, 16, 3.0
+
+# Lane instructions of the FP32/INT pipes per ALGORITHMIC evaluation, counted from
+# the method's arithmetic with the project-written exp2 (range reduction 3 FADD,
+# degree-6 Horner 6 FFMA, exponent insert 2 INT): forward = offset 1 + quadratic
+# form 2 + clamp 1 + exp2 11 + accumulate 1; backward = the same 15 up to the
+# exponential + 5 moment updates (g = G E, 2 sums, 1 product, 1 FMA).
+OPS_PER_EVAL = {"fwd": 16, "bwd": 20}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({nm for r in rows for nm, v in zip(names, r[5:9]) if v.strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].strip().replace(".", "").isdigit())
+                if any(r[3].strip().replace(".", "").isdigit() for r in rows) else None}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return None
+
+
+def make_workload(B, synth, torch, dev, ctx):
+    g = synth.microscopy(seed=1002)
+    gs = B.GaussianSet.from_numpy(g, dev)
+    tgt = B.GaussianSet.from_numpy(synth.microscopy(seed=2002), dev)
+    target = torch.empty(DEPTH, H, W, device=dev)
+    for s0 in range(0, DEPTH, 32):
+        B.gp_render_slices(ctx, tgt, synth.slice_positions(range(s0, s0 + 32)), H, W, SIGMA,
+                           out=target[s0:s0 + 32])
+    torch.cuda.synchronize()
+    del tgt
+    return g, gs, target
+
+
+def step_batches(synth, rank, count):
+    return [synth.slice_batch(3000 + 7919 * rank + k, DEPTH, DEPTH, S) for k in range(count)]
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def oracle_step_seconds(oracle, synth, g, idx, n_px, n_gauss, seed):
+    """Seconds the FP64 oracle would take for one full step, extrapolated from a
+    bounded sample: the forward at n_px sampled pixels of the step's slices (its
+    per-slice projection of every Gaussian timed separately with one pixel per
+    slice), and the backward of n_gauss sampled Gaussians against a seeded
+    dL/dI (its brute force costs the same for every Gaussian).  Returns
+    (step seconds, sample seconds)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    z = synth.slice_positions(idx)
+    G = synth.random_field(seed + 1, (S, H, W))
+    one = np.arange(S, dtype=np.int32)
+    ps = rng.integers(0, S, n_px).astype(np.int32)
+    px = rng.integers(0, W, n_px) + 0.5
+    py = rng.integers(0, H, n_px) + 0.5
+    pick = np.sort(rng.choice(g.n, n_gauss, replace=False))
+    t0 = time.perf_counter()
+    oracle.render_points(g.mu, g.scale, g.quat, g.alpha, z, SIGMA, one, np.full(S, 0.5), np.full(S, 0.5))
+    t1 = time.perf_counter()
+    oracle.render_points(g.mu, g.scale, g.quat, g.alpha, z, SIGMA, ps, px, py)
+    t2 = time.perf_counter()
+    oracle.render_backward(g.mu[pick], g.scale[pick], g.quat[pick], g.alpha[pick], z, H, W, SIGMA, G)
+    t3 = time.perf_counter()
+    t_fixed = t1 - t0
+    per_px = max(t2 - t1 - t_fixed, 0.0) / max(n_px - S, 1)
+    step = t_fixed + per_px * S * H * W + (t3 - t2) / n_gauss * g.n
+    return step, t3 - t0
+
+
+def oracle_evals(oracle, synth, g, idx):
+    """Forward algorithmic evaluations of one step, counted by the oracle."""
+    return oracle.count_evals(g.mu, g.scale, g.quat, g.alpha, synth.slice_positions(idx), H, W, SIGMA,
+                              eps=WORKLOAD["eps"])
+
+
+def oracle_baseline(oracle, synth, g, idx, n_px, n_gauss, seed, evals_fwd):
+    step_s, sample_s = oracle_step_seconds(oracle, synth, g, idx, n_px, n_gauss, seed)
+    return {"value": 2.0 * evals_fwd / step_s, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one step's forward at {n_px} sampled pixels (+1 pixel per slice to separate the "
+                      f"per-slice projection cost) and backward of {n_gauss} sampled Gaussians, FP64 brute force, "
+                      f"{sample_s:.1f}s of CPU work, extrapolated to the full step "
+                      f"({2.0 * evals_fwd:.3e} algorithmic evaluations)"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle, timed on host cores, on bounded samples."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2603_20611_b300 import synth
+    g = synth.microscopy(seed=1002)
+    batches = step_batches(synth, 0, args.warmup + args.steps)
+    step_s, evals, sample_s = [], [], 0.0
+    for k, idx in enumerate(batches):
+        ev = oracle_evals(oracle, synth, g, idx)
+        st, ss = oracle_step_seconds(oracle, synth, g, idx, args.ref_px, args.ref_gauss, 5000 + k)
+        if k >= args.warmup:
+            step_s.append(st)
+            evals.append(2.0 * ev)
+            sample_s += ss
+    value = sum(evals) / sum(step_s)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(step_s)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": WORKLOAD, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"per step: forward at {args.ref_px} sampled pixels and backward of "
+                                       f"{args.ref_gauss} sampled Gaussians (FP64 brute force), extrapolated to "
+                                       f"the full step; {sample_s:.1f}s of CPU work in the timed steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ native arm
+
+def run_native(args, rank, world):
+    import torch
+    from paper_2603_20611_b300 import binding as B
+    from paper_2603_20611_b300 import synth
+    dev_index = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev_index)
+    dev = f"cuda:{dev_index}"
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ctx = B.Context(dev_index, exp_mode=B.GP_EXP_HW if args.exp == "hw" else B.GP_EXP_POLY,
+                    deterministic=args.det, tile=args.tile, fwd_px=args.fwd_px, bwd_px=args.bwd_px)
+    stream = torch.cuda.current_stream()
+    t_setup = time.perf_counter()
+    g, gs, target = make_workload(B, synth, torch, dev, ctx)
+    batches = step_batches(synth, rank, args.warmup + args.steps)
+    zs = [synth.slice_positions(b) for b in batches]
+    evals = [B.gp_count_evals(ctx, gs, z, H, W, SIGMA) for z in zs]
+    log(f"setup {time.perf_counter() - t_setup:.1f}s; evals/step (fwd) ~{np.mean(evals):.3e}")
+    I = torch.empty(S, H, W, device=dev)
+    G = torch.empty(S, H, W, device=dev)
+    loss = torch.zeros(1, device=dev)
+    grads = (torch.empty(N, 3, device=dev), torch.empty(N, 3, device=dev), torch.empty(N, 4, device=dev),
+             torch.empty(N, device=dev))
+    flush = torch.empty(64 * 1024 * 1024, device=dev)  # 256 MiB > 126 MB L2
+
+    def step(k):
+        B.gp_render_slices(ctx, gs, zs[k], H, W, SIGMA, out=I)
+        B.gp_mse_grad(ctx, I, target, t_index=batches[k], dL_dI=G, loss=loss)
+        B.gp_render_backward(ctx, gs, zs[k], H, W, SIGMA, G, grads=grads)
+
+    for k in range(args.warmup):
+        flush.zero_()
+        step(k)
+    torch.cuda.synchronize()
+    # FP32-pipe peak at the clocks in force (burst, just before the timed region)
+    ctx.fma_probe(2000)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    ctx.fma_probe(20000)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    n_thr = int(B.lib.gp_fma_probe_threads(ctx.h))
+    fp32_peak = n_thr * 20000 * 8 / (pe0.elapsed_time(pe1) * 1e-3)  # lane instructions / s
+
+    clocks = ClockSampler(dev_index)
+    ctx.timing(True)
+    ctx.timing_read()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = int(B.lib.gp_launch_count())
+    clocks.start()
+    evs = []
+    wall0 = time.perf_counter()
+    for k in range(args.warmup, args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(k)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = int(B.lib.gp_launch_count()) - launches0
+    phases = ctx.timing_read()
+    ctx.timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_total = sum(step_ms) * 1e-3
+    ev_steps = evals[args.warmup:]
+    my_evals = 2.0 * sum(ev_steps)
+    if dist:
+        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e = torch.tensor([my_evals], device=dev, dtype=torch.float64)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        t_total, tot_evals = float(t.item()), float(e.item())
+    else:
+        tot_evals = my_evals
+    value = tot_evals / t_total
+    pairs, issued = ctx.last_counts()
+
+    # roofline of the dominant kernel (the larger of the two rasterisers)
+    dom = "bwd" if phases["bwd"][0] >= phases["fwd"][0] else "fwd"
+    ms_dom, _, calls_dom = phases[dom]
+    avg_launch_s = ms_dom * 1e-3 / max(calls_dom, 1)
+    alg_ops_per_launch = float(np.mean(ev_steps)) * OPS_PER_EVAL[dom]
+    achieved = alg_ops_per_launch / avg_launch_s / 1e12
+    peak = fp32_peak / 1e12
+    nominal = 148 * 128 * 2.032e9 / 1e12
+
+    # end to end through host buffers: parameters and the batch's target slices
+    # in (pinned host -> device), loss and gradients out (device -> pinned host)
+    host_params = [t.cpu().pin_memory() for t in (gs.mu, gs.scale, gs.quat, gs.alpha)]
+    host_target = target[:S].cpu().pin_memory()
+    host_grads = [torch.empty(t.shape, pin_memory=True) for t in grads]
+    host_loss = torch.empty(1, pin_memory=True)
+    tgt_dev = torch.empty(S, H, W, device=dev)
+    h2d = sum(t.numel() * 4 for t in host_params) + host_target.numel() * 4
+    d2h = sum(t.numel() * 4 for t in host_grads) + 4
+    e2e_ms = []
+    for k in range(args.warmup, args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for d, h in zip((gs.mu, gs.scale, gs.quat, gs.alpha), host_params):
+            d.copy_(h, non_blocking=True)
+        tgt_dev.copy_(host_target, non_blocking=True)
+        B.gp_render_slices(ctx, gs, zs[k], H, W, SIGMA, out=I)
+        B.gp_mse_grad(ctx, I, tgt_dev, dL_dI=G, loss=loss)
+        B.gp_render_backward(ctx, gs, zs[k], H, W, SIGMA, G, grads=grads)
+        for h, d in zip(host_grads, grads):
+            h.copy_(d, non_blocking=True)
+        host_loss.copy_(loss, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = world * my_evals / (sum(e2e_ms) * 1e-3)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        cpu = oracle_baseline(oracle, synth, g, batches[args.warmup], args.ref_px, args.ref_gauss, 4242,
+                              ev_steps[0])
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(WORKLOAD, exp=args.exp, deterministic=bool(args.det), tile=args.tile,
+                               parallelism="replicas" if world > 1 else "single"),
+                "slices_per_s": world * S * args.steps / t_total,
+                "evals_fwd_per_step": float(np.mean(ev_steps)),
+                "issued_evals_last_call": issued, "pairs_last_call": pairs,
+                "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[2]},
+                "roofline": {"bound": "alu", "kernel": f"k_raster_{dom}", "achieved": achieved, "peak": peak,
+                             "unit": "Tinst/s (FP32+INT lane instructions)", "frac": achieved / peak,
+                             "traffic": None, "peak_kind": "measured FMA probe, burst, same run",
+                             "nominal_peak_2032mhz": nominal, "ops_per_eval": OPS_PER_EVAL[dom]},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "ms_per_step": float(np.mean(e2e_ms))},
+                "gpu_launches": launches, "clocks": clk, "wall_s_timed": wall}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--exp", default="poly", choices=["poly", "hw"])
+    ap.add_argument("--det", action="store_true")
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--fwd-px", type=int, default=0)
+    ap.add_argument("--bwd-px", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-px", type=int, default=2048)
+    ap.add_argument("--ref-gauss", type=int, default=2)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.warmup < 3 and args.impl == "native":
+        log("note: fewer than 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_native(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

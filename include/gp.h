@@ -170,6 +170,34 @@ GP_API gp_status gp_count_evals(gp_ctx* ctx, const gp_set* set, const float* z, 
 GP_API gp_status gp_exp2_eval(gp_ctx* ctx, const float* x, float* y, int64_t n, int mode,
                        void* stream);
 
+/* Phase timing.  When enabled, every call records a CUDA event pair on its
+ * stream around each phase below; gp_timing_read synchronises those events,
+ * returns the summed milliseconds and launch counts per phase since the last
+ * read, and clears them.  Phases: */
+#define GP_PHASE_BIN 0        /* K-pre, scan, K-emit, radix sort, K-range */
+#define GP_PHASE_FWD 1        /* K-fwd rasteriser */
+#define GP_PHASE_BWD 2        /* K-bwd rasteriser */
+#define GP_PHASE_BWD_PRE 3    /* K-det (deterministic mode) and K-bwd-pre */
+#define GP_PHASE_LOSS 4       /* K-loss */
+#define GP_PHASE_VOX_FWD 5    /* voxelizer forward rasteriser */
+#define GP_PHASE_VOX_BWD 6    /* voxelizer backward rasteriser + gradient finish */
+#define GP_NUM_PHASES 7
+GP_API gp_status gp_timing_enable(gp_ctx* ctx, int enable);
+GP_API gp_status gp_timing_read(gp_ctx* ctx, double* ms /* [GP_NUM_PHASES] */,
+                                int64_t* launches /* [GP_NUM_PHASES] */,
+                                int64_t* calls /* [GP_NUM_PHASES], may be NULL */);
+
+/* Total number of kernels this library has launched in the process (all
+ * contexts), for accounting in benchmarks. */
+GP_API int64_t gp_launch_count(void);
+
+/* FP32-pipe throughput probe: every thread of a grid sized to fill the device
+ * runs `iters` iterations of 8 independent FMA chains; out (DEVICE, one float
+ * per thread of the grid, see gp_fma_probe_threads) receives the chain sums.
+ * Used to measure the FP32 lane-instruction peak at the clocks in force. */
+GP_API int64_t gp_fma_probe_threads(gp_ctx* ctx);
+GP_API gp_status gp_fma_probe(gp_ctx* ctx, int iters, float* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,8 @@ def _load():
         lib.orc_voxelize_points.argtypes = [SP, I64, P, P, P, P]
         lib.orc_voxelize_backward.argtypes = [SP, I, I, I, P, P, P, P, P]
         lib.orc_mse.argtypes = [I64, P, P, P]
+        lib.orc_count_evals.argtypes = [SP, I, P, I, I, D, I, D]
+        lib.orc_count_evals.restype = I64
         lib.orc_mse.restype = D
         lib.orc_num_threads.restype = I
         for f in ("orc_render", "orc_render_points", "orc_render_backward",
@@ -174,6 +176,17 @@ def voxelize_backward(mu, scale, quat, alpha, X, Y, Z, dL_dV, scale_mod=1.0):
                                          _ptr(ds), _ptr(dq), _ptr(da)),
            "orc_voxelize_backward")
     return dmu, ds, dq, da
+
+
+def count_evals(mu, scale, quat, alpha, z, H, W, sigma_z, axis=2, eps=1e-6, scale_mod=1.0):
+    """Algorithmic evaluations of a render with culling bound eps (see oracle.h)."""
+    g = _GaussianSet(mu, scale, quat, alpha, scale_mod)
+    z = _f64(z, (-1,))
+    r = _load().orc_count_evals(ctypes.byref(g.c), z.shape[0], _ptr(z), H, W, float(sigma_z), axis,
+                                float(eps))
+    if r < 0:
+        raise ValueError("orc_count_evals rejected its arguments")
+    return int(r)
 
 
 def mse(I, T):

@@ -568,6 +568,44 @@ int orc_voxelize_backward(const orc_set* g, int X, int Y, int Z, const double* d
   return 0;
 }
 
+/* ------------------------------------------------------------ work count */
+
+int64_t orc_count_evals(const orc_set* g, int S, const double* z, int H, int W, double sigma_z,
+                        int axis, double eps) {
+  int perm[3];
+  if (check_set(g) || S < 0 || H < 0 || W < 0 || !(sigma_z > 0) || axis_perm(axis, perm) ||
+      !(eps > 0 && eps < 1))
+    return -1;
+  double Rc[3][3];
+  perm_matrix(perm, Rc);
+  const double k2 = 2.0 * log(1.0 / eps);
+  int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : total)
+  for (int64_t i = 0; i < g->n; ++i) {
+    world_cov w;
+    world_covariance(g, i, &w);
+    for (int s = 0; s < S; ++s) {
+      slice_proj p;
+      project(g, i, &w, Rc, z[s], sigma_z, &p);
+      if (!(p.op >= eps)) continue;
+      /* per row: C00 dx^2 + 2 C01 dx dy + C11 dy^2 <= k2 is an interval in dx */
+      for (int iy = 0; iy < H; ++iy) {
+        double dy = iy + 0.5 - p.mue[1];
+        double disc = p.C[0][1] * p.C[0][1] * dy * dy - p.C[0][0] * (p.C[1][1] * dy * dy - k2);
+        if (disc < 0) continue;
+        double sq = sqrt(disc);
+        double lo = p.mue[0] + (-p.C[0][1] * dy - sq) / p.C[0][0];
+        double hi = p.mue[0] + (-p.C[0][1] * dy + sq) / p.C[0][0];
+        int64_t x0 = (int64_t)ceil(lo - 0.5), x1 = (int64_t)floor(hi - 0.5);
+        if (x0 < 0) x0 = 0;
+        if (x1 > W - 1) x1 = W - 1;
+        if (x1 >= x0) total += x1 - x0 + 1;
+      }
+    }
+  }
+  return total;
+}
+
 /* ------------------------------------------------------------------- loss */
 
 double orc_mse(int64_t n, const double* I, const double* T, double* dL_dI) {

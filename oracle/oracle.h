@@ -72,6 +72,13 @@ int orc_voxelize_backward(const orc_set* g, int X, int Y, int Z,
                           const double* dL_dV, double* d_mu, double* d_scale,
                           double* d_quat, double* d_alpha);
 
+/* Number of (pixel, Gaussian) evaluations inside the culling region of a
+ * render with bound eps: pairs (Gaussian, slice) with opacity_r >= eps, pixels
+ * with d^T Sigma_2d^-1 d <= 2 ln(1/eps).  This is the algorithmic work of Eq. 10
+ * under that culling (the oracle itself never culls). */
+int64_t orc_count_evals(const orc_set* g, int S, const double* z, int H, int W,
+                        double sigma_z, int axis, double eps);
+
 /* Mean squared error L = 1/n sum (I - T)^2 and its gradient 2 (I - T) / n. */
 double orc_mse(int64_t n, const double* I, const double* T, double* dL_dI);
 

@@ -31,8 +31,11 @@ GP_EXP_HW = 1
 EXPORTS = (
     "gp_config_default", "gp_create", "gp_destroy", "gp_last_error", "gp_workspace_bytes",
     "gp_render_slices", "gp_render_backward", "gp_mse_grad", "gp_voxelize", "gp_voxelize_backward",
-    "gp_last_counts", "gp_count_evals", "gp_exp2_eval",
+    "gp_last_counts", "gp_count_evals", "gp_exp2_eval", "gp_timing_enable", "gp_timing_read",
+    "gp_launch_count", "gp_fma_probe_threads", "gp_fma_probe",
 )
+GP_NUM_PHASES = 7
+PHASES = ("bin", "fwd", "bwd", "bwd_pre", "loss", "vox_fwd", "vox_bwd")
 
 
 class GPError(RuntimeError):
@@ -73,6 +76,11 @@ def _load():
         "gp_last_counts": [P, ctypes.POINTER(I64), ctypes.POINTER(I64)],
         "gp_count_evals": [P, SP, P, I, I, I, F, I, ctypes.POINTER(I64)],
         "gp_exp2_eval": [P, P, P, I64, I, P],
+        "gp_timing_enable": [P, I],
+        "gp_timing_read": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), ctypes.POINTER(I64)],
+        "gp_launch_count": [],
+        "gp_fma_probe_threads": [P],
+        "gp_fma_probe": [P, I, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -80,6 +88,8 @@ def _load():
         fn.restype = I
     lib.gp_last_error.restype = ctypes.c_char_p
     lib.gp_workspace_bytes.restype = I64
+    lib.gp_launch_count.restype = I64
+    lib.gp_fma_probe_threads.restype = I64
     return lib
 
 
@@ -143,6 +153,25 @@ class Context:
 
     def workspace_bytes(self):
         return int(lib.gp_workspace_bytes(self.h))
+
+    def timing(self, enable=True):
+        self.check(lib.gp_timing_enable(self.h, int(bool(enable))), "gp_timing_enable")
+
+    def timing_read(self):
+        """{phase: (ms, launches, calls)} since the last read."""
+        ms = (ctypes.c_double * GP_NUM_PHASES)()
+        ln = (ctypes.c_int64 * GP_NUM_PHASES)()
+        cl = (ctypes.c_int64 * GP_NUM_PHASES)()
+        self.check(lib.gp_timing_read(self.h, ms, ln, cl), "gp_timing_read")
+        return {PHASES[k]: (ms[k], ln[k], cl[k]) for k in range(GP_NUM_PHASES)}
+
+    def fma_probe(self, iters, out=None, stream=None):
+        n = int(lib.gp_fma_probe_threads(self.h))
+        if out is None:
+            out = torch.empty(n, device=f"cuda:{self.device}")
+        self.check(lib.gp_fma_probe(self.h, int(iters), _dev(out, "out", shape=(n,)), _stream(stream)),
+                   "gp_fma_probe")
+        return out, n * int(iters) * 8
 
     def last_counts(self):
         p, e = ctypes.c_int64(), ctypes.c_int64()

@@ -49,8 +49,23 @@ struct BinBufs {
   DevBuf loss_tmp;
 };
 
+// Adds k to the process-wide count of kernels this library launched.
+void note_launch(int k = 1);
+int64_t launch_count();
+int64_t fma_probe_threads(int sm_count);
+void launch_fma_probe(int sm_count, int iters, float* out, cudaStream_t st);
+
+struct PhaseEvent {
+  int phase;
+  cudaEvent_t start, stop;
+  int64_t launches;
+};
+
 struct Ctx {
   int device = 0;
+  bool timing = false;
+  std::vector<PhaseEvent> events;
+  std::vector<cudaEvent_t> event_pool;
   gp_config cfg{};
   std::string err;
   int64_t ws_bytes = 0;
@@ -61,6 +76,20 @@ struct Ctx {
 };
 
 gp_status set_err(Ctx* c, gp_status st, const std::string& msg);
+
+// Records an event pair around a phase on stream st when timing is enabled.
+class PhaseTimer {
+ public:
+  PhaseTimer(Ctx* c, int phase, cudaStream_t st);
+  ~PhaseTimer();
+
+ private:
+  Ctx* c_;
+  int phase_;
+  cudaStream_t st_;
+  cudaEvent_t start_ = nullptr;
+  int64_t l0_ = 0;
+};
 gp_status cuda_err(Ctx* c, cudaError_t e, const char* where);
 
 }  // namespace gp

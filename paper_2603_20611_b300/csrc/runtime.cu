@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <numeric>
 #include <string>
@@ -18,6 +19,47 @@
 #include "voxel.cuh"
 
 namespace gp {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+static cudaEvent_t pooled_event(Ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+PhaseTimer::PhaseTimer(Ctx* c, int phase, cudaStream_t st) : c_(c), phase_(phase), st_(st) {
+  if (!c->timing) return;
+  start_ = pooled_event(c);
+  if (start_ && cudaEventRecord(start_, st) != cudaSuccess) {
+    cudaGetLastError();
+    c->event_pool.push_back(start_);
+    start_ = nullptr;
+  }
+  l0_ = launch_count();
+}
+
+PhaseTimer::~PhaseTimer() {
+  if (!start_) return;
+  cudaEvent_t stop = pooled_event(c_);
+  if (!stop || cudaEventRecord(stop, st_) != cudaSuccess) {
+    cudaGetLastError();
+    c_->event_pool.push_back(start_);
+    if (stop) c_->event_pool.push_back(stop);
+    return;
+  }
+  c_->events.push_back(PhaseEvent{phase_, start_, stop, launch_count() - l0_});
+}
 
 gp_status set_err(Ctx* c, gp_status st, const std::string& msg) {
   if (c) c->err = msg;
@@ -107,7 +149,7 @@ static gp_status sort_and_range(Ctx* c, uint32_t P, int64_t nkeys, cudaStream_t 
           "radix sort");
   const uint32_t* sk = (const uint32_t*)(in_alt ? b.keys_alt.ptr : b.keys.ptr);
   *sorted_vals = (const uint32_t*)(in_alt ? b.vals_alt.ptr : b.vals.ptr);
-  launch_ranges(sk, (const unsigned long long*)b.total.ptr, P, (uint2*)b.ranges.ptr, st);
+  launch_ranges(sk, (const unsigned long long*)b.total.ptr, P, (uint32_t)nkeys, (uint2*)b.ranges.ptr, st);
   return GP_OK;
 }
 
@@ -151,9 +193,11 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
   if ((int64_t)S * H * W > (int64_t)INT32_MAX) return set_err(c, GP_ERR_ARG, "S*H*W exceeds 2^31");
   for (int s = 0; s < S; ++s)
     if (!isfinite(z[s])) return set_err(c, GP_ERR_ARG, "z contains a non-finite value");
+  PhaseTimer timer(c, GP_PHASE_BIN, st);
   const int tile = tile_of(c);
   const int TX = ceil_div(W, tile), TY = ceil_div(H, tile);
   const int64_t nkeys = (int64_t)S * TX * TY;
+  if (nkeys >= (int64_t)UINT32_MAX) return set_err(c, GP_ERR_ARG, "too many (slice, tile) bins");
   BinBufs& b = c->b;
   const int n = (int)set->n;
   // slice positions: sorted copy + order (host), uploaded once per call
@@ -195,7 +239,7 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
   if (P > 0) {
     GP_TRY(reserve_pairs(c, P));
     launch_slice_emit(A, (const SliceRec*)b.rec.ptr, (const unsigned long long*)b.offsets.ptr,
-                      (uint32_t*)b.keys.ptr, (uint32_t*)b.vals.ptr, (uint32_t*)b.emit_gid.ptr, st);
+                      (const unsigned long long*)b.counts.ptr, (uint32_t*)b.keys.ptr, (uint32_t*)b.vals.ptr, (uint32_t*)b.emit_gid.ptr, st);
     GP_TRY(sort_and_range(c, P, nkeys, st, sorted_vals));
   }
   *pairs_out = P;
@@ -210,6 +254,7 @@ static gp_status bin_voxels(Ctx* c, const gp_set* set, int X, int Y, int Z, cuda
                             uint32_t* pairs_out, const uint32_t** sorted_vals) {
   if (X <= 0 || Y <= 0 || Z <= 0) return set_err(c, GP_ERR_ARG, "need X, Y, Z > 0");
   if ((int64_t)X * Y * Z > (int64_t)INT32_MAX * 4) return set_err(c, GP_ERR_ARG, "volume too large");
+  PhaseTimer timer(c, GP_PHASE_BIN, st);
   const int TX = ceil_div(X, VOX_TILE), TY = ceil_div(Y, VOX_TILE), TZ = ceil_div(Z, VOX_TILE);
   const int64_t nkeys = (int64_t)TX * TY * TZ;
   BinBufs& b = c->b;
@@ -233,7 +278,8 @@ static gp_status bin_voxels(Ctx* c, const gp_set* set, int X, int Y, int Z, cuda
   *sorted_vals = nullptr;
   if (P > 0) {
     GP_TRY(reserve_pairs(c, P));
-    launch_vox_emit(A, (const VoxRec*)b.rec.ptr, (const unsigned long long*)b.offsets.ptr, (uint32_t*)b.keys.ptr,
+    launch_vox_emit(A, (const VoxRec*)b.rec.ptr, (const unsigned long long*)b.offsets.ptr,
+                    (const unsigned long long*)b.counts.ptr, (uint32_t*)b.keys.ptr,
                     (uint32_t*)b.vals.ptr, (uint32_t*)b.emit_gid.ptr, st);
     GP_TRY(sort_and_range(c, P, nkeys, st, sorted_vals));
   }
@@ -312,6 +358,11 @@ gp_status gp_destroy(gp_ctx* ctx) {
                    &b.emit_gid, &b.ranges, &b.scan_tmp, &b.sort_tmp, &b.zs, &b.zorder, &b.zorig,
                    &b.accum, &b.partial, &b.loss_tmp};
   for (DevBuf* d : all) ws_release(c, *d);
+  for (auto& e : c->events) {
+    cudaEventDestroy(e.start);
+    cudaEventDestroy(e.stop);
+  }
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   if (c->h_total) cudaFreeHost(c->h_total);
   delete ctx;
   return GP_OK;
@@ -348,6 +399,7 @@ gp_status gp_render_slices(gp_ctx* ctx, const gp_set* set, const float* z, int S
     GP_CUDA(c, cudaMemsetAsync(out, 0, (size_t)S * H * W * 4, st), "clear out");
     return GP_OK;
   }
+  PhaseTimer timer(c, GP_PHASE_FWD, st);
   GP_CUDA(c, launch_raster_fwd(a, fwd_px(c), c->cfg.exp_mode, (const SliceRec*)c->b.rec.ptr, vals,
                                (const uint32_t*)c->b.emit_gid.ptr, (const uint2*)c->b.ranges.ptr, out, st),
           "raster forward");
@@ -379,15 +431,19 @@ gp_status gp_render_backward(gp_ctx* ctx, const gp_set* set, const float* z, int
     GP_CUDA(c, cudaMemsetAsync(b.accum.ptr, 0, (size_t)n * 10 * 4, st), "clear accumulators");
   }
   if (P > 0) {
+    PhaseTimer timer(c, GP_PHASE_BWD, st);
     GP_CUDA(c, launch_raster_bwd(a, bwd_px(c), c->cfg.exp_mode, det, (const SliceRec*)b.rec.ptr, vals,
                                  (const uint32_t*)b.emit_gid.ptr, (const uint2*)b.ranges.ptr, dL_dI,
                                  (float*)b.accum.ptr, (float4*)b.partial.ptr, st),
             "raster backward");
   }
-  if (det)
-    launch_det_reduce(n, (const unsigned long long*)b.offsets.ptr, (const unsigned long long*)b.counts.ptr,
-                      (const float4*)b.partial.ptr, (float*)b.accum.ptr, st);
-  launch_slice_bwd_pre(a, (const float*)b.accum.ptr, d_mu, d_scale, d_quat, d_alpha, st);
+  {
+    PhaseTimer timer(c, GP_PHASE_BWD_PRE, st);
+    if (det)
+      launch_det_reduce(n, (const unsigned long long*)b.offsets.ptr, (const unsigned long long*)b.counts.ptr,
+                        (const float4*)b.partial.ptr, (float*)b.accum.ptr, st);
+    launch_slice_bwd_pre(a, (const float*)b.accum.ptr, d_mu, d_scale, d_quat, d_alpha, st);
+  }
   return cuda_err(c, cudaGetLastError(), "backward kernels");
 }
 
@@ -412,6 +468,7 @@ gp_status gp_mse_grad(gp_ctx* ctx, const float* I, const float* T, const int* t_
     GP_CUDA(c, cudaMemcpyAsync(dst, t_index, (size_t)S * 4, cudaMemcpyHostToDevice, st), "upload t_index");
     tid = dst;
   }
+  PhaseTimer timer(c, GP_PHASE_LOSS, st);
   launch_mse(I, T, tid, S, HW, dL_dI, loss, (float*)b.loss_tmp.ptr, st);
   return cuda_err(c, cudaGetLastError(), "mse");
 }
@@ -461,6 +518,7 @@ gp_status gp_voxelize(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, float
     GP_CUDA(c, cudaMemsetAsync(vol, 0, (size_t)X * Y * Z * 4, st), "clear vol");
     return GP_OK;
   }
+  PhaseTimer timer(c, GP_PHASE_VOX_FWD, st);
   GP_CUDA(c, launch_vox_fwd(a, (const VoxRec*)c->b.rec.ptr, vals, (const uint32_t*)c->b.emit_gid.ptr,
                             (const uint2*)c->b.ranges.ptr, vol, st),
           "voxelize forward");
@@ -487,6 +545,7 @@ gp_status gp_voxelize_backward(gp_ctx* ctx, const gp_set* set, int X, int Y, int
   const bool det = c->cfg.deterministic != 0;
   if (det) GP_TRY(ws_reserve(c, b.partial, (size_t)std::max<uint32_t>(P, 1) * 48));
   else GP_CUDA(c, cudaMemsetAsync(b.accum.ptr, 0, (size_t)n * 10 * 4, st), "clear accumulators");
+  PhaseTimer timer(c, GP_PHASE_VOX_BWD, st);
   if (P > 0)
     GP_CUDA(c, launch_vox_bwd(a, det, (const VoxRec*)b.rec.ptr, vals, (const uint32_t*)b.emit_gid.ptr,
                               (const uint2*)b.ranges.ptr, dL_dV, (float*)b.accum.ptr, (float4*)b.partial.ptr, st),
@@ -496,6 +555,51 @@ gp_status gp_voxelize_backward(gp_ctx* ctx, const gp_set* set, int X, int Y, int
                           (const float4*)b.partial.ptr, (float*)b.accum.ptr, st);
   launch_vox_bwd_pre(a, (const float*)b.accum.ptr, d_mu, d_scale, d_quat, d_alpha, st);
   return cuda_err(c, cudaGetLastError(), "voxelize backward kernels");
+}
+
+gp_status gp_timing_enable(gp_ctx* ctx, int enable) {
+  if (!ctx) return GP_ERR_ARG;
+  ctx->impl.timing = enable != 0;
+  return GP_OK;
+}
+
+gp_status gp_timing_read(gp_ctx* ctx, double* ms, int64_t* launches, int64_t* calls) {
+  if (!ctx || !ms || !launches) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+  for (int k = 0; k < GP_NUM_PHASES; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+    if (calls) calls[k] = 0;
+  }
+  gp_status st = GP_OK;
+  for (auto& e : c->events) {
+    float t = 0.f;
+    cudaError_t r = cudaEventSynchronize(e.stop);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(&t, e.start, e.stop);
+    if (r != cudaSuccess) st = cuda_err(c, r, "timing event");
+    if (e.phase >= 0 && e.phase < GP_NUM_PHASES) {
+      ms[e.phase] += t;
+      launches[e.phase] += e.launches;
+      if (calls) calls[e.phase] += 1;
+    }
+    c->event_pool.push_back(e.start);
+    c->event_pool.push_back(e.stop);
+  }
+  c->events.clear();
+  return st;
+}
+
+int64_t gp_launch_count(void) { return launch_count(); }
+
+int64_t gp_fma_probe_threads(gp_ctx* ctx) { return ctx ? fma_probe_threads(ctx->impl.sm_count) : 0; }
+
+gp_status gp_fma_probe(gp_ctx* ctx, int iters, float* out, void* stream) {
+  if (!ctx) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+  if (iters <= 0 || !out) return set_err(c, GP_ERR_ARG, "bad probe arguments");
+  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  launch_fma_probe(c->sm_count, iters, out, (cudaStream_t)stream);
+  return cuda_err(c, cudaGetLastError(), "fma probe");
 }
 
 }  // extern "C"

@@ -35,6 +35,7 @@
 #include <algorithm>
 
 #include "gp_common.cuh"
+#include "gp_internal.h"
 #include "slice.cuh"
 
 namespace gp {
@@ -135,11 +136,13 @@ __global__ void __launch_bounds__(PRE_THREADS) k_slice_pre(SliceArgs a, SliceRec
 void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
   if (a.n <= 0) return;
   k_slice_pre<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, counts);
+  note_launch();
 }
 
 // ------------------------------------------------------------ K-emit
 __global__ void __launch_bounds__(PRE_THREADS) k_slice_emit(SliceArgs a, const SliceRec* __restrict__ rec,
                                                             const unsigned long long* __restrict__ offsets,
+                                                            const unsigned long long* __restrict__ counts,
                                                             uint32_t* __restrict__ keys,
                                                             uint32_t* __restrict__ vals,
                                                             uint32_t* __restrict__ emit_gid) {
@@ -147,39 +150,46 @@ __global__ void __launch_bounds__(PRE_THREADS) k_slice_emit(SliceArgs a, const S
   if (i >= a.n) return;
   SliceRec r = rec[i];
   uint32_t e = (uint32_t)offsets[i];
+  const uint32_t e_end = (uint32_t)(offsets[i] + counts[i]);  // never write past this Gaussian's slots
   const uint32_t T = (uint32_t)(a.TX * a.TY);
   for_each_pair(a, r, [&](int j, int tile) {
-    uint32_t s = (uint32_t)a.zorder[j];
-    keys[e] = s * T + (uint32_t)tile;
-    vals[e] = e;
-    emit_gid[e] = (uint32_t)i;
+    if (e < e_end) {
+      uint32_t s = (uint32_t)a.zorder[j];
+      keys[e] = s * T + (uint32_t)tile;
+      vals[e] = e;
+      emit_gid[e] = (uint32_t)i;
+    }
     ++e;
   });
 }
 
 void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* offsets,
-                       uint32_t* keys, uint32_t* vals, uint32_t* emit_gid, cudaStream_t st) {
+                       const unsigned long long* counts, uint32_t* keys, uint32_t* vals, uint32_t* emit_gid,
+                       cudaStream_t st) {
   if (a.n <= 0) return;
-  k_slice_emit<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, offsets, keys, vals, emit_gid);
+  k_slice_emit<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, offsets, counts, keys, vals, emit_gid);
+  note_launch();
 }
 
 // ------------------------------------------------------------ K-range
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long long* __restrict__ n_dev,
-                         uint32_t cap, uint2* __restrict__ ranges) {
+                         uint32_t cap, uint32_t nkeys, uint2* __restrict__ ranges) {
   unsigned long long nn = *n_dev;
   uint32_t n = nn < cap ? (uint32_t)nn : cap;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint32_t k = keys[i];
+    if (k >= nkeys) continue;  // cannot happen for emitted keys; keeps the store in bounds
     if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
     if (i + 1 == n || keys[i + 1] != k) ranges[k].y = i + 1;
   }
 }
 
-void launch_ranges(const uint32_t* keys, const unsigned long long* n_dev, uint32_t cap, uint2* ranges,
-                   cudaStream_t st) {
+void launch_ranges(const uint32_t* keys, const unsigned long long* n_dev, uint32_t cap, uint32_t nkeys,
+                   uint2* ranges, cudaStream_t st) {
   if (cap == 0) return;
   int blocks = (int)std::min<int64_t>(((int64_t)cap + 255) / 256, 148 * 16);
-  k_ranges<<<blocks, 256, 0, st>>>(keys, n_dev, cap, ranges);
+  k_ranges<<<blocks, 256, 0, st>>>(keys, n_dev, cap, nkeys, ranges);
+  note_launch();
 }
 
 // ------------------------------------------------------------ K-fwd
@@ -273,6 +283,7 @@ static cudaError_t fwd_dispatch(const SliceArgs& a, int exp_mode, const SliceRec
     k_raster_fwd<TILE, PX, GP_EXP_HW><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, out);
   else
     k_raster_fwd<TILE, PX, GP_EXP_POLY><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, out);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -450,6 +461,7 @@ static cudaError_t bwd_dispatch(const SliceArgs& a, int exp_mode, bool det, cons
     if (det) k_raster_bwd<TILE, PX, GP_EXP_POLY, true><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, dL_dI, accum, partial);
     else k_raster_bwd<TILE, PX, GP_EXP_POLY, false><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, dL_dI, accum, partial);
   }
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -502,6 +514,7 @@ void launch_det_reduce(int n, const unsigned long long* offsets, const unsigned 
                        const float4* partial, float* accum, cudaStream_t st) {
   if (n <= 0) return;
   k_det_reduce<<<ceil_div(n, 256), 256, 0, st>>>(n, offsets, counts, partial, accum);
+  note_launch();
 }
 
 // ------------------------------------------------------------ K-bwd-pre
@@ -582,6 +595,7 @@ void launch_slice_bwd_pre(const SliceArgs& a, const float* accum, float* d_mu, f
   if (a.n <= 0) return;
   k_slice_bwd_pre<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, accum, d_mu, d_scale, d_quat,
                                                                       d_alpha);
+  note_launch();
 }
 
 // ------------------------------------------------------------ K-loss
@@ -641,7 +655,11 @@ void launch_mse(const float* I, const float* T, const int* t_index, int S, int64
   int bpsl = mse_blocks_per_slice(HW);
   float scale = 1.0f / ((float)S * (float)HW);
   k_mse<<<S * bpsl, MSE_THREADS, 0, st>>>(I, T, t_index, HW, bpsl, scale, dL_dI, tmp);
-  if (loss) k_mse_final<<<1, 1024, 0, st>>>(tmp, S * bpsl, scale, loss);
+  note_launch();
+  if (loss) {
+    k_mse_final<<<1, 1024, 0, st>>>(tmp, S * bpsl, scale, loss);
+    note_launch();
+  }
 }
 
 // ------------------------------------------------------------ counting
@@ -679,6 +697,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_count_evals(SliceArgs a, const 
 void launch_count_evals(const SliceArgs& a, const SliceRec* rec, unsigned long long* out, cudaStream_t st) {
   if (a.n <= 0) return;
   k_count_evals<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, out);
+  note_launch();
 }
 
 __global__ void k_exp2_eval(const float* __restrict__ x, float* __restrict__ y, int64_t n, int mode) {
@@ -691,6 +710,7 @@ __global__ void k_exp2_eval(const float* __restrict__ x, float* __restrict__ y, 
 void launch_exp2_eval(const float* x, float* y, int64_t n, int mode, cudaStream_t st) {
   if (n <= 0) return;
   k_exp2_eval<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n, mode);
+  note_launch();
 }
 
 }  // namespace gp

@@ -29,10 +29,11 @@ struct SliceArgs {
 void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st);
 // K-emit: (slice, tile) keys, identity values, emission -> Gaussian id.
 void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* offsets,
-                       uint32_t* keys, uint32_t* vals, uint32_t* emit_gid, cudaStream_t st);
+                       const unsigned long long* counts, uint32_t* keys, uint32_t* vals, uint32_t* emit_gid,
+                       cudaStream_t st);
 // K-range: [start, end) of each key in the sorted key list; ranges must be zeroed.
-void launch_ranges(const uint32_t* keys, const unsigned long long* n_dev, uint32_t cap, uint2* ranges,
-                   cudaStream_t st);
+void launch_ranges(const uint32_t* keys, const unsigned long long* n_dev, uint32_t cap, uint32_t nkeys,
+                   uint2* ranges, cudaStream_t st);
 // K-fwd.
 cudaError_t launch_raster_fwd(const SliceArgs& a, int px, int exp_mode, const SliceRec* rec,
                               const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,

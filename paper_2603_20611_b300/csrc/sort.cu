@@ -136,6 +136,7 @@ cudaError_t exclusive_scan(const T* in, T* out, int64_t n, unsigned long long* t
   k_scan_reduce<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, part);
   k_scan_partials<<<1, 1024, 0, st>>>(part, (int)nb, total);
   k_scan_down<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, part);
+  note_launch(3);
   return cudaGetLastError();
 }
 
@@ -243,6 +244,7 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
     cudaError_t e = exclusive_scan<uint32_t>(hist, hist, nh, nullptr, stemp, st);
     if (e != cudaSuccess) return e;
     k_radix_scatter<<<nb, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, hist, nb);
+    note_launch(2);
     uint32_t* tk = ki; ki = ko; ko = tk;
     uint32_t* tv = vi; vi = vo; vo = tv;
     *result_in_alt = !*result_in_alt;

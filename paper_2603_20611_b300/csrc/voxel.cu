@@ -19,6 +19,7 @@
 #include <stdint.h>
 
 #include "gp_common.cuh"
+#include "gp_internal.h"
 #include "voxel.cuh"
 
 namespace gp {
@@ -97,10 +98,12 @@ __global__ void __launch_bounds__(VPRE_THREADS) k_vox_pre(VoxArgs a, VoxRec* __r
 void launch_vox_pre(const VoxArgs& a, VoxRec* rec, unsigned long long* counts, cudaStream_t st) {
   if (a.n <= 0) return;
   k_vox_pre<<<ceil_div(a.n, VPRE_THREADS), VPRE_THREADS, 0, st>>>(a, rec, counts);
+  note_launch();
 }
 
 __global__ void __launch_bounds__(VPRE_THREADS) k_vox_emit(VoxArgs a, const VoxRec* __restrict__ rec,
                                                            const unsigned long long* __restrict__ offsets,
+                                                           const unsigned long long* __restrict__ counts,
                                                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                            uint32_t* __restrict__ emit_gid) {
   int i = blockIdx.x * VPRE_THREADS + threadIdx.x;
@@ -109,20 +112,25 @@ __global__ void __launch_bounds__(VPRE_THREADS) k_vox_emit(VoxArgs a, const VoxR
   if (r.r3.y == 0.0f) return;
   TileBox b = vox_tiles(a, r);
   uint32_t e = (uint32_t)offsets[i];
+  const uint32_t e_end = (uint32_t)(offsets[i] + counts[i]);  // never write past this Gaussian's slots
   for (int tz = b.z0; tz <= b.z1; ++tz)
     for (int ty = b.y0; ty <= b.y1; ++ty)
       for (int tx = b.x0; tx <= b.x1; ++tx) {
-        keys[e] = (uint32_t)((tz * a.TY + ty) * a.TX + tx);
-        vals[e] = e;
-        emit_gid[e] = (uint32_t)i;
+        if (e < e_end) {
+          keys[e] = (uint32_t)((tz * a.TY + ty) * a.TX + tx);
+          vals[e] = e;
+          emit_gid[e] = (uint32_t)i;
+        }
         ++e;
       }
 }
 
-void launch_vox_emit(const VoxArgs& a, const VoxRec* rec, const unsigned long long* offsets, uint32_t* keys,
-                     uint32_t* vals, uint32_t* emit_gid, cudaStream_t st) {
+void launch_vox_emit(const VoxArgs& a, const VoxRec* rec, const unsigned long long* offsets,
+                     const unsigned long long* counts, uint32_t* keys, uint32_t* vals, uint32_t* emit_gid,
+                     cudaStream_t st) {
   if (a.n <= 0) return;
-  k_vox_emit<<<ceil_div(a.n, VPRE_THREADS), VPRE_THREADS, 0, st>>>(a, rec, offsets, keys, vals, emit_gid);
+  k_vox_emit<<<ceil_div(a.n, VPRE_THREADS), VPRE_THREADS, 0, st>>>(a, rec, offsets, counts, keys, vals, emit_gid);
+  note_launch();
 }
 
 // Staging: mean relative to the tile origin (exact), alpha, and the quadratic
@@ -196,6 +204,7 @@ cudaError_t launch_vox_fwd(const VoxArgs& a, const VoxRec* rec, const uint32_t* 
   int64_t tiles = (int64_t)a.TX * a.TY * a.TZ;
   if (tiles == 0) return cudaSuccess;
   k_vox_fwd<<<(unsigned)tiles, VNT, 0, st>>>(a, rec, vals, emit_gid, ranges, vol);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -304,6 +313,7 @@ cudaError_t launch_vox_bwd(const VoxArgs& a, bool det, const VoxRec* rec, const 
   if (tiles == 0) return cudaSuccess;
   if (det) k_vox_bwd<true><<<(unsigned)tiles, VNT, 0, st>>>(a, rec, vals, emit_gid, ranges, dL_dV, accum, partial);
   else k_vox_bwd<false><<<(unsigned)tiles, VNT, 0, st>>>(a, rec, vals, emit_gid, ranges, dL_dV, accum, partial);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -330,6 +340,7 @@ void launch_vox_det_reduce(int n, const unsigned long long* offsets, const unsig
                            const float4* partial, float* accum, cudaStream_t st) {
   if (n <= 0) return;
   k_vox_det_reduce<<<ceil_div(n, 256), 256, 0, st>>>(n, offsets, counts, partial, accum);
+  note_launch();
 }
 
 // Moments -> gradients:  dL/dalpha = M0,  dL/dmu = alpha K (M1, M2, M3),
@@ -386,6 +397,7 @@ void launch_vox_bwd_pre(const VoxArgs& a, const float* accum, float* d_mu, float
                         float* d_alpha, cudaStream_t st) {
   if (a.n <= 0) return;
   k_vox_bwd_pre<<<ceil_div(a.n, VPRE_THREADS), VPRE_THREADS, 0, st>>>(a, accum, d_mu, d_scale, d_quat, d_alpha);
+  note_launch();
 }
 
 }  // namespace gp

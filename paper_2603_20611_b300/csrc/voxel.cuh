@@ -22,8 +22,9 @@ struct VoxArgs {
 };
 
 void launch_vox_pre(const VoxArgs& a, VoxRec* rec, unsigned long long* counts, cudaStream_t st);
-void launch_vox_emit(const VoxArgs& a, const VoxRec* rec, const unsigned long long* offsets, uint32_t* keys,
-                     uint32_t* vals, uint32_t* emit_gid, cudaStream_t st);
+void launch_vox_emit(const VoxArgs& a, const VoxRec* rec, const unsigned long long* offsets,
+                     const unsigned long long* counts, uint32_t* keys, uint32_t* vals, uint32_t* emit_gid,
+                     cudaStream_t st);
 cudaError_t launch_vox_fwd(const VoxArgs& a, const VoxRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
                            const uint2* ranges, float* vol, cudaStream_t st);
 cudaError_t launch_vox_bwd(const VoxArgs& a, bool deterministic, const VoxRec* rec, const uint32_t* vals,

@@ -415,3 +415,30 @@ def test_mse_gradient():
         e[k] = 1e-6
         num = (oracle.mse(I + e, T)[0] - oracle.mse(I - e, T)[0]) / 2e-6
         assert g[k] == pytest.approx(num, rel=1e-6)
+
+
+def test_count_evals_brute_force():
+    """The oracle's count of evaluations inside the culling region equals a direct
+    per-pixel count with the conditional covariance Sigma_pp - Sigma_pc Sigma_cp / v
+    built from scipy rotations (an independent route to Eq. 6-8)."""
+    g = synth.small(seed=4, n=30, extent=(20, 20, 8))
+    z = synth.slice_positions(range(8))
+    eps, sig, H, W = 1e-3, 1.5, 20, 20
+    k2 = 2 * math.log(1 / eps)
+    xx, yy = pixel_grid(H, W)
+    count = 0
+    for i in range(g.n):
+        Sg = cov(g.scale[i].astype(np.float64), g.quat[i])
+        v = Sg[2, 2] + sig * sig
+        b = Sg[:2, 2]
+        S2 = Sg[:2, :2] - np.outer(b, b) / v
+        Ki = np.linalg.inv(S2)
+        for zs in z:
+            delta = g.mu[i, 2] - zs
+            if math.exp(-0.5 * delta * delta / v) < eps:
+                continue
+            m2 = g.mu[i, :2].astype(np.float64) - b * delta / v
+            dx, dy = xx - m2[0], yy - m2[1]
+            q = Ki[0, 0] * dx * dx + 2 * Ki[0, 1] * dx * dy + Ki[1, 1] * dy * dy
+            count += int((q <= k2).sum())
+    assert oracle.count_evals(g.mu, g.scale, g.quat, g.alpha, z, H, W, sig, eps=eps) == count
