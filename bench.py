@@ -41,6 +41,23 @@ WORKLOAD = {"workload": "microscopy fit step: 500k Gaussians, 1024x1024x256 volu
             "n_gaussians": 500_000, "slice_hw": [1024, 1024], "n_planes": 256, "slices_per_step": 16,
             "sigma_z": 3.0, "eps": 1e-6, "l2": "flushed between steps (256 MiB write)"}
 N, H, W, DEPTH, S, SIGMA = 500_000, 1024, 1024, 256, 16, 3.0
+# A quarter-size case with the same Gaussian density and list lengths (125k
+# Gaussians, 512 x 512 x 256), used for profiler captures.
+SMALL = dict(N=125_000, H=512, W=512, extent=(512, 512, 256))
+
+
+def use_small_case():
+    global N, H, W, WORKLOAD
+    N, H, W = SMALL["N"], SMALL["H"], SMALL["W"]
+    WORKLOAD = dict(WORKLOAD, workload="microscopy fit step, quarter size for profiling: 125k Gaussians, "
+                                       "512x512x256 volume, sigma_z=3, 16 slices per step",
+                    n_gaussians=N, slice_hw=[H, W])
+
+
+def microscopy_set(synth, seed):
+    if N == SMALL["N"]:
+        return synth.microscopy(seed=seed, n=N, extent=SMALL["extent"])
+    return synth.microscopy(seed=seed)
 
 # Lane instructions of the FP32/INT pipes per ALGORITHMIC evaluation, counted from
 # the method's arithmetic with the project-written exp2 (range reduction 3 FADD,
@@ -104,9 +121,9 @@ def measured_peaks():
 
 
 def make_workload(B, synth, torch, dev, ctx):
-    g = synth.microscopy(seed=1002)
+    g = microscopy_set(synth, 1002)
     gs = B.GaussianSet.from_numpy(g, dev)
-    tgt = B.GaussianSet.from_numpy(synth.microscopy(seed=2002), dev)
+    tgt = B.GaussianSet.from_numpy(microscopy_set(synth, 2002), dev)
     target = torch.empty(DEPTH, H, W, device=dev)
     for s0 in range(0, DEPTH, 32):
         B.gp_render_slices(ctx, tgt, synth.slice_positions(range(s0, s0 + 32)), H, W, SIGMA,
@@ -171,12 +188,13 @@ def run_reference(args, rank, world):
         return 0
     import oracle
     from paper_2603_20611_b300 import synth
-    g = synth.microscopy(seed=1002)
+    g = microscopy_set(synth, 1002)
     batches = step_batches(synth, 0, args.warmup + args.steps)
     step_s, evals, sample_s = [], [], 0.0
+    n_gauss = args.ref_gauss or 2 * oracle.num_threads()
     for k, idx in enumerate(batches):
         ev = oracle_evals(oracle, synth, g, idx)
-        st, ss = oracle_step_seconds(oracle, synth, g, idx, args.ref_px, args.ref_gauss, 5000 + k)
+        st, ss = oracle_step_seconds(oracle, synth, g, idx, args.ref_px, n_gauss, 5000 + k)
         if k >= args.warmup:
             step_s.append(st)
             evals.append(2.0 * ev)
@@ -188,7 +206,7 @@ def run_reference(args, rank, world):
             "config": WORKLOAD, "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": f"per step: forward at {args.ref_px} sampled pixels and backward of "
-                                       f"{args.ref_gauss} sampled Gaussians (FP64 brute force), extrapolated to "
+                                       f"{n_gauss} sampled Gaussians (FP64 brute force), extrapolated to "
                                        f"the full step; {sample_s:.1f}s of CPU work in the timed steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -323,8 +341,8 @@ def run_native(args, rank, world):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
-        cpu = oracle_baseline(oracle, synth, g, batches[args.warmup], args.ref_px, args.ref_gauss, 4242,
-                              ev_steps[0])
+        cpu = oracle_baseline(oracle, synth, g, batches[args.warmup], args.ref_px,
+                              args.ref_gauss or 2 * oracle.num_threads(), 4242, ev_steps[0])
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -363,8 +381,11 @@ def main():
     ap.add_argument("--bwd-px", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-px", type=int, default=2048)
-    ap.add_argument("--ref-gauss", type=int, default=2)
+    ap.add_argument("--ref-gauss", type=int, default=0, help="0 = twice the oracle's threads")
+    ap.add_argument("--case", default="microscopy", choices=["microscopy", "small"])
     args = ap.parse_args()
+    if args.case == "small":
+        use_small_case()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.warmup < 3 and args.impl == "native":
