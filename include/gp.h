@@ -140,6 +140,34 @@ GP_API gp_status gp_render_backward(gp_ctx* ctx, const gp_set* set, const float*
 GP_API gp_status gp_mse_grad(gp_ctx* ctx, const float* I, const float* T, const int* t_index,
                       int S, int H, int W, float* dL_dI, float* loss, void* stream);
 
+/* Allocation-free variant of gp_mse_grad (the paper has no counterpart: this is a
+ * deployment convenience).  For callers that must not allocate device memory:
+ * processes whose device memory is already reserved by another allocator (a
+ * framework's caching allocator or a fixed pool), where a fresh cudaMalloc can
+ * fail although the pool has room, and latency-bound serving loops that cannot
+ * pay for cudaMalloc / cudaFree, which synchronise the device.  It needs no
+ * context and calls no allocating routine.
+ *
+ * Same arguments and results as gp_mse_grad (I, T, dL_dI, loss on the device,
+ * t_index on the host or NULL), on the CURRENT device and the given stream.
+ * Scratch: one fixed device array inside the library, 2^18 floats of per-block
+ * partial sums plus 2^14 target indices (about 1.06 MiB, held by every GPU that
+ * loads the library until the process exits).  Limits: S <= 2^18 slices, the
+ * per-block partials of S slices of H*W pixels (S * ceil(H*W / 2048), at most
+ * 4096 blocks per slice) <= 2^18, and S <= 2^14 when t_index is given; larger
+ * calls return GP_ERR_OVERFLOW before anything runs.  GP_ERR_ARG for H or W
+ * <= 0, S < 0, NULL pointers or a negative index; GP_ERR_CUDA if the scratch
+ * address cannot be obtained.
+ *
+ * The first call on a device looks up the scratch's device address with
+ * cudaGetSymbolAddress (once per device, thread-safe); make that first call
+ * before any stream capture.  Every call shares the one array, and each call
+ * overwrites what it reads, so nothing carries over between calls; but calls
+ * whose work overlaps on the GPU (different streams, or different host threads
+ * without ordering) race on it and must be serialised by the caller. */
+GP_API gp_status gp_mse_grad_noalloc(const float* I, const float* T, const int* t_index, int S,
+                                     int H, int W, float* dL_dI, float* loss, void* stream);
+
 /* Differentiable voxelizer (Sec. 4.3 "Differentiable Voxelization", Eq. 12):
  * V(x) = sum_i alpha_i exp(-1/2 (x - mu_i)^T Sigma_i^-1 (x - mu_i)) on the
  * X x Y x Z voxel grid, written to vol (DEVICE, [Z][Y][X], overwritten).

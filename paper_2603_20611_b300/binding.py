@@ -32,7 +32,7 @@ EXPORTS = (
     "gp_config_default", "gp_create", "gp_destroy", "gp_last_error", "gp_workspace_bytes",
     "gp_render_slices", "gp_render_backward", "gp_mse_grad", "gp_voxelize", "gp_voxelize_backward",
     "gp_last_counts", "gp_count_evals", "gp_exp2_eval", "gp_timing_enable", "gp_timing_read",
-    "gp_launch_count", "gp_fma_probe_threads", "gp_fma_probe",
+    "gp_launch_count", "gp_fma_probe_threads", "gp_fma_probe", "gp_mse_grad_noalloc",
 )
 GP_NUM_PHASES = 7
 PHASES = ("bin", "fwd", "bwd", "bwd_pre", "loss", "vox_fwd", "vox_bwd")
@@ -81,6 +81,7 @@ def _load():
         "gp_launch_count": [],
         "gp_fma_probe_threads": [P],
         "gp_fma_probe": [P, I, P, P],
+        "gp_mse_grad_noalloc": [P, P, P, I, I, I, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -252,6 +253,28 @@ def gp_mse_grad(ctx, I, T, t_index=None, dL_dI=None, loss=None, stream=None):
                          _dev(dL_dI, "dL_dI", shape=(S, H, W)),
                          None if loss is None else _dev(loss, "loss", shape=(1,)), _stream(stream))
     ctx.check(st, "gp_mse_grad")
+    return dL_dI, loss
+
+
+def gp_mse_grad_noalloc(I, T, t_index=None, dL_dI=None, loss=None, stream=None):
+    """gp_mse_grad without a context or any device allocation by the library
+    (scratch is a fixed array inside the library; see include/gp.h)."""
+    S, H, W = I.shape
+    if dL_dI is None:
+        dL_dI = torch.empty_like(I)
+    tid = None
+    if t_index is not None:
+        tid = np.ascontiguousarray(np.asarray(t_index, np.int32).reshape(-1))
+        if tid.shape[0] != S or int(tid.max(initial=0)) >= T.shape[0]:
+            raise ValueError("t_index needs one in-range entry per slice")
+    elif tuple(T.shape) != tuple(I.shape):
+        raise ValueError("T must match I when t_index is None")
+    st = lib.gp_mse_grad_noalloc(_dev(I, "I"), _dev(T, "T"),
+                                 None if tid is None else tid.ctypes.data_as(ctypes.c_void_p), S, H, W,
+                                 _dev(dL_dI, "dL_dI", shape=(S, H, W)),
+                                 None if loss is None else _dev(loss, "loss", shape=(1,)), _stream(stream))
+    if st != GP_OK:
+        raise GPError(st, "gp_mse_grad_noalloc")
     return dL_dI, loss
 
 
