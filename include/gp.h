@@ -79,8 +79,11 @@ typedef struct {
                              (bitwise repeatable); 0: warp-reduced atomics (default 0) */
   int exp_mode;           /* GP_EXP_POLY (default) or GP_EXP_HW */
   int tile;               /* screen tile side in pixels: 16 (default) or 8 */
-  int fwd_px;             /* pixels per thread in the forward rasteriser (0 = default) */
-  int bwd_px;             /* pixels per thread in the backward rasteriser (0 = default) */
+  int fwd_px;             /* forward rasteriser: 0 (default) = block-culled kernel (16x16
+                             tiles; 8x8 tiles use one pixel per thread), or the per-thread
+                             kernel with this many pixels per thread (16: 1, 2, 4; 8: 1, 2) */
+  int bwd_px;             /* backward rasteriser: 0 (default) = block-culled kernel, or the
+                             per-thread kernel (16: 2, 4, 8 pixels per thread; 8: 2) */
   int64_t workspace_limit;/* max device bytes of library scratch, 0 = no limit */
 } gp_config;
 

@@ -62,7 +62,7 @@ constexpr float kExpFloor = -125.0f;  // 2^-125 ~ 2.4e-38: below fp32 resolution
 //   r1 = (a_x, a_y, A, zr)                a = Sigma_{xy,z}/v, A = alpha/sqrt(det Sigma_2d),
 //                                         zr = axial half range sqrt(2 v ln(1/eps))
 //   r2 = (C00, C01, C11, rx)              C = Sigma_2d^-1, rx = k sqrt(Sigma_2d,xx)
-//   r3 = (ry, valid, 0, 0)                ry = k sqrt(Sigma_2d,yy)
+//   r3 = (ry, valid, 1/C00, 1/C11)        reciprocals for the ellipse-tile test
 struct __align__(16) SliceRec {
   float4 r0, r1, r2, r3;
 };
@@ -161,24 +161,25 @@ __device__ __forceinline__ float qform(float c00, float c01, float c11, float dx
 }
 
 // Minimum of q along one edge: the fixed coordinate offset is dfix, the free one
-// runs over [dlo, dhi]; the free-coordinate minimiser is -c01 dfix / c_var.
-__device__ __forceinline__ float edge_min(float c_fixed, float c01, float c_var, float dfix,
+// runs over [dlo, dhi]; the free-coordinate minimiser is -c01 dfix / c_var
+// (inv_var = 1 / c_var is precomputed per Gaussian).
+__device__ __forceinline__ float edge_min(float c_fixed, float c01, float c_var, float inv_var, float dfix,
                                           float dlo, float dhi, bool fixed_is_x) {
-  float dstar = __fdiv_rn(-__fmul_rn(c01, dfix), c_var);
+  float dstar = __fmul_rn(-__fmul_rn(c01, dfix), inv_var);
   dstar = fminf(fmaxf(dstar, dlo), dhi);
   return fixed_is_x ? qform(c_fixed, c01, c_var, dfix, dstar) : qform(c_var, c01, c_fixed, dstar, dfix);
 }
 
-__device__ __forceinline__ bool ellipse_hits_rect(float mx, float my, float c00, float c01,
-                                                  float c11, float k2, float x0, float x1,
+__device__ __forceinline__ bool ellipse_hits_rect(float mx, float my, float c00, float c01, float c11,
+                                                  float inv00, float inv11, float k2, float x0, float x1,
                                                   float y0, float y1) {
   if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
   float dxl = __fsub_rn(x0, mx), dxh = __fsub_rn(x1, mx);
   float dyl = __fsub_rn(y0, my), dyh = __fsub_rn(y1, my);
-  float m = edge_min(c00, c01, c11, dxl, dyl, dyh, true);
-  m = fminf(m, edge_min(c00, c01, c11, dxh, dyl, dyh, true));
-  m = fminf(m, edge_min(c11, c01, c00, dyl, dxl, dxh, false));
-  m = fminf(m, edge_min(c11, c01, c00, dyh, dxl, dxh, false));
+  float m = edge_min(c00, c01, c11, inv11, dxl, dyl, dyh, true);
+  m = fminf(m, edge_min(c00, c01, c11, inv11, dxh, dyl, dyh, true));
+  m = fminf(m, edge_min(c11, c01, c00, inv00, dyl, dxl, dxh, false));
+  m = fminf(m, edge_min(c11, c01, c00, inv00, dyh, dxl, dxh, false));
   return m <= k2;
 }
 

@@ -16,6 +16,8 @@ template <typename T>
 cudaError_t exclusive_scan(const T* in, T* out, int64_t n, unsigned long long* total, void* temp,
                            cudaStream_t st);
 int64_t radix_temp_bytes(int64_t cap);
+// The first pass takes the identity 0..n-1 as input values (vals is not read);
+// later passes ping-pong between vals and vals_alt.
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                              const unsigned long long* n_dev, uint32_t cap, int bits, void* temp,
                              cudaStream_t st, bool* result_in_alt);

@@ -134,8 +134,8 @@ static gp_status check_set(Ctx* c, const gp_set* s) {
 }
 
 static int tile_of(const Ctx* c) { return c->cfg.tile == 8 ? 8 : 16; }
-static int fwd_px(const Ctx* c) { return c->cfg.fwd_px > 0 ? c->cfg.fwd_px : 1; }
-static int bwd_px(const Ctx* c) { return c->cfg.bwd_px > 0 ? c->cfg.bwd_px : (c->cfg.tile == 8 ? 2 : 4); }
+static int fwd_px(const Ctx* c) { return c->cfg.fwd_px; }
+static int bwd_px(const Ctx* c) { return c->cfg.bwd_px; }
 
 // Sorts the sorted keys' pairs after emission; shared tail of both binnings.
 static gp_status sort_and_range(Ctx* c, uint32_t P, int64_t nkeys, cudaStream_t st, const uint32_t** sorted_vals) {

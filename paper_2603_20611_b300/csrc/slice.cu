@@ -71,31 +71,52 @@ __device__ __forceinline__ int clamp_tile(float t, int nt) {
 // |mu_z - z_s| <= zr, tiles whose pixel-centre rectangle the ellipse
 // d^T C d <= k2 around mu_2d touches.  Arithmetic uses explicit rounding so every
 // caller takes identical decisions.
+// Planes of one Gaussian: sorted positions [lo, hi) with |mu_z - z_s| <= zr.
+__device__ __forceinline__ void plane_range(const SliceArgs& a, const SliceRec& r, int& lo, int& hi) {
+  const float mz = r.r0.z, zr = r.r1.w;
+  lo = lower_bound_f(a.zs, a.S, __fsub_rn(mz, zr));
+  hi = upper_bound_f(a.zs, a.S, __fadd_rn(mz, zr));
+}
+
+// mu_2d on sorted plane j and the clamped tile bounding box of the ellipse.
+struct PlaneBox {
+  float mx, my;
+  int tx0, tx1, ty0, ty1;
+};
+
+__device__ __forceinline__ PlaneBox plane_box(const SliceArgs& a, const SliceRec& r, int j) {
+  PlaneBox b;
+  const float inv_tile = 1.0f / (float)a.tile;
+  const float rx = r.r2.w, ry = r.r3.x;
+  const float d = __fsub_rn(r.r0.z, a.zs[j]);
+  b.mx = __fsub_rn(r.r0.x, __fmul_rn(r.r1.x, d));
+  b.my = __fsub_rn(r.r0.y, __fmul_rn(r.r1.y, d));
+  b.tx0 = max(0, clamp_tile(__fmul_rn(__fsub_rn(__fsub_rn(b.mx, rx), 0.5f), inv_tile), a.TX));
+  b.tx1 = min(a.TX - 1, clamp_tile(__fmul_rn(__fsub_rn(__fadd_rn(b.mx, rx), 0.5f), inv_tile), a.TX));
+  b.ty0 = max(0, clamp_tile(__fmul_rn(__fsub_rn(__fsub_rn(b.my, ry), 0.5f), inv_tile), a.TY));
+  b.ty1 = min(a.TY - 1, clamp_tile(__fmul_rn(__fsub_rn(__fadd_rn(b.my, ry), 0.5f), inv_tile), a.TY));
+  return b;
+}
+
+__device__ __forceinline__ bool tile_hit(const SliceArgs& a, const SliceRec& r, const PlaneBox& b, int tx,
+                                         int ty) {
+  const float y0 = (float)(ty * a.tile) + 0.5f;
+  const float y1 = (float)(min((ty + 1) * a.tile, a.H)) - 0.5f;
+  const float x0 = (float)(tx * a.tile) + 0.5f;
+  const float x1 = (float)(min((tx + 1) * a.tile, a.W)) - 0.5f;
+  return ellipse_hits_rect(b.mx, b.my, r.r2.x, r.r2.y, r.r2.z, r.r3.z, r.r3.w, a.k2, x0, x1, y0, y1);
+}
+
 template <class F>
 __device__ __forceinline__ void for_each_pair(const SliceArgs& a, const SliceRec& r, F&& f) {
   if (r.r3.y == 0.0f) return;
-  const float mz = r.r0.z, zr = r.r1.w;
-  const int lo = lower_bound_f(a.zs, a.S, __fsub_rn(mz, zr));
-  const int hi = upper_bound_f(a.zs, a.S, __fadd_rn(mz, zr));
-  const float rx = r.r2.w, ry = r.r3.x;
-  const float inv_tile = 1.0f / (float)a.tile;
+  int lo, hi;
+  plane_range(a, r, lo, hi);
   for (int j = lo; j < hi; ++j) {
-    float d = __fsub_rn(mz, a.zs[j]);
-    float mx = __fsub_rn(r.r0.x, __fmul_rn(r.r1.x, d));
-    float my = __fsub_rn(r.r0.y, __fmul_rn(r.r1.y, d));
-    int tx0 = max(0, clamp_tile(__fmul_rn(__fsub_rn(__fsub_rn(mx, rx), 0.5f), inv_tile), a.TX));
-    int tx1 = min(a.TX - 1, clamp_tile(__fmul_rn(__fsub_rn(__fadd_rn(mx, rx), 0.5f), inv_tile), a.TX));
-    int ty0 = max(0, clamp_tile(__fmul_rn(__fsub_rn(__fsub_rn(my, ry), 0.5f), inv_tile), a.TY));
-    int ty1 = min(a.TY - 1, clamp_tile(__fmul_rn(__fsub_rn(__fadd_rn(my, ry), 0.5f), inv_tile), a.TY));
-    for (int ty = ty0; ty <= ty1; ++ty) {
-      float y0 = (float)(ty * a.tile) + 0.5f;
-      float y1 = (float)(min((ty + 1) * a.tile, a.H)) - 0.5f;
-      for (int tx = tx0; tx <= tx1; ++tx) {
-        float x0 = (float)(tx * a.tile) + 0.5f;
-        float x1 = (float)(min((tx + 1) * a.tile, a.W)) - 0.5f;
-        if (ellipse_hits_rect(mx, my, r.r2.x, r.r2.y, r.r2.z, a.k2, x0, x1, y0, y1)) f(j, ty * a.TX + tx);
-      }
-    }
+    const PlaneBox b = plane_box(a, r, j);
+    for (int ty = b.ty0; ty <= b.ty1; ++ty)
+      for (int tx = b.tx0; tx <= b.tx1; ++tx)
+        if (tile_hit(a, r, b, tx, ty)) f(j, ty * a.TX + tx);
   }
 }
 
@@ -126,7 +147,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_slice_pre(SliceArgs a, SliceRec
   r.r0 = make_float4(mux, muy, muz, iv);
   r.r1 = make_float4(ax, ay, a.alpha[i] / sqrtf(det), sqrtf(a.k2 * v));
   r.r2 = make_float4(syy * idet, -sxy * idet, sxx * idet, sqrtf(a.k2 * sxx));
-  r.r3 = make_float4(sqrtf(a.k2 * syy), valid ? 1.0f : 0.0f, 0.0f, 0.0f);
+  r.r3 = make_float4(sqrtf(a.k2 * syy), valid ? 1.0f : 0.0f, det / syy, det / sxx);
   rec[i] = r;
   unsigned long long cnt = 0;
   for_each_pair(a, r, [&](int, int) { ++cnt; });
@@ -140,34 +161,62 @@ void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* cou
 }
 
 // ------------------------------------------------------------ K-emit
-__global__ void __launch_bounds__(PRE_THREADS) k_slice_emit(SliceArgs a, const SliceRec* __restrict__ rec,
-                                                            const unsigned long long* __restrict__ offsets,
-                                                            const unsigned long long* __restrict__ counts,
-                                                            uint32_t* __restrict__ keys,
-                                                            uint32_t* __restrict__ vals,
-                                                            uint32_t* __restrict__ emit_gid) {
-  int i = blockIdx.x * PRE_THREADS + threadIdx.x;
-  if (i >= a.n) return;
-  SliceRec r = rec[i];
-  uint32_t e = (uint32_t)offsets[i];
-  const uint32_t e_end = (uint32_t)(offsets[i] + counts[i]);  // never write past this Gaussian's slots
+// One warp per Gaussian: for each of its planes the lanes take the candidate
+// tiles of the bounding box in row-major order, test them, and the hits are
+// compacted with a ballot and written contiguously (coalesced), in the same
+// order as the enumeration K-pre counted.
+constexpr int EMIT_WARPS = 8;
+
+__global__ void __launch_bounds__(EMIT_WARPS * 32) k_slice_emit(SliceArgs a, const SliceRec* __restrict__ rec,
+                                                                const unsigned long long* __restrict__ offsets,
+                                                                const unsigned long long* __restrict__ counts,
+                                                                uint32_t* __restrict__ keys,
+                                                                uint32_t* __restrict__ emit_gid) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * EMIT_WARPS;
   const uint32_t T = (uint32_t)(a.TX * a.TY);
-  for_each_pair(a, r, [&](int j, int tile) {
-    if (e < e_end) {
-      uint32_t s = (uint32_t)a.zorder[j];
-      keys[e] = s * T + (uint32_t)tile;
-      vals[e] = e;
-      emit_gid[e] = (uint32_t)i;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int i = blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); i < a.n; i += nwarps) {
+    const SliceRec r = rec[i];
+    if (r.r3.y == 0.0f) continue;
+    uint32_t e = (uint32_t)offsets[i];
+    const uint32_t e_end = (uint32_t)(offsets[i] + counts[i]);  // never write past this Gaussian's slots
+    int lo, hi;
+    plane_range(a, r, lo, hi);
+    for (int j = lo; j < hi; ++j) {
+      const PlaneBox b = plane_box(a, r, j);
+      const int nx = b.tx1 - b.tx0 + 1, ny = b.ty1 - b.ty0 + 1;
+      if (nx <= 0 || ny <= 0) continue;
+      const int nt = nx * ny;
+      const uint32_t s = (uint32_t)a.zorder[j];
+      for (int k0 = 0; k0 < nt; k0 += 32) {
+        const int k = k0 + lane;
+        int ty = 0, tx = 0;
+        bool hit = false;
+        if (k < nt) {
+          ty = b.ty0 + k / nx;
+          tx = b.tx0 + (k - (k / nx) * nx);
+          hit = tile_hit(a, r, b, tx, ty);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        const uint32_t pos = e + (uint32_t)__popc(m & lt);
+        if (hit && pos < e_end) {
+          keys[pos] = s * T + (uint32_t)(ty * a.TX + tx);
+          emit_gid[pos] = (uint32_t)i;
+        }
+        e += (uint32_t)__popc(m);
+      }
     }
-    ++e;
-  });
+  }
 }
 
 void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* offsets,
                        const unsigned long long* counts, uint32_t* keys, uint32_t* vals, uint32_t* emit_gid,
                        cudaStream_t st) {
+  (void)vals;  // the sort generates the identity values itself
   if (a.n <= 0) return;
-  k_slice_emit<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, offsets, counts, keys, vals, emit_gid);
+  const int blocks = (int)std::min<int64_t>(((int64_t)a.n + EMIT_WARPS - 1) / EMIT_WARPS, 148 * 64);
+  k_slice_emit<<<blocks, EMIT_WARPS * 32, 0, st>>>(a, rec, offsets, counts, keys, emit_gid);
   note_launch();
 }
 
@@ -288,12 +337,16 @@ static cudaError_t fwd_dispatch(const SliceArgs& a, int exp_mode, const SliceRec
 }
 
 bool fwd_px_supported(int tile, int px) {
-  return tile == 16 ? (px == 1 || px == 2 || px == 4) : (tile == 8 ? (px == 1 || px == 2) : false);
+  return px == 0 || (tile == 16 ? (px == 1 || px == 2 || px == 4) : (tile == 8 ? (px == 1 || px == 2) : false));
 }
 
 cudaError_t launch_raster_fwd(const SliceArgs& a, int px, int exp_mode, const SliceRec* rec,
                               const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
                               float* out, cudaStream_t st) {
+  if (px == 0) {
+    if (a.tile == 16) return launch_raster_fwd_blocked(a, exp_mode, rec, vals, emit_gid, ranges, out, st);
+    px = 1;
+  }
   if (a.tile == 16) {
     switch (px) {
       case 1: return fwd_dispatch<16, 1>(a, exp_mode, rec, vals, emit_gid, ranges, out, st);
@@ -466,12 +519,17 @@ static cudaError_t bwd_dispatch(const SliceArgs& a, int exp_mode, bool det, cons
 }
 
 bool bwd_px_supported(int tile, int px) {
-  return tile == 16 ? (px == 2 || px == 4 || px == 8) : (tile == 8 ? px == 2 : false);
+  return px == 0 || (tile == 16 ? (px == 2 || px == 4 || px == 8) : (tile == 8 ? px == 2 : false));
 }
 
 cudaError_t launch_raster_bwd(const SliceArgs& a, int px, int exp_mode, bool det, const SliceRec* rec,
                               const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
                               const float* dL_dI, float* accum, float4* partial, cudaStream_t st) {
+  if (px == 0) {
+    if (a.tile == 16)
+      return launch_raster_bwd_blocked(a, exp_mode, det, rec, vals, emit_gid, ranges, dL_dI, accum, partial, st);
+    px = 2;
+  }
   if (a.tile == 16) {
     switch (px) {
       case 2: return bwd_dispatch<16, 2>(a, exp_mode, det, rec, vals, emit_gid, ranges, dL_dI, accum, partial, st);

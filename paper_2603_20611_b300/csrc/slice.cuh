@@ -59,7 +59,15 @@ void launch_count_evals(const SliceArgs& a, const SliceRec* rec, unsigned long l
                         cudaStream_t st);
 void launch_exp2_eval(const float* x, float* y, int64_t n, int mode, cudaStream_t st);
 
-// Supported pixels-per-thread of the rasterisers for a tile side.
+// Block-culled rasterisers (raster.cu), the default for 16 x 16 tiles.
+cudaError_t launch_raster_fwd_blocked(const SliceArgs& a, int exp_mode, const SliceRec* rec, const uint32_t* vals,
+                                      const uint32_t* emit_gid, const uint2* ranges, float* out, cudaStream_t st);
+cudaError_t launch_raster_bwd_blocked(const SliceArgs& a, int exp_mode, bool det, const SliceRec* rec,
+                                      const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
+                                      const float* dL_dI, float* accum, float4* partial, cudaStream_t st);
+
+// Supported pixels-per-thread of the rasterisers for a tile side (0 = the
+// default: block-culled kernel for 16 x 16 tiles, one pixel per thread for 8 x 8).
 bool fwd_px_supported(int tile, int px);
 bool bwd_px_supported(int tile, int px);
 

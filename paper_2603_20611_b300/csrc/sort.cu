@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     uint32_t i = round0 + t;
     bool valid = i < n;
     uint32_t key = valid ? kin[i] : 0u;
-    uint32_t val = valid ? vin[i] : 0u;
+    uint32_t val = valid ? (vin ? vin[i] : i) : 0u;  // no input values: the identity
     uint32_t d = valid ? ((key >> shift) & 0xffu) : (RS_BINS + lane);
     uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t rank = __popc(peers & lt_mask);
@@ -243,7 +243,7 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
     k_radix_hist<<<nb, RS_THREADS, 0, st>>>(ki, n_dev, cap, shift, hist, nb);
     cudaError_t e = exclusive_scan<uint32_t>(hist, hist, nh, nullptr, stemp, st);
     if (e != cudaSuccess) return e;
-    k_radix_scatter<<<nb, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n_dev, cap, shift, hist, nb);
+    k_radix_scatter<<<nb, RS_THREADS, 0, st>>>(ki, shift == 0 ? nullptr : vi, ko, vo, n_dev, cap, shift, hist, nb);
     note_launch(2);
     uint32_t* tk = ki; ki = ko; ko = tk;
     uint32_t* tv = vi; vi = vo; vo = tv;

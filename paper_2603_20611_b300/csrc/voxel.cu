@@ -118,7 +118,6 @@ __global__ void __launch_bounds__(VPRE_THREADS) k_vox_emit(VoxArgs a, const VoxR
       for (int tx = b.x0; tx <= b.x1; ++tx) {
         if (e < e_end) {
           keys[e] = (uint32_t)((tz * a.TY + ty) * a.TX + tx);
-          vals[e] = e;
           emit_gid[e] = (uint32_t)i;
         }
         ++e;

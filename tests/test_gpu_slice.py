@@ -66,7 +66,7 @@ def test_forward_small_full(ctx):
 
 
 @pytest.mark.parametrize("axis", [0, 1, 2])
-@pytest.mark.parametrize("tile,fpx", [(16, 1), (16, 2), (16, 4), (8, 1), (8, 2)])
+@pytest.mark.parametrize("tile,fpx", [(16, 0), (16, 1), (16, 2), (16, 4), (8, 0), (8, 1), (8, 2)])
 def test_forward_ragged_axes_tiles(axis, tile, fpx):
     """Ragged image (37 x 45, not a tile multiple), unsorted and off-centre planes,
     slices through each axis, every tile size and pixels-per-thread variant."""
@@ -183,7 +183,7 @@ def test_backward_small_full(ctx):
 
 
 @pytest.mark.parametrize("axis", [0, 1])
-@pytest.mark.parametrize("tile,bpx", [(16, 2), (16, 4), (16, 8), (8, 2)])
+@pytest.mark.parametrize("tile,bpx", [(16, 0), (16, 2), (16, 4), (16, 8), (8, 0), (8, 2)])
 def test_backward_ragged_axes_tiles(axis, tile, bpx):
     c = B.Context(0, tile=tile, bwd_px=bpx)
     g = synth.small(seed=88, n=300, extent=(29, 35, 26))
