@@ -78,46 +78,90 @@ __device__ __forceinline__ void plane_range(const SliceArgs& a, const SliceRec& 
   hi = upper_bound_f(a.zs, a.S, __fadd_rn(mz, zr));
 }
 
-// mu_2d on sorted plane j and the clamped tile bounding box of the ellipse.
+// mu_2d on sorted plane j and the clamped range of tile rows the ellipse spans.
 struct PlaneBox {
   float mx, my;
-  int tx0, tx1, ty0, ty1;
+  int ty0, ty1;
 };
 
 __device__ __forceinline__ PlaneBox plane_box(const SliceArgs& a, const SliceRec& r, int j) {
   PlaneBox b;
   const float inv_tile = 1.0f / (float)a.tile;
-  const float rx = r.r2.w, ry = r.r3.x;
+  const float ry = r.r3.x;
   const float d = __fsub_rn(r.r0.z, a.zs[j]);
   b.mx = __fsub_rn(r.r0.x, __fmul_rn(r.r1.x, d));
   b.my = __fsub_rn(r.r0.y, __fmul_rn(r.r1.y, d));
-  b.tx0 = max(0, clamp_tile(__fmul_rn(__fsub_rn(__fsub_rn(b.mx, rx), 0.5f), inv_tile), a.TX));
-  b.tx1 = min(a.TX - 1, clamp_tile(__fmul_rn(__fsub_rn(__fadd_rn(b.mx, rx), 0.5f), inv_tile), a.TX));
   b.ty0 = max(0, clamp_tile(__fmul_rn(__fsub_rn(__fsub_rn(b.my, ry), 0.5f), inv_tile), a.TY));
   b.ty1 = min(a.TY - 1, clamp_tile(__fmul_rn(__fsub_rn(__fadd_rn(b.my, ry), 0.5f), inv_tile), a.TY));
   return b;
 }
 
-__device__ __forceinline__ bool tile_hit(const SliceArgs& a, const SliceRec& r, const PlaneBox& b, int tx,
-                                         int ty) {
+// Tile columns [*lo, *hi] of tile row ty whose pixel-centre rectangle the ellipse
+// d^T C d <= k2 touches.  Over the row's band of pixel-centre heights the ellipse
+// spans x in [xmin, xmax]: with s = C01/C00 and D = C11 - C01 s, the chord at
+// height dy is centred on -s dy with half-width sqrt((k2 - D dy^2)/C00), and its
+// right (left) end is largest (smallest) at the tangent height dy_t = -C01 rx/C11
+// (-dy_t), clamped to the band.  A tile is touched iff its x-range meets
+// [xmin, xmax].  Explicit roundings keep the count and the emission identical.
+__device__ __forceinline__ bool row_tiles(const SliceArgs& a, const SliceRec& r, const PlaneBox& b, int ty,
+                                          int* lo, int* hi) {
+  const float c00 = r.r2.x, c01 = r.r2.y, c11 = r.r2.z, rx = r.r2.w, ry = r.r3.x;
+  const float inv00 = r.r3.z, inv11 = r.r3.w;
   const float y0 = (float)(ty * a.tile) + 0.5f;
   const float y1 = (float)(min((ty + 1) * a.tile, a.H)) - 0.5f;
-  const float x0 = (float)(tx * a.tile) + 0.5f;
-  const float x1 = (float)(min((tx + 1) * a.tile, a.W)) - 0.5f;
-  return ellipse_hits_rect(b.mx, b.my, r.r2.x, r.r2.y, r.r2.z, r.r3.z, r.r3.w, a.k2, x0, x1, y0, y1);
+  const float dya = fmaxf(__fsub_rn(y0, b.my), -ry);
+  const float dyb = fminf(__fsub_rn(y1, b.my), ry);
+  if (dya > dyb) return false;
+  const float s = __fmul_rn(c01, inv00);
+  const float D = __fsub_rn(c11, __fmul_rn(c01, s));
+  const float dyt = -__fmul_rn(__fmul_rn(c01, inv11), rx);
+  const float dM = fminf(fmaxf(dyt, dya), dyb);
+  const float dm = fminf(fmaxf(-dyt, dya), dyb);
+  const float wM = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(a.k2, __fmul_rn(D, __fmul_rn(dM, dM))), inv00), 0.0f));
+  const float wm = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(a.k2, __fmul_rn(D, __fmul_rn(dm, dm))), inv00), 0.0f));
+  const float xmax = __fadd_rn(__fsub_rn(b.mx, __fmul_rn(s, dM)), wM);
+  const float xmin = __fsub_rn(__fsub_rn(b.mx, __fmul_rn(s, dm)), wm);
+  const float inv_tile = 1.0f / (float)a.tile;
+  // tile tx spans pixel centres [tx T + 0.5, (tx + 1) T - 0.5] (the last one ends at W - 0.5)
+  int l = max(0, clamp_tile(__fmul_rn(__fadd_rn(xmin, 0.5f), inv_tile), a.TX + 1) - 1);
+  const float lf = __fsub_rn(__fmul_rn(__fadd_rn(xmin, 0.5f), inv_tile), 1.0f);
+  if ((float)l < lf) l += 1;  // ceil of (xmin + 0.5)/T - 1
+  int h = min(a.TX - 1, clamp_tile(__fmul_rn(__fsub_rn(xmax, 0.5f), inv_tile), a.TX));
+  if (h == a.TX - 1 && xmin > (float)a.W - 0.5f) h = a.TX - 2;
+  *lo = l;
+  *hi = h;
+  return h >= l;
 }
 
 template <class F>
 __device__ __forceinline__ void for_each_pair(const SliceArgs& a, const SliceRec& r, F&& f) {
   if (r.r3.y == 0.0f) return;
-  int lo, hi;
-  plane_range(a, r, lo, hi);
-  for (int j = lo; j < hi; ++j) {
+  int plo, phi;
+  plane_range(a, r, plo, phi);
+  for (int j = plo; j < phi; ++j) {
     const PlaneBox b = plane_box(a, r, j);
-    for (int ty = b.ty0; ty <= b.ty1; ++ty)
-      for (int tx = b.tx0; tx <= b.tx1; ++tx)
-        if (tile_hit(a, r, b, tx, ty)) f(j, ty * a.TX + tx);
+    for (int ty = b.ty0; ty <= b.ty1; ++ty) {
+      int lo, hi;
+      if (!row_tiles(a, r, b, ty, &lo, &hi)) continue;
+      for (int tx = lo; tx <= hi; ++tx) f(j, ty * a.TX + tx);
+    }
   }
+}
+
+// Number of pairs of one Gaussian (same enumeration, whole runs at a time).
+__device__ __forceinline__ unsigned long long count_pairs(const SliceArgs& a, const SliceRec& r) {
+  if (r.r3.y == 0.0f) return 0;
+  int plo, phi;
+  plane_range(a, r, plo, phi);
+  unsigned long long c = 0;
+  for (int j = plo; j < phi; ++j) {
+    const PlaneBox b = plane_box(a, r, j);
+    for (int ty = b.ty0; ty <= b.ty1; ++ty) {
+      int lo, hi;
+      if (row_tiles(a, r, b, ty, &lo, &hi)) c += (unsigned long long)(hi - lo + 1);
+    }
+  }
+  return c;
 }
 
 __global__ void __launch_bounds__(PRE_THREADS) k_slice_pre(SliceArgs a, SliceRec* __restrict__ rec,
@@ -149,9 +193,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_slice_pre(SliceArgs a, SliceRec
   r.r2 = make_float4(syy * idet, -sxy * idet, sxx * idet, sqrtf(a.k2 * sxx));
   r.r3 = make_float4(sqrtf(a.k2 * syy), valid ? 1.0f : 0.0f, det / syy, det / sxx);
   rec[i] = r;
-  unsigned long long cnt = 0;
-  for_each_pair(a, r, [&](int, int) { ++cnt; });
-  counts[i] = cnt;
+  counts[i] = count_pairs(a, r);
 }
 
 void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
@@ -161,52 +203,52 @@ void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* cou
 }
 
 // ------------------------------------------------------------ K-emit
-// One warp per Gaussian: for each of its planes the lanes take the candidate
-// tiles of the bounding box in row-major order, test them, and the hits are
-// compacted with a ballot and written contiguously (coalesced), in the same
-// order as the enumeration K-pre counted.
-constexpr int EMIT_WARPS = 8;
+// One thread per Gaussian, enumerating exactly as K-pre counted.  The 32
+// Gaussians of a warp own one contiguous run of the output (their offsets are
+// consecutive), so the warp gathers its pairs in a shared-memory window and
+// writes the window with coalesced stores.
+constexpr int EMIT_THREADS = 128;
+constexpr int EMIT_WIN = 1024;  // pairs per warp window
 
-__global__ void __launch_bounds__(EMIT_WARPS * 32) k_slice_emit(SliceArgs a, const SliceRec* __restrict__ rec,
-                                                                const unsigned long long* __restrict__ offsets,
-                                                                const unsigned long long* __restrict__ counts,
-                                                                uint32_t* __restrict__ keys,
-                                                                uint32_t* __restrict__ emit_gid) {
-  const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * EMIT_WARPS;
+__global__ void __launch_bounds__(EMIT_THREADS) k_slice_emit(SliceArgs a, const SliceRec* __restrict__ rec,
+                                                             const unsigned long long* __restrict__ offsets,
+                                                             const unsigned long long* __restrict__ counts,
+                                                             uint32_t* __restrict__ keys,
+                                                             uint32_t* __restrict__ emit_gid) {
+  __shared__ uint32_t wkey[EMIT_THREADS / 32][EMIT_WIN];
+  __shared__ uint32_t wgid[EMIT_THREADS / 32][EMIT_WIN];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * EMIT_THREADS + threadIdx.x;
+  const int i0 = i - lane;
+  if (i0 >= a.n) return;  // whole warp past the end
+  const int ilast = min(i0 + 31, a.n - 1);
+  const unsigned long long wstart = offsets[i0];
+  const unsigned long long wend = offsets[ilast] + counts[ilast];
+  const bool mine = i < a.n;
+  const unsigned long long my0 = mine ? offsets[i] : 0ull;
+  const unsigned long long my1 = mine ? my0 + counts[i] : 0ull;
+  SliceRec r;
+  if (mine) r = rec[i];
   const uint32_t T = (uint32_t)(a.TX * a.TY);
-  const unsigned lt = (1u << lane) - 1u;
-  for (int i = blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); i < a.n; i += nwarps) {
-    const SliceRec r = rec[i];
-    if (r.r3.y == 0.0f) continue;
-    uint32_t e = (uint32_t)offsets[i];
-    const uint32_t e_end = (uint32_t)(offsets[i] + counts[i]);  // never write past this Gaussian's slots
-    int lo, hi;
-    plane_range(a, r, lo, hi);
-    for (int j = lo; j < hi; ++j) {
-      const PlaneBox b = plane_box(a, r, j);
-      const int nx = b.tx1 - b.tx0 + 1, ny = b.ty1 - b.ty0 + 1;
-      if (nx <= 0 || ny <= 0) continue;
-      const int nt = nx * ny;
-      const uint32_t s = (uint32_t)a.zorder[j];
-      for (int k0 = 0; k0 < nt; k0 += 32) {
-        const int k = k0 + lane;
-        int ty = 0, tx = 0;
-        bool hit = false;
-        if (k < nt) {
-          ty = b.ty0 + k / nx;
-          tx = b.tx0 + (k - (k / nx) * nx);
-          hit = tile_hit(a, r, b, tx, ty);
+  for (unsigned long long wb = wstart; wb < wend; wb += EMIT_WIN) {
+    const unsigned long long we = wb + EMIT_WIN;
+    if (mine && my1 > wb && my0 < we) {
+      unsigned long long e = my0;
+      for_each_pair(a, r, [&](int j, int tile) {
+        if (e >= wb && e < we && e < my1) {
+          wkey[warp][e - wb] = (uint32_t)a.zorder[j] * T + (uint32_t)tile;
+          wgid[warp][e - wb] = (uint32_t)i;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
-        const uint32_t pos = e + (uint32_t)__popc(m & lt);
-        if (hit && pos < e_end) {
-          keys[pos] = s * T + (uint32_t)(ty * a.TX + tx);
-          emit_gid[pos] = (uint32_t)i;
-        }
-        e += (uint32_t)__popc(m);
-      }
+        ++e;
+      });
     }
+    __syncwarp();
+    const int cnt = (int)min((unsigned long long)EMIT_WIN, wend - wb);
+    for (int k = lane; k < cnt; k += 32) {
+      keys[wb + k] = wkey[warp][k];
+      emit_gid[wb + k] = wgid[warp][k];
+    }
+    __syncwarp();
   }
 }
 
@@ -215,8 +257,7 @@ void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned l
                        cudaStream_t st) {
   (void)vals;  // the sort generates the identity values itself
   if (a.n <= 0) return;
-  const int blocks = (int)std::min<int64_t>(((int64_t)a.n + EMIT_WARPS - 1) / EMIT_WARPS, 148 * 64);
-  k_slice_emit<<<blocks, EMIT_WARPS * 32, 0, st>>>(a, rec, offsets, counts, keys, emit_gid);
+  k_slice_emit<<<ceil_div(a.n, EMIT_THREADS), EMIT_THREADS, 0, st>>>(a, rec, offsets, counts, keys, emit_gid);
   note_launch();
 }
 

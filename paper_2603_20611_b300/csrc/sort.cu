@@ -177,49 +177,63 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __res
   hist[(size_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
 }
 
+// Stable scatter of one 4096-key tile.  Warp w owns the tile's keys
+// [w * 512, (w + 1) * 512) and ranks them in 16 rounds of 32 against its own
+// per-digit counters (match_any gives the rank among equal digits in a round),
+// keeping key, value and rank in registers.  One block-wide pass then turns the
+// per-warp digit counts into output offsets (global digit base of the tile from
+// the scanned histogram, then warps in order), and every key is written once.
+constexpr int RS_PER_WARP = RS_TILE / RS_WARPS;     // 512 keys
+constexpr int RS_ROUNDS_W = RS_PER_WARP / 32;       // 16 rounds
+
 __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const unsigned long long* __restrict__ n_dev, uint32_t cap, int shift,
     const uint32_t* __restrict__ hist, int nb) {
-  __shared__ uint32_t base_d[RS_BINS];
   __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  uint32_t n = load_count(n_dev, cap);
-  uint32_t tile0 = blockIdx.x * RS_TILE;
+  const uint32_t n = load_count(n_dev, cap);
+  const uint32_t tile0 = blockIdx.x * RS_TILE;
   if (tile0 >= n) return;  // uniform across the block
-  base_d[t] = hist[(size_t)t * nb + blockIdx.x];
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  for (int r = 0; r < RS_ROUNDS; ++r) {
-    uint32_t round0 = tile0 + r * RS_THREADS;
-    if (round0 >= n) break;  // uniform
 #pragma unroll
-    for (int w = 0; w < RS_WARPS; ++w) wcnt[w][t] = 0;
-    __syncthreads();
-    uint32_t i = round0 + t;
-    bool valid = i < n;
-    uint32_t key = valid ? kin[i] : 0u;
-    uint32_t val = valid ? (vin ? vin[i] : i) : 0u;  // no input values: the identity
-    uint32_t d = valid ? ((key >> shift) & 0xffu) : (RS_BINS + lane);
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t rank = __popc(peers & lt_mask);
-    if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
-    __syncthreads();
-    // thread t owns digit t: exclusive prefix over warps, and the round total
-    uint32_t run = 0;
+  for (int w = 0; w < RS_WARPS; ++w) wcnt[w][t] = 0;
+  __syncthreads();
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint32_t base = tile0 + warp * RS_PER_WARP;
+  uint32_t key[RS_ROUNDS_W], val[RS_ROUNDS_W], rank[RS_ROUNDS_W];
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS_W; ++r) {
+    const uint32_t i = base + r * 32 + lane;
+    const bool valid = i < n;
+    key[r] = valid ? kin[i] : 0u;
+    val[r] = valid ? (vin ? vin[i] : i) : 0u;  // no input values: the identity
+    const uint32_t d = valid ? ((key[r] >> shift) & 0xffu) : (RS_BINS + lane);
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t c = 0u;
+    if (valid) c = wcnt[warp][d];
+    rank[r] = valid ? c + __popc(peers & lt_mask) : 0xffffffffu;
+    __syncwarp();
+    if (valid && __popc(peers & lt_mask) == 0) wcnt[warp][d] = c + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    uint32_t run = hist[(size_t)t * nb + blockIdx.x];
 #pragma unroll
     for (int w = 0; w < RS_WARPS; ++w) {
-      uint32_t c = wcnt[w][t];
+      const uint32_t c = wcnt[w][t];
       wcnt[w][t] = run;
       run += c;
     }
-    __syncthreads();
-    if (valid) {
-      uint32_t pos = base_d[d] + wcnt[warp][d] + rank;
-      kout[pos] = key;
-      vout[pos] = val;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS_W; ++r) {
+    if (rank[r] != 0xffffffffu) {
+      const uint32_t pos = wcnt[warp][(key[r] >> shift) & 0xffu] + rank[r];
+      kout[pos] = key[r];
+      vout[pos] = val[r];
     }
-    __syncthreads();
-    base_d[t] += run;
   }
 }
 
