@@ -180,9 +180,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __res
 // Stable scatter of one 4096-key tile.  Warp w owns the tile's keys
 // [w * 512, (w + 1) * 512) and ranks them in 16 rounds of 32 against its own
 // per-digit counters (match_any gives the rank among equal digits in a round),
-// keeping key, value and rank in registers.  One block-wide pass then turns the
-// per-warp digit counts into output offsets (global digit base of the tile from
-// the scanned histogram, then warps in order), and every key is written once.
+// keeping key, value and rank in registers.  A block-wide pass turns the
+// per-warp counts into tile-local digit offsets; the keys are first placed in
+// shared memory in digit order (a stable local sort), and then written out in
+// that order, so each digit's run leaves the block as contiguous stores.
 constexpr int RS_PER_WARP = RS_TILE / RS_WARPS;     // 512 keys
 constexpr int RS_ROUNDS_W = RS_PER_WARP / 32;       // 16 rounds
 
@@ -191,6 +192,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     uint32_t* __restrict__ vout, const unsigned long long* __restrict__ n_dev, uint32_t cap, int shift,
     const uint32_t* __restrict__ hist, int nb) {
   __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
+  __shared__ uint32_t dlocal[RS_BINS];   // tile-local start of each digit
+  __shared__ uint32_t dglobal[RS_BINS];  // global start of each digit of this tile
+  __shared__ uint32_t skey[RS_TILE], sval[RS_TILE];
+  __shared__ uint32_t swarp[RS_WARPS + 1];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t n = load_count(n_dev, cap);
   const uint32_t tile0 = blockIdx.x * RS_TILE;
@@ -217,23 +222,54 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     __syncwarp();
   }
   __syncthreads();
-  {
-    uint32_t run = hist[(size_t)t * nb + blockIdx.x];
+  // thread t owns digit t: per-warp offsets inside the digit, the digit's tile total
+  uint32_t tot = 0;
 #pragma unroll
+  for (int w = 0; w < RS_WARPS; ++w) {
+    const uint32_t c = wcnt[w][t];
+    wcnt[w][t] = tot;
+    tot += c;
+  }
+  dglobal[t] = hist[(size_t)t * nb + blockIdx.x];
+  // exclusive scan of the digit totals over the 256 digits (warp scans + warp sums)
+  uint32_t inc = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) swarp[warp] = inc;
+  __syncthreads();
+  if (t == 0) {
+    uint32_t run = 0;
     for (int w = 0; w < RS_WARPS; ++w) {
-      const uint32_t c = wcnt[w][t];
-      wcnt[w][t] = run;
+      const uint32_t c = swarp[w];
+      swarp[w] = run;
       run += c;
     }
+    swarp[RS_WARPS] = run;
   }
   __syncthreads();
+  dlocal[t] = swarp[warp] + inc - tot;
+  __syncthreads();
+  // local stable placement in digit order
 #pragma unroll
   for (int r = 0; r < RS_ROUNDS_W; ++r) {
     if (rank[r] != 0xffffffffu) {
-      const uint32_t pos = wcnt[warp][(key[r] >> shift) & 0xffu] + rank[r];
-      kout[pos] = key[r];
-      vout[pos] = val[r];
+      const uint32_t d = (key[r] >> shift) & 0xffu;
+      const uint32_t lp = dlocal[d] + wcnt[warp][d] + rank[r];
+      skey[lp] = key[r];
+      sval[lp] = val[r];
     }
+  }
+  __syncthreads();
+  const uint32_t count = swarp[RS_WARPS];
+  for (uint32_t lp = t; lp < count; lp += RS_THREADS) {
+    const uint32_t k = skey[lp];
+    const uint32_t d = (k >> shift) & 0xffu;
+    const uint32_t pos = dglobal[d] + (lp - dlocal[d]);
+    kout[pos] = k;
+    vout[pos] = sval[lp];
   }
 }
 
