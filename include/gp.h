@@ -201,6 +201,53 @@ GP_API gp_status gp_count_evals(gp_ctx* ctx, const gp_set* set, const float* z, 
 GP_API gp_status gp_exp2_eval(gp_ctx* ctx, const float* x, float* y, int64_t n, int mode,
                        void* stream);
 
+/* ------------------------------------------------------------------ batching
+ * Many Gaussian sets of uneven sizes, each with its own slice stack, image size,
+ * sigma_z and axis, rendered and differentiated by ONE CUDA-graph launch (the
+ * paper renders one stack at a time).  The plan
+ * bins every item into one batch-wide key space and rasterises with
+ * persistent kernels that take (item, slice, tile) work from a global counter.
+ *
+ * Per item (all pointers DEVICE except z):
+ *   out     [S][H][W] forward image, or NULL;
+ *   target  [S][H][W] MSE target: the plan computes loss (if `loss` != NULL),
+ *           dL/dI = 2 (I - T) / (S H W) and, with d_mu != NULL, the backward;
+ *   dL_dI   [S][H][W] upstream gradient, used when target is NULL;
+ *   d_mu, d_scale, d_quat, d_alpha: gradient outputs (overwritten), or NULL.
+ * The plan keeps the pointers; every run reads the current parameter values
+ * and writes the outputs.  Pair buffers are sized at plan time with 25%
+ * headroom; if a later run needs more (parameters moved a lot), every kernel
+ * clamps to the capacity and gp_batch_wait returns GP_ERR_OVERFLOW: re-plan.
+ * A plan belongs to its context (same device, not thread-safe). */
+typedef struct {
+  gp_set set;
+  const float* z;   /* HOST [S] plane positions */
+  int S, H, W;
+  float sigma_z;
+  int axis;
+  float* out;
+  const float* target;
+  const float* dL_dI;
+  float *d_mu, *d_scale, *d_quat, *d_alpha;
+  float* loss;
+} gp_batch_item;
+
+typedef struct gp_plan gp_plan;
+
+#define GP_BATCH_AUTOTUNE 1  /* time tile side (8/16) and staging chunks on this workload */
+
+/* Builds the plan (allocates its buffers, counts pairs once, optionally
+ * autotunes, captures the graph).  Synchronous.  GP_ERR_ARG for invalid items. */
+GP_API gp_status gp_batch_plan(gp_ctx* ctx, const gp_batch_item* items, int n, int flags, gp_plan** out);
+/* Enqueues the captured graph on `stream` (asynchronous). */
+GP_API gp_status gp_batch_run(gp_plan* plan, void* stream);
+/* Synchronises `stream`; GP_ERR_OVERFLOW if the last run outgrew the plan. */
+GP_API gp_status gp_batch_wait(gp_plan* plan, void* stream);
+/* Chosen configuration and memory of a plan (any pointer may be NULL). */
+GP_API gp_status gp_batch_info(gp_plan* plan, int64_t* pair_capacity, int* tile, int* fwd_chunk,
+                               int* bwd_chunk, int64_t* device_bytes);
+GP_API gp_status gp_batch_destroy(gp_plan* plan);
+
 /* Phase timing.  When enabled, every call records a CUDA event pair on its
  * stream around each phase below; gp_timing_read synchronises those events,
  * returns the summed milliseconds and launch counts per phase since the last

@@ -33,7 +33,9 @@ EXPORTS = (
     "gp_render_slices", "gp_render_backward", "gp_mse_grad", "gp_voxelize", "gp_voxelize_backward",
     "gp_last_counts", "gp_count_evals", "gp_exp2_eval", "gp_timing_enable", "gp_timing_read",
     "gp_launch_count", "gp_fma_probe_threads", "gp_fma_probe", "gp_mse_grad_noalloc",
+    "gp_batch_plan", "gp_batch_run", "gp_batch_wait", "gp_batch_info", "gp_batch_destroy",
 )
+GP_BATCH_AUTOTUNE = 1
 GP_NUM_PHASES = 7
 PHASES = ("bin", "fwd", "bwd", "bwd_pre", "loss", "vox_fwd", "vox_bwd")
 
@@ -53,6 +55,14 @@ class gp_config(ctypes.Structure):
 class gp_set(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("quat", ctypes.c_void_p),
                 ("alpha", ctypes.c_void_p), ("n", ctypes.c_int64), ("scale_mod", ctypes.c_float)]
+
+
+class gp_batch_item(ctypes.Structure):
+    _fields_ = [("set", gp_set), ("z", ctypes.c_void_p), ("S", ctypes.c_int), ("H", ctypes.c_int),
+                ("W", ctypes.c_int), ("sigma_z", ctypes.c_float), ("axis", ctypes.c_int),
+                ("out", ctypes.c_void_p), ("target", ctypes.c_void_p), ("dL_dI", ctypes.c_void_p),
+                ("d_mu", ctypes.c_void_p), ("d_scale", ctypes.c_void_p), ("d_quat", ctypes.c_void_p),
+                ("d_alpha", ctypes.c_void_p), ("loss", ctypes.c_void_p)]
 
 
 def _load():
@@ -82,6 +92,12 @@ def _load():
         "gp_fma_probe_threads": [P],
         "gp_fma_probe": [P, I, P, P],
         "gp_mse_grad_noalloc": [P, P, P, I, I, I, P, P, P],
+        "gp_batch_plan": [P, ctypes.POINTER(gp_batch_item), I, I, ctypes.POINTER(P)],
+        "gp_batch_run": [P, P],
+        "gp_batch_wait": [P, P],
+        "gp_batch_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                          ctypes.POINTER(I64)],
+        "gp_batch_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -276,6 +292,69 @@ def gp_mse_grad_noalloc(I, T, t_index=None, dL_dI=None, loss=None, stream=None):
     if st != GP_OK:
         raise GPError(st, "gp_mse_grad_noalloc")
     return dL_dI, loss
+
+
+class BatchPlan:
+    """A captured batch of renders (gp_batch_plan); run() replays its graph.
+
+    items: dicts with keys gs (GaussianSet), z, H, W, sigma_z, axis and any of
+    out, target, dL_dI, grads (4-tuple of tensors), loss (1-element tensor)."""
+
+    def __init__(self, ctx, items, autotune=False):
+        self.ctx = ctx
+        self._keep = []
+        arr = (gp_batch_item * len(items))()
+        for k, it in enumerate(items):
+            gs = it["gs"]
+            z = _host_f32(it["z"])
+            self._keep.append(z)
+            S, H, W = z.shape[0], int(it["H"]), int(it["W"])
+            c = arr[k]
+            c.set = gs.c()
+            c.z = z.ctypes.data_as(ctypes.c_void_p).value
+            c.S, c.H, c.W = S, H, W
+            c.sigma_z = float(it["sigma_z"])
+            c.axis = int(it.get("axis", 2))
+            for key in ("out", "target", "dL_dI"):
+                t = it.get(key)
+                setattr(c, key, None if t is None else _dev(t, key, shape=(S, H, W)).value)
+            g = it.get("grads")
+            if g is not None:
+                c.d_mu, c.d_scale, c.d_quat, c.d_alpha = [_dev(t, "grad").value for t in g]
+            if it.get("loss") is not None:
+                c.loss = _dev(it["loss"], "loss", shape=(1,)).value
+            self._keep.append(it)
+        h = ctypes.c_void_p()
+        ctx.check(lib.gp_batch_plan(ctx.h, arr, len(items), GP_BATCH_AUTOTUNE if autotune else 0, ctypes.byref(h)),
+                  "gp_batch_plan")
+        self.h = h
+
+    def run(self, stream=None):
+        self.ctx.check(lib.gp_batch_run(self.h, _stream(stream)), "gp_batch_run")
+
+    def wait(self, stream=None):
+        st = lib.gp_batch_wait(self.h, _stream(stream))
+        if st != GP_OK:
+            raise GPError(st, "gp_batch_wait: " + lib.gp_last_error(self.ctx.h).decode(errors="replace"))
+
+    def info(self):
+        cap, b = ctypes.c_int64(), ctypes.c_int64()
+        t, f, bw = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.ctx.check(lib.gp_batch_info(self.h, ctypes.byref(cap), ctypes.byref(t), ctypes.byref(f),
+                                         ctypes.byref(bw), ctypes.byref(b)), "gp_batch_info")
+        return {"pair_capacity": cap.value, "tile": t.value, "fwd_chunk": f.value, "bwd_chunk": bw.value,
+                "device_bytes": b.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.gp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gp_voxelize(ctx, gs, X, Y, Z, vol=None, stream=None):

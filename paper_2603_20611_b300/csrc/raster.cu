@@ -1,8 +1,9 @@
 // raster.cu -- block-culled tile rasterisers of the slice renderer (the default
-// K-fwd and K-bwd for 16 x 16 tiles), sm_103a.
+// K-fwd and K-bwd), sm_103a; plain (one CTA per tile) and persistent (a work
+// queue over every tile of a batch of renders) launches share the tile bodies.
 //
-// A CTA owns one (slice, 16x16 tile) and its binned Gaussian list; its four
-// warps own the four 8x8 blocks of the tile.  Per round the CTA stages a chunk
+// A CTA owns one (slice, tile) and its binned Gaussian list; its warps own the
+// 8x8 blocks of the tile (four for 16x16 tiles, one for 8x8).  Per round the CTA stages a chunk
 // of Gaussians in shared memory (16-byte loads of the 64-byte records, mu_2d
 // and a~ of this slice computed once per Gaussian).  Each warp then tests 32
 // staged Gaussians at a time against its block -- lane l tests Gaussian l with
@@ -32,10 +33,6 @@
 
 namespace gp {
 
-constexpr int BT = 16;          // tile side
-constexpr int BNT = 128;        // threads per CTA: 4 warps, one 8x8 block each
-constexpr int FCH = 128;        // Gaussians staged per round, forward
-constexpr int BCH = 64;         // Gaussians staged per round, backward
 constexpr float kHalfBlock = 3.5f;  // pixel centres of an 8-wide block lie within +-3.5 of its centre
 
 // Staging of one Gaussian for one (slice, tile):
@@ -77,44 +74,49 @@ __device__ __forceinline__ int block_hits(const float4* __restrict__ s0, const f
   return __popc(m);
 }
 
-template <int EXPM>
-__global__ void __launch_bounds__(BNT) k_raster_fwd_blk(SliceArgs a, const SliceRec* __restrict__ rec,
-                                                        const uint32_t* __restrict__ vals,
-                                                        const uint32_t* __restrict__ emit_gid,
-                                                        const uint2* __restrict__ ranges, float* __restrict__ out) {
-  __shared__ float4 s0[FCH], s1[FCH];
-  __shared__ int hitlist[BNT / 32][32];
+// Shared memory of the forward body.
+template <int TILE, int CH>
+struct FwdSmem {
+  float4 s0[CH], s1[CH];
+  int hitlist[(TILE / 8) * (TILE / 8)][32];
+};
+
+// One (slice s, tile t) of item a: every pixel of the tile is written.
+template <int TILE, int CH, int EXPM>
+__device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, const SliceRec* __restrict__ rec,
+                                         const uint32_t* __restrict__ vals, const uint32_t* __restrict__ emit_gid,
+                                         const uint2* __restrict__ ranges, FwdSmem<TILE, CH>& sm) {
+  constexpr int NT = (TILE / 8) * (TILE / 8) * 32;
   const int T = a.TX * a.TY;
-  const int tile_id = blockIdx.x;
-  const int s = tile_id / T, t = tile_id - s * T;
+  const int s = local_key / T, t = local_key - s * T;
   const int ty = t / a.TX, tx = t - ty * a.TX;
-  const uint2 rg = ranges[tile_id];
+  const uint2 rg = ranges[a.key_base + (uint32_t)local_key];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane >> 3, row = lane & 7;
-  const float bx = (float)((warp & 1) * 8), by = (float)((warp >> 1) * 8);
+  const float bx = (float)((warp % (TILE / 8)) * 8), by = (float)((warp / (TILE / 8)) * 8);
   const float cx = bx + 4.0f, cy = by + 4.0f;
   const float pyr = by + (float)row + 0.5f;
-  const float x0 = (float)(tx * BT), y0 = (float)(ty * BT);
+  const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
   const float zsv = a.zorig[s];
   const float sqrt_k2 = sqrtf(a.k2);
-  int* list = hitlist[warp];
+  int* list = sm.hitlist[warp];
   float acc[8];
 #pragma unroll
   for (int p = 0; p < 8; ++p) acc[p] = 0.0f;
-  for (uint32_t base = rg.x; base < rg.y; base += FCH) {
-    const int cnt = (int)min((uint32_t)FCH, rg.y - base);
-    for (int j = threadIdx.x; j < cnt; j += BNT) {
+  for (uint32_t base = rg.x; base < rg.y; base += CH) {
+    const int cnt = (int)min((uint32_t)CH, rg.y - base);
+    for (int j = threadIdx.x; j < cnt; j += NT) {
       float4 a0, a1, a2;
       stage_blk<EXPM>(rec, emit_gid[vals[base + j]], zsv, x0, y0, sqrt_k2, a0, a1, a2);
-      s0[j] = a0;
-      s1[j] = a1;
+      sm.s0[j] = a0;
+      sm.s1[j] = a1;
     }
     __syncthreads();
     for (int jb = 0; jb < cnt; jb += 32) {
-      const int nh = block_hits(s0, s1, jb, cnt, cx, cy, lane, list);
+      const int nh = block_hits(sm.s0, sm.s1, jb, cnt, cx, cy, lane, list);
       for (int h = grp; h < nh; h += 4) {
         const int jj = list[h];
-        const float4 g0 = s0[jj], g1 = s1[jj];
+        const float4 g0 = sm.s0[jj], g1 = sm.s1[jj];
         const float dy = pyr - g0.y;
         const float u = g1.y * dy;
         const float wy = g1.z * dy * dy;
@@ -137,10 +139,10 @@ __global__ void __launch_bounds__(BNT) k_raster_fwd_blk(SliceArgs a, const Slice
     acc[p] += __shfl_xor_sync(0xffffffffu, acc[p], 16);
   }
   if (grp == 0) {
-    const int py = ty * BT + (int)by + row;
-    const int px0 = tx * BT + (int)bx;
+    const int py = ty * TILE + (int)by + row;
+    const int px0 = tx * TILE + (int)bx;
     if (py < a.H) {
-      float* o = out + ((int64_t)s * a.H + py) * a.W + px0;
+      float* o = a.out + ((int64_t)s * a.H + py) * a.W + px0;
       if (px0 + 8 <= a.W && ((((uintptr_t)o) & 15u) == 0)) {
         reinterpret_cast<float4*>(o)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
         reinterpret_cast<float4*>(o)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
@@ -155,60 +157,63 @@ __global__ void __launch_bounds__(BNT) k_raster_fwd_blk(SliceArgs a, const Slice
 
 constexpr int ACC10 = 10;
 
-template <int EXPM, bool DET>
-__global__ void __launch_bounds__(BNT) k_raster_bwd_blk(SliceArgs a, const SliceRec* __restrict__ rec,
-                                                        const uint32_t* __restrict__ vals,
-                                                        const uint32_t* __restrict__ emit_gid,
-                                                        const uint2* __restrict__ ranges,
-                                                        const float* __restrict__ dL_dI, float* __restrict__ accum,
-                                                        float4* __restrict__ partial) {
-  constexpr int NW = BNT / 32;
-  __shared__ float4 s0[BCH], s1[BCH], s2[BCH];
-  __shared__ uint32_t sg[BCH];
-  __shared__ float sp[NW][6][BCH];
-  __shared__ int hitlist[NW][32];
+template <int TILE, int CH>
+struct BwdSmem {
+  static constexpr int NW = (TILE / 8) * (TILE / 8);
+  float4 s0[CH], s1[CH], s2[CH];
+  uint32_t sg[CH];
+  float sp[NW][6][CH];
+  int hitlist[NW][32];
+};
+
+template <int TILE, int CH, int EXPM, bool DET>
+__device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, const SliceRec* __restrict__ rec,
+                                         const uint32_t* __restrict__ vals, const uint32_t* __restrict__ emit_gid,
+                                         const uint2* __restrict__ ranges, float* __restrict__ accum,
+                                         float4* __restrict__ partial, BwdSmem<TILE, CH>& sm) {
+  constexpr int NW = BwdSmem<TILE, CH>::NW;
+  constexpr int NT = NW * 32;
+  const uint2 rg = ranges[a.key_base + (uint32_t)local_key];
+  if (rg.y <= rg.x) return;  // uniform over the CTA
   const int T = a.TX * a.TY;
-  const int tile_id = blockIdx.x;
-  const uint2 rg = ranges[tile_id];
-  if (rg.y <= rg.x) return;
-  const int s = tile_id / T, t = tile_id - s * T;
+  const int s = local_key / T, t = local_key - s * T;
   const int ty = t / a.TX, tx = t - ty * a.TX;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane >> 3, row = lane & 7;
   const unsigned gmask = 0xffu << (grp * 8);
-  const float bx = (float)((warp & 1) * 8), by = (float)((warp >> 1) * 8);
+  const float bx = (float)((warp % (TILE / 8)) * 8), by = (float)((warp / (TILE / 8)) * 8);
   const float cx = bx + 4.0f, cy = by + 4.0f;
   const float pyr = by + (float)row + 0.5f;
-  const float x0 = (float)(tx * BT), y0 = (float)(ty * BT);
+  const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
   const float zsv = a.zorig[s];
   const float sqrt_k2 = sqrtf(a.k2);
-  int* list = hitlist[warp];
+  int* list = sm.hitlist[warp];
   float G[8];
   {
-    const int py = ty * BT + (int)by + row;
-    const int px0 = tx * BT + (int)bx;
+    const int py = ty * TILE + (int)by + row;
+    const int px0 = tx * TILE + (int)bx;
 #pragma unroll
     for (int p = 0; p < 8; ++p)
-      G[p] = (py < a.H && px0 + p < a.W) ? dL_dI[((int64_t)s * a.H + py) * a.W + px0 + p] : 0.0f;
+      G[p] = (py < a.H && px0 + p < a.W) ? a.dL_dI[((int64_t)s * a.H + py) * a.W + px0 + p] : 0.0f;
   }
-  for (uint32_t base = rg.x; base < rg.y; base += BCH) {
-    const int cnt = (int)min((uint32_t)BCH, rg.y - base);
-    for (int j = threadIdx.x; j < cnt; j += BNT) {
+  for (uint32_t base = rg.x; base < rg.y; base += CH) {
+    const int cnt = (int)min((uint32_t)CH, rg.y - base);
+    for (int j = threadIdx.x; j < cnt; j += NT) {
       const uint32_t g = emit_gid[vals[base + j]];
       float4 a0, a1, a2;
       stage_blk<EXPM>(rec, g, zsv, x0, y0, sqrt_k2, a0, a1, a2);
-      s0[j] = a0;
-      s1[j] = a1;
-      s2[j] = a2;
-      sg[j] = g;
+      sm.s0[j] = a0;
+      sm.s1[j] = a1;
+      sm.s2[j] = a2;
+      sm.sg[j] = g;
     }
-    for (int i = threadIdx.x; i < NW * 6 * BCH; i += BNT) (&sp[0][0][0])[i] = 0.0f;
+    for (int i = threadIdx.x; i < NW * 6 * CH; i += NT) (&sm.sp[0][0][0])[i] = 0.0f;
     __syncthreads();
     for (int jb = 0; jb < cnt; jb += 32) {
-      const int nh = block_hits(s0, s1, jb, cnt, cx, cy, lane, list);
+      const int nh = block_hits(sm.s0, sm.s1, jb, cnt, cx, cy, lane, list);
       for (int h = grp; h < nh; h += 4) {
         const int jj = list[h];
-        const float4 g0 = s0[jj], g1 = s1[jj];
+        const float4 g0 = sm.s0[jj], g1 = sm.s1[jj];
         const float dy = pyr - g0.y;
         const float u = g1.y * dy;
         const float wy = g1.z * dy * dy;
@@ -233,22 +238,22 @@ __global__ void __launch_bounds__(BNT) k_raster_bwd_blk(SliceArgs a, const Slice
         }
         if (row == 0) {
 #pragma unroll
-          for (int k = 0; k < 6; ++k) sp[warp][k][jj] = v[k];
+          for (int k = 0; k < 6; ++k) sm.sp[warp][k][jj] = v[k];
         }
       }
       __syncwarp();
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < cnt; j += BNT) {
+    for (int j = threadIdx.x; j < cnt; j += NT) {
       float m[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
         float acc = 0.f;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) acc += sp[w][k][j];
+        for (int w = 0; w < NW; ++w) acc += sm.sp[w][k][j];
         m[k] = acc;
       }
-      const float4 g0 = s0[j], g1 = s1[j], g2 = s2[j];
+      const float4 g0 = sm.s0[j], g1 = sm.s1[j], g2 = sm.s2[j];
       const float at = g0.z;
       const float C00 = g1.w, C01 = g2.z, C11 = g2.w;
       // dE/dmu_2d = E C d; dE/dC00 = -E dx^2/2, dE/dC01 = -E dx dy, dE/dC11 = -E dy^2/2
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(BNT) k_raster_bwd_blk(SliceArgs a, const Slice
         partial[2 * (size_t)e] = make_float4(g_at, gmx, gmy, gc00);
         partial[2 * (size_t)e + 1] = make_float4(gc01, gc11, d, w);
       } else {
-        float* A = accum + (size_t)sg[j] * ACC10;
+        float* A = accum + (size_t)sm.sg[j] * ACC10;
         const float gw = g_at * w;
         atomicAdd(A + 0, gmx);
         atomicAdd(A + 1, gmy);
@@ -282,15 +287,123 @@ __global__ void __launch_bounds__(BNT) k_raster_bwd_blk(SliceArgs a, const Slice
   }
 }
 
+// ------------------------------------------------------------ plain kernels
+template <int TILE, int CH, int EXPM>
+__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32) k_raster_fwd_blk(
+    SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges) {
+  __shared__ FwdSmem<TILE, CH> sm;
+  fwd_tile<TILE, CH, EXPM>(a, blockIdx.x, rec, vals, emit_gid, ranges, sm);
+}
+
+template <int TILE, int CH, int EXPM, bool DET>
+__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32) k_raster_bwd_blk(
+    SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, float* __restrict__ accum,
+    float4* __restrict__ partial) {
+  __shared__ BwdSmem<TILE, CH> sm;
+  bwd_tile<TILE, CH, EXPM, DET>(a, blockIdx.x, rec, vals, emit_gid, ranges, accum, partial, sm);
+}
+
+// ------------------------------------------------------- persistent kernels
+// Every CTA takes chunks of KEY_CHUNK consecutive keys from the work counter and
+// renders each (item, slice, tile) key of the chunk; the item of a key is found
+// by binary search over the items' key starts.
+constexpr int KEY_CHUNK = 8;
+
+template <typename T>
+__device__ __forceinline__ int find_item_k(const T* __restrict__ t, int n, T x) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int m = (lo + hi) >> 1;
+    if (t[m] <= x) lo = m; else hi = m;
+  }
+  return lo;
+}
+
+template <int TILE, int CH, int EXPM>
+__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32) k_raster_fwd_persist(
+    BatchItems b, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, unsigned* __restrict__ work) {
+  __shared__ FwdSmem<TILE, CH> sm;
+  __shared__ uint32_t next;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(work, (unsigned)KEY_CHUNK);
+    __syncthreads();
+    const uint32_t k0 = next;
+    __syncthreads();
+    if (k0 >= b.n_keys) break;
+    const uint32_t k1 = min(k0 + (uint32_t)KEY_CHUNK, b.n_keys);
+    for (uint32_t key = k0; key < k1; ++key) {
+      const int it = find_item_k(b.kstart, b.n_items, key);
+      const SliceArgs a = b.args[it];
+      if (a.out) fwd_tile<TILE, CH, EXPM>(a, (int)(key - b.kstart[it]), rec, vals, emit_gid, ranges, sm);
+      __syncthreads();
+    }
+  }
+}
+
+template <int TILE, int CH, int EXPM, bool DET>
+__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32) k_raster_bwd_persist(
+    BatchItems b, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, float* __restrict__ accum,
+    float4* __restrict__ partial, unsigned* __restrict__ work) {
+  __shared__ BwdSmem<TILE, CH> sm;
+  __shared__ uint32_t next;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(work, (unsigned)KEY_CHUNK);
+    __syncthreads();
+    const uint32_t k0 = next;
+    __syncthreads();
+    if (k0 >= b.n_keys) break;
+    const uint32_t k1 = min(k0 + (uint32_t)KEY_CHUNK, b.n_keys);
+    for (uint32_t key = k0; key < k1; ++key) {
+      const int it = find_item_k(b.kstart, b.n_items, key);
+      const SliceArgs a = b.args[it];
+      if (a.dL_dI) bwd_tile<TILE, CH, EXPM, DET>(a, (int)(key - b.kstart[it]), rec, vals, emit_gid, ranges, accum,
+                                                 partial, sm);
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------ launchers
+template <int TILE, int CH>
+static cudaError_t fwd_blk(const SliceArgs& a, int exp_mode, const SliceRec* rec, const uint32_t* vals,
+                           const uint32_t* emit_gid, const uint2* ranges, cudaStream_t st) {
+  const int64_t tiles = (int64_t)a.S * a.TX * a.TY;
+  constexpr int NT = (TILE / 8) * (TILE / 8) * 32;
+  if (exp_mode == GP_EXP_HW)
+    k_raster_fwd_blk<TILE, CH, GP_EXP_HW><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges);
+  else
+    k_raster_fwd_blk<TILE, CH, GP_EXP_POLY><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_raster_fwd_blocked(const SliceArgs& a, int exp_mode, const SliceRec* rec, const uint32_t* vals,
                                       const uint32_t* emit_gid, const uint2* ranges, float* out, cudaStream_t st) {
-  const int64_t tiles = (int64_t)a.S * a.TX * a.TY;
-  if (tiles == 0) return cudaSuccess;
-  if (a.tile != BT) return cudaErrorInvalidValue;
-  if (exp_mode == GP_EXP_HW)
-    k_raster_fwd_blk<GP_EXP_HW><<<(unsigned)tiles, BNT, 0, st>>>(a, rec, vals, emit_gid, ranges, out);
-  else
-    k_raster_fwd_blk<GP_EXP_POLY><<<(unsigned)tiles, BNT, 0, st>>>(a, rec, vals, emit_gid, ranges, out);
+  if ((int64_t)a.S * a.TX * a.TY == 0) return cudaSuccess;
+  SliceArgs b = a;
+  b.out = out;
+  if (a.tile == 16) return fwd_blk<16, 128>(b, exp_mode, rec, vals, emit_gid, ranges, st);
+  if (a.tile == 8) return fwd_blk<8, 64>(b, exp_mode, rec, vals, emit_gid, ranges, st);
+  return cudaErrorInvalidValue;
+}
+
+template <int TILE, int CH>
+static cudaError_t bwd_blk(const SliceArgs& a, int exp_mode, bool det, const SliceRec* rec, const uint32_t* vals,
+                           const uint32_t* emit_gid, const uint2* ranges, float* accum, float4* partial,
+                           cudaStream_t st) {
+  const unsigned g = (unsigned)((int64_t)a.S * a.TX * a.TY);
+  constexpr int NT = (TILE / 8) * (TILE / 8) * 32;
+  if (exp_mode == GP_EXP_HW) {
+    if (det) k_raster_bwd_blk<TILE, CH, GP_EXP_HW, true><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+    else k_raster_bwd_blk<TILE, CH, GP_EXP_HW, false><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+  } else {
+    if (det) k_raster_bwd_blk<TILE, CH, GP_EXP_POLY, true><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+    else k_raster_bwd_blk<TILE, CH, GP_EXP_POLY, false><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -298,19 +411,88 @@ cudaError_t launch_raster_fwd_blocked(const SliceArgs& a, int exp_mode, const Sl
 cudaError_t launch_raster_bwd_blocked(const SliceArgs& a, int exp_mode, bool det, const SliceRec* rec,
                                       const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
                                       const float* dL_dI, float* accum, float4* partial, cudaStream_t st) {
-  const int64_t tiles = (int64_t)a.S * a.TX * a.TY;
-  if (tiles == 0) return cudaSuccess;
-  if (a.tile != BT) return cudaErrorInvalidValue;
-  const unsigned g = (unsigned)tiles;
+  if ((int64_t)a.S * a.TX * a.TY == 0) return cudaSuccess;
+  SliceArgs b = a;
+  b.dL_dI = dL_dI;
+  if (a.tile == 16) return bwd_blk<16, 64>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
+  if (a.tile == 8) return bwd_blk<8, 64>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
+  return cudaErrorInvalidValue;
+}
+
+// Persistent launchers: chunk in {64, 128, 256} Gaussians per staging round.
+template <int TILE, int CH>
+static cudaError_t fwd_persist(const BatchItems& b, int ctas, int exp_mode, const SliceRec* rec, const uint32_t* vals,
+                               const uint32_t* emit_gid, const uint2* ranges, unsigned* work, cudaStream_t st) {
+  constexpr int NT = (TILE / 8) * (TILE / 8) * 32;
+  if (exp_mode == GP_EXP_HW)
+    k_raster_fwd_persist<TILE, CH, GP_EXP_HW><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, work);
+  else
+    k_raster_fwd_persist<TILE, CH, GP_EXP_POLY><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, work);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int TILE, int CH>
+static cudaError_t bwd_persist(const BatchItems& b, int ctas, int exp_mode, bool det, const SliceRec* rec,
+                               const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges, float* accum,
+                               float4* partial, unsigned* work, cudaStream_t st) {
+  constexpr int NT = (TILE / 8) * (TILE / 8) * 32;
   if (exp_mode == GP_EXP_HW) {
-    if (det) k_raster_bwd_blk<GP_EXP_HW, true><<<g, BNT, 0, st>>>(a, rec, vals, emit_gid, ranges, dL_dI, accum, partial);
-    else k_raster_bwd_blk<GP_EXP_HW, false><<<g, BNT, 0, st>>>(a, rec, vals, emit_gid, ranges, dL_dI, accum, partial);
+    if (det) k_raster_bwd_persist<TILE, CH, GP_EXP_HW, true><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work);
+    else k_raster_bwd_persist<TILE, CH, GP_EXP_HW, false><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work);
   } else {
-    if (det) k_raster_bwd_blk<GP_EXP_POLY, true><<<g, BNT, 0, st>>>(a, rec, vals, emit_gid, ranges, dL_dI, accum, partial);
-    else k_raster_bwd_blk<GP_EXP_POLY, false><<<g, BNT, 0, st>>>(a, rec, vals, emit_gid, ranges, dL_dI, accum, partial);
+    if (det) k_raster_bwd_persist<TILE, CH, GP_EXP_POLY, true><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work);
+    else k_raster_bwd_persist<TILE, CH, GP_EXP_POLY, false><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work);
   }
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_raster_fwd_batch(const BatchItems& b, int tile, int chunk, int ctas, int exp_mode,
+                                    const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
+                                    const uint2* ranges, unsigned* work, cudaStream_t st) {
+  if (b.n_keys == 0) return cudaSuccess;
+#define GP_FWD_P(T, C) \
+  if (tile == T && chunk == C) return fwd_persist<T, C>(b, ctas, exp_mode, rec, vals, emit_gid, ranges, work, st);
+  GP_FWD_P(16, 64) GP_FWD_P(16, 128) GP_FWD_P(16, 256) GP_FWD_P(8, 64) GP_FWD_P(8, 128) GP_FWD_P(8, 256)
+#undef GP_FWD_P
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_raster_bwd_batch(const BatchItems& b, int tile, int chunk, int ctas, int exp_mode, bool det,
+                                    const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
+                                    const uint2* ranges, float* accum, float4* partial, unsigned* work,
+                                    cudaStream_t st) {
+  if (b.n_keys == 0) return cudaSuccess;
+#define GP_BWD_P(T, C)                                                                                       \
+  if (tile == T && chunk == C)                                                                               \
+    return bwd_persist<T, C>(b, ctas, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, work, st);
+  GP_BWD_P(16, 32) GP_BWD_P(16, 64) GP_BWD_P(16, 128) GP_BWD_P(8, 32) GP_BWD_P(8, 64) GP_BWD_P(8, 128)
+#undef GP_BWD_P
+  return cudaErrorInvalidValue;
+}
+
+// Resident CTAs per SM of a persistent kernel (occupancy calculator).
+int raster_batch_ctas_per_sm(int tile, int chunk, bool backward) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define GP_OCC_F(T, C)                                                                                       \
+  if (!backward && tile == T && chunk == C)                                                                  \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd_persist<T, C, GP_EXP_POLY>,          \
+                                                      (T / 8) * (T / 8) * 32, 0);
+#define GP_OCC_B(T, C)                                                                                       \
+  if (backward && tile == T && chunk == C)                                                                   \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_bwd_persist<T, C, GP_EXP_POLY, false>,   \
+                                                      (T / 8) * (T / 8) * 32, 0);
+  GP_OCC_F(16, 64) GP_OCC_F(16, 128) GP_OCC_F(16, 256) GP_OCC_F(8, 64) GP_OCC_F(8, 128) GP_OCC_F(8, 256)
+  GP_OCC_B(16, 32) GP_OCC_B(16, 64) GP_OCC_B(16, 128) GP_OCC_B(8, 32) GP_OCC_B(8, 64) GP_OCC_B(8, 128)
+#undef GP_OCC_F
+#undef GP_OCC_B
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 }  // namespace gp

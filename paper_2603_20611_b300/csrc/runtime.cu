@@ -215,6 +215,7 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
     GP_CUDA(c, cudaMemcpyAsync(b.zorig.ptr, z, S * 4, cudaMemcpyHostToDevice, st), "upload z");
   }
   SliceArgs& A = *a;
+  A = SliceArgs{};
   A.mu = set->mu; A.scale = set->scale; A.quat = set->quat; A.alpha = set->alpha;
   A.n = n; A.mod = set->scale_mod; A.axis = axis; A.sigma2 = sigma_z * sigma_z;
   A.k2 = 2.0f * logf(1.0f / c->cfg.eps);

@@ -164,10 +164,9 @@ __device__ __forceinline__ unsigned long long count_pairs(const SliceArgs& a, co
   return c;
 }
 
-__global__ void __launch_bounds__(PRE_THREADS) k_slice_pre(SliceArgs a, SliceRec* __restrict__ rec,
-                                                           unsigned long long* __restrict__ counts) {
-  int i = blockIdx.x * PRE_THREADS + threadIdx.x;
-  if (i >= a.n) return;
+// Record and pair count of Gaussian i of item a, stored at batch-wide index ig.
+__device__ __forceinline__ void slice_pre_one(const SliceArgs& a, int i, int ig, SliceRec* __restrict__ rec,
+                                              unsigned long long* __restrict__ counts) {
   float4 q = reinterpret_cast<const float4*>(a.quat)[i];
   float R[3][3], qn[4], qnorm;
   quat_rot(q, R, qn, qnorm);
@@ -192,8 +191,40 @@ __global__ void __launch_bounds__(PRE_THREADS) k_slice_pre(SliceArgs a, SliceRec
   r.r1 = make_float4(ax, ay, a.alpha[i] / sqrtf(det), sqrtf(a.k2 * v));
   r.r2 = make_float4(syy * idet, -sxy * idet, sxx * idet, sqrtf(a.k2 * sxx));
   r.r3 = make_float4(sqrtf(a.k2 * syy), valid ? 1.0f : 0.0f, det / syy, det / sxx);
-  rec[i] = r;
-  counts[i] = count_pairs(a, r);
+  rec[ig] = r;
+  counts[ig] = count_pairs(a, r);
+}
+
+__global__ void __launch_bounds__(PRE_THREADS) k_slice_pre(SliceArgs a, SliceRec* __restrict__ rec,
+                                                           unsigned long long* __restrict__ counts) {
+  const int i = blockIdx.x * PRE_THREADS + threadIdx.x;
+  if (i < a.n) slice_pre_one(a, i, i, rec, counts);
+}
+
+// Item owning batch-wide index x of a prefix table t[0..n] (t[0] = 0).
+template <typename T>
+__device__ __forceinline__ int find_item(const T* __restrict__ t, int n, T x) {
+  int lo = 0, hi = n;  // invariant: t[lo] <= x < t[hi]
+  while (hi - lo > 1) {
+    const int m = (lo + hi) >> 1;
+    if (t[m] <= x) lo = m; else hi = m;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(PRE_THREADS) k_slice_pre_batch(BatchItems b, SliceRec* __restrict__ rec,
+                                                                 unsigned long long* __restrict__ counts) {
+  const int ig = blockIdx.x * PRE_THREADS + threadIdx.x;
+  if (ig >= b.n_gauss) return;
+  const int k = find_item(b.gstart, b.n_items, ig);
+  const SliceArgs a = b.args[k];
+  slice_pre_one(a, ig - b.gstart[k], ig, rec, counts);
+}
+
+void launch_slice_pre_batch(const BatchItems& b, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
+  if (b.n_gauss <= 0) return;
+  k_slice_pre_batch<<<ceil_div(b.n_gauss, PRE_THREADS), PRE_THREADS, 0, st>>>(b, rec, counts);
+  note_launch();
 }
 
 void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
@@ -210,25 +241,31 @@ void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* cou
 constexpr int EMIT_THREADS = 128;
 constexpr int EMIT_WIN = 1024;  // pairs per warp window
 
-__global__ void __launch_bounds__(EMIT_THREADS) k_slice_emit(SliceArgs a, const SliceRec* __restrict__ rec,
+template <bool BATCH>
+__global__ void __launch_bounds__(EMIT_THREADS) k_slice_emit(SliceArgs a1, BatchItems b, int n,
+                                                             const SliceRec* __restrict__ rec,
                                                              const unsigned long long* __restrict__ offsets,
                                                              const unsigned long long* __restrict__ counts,
-                                                             uint32_t* __restrict__ keys,
+                                                             unsigned long long cap, uint32_t* __restrict__ keys,
                                                              uint32_t* __restrict__ emit_gid) {
   __shared__ uint32_t wkey[EMIT_THREADS / 32][EMIT_WIN];
   __shared__ uint32_t wgid[EMIT_THREADS / 32][EMIT_WIN];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i = blockIdx.x * EMIT_THREADS + threadIdx.x;
   const int i0 = i - lane;
-  if (i0 >= a.n) return;  // whole warp past the end
-  const int ilast = min(i0 + 31, a.n - 1);
+  if (i0 >= n) return;  // whole warp past the end
+  const int ilast = min(i0 + 31, n - 1);
   const unsigned long long wstart = offsets[i0];
-  const unsigned long long wend = offsets[ilast] + counts[ilast];
-  const bool mine = i < a.n;
+  const unsigned long long wend = min(offsets[ilast] + counts[ilast], cap);
+  const bool mine = i < n;
   const unsigned long long my0 = mine ? offsets[i] : 0ull;
   const unsigned long long my1 = mine ? my0 + counts[i] : 0ull;
   SliceRec r;
-  if (mine) r = rec[i];
+  SliceArgs a = a1;
+  if (mine) {
+    r = rec[i];
+    if (BATCH) a = b.args[find_item(b.gstart, b.n_items, i)];
+  }
   const uint32_t T = (uint32_t)(a.TX * a.TY);
   for (unsigned long long wb = wstart; wb < wend; wb += EMIT_WIN) {
     const unsigned long long we = wb + EMIT_WIN;
@@ -236,7 +273,7 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_slice_emit(SliceArgs a, const 
       unsigned long long e = my0;
       for_each_pair(a, r, [&](int j, int tile) {
         if (e >= wb && e < we && e < my1) {
-          wkey[warp][e - wb] = (uint32_t)a.zorder[j] * T + (uint32_t)tile;
+          wkey[warp][e - wb] = a.key_base + (uint32_t)a.zorder[j] * T + (uint32_t)tile;
           wgid[warp][e - wb] = (uint32_t)i;
         }
         ++e;
@@ -257,7 +294,19 @@ void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned l
                        cudaStream_t st) {
   (void)vals;  // the sort generates the identity values itself
   if (a.n <= 0) return;
-  k_slice_emit<<<ceil_div(a.n, EMIT_THREADS), EMIT_THREADS, 0, st>>>(a, rec, offsets, counts, keys, emit_gid);
+  BatchItems none{};
+  k_slice_emit<false><<<ceil_div(a.n, EMIT_THREADS), EMIT_THREADS, 0, st>>>(a, none, a.n, rec, offsets, counts,
+                                                                            ~0ull, keys, emit_gid);
+  note_launch();
+}
+
+void launch_slice_emit_batch(const BatchItems& b, const SliceRec* rec, const unsigned long long* offsets,
+                             const unsigned long long* counts, uint32_t cap, uint32_t* keys, uint32_t* emit_gid,
+                             cudaStream_t st) {
+  if (b.n_gauss <= 0) return;
+  SliceArgs none{};
+  k_slice_emit<true><<<ceil_div(b.n_gauss, EMIT_THREADS), EMIT_THREADS, 0, st>>>(none, b, b.n_gauss, rec, offsets,
+                                                                                 counts, cap, keys, emit_gid);
   note_launch();
 }
 
@@ -384,10 +433,7 @@ bool fwd_px_supported(int tile, int px) {
 cudaError_t launch_raster_fwd(const SliceArgs& a, int px, int exp_mode, const SliceRec* rec,
                               const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
                               float* out, cudaStream_t st) {
-  if (px == 0) {
-    if (a.tile == 16) return launch_raster_fwd_blocked(a, exp_mode, rec, vals, emit_gid, ranges, out, st);
-    px = 1;
-  }
+  if (px == 0) return launch_raster_fwd_blocked(a, exp_mode, rec, vals, emit_gid, ranges, out, st);
   if (a.tile == 16) {
     switch (px) {
       case 1: return fwd_dispatch<16, 1>(a, exp_mode, rec, vals, emit_gid, ranges, out, st);
@@ -566,11 +612,8 @@ bool bwd_px_supported(int tile, int px) {
 cudaError_t launch_raster_bwd(const SliceArgs& a, int px, int exp_mode, bool det, const SliceRec* rec,
                               const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
                               const float* dL_dI, float* accum, float4* partial, cudaStream_t st) {
-  if (px == 0) {
-    if (a.tile == 16)
-      return launch_raster_bwd_blocked(a, exp_mode, det, rec, vals, emit_gid, ranges, dL_dI, accum, partial, st);
-    px = 2;
-  }
+  if (px == 0)
+    return launch_raster_bwd_blocked(a, exp_mode, det, rec, vals, emit_gid, ranges, dL_dI, accum, partial, st);
   if (a.tile == 16) {
     switch (px) {
       case 2: return bwd_dispatch<16, 2>(a, exp_mode, det, rec, vals, emit_gid, ranges, dL_dI, accum, partial, st);
@@ -590,13 +633,14 @@ cudaError_t launch_raster_bwd(const SliceArgs& a, int px, int exp_mode, bool det
 // ------------------------------------------------------------ K-det
 __global__ void k_det_reduce(int n, const unsigned long long* __restrict__ offsets,
                              const unsigned long long* __restrict__ counts,
-                             const float4* __restrict__ partial, float* __restrict__ accum) {
+                             const float4* __restrict__ partial, float* __restrict__ accum,
+                             unsigned long long cap) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float A[ACC];
 #pragma unroll
   for (int k = 0; k < ACC; ++k) A[k] = 0.f;
-  unsigned long long e0 = offsets[i], e1 = e0 + counts[i];
+  unsigned long long e0 = offsets[i], e1 = min(e0 + counts[i], cap);
   for (unsigned long long e = e0; e < e1; ++e) {
     float4 p0 = partial[2 * e], p1 = partial[2 * e + 1];
     const float g_at = p0.x, gmx = p0.y, gmy = p0.z, gc00 = p0.w, gc01 = p1.x, gc11 = p1.y;
@@ -609,10 +653,17 @@ __global__ void k_det_reduce(int n, const unsigned long long* __restrict__ offse
   for (int k = 0; k < ACC; ++k) accum[(size_t)i * ACC + k] = A[k];
 }
 
+void launch_det_reduce_n(int n, const unsigned long long* offsets, const unsigned long long* counts,
+                         const float4* partial, float* accum, unsigned long long cap, cudaStream_t st) {
+  if (n <= 0) return;
+  k_det_reduce<<<ceil_div(n, 256), 256, 0, st>>>(n, offsets, counts, partial, accum, cap);
+  note_launch();
+}
+
 void launch_det_reduce(int n, const unsigned long long* offsets, const unsigned long long* counts,
                        const float4* partial, float* accum, cudaStream_t st) {
   if (n <= 0) return;
-  k_det_reduce<<<ceil_div(n, 256), 256, 0, st>>>(n, offsets, counts, partial, accum);
+  k_det_reduce<<<ceil_div(n, 256), 256, 0, st>>>(n, offsets, counts, partial, accum, ~0ull);
   note_launch();
 }
 
@@ -624,16 +675,13 @@ void launch_det_reduce(int n, const unsigned long long* offsets, const unsigned 
 //   dL/dSigma_2d = -C Gc C + dL/ddet det C   (Gc = symmetric dL/dC),
 //   Sigma_2d = Sigma_pp - b b^T / v, a = b / v, v = Sigma_cc + sigma_z^2, b = Sigma_pc,
 //   Sigma = M M^T, M = R diag(mod s), R = R(q/|q|).
-__global__ void __launch_bounds__(PRE_THREADS) k_slice_bwd_pre(SliceArgs a, const float* __restrict__ accum,
-                                                               float* __restrict__ d_mu,
-                                                               float* __restrict__ d_scale,
-                                                               float* __restrict__ d_quat,
-                                                               float* __restrict__ d_alpha) {
-  int i = blockIdx.x * PRE_THREADS + threadIdx.x;
-  if (i >= a.n) return;
+// Gradients of Gaussian i of item a from the accumulators at batch-wide index ig.
+__device__ __forceinline__ void slice_bwd_pre_one(const SliceArgs& a, int i, int ig, const float* __restrict__ accum,
+                                                  float* __restrict__ d_mu, float* __restrict__ d_scale,
+                                                  float* __restrict__ d_quat, float* __restrict__ d_alpha) {
   float acc[ACC];
 #pragma unroll
-  for (int k = 0; k < ACC; ++k) acc[k] = accum[(size_t)i * ACC + k];
+  for (int k = 0; k < ACC; ++k) acc[k] = accum[(size_t)ig * ACC + k];
   float4 q = reinterpret_cast<const float4*>(a.quat)[i];
   float R[3][3], qn[4], qnorm;
   quat_rot(q, R, qn, qnorm);
@@ -687,6 +735,30 @@ __global__ void __launch_bounds__(PRE_THREADS) k_slice_bwd_pre(SliceArgs a, cons
   }
   reinterpret_cast<float4*>(d_quat)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
   d_alpha[i] = galpha;
+}
+
+__global__ void __launch_bounds__(PRE_THREADS) k_slice_bwd_pre(SliceArgs a, const float* __restrict__ accum,
+                                                               float* __restrict__ d_mu,
+                                                               float* __restrict__ d_scale,
+                                                               float* __restrict__ d_quat,
+                                                               float* __restrict__ d_alpha) {
+  const int i = blockIdx.x * PRE_THREADS + threadIdx.x;
+  if (i < a.n) slice_bwd_pre_one(a, i, i, accum, d_mu, d_scale, d_quat, d_alpha);
+}
+
+__global__ void __launch_bounds__(PRE_THREADS) k_slice_bwd_pre_batch(BatchItems b, const float* __restrict__ accum) {
+  const int ig = blockIdx.x * PRE_THREADS + threadIdx.x;
+  if (ig >= b.n_gauss) return;
+  const int k = find_item(b.gstart, b.n_items, ig);
+  const SliceArgs a = b.args[k];
+  if (!a.d_mu) return;  // item without gradient outputs
+  slice_bwd_pre_one(a, ig - b.gstart[k], ig, accum, a.d_mu, a.d_scale, a.d_quat, a.d_alpha);
+}
+
+void launch_slice_bwd_pre_batch(const BatchItems& b, const float* accum, cudaStream_t st) {
+  if (b.n_gauss <= 0) return;
+  k_slice_bwd_pre_batch<<<ceil_div(b.n_gauss, PRE_THREADS), PRE_THREADS, 0, st>>>(b, accum);
+  note_launch();
 }
 
 void launch_slice_bwd_pre(const SliceArgs& a, const float* accum, float* d_mu, float* d_scale,

@@ -23,7 +23,44 @@ struct SliceArgs {
   const float* zorig;   // [S] plane position of slice index s
   int S, H, W;
   int tile, TX, TY;     // tile side and tile grid (TX * TY tiles per slice)
+  // batched launches: this item's first Gaussian and first (slice, tile) key in
+  // the batch-wide index spaces (0 for a single render), its output image,
+  // upstream gradient and parameter-gradient outputs
+  int gbase;
+  uint32_t key_base;
+  float* out;
+  const float* dL_dI;
+  float *d_mu, *d_scale, *d_quat, *d_alpha;
 };
+
+// Items of a batched launch, in device memory: args[k] describes item k, whose
+// Gaussians are [gstart[k], gstart[k+1]) and keys [kstart[k], kstart[k+1]).
+struct BatchItems {
+  const SliceArgs* args;
+  const int* gstart;
+  const uint32_t* kstart;
+  int n_items;
+  int n_gauss;        // gstart[n_items]
+  uint32_t n_keys;    // kstart[n_items]
+};
+
+void launch_slice_pre_batch(const BatchItems& b, SliceRec* rec, unsigned long long* counts, cudaStream_t st);
+void launch_slice_emit_batch(const BatchItems& b, const SliceRec* rec, const unsigned long long* offsets,
+                             const unsigned long long* counts, uint32_t cap, uint32_t* keys, uint32_t* emit_gid,
+                             cudaStream_t st);
+void launch_slice_bwd_pre_batch(const BatchItems& b, const float* accum, cudaStream_t st);
+void launch_det_reduce_n(int n, const unsigned long long* offsets, const unsigned long long* counts,
+                         const float4* partial, float* accum, unsigned long long cap, cudaStream_t st);
+// Persistent block-culled rasterisers over every (item, slice, tile) key of a
+// batch: CTAs take chunks of keys from *work (zeroed before each launch).
+cudaError_t launch_raster_fwd_batch(const BatchItems& b, int tile, int chunk, int ctas, int exp_mode,
+                                    const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
+                                    const uint2* ranges, unsigned* work, cudaStream_t st);
+cudaError_t launch_raster_bwd_batch(const BatchItems& b, int tile, int chunk, int ctas, int exp_mode, bool det,
+                                    const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
+                                    const uint2* ranges, float* accum, float4* partial, unsigned* work,
+                                    cudaStream_t st);
+int raster_batch_ctas_per_sm(int tile, int chunk, bool backward);
 
 // K-pre: records + per-Gaussian pair counts.
 void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st);

@@ -1,0 +1,133 @@
+"""GPU tests of the batched form: one graph launch renders and differentiates
+many uneven Gaussian sets; every item must agree with its own plain launch and
+with the FP64 oracle, repeated runs must see updated parameters, and a run that
+outgrows the plan must report GP_ERR_OVERFLOW."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_20611_b300 import binding as B
+from paper_2603_20611_b300 import synth
+from tests.gpu_util import assert_forward_close, assert_grads_close, dev_set, np32, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _items(seed=7, n=6, with_target=False):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    items, meta = [], []
+    for k in range(n):
+        side = int(rng.choice([24, 40, 64, 72]))
+        depth = int(rng.integers(8, 20))
+        cnt = int(rng.integers(50, 600))
+        g = synth.small(seed=seed * 100 + k, n=cnt, extent=(side, side + 3, depth))
+        S = int(rng.integers(2, 7))
+        sig = float(rng.uniform(1.0, 4.0))
+        axis = int(rng.integers(0, 3))
+        # extent (x, y, z) = (side, side + 3, depth); planes across the slice axis
+        span = {2: depth, 1: side + 3, 0: side}[axis]
+        z = np.sort(rng.uniform(0.0, span, S)).astype(np.float32)[rng.permutation(S)]
+        H, W = {2: (side + 3, side), 1: (depth, side), 0: (depth, side + 3)}[axis]
+        gs = dev_set(g)
+        it = {"gs": gs, "z": z, "H": H, "W": W, "sigma_z": sig, "axis": axis,
+              "out": torch.empty(S, H, W, device="cuda"),
+              "grads": (torch.empty(cnt, 3, device="cuda"), torch.empty(cnt, 3, device="cuda"),
+                        torch.empty(cnt, 4, device="cuda"), torch.empty(cnt, device="cuda"))}
+        if with_target:
+            it["target"] = torch.from_numpy(synth.random_field(500 + k, (S, H, W), 0.05)).cuda()
+            it["loss"] = torch.zeros(1, device="cuda")
+        else:
+            it["dL_dI"] = torch.from_numpy(synth.random_field(500 + k, (S, H, W))).cuda()
+        items.append(it)
+        meta.append(g)
+    return items, meta
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batch_matches_plain_and_oracle(autotune):
+    ctx = B.Context(0)
+    items, meta = _items()
+    plan = B.BatchPlan(ctx, items, autotune=autotune)
+    plan.run()
+    plan.wait()
+    info = plan.info()
+    assert info["tile"] in (8, 16) and info["pair_capacity"] > 0
+    plain = B.Context(0, tile=info["tile"])
+    for k, (it, g) in enumerate(zip(items, meta)):
+        ref_img = B.gp_render_slices(plain, it["gs"], it["z"], it["H"], it["W"], it["sigma_z"], it["axis"])
+        assert rel_l2(np32(it["out"]), np32(ref_img)) < 1e-6, k
+        ref_g = B.gp_render_backward(plain, it["gs"], it["z"], it["H"], it["W"], it["sigma_z"], it["dL_dI"],
+                                     it["axis"])
+        for a, b in zip(it["grads"], ref_g):
+            assert rel_l2(np32(a), np32(b)) < 1e-4, k
+        if k < 3:
+            o = oracle.render(g.mu, g.scale, g.quat, g.alpha, it["z"], it["H"], it["W"], it["sigma_z"],
+                              axis=it["axis"])
+            assert_forward_close(np32(it["out"]), o, f"batch item {k}")
+            og = oracle.render_backward(g.mu, g.scale, g.quat, g.alpha, it["z"], it["H"], it["W"], it["sigma_z"],
+                                        it["dL_dI"].cpu().numpy(), axis=it["axis"])
+            assert_grads_close(it["grads"], og, f"batch item {k}")
+    plan.close()
+
+
+def test_batch_with_targets_runs_loss_and_backward():
+    ctx = B.Context(0)
+    items, meta = _items(seed=9, n=4, with_target=True)
+    plan = B.BatchPlan(ctx, items)
+    plan.run()
+    plan.wait()
+    for k, (it, g) in enumerate(zip(items, meta)):
+        I = B.gp_render_slices(ctx, it["gs"], it["z"], it["H"], it["W"], it["sigma_z"], it["axis"])
+        loss = torch.zeros(1, device="cuda")
+        dL, _ = B.gp_mse_grad(ctx, I, it["target"], loss=loss)
+        ref = B.gp_render_backward(ctx, it["gs"], it["z"], it["H"], it["W"], it["sigma_z"], dL, it["axis"])
+        assert it["loss"].item() == pytest.approx(loss.item(), rel=1e-5)
+        for a, b in zip(it["grads"], ref):
+            assert rel_l2(np32(a), np32(b)) < 1e-4, k
+    plan.close()
+
+
+def test_batch_replay_sees_parameter_updates_and_is_deterministic():
+    ctx = B.Context(0, deterministic=True)
+    items, meta = _items(seed=11, n=5)
+    plan = B.BatchPlan(ctx, items)
+    plan.run()
+    plan.wait()
+    first = [it["out"].clone() for it in items]
+    grads1 = [[t.clone() for t in it["grads"]] for it in items]
+    plan.run()
+    plan.wait()
+    for it, f, g1 in zip(items, first, grads1):
+        assert torch.equal(it["out"], f)
+        for a, b in zip(it["grads"], g1):
+            assert torch.equal(a, b)
+    # intensities are linear: doubling alpha in place doubles every image
+    for it in items:
+        it["gs"].alpha.mul_(2.0)
+    plan.run()
+    plan.wait()
+    for it, f in zip(items, first):
+        assert rel_l2(np32(it["out"]), 2.0 * np32(f)) < 1e-6
+    plan.close()
+
+
+def test_batch_overflow_is_reported_not_faulted():
+    ctx = B.Context(0)
+    items, meta = _items(seed=13, n=3)
+    plan = B.BatchPlan(ctx, items)
+    plan.run()
+    plan.wait()
+    # grow every Gaussian 4x: far more (slice, tile) pairs than the plan holds
+    for it in items:
+        it["gs"].scale.mul_(4.0)
+    plan.run()
+    with pytest.raises(B.GPError) as ei:
+        plan.wait()
+    assert ei.value.status == B.GP_ERR_OVERFLOW
+    plan.close()
+    # a fresh plan sized for the new parameters runs clean
+    plan2 = B.BatchPlan(ctx, items)
+    plan2.run()
+    plan2.wait()
+    plan2.close()
