@@ -114,13 +114,13 @@ def test_batch_replay_sees_parameter_updates_and_is_deterministic():
 
 def test_batch_overflow_is_reported_not_faulted():
     ctx = B.Context(0)
-    items, meta = _items(seed=13, n=3)
+    items, meta = _items(seed=13, n=6)
     plan = B.BatchPlan(ctx, items)
     plan.run()
     plan.wait()
-    # grow every Gaussian 4x: far more (slice, tile) pairs than the plan holds
+    # grow every Gaussian 8x: far more (slice, tile) pairs than the plan holds
     for it in items:
-        it["gs"].scale.mul_(4.0)
+        it["gs"].scale.mul_(8.0)
     plan.run()
     with pytest.raises(B.GPError) as ei:
         plan.wait()
