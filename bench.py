@@ -445,6 +445,106 @@ def run_batched(args):
     return 0
 
 
+# ------------------------------------------------------------- serving workload
+
+def run_serving(args):
+    """8 resident sets (50k-2M Gaussians in 1024^3), Poisson arrivals at swept
+    rates; each request is a random axis-aligned slice (side 256-1024, random
+    axis), a 16-slice 512^2 stack, or a 256^3 voxelize.  Reports throughput and
+    p50 / p99 latency per rate."""
+    import threading
+    import torch
+    from paper_2603_20611_b300 import binding as B
+    from paper_2603_20611_b300 import synth
+    torch.cuda.set_device(0)
+    dev = "cuda:0"
+    ctx = B.Context(0)
+    sets = [B.GaussianSet.from_numpy(g, dev) for g in synth.serving_sets()]
+    srv = B.Server(ctx, workers=args.serve_workers, max_batch_slices=64)
+    for g in sets:
+        srv.load_set(g)
+    pools = {B.GP_REQ_SLICE: [torch.empty(1024 * 1024, device=dev) for _ in range(48)],
+             B.GP_REQ_STACK: [torch.empty(16 * 512 * 512, device=dev) for _ in range(48)],
+             B.GP_REQ_VOXELIZE: [torch.empty(256 ** 3, device=dev) for _ in range(24)]}
+    rng = np.random.Generator(np.random.PCG64(5005))
+    rates = [float(r) for r in args.rates.split(",")]
+    per_rate = []
+    for rate in rates:
+        n_req = int(max(20, min(args.serve_requests, rate * args.serve_seconds)))
+        free = {k: list(range(len(v))) for k, v in pools.items()}
+        lock = threading.Lock()
+        lat, pend = [], {}
+        done_evt = threading.Event()
+
+        def poller():
+            while not (done_evt.is_set() and not pend):
+                with lock:
+                    items = list(pend.items())
+                if not items:
+                    time.sleep(0.0005)
+                    continue
+                for t, (kind, slot) in items:
+                    res = srv.poll(t, timeout_ms=0)
+                    if res is not None:
+                        with lock:
+                            lat.append(res["latency_ms"])
+                            free[kind].append(slot)
+                            del pend[t]
+                time.sleep(0.0002)
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        next_t = t0
+        kinds = rng.choice(3, n_req)
+        for i in range(n_req):
+            next_t += rng.exponential(1.0 / rate)
+            while time.perf_counter() < next_t:
+                time.sleep(min(0.0005, max(0.0, next_t - time.perf_counter())))
+            kind = [B.GP_REQ_SLICE, B.GP_REQ_STACK, B.GP_REQ_VOXELIZE][int(kinds[i])]
+            while True:
+                with lock:
+                    if free[kind]:
+                        slot = free[kind].pop()
+                        break
+                time.sleep(0.0002)
+            buf = pools[kind][slot]
+            sid = int(rng.integers(0, len(sets)))
+            if kind == B.GP_REQ_VOXELIZE:
+                t = srv.submit(kind, sid, buf, X=256, Y=256, Z=256)
+            elif kind == B.GP_REQ_SLICE:
+                side = int(rng.integers(256, 1025))
+                axis = int(rng.integers(0, 3))
+                z = np.array([rng.uniform(0, 1024)], np.float32)
+                t = srv.submit(kind, sid, buf[:side * side], z=z, H=side, W=side, sigma_z=3.0, axis=axis)
+            else:
+                z0 = rng.uniform(0, 1024 - 16)
+                z = (z0 + np.arange(16)).astype(np.float32)
+                t = srv.submit(kind, sid, buf, z=z, H=512, W=512, sigma_z=3.0, axis=2)
+            with lock:
+                pend[t] = (kind, slot)
+        done_evt.set()
+        th.join()
+        wall = time.perf_counter() - t0
+        lat_a = np.array(lat)
+        per_rate.append({"offered_req_per_s": rate, "requests": n_req, "throughput_req_per_s": n_req / wall,
+                         "p50_ms": float(np.percentile(lat_a, 50)), "p99_ms": float(np.percentile(lat_a, 99)),
+                         "mean_ms": float(lat_a.mean())})
+        log(f"rate {rate}: {per_rate[-1]}")
+    st = srv.stats()
+    srv.close()
+    best = max(per_rate, key=lambda r: r["throughput_req_per_s"])
+    line = {"metric": "served requests/s with p50/p99 latency", "value": best["throughput_req_per_s"],
+            "unit": "req/s", "n_gpus": 1, "steps": len(rates), "warmup": 0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving: 8 resident sets of 50k-2M Gaussians in 1024^3; Poisson arrivals; "
+                                   "requests uniform over {1 slice 256^2-1024^2 on a random axis, 16-slice 512^2 "
+                                   "stack, 256^3 voxelize}", "workers": args.serve_workers},
+            "per_rate": per_rate, "server_stats": st}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -460,7 +560,11 @@ def main():
     ap.add_argument("--ref-px", type=int, default=2048)
     ap.add_argument("--ref-gauss", type=int, default=0, help="0 = twice the oracle's threads")
     ap.add_argument("--case", default="microscopy", choices=["microscopy", "small"])
-    ap.add_argument("--workload", default="fit", choices=["fit", "batched"])
+    ap.add_argument("--workload", default="fit", choices=["fit", "batched", "serving"])
+    ap.add_argument("--rates", default="10,30,100,300,1000")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-workers", type=int, default=4)
     args = ap.parse_args()
     if args.case == "small":
         use_small_case()
@@ -472,6 +576,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_native(args, rank, world)
 
 

@@ -248,6 +248,66 @@ GP_API gp_status gp_batch_info(gp_plan* plan, int64_t* pair_capacity, int* tile,
                                int* bwd_chunk, int64_t* device_bytes);
 GP_API gp_status gp_batch_destroy(gp_plan* plan);
 
+/* ------------------------------------------------------------------- serving
+ * A request loop over resident Gaussian sets (deployment form; the paper has no
+ * server).  Requests -- one slice, a stack of slices, or a voxelize -- enter a
+ * queue; worker threads, each with its own context (workspace) and CUDA
+ * stream, take them as soon as a worker is free and the request's estimated
+ * device memory fits the budget (free HBM minus a reserve, or a fixed budget),
+ * so requests that arrive while others run overlap with them on the GPU.  A
+ * worker taking a slice/stack request also takes every pending request for the
+ * same set, axis, image size and sigma_z (up to max_batch_slices planes) and
+ * renders them in one call; results are bitwise the same alone and in a batch.
+ * Outputs are caller-owned device buffers that must stay valid until the
+ * request completes.  submit / poll / stats may be called from any thread. */
+#define GP_REQ_SLICE 0     /* one plane: S must be 1 */
+#define GP_REQ_STACK 1     /* S planes */
+#define GP_REQ_VOXELIZE 2  /* X x Y x Z volume */
+
+typedef struct {
+  int workers;                 /* concurrent requests on the device (default 4) */
+  int max_batch_slices;        /* planes per batched render (default 64) */
+  int64_t hbm_budget_bytes;    /* fixed admission budget; 0 = free HBM minus reserve */
+  int64_t hbm_reserve_bytes;   /* kept free when the budget follows free HBM (default 4 GiB) */
+} gp_serve_cfg;
+
+typedef struct {
+  int kind;
+  int set_id;
+  const float* z;   /* HOST plane positions [S] (copied at submit) */
+  int S, H, W;
+  float sigma_z;
+  int axis;
+  int X, Y, Z;      /* voxelize */
+  float* out;       /* DEVICE [S][H][W] or [Z][Y][X] */
+} gp_request;
+
+typedef struct {
+  gp_status status;
+  double latency_ms;   /* submit -> completion */
+  double queue_ms;     /* submit -> start on a worker */
+  int batch_size;      /* requests rendered together */
+} gp_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, batches, admission_waits, pending, inflight_bytes;
+} gp_serve_stats;
+
+typedef struct gp_server gp_server;
+
+/* Starts the workers (cfg NULL = defaults) on ctx's device, with ctx's config. */
+GP_API gp_status gp_serve_open(gp_ctx* ctx, const gp_serve_cfg* cfg, gp_server** out);
+/* Registers a resident set (caller keeps its device memory valid); returns its id. */
+GP_API gp_status gp_serve_load_set(gp_server* server, const gp_set* set, int* set_id);
+/* Queues a request (validated here: GP_ERR_ARG) and returns its ticket. */
+GP_API gp_status gp_serve_submit(gp_server* server, const gp_request* req, uint64_t* ticket);
+/* Waits up to timeout_ms for the ticket: GP_OK with *out filled (once per
+ * ticket), or GP_PENDING if it is still queued or running. */
+GP_API gp_status gp_serve_poll(gp_server* server, uint64_t ticket, int timeout_ms, gp_result* out);
+GP_API gp_status gp_serve_stats_get(gp_server* server, gp_serve_stats* out);
+/* Stops the workers after their current requests; still-queued requests are dropped. */
+GP_API gp_status gp_serve_close(gp_server* server);
+
 /* Phase timing.  When enabled, every call records a CUDA event pair on its
  * stream around each phase below; gp_timing_read synchronises those events,
  * returns the summed milliseconds and launch counts per phase since the last

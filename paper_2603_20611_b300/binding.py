@@ -34,7 +34,10 @@ EXPORTS = (
     "gp_last_counts", "gp_count_evals", "gp_exp2_eval", "gp_timing_enable", "gp_timing_read",
     "gp_launch_count", "gp_fma_probe_threads", "gp_fma_probe", "gp_mse_grad_noalloc",
     "gp_batch_plan", "gp_batch_run", "gp_batch_wait", "gp_batch_info", "gp_batch_destroy",
+    "gp_serve_open", "gp_serve_load_set", "gp_serve_submit", "gp_serve_poll", "gp_serve_stats_get",
+    "gp_serve_close",
 )
+GP_REQ_SLICE, GP_REQ_STACK, GP_REQ_VOXELIZE = 0, 1, 2
 GP_BATCH_AUTOTUNE = 1
 GP_NUM_PHASES = 7
 PHASES = ("bin", "fwd", "bwd", "bwd_pre", "loss", "vox_fwd", "vox_bwd")
@@ -63,6 +66,27 @@ class gp_batch_item(ctypes.Structure):
                 ("out", ctypes.c_void_p), ("target", ctypes.c_void_p), ("dL_dI", ctypes.c_void_p),
                 ("d_mu", ctypes.c_void_p), ("d_scale", ctypes.c_void_p), ("d_quat", ctypes.c_void_p),
                 ("d_alpha", ctypes.c_void_p), ("loss", ctypes.c_void_p)]
+
+
+class gp_serve_cfg(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int), ("max_batch_slices", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_int64), ("hbm_reserve_bytes", ctypes.c_int64)]
+
+
+class gp_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("set_id", ctypes.c_int), ("z", ctypes.c_void_p), ("S", ctypes.c_int),
+                ("H", ctypes.c_int), ("W", ctypes.c_int), ("sigma_z", ctypes.c_float), ("axis", ctypes.c_int),
+                ("X", ctypes.c_int), ("Y", ctypes.c_int), ("Z", ctypes.c_int), ("out", ctypes.c_void_p)]
+
+
+class gp_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("batch_size", ctypes.c_int)]
+
+
+class gp_serve_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "batches", "admission_waits",
+                                              "pending", "inflight_bytes")]
 
 
 def _load():
@@ -98,6 +122,12 @@ def _load():
         "gp_batch_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                           ctypes.POINTER(I64)],
         "gp_batch_destroy": [P],
+        "gp_serve_open": [P, ctypes.POINTER(gp_serve_cfg), ctypes.POINTER(P)],
+        "gp_serve_load_set": [P, SP, ctypes.POINTER(I)],
+        "gp_serve_submit": [P, ctypes.POINTER(gp_request), ctypes.POINTER(ctypes.c_uint64)],
+        "gp_serve_poll": [P, ctypes.c_uint64, I, ctypes.POINTER(gp_result)],
+        "gp_serve_stats_get": [P, ctypes.POINTER(gp_serve_stats)],
+        "gp_serve_close": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -348,6 +378,73 @@ class BatchPlan:
     def close(self):
         if getattr(self, "h", None):
             lib.gp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """gp_serve_*: resident sets, asynchronous requests, poll for completion."""
+
+    def __init__(self, ctx, workers=4, max_batch_slices=64, hbm_budget_bytes=0, hbm_reserve_bytes=4 << 30):
+        cfg = gp_serve_cfg(workers, max_batch_slices, hbm_budget_bytes, hbm_reserve_bytes)
+        h = ctypes.c_void_p()
+        st = lib.gp_serve_open(ctx.h, ctypes.byref(cfg), ctypes.byref(h))
+        if st != GP_OK:
+            raise GPError(st, "gp_serve_open")
+        self.h = h
+        self._sets = []
+        self._outs = {}
+
+    def load_set(self, gs):
+        self._sets.append(gs)
+        sid = ctypes.c_int()
+        st = lib.gp_serve_load_set(self.h, ctypes.byref(gs.c()), ctypes.byref(sid))
+        if st != GP_OK:
+            raise GPError(st, "gp_serve_load_set")
+        return sid.value
+
+    def submit(self, kind, set_id, out, z=None, H=0, W=0, sigma_z=1.0, axis=2, X=0, Y=0, Z=0):
+        r = gp_request()
+        r.kind, r.set_id = int(kind), int(set_id)
+        zz = None
+        if z is not None:
+            zz = _host_f32(z)
+            r.z, r.S = zz.ctypes.data_as(ctypes.c_void_p).value, zz.shape[0]
+        r.H, r.W, r.sigma_z, r.axis = int(H), int(W), float(sigma_z), int(axis)
+        r.X, r.Y, r.Z = int(X), int(Y), int(Z)
+        r.out = _dev(out, "out").value
+        t = ctypes.c_uint64()
+        st = lib.gp_serve_submit(self.h, ctypes.byref(r), ctypes.byref(t))
+        if st != GP_OK:
+            raise GPError(st, "gp_serve_submit")
+        self._outs[t.value] = out
+        return t.value
+
+    def poll(self, ticket, timeout_ms=0):
+        """None while pending, else a dict with status and latencies."""
+        res = gp_result()
+        st = lib.gp_serve_poll(self.h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(res))
+        if st == GP_PENDING:
+            return None
+        if st != GP_OK:
+            raise GPError(st, "gp_serve_poll")
+        self._outs.pop(ticket, None)
+        return {"status": res.status, "latency_ms": res.latency_ms, "queue_ms": res.queue_ms,
+                "batch_size": res.batch_size}
+
+    def stats(self):
+        s = gp_serve_stats()
+        lib.gp_serve_stats_get(self.h, ctypes.byref(s))
+        return {n: getattr(s, n) for n, _ in gp_serve_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.gp_serve_close(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,131 @@
+"""GPU tests of the serving loop: each result is the same alone and in a mix of
+concurrent, batched requests; slice results equal the plain render (and the
+oracle); admission holds requests back under a small memory budget; bad
+requests are rejected at submit."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_20611_b300 import binding as B
+from paper_2603_20611_b300 import synth
+from tests.gpu_util import assert_forward_close, dev_set, np32
+
+pytestmark = pytest.mark.gpu
+
+
+def _sets():
+    a = synth.small(seed=71, n=3000, extent=(96, 96, 48))
+    b = synth.small(seed=72, n=1500, extent=(96, 96, 48))
+    return [a, b]
+
+
+def _requests(rng, n):
+    reqs = []
+    for _ in range(n):
+        kind = int(rng.choice([B.GP_REQ_SLICE, B.GP_REQ_STACK, B.GP_REQ_VOXELIZE], p=[0.5, 0.3, 0.2]))
+        sid = int(rng.integers(0, 2))
+        if kind == B.GP_REQ_VOXELIZE:
+            reqs.append(dict(kind=kind, set_id=sid, X=40, Y=36, Z=24, shape=(24, 36, 40)))
+        else:
+            S = 1 if kind == B.GP_REQ_SLICE else int(rng.integers(2, 6))
+            z = rng.uniform(0, 48, S).astype(np.float32)
+            reqs.append(dict(kind=kind, set_id=sid, z=z, H=96, W=96, sigma_z=2.0, axis=2, shape=(S, 96, 96)))
+    return reqs
+
+
+def _submit(srv, r, out):
+    if r["kind"] == B.GP_REQ_VOXELIZE:
+        return srv.submit(r["kind"], r["set_id"], out, X=r["X"], Y=r["Y"], Z=r["Z"])
+    return srv.submit(r["kind"], r["set_id"], out, z=r["z"], H=r["H"], W=r["W"], sigma_z=r["sigma_z"],
+                      axis=r["axis"])
+
+
+def _wait(srv, t):
+    for _ in range(600):
+        res = srv.poll(t, timeout_ms=100)
+        if res is not None:
+            return res
+    raise AssertionError("request did not complete")
+
+
+def test_results_alone_equal_results_in_the_mix():
+    ctx = B.Context(0)
+    sets = [dev_set(g) for g in _sets()]
+    rng = np.random.Generator(np.random.PCG64(5))
+    reqs = _requests(rng, 24)
+    srv = B.Server(ctx, workers=3, max_batch_slices=32)
+    ids = [srv.load_set(g) for g in sets]
+    assert ids == [0, 1]
+    alone = []
+    for r in reqs:
+        out = torch.full(r["shape"], float("nan"), device="cuda")
+        res = _wait(srv, _submit(srv, r, out))
+        assert res["status"] == B.GP_OK
+        alone.append(out)
+    outs = [torch.full(r["shape"], float("nan"), device="cuda") for r in reqs]
+    tickets = [_submit(srv, r, o) for r, o in zip(reqs, outs)]
+    results = [_wait(srv, t) for t in tickets]
+    assert all(res["status"] == B.GP_OK for res in results)
+    for a, b in zip(alone, outs):
+        assert torch.equal(a, b)
+    st = srv.stats()
+    assert st["completed"] == 2 * len(reqs) and st["failed"] == 0
+    srv.close()
+
+
+def test_batched_slices_match_plain_render_and_oracle():
+    ctx = B.Context(0)
+    g = _sets()[0]
+    gs = dev_set(g)
+    srv = B.Server(ctx, workers=1, max_batch_slices=64)
+    sid = srv.load_set(gs)
+    rng = np.random.Generator(np.random.PCG64(6))
+    zs = [rng.uniform(0, 48, 1).astype(np.float32) for _ in range(12)]
+    outs = [torch.empty(1, 96, 96, device="cuda") for _ in zs]
+    tickets = [srv.submit(B.GP_REQ_SLICE, sid, o, z=z, H=96, W=96, sigma_z=2.0) for z, o in zip(zs, outs)]
+    res = [_wait(srv, t) for t in tickets]
+    assert max(r["batch_size"] for r in res) > 1  # queued slices were rendered together
+    for z, o in zip(zs, outs):
+        ref = B.gp_render_slices(ctx, gs, z, 96, 96, 2.0)
+        assert torch.equal(o, ref)
+    z_all = np.concatenate(zs)
+    ref = oracle.render(g.mu, g.scale, g.quat, g.alpha, z_all, 96, 96, 2.0)
+    assert_forward_close(np.concatenate([np32(o) for o in outs]), ref, "served slices")
+    srv.close()
+
+
+def test_admission_under_a_small_budget():
+    ctx = B.Context(0)
+    sets = [dev_set(g) for g in _sets()]
+    srv = B.Server(ctx, workers=4, hbm_budget_bytes=1)  # only one request in flight at a time
+    for g in sets:
+        srv.load_set(g)
+    rng = np.random.Generator(np.random.PCG64(7))
+    reqs = _requests(rng, 12)
+    outs = [torch.empty(r["shape"], device="cuda") for r in reqs]
+    tickets = [_submit(srv, r, o) for r, o in zip(reqs, outs)]
+    results = [_wait(srv, t) for t in tickets]
+    assert all(r["status"] == B.GP_OK for r in results)
+    assert srv.stats()["admission_waits"] > 0
+    srv.close()
+
+
+def test_bad_requests_are_rejected():
+    ctx = B.Context(0)
+    srv = B.Server(ctx, workers=1)
+    sid = srv.load_set(dev_set(_sets()[1]))
+    out = torch.empty(1, 8, 8, device="cuda")
+    z = np.array([3.0], np.float32)
+    for kw in (dict(set_id=5), dict(H=0), dict(sigma_z=0.0), dict(axis=4)):
+        a = dict(set_id=sid, H=8, W=8, sigma_z=1.0, axis=2)
+        a.update(kw)
+        with pytest.raises(B.GPError) as ei:
+            srv.submit(B.GP_REQ_SLICE, a["set_id"], out, z=z, H=a["H"], W=a["W"], sigma_z=a["sigma_z"],
+                       axis=a["axis"])
+        assert ei.value.status == B.GP_ERR_ARG
+    with pytest.raises(B.GPError):
+        srv.submit(B.GP_REQ_SLICE, sid, out, z=np.array([1.0, 2.0], np.float32), H=8, W=8)  # SLICE needs S == 1
+    with pytest.raises(B.GPError):
+        srv.poll(12345)
+    srv.close()
