@@ -227,7 +227,8 @@ def run_native(args, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     ctx = B.Context(dev_index, exp_mode=B.GP_EXP_HW if args.exp == "hw" else B.GP_EXP_POLY,
-                    deterministic=args.det, tile=args.tile, fwd_px=args.fwd_px, bwd_px=args.bwd_px)
+                    deterministic=args.det, tile=args.tile, fwd_px=args.fwd_px, bwd_px=args.bwd_px,
+                    reuse_bins=not args.rebin)
     stream = torch.cuda.current_stream()
     t_setup = time.perf_counter()
     g, gs, target = make_workload(B, synth, torch, dev, ctx)
@@ -349,6 +350,7 @@ def run_native(args, rank, world):
                 "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(WORKLOAD, exp=args.exp, deterministic=bool(args.det), tile=args.tile,
+                               backward_bins="re-binned" if args.rebin else "reused from the step's forward",
                                parallelism="replicas" if world > 1 else "single"),
                 "slices_per_s": world * S * args.steps / t_total,
                 "evals_fwd_per_step": float(np.mean(ev_steps)),
@@ -557,6 +559,7 @@ def main():
     ap.add_argument("--fwd-px", type=int, default=0)
     ap.add_argument("--bwd-px", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rebin", action="store_true", help="the backward re-bins instead of reusing the forward's")
     ap.add_argument("--ref-px", type=int, default=2048)
     ap.add_argument("--ref-gauss", type=int, default=0, help="0 = twice the oracle's threads")
     ap.add_argument("--case", default="microscopy", choices=["microscopy", "small"])

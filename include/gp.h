@@ -85,6 +85,12 @@ typedef struct {
   int bwd_px;             /* backward rasteriser: 0 (default) = block-culled kernel, or the
                              per-thread kernel (16: 2, 4, 8 pixels per thread; 8: 2) */
   int64_t workspace_limit;/* max device bytes of library scratch, 0 = no limit */
+  int reuse_bins;         /* 1: gp_render_backward reuses the binning of the immediately
+                             preceding gp_render_slices on this context when called with the
+                             same set pointers, n, scale_mod, planes, image size, sigma_z and
+                             axis; the caller guarantees the parameter VALUES are unchanged
+                             in between (true inside one forward/backward step).  0 (default):
+                             the backward always re-bins. */
 } gp_config;
 
 /* Fills *cfg with the defaults above.  Returns GP_ERR_ARG if cfg is NULL. */

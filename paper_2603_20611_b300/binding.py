@@ -52,7 +52,7 @@ class GPError(RuntimeError):
 class gp_config(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("deterministic", ctypes.c_int), ("exp_mode", ctypes.c_int),
                 ("tile", ctypes.c_int), ("fwd_px", ctypes.c_int), ("bwd_px", ctypes.c_int),
-                ("workspace_limit", ctypes.c_int64)]
+                ("workspace_limit", ctypes.c_int64), ("reuse_bins", ctypes.c_int)]
 
 
 class gp_set(ctypes.Structure):
@@ -168,12 +168,13 @@ class Context:
     """Owns a gp_ctx (device workspace pool) on one CUDA device."""
 
     def __init__(self, device=0, eps=1e-6, deterministic=False, exp_mode=GP_EXP_POLY, tile=16,
-                 fwd_px=0, bwd_px=0, workspace_limit=0):
+                 fwd_px=0, bwd_px=0, workspace_limit=0, reuse_bins=False):
         cfg = gp_config()
         lib.gp_config_default(ctypes.byref(cfg))
         cfg.eps, cfg.deterministic, cfg.exp_mode = float(eps), int(bool(deterministic)), int(exp_mode)
         cfg.tile, cfg.fwd_px, cfg.bwd_px = int(tile), int(fwd_px), int(bwd_px)
         cfg.workspace_limit = int(workspace_limit)
+        cfg.reuse_bins = int(bool(reuse_bins))
         self.device = int(device)
         self.cfg = cfg
         h = ctypes.c_void_p()

@@ -63,8 +63,22 @@ struct PhaseEvent {
   int64_t launches;
 };
 
+// Arguments of the binning currently held in a context's buffers.
+struct BinKey {
+  bool valid = false;
+  const float *mu = nullptr, *scale = nullptr, *quat = nullptr, *alpha = nullptr;
+  int64_t n = 0;
+  float mod = 0.f, sigma_z = 0.f;
+  std::vector<float> z;
+  int S = 0, H = 0, W = 0, axis = 0, tile = 0;
+};
+
 struct Ctx {
   int device = 0;
+  BinKey bin_key;          // what b.rec / b.ranges / the sorted values describe
+  uint32_t bin_pairs = 0;
+  const uint32_t* bin_vals = nullptr;
+  char bin_args[256];      // the SliceArgs of that binning (opaque here)
   bool timing = false;
   std::vector<PhaseEvent> events;
   std::vector<cudaEvent_t> event_pool;

@@ -289,7 +289,7 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
 
 // ------------------------------------------------------------ plain kernels
 template <int TILE, int CH, int EXPM>
-__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32) k_raster_fwd_blk(
+__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? 12 : 32) k_raster_fwd_blk(
     SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges) {
   __shared__ FwdSmem<TILE, CH> sm;
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32) k_raster_fwd_blk
 }
 
 template <int TILE, int CH, int EXPM, bool DET>
-__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32) k_raster_bwd_blk(
+__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? 10 : 32) k_raster_bwd_blk(
     SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, float* __restrict__ accum,
     float4* __restrict__ partial) {

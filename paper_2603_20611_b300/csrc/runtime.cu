@@ -194,6 +194,7 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
   for (int s = 0; s < S; ++s)
     if (!isfinite(z[s])) return set_err(c, GP_ERR_ARG, "z contains a non-finite value");
   PhaseTimer timer(c, GP_PHASE_BIN, st);
+  c->bin_key.valid = false;  // until this binning completes
   const int tile = tile_of(c);
   const int TX = ceil_div(W, tile), TY = ceil_div(H, tile);
   const int64_t nkeys = (int64_t)S * TX * TY;
@@ -246,7 +247,30 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
   *pairs_out = P;
   c->last_pairs = P;
   c->last_issued = (int64_t)P * tile * tile;
+  BinKey& k = c->bin_key;
+  k.valid = true;
+  k.mu = set->mu; k.scale = set->scale; k.quat = set->quat; k.alpha = set->alpha;
+  k.n = set->n; k.mod = set->scale_mod; k.sigma_z = sigma_z;
+  k.z.assign(z, z + S);
+  k.S = S; k.H = H; k.W = W; k.axis = axis; k.tile = tile;
+  c->bin_pairs = P;
+  c->bin_vals = *sorted_vals;
+  static_assert(sizeof(SliceArgs) <= sizeof(c->bin_args), "SliceArgs too large");
+  memcpy(c->bin_args, a, sizeof(SliceArgs));
   return cuda_err(c, cudaGetLastError(), "binning kernels");
+}
+
+// True if the context still holds a binning made with exactly these arguments.
+static bool bins_match(const Ctx* c, const gp_set* set, const float* z, int S, int H, int W, float sigma_z,
+                       int axis) {
+  const BinKey& k = c->bin_key;
+  if (!k.valid || k.mu != set->mu || k.scale != set->scale || k.quat != set->quat || k.alpha != set->alpha ||
+      k.n != set->n || k.mod != set->scale_mod || k.sigma_z != sigma_z || k.S != S || k.H != H || k.W != W ||
+      k.axis != axis || k.tile != tile_of(c))
+    return false;
+  for (int s = 0; s < S; ++s)
+    if (k.z[s] != z[s]) return false;
+  return true;
 }
 
 // Bins the voxelizer's (Gaussian, 8^3 tile) pairs: K-vpre, scan, count
@@ -287,6 +311,7 @@ static gp_status bin_voxels(Ctx* c, const gp_set* set, int X, int Y, int Z, cuda
   *pairs_out = P;
   c->last_pairs = P;
   c->last_issued = (int64_t)P * VOX_TILE * VOX_TILE * VOX_TILE;
+  c->bin_key.valid = false;  // the slice binning's buffers now hold voxel pairs
   return cuda_err(c, cudaGetLastError(), "voxel binning kernels");
 }
 
@@ -312,6 +337,7 @@ gp_status gp_config_default(gp_config* cfg) {
   cfg->fwd_px = 0;
   cfg->bwd_px = 0;
   cfg->workspace_limit = 0;
+  cfg->reuse_bins = 0;
   return GP_OK;
 }
 
@@ -421,7 +447,13 @@ gp_status gp_render_backward(gp_ctx* ctx, const gp_set* set, const float* z, int
   SliceArgs a;
   uint32_t P = 0;
   const uint32_t* vals = nullptr;
-  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, axis, st, &a, &P, &vals));
+  if (c->cfg.reuse_bins && S > 0 && z && bins_match(c, set, z, S, H, W, sigma_z, axis)) {
+    memcpy(&a, c->bin_args, sizeof(SliceArgs));
+    P = c->bin_pairs;
+    vals = c->bin_vals;
+  } else {
+    GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, axis, st, &a, &P, &vals));
+  }
   if (n == 0) return GP_OK;
   BinBufs& b = c->b;
   GP_TRY(ws_reserve(c, b.accum, (size_t)n * 10 * 4));

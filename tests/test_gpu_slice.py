@@ -295,3 +295,27 @@ def test_ultrasound_full_size_sampled_and_crop():
     grads = B.gp_render_backward(c, dev_set(crop), zc, 64, 64, 5.0, torch.from_numpy(Tc).cuda())
     ref = oracle.render_backward(*orc(crop), zc, 64, 64, 5.0, Tc)
     assert_grads_close(grads, ref, "ultrasound crop")
+
+
+def test_backward_reuses_forward_bins_only_for_identical_calls():
+    """reuse_bins: the backward right after a forward with the same arguments
+    uses its binning (bitwise the same result in deterministic mode); any other
+    call re-bins."""
+    g = synth.small(seed=51, n=800, extent=(48, 40, 16))
+    z = synth.slice_positions(range(0, 16, 2))
+    G = torch.from_numpy(synth.random_field(52, (8, 40, 48))).cuda()
+    plain = B.Context(0, deterministic=True)
+    reuse = B.Context(0, deterministic=True, reuse_bins=True)
+    gs = dev_set(g)
+    ref = B.gp_render_backward(plain, gs, z, 40, 48, 2.0, G)
+    B.gp_render_slices(reuse, gs, z, 40, 48, 2.0)
+    got = B.gp_render_backward(reuse, gs, z, 40, 48, 2.0, G)
+    for a, b in zip(got, ref):
+        assert torch.equal(a, b)
+    # different planes after the forward: must not reuse
+    z2 = (z + np.float32(0.5)).astype(np.float32)
+    ref2 = B.gp_render_backward(plain, gs, z2, 40, 48, 2.0, G)
+    B.gp_render_slices(reuse, gs, z, 40, 48, 2.0)
+    got2 = B.gp_render_backward(reuse, gs, z2, 40, 48, 2.0, G)
+    for a, b in zip(got2, ref2):
+        assert torch.equal(a, b)
