@@ -297,6 +297,7 @@ typedef struct {
 
 typedef struct {
   int64_t submitted, completed, failed, batches, admission_waits, pending, inflight_bytes;
+  int64_t inflight_requests, max_inflight_requests;  /* admitted and not finished; its maximum */
 } gp_serve_stats;
 
 typedef struct gp_server gp_server;

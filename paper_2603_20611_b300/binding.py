@@ -86,7 +86,8 @@ class gp_result(ctypes.Structure):
 
 class gp_serve_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "batches", "admission_waits",
-                                              "pending", "inflight_bytes")]
+                                              "pending", "inflight_bytes", "inflight_requests",
+                                              "max_inflight_requests")]
 
 
 def _load():

@@ -112,6 +112,7 @@ void finish(gp_server* s, const std::vector<Request>& reqs, gp_status st, Clock:
     res.batch_size = (int)reqs.size();
     s->done[q.ticket] = res;
     s->inflight_bytes -= q.est_bytes;
+    s->stats.inflight_requests -= 1;
     s->stats.completed += 1;
     if (st != GP_OK) s->stats.failed += 1;
   }
@@ -170,15 +171,16 @@ void worker_loop(gp_server* s, int wi) {
     std::vector<Request> batch;
     {
       std::unique_lock<std::mutex> lk(s->mu);
+      int64_t budget = 0;
       for (;;) {
         if (s->stop) return;
         if (!s->pending.empty()) {
           // admission: the oldest request first; it runs if its estimate fits in
           // the memory budget (always, when nothing else is in flight)
           const Request& head = s->pending.front();
-          const int64_t budget = s->cfg.hbm_budget_bytes > 0
-                                     ? s->cfg.hbm_budget_bytes
-                                     : free_device_bytes(s->device) - s->cfg.hbm_reserve_bytes + s->inflight_bytes;
+          budget = s->cfg.hbm_budget_bytes > 0
+                       ? s->cfg.hbm_budget_bytes
+                       : free_device_bytes(s->device) - s->cfg.hbm_reserve_bytes + s->inflight_bytes;
           if (s->inflight_bytes == 0 || s->inflight_bytes + head.est_bytes <= budget) break;
           s->stats.admission_waits += 1;
         }
@@ -190,7 +192,8 @@ void worker_loop(gp_server* s, int wi) {
       if (batch[0].r.kind != GP_REQ_VOXELIZE) {
         int planes = batch[0].r.S;
         for (auto it = s->pending.begin(); it != s->pending.end();) {
-          if (same_batch(batch[0].r, it->r) && planes + it->r.S <= s->cfg.max_batch_slices) {
+          if (same_batch(batch[0].r, it->r) && planes + it->r.S <= s->cfg.max_batch_slices &&
+              s->inflight_bytes + it->est_bytes <= budget) {
             planes += it->r.S;
             s->inflight_bytes += it->est_bytes;
             batch.push_back(std::move(*it));
@@ -200,6 +203,8 @@ void worker_loop(gp_server* s, int wi) {
           }
         }
       }
+      s->stats.inflight_requests += (int64_t)batch.size();
+      s->stats.max_inflight_requests = std::max(s->stats.max_inflight_requests, s->stats.inflight_requests);
     }
     const Clock::time_point started = Clock::now();
     gp_status st;

@@ -107,7 +107,12 @@ def test_admission_under_a_small_budget():
     tickets = [_submit(srv, r, o) for r, o in zip(reqs, outs)]
     results = [_wait(srv, t) for t in tickets]
     assert all(r["status"] == B.GP_OK for r in results)
-    assert srv.stats()["admission_waits"] > 0
+    st = srv.stats()
+    assert st["max_inflight_requests"] == 1 and st["inflight_requests"] == 0
+    for r, o in zip(reqs, outs):  # and the results are right
+        if r["kind"] != B.GP_REQ_VOXELIZE:
+            ref = B.gp_render_slices(ctx, sets[r["set_id"]], r["z"], r["H"], r["W"], r["sigma_z"], r["axis"])
+            assert torch.equal(o, ref)
     srv.close()
 
 
