@@ -7,10 +7,9 @@
 // of Gaussians in shared memory (16-byte loads of the 64-byte records, mu_2d
 // and a~ of this slice computed once per Gaussian).  Each warp then tests 32
 // staged Gaussians at a time against its block -- lane l tests Gaussian l with
-//     || c - mu_2d ||_C  >  k + max_{p in block} || p - c ||_C
-// (c the block centre, ||x||_C^2 = x^T Sigma_2d^-1 x, k^2 = 2 ln(1/eps)), which
-// by the triangle inequality proves every pixel of the block lies outside the
-// culling ellipse -- and compacts the hits with a ballot.  The warp's four
+//     min over the block's pixel-centre rectangle of d^T Sigma_2d^-1 d  >  k^2
+// (k^2 = 2 ln(1/eps)), i.e. every pixel of the block lies outside the culling
+// ellipse -- and compacts the hits with a ballot.  The warp's four
 // 8-lane groups then take four hits at a time; lane r of a group evaluates row r
 // of the block (8 pixels), so the per-Gaussian terms (row offset, shared part
 // of the quadratic form) are paid once per 8 pixels and the backward's
@@ -18,9 +17,12 @@
 //
 // Forward: each lane keeps 8 partial sums per group; the four groups are added
 // in a fixed shuffle tree at the end, so results are bitwise reproducible.
+// Along a row the exponent is a quadratic in the pixel offset q from the block's
+// centre column, evaluated with two FMAs per pixel.
 // Backward: six pixel moments per (Gaussian, block) -- sum G E, sum G E dx,
 // sum G E dy, sum G E dx^2, sum G E dx dy, sum G E dy^2 with E the Gaussian's
-// exponential and G = dL/dI -- reduced over the group's 8 rows, stored per warp,
+// exponential and G = dL/dI, formed from three row sums about the centre
+// column -- reduced over the group's 8 rows by a transposed butterfly, stored per warp,
 // summed over the 4 warps in a fixed order, then folded into the 10
 // accumulators of the Gaussian (atomics) or written as a per-pair partial
 // (deterministic mode).
@@ -33,51 +35,66 @@
 
 namespace gp {
 
-constexpr float kHalfBlock = 3.5f;  // pixel centres of an 8-wide block lie within +-3.5 of its centre
-
 // Staging of one Gaussian for one (slice, tile):
-//   s0 = (mu_2d,x - x0, mu_2d,y - y0, a~, thr)   thr: block-cull threshold (base-2 exponent units)
-//   s1 = (c0, c1, c2, C00)                        e = c0 dx^2 + c1 dx dy + c2 dy^2 = -log2(e)/2 d^T C d
-//   s2 = (delta, opacity_r, C01, C11)             backward only
+//   s0 = (mu_2d,x - x0, mu_2d,y - y0, a~, C11)
+//   s1 = (c0, c1, c2, C00)     e = c0 dx^2 + c1 dx dy + c2 dy^2 = -log2(e)/2 d^T C d
+//   s2 = (delta, opacity_r, C01, 0)    (backward)
+//   sc = (C01, 1/C00, 1/C11, 0)        block test
 template <int EXPM>
 __device__ __forceinline__ void stage_blk(const SliceRec* __restrict__ rec, uint32_t g, float zsv, float x0,
-                                          float y0, float sqrt_k2, float4& s0, float4& s1, float4& s2) {
+                                          float y0, float4& s0, float4& s1, float4& s2, float4& sc) {
   const float4* rp = reinterpret_cast<const float4*>(rec + g);
-  const float4 r0 = __ldg(rp), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2);
+  const float4 r0 = __ldg(rp), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3);
   const float d = r0.z - zsv;
   const float w = exp2_sel<EXPM>(fmaxf(-0.5f * kLog2e * d * d * r0.w, kExpFloor));
   const float mxr = (r0.x - x0) - r1.x * d;
   const float myr = (r0.y - y0) - r1.y * d;
   const float C00 = r2.x, C01 = r2.y, C11 = r2.z;
-  const float R2 = kHalfBlock * kHalfBlock * (C00 + C11) + 2.0f * kHalfBlock * kHalfBlock * fabsf(C01);
-  const float kr = sqrt_k2 + sqrtf(R2);
-  s0 = make_float4(mxr, myr, r1.z * w, -0.5f * kLog2e * kr * kr);
+  s0 = make_float4(mxr, myr, r1.z * w, C11);
   s1 = make_float4(-0.5f * kLog2e * C00, -kLog2e * C01, -0.5f * kLog2e * C11, C00);
-  s2 = make_float4(d, w, C01, C11);
+  s2 = make_float4(d, w, C01, 0.0f);
+  sc = make_float4(C01, r3.z, r3.w, 0.0f);
 }
 
-// Ballot of the Gaussians jb..jb+31 that may touch this warp's block; their
-// chunk indices are compacted into list[0..n).  Returns n.
-__device__ __forceinline__ int block_hits(const float4* __restrict__ s0, const float4* __restrict__ s1, int jb,
-                                          int cnt, float cx, float cy, int lane, int* list) {
+// min over the segment of the quadratic form along one block edge
+__device__ __forceinline__ float edge_q(float cf, float c01, float cv, float inv_v, float dfix, float lo, float hi) {
+  const float t = fminf(fmaxf(-c01 * dfix * inv_v, lo), hi);
+  return fmaf(cf * dfix, dfix, fmaf(2.0f * c01 * dfix, t, cv * t * t));
+}
+
+// Ballot of the Gaussians jb..jb+31 whose culling ellipse d^T C d <= k2 touches
+// this warp's block (pixel centres [bx + .5, bx + 7.5] x [by + .5, by + 7.5]):
+// the minimum of the quadratic form over the block rectangle, taken at the
+// centre if it lies inside and otherwise on the nearest of the four edges.
+// Their chunk indices are compacted into list[0..n).  Returns n.
+__device__ __forceinline__ int block_hits(const float4* __restrict__ s0, const float4* __restrict__ s1,
+                                          const float4* __restrict__ sc, int jb, int cnt, float bx, float by,
+                                          float k2, int lane, int* list) {
   const int j = jb + lane;
   bool hit = false;
   if (j < cnt) {
-    const float4 g0 = s0[j], g1 = s1[j];
-    const float dx = cx - g0.x, dy = cy - g0.y;
-    const float e = fmaf(dx, fmaf(g1.x, dx, g1.y * dy), g1.z * dy * dy);
-    hit = e >= g0.w;
+    const float4 g0 = s0[j], g1 = s1[j], gc = sc[j];
+    const float C00 = g1.w, C01 = gc.x, C11 = g0.w;
+    const float xl = bx + 0.5f - g0.x, xh = bx + 7.5f - g0.x;
+    const float yl = by + 0.5f - g0.y, yh = by + 7.5f - g0.y;
+    if (xl <= 0.0f && xh >= 0.0f && yl <= 0.0f && yh >= 0.0f) {
+      hit = true;
+    } else {
+      float m = fminf(edge_q(C00, C01, C11, gc.z, xl, yl, yh), edge_q(C00, C01, C11, gc.z, xh, yl, yh));
+      m = fminf(m, fminf(edge_q(C11, C01, C00, gc.y, yl, xl, xh), edge_q(C11, C01, C00, gc.y, yh, xl, xh)));
+      hit = m <= k2;
+    }
   }
-  const unsigned m = __ballot_sync(0xffffffffu, hit);
-  if (hit) list[__popc(m & ((1u << lane) - 1u))] = j;
+  const unsigned msk = __ballot_sync(0xffffffffu, hit);
+  if (hit) list[__popc(msk & ((1u << lane) - 1u))] = j;
   __syncwarp();
-  return __popc(m);
+  return __popc(msk);
 }
 
 // Shared memory of the forward body.
 template <int TILE, int CH>
 struct FwdSmem {
-  float4 s0[CH], s1[CH];
+  float4 s0[CH], s1[CH], sc[CH];
   int hitlist[(TILE / 8) * (TILE / 8)][32];
 };
 
@@ -94,11 +111,10 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane >> 3, row = lane & 7;
   const float bx = (float)((warp % (TILE / 8)) * 8), by = (float)((warp / (TILE / 8)) * 8);
-  const float cx = bx + 4.0f, cy = by + 4.0f;
   const float pyr = by + (float)row + 0.5f;
+  const float cxb = bx + 4.0f;  // centre column of the block's 8 pixel centres
   const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
   const float zsv = a.zorig[s];
-  const float sqrt_k2 = sqrtf(a.k2);
   int* list = sm.hitlist[warp];
   float acc[8];
 #pragma unroll
@@ -106,24 +122,29 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
   for (uint32_t base = rg.x; base < rg.y; base += CH) {
     const int cnt = (int)min((uint32_t)CH, rg.y - base);
     for (int j = threadIdx.x; j < cnt; j += NT) {
-      float4 a0, a1, a2;
-      stage_blk<EXPM>(rec, emit_gid[vals[base + j]], zsv, x0, y0, sqrt_k2, a0, a1, a2);
+      float4 a0, a1, a2, a3;
+      stage_blk<EXPM>(rec, emit_gid[vals[base + j]], zsv, x0, y0, a0, a1, a2, a3);
       sm.s0[j] = a0;
       sm.s1[j] = a1;
+      sm.sc[j] = a3;
     }
     __syncthreads();
     for (int jb = 0; jb < cnt; jb += 32) {
-      const int nh = block_hits(sm.s0, sm.s1, jb, cnt, cx, cy, lane, list);
+      const int nh = block_hits(sm.s0, sm.s1, sm.sc, jb, cnt, bx, by, a.k2, lane, list);
       for (int h = grp; h < nh; h += 4) {
         const int jj = list[h];
         const float4 g0 = sm.s0[jj], g1 = sm.s1[jj];
+        // along the row, with q = p - 3.5 the pixel offset from the block's centre
+        // column, the exponent is A + B q + C q^2
         const float dy = pyr - g0.y;
         const float u = g1.y * dy;
-        const float wy = g1.z * dy * dy;
+        const float dxc = cxb - g0.x;
+        const float A = fmaf(dxc, fmaf(g1.x, dxc, u), g1.z * dy * dy);
+        const float Bq = fmaf(2.0f * g1.x, dxc, u);
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
-          const float dx = (bx + (float)p + 0.5f) - g0.x;
-          float e = fmaf(dx, fmaf(g1.x, dx, u), wy);
+          const float q = (float)p - 3.5f;
+          float e = fmaf(fmaf(g1.x, q, Bq), q, A);
           e = fmaxf(e, kExpFloor);
           acc[p] = fmaf(g0.z, exp2_sel<EXPM>(e), acc[p]);
         }
@@ -160,7 +181,7 @@ constexpr int ACC10 = 10;
 template <int TILE, int CH>
 struct BwdSmem {
   static constexpr int NW = (TILE / 8) * (TILE / 8);
-  float4 s0[CH], s1[CH], s2[CH];
+  float4 s0[CH], s1[CH], s2[CH], sc[CH];
   uint32_t sg[CH];
   float sp[NW][6][CH];
   int hitlist[NW][32];
@@ -182,12 +203,14 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
   const int grp = lane >> 3, row = lane & 7;
   const unsigned gmask = 0xffu << (grp * 8);
   const float bx = (float)((warp % (TILE / 8)) * 8), by = (float)((warp / (TILE / 8)) * 8);
-  const float cx = bx + 4.0f, cy = by + 4.0f;
   const float pyr = by + (float)row + 0.5f;
+  const float cxb = bx + 4.0f;
   const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
   const float zsv = a.zorig[s];
-  const float sqrt_k2 = sqrtf(a.k2);
   int* list = sm.hitlist[warp];
+  const bool rb2 = (row >> 2) & 1, rb1 = (row >> 1) & 1, rb0 = row & 1;
+  const int vidx = 3 * (int)rb2 + 2 * (int)rb1 + (int)rb0;  // moment this lane holds after the butterfly
+  const bool vvalid = 2 * (int)rb1 + (int)rb0 < 3;
   float G[8];
   {
     const int py = ty * TILE + (int)by + row;
@@ -200,46 +223,54 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
     const int cnt = (int)min((uint32_t)CH, rg.y - base);
     for (int j = threadIdx.x; j < cnt; j += NT) {
       const uint32_t g = emit_gid[vals[base + j]];
-      float4 a0, a1, a2;
-      stage_blk<EXPM>(rec, g, zsv, x0, y0, sqrt_k2, a0, a1, a2);
+      float4 a0, a1, a2, a3;
+      stage_blk<EXPM>(rec, g, zsv, x0, y0, a0, a1, a2, a3);
       sm.s0[j] = a0;
       sm.s1[j] = a1;
       sm.s2[j] = a2;
+      sm.sc[j] = a3;
       sm.sg[j] = g;
     }
     for (int i = threadIdx.x; i < NW * 6 * CH; i += NT) (&sm.sp[0][0][0])[i] = 0.0f;
     __syncthreads();
     for (int jb = 0; jb < cnt; jb += 32) {
-      const int nh = block_hits(sm.s0, sm.s1, jb, cnt, cx, cy, lane, list);
+      const int nh = block_hits(sm.s0, sm.s1, sm.sc, jb, cnt, bx, by, a.k2, lane, list);
       for (int h = grp; h < nh; h += 4) {
         const int jj = list[h];
         const float4 g0 = sm.s0[jj], g1 = sm.s1[jj];
         const float dy = pyr - g0.y;
         const float u = g1.y * dy;
-        const float wy = g1.z * dy * dy;
-        float m0 = 0.f, mx = 0.f, mxx = 0.f;
+        const float dxc = cxb - g0.x;
+        const float A = fmaf(dxc, fmaf(g1.x, dxc, u), g1.z * dy * dy);
+        const float Bq = fmaf(2.0f * g1.x, dxc, u);
+        // row sums about the centre column: S0 = sum G E, S1 = sum q G E, S2 = sum q^2 G E
+        float S0 = 0.f, S1 = 0.f, S2 = 0.f;
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
-          const float dx = (bx + (float)p + 0.5f) - g0.x;
-          float e = fmaf(dx, fmaf(g1.x, dx, u), wy);
+          const float q = (float)p - 3.5f;
+          float e = fmaf(fmaf(g1.x, q, Bq), q, A);
           e = fmaxf(e, kExpFloor);
           const float gE = G[p] * exp2_sel<EXPM>(e);
-          m0 += gE;
-          const float tdx = gE * dx;
-          mx += tdx;
-          mxx = fmaf(tdx, dx, mxx);
+          S0 += gE;
+          S1 = fmaf(q, gE, S1);
+          S2 = fmaf(q * q, gE, S2);
         }
-        float v[6] = {m0, mx, m0 * dy, mxx, mx * dy, m0 * dy * dy};
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          v[k] += __shfl_xor_sync(gmask, v[k], 1);
-          v[k] += __shfl_xor_sync(gmask, v[k], 2);
-          v[k] += __shfl_xor_sync(gmask, v[k], 4);
-        }
-        if (row == 0) {
-#pragma unroll
-          for (int k = 0; k < 6; ++k) sm.sp[warp][k][jj] = v[k];
-        }
+        // this row's six moments (dx = dxc + q): sum G E {1, dx, dy, dx^2, dx dy, dy^2}
+        const float mxr = fmaf(dxc, S0, S1);
+        const float v0 = S0, v1 = mxr, v2 = S0 * dy;
+        const float v3 = fmaf(dxc, fmaf(dxc, S0, 2.0f * S1), S2), v4 = mxr * dy, v5 = v2 * dy;
+        // sum over the group's 8 rows, transposed butterfly: each level halves the
+        // values a lane carries; lane (b2 b1 b0) ends with moment 3 b2 + 2 b1 + b0
+        float k0 = rb2 ? v3 : v0, k1 = rb2 ? v4 : v1, k2 = rb2 ? v5 : v2;
+        k0 += __shfl_xor_sync(gmask, rb2 ? v0 : v3, 4);
+        k1 += __shfl_xor_sync(gmask, rb2 ? v1 : v4, 4);
+        k2 += __shfl_xor_sync(gmask, rb2 ? v2 : v5, 4);
+        float q0 = rb1 ? k2 : k0, q1 = rb1 ? 0.0f : k1;
+        q0 += __shfl_xor_sync(gmask, rb1 ? k0 : k2, 2);
+        q1 += __shfl_xor_sync(gmask, rb1 ? k1 : 0.0f, 2);
+        float r = rb0 ? q1 : q0;
+        r += __shfl_xor_sync(gmask, rb0 ? q0 : q1, 1);
+        if (vvalid) sm.sp[warp][vidx][jj] = r;
       }
       __syncwarp();
     }
@@ -255,7 +286,7 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
       }
       const float4 g0 = sm.s0[j], g1 = sm.s1[j], g2 = sm.s2[j];
       const float at = g0.z;
-      const float C00 = g1.w, C01 = g2.z, C11 = g2.w;
+      const float C00 = g1.w, C01 = g2.z, C11 = g0.w;
       // dE/dmu_2d = E C d; dE/dC00 = -E dx^2/2, dE/dC01 = -E dx dy, dE/dC11 = -E dy^2/2
       const float g_at = m[0];
       const float gmx = at * (C00 * m[1] + C01 * m[2]);
