@@ -22,6 +22,7 @@ and the FP64 oracle timed on host cores on a bounded sample.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -72,44 +73,108 @@ def log(*a):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms; only the
+    samples whose timestamps fall inside the timed window are summarised."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index):
         self.dev = device_index
         self.p = None
+        self.window = None
 
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
+        time.sleep(0.3)  # let the first samples arrive before the timed region
+
+    def mark(self, t0, t1):
+        """Wall-clock (time.time()) bounds of the timed region."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.p is None:
             return None
-        time.sleep(0.25)
+        time.sleep(0.15)
         self.p.terminate()
         try:
             out, _ = self.p.communicate(timeout=5)
         except subprocess.TimeoutExpired:
             self.p.kill()
             out, _ = self.p.communicate()
-        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({nm for r in rows for nm, v in zip(names, r[5:9]) if v.strip() == "Active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows),
-                "power_w_max": max(float(r[3]) for r in rows if r[3].strip().replace(".", "").isdigit())
-                if any(r[3].strip().replace(".", "").isdigit() for r in rows) else None}
+        return summarise_clocks(out, self.window)
+
+
+def _num(x):
+    try:
+        return float(x)
+    except ValueError:
+        return None
+
+
+def summarise_clocks(text, window=None):
+    """Median SM clock, max clock, active slowdown reasons and sample count of
+    nvidia-smi CSV rows; rows outside the (t0, t1) window are dropped unless
+    none fall inside it (then all are kept and 'in_window' says so)."""
+    import datetime
+    rows = [[c.strip() for c in r.split(",")] for r in text.strip().splitlines() if r.count(",") >= 9]
+    if not rows:
+        return None
+    inside = rows
+    if window is not None:
+        def ts(r):
+            try:
+                return datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                return None
+        inside = [r for r in rows if ts(r) is not None and window[0] - 0.05 <= ts(r) <= window[1] + 0.05]
+    in_window = bool(inside) and window is not None
+    use = inside if inside else rows
+    sm = [v for v in (_num(r[2]) for r in use) if v is not None]
+    mx = [v for v in (_num(r[3]) for r in rows) if v is not None]
+    pw = [v for v in (_num(r[4]) for r in use) if v is not None]
+    names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    reasons = sorted({nm for r in use for nm, v in zip(names, r[6:10]) if v == "Active"})
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(use), "in_window": in_window,
+            "power_w_max": max(pw) if pw else None}
+
+
+# Per-launch DRAM traffic of the rasterisers, from a full-size ncu capture of
+# the default configuration (single-pass dram__bytes metrics), keyed by a hash
+# of the kernels' sources so that a changed kernel reports null.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_raster_traffic_microscopy_fit_step.md")
+KERNEL_SOURCES = ("paper_2603_20611_b300/csrc/raster.cu", "paper_2603_20611_b300/csrc/gp_common.cuh",
+                  "paper_2603_20611_b300/csrc/slice.cuh")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """(bytes per launch, note) for `kernel` ('k_raster_fwd_blk' / 'k_raster_bwd_blk')."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None, "no capture recorded"
+    want = kernel_source_hash()
+    with open(TRAFFIC_FILE) as f:
+        for line in f:
+            c = [x.strip() for x in line.strip().strip("|").split("|")]
+            if len(c) >= 5 and c[0] == kernel:
+                if c[1] != want:
+                    return None, "stale: the kernel sources changed since the capture"
+                return float(c[2]) + float(c[3]), ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                                                   "full-size capture of the default configuration")
+    return None, "kernel not in the capture"
 
 
 def measured_peaks():
@@ -134,7 +199,8 @@ def make_workload(B, synth, torch, dev, ctx):
 
 
 def step_batches(synth, rank, count):
-    return [synth.slice_batch(3000 + 7919 * rank + k, DEPTH, DEPTH, S) for k in range(count)]
+    from paper_2603_20611_b300.replicas import batch_seed
+    return [synth.slice_batch(batch_seed(rank, k), DEPTH, DEPTH, S) for k in range(count)]
 
 
 # ------------------------------------------------------------------ oracle arm
@@ -219,6 +285,7 @@ def run_native(args, rank, world):
     import torch
     from paper_2603_20611_b300 import binding as B
     from paper_2603_20611_b300 import synth
+    from paper_2603_20611_b300.replicas import reduce_timing
     dev_index = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev_index)
     dev = f"cuda:{dev_index}"
@@ -272,6 +339,7 @@ def run_native(args, rank, world):
     clocks.start()
     evs = []
     wall0 = time.perf_counter()
+    tw0 = time.time()
     for k in range(args.warmup, args.warmup + args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -281,6 +349,7 @@ def run_native(args, rank, world):
         evs.append((e0, e1))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    clocks.mark(tw0, time.time())
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -291,14 +360,7 @@ def run_native(args, rank, world):
     t_total = sum(step_ms) * 1e-3
     ev_steps = evals[args.warmup:]
     my_evals = 2.0 * sum(ev_steps)
-    if dist:
-        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([my_evals], device=dev, dtype=torch.float64)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        t_total, tot_evals = float(t.item()), float(e.item())
-    else:
-        tot_evals = my_evals
+    t_total, tot_evals = reduce_timing(t_total, my_evals, device=dev if dist else None)
     value = tot_evals / t_total
     pairs, issued = ctx.last_counts()
 
@@ -310,6 +372,10 @@ def run_native(args, rank, world):
     achieved = alg_ops_per_launch / avg_launch_s / 1e12
     peak = fp32_peak / 1e12
     nominal = 148 * 128 * 2.032e9 / 1e12
+    default_cfg = (args.exp == "poly" and not args.det and args.tile == 16 and args.fwd_px == 0
+                   and args.bwd_px == 0 and args.case == "microscopy")
+    traffic, traffic_note = recorded_traffic(f"k_raster_{dom}_blk") if default_cfg else \
+        (None, "recorded for the default configuration only")
 
     # end to end through host buffers: parameters and the batch's target slices
     # in (pinned host -> device), loss and gradients out (device -> pinned host)
@@ -358,7 +424,8 @@ def run_native(args, rank, world):
                 "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[2]},
                 "roofline": {"bound": "alu", "kernel": f"k_raster_{dom}", "achieved": achieved, "peak": peak,
                              "unit": "Tinst/s (FP32+INT lane instructions)", "frac": achieved / peak,
-                             "traffic": None, "peak_kind": "measured FMA probe, burst, same run",
+                             "traffic": traffic, "traffic_note": traffic_note,
+                             "peak_kind": "measured FMA probe, burst, same run",
                              "nominal_peak_2032mhz": nominal, "ops_per_eval": OPS_PER_EVAL[dom]},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -550,7 +617,7 @@ def run_serving(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--exp", default="poly", choices=["poly", "hw"])
