@@ -40,6 +40,18 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+class _View(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3)]
+
+
+def _view(view):
+    """(R [3, 3], t [3]) -> the C view struct (kept alive by the caller)."""
+    R, t = view
+    R = _f64(R, (9,))
+    t = _f64(t, (3,))
+    return _View((ctypes.c_double * 9)(*R), (ctypes.c_double * 3)(*t))
+
+
 class _Set(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64),
                 ("mu", ctypes.c_void_p),
@@ -59,6 +71,14 @@ def _load():
         I64 = ctypes.c_int64
         D = ctypes.c_double
         SP = ctypes.POINTER(_Set)
+        VP = ctypes.POINTER(_View)
+        lib.orc_render_view.argtypes = [SP, VP, I, P, I, I, D, P]
+        lib.orc_render_points_view.argtypes = [SP, VP, I, P, D, I64, P, P, P, P]
+        lib.orc_render_backward_view.argtypes = [SP, VP, I, P, I, I, D, P, P, P, P, P]
+        lib.orc_count_evals_view.argtypes = [SP, VP, I, P, I, I, D, D]
+        lib.orc_count_evals_view.restype = I64
+        for f in ("orc_render_view", "orc_render_points_view", "orc_render_backward_view"):
+            getattr(lib, f).restype = I
         lib.orc_render.argtypes = [SP, I, P, I, I, D, I, P]
         lib.orc_render_points.argtypes = [SP, I, P, D, I, I64, P, P, P, P]
         lib.orc_render_backward.argtypes = [SP, I, P, I, I, D, I, P, P, P, P, P]
@@ -112,18 +132,25 @@ def num_threads() -> int:
     return int(_load().orc_num_threads())
 
 
-def render(mu, scale, quat, alpha, z, H, W, sigma_z, axis=2, scale_mod=1.0):
-    """Slice stack [S, H, W] by brute force over every Gaussian (Eq. 6-10)."""
+def render(mu, scale, quat, alpha, z, H, W, sigma_z, axis=2, scale_mod=1.0, view=None):
+    """Slice stack [S, H, W] by brute force over every Gaussian (Eq. 6-10).
+    view = (R [3, 3], t [3]) selects a general slice orientation (axis is then
+    ignored): camera coordinates x_c = R x + t, slice s is the plane z_c = z[s]."""
     g = _GaussianSet(mu, scale, quat, alpha, scale_mod)
     z = _f64(z, (-1,))
     out = np.zeros((z.shape[0], H, W), np.float64)
+    if view is not None:
+        v = _view(view)
+        _check(_load().orc_render_view(ctypes.byref(g.c), ctypes.byref(v), z.shape[0], _ptr(z), H, W,
+                                       float(sigma_z), _ptr(out)), "orc_render_view")
+        return out
     _check(_load().orc_render(ctypes.byref(g.c), z.shape[0], _ptr(z), H, W,
                               float(sigma_z), axis, _ptr(out)), "orc_render")
     return out
 
 
 def render_points(mu, scale, quat, alpha, z, sigma_z, pt_slice, pt_x, pt_y, axis=2,
-                  scale_mod=1.0):
+                  scale_mod=1.0, view=None):
     """Eq. 10 at sample points (slice index, camera x, camera y)."""
     g = _GaussianSet(mu, scale, quat, alpha, scale_mod)
     z = _f64(z, (-1,))
@@ -131,19 +158,31 @@ def render_points(mu, scale, quat, alpha, z, sigma_z, pt_slice, pt_x, pt_y, axis
     px = _f64(pt_x, (-1,))
     py = _f64(pt_y, (-1,))
     out = np.zeros(ps.shape[0], np.float64)
+    if view is not None:
+        v = _view(view)
+        _check(_load().orc_render_points_view(ctypes.byref(g.c), ctypes.byref(v), z.shape[0], _ptr(z),
+                                              float(sigma_z), ps.shape[0], _ptr(ps), _ptr(px), _ptr(py),
+                                              _ptr(out)), "orc_render_points_view")
+        return out
     _check(_load().orc_render_points(ctypes.byref(g.c), z.shape[0], _ptr(z), float(sigma_z),
                                      axis, ps.shape[0], _ptr(ps), _ptr(px), _ptr(py),
                                      _ptr(out)), "orc_render_points")
     return out
 
 
-def render_backward(mu, scale, quat, alpha, z, H, W, sigma_z, dL_dI, axis=2, scale_mod=1.0):
+def render_backward(mu, scale, quat, alpha, z, H, W, sigma_z, dL_dI, axis=2, scale_mod=1.0, view=None):
     """(dL/dmu [n,3], dL/dscale [n,3], dL/dquat [n,4], dL/dalpha [n]) for a given dL/dI."""
     g = _GaussianSet(mu, scale, quat, alpha, scale_mod)
     z = _f64(z, (-1,))
     G = _f64(dL_dI, (z.shape[0], H, W))
     n = g.n
     dmu = np.zeros((n, 3)); ds = np.zeros((n, 3)); dq = np.zeros((n, 4)); da = np.zeros(n)
+    if view is not None:
+        v = _view(view)
+        _check(_load().orc_render_backward_view(ctypes.byref(g.c), ctypes.byref(v), z.shape[0], _ptr(z), H,
+                                                W, float(sigma_z), _ptr(G), _ptr(dmu), _ptr(ds),
+                                                _ptr(dq), _ptr(da)), "orc_render_backward_view")
+        return dmu, ds, dq, da
     _check(_load().orc_render_backward(ctypes.byref(g.c), z.shape[0], _ptr(z), H, W,
                                        float(sigma_z), axis, _ptr(G), _ptr(dmu), _ptr(ds),
                                        _ptr(dq), _ptr(da)), "orc_render_backward")
@@ -178,10 +217,17 @@ def voxelize_backward(mu, scale, quat, alpha, X, Y, Z, dL_dV, scale_mod=1.0):
     return dmu, ds, dq, da
 
 
-def count_evals(mu, scale, quat, alpha, z, H, W, sigma_z, axis=2, eps=1e-6, scale_mod=1.0):
+def count_evals(mu, scale, quat, alpha, z, H, W, sigma_z, axis=2, eps=1e-6, scale_mod=1.0, view=None):
     """Algorithmic evaluations of a render with culling bound eps (see oracle.h)."""
     g = _GaussianSet(mu, scale, quat, alpha, scale_mod)
     z = _f64(z, (-1,))
+    if view is not None:
+        v = _view(view)
+        r = _load().orc_count_evals_view(ctypes.byref(g.c), ctypes.byref(v), z.shape[0], _ptr(z), H, W,
+                                         float(sigma_z), float(eps))
+        if r < 0:
+            raise ValueError("orc_count_evals_view rejected its arguments")
+        return int(r)
     r = _load().orc_count_evals(ctypes.byref(g.c), z.shape[0], _ptr(z), H, W, float(sigma_z), axis,
                                 float(eps))
     if r < 0:

@@ -124,6 +124,35 @@ static void perm_matrix(const int perm[3], double Rc[3][3]) {
   for (int j = 0; j < 3; ++j) Rc[j][perm[j]] = 1.0;
 }
 
+/* View matrix [R_c | t] of a general slice orientation (Sec. S1): R_c must be
+ * finite and orthonormal to within 1e-3 (the focal plane is then a true plane
+ * with unit pixel spacing), t finite.  Returns -1 otherwise. */
+static int view_matrix(const orc_view* v, double Rc[3][3], double tc[3]) {
+  if (!v) return -1;
+  for (int k = 0; k < 9; ++k)
+    if (!isfinite(v->R[k])) return -1;
+  for (int k = 0; k < 3; ++k)
+    if (!isfinite(v->t[k])) return -1;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) Rc[r][c] = v->R[3 * r + c];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double d = Rc[r][0] * Rc[c][0] + Rc[r][1] * Rc[c][1] + Rc[r][2] * Rc[c][2];
+      if (fabs(d - (r == c ? 1.0 : 0.0)) > 1e-3) return -1;
+    }
+  for (int k = 0; k < 3; ++k) tc[k] = v->t[k];
+  return 0;
+}
+
+/* The view of an axis-aligned slice: R_c the permutation of axis, t = 0. */
+static int axis_view(int axis, double Rc[3][3], double tc[3]) {
+  int perm[3];
+  if (axis_perm(axis, perm)) return -1;
+  perm_matrix(perm, Rc);
+  tc[0] = tc[1] = tc[2] = 0.0;
+  return 0;
+}
+
 /* World covariance of Gaussian i: Sigma = M M^T with M = R S, S = diag(mod s). */
 typedef struct {
   double R[3][3], M[3][3], Sig[3][3], qn[4], qnorm, Sd[3];
@@ -158,9 +187,11 @@ typedef struct {
 } slice_proj;
 
 static void project(const orc_set* g, int64_t i, const world_cov* w, const double Rc[3][3],
-                    double zs, double sigma_z, slice_proj* p) {
-  /* camera transform (Sec. S1): mu_c = R_c mu + t, t = -z_s e3 */
+                    const double tc[3], double zs, double sigma_z, slice_proj* p) {
+  /* camera transform (Sec. S1): mu_c = R_c mu + t, with the view's t shifted by
+   * -z_s e3 so that the plane of slice s is z_c = 0 */
   matvec3(Rc, g->mu + 3 * i, p->muc);
+  for (int k = 0; k < 3; ++k) p->muc[k] += tc[k];
   p->muc[2] -= zs;
   double Rct[3][3], tmp[3][3];
   transpose3(Rc, Rct);
@@ -208,13 +239,9 @@ static int check_set(const orc_set* g) {
 
 /* ---------------------------------------------------------------- forward */
 
-int orc_render(const orc_set* g, int S, const double* z, int H, int W, double sigma_z,
-               int axis, double* out) {
-  int perm[3];
-  if (check_set(g) || S < 0 || H < 0 || W < 0 || !(sigma_z > 0) || axis_perm(axis, perm))
-    return -1;
-  double Rc[3][3];
-  perm_matrix(perm, Rc);
+static int render_rc(const orc_set* g, int S, const double* z, int H, int W, double sigma_z,
+                     const double Rc[3][3], const double tc[3], double* out) {
+  if (check_set(g) || S < 0 || H < 0 || W < 0 || !(sigma_z > 0)) return -1;
   int64_t n = g->n;
   slice_proj* P = (slice_proj*)malloc(sizeof(slice_proj) * (size_t)(n > 0 ? n : 1));
   world_cov* Wc = (world_cov*)malloc(sizeof(world_cov) * (size_t)(n > 0 ? n : 1));
@@ -223,7 +250,7 @@ int orc_render(const orc_set* g, int S, const double* z, int H, int W, double si
   for (int64_t i = 0; i < n; ++i) world_covariance(g, i, &Wc[i]);
   for (int s = 0; s < S; ++s) {
 #pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < n; ++i) project(g, i, &Wc[i], Rc, z[s], sigma_z, &P[i]);
+    for (int64_t i = 0; i < n; ++i) project(g, i, &Wc[i], Rc, tc, z[s], sigma_z, &P[i]);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int iy = 0; iy < H; ++iy)
       for (int ix = 0; ix < W; ++ix) {
@@ -237,15 +264,13 @@ int orc_render(const orc_set* g, int S, const double* z, int H, int W, double si
   return 0;
 }
 
-int orc_render_points(const orc_set* g, int S, const double* z, double sigma_z, int axis,
-                      int64_t npts, const int* pt_slice, const double* pt_x,
-                      const double* pt_y, double* out) {
-  int perm[3];
-  if (check_set(g) || S < 0 || npts < 0 || !(sigma_z > 0) || axis_perm(axis, perm)) return -1;
+static int render_points_rc(const orc_set* g, int S, const double* z, double sigma_z,
+                            const double Rc[3][3], const double tc[3], int64_t npts,
+                            const int* pt_slice, const double* pt_x, const double* pt_y,
+                            double* out) {
+  if (check_set(g) || S < 0 || npts < 0 || !(sigma_z > 0)) return -1;
   for (int64_t k = 0; k < npts; ++k)
     if (pt_slice[k] < 0 || pt_slice[k] >= S) return -1;
-  double Rc[3][3];
-  perm_matrix(perm, Rc);
   int64_t n = g->n;
   slice_proj* P = (slice_proj*)malloc(sizeof(slice_proj) * (size_t)(n > 0 ? n : 1));
   world_cov* Wc = (world_cov*)malloc(sizeof(world_cov) * (size_t)(n > 0 ? n : 1));
@@ -257,7 +282,7 @@ int orc_render_points(const orc_set* g, int S, const double* z, double sigma_z, 
     for (int64_t k = 0; k < npts; ++k) used |= (pt_slice[k] == s);
     if (!used) continue;
 #pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < n; ++i) project(g, i, &Wc[i], Rc, z[s], sigma_z, &P[i]);
+    for (int64_t i = 0; i < n; ++i) project(g, i, &Wc[i], Rc, tc, z[s], sigma_z, &P[i]);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t k = 0; k < npts; ++k) {
       if (pt_slice[k] != s) continue;
@@ -399,14 +424,11 @@ static void back_project(const orc_set* g, int64_t i, const double Rc[3][3],
     for (int c = 0; c < 3; ++c) gSig[r][c] += gW[r][c];
 }
 
-int orc_render_backward(const orc_set* g, int S, const double* z, int H, int W,
-                        double sigma_z, int axis, const double* dL_dI, double* d_mu,
-                        double* d_scale, double* d_quat, double* d_alpha) {
-  int perm[3];
-  if (check_set(g) || S < 0 || H < 0 || W < 0 || !(sigma_z > 0) || axis_perm(axis, perm))
-    return -1;
-  double Rc[3][3];
-  perm_matrix(perm, Rc);
+static int render_backward_rc(const orc_set* g, int S, const double* z, int H, int W,
+                              double sigma_z, const double Rc[3][3], const double tc[3],
+                              const double* dL_dI, double* d_mu, double* d_scale,
+                              double* d_quat, double* d_alpha) {
+  if (check_set(g) || S < 0 || H < 0 || W < 0 || !(sigma_z > 0)) return -1;
   int64_t n = g->n;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t i = 0; i < n; ++i) {
@@ -417,7 +439,7 @@ int orc_render_backward(const orc_set* g, int S, const double* z, int H, int W,
     memset(gSig, 0, sizeof(gSig));
     for (int s = 0; s < S; ++s) {
       slice_proj p;
-      project(g, i, &w, Rc, z[s], sigma_z, &p);
+      project(g, i, &w, Rc, tc, z[s], sigma_z, &p);
       /* Eq. 10 per pixel: I += a~ E, E = exp(-1/2 d^T C d), d = p - mu_2d */
       double g_at = 0, g_mu2[2] = {0, 0}, gC[2][2] = {{0, 0}, {0, 0}};
       const double* G = dL_dI + (int64_t)s * H * W;
@@ -570,14 +592,11 @@ int orc_voxelize_backward(const orc_set* g, int X, int Y, int Z, const double* d
 
 /* ------------------------------------------------------------ work count */
 
-int64_t orc_count_evals(const orc_set* g, int S, const double* z, int H, int W, double sigma_z,
-                        int axis, double eps) {
-  int perm[3];
-  if (check_set(g) || S < 0 || H < 0 || W < 0 || !(sigma_z > 0) || axis_perm(axis, perm) ||
-      !(eps > 0 && eps < 1))
+static int64_t count_evals_rc(const orc_set* g, int S, const double* z, int H, int W,
+                              double sigma_z, const double Rc[3][3], const double tc[3],
+                              double eps) {
+  if (check_set(g) || S < 0 || H < 0 || W < 0 || !(sigma_z > 0) || !(eps > 0 && eps < 1))
     return -1;
-  double Rc[3][3];
-  perm_matrix(perm, Rc);
   const double k2 = 2.0 * log(1.0 / eps);
   int64_t total = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : total)
@@ -586,7 +605,7 @@ int64_t orc_count_evals(const orc_set* g, int S, const double* z, int H, int W, 
     world_covariance(g, i, &w);
     for (int s = 0; s < S; ++s) {
       slice_proj p;
-      project(g, i, &w, Rc, z[s], sigma_z, &p);
+      project(g, i, &w, Rc, tc, z[s], sigma_z, &p);
       if (!(p.op >= eps)) continue;
       /* per row: C00 dx^2 + 2 C01 dx dy + C11 dy^2 <= k2 is an interval in dx */
       for (int iy = 0; iy < H; ++iy) {
@@ -604,6 +623,70 @@ int64_t orc_count_evals(const orc_set* g, int S, const double* z, int H, int W, 
     }
   }
   return total;
+}
+
+/* ------------------------------------------- axis-aligned and general views */
+
+int orc_render(const orc_set* g, int S, const double* z, int H, int W, double sigma_z,
+               int axis, double* out) {
+  double Rc[3][3], tc[3];
+  if (axis_view(axis, Rc, tc)) return -1;
+  return render_rc(g, S, z, H, W, sigma_z, Rc, tc, out);
+}
+
+int orc_render_view(const orc_set* g, const orc_view* view, int S, const double* z, int H,
+                    int W, double sigma_z, double* out) {
+  double Rc[3][3], tc[3];
+  if (view_matrix(view, Rc, tc)) return -1;
+  return render_rc(g, S, z, H, W, sigma_z, Rc, tc, out);
+}
+
+int orc_render_points(const orc_set* g, int S, const double* z, double sigma_z, int axis,
+                      int64_t npts, const int* pt_slice, const double* pt_x,
+                      const double* pt_y, double* out) {
+  double Rc[3][3], tc[3];
+  if (axis_view(axis, Rc, tc)) return -1;
+  return render_points_rc(g, S, z, sigma_z, Rc, tc, npts, pt_slice, pt_x, pt_y, out);
+}
+
+int orc_render_points_view(const orc_set* g, const orc_view* view, int S, const double* z,
+                           double sigma_z, int64_t npts, const int* pt_slice,
+                           const double* pt_x, const double* pt_y, double* out) {
+  double Rc[3][3], tc[3];
+  if (view_matrix(view, Rc, tc)) return -1;
+  return render_points_rc(g, S, z, sigma_z, Rc, tc, npts, pt_slice, pt_x, pt_y, out);
+}
+
+int orc_render_backward(const orc_set* g, int S, const double* z, int H, int W,
+                        double sigma_z, int axis, const double* dL_dI, double* d_mu,
+                        double* d_scale, double* d_quat, double* d_alpha) {
+  double Rc[3][3], tc[3];
+  if (axis_view(axis, Rc, tc)) return -1;
+  return render_backward_rc(g, S, z, H, W, sigma_z, Rc, tc, dL_dI, d_mu, d_scale, d_quat,
+                            d_alpha);
+}
+
+int orc_render_backward_view(const orc_set* g, const orc_view* view, int S, const double* z,
+                             int H, int W, double sigma_z, const double* dL_dI, double* d_mu,
+                             double* d_scale, double* d_quat, double* d_alpha) {
+  double Rc[3][3], tc[3];
+  if (view_matrix(view, Rc, tc)) return -1;
+  return render_backward_rc(g, S, z, H, W, sigma_z, Rc, tc, dL_dI, d_mu, d_scale, d_quat,
+                            d_alpha);
+}
+
+int64_t orc_count_evals(const orc_set* g, int S, const double* z, int H, int W, double sigma_z,
+                        int axis, double eps) {
+  double Rc[3][3], tc[3];
+  if (axis_view(axis, Rc, tc)) return -1;
+  return count_evals_rc(g, S, z, H, W, sigma_z, Rc, tc, eps);
+}
+
+int64_t orc_count_evals_view(const orc_set* g, const orc_view* view, int S, const double* z,
+                             int H, int W, double sigma_z, double eps) {
+  double Rc[3][3], tc[3];
+  if (view_matrix(view, Rc, tc)) return -1;
+  return count_evals_rc(g, S, z, H, W, sigma_z, Rc, tc, eps);
 }
 
 /* ------------------------------------------------------------------- loss */
