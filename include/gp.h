@@ -26,7 +26,8 @@
  *     S = diag(scale_mod * s) (Sec. S1).
  *   - Slice axis `axis` = 2 (planes z = z_s; image columns x, rows y),
  *     1 (planes y = z_s; columns x, rows z) or 0 (planes x = z_s; columns y,
- *     rows z).  Pixel (ix, iy) sits at (ix + 0.5, iy + 0.5) in the plane;
+ *     rows z); any other orientation through gp_view (the *_view calls).
+ *     Pixel (ix, iy) sits at (ix + 0.5, iy + 0.5) in the plane;
  *     voxel (ix, iy, iz) at (ix + .5, iy + .5, iz + .5).
  *   - Images are [S][H][W] fp32 row-major, volumes [Z][Y][X] fp32.
  *   - Every call is asynchronous on the caller's CUDA stream (`stream` is a
@@ -140,6 +141,35 @@ GP_API gp_status gp_render_backward(gp_ctx* ctx, const gp_set* set, const float*
                              float* d_mu, float* d_scale, float* d_quat, float* d_alpha,
                              void* stream);
 
+/* ------------------------------------------------------- oblique slices
+ * A general slice orientation: the view matrix [R_c | t] of Sec. S1, which maps
+ * a world point x to camera coordinates x_c = R_c x + t.  Slice s of a stack is
+ * the plane z_c = z[s]; pixel (ix, iy) sits at (x_c, y_c) = (ix + .5, iy + .5).
+ * R (row-major: row j is camera axis j in world coordinates) must be finite and
+ * orthonormal to within 1e-3 (checked: GP_ERR_ARG otherwise), t finite.  All
+ * planes of one call share R_c, so Sigma_2d stays slice-invariant and the
+ * kernels are the axis-aligned ones; a different orientation is another call.
+ * The axis-aligned calls are the special case R_c = the axis permutation
+ * (gp_view_from_axis), t = 0, and give bitwise the same results as the view
+ * calls with that view. */
+typedef struct {
+  float R[9];
+  float t[3];
+} gp_view;
+
+/* Fills *view with the permutation view of a slice axis (0, 1, 2); GP_ERR_ARG otherwise. */
+GP_API gp_status gp_view_from_axis(int axis, gp_view* view);
+
+/* gp_render_slices / gp_render_backward / gp_count_evals for a general view
+ * (HOST gp_view; NULL or invalid: GP_ERR_ARG).  Everything else as there. */
+GP_API gp_status gp_render_slices_view(gp_ctx* ctx, const gp_set* set, const gp_view* view, const float* z,
+                                       int S, int H, int W, float sigma_z, float* out, void* stream);
+GP_API gp_status gp_render_backward_view(gp_ctx* ctx, const gp_set* set, const gp_view* view, const float* z,
+                                         int S, int H, int W, float sigma_z, const float* dL_dI, float* d_mu,
+                                         float* d_scale, float* d_quat, float* d_alpha, void* stream);
+GP_API gp_status gp_count_evals_view(gp_ctx* ctx, const gp_set* set, const gp_view* view, const float* z, int S,
+                                     int H, int W, float sigma_z, int64_t* evals);
+
 /* Mean squared error of a rendered stack against target slices (the loss the
  * operator is driven with here; the paper's L1 + D-SSIM of Eq. 11 is not
  * built).  I: [S][H][W] DEVICE.  T: DEVICE target stack of at least
@@ -236,6 +266,7 @@ typedef struct {
   const float* dL_dI;
   float *d_mu, *d_scale, *d_quat, *d_alpha;
   float* loss;
+  const gp_view* view;  /* HOST, copied at plan time; NULL = the view of `axis` */
 } gp_batch_item;
 
 typedef struct gp_plan gp_plan;
@@ -262,7 +293,7 @@ GP_API gp_status gp_batch_destroy(gp_plan* plan);
  * device memory fits the budget (free HBM minus a reserve, or a fixed budget),
  * so requests that arrive while others run overlap with them on the GPU.  A
  * worker taking a slice/stack request also takes every pending request for the
- * same set, axis, image size and sigma_z (up to max_batch_slices planes) and
+ * same set, view, image size and sigma_z (up to max_batch_slices planes) and
  * renders them in one call; results are bitwise the same alone and in a batch.
  * Outputs are caller-owned device buffers that must stay valid until the
  * request completes.  submit / poll / stats may be called from any thread. */
@@ -286,6 +317,7 @@ typedef struct {
   int axis;
   int X, Y, Z;      /* voxelize */
   float* out;       /* DEVICE [S][H][W] or [Z][Y][X] */
+  const gp_view* view;  /* HOST, copied at submit; NULL = the view of `axis` (slice / stack) */
 } gp_request;
 
 typedef struct {

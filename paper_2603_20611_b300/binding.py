@@ -35,7 +35,8 @@ EXPORTS = (
     "gp_launch_count", "gp_fma_probe_threads", "gp_fma_probe", "gp_mse_grad_noalloc",
     "gp_batch_plan", "gp_batch_run", "gp_batch_wait", "gp_batch_info", "gp_batch_destroy",
     "gp_serve_open", "gp_serve_load_set", "gp_serve_submit", "gp_serve_poll", "gp_serve_stats_get",
-    "gp_serve_close",
+    "gp_serve_close", "gp_view_from_axis", "gp_render_slices_view", "gp_render_backward_view",
+    "gp_count_evals_view",
 )
 GP_REQ_SLICE, GP_REQ_STACK, GP_REQ_VOXELIZE = 0, 1, 2
 GP_BATCH_AUTOTUNE = 1
@@ -60,12 +61,27 @@ class gp_set(ctypes.Structure):
                 ("alpha", ctypes.c_void_p), ("n", ctypes.c_int64), ("scale_mod", ctypes.c_float)]
 
 
+class gp_view(ctypes.Structure):
+    """Slice orientation [R_c | t]: camera coordinates x_c = R x + t (R row-major)."""
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3)]
+
+
+def make_view(view):
+    """A gp_view from a gp_view or an (R [3, 3], t [3]) pair."""
+    if isinstance(view, gp_view):
+        return view
+    R, t = view
+    R = np.asarray(R, np.float32).reshape(9)
+    t = np.asarray(t, np.float32).reshape(3)
+    return gp_view((ctypes.c_float * 9)(*R.tolist()), (ctypes.c_float * 3)(*t.tolist()))
+
+
 class gp_batch_item(ctypes.Structure):
     _fields_ = [("set", gp_set), ("z", ctypes.c_void_p), ("S", ctypes.c_int), ("H", ctypes.c_int),
                 ("W", ctypes.c_int), ("sigma_z", ctypes.c_float), ("axis", ctypes.c_int),
                 ("out", ctypes.c_void_p), ("target", ctypes.c_void_p), ("dL_dI", ctypes.c_void_p),
                 ("d_mu", ctypes.c_void_p), ("d_scale", ctypes.c_void_p), ("d_quat", ctypes.c_void_p),
-                ("d_alpha", ctypes.c_void_p), ("loss", ctypes.c_void_p)]
+                ("d_alpha", ctypes.c_void_p), ("loss", ctypes.c_void_p), ("view", ctypes.c_void_p)]
 
 
 class gp_serve_cfg(ctypes.Structure):
@@ -76,7 +92,8 @@ class gp_serve_cfg(ctypes.Structure):
 class gp_request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("set_id", ctypes.c_int), ("z", ctypes.c_void_p), ("S", ctypes.c_int),
                 ("H", ctypes.c_int), ("W", ctypes.c_int), ("sigma_z", ctypes.c_float), ("axis", ctypes.c_int),
-                ("X", ctypes.c_int), ("Y", ctypes.c_int), ("Z", ctypes.c_int), ("out", ctypes.c_void_p)]
+                ("X", ctypes.c_int), ("Y", ctypes.c_int), ("Z", ctypes.c_int), ("out", ctypes.c_void_p),
+                ("view", ctypes.c_void_p)]
 
 
 class gp_result(ctypes.Structure):
@@ -129,6 +146,10 @@ def _load():
         "gp_serve_poll": [P, ctypes.c_uint64, I, ctypes.POINTER(gp_result)],
         "gp_serve_stats_get": [P, ctypes.POINTER(gp_serve_stats)],
         "gp_serve_close": [P],
+        "gp_view_from_axis": [I, ctypes.POINTER(gp_view)],
+        "gp_render_slices_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, P, P],
+        "gp_render_backward_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, P, P, P, P, P, P],
+        "gp_count_evals_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, ctypes.POINTER(I64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -260,25 +281,46 @@ def _grads_like(gs, grads):
     return grads
 
 
-def gp_render_slices(ctx, gs, z, H, W, sigma_z, axis=2, out=None, stream=None):
+def view_from_axis(axis):
+    v = gp_view()
+    st = lib.gp_view_from_axis(int(axis), ctypes.byref(v))
+    if st != GP_OK:
+        raise GPError(st, "gp_view_from_axis")
+    return v
+
+
+def gp_render_slices(ctx, gs, z, H, W, sigma_z, axis=2, out=None, stream=None, view=None):
+    """view (a gp_view or (R, t)) selects a general slice orientation; axis is then ignored."""
     z = _host_f32(z)
     S = z.shape[0]
     if out is None:
         out = torch.empty(S, H, W, device=gs.alpha.device)
-    st = lib.gp_render_slices(ctx.h, ctypes.byref(gs.c()), z.ctypes.data_as(ctypes.c_void_p), S, H, W,
-                              float(sigma_z), axis, _dev(out, "out", shape=(S, H, W)), _stream(stream))
+    zp = z.ctypes.data_as(ctypes.c_void_p)
+    o = _dev(out, "out", shape=(S, H, W))
+    if view is not None:
+        v = make_view(view)
+        st = lib.gp_render_slices_view(ctx.h, ctypes.byref(gs.c()), ctypes.byref(v), zp, S, H, W, float(sigma_z),
+                                       o, _stream(stream))
+    else:
+        st = lib.gp_render_slices(ctx.h, ctypes.byref(gs.c()), zp, S, H, W, float(sigma_z), axis, o,
+                                  _stream(stream))
     ctx.check(st, "gp_render_slices")
     return out
 
 
-def gp_render_backward(ctx, gs, z, H, W, sigma_z, dL_dI, axis=2, grads=None, stream=None):
+def gp_render_backward(ctx, gs, z, H, W, sigma_z, dL_dI, axis=2, grads=None, stream=None, view=None):
     z = _host_f32(z)
     S = z.shape[0]
     d_mu, d_s, d_q, d_a = _grads_like(gs, grads)
-    st = lib.gp_render_backward(ctx.h, ctypes.byref(gs.c()), z.ctypes.data_as(ctypes.c_void_p), S, H, W,
-                                float(sigma_z), axis, _dev(dL_dI, "dL_dI", shape=(S, H, W)),
-                                _dev(d_mu, "d_mu"), _dev(d_s, "d_scale"), _dev(d_q, "d_quat"),
-                                _dev(d_a, "d_alpha"), _stream(stream))
+    zp = z.ctypes.data_as(ctypes.c_void_p)
+    gargs = (_dev(dL_dI, "dL_dI", shape=(S, H, W)), _dev(d_mu, "d_mu"), _dev(d_s, "d_scale"),
+             _dev(d_q, "d_quat"), _dev(d_a, "d_alpha"), _stream(stream))
+    if view is not None:
+        v = make_view(view)
+        st = lib.gp_render_backward_view(ctx.h, ctypes.byref(gs.c()), ctypes.byref(v), zp, S, H, W,
+                                         float(sigma_z), *gargs)
+    else:
+        st = lib.gp_render_backward(ctx.h, ctypes.byref(gs.c()), zp, S, H, W, float(sigma_z), axis, *gargs)
     ctx.check(st, "gp_render_backward")
     return d_mu, d_s, d_q, d_a
 
@@ -347,6 +389,10 @@ class BatchPlan:
             c.S, c.H, c.W = S, H, W
             c.sigma_z = float(it["sigma_z"])
             c.axis = int(it.get("axis", 2))
+            if it.get("view") is not None:
+                v = make_view(it["view"])
+                self._keep.append(v)
+                c.view = ctypes.addressof(v)
             for key in ("out", "target", "dL_dI"):
                 t = it.get(key)
                 setattr(c, key, None if t is None else _dev(t, key, shape=(S, H, W)).value)
@@ -410,7 +456,7 @@ class Server:
             raise GPError(st, "gp_serve_load_set")
         return sid.value
 
-    def submit(self, kind, set_id, out, z=None, H=0, W=0, sigma_z=1.0, axis=2, X=0, Y=0, Z=0):
+    def submit(self, kind, set_id, out, z=None, H=0, W=0, sigma_z=1.0, axis=2, X=0, Y=0, Z=0, view=None):
         r = gp_request()
         r.kind, r.set_id = int(kind), int(set_id)
         zz = None
@@ -420,6 +466,10 @@ class Server:
         r.H, r.W, r.sigma_z, r.axis = int(H), int(W), float(sigma_z), int(axis)
         r.X, r.Y, r.Z = int(X), int(Y), int(Z)
         r.out = _dev(out, "out").value
+        v = None
+        if view is not None:
+            v = make_view(view)
+            r.view = ctypes.addressof(v)
         t = ctypes.c_uint64()
         st = lib.gp_serve_submit(self.h, ctypes.byref(r), ctypes.byref(t))
         if st != GP_OK:
@@ -474,11 +524,17 @@ def gp_voxelize_backward(ctx, gs, X, Y, Z, dL_dV, grads=None, stream=None):
     return d_mu, d_s, d_q, d_a
 
 
-def gp_count_evals(ctx, gs, z, H, W, sigma_z, axis=2):
+def gp_count_evals(ctx, gs, z, H, W, sigma_z, axis=2, view=None):
     z = _host_f32(z)
     out = ctypes.c_int64()
-    st = lib.gp_count_evals(ctx.h, ctypes.byref(gs.c()), z.ctypes.data_as(ctypes.c_void_p), z.shape[0], H, W,
-                            float(sigma_z), axis, ctypes.byref(out))
+    zp = z.ctypes.data_as(ctypes.c_void_p)
+    if view is not None:
+        v = make_view(view)
+        st = lib.gp_count_evals_view(ctx.h, ctypes.byref(gs.c()), ctypes.byref(v), zp, z.shape[0], H, W,
+                                     float(sigma_z), ctypes.byref(out))
+    else:
+        st = lib.gp_count_evals(ctx.h, ctypes.byref(gs.c()), zp, z.shape[0], H, W, float(sigma_z), axis,
+                                ctypes.byref(out))
     ctx.check(st, "gp_count_evals")
     return int(out.value)
 
@@ -496,21 +552,22 @@ class SliceRender(torch.autograd.Function):
     gp_render_backward (per-tile lists rebuilt, no per-pixel state kept)."""
 
     @staticmethod
-    def forward(fctx, ctx, z, H, W, sigma_z, axis, scale_mod, mu, scale, quat, alpha):
+    def forward(fctx, ctx, z, H, W, sigma_z, axis, scale_mod, view, mu, scale, quat, alpha):
         gs = GaussianSet(mu.contiguous(), scale.contiguous(), quat.contiguous(), alpha.contiguous(), scale_mod)
-        fctx.meta = (ctx, _host_f32(z).copy(), H, W, sigma_z, axis, scale_mod)
+        v = None if view is None else make_view(view)
+        fctx.meta = (ctx, _host_f32(z).copy(), H, W, sigma_z, axis, scale_mod, v)
         fctx.save_for_backward(gs.mu, gs.scale, gs.quat, gs.alpha)
-        return gp_render_slices(ctx, gs, z, H, W, sigma_z, axis)
+        return gp_render_slices(ctx, gs, z, H, W, sigma_z, axis, view=v)
 
     @staticmethod
     def backward(fctx, g):
-        ctx, z, H, W, sigma_z, axis, scale_mod = fctx.meta
+        ctx, z, H, W, sigma_z, axis, scale_mod, v = fctx.meta
         mu, scale, quat, alpha = fctx.saved_tensors
         gs = GaussianSet(mu, scale, quat, alpha, scale_mod)
-        dm, ds, dq, da = gp_render_backward(ctx, gs, z, H, W, sigma_z, g.contiguous(), axis)
-        return None, None, None, None, None, None, None, dm, ds, dq, da
+        dm, ds, dq, da = gp_render_backward(ctx, gs, z, H, W, sigma_z, g.contiguous(), axis, view=v)
+        return None, None, None, None, None, None, None, None, dm, ds, dq, da
 
 
-def render(ctx, mu, scale, quat, alpha, z, H, W, sigma_z, axis=2, scale_mod=1.0):
-    """Autograd-aware slice stack [S, H, W]."""
-    return SliceRender.apply(ctx, z, H, W, sigma_z, axis, scale_mod, mu, scale, quat, alpha)
+def render(ctx, mu, scale, quat, alpha, z, H, W, sigma_z, axis=2, scale_mod=1.0, view=None):
+    """Autograd-aware slice stack [S, H, W]; view = (R, t) for an oblique stack."""
+    return SliceRender.apply(ctx, z, H, W, sigma_z, axis, scale_mod, view, mu, scale, quat, alpha)

@@ -44,6 +44,7 @@ using namespace gp;
 struct gp_plan {
   Ctx* c = nullptr;
   std::vector<gp_batch_item> items;
+  std::vector<View> views;  // per item, copied at plan time (item.view is not kept)
   int flags = 0;
   int tile = 16, fchunk = 128, bchunk = 64, ctas_f = 0, ctas_b = 0;
   bool any_fwd = false, any_bwd = false, det = false;
@@ -139,7 +140,9 @@ static gp_status build_layout(gp_plan* p, int tile) {
     const gp_batch_item& it = p->items[k];
     SliceArgs& a = p->args[k];
     a.mu = it.set.mu; a.scale = it.set.scale; a.quat = it.set.quat; a.alpha = it.set.alpha;
-    a.n = (int)it.set.n; a.mod = it.set.scale_mod; a.axis = it.axis;
+    a.n = (int)it.set.n; a.mod = it.set.scale_mod;
+    memcpy(a.Rc, p->views[k].R, sizeof(a.Rc));
+    memcpy(a.tc, p->views[k].t, sizeof(a.tc));
     a.sigma2 = it.sigma_z * it.sigma_z; a.k2 = k2;
     a.S = it.S; a.H = it.H; a.W = it.W; a.tile = tile;
     a.TX = ceil_div(it.W, tile); a.TY = ceil_div(it.H, tile);
@@ -368,6 +371,7 @@ static gp_status plan_build(gp_plan* p) {
   // validate items and lay out Gaussians, planes and plan-owned images
   p->gstart.assign(n + 1, 0);
   p->img_off.assign(n, 0);
+  p->views.assign(n, View{});
   int64_t gs = 0, imgs = 0, zs = 0, mse_tmp = 1;
   for (int k = 0; k < n; ++k) {
     const gp_batch_item& it = p->items[k];
@@ -377,8 +381,10 @@ static gp_status plan_build(gp_plan* p) {
     if (!(it.set.scale_mod > 0.0f)) return set_err(c, GP_ERR_ARG, "scale_mod must be > 0");
     if (it.S < 0 || it.H <= 0 || it.W <= 0 || (it.S > 0 && !it.z))
       return set_err(c, GP_ERR_ARG, "batch item " + std::to_string(k) + ": bad slice stack");
-    if (!(it.sigma_z > 0.0f) || !isfinite(it.sigma_z) || it.axis < 0 || it.axis > 2)
-      return set_err(c, GP_ERR_ARG, "batch item " + std::to_string(k) + ": bad sigma_z or axis");
+    if (!(it.sigma_z > 0.0f) || !isfinite(it.sigma_z))
+      return set_err(c, GP_ERR_ARG, "batch item " + std::to_string(k) + ": bad sigma_z");
+    if (it.view ? !check_view(it.view, &p->views[k]) : !axis_view(it.axis, &p->views[k]))
+      return set_err(c, GP_ERR_ARG, "batch item " + std::to_string(k) + ": bad axis or view");
     if ((int64_t)it.S * it.H * it.W > (int64_t)INT32_MAX) return set_err(c, GP_ERR_ARG, "item image too large");
     for (int s = 0; s < it.S; ++s)
       if (!isfinite(it.z[s])) return set_err(c, GP_ERR_ARG, "z contains a non-finite value");

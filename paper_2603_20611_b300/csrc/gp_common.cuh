@@ -150,6 +150,36 @@ __host__ __device__ __forceinline__ int sym_index(int a, int b) {
   return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
 }
 
+// Camera frame of a view [R_c | t] (Sec. S1): mu_c = R_c mu + t, accumulated in
+// FP64 and rounded once (the plane positions are compared against it, so an
+// oblique view loses no more than the rounding of mu_c itself), and the unique
+// entries (xx, xy, xz, yy, yz, zz) of Sigma_c = R_c Sigma R_c^T.  For a
+// permutation R_c both are exact.
+__device__ __forceinline__ void camera_frame(const float* __restrict__ Rc, const float* __restrict__ tc,
+                                             const float* __restrict__ mu, const float Sw[6], float muc[3],
+                                             float Sc[6]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    double acc = (double)tc[r];
+    acc = fma((double)Rc[3 * r], (double)mu[0], acc);
+    acc = fma((double)Rc[3 * r + 1], (double)mu[1], acc);
+    acc = fma((double)Rc[3 * r + 2], (double)mu[2], acc);
+    muc[r] = (float)acc;
+  }
+  float T[3][3];  // R_c Sigma
+#pragma unroll
+  for (int u = 0; u < 3; ++u)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      T[u][k] = fmaf(Rc[3 * u + 2], Sw[sym_index(2, k)],
+                     fmaf(Rc[3 * u + 1], Sw[sym_index(1, k)], Rc[3 * u] * Sw[sym_index(0, k)]));
+  auto sc = [&](int u, int w) {
+    return fmaf(T[u][2], Rc[3 * w + 2], fmaf(T[u][1], Rc[3 * w + 1], T[u][0] * Rc[3 * w]));
+  };
+  Sc[0] = sc(0, 0); Sc[1] = sc(0, 1); Sc[2] = sc(0, 2);
+  Sc[3] = sc(1, 1); Sc[4] = sc(1, 2); Sc[5] = sc(2, 2);
+}
+
 // --------------------------------------------------- ellipse vs rectangle
 // Minimum over the rectangle [x0, x1] x [y0, y1] of q(p) = (p-m)^T C (p-m),
 // C = [[c00, c01], [c01, c11]] positive definite, compared with k2.  Written with

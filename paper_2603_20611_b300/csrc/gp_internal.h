@@ -63,6 +63,17 @@ struct PhaseEvent {
   int64_t launches;
 };
 
+// A validated slice orientation [R_c | t] (camera x_c = R_c x + t, row-major R_c).
+struct View {
+  float R[9];
+  float t[3];
+};
+// The permutation view of slice axis 0, 1 or 2 (false for any other axis).
+bool axis_view(int axis, View* v);
+// Copies a caller's view if it is finite and R is orthonormal to within 1e-3.
+bool check_view(const gp_view* in, View* out);
+bool same_view(const View& a, const View& b);
+
 // Arguments of the binning currently held in a context's buffers.
 struct BinKey {
   bool valid = false;
@@ -70,7 +81,8 @@ struct BinKey {
   int64_t n = 0;
   float mod = 0.f, sigma_z = 0.f;
   std::vector<float> z;
-  int S = 0, H = 0, W = 0, axis = 0, tile = 0;
+  View view{};
+  int S = 0, H = 0, W = 0, tile = 0;
 };
 
 struct Ctx {

@@ -184,12 +184,11 @@ static gp_status scan_counts(Ctx* c, int n, cudaStream_t st, uint32_t* P) {
 // buffers hold the records, the sorted emission indices and the tile ranges,
 // and *a describes the launch.
 static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, int H, int W, float sigma_z,
-                            int axis, cudaStream_t st, SliceArgs* a, uint32_t* pairs_out,
+                            const View& view, cudaStream_t st, SliceArgs* a, uint32_t* pairs_out,
                             const uint32_t** sorted_vals) {
   if (S < 0 || H <= 0 || W <= 0) return set_err(c, GP_ERR_ARG, "need S >= 0, H > 0, W > 0");
   if (S > 0 && !z) return set_err(c, GP_ERR_ARG, "z is NULL");
   if (!(sigma_z > 0.0f) || !isfinite(sigma_z)) return set_err(c, GP_ERR_ARG, "sigma_z must be in (0, inf)");
-  if (axis < 0 || axis > 2) return set_err(c, GP_ERR_ARG, "axis must be 0, 1 or 2");
   if ((int64_t)S * H * W > (int64_t)INT32_MAX) return set_err(c, GP_ERR_ARG, "S*H*W exceeds 2^31");
   for (int s = 0; s < S; ++s)
     if (!isfinite(z[s])) return set_err(c, GP_ERR_ARG, "z contains a non-finite value");
@@ -218,7 +217,9 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
   SliceArgs& A = *a;
   A = SliceArgs{};
   A.mu = set->mu; A.scale = set->scale; A.quat = set->quat; A.alpha = set->alpha;
-  A.n = n; A.mod = set->scale_mod; A.axis = axis; A.sigma2 = sigma_z * sigma_z;
+  A.n = n; A.mod = set->scale_mod; A.sigma2 = sigma_z * sigma_z;
+  memcpy(A.Rc, view.R, sizeof(A.Rc));
+  memcpy(A.tc, view.t, sizeof(A.tc));
   A.k2 = 2.0f * logf(1.0f / c->cfg.eps);
   A.zs = (const float*)b.zs.ptr; A.zorder = (const int*)b.zorder.ptr; A.zorig = (const float*)b.zorig.ptr;
   A.S = S; A.H = H; A.W = W; A.tile = tile; A.TX = TX; A.TY = TY;
@@ -252,7 +253,7 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
   k.mu = set->mu; k.scale = set->scale; k.quat = set->quat; k.alpha = set->alpha;
   k.n = set->n; k.mod = set->scale_mod; k.sigma_z = sigma_z;
   k.z.assign(z, z + S);
-  k.S = S; k.H = H; k.W = W; k.axis = axis; k.tile = tile;
+  k.S = S; k.H = H; k.W = W; k.view = view; k.tile = tile;
   c->bin_pairs = P;
   c->bin_vals = *sorted_vals;
   static_assert(sizeof(SliceArgs) <= sizeof(c->bin_args), "SliceArgs too large");
@@ -262,11 +263,11 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
 
 // True if the context still holds a binning made with exactly these arguments.
 static bool bins_match(const Ctx* c, const gp_set* set, const float* z, int S, int H, int W, float sigma_z,
-                       int axis) {
+                       const View& view) {
   const BinKey& k = c->bin_key;
   if (!k.valid || k.mu != set->mu || k.scale != set->scale || k.quat != set->quat || k.alpha != set->alpha ||
       k.n != set->n || k.mod != set->scale_mod || k.sigma_z != sigma_z || k.S != S || k.H != H || k.W != W ||
-      k.axis != axis || k.tile != tile_of(c))
+      !same_view(k.view, view) || k.tile != tile_of(c))
     return false;
   for (int s = 0; s < S; ++s)
     if (k.z[s] != z[s]) return false;
@@ -320,6 +321,32 @@ static gp_status check_grads(Ctx* c, int64_t n, float* d_mu, float* d_scale, flo
   if (n > 0 && !aligned16(d_quat)) return set_err(c, GP_ERR_ARG, "d_quat must be 16-byte aligned");
   return GP_OK;
 }
+
+bool axis_view(int axis, View* v) {
+  if (axis < 0 || axis > 2) return false;
+  memset(v, 0, sizeof(*v));
+  for (int j = 0; j < 3; ++j) v->R[3 * j + axis_perm(axis, j)] = 1.0f;
+  return true;
+}
+
+bool check_view(const gp_view* in, View* out) {
+  if (!in) return false;
+  for (int k = 0; k < 9; ++k)
+    if (!isfinite(in->R[k])) return false;
+  for (int k = 0; k < 3; ++k)
+    if (!isfinite(in->t[k])) return false;
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) {
+      double d = 0.0;
+      for (int k = 0; k < 3; ++k) d += (double)in->R[3 * r + k] * (double)in->R[3 * q + k];
+      if (fabs(d - (r == q ? 1.0 : 0.0)) > 1e-3) return false;
+    }
+  memcpy(out->R, in->R, sizeof(out->R));
+  memcpy(out->t, in->t, sizeof(out->t));
+  return true;
+}
+
+bool same_view(const View& a, const View& b) { return memcmp(&a, &b, sizeof(View)) == 0; }
 
 }  // namespace gp
 
@@ -409,9 +436,8 @@ gp_status gp_last_counts(gp_ctx* ctx, int64_t* pairs, int64_t* issued) {
   return GP_OK;
 }
 
-gp_status gp_render_slices(gp_ctx* ctx, const gp_set* set, const float* z, int S, int H, int W,
-                           float sigma_z, int axis, float* out, void* stream) {
-  if (!ctx) return GP_ERR_ARG;
+static gp_status render_impl(gp_ctx* ctx, const gp_set* set, const View& view, const float* z, int S, int H,
+                             int W, float sigma_z, float* out, void* stream) {
   Ctx* c = &ctx->impl;
   GP_TRY(check_set(c, set));
   if (!out && S > 0) return set_err(c, GP_ERR_ARG, "out is NULL");
@@ -420,7 +446,7 @@ gp_status gp_render_slices(gp_ctx* ctx, const gp_set* set, const float* z, int S
   SliceArgs a;
   uint32_t P = 0;
   const uint32_t* vals = nullptr;
-  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, axis, st, &a, &P, &vals));
+  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals));
   if (S == 0) return GP_OK;
   if (P == 0) {
     GP_CUDA(c, cudaMemsetAsync(out, 0, (size_t)S * H * W * 4, st), "clear out");
@@ -433,10 +459,9 @@ gp_status gp_render_slices(gp_ctx* ctx, const gp_set* set, const float* z, int S
   return GP_OK;
 }
 
-gp_status gp_render_backward(gp_ctx* ctx, const gp_set* set, const float* z, int S, int H, int W,
-                             float sigma_z, int axis, const float* dL_dI, float* d_mu, float* d_scale,
-                             float* d_quat, float* d_alpha, void* stream) {
-  if (!ctx) return GP_ERR_ARG;
+static gp_status backward_impl(gp_ctx* ctx, const gp_set* set, const View& view, const float* z, int S, int H,
+                               int W, float sigma_z, const float* dL_dI, float* d_mu, float* d_scale,
+                               float* d_quat, float* d_alpha, void* stream) {
   Ctx* c = &ctx->impl;
   GP_TRY(check_set(c, set));
   const int n = (int)set->n;
@@ -447,12 +472,12 @@ gp_status gp_render_backward(gp_ctx* ctx, const gp_set* set, const float* z, int
   SliceArgs a;
   uint32_t P = 0;
   const uint32_t* vals = nullptr;
-  if (c->cfg.reuse_bins && S > 0 && z && bins_match(c, set, z, S, H, W, sigma_z, axis)) {
+  if (c->cfg.reuse_bins && S > 0 && z && bins_match(c, set, z, S, H, W, sigma_z, view)) {
     memcpy(&a, c->bin_args, sizeof(SliceArgs));
     P = c->bin_pairs;
     vals = c->bin_vals;
   } else {
-    GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, axis, st, &a, &P, &vals));
+    GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals));
   }
   if (n == 0) return GP_OK;
   BinBufs& b = c->b;
@@ -506,9 +531,8 @@ gp_status gp_mse_grad(gp_ctx* ctx, const float* I, const float* T, const int* t_
   return cuda_err(c, cudaGetLastError(), "mse");
 }
 
-gp_status gp_count_evals(gp_ctx* ctx, const gp_set* set, const float* z, int S, int H, int W, float sigma_z,
-                         int axis, int64_t* evals) {
-  if (!ctx || !evals) return GP_ERR_ARG;
+static gp_status count_impl(gp_ctx* ctx, const gp_set* set, const View& view, const float* z, int S, int H,
+                            int W, float sigma_z, int64_t* evals) {
   Ctx* c = &ctx->impl;
   GP_TRY(check_set(c, set));
   GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
@@ -516,7 +540,7 @@ gp_status gp_count_evals(gp_ctx* ctx, const gp_set* set, const float* z, int S, 
   SliceArgs a;
   uint32_t P = 0;
   const uint32_t* vals = nullptr;
-  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, axis, st, &a, &P, &vals));
+  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals));
   unsigned long long* d = (unsigned long long*)c->b.total.ptr + 1;
   GP_CUDA(c, cudaMemsetAsync(d, 0, 8, st), "count");
   if (set->n > 0 && S > 0) launch_count_evals(a, (const SliceRec*)c->b.rec.ptr, d, st);
@@ -524,6 +548,67 @@ gp_status gp_count_evals(gp_ctx* ctx, const gp_set* set, const float* z, int S, 
   GP_CUDA(c, cudaStreamSynchronize(st), "count readback");
   *evals = (int64_t)*c->h_total;
   return GP_OK;
+}
+
+gp_status gp_view_from_axis(int axis, gp_view* view) {
+  View v;
+  if (!view || !axis_view(axis, &v)) return GP_ERR_ARG;
+  memcpy(view->R, v.R, sizeof(v.R));
+  memcpy(view->t, v.t, sizeof(v.t));
+  return GP_OK;
+}
+
+gp_status gp_render_slices(gp_ctx* ctx, const gp_set* set, const float* z, int S, int H, int W, float sigma_z,
+                           int axis, float* out, void* stream) {
+  if (!ctx) return GP_ERR_ARG;
+  View v;
+  if (!axis_view(axis, &v)) return set_err(&ctx->impl, GP_ERR_ARG, "axis must be 0, 1 or 2");
+  return render_impl(ctx, set, v, z, S, H, W, sigma_z, out, stream);
+}
+
+gp_status gp_render_slices_view(gp_ctx* ctx, const gp_set* set, const gp_view* view, const float* z, int S,
+                                int H, int W, float sigma_z, float* out, void* stream) {
+  if (!ctx) return GP_ERR_ARG;
+  View v;
+  if (!check_view(view, &v))
+    return set_err(&ctx->impl, GP_ERR_ARG, "view must be finite with R orthonormal to 1e-3");
+  return render_impl(ctx, set, v, z, S, H, W, sigma_z, out, stream);
+}
+
+gp_status gp_render_backward(gp_ctx* ctx, const gp_set* set, const float* z, int S, int H, int W,
+                             float sigma_z, int axis, const float* dL_dI, float* d_mu, float* d_scale,
+                             float* d_quat, float* d_alpha, void* stream) {
+  if (!ctx) return GP_ERR_ARG;
+  View v;
+  if (!axis_view(axis, &v)) return set_err(&ctx->impl, GP_ERR_ARG, "axis must be 0, 1 or 2");
+  return backward_impl(ctx, set, v, z, S, H, W, sigma_z, dL_dI, d_mu, d_scale, d_quat, d_alpha, stream);
+}
+
+gp_status gp_render_backward_view(gp_ctx* ctx, const gp_set* set, const gp_view* view, const float* z, int S,
+                                  int H, int W, float sigma_z, const float* dL_dI, float* d_mu, float* d_scale,
+                                  float* d_quat, float* d_alpha, void* stream) {
+  if (!ctx) return GP_ERR_ARG;
+  View v;
+  if (!check_view(view, &v))
+    return set_err(&ctx->impl, GP_ERR_ARG, "view must be finite with R orthonormal to 1e-3");
+  return backward_impl(ctx, set, v, z, S, H, W, sigma_z, dL_dI, d_mu, d_scale, d_quat, d_alpha, stream);
+}
+
+gp_status gp_count_evals(gp_ctx* ctx, const gp_set* set, const float* z, int S, int H, int W, float sigma_z,
+                         int axis, int64_t* evals) {
+  if (!ctx || !evals) return GP_ERR_ARG;
+  View v;
+  if (!axis_view(axis, &v)) return set_err(&ctx->impl, GP_ERR_ARG, "axis must be 0, 1 or 2");
+  return count_impl(ctx, set, v, z, S, H, W, sigma_z, evals);
+}
+
+gp_status gp_count_evals_view(gp_ctx* ctx, const gp_set* set, const gp_view* view, const float* z, int S,
+                              int H, int W, float sigma_z, int64_t* evals) {
+  if (!ctx || !evals) return GP_ERR_ARG;
+  View v;
+  if (!check_view(view, &v))
+    return set_err(&ctx->impl, GP_ERR_ARG, "view must be finite with R orthonormal to 1e-3");
+  return count_impl(ctx, set, v, z, S, H, W, sigma_z, evals);
 }
 
 gp_status gp_exp2_eval(gp_ctx* ctx, const float* x, float* y, int64_t n, int mode, void* stream) {

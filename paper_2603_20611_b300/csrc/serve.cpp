@@ -37,6 +37,7 @@ struct Request {
   uint64_t ticket;
   gp_request r;
   std::vector<float> z;  // copy of the plane positions
+  gp::View view{};       // slice orientation (the request's view, or its axis's)
   Clock::time_point submitted;
   int64_t est_bytes;
 };
@@ -86,9 +87,11 @@ int64_t estimate_bytes(const gp_server* s, const gp_request& r) {
   return px * 4 + g.n * 64 + g.n * 24 * 20;  // staging + records + pair buffers
 }
 
-bool same_batch(const gp_request& a, const gp_request& b) {
+bool same_batch(const Request& qa, const Request& qb) {
+  const gp_request &a = qa.r, &b = qb.r;
   return (a.kind == GP_REQ_SLICE || a.kind == GP_REQ_STACK) && (b.kind == GP_REQ_SLICE || b.kind == GP_REQ_STACK) &&
-         a.set_id == b.set_id && a.axis == b.axis && a.H == b.H && a.W == b.W && a.sigma_z == b.sigma_z;
+         a.set_id == b.set_id && gp::same_view(qa.view, qb.view) && a.H == b.H && a.W == b.W &&
+         a.sigma_z == b.sigma_z;
 }
 
 int64_t free_device_bytes(int device) {
@@ -143,8 +146,11 @@ gp_status run_slices(gp_server* s, Worker& w, std::vector<Request>& batch) {
     }
     dst = w.staging;
   }
-  gp_status st = gp_render_slices(w.ctx, &s->sets[r0.set_id], z.data(), S, r0.H, r0.W, r0.sigma_z, r0.axis, dst,
-                                  w.stream);
+  gp_view v;
+  memcpy(v.R, batch[0].view.R, sizeof(v.R));
+  memcpy(v.t, batch[0].view.t, sizeof(v.t));
+  gp_status st = gp_render_slices_view(w.ctx, &s->sets[r0.set_id], &v, z.data(), S, r0.H, r0.W, r0.sigma_z, dst,
+                                       w.stream);
   if (st != GP_OK) return st;
   if (batch.size() > 1) {
     size_t off = 0;
@@ -192,7 +198,7 @@ void worker_loop(gp_server* s, int wi) {
       if (batch[0].r.kind != GP_REQ_VOXELIZE) {
         int planes = batch[0].r.S;
         for (auto it = s->pending.begin(); it != s->pending.end();) {
-          if (same_batch(batch[0].r, it->r) && planes + it->r.S <= s->cfg.max_batch_slices &&
+          if (same_batch(batch[0], *it) && planes + it->r.S <= s->cfg.max_batch_slices &&
               s->inflight_bytes + it->est_bytes <= budget) {
             planes += it->r.S;
             s->inflight_bytes += it->est_bytes;
@@ -231,8 +237,9 @@ gp_status check_request(gp_server* s, const gp_request* r) {
     return GP_OK;
   }
   if (r->kind != GP_REQ_SLICE && r->kind != GP_REQ_STACK) return GP_ERR_ARG;
-  if (r->S <= 0 || !r->z || r->H <= 0 || r->W <= 0 || !(r->sigma_z > 0.0f) || r->axis < 0 || r->axis > 2)
-    return GP_ERR_ARG;
+  if (r->S <= 0 || !r->z || r->H <= 0 || r->W <= 0 || !(r->sigma_z > 0.0f)) return GP_ERR_ARG;
+  gp::View v;
+  if (r->view ? !gp::check_view(r->view, &v) : !gp::axis_view(r->axis, &v)) return GP_ERR_ARG;
   if (r->kind == GP_REQ_SLICE && r->S != 1) return GP_ERR_ARG;
   if (r->S > s->cfg.max_batch_slices) return GP_ERR_ARG;
   return GP_OK;
@@ -302,7 +309,14 @@ gp_status gp_serve_submit(gp_server* s, const gp_request* r, uint64_t* ticket) {
   Request q;
   q.ticket = s->next_ticket++;
   q.r = *r;
-  if (r->kind != GP_REQ_VOXELIZE) q.z.assign(r->z, r->z + r->S);
+  if (r->kind != GP_REQ_VOXELIZE) {
+    q.z.assign(r->z, r->z + r->S);
+    if (r->view)
+      gp::check_view(r->view, &q.view);
+    else
+      gp::axis_view(r->axis, &q.view);
+  }
+  q.r.view = nullptr;  // the caller's view need not outlive the submit
   q.submitted = Clock::now();
   q.est_bytes = estimate_bytes(s, *r);
   *ticket = q.ticket;

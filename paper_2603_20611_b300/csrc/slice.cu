@@ -1,8 +1,10 @@
 // slice.cu -- sm_103a kernels of the finite-thickness slice projection operator
 // (GaussianPile, arXiv 2603.20611, Sec. 4.2 Eq. 6-10 forward, Sec. 4.3 backward).
 //
-// Closed form used on the device.  For slice axis c with in-plane axes p and a
-// plane at z_s, the paper's inverse-covariance update (Eq. 6), opacity
+// Closed form used on the device.  In the camera frame of the view [R_c | t]
+// (Sec. S1: mu_c = R_c mu + t, Sigma_c = R_c Sigma R_c^T; R_c an axis
+// permutation or any rotation shared by the stack's planes), with slice axis c,
+// in-plane axes p and a plane at z_s, the paper's inverse-covariance update (Eq. 6), opacity
 // modulation (Eq. 7) and marginal (Eq. 8) reduce, by the Sherman-Morrison
 // identity, to
 //     v = Sigma_cc + sigma_z^2,  a = Sigma_pc / v,
@@ -173,11 +175,11 @@ __device__ __forceinline__ void slice_pre_one(const SliceArgs& a, int i, int ig,
   float d3[3] = {a.mod * a.scale[3 * i], a.mod * a.scale[3 * i + 1], a.mod * a.scale[3 * i + 2]};
   float M[3][3], Sw[6];
   covariance(R, d3, M, Sw);
-  // camera frame (axis permutation): Sc[u][w] = Sigma[perm u][perm w]
-  const int p0 = axis_perm(a.axis, 0), p1 = axis_perm(a.axis, 1), p2 = axis_perm(a.axis, 2);
-  float cxx = Sw[sym_index(p0, p0)], cxy = Sw[sym_index(p0, p1)], cxz = Sw[sym_index(p0, p2)];
-  float cyy = Sw[sym_index(p1, p1)], cyz = Sw[sym_index(p1, p2)], czz = Sw[sym_index(p2, p2)];
-  float mux = a.mu[3 * i + p0], muy = a.mu[3 * i + p1], muz = a.mu[3 * i + p2];
+  // camera frame of the view: mu_c = R_c mu + t, Sigma_c = R_c Sigma R_c^T
+  float mc[3], Sc[6];
+  camera_frame(a.Rc, a.tc, a.mu + 3 * i, Sw, mc, Sc);
+  float cxx = Sc[0], cxy = Sc[1], cxz = Sc[2], cyy = Sc[3], cyz = Sc[4], czz = Sc[5];
+  float mux = mc[0], muy = mc[1], muz = mc[2];
   float v = czz + a.sigma2;
   float iv = 1.0f / v;
   float ax = cxz * iv, ay = cyz * iv;
@@ -688,9 +690,9 @@ __device__ __forceinline__ void slice_bwd_pre_one(const SliceArgs& a, int i, int
   float dd[3] = {a.mod * a.scale[3 * i], a.mod * a.scale[3 * i + 1], a.mod * a.scale[3 * i + 2]};
   float M[3][3], Sw[6];
   covariance(R, dd, M, Sw);
-  const int p[3] = {axis_perm(a.axis, 0), axis_perm(a.axis, 1), axis_perm(a.axis, 2)};
-  float cxx = Sw[sym_index(p[0], p[0])], cxy = Sw[sym_index(p[0], p[1])], cxz = Sw[sym_index(p[0], p[2])];
-  float cyy = Sw[sym_index(p[1], p[1])], cyz = Sw[sym_index(p[1], p[2])], czz = Sw[sym_index(p[2], p[2])];
+  float mc[3], Sc[6];
+  camera_frame(a.Rc, a.tc, a.mu + 3 * i, Sw, mc, Sc);
+  float cxx = Sc[0], cxy = Sc[1], cxz = Sc[2], cyy = Sc[3], cyz = Sc[4], czz = Sc[5];
   float v = czz + a.sigma2, iv = 1.0f / v;
   float ax = cxz * iv, ay = cyz * iv;
   float sxx = cxx - cxz * ax, sxy = cxy - cxz * ay, syy = cyy - cyz * ay;
@@ -717,14 +719,22 @@ __device__ __forceinline__ void slice_bwd_pre_one(const SliceArgs& a, int i, int
     float gv = A * T2 * iv * iv * 0.5f + (cxz * Hbx + cyz * Hby) * iv * iv - (gax * cxz + gay * cyz) * iv * iv;
     float gbx = -2.0f * Hbx * iv + gax * iv, gby = -2.0f * Hby * iv + gay * iv;
     float gmc[3] = {S1x, S1y, -(ax * S1x + ay * S1y) - A * iv * T1};
-    // camera-frame symmetric gradient -> world (inverse axis permutation)
+    // camera frame -> world: dL/dmu = R_c^T dL/dmu_c, dL/dSigma = R_c^T dL/dSigma_c R_c
+    const float* Rc = a.Rc;
     float Gc[3][3] = {{H00, H01, 0.5f * gbx}, {H01, H11, 0.5f * gby}, {0.5f * gbx, 0.5f * gby, gv}};
+    float GR[3][3];  // Gc R_c
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        GR[u][l] = fmaf(Gc[u][2], Rc[6 + l], fmaf(Gc[u][1], Rc[3 + l], Gc[u][0] * Rc[l]));
     float Gw[3][3];
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      gmu[p[u]] = gmc[u];
+    for (int k = 0; k < 3; ++k) {
+      gmu[k] = fmaf(Rc[6 + k], gmc[2], fmaf(Rc[3 + k], gmc[1], Rc[k] * gmc[0]));
 #pragma unroll
-      for (int w = 0; w < 3; ++w) Gw[p[u]][p[w]] = Gc[u][w];
+      for (int l = 0; l < 3; ++l)
+        Gw[k][l] = fmaf(Rc[6 + k], GR[2][l], fmaf(Rc[3 + k], GR[1][l], Rc[k] * GR[0][l]));
     }
     scale_quat_backward(R, M, dd, qn, qnorm, a.mod, Gw, gs, gq);
   }

@@ -15,7 +15,8 @@ struct SliceArgs {
   const float* alpha;
   int n;
   float mod;
-  int axis;
+  float Rc[9];    // view [R_c | t]: camera coordinates x_c = R_c x + t (row-major R_c)
+  float tc[3];
   float sigma2;   // sigma_z^2
   float k2;       // 2 ln(1/eps): squared Mahalanobis culling radius
   const float* zs;      // [S] plane positions sorted ascending
