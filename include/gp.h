@@ -73,6 +73,8 @@ typedef struct gp_ctx gp_ctx;
 #define GP_EXP_POLY 0  /* project-written exp2: range reduction + degree-6 polynomial on
                           the FP32 pipe (no ex2.approx); the default */
 #define GP_EXP_HW 1    /* the SFU ex2.approx instruction (benchmarked alternative) */
+#define GP_EXP_POLY_PACKED 2  /* gp_exp2_eval only: GP_EXP_POLY in the packed two-value form
+                                 the rasterisers use (bitwise equal to GP_EXP_POLY) */
 
 typedef struct {
   float eps;              /* culling bound: truncated mass per pair <= eps (default 1e-6) */
@@ -233,7 +235,8 @@ GP_API gp_status gp_count_evals(gp_ctx* ctx, const gp_set* set, const float* z, 
                          int W, float sigma_z, int axis, int64_t* evals);
 
 /* Test hook for the rasterisers' exponential: y[i] = 2^x[i] for n DEVICE floats
- * with the given mode (GP_EXP_POLY or GP_EXP_HW).  Inputs below -125 clamp. */
+ * with the given mode (GP_EXP_POLY, GP_EXP_HW or GP_EXP_POLY_PACKED).  Inputs
+ * below -125 clamp. */
 GP_API gp_status gp_exp2_eval(gp_ctx* ctx, const float* x, float* y, int64_t n, int mode,
                        void* stream);
 

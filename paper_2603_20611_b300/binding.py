@@ -26,6 +26,7 @@ GP_ERR_OVERFLOW = -5
 GP_ERR_STATE = -6
 GP_EXP_POLY = 0
 GP_EXP_HW = 1
+GP_EXP_POLY_PACKED = 2
 
 # Every symbol include/gp.h declares (checked by the CPU ABI test).
 EXPORTS = (

@@ -40,6 +40,26 @@ __device__ __forceinline__ float exp2_poly(float x) {
   return __int_as_float(__float_as_int(p) + (__float_as_int(t) << 23));
 }
 
+// exp2_poly on two values at once with the packed fp32x2 instructions of
+// sm_100-class SMs (one instruction issues both lanes' add / fma): the same
+// operations, each rounded exactly as in exp2_poly, so the results are
+// bitwise those of two exp2_poly calls.
+__device__ __forceinline__ float2 exp2_poly2(float2 x) {
+  const float kShift = 12582912.0f;  // 1.5 * 2^23
+  const float2 t = __fadd2_rn(x, make_float2(kShift, kShift));
+  const float2 n = __fadd2_rn(t, make_float2(-kShift, -kShift));
+  const float2 f = __ffma2_rn(n, make_float2(-1.0f, -1.0f), x);  // x - n, rounded once
+  float2 p = make_float2(GP_EXP2_C6, GP_EXP2_C6);
+  p = __ffma2_rn(p, f, make_float2(GP_EXP2_C5, GP_EXP2_C5));
+  p = __ffma2_rn(p, f, make_float2(GP_EXP2_C4, GP_EXP2_C4));
+  p = __ffma2_rn(p, f, make_float2(GP_EXP2_C3, GP_EXP2_C3));
+  p = __ffma2_rn(p, f, make_float2(GP_EXP2_C2, GP_EXP2_C2));
+  p = __ffma2_rn(p, f, make_float2(GP_EXP2_C1, GP_EXP2_C1));
+  p = __ffma2_rn(p, f, make_float2(1.0f, 1.0f));
+  return make_float2(__int_as_float(__float_as_int(p.x) + (__float_as_int(t.x) << 23)),
+                     __int_as_float(__float_as_int(p.y) + (__float_as_int(t.y) << 23)));
+}
+
 // The SFU instruction, as a benchmarked alternative (GP_EXP_HW).
 __device__ __forceinline__ float exp2_hw(float x) {
   float y;
@@ -51,6 +71,12 @@ template <int MODE>
 __device__ __forceinline__ float exp2_sel(float x) {
   if constexpr (MODE == GP_EXP_HW) return exp2_hw(x);
   else return exp2_poly(x);
+}
+
+template <int MODE>
+__device__ __forceinline__ float2 exp2_sel2(float2 x) {
+  if constexpr (MODE == GP_EXP_HW) return make_float2(exp2_hw(x.x), exp2_hw(x.y));
+  else return exp2_poly2(x);
 }
 
 constexpr float kExpFloor = -125.0f;  // 2^-125 ~ 2.4e-38: below fp32 resolution of any sum

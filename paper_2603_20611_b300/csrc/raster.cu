@@ -35,6 +35,17 @@
 
 namespace gp {
 
+// Exponentials of pixels (2p, 2p + 1) of a row: e = A + B q + C q^2 floored at
+// kExpFloor, two pixels per packed fp32x2 instruction (each pixel rounded as the
+// scalar form rounds it).
+template <int EXPM>
+__device__ __forceinline__ float2 pair_exp2(float2 C2, float2 B2, float2 A2, float2 q) {
+  float2 e = __ffma2_rn(__ffma2_rn(C2, q, B2), q, A2);
+  e.x = fmaxf(e.x, kExpFloor);
+  e.y = fmaxf(e.y, kExpFloor);
+  return exp2_sel2<EXPM>(e);
+}
+
 // Staging of one Gaussian for one (slice, tile):
 //   s0 = (mu_2d,x - x0, mu_2d,y - y0, a~, C11)
 //   s1 = (c0, c1, c2, C00)     e = c0 dx^2 + c1 dx dy + c2 dy^2 = -log2(e)/2 d^T C d
@@ -116,9 +127,9 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
   const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
   const float zsv = a.zorig[s];
   int* list = sm.hitlist[warp];
-  float acc[8];
+  float2 acc[4];  // pixels (2p, 2p + 1) of the lane's row
 #pragma unroll
-  for (int p = 0; p < 8; ++p) acc[p] = 0.0f;
+  for (int p = 0; p < 4; ++p) acc[p] = make_float2(0.0f, 0.0f);
   for (uint32_t base = rg.x; base < rg.y; base += CH) {
     const int cnt = (int)min((uint32_t)CH, rg.y - base);
     for (int j = threadIdx.x; j < cnt; j += NT) {
@@ -141,12 +152,14 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
         const float dxc = cxb - g0.x;
         const float A = fmaf(dxc, fmaf(g1.x, dxc, u), g1.z * dy * dy);
         const float Bq = fmaf(2.0f * g1.x, dxc, u);
+        const float2 C2 = make_float2(g1.x, g1.x), B2 = make_float2(Bq, Bq), A2 = make_float2(A, A);
+        const float2 at2 = make_float2(g0.z, g0.z);
+        // two pixels per packed instruction; each lane of a pair is rounded as
+        // the scalar form would round it
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          const float q = (float)p - 3.5f;
-          float e = fmaf(fmaf(g1.x, q, Bq), q, A);
-          e = fmaxf(e, kExpFloor);
-          acc[p] = fmaf(g0.z, exp2_sel<EXPM>(e), acc[p]);
+        for (int p = 0; p < 4; ++p) {
+          const float2 q = make_float2((float)(2 * p) - 3.5f, (float)(2 * p + 1) - 3.5f);
+          acc[p] = __ffma2_rn(at2, pair_exp2<EXPM>(C2, B2, A2, q), acc[p]);
         }
       }
       __syncwarp();
@@ -155,9 +168,11 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
   }
   // the four groups' partial sums of the same pixels, in a fixed tree
 #pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    acc[p] += __shfl_xor_sync(0xffffffffu, acc[p], 8);
-    acc[p] += __shfl_xor_sync(0xffffffffu, acc[p], 16);
+  for (int p = 0; p < 4; ++p) {
+    acc[p].x += __shfl_xor_sync(0xffffffffu, acc[p].x, 8);
+    acc[p].y += __shfl_xor_sync(0xffffffffu, acc[p].y, 8);
+    acc[p].x += __shfl_xor_sync(0xffffffffu, acc[p].x, 16);
+    acc[p].y += __shfl_xor_sync(0xffffffffu, acc[p].y, 16);
   }
   if (grp == 0) {
     const int py = ty * TILE + (int)by + row;
@@ -165,12 +180,14 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
     if (py < a.H) {
       float* o = a.out + ((int64_t)s * a.H + py) * a.W + px0;
       if (px0 + 8 <= a.W && ((((uintptr_t)o) & 15u) == 0)) {
-        reinterpret_cast<float4*>(o)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        reinterpret_cast<float4*>(o)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        reinterpret_cast<float4*>(o)[0] = make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y);
+        reinterpret_cast<float4*>(o)[1] = make_float4(acc[2].x, acc[2].y, acc[3].x, acc[3].y);
       } else {
 #pragma unroll
-        for (int p = 0; p < 8; ++p)
-          if (px0 + p < a.W) o[p] = acc[p];
+        for (int p = 0; p < 4; ++p) {
+          if (px0 + 2 * p < a.W) o[2 * p] = acc[p].x;
+          if (px0 + 2 * p + 1 < a.W) o[2 * p + 1] = acc[p].y;
+        }
       }
     }
   }
@@ -211,13 +228,16 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
   const bool rb2 = (row >> 2) & 1, rb1 = (row >> 1) & 1, rb0 = row & 1;
   const int vidx = 3 * (int)rb2 + 2 * (int)rb1 + (int)rb0;  // moment this lane holds after the butterfly
   const bool vvalid = 2 * (int)rb1 + (int)rb0 < 3;
-  float G[8];
+  float2 G[4];  // dL/dI of pixels (2p, 2p + 1) of the lane's row
   {
     const int py = ty * TILE + (int)by + row;
     const int px0 = tx * TILE + (int)bx;
+    float g8[8];
 #pragma unroll
     for (int p = 0; p < 8; ++p)
-      G[p] = (py < a.H && px0 + p < a.W) ? a.dL_dI[((int64_t)s * a.H + py) * a.W + px0 + p] : 0.0f;
+      g8[p] = (py < a.H && px0 + p < a.W) ? a.dL_dI[((int64_t)s * a.H + py) * a.W + px0 + p] : 0.0f;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) G[p] = make_float2(g8[2 * p], g8[2 * p + 1]);
   }
   for (uint32_t base = rg.x; base < rg.y; base += CH) {
     const int cnt = (int)min((uint32_t)CH, rg.y - base);
@@ -243,18 +263,20 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
         const float dxc = cxb - g0.x;
         const float A = fmaf(dxc, fmaf(g1.x, dxc, u), g1.z * dy * dy);
         const float Bq = fmaf(2.0f * g1.x, dxc, u);
-        // row sums about the centre column: S0 = sum G E, S1 = sum q G E, S2 = sum q^2 G E
-        float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+        // row sums about the centre column: S0 = sum G E, S1 = sum q G E, S2 = sum q^2 G E,
+        // kept as two interleaved partial sums (even / odd pixels) and added at the end
+        const float2 C2 = make_float2(g1.x, g1.x), B2 = make_float2(Bq, Bq), A2 = make_float2(A, A);
+        float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          const float q = (float)p - 3.5f;
-          float e = fmaf(fmaf(g1.x, q, Bq), q, A);
-          e = fmaxf(e, kExpFloor);
-          const float gE = G[p] * exp2_sel<EXPM>(e);
-          S0 += gE;
-          S1 = fmaf(q, gE, S1);
-          S2 = fmaf(q * q, gE, S2);
+        for (int p = 0; p < 4; ++p) {
+          const float qa = (float)(2 * p) - 3.5f, qb = (float)(2 * p + 1) - 3.5f;
+          const float2 q = make_float2(qa, qb);
+          const float2 gE = __fmul2_rn(G[p], pair_exp2<EXPM>(C2, B2, A2, q));
+          P0 = __fadd2_rn(P0, gE);
+          P1 = __ffma2_rn(q, gE, P1);
+          P2 = __ffma2_rn(make_float2(qa * qa, qb * qb), gE, P2);
         }
+        const float S0 = P0.x + P0.y, S1 = P1.x + P1.y, S2 = P2.x + P2.y;
         // this row's six moments (dx = dxc + q): sum G E {1, dx, dy, dx^2, dx dy, dy^2}
         const float mxr = fmaf(dxc, S0, S1);
         const float v0 = S0, v1 = mxr, v2 = S0 * dy;

@@ -885,6 +885,14 @@ __global__ void k_exp2_eval(const float* __restrict__ x, float* __restrict__ y, 
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float v = fmaxf(x[i], kExpFloor);
+  if (mode == GP_EXP_POLY_PACKED) {
+    // the packed two-value form, paired with the neighbouring element
+    const int64_t j = i ^ 1;
+    const float w = j < n ? fmaxf(x[j], kExpFloor) : 0.0f;
+    const float2 r = exp2_poly2((i & 1) ? make_float2(w, v) : make_float2(v, w));
+    y[i] = (i & 1) ? r.y : r.x;
+    return;
+  }
   y[i] = mode == GP_EXP_HW ? exp2_hw(v) : exp2_poly(v);
 }
 

@@ -44,6 +44,18 @@ def test_exp2_accuracy(ctx, mode, tol):
     assert rel.max() <= tol, rel.max()
 
 
+def test_packed_exp2_is_bitwise_the_scalar_form(ctx):
+    """The rasterisers evaluate two pixels per packed fp32x2 instruction; every
+    lane must round exactly as the scalar exp2 does (odd length: the last
+    element pairs with a dummy)."""
+    rng = np.random.Generator(np.random.PCG64(2))
+    x = torch.from_numpy(np.concatenate([np.linspace(-125.0, 0.5, (1 << 20) + 1),
+                                         rng.uniform(-130, 0.5, 4097)]).astype(np.float32)).cuda()
+    a = B.gp_exp2_eval(ctx, x, B.GP_EXP_POLY)
+    b = B.gp_exp2_eval(ctx, x, B.GP_EXP_POLY_PACKED)
+    assert torch.equal(a, b)
+
+
 def test_exp2_matches_cuda_exp2f(ctx):
     """Cross-check with CUDA's own exp2 (through torch) on the same inputs."""
     x = torch.linspace(-60.0, 0.0, 1 << 18, device="cuda")
