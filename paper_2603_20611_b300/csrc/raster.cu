@@ -77,7 +77,8 @@ __device__ __forceinline__ float edge_q(float cf, float c01, float cv, float inv
 // this warp's block (pixel centres [bx + .5, bx + 7.5] x [by + .5, by + 7.5]):
 // the minimum of the quadratic form over the block rectangle, taken at the
 // centre if it lies inside and otherwise on the nearest of the four edges.
-// Their chunk indices are compacted into list[0..n).  Returns n.
+// Their chunk indices are compacted into list[0..n) (list points past the hits
+// already found in this chunk).  Returns n.
 __device__ __forceinline__ int block_hits(const float4* __restrict__ s0, const float4* __restrict__ s1,
                                           const float4* __restrict__ sc, int jb, int cnt, float bx, float by,
                                           float k2, int lane, int* list) {
@@ -106,7 +107,7 @@ __device__ __forceinline__ int block_hits(const float4* __restrict__ s0, const f
 template <int TILE, int CH>
 struct FwdSmem {
   float4 s0[CH], s1[CH], sc[CH];
-  int hitlist[(TILE / 8) * (TILE / 8)][32];
+  int hitlist[(TILE / 8) * (TILE / 8)][CH];  // per warp: the chunk's Gaussians that hit its block
 };
 
 // One (slice s, tile t) of item a: every pixel of the tile is written.
@@ -140,8 +141,11 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
       sm.sc[j] = a3;
     }
     __syncthreads();
-    for (int jb = 0; jb < cnt; jb += 32) {
-      const int nh = block_hits(sm.s0, sm.s1, sm.sc, jb, cnt, bx, by, a.k2, lane, list);
+    // test the whole chunk first, so that the hits are taken four at a time
+    // with at most one partly idle round per chunk
+    int nh = 0;
+    for (int jb = 0; jb < cnt; jb += 32) nh += block_hits(sm.s0, sm.s1, sm.sc, jb, cnt, bx, by, a.k2, lane, list + nh);
+    {
       for (int h = grp; h < nh; h += 4) {
         const int jj = list[h];
         const float4 g0 = sm.s0[jj], g1 = sm.s1[jj];
@@ -201,7 +205,7 @@ struct BwdSmem {
   float4 s0[CH], s1[CH], s2[CH], sc[CH];
   uint32_t sg[CH];
   float sp[NW][6][CH];
-  int hitlist[NW][32];
+  int hitlist[NW][CH];
 };
 
 template <int TILE, int CH, int EXPM, bool DET>
@@ -253,8 +257,9 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
     }
     for (int i = threadIdx.x; i < NW * 6 * CH; i += NT) (&sm.sp[0][0][0])[i] = 0.0f;
     __syncthreads();
-    for (int jb = 0; jb < cnt; jb += 32) {
-      const int nh = block_hits(sm.s0, sm.s1, sm.sc, jb, cnt, bx, by, a.k2, lane, list);
+    int nh = 0;
+    for (int jb = 0; jb < cnt; jb += 32) nh += block_hits(sm.s0, sm.s1, sm.sc, jb, cnt, bx, by, a.k2, lane, list + nh);
+    {
       for (int h = grp; h < nh; h += 4) {
         const int jj = list[h];
         const float4 g0 = sm.s0[jj], g1 = sm.s1[jj];
