@@ -199,49 +199,69 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
 
 constexpr int ACC10 = 10;
 
+// Rectangle test of one staged Gaussian (as block_hits): does its culling
+// ellipse touch the pixel centres [x0, x1] x [y0, y1] (tile-relative)?
+__device__ __forceinline__ bool rect_hit(float4 g0, float4 g1, float4 gc, float x0, float x1, float y0, float y1,
+                                         float k2) {
+  const float C00 = g1.w, C01 = gc.x, C11 = g0.w;
+  const float xl = x0 - g0.x, xh = x1 - g0.x, yl = y0 - g0.y, yh = y1 - g0.y;
+  if (xl <= 0.0f && xh >= 0.0f && yl <= 0.0f && yh >= 0.0f) return true;
+  float m = fminf(edge_q(C00, C01, C11, gc.z, xl, yl, yh), edge_q(C00, C01, C11, gc.z, xh, yl, yh));
+  m = fminf(m, fminf(edge_q(C11, C01, C00, gc.y, yl, xl, xh), edge_q(C11, C01, C00, gc.y, yh, xl, xh)));
+  return m <= k2;
+}
+
+// Shared memory of the backward body.  The tile's dL/dI is held with rows
+// padded to TILE + 4 floats (16-byte aligned rows).
 template <int TILE, int CH>
 struct BwdSmem {
   static constexpr int NW = (TILE / 8) * (TILE / 8);
+  static constexpr int NH = 2 * NW;  // 8 x 4 half-blocks per tile
+  static constexpr int GS = TILE + 4;
   float4 s0[CH], s1[CH], s2[CH], sc[CH];
   uint32_t sg[CH];
-  float sp[NW][6][CH];
-  int hitlist[NW][CH];
+  alignas(16) float G[TILE * GS];
+  int units[NW][CH * NH / NW];  // per warp: the hit (Gaussian, half-block) pairs it tested, (j << 4) | hb
+  int nunits[NW + 1];           // their counts, then offsets
+  unsigned char hmask[CH];      // per Gaussian: which half-blocks were hit (bit hb)
+  float sp[NH][6][CH];          // per (half-block, Gaussian): the six pixel moments
 };
 
+// Backward of one (slice s, tile t) of item a.  The tile is cut into 8 x 4
+// half-blocks; every (staged Gaussian, half-block) pair whose ellipse touches
+// the half-block is a unit of work, and the CTA's threads take the units of a
+// chunk round-robin, so all warps get the same share whatever the Gaussians'
+// layout.  A thread sums, over its unit's 32 pixels, the six moments
+//     sum G E {1, dx, dy, dx^2, dx dy, dy^2}      (E the Gaussian's exponential,
+// G = dL/dI, d = pixel - mu_2d), row by row with two pixels per packed
+// instruction; no unit is shared, so nothing is reduced across lanes.  The
+// per-half-block moments of a Gaussian are summed in a fixed order and folded
+// into its 10 accumulators (atomics) or written as a per-pair partial
+// (deterministic mode).
 template <int TILE, int CH, int EXPM, bool DET>
 __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, const SliceRec* __restrict__ rec,
                                          const uint32_t* __restrict__ vals, const uint32_t* __restrict__ emit_gid,
                                          const uint2* __restrict__ ranges, float* __restrict__ accum,
                                          float4* __restrict__ partial, BwdSmem<TILE, CH>& sm) {
   constexpr int NW = BwdSmem<TILE, CH>::NW;
+  constexpr int NH = BwdSmem<TILE, CH>::NH;
+  constexpr int GS = BwdSmem<TILE, CH>::GS;
   constexpr int NT = NW * 32;
+  constexpr int ROUNDS = CH * NH / NT;  // test rounds per chunk
+  static_assert((CH * NH) % NT == 0 && NH <= 8 && (NH & (NH - 1)) == 0, "tile / chunk shape");
   const uint2 rg = ranges[a.key_base + (uint32_t)local_key];
   if (rg.y <= rg.x) return;  // uniform over the CTA
   const int T = a.TX * a.TY;
   const int s = local_key / T, t = local_key - s * T;
   const int ty = t / a.TX, tx = t - ty * a.TX;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int grp = lane >> 3, row = lane & 7;
-  const unsigned gmask = 0xffu << (grp * 8);
-  const float bx = (float)((warp % (TILE / 8)) * 8), by = (float)((warp / (TILE / 8)) * 8);
-  const float pyr = by + (float)row + 0.5f;
-  const float cxb = bx + 4.0f;
   const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
   const float zsv = a.zorig[s];
-  int* list = sm.hitlist[warp];
-  const bool rb2 = (row >> 2) & 1, rb1 = (row >> 1) & 1, rb0 = row & 1;
-  const int vidx = 3 * (int)rb2 + 2 * (int)rb1 + (int)rb0;  // moment this lane holds after the butterfly
-  const bool vvalid = 2 * (int)rb1 + (int)rb0 < 3;
-  float2 G[4];  // dL/dI of pixels (2p, 2p + 1) of the lane's row
-  {
-    const int py = ty * TILE + (int)by + row;
-    const int px0 = tx * TILE + (int)bx;
-    float g8[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p)
-      g8[p] = (py < a.H && px0 + p < a.W) ? a.dL_dI[((int64_t)s * a.H + py) * a.W + px0 + p] : 0.0f;
-#pragma unroll
-    for (int p = 0; p < 4; ++p) G[p] = make_float2(g8[2 * p], g8[2 * p + 1]);
+  // the tile's dL/dI (zero outside the image)
+  for (int i = threadIdx.x; i < TILE * TILE; i += NT) {
+    const int yy = i / TILE, xx = i - yy * TILE;
+    const int py = ty * TILE + yy, px = tx * TILE + xx;
+    sm.G[yy * GS + xx] = (py < a.H && px < a.W) ? a.dL_dI[((int64_t)s * a.H + py) * a.W + px] : 0.0f;
   }
   for (uint32_t base = rg.x; base < rg.y; base += CH) {
     const int cnt = (int)min((uint32_t)CH, rg.y - base);
@@ -255,62 +275,105 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
       sm.sc[j] = a3;
       sm.sg[j] = g;
     }
-    for (int i = threadIdx.x; i < NW * 6 * CH; i += NT) (&sm.sp[0][0][0])[i] = 0.0f;
     __syncthreads();
-    int nh = 0;
-    for (int jb = 0; jb < cnt; jb += 32) nh += block_hits(sm.s0, sm.s1, sm.sc, jb, cnt, bx, by, a.k2, lane, list + nh);
-    {
-      for (int h = grp; h < nh; h += 4) {
-        const int jj = list[h];
-        const float4 g0 = sm.s0[jj], g1 = sm.s1[jj];
-        const float dy = pyr - g0.y;
-        const float u = g1.y * dy;
-        const float dxc = cxb - g0.x;
-        const float A = fmaf(dxc, fmaf(g1.x, dxc, u), g1.z * dy * dy);
-        const float Bq = fmaf(2.0f * g1.x, dxc, u);
-        // row sums about the centre column: S0 = sum G E, S1 = sum q G E, S2 = sum q^2 G E,
-        // kept as two interleaved partial sums (even / odd pixels) and added at the end
-        const float2 C2 = make_float2(g1.x, g1.x), B2 = make_float2(Bq, Bq), A2 = make_float2(A, A);
+    // test every (Gaussian, half-block) pair; pair i = j * NH + hb, so the NH
+    // tests of one Gaussian sit in NH consecutive lanes
+    int nu = 0;
+    int* units = sm.units[warp];
+#pragma unroll 1
+    for (int r = 0; r < ROUNDS; ++r) {
+      const int i = (r * NW + warp) * 32 + lane;
+      const int j = i / NH, hb = i & (NH - 1);
+      bool hit = false;
+      if (j < cnt) {
+        const float bxf = (float)(((hb >> 1) % (TILE / 8)) * 8);
+        const float byf = (float)(((hb >> 1) / (TILE / 8)) * 8 + 4 * (hb & 1));
+        hit = rect_hit(sm.s0[j], sm.s1[j], sm.sc[j], bxf + 0.5f, bxf + 7.5f, byf + 0.5f, byf + 3.5f, a.k2);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (hit) units[nu + __popc(m & ((1u << lane) - 1u))] = (j << 4) | hb;
+      if ((lane & (NH - 1)) == 0 && j < CH) sm.hmask[j] = (unsigned char)((m >> lane) & ((1u << NH) - 1u));
+      nu += __popc(m);
+    }
+    if (lane == 0) sm.nunits[warp] = nu;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int off = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const int c = sm.nunits[w];
+        sm.nunits[w] = off;
+        off += c;
+      }
+      sm.nunits[NW] = off;
+    }
+    __syncthreads();
+    const int total = sm.nunits[NW];
+    for (int u = threadIdx.x; u < total; u += NT) {
+      int w = 0;
+#pragma unroll
+      for (int k = 1; k < NW; ++k) w += (u >= sm.nunits[k]);
+      const int code = sm.units[w][u - sm.nunits[w]];
+      const int jj = code >> 4, hb = code & 15;
+      const float4 g0 = sm.s0[jj], g1 = sm.s1[jj];
+      const float c0 = g1.x, c1 = g1.y, c2 = g1.z;
+      const int hbx = ((hb >> 1) % (TILE / 8)) * 8, hby = ((hb >> 1) / (TILE / 8)) * 8 + 4 * (hb & 1);
+      const float dxc = (float)hbx + 4.0f - g0.x, dy0 = (float)hby + 0.5f - g0.y;
+      // row r of the half-block: exponent A(r) + B(r) q + c0 q^2 along the row,
+      // q the offset from the half-block's centre column
+      const float A0 = fmaf(dxc, fmaf(c0, dxc, c1 * dy0), c2 * dy0 * dy0);
+      const float A1 = fmaf(c1, dxc, 2.0f * c2 * dy0);
+      const float B0 = fmaf(2.0f * c0, dxc, c1 * dy0);
+      const float2 C2 = make_float2(c0, c0);
+      float M00 = 0.f, M10 = 0.f, M20 = 0.f, M01 = 0.f, M11 = 0.f, M02 = 0.f;
+      const float* Gr = sm.G + hby * GS + hbx;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float rf = (float)r;
+        const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
+        const float B = fmaf(c1, rf, B0);
+        const float2 A2 = make_float2(A, A), B2 = make_float2(B, B);
+        const float4 ga = *reinterpret_cast<const float4*>(Gr + r * GS);
+        const float4 gb = *reinterpret_cast<const float4*>(Gr + r * GS + 4);
+        const float2 Gp[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w), make_float2(gb.x, gb.y),
+                              make_float2(gb.z, gb.w)};
         float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           const float qa = (float)(2 * p) - 3.5f, qb = (float)(2 * p + 1) - 3.5f;
           const float2 q = make_float2(qa, qb);
-          const float2 gE = __fmul2_rn(G[p], pair_exp2<EXPM>(C2, B2, A2, q));
+          const float2 gE = __fmul2_rn(Gp[p], pair_exp2<EXPM>(C2, B2, A2, q));
           P0 = __fadd2_rn(P0, gE);
           P1 = __ffma2_rn(q, gE, P1);
           P2 = __ffma2_rn(make_float2(qa * qa, qb * qb), gE, P2);
         }
         const float S0 = P0.x + P0.y, S1 = P1.x + P1.y, S2 = P2.x + P2.y;
-        // this row's six moments (dx = dxc + q): sum G E {1, dx, dy, dx^2, dx dy, dy^2}
-        const float mxr = fmaf(dxc, S0, S1);
-        const float v0 = S0, v1 = mxr, v2 = S0 * dy;
-        const float v3 = fmaf(dxc, fmaf(dxc, S0, 2.0f * S1), S2), v4 = mxr * dy, v5 = v2 * dy;
-        // sum over the group's 8 rows, transposed butterfly: each level halves the
-        // values a lane carries; lane (b2 b1 b0) ends with moment 3 b2 + 2 b1 + b0
-        float k0 = rb2 ? v3 : v0, k1 = rb2 ? v4 : v1, k2 = rb2 ? v5 : v2;
-        k0 += __shfl_xor_sync(gmask, rb2 ? v0 : v3, 4);
-        k1 += __shfl_xor_sync(gmask, rb2 ? v1 : v4, 4);
-        k2 += __shfl_xor_sync(gmask, rb2 ? v2 : v5, 4);
-        float q0 = rb1 ? k2 : k0, q1 = rb1 ? 0.0f : k1;
-        q0 += __shfl_xor_sync(gmask, rb1 ? k0 : k2, 2);
-        q1 += __shfl_xor_sync(gmask, rb1 ? k1 : 0.0f, 2);
-        float r = rb0 ? q1 : q0;
-        r += __shfl_xor_sync(gmask, rb0 ? q0 : q1, 1);
-        if (vvalid) sm.sp[warp][vidx][jj] = r;
+        M00 += S0;
+        M10 += S1;
+        M20 += S2;
+        M01 = fmaf(rf, S0, M01);
+        M11 = fmaf(rf, S1, M11);
+        M02 = fmaf(rf * rf, S0, M02);
       }
-      __syncwarp();
+      // moments in d = (dxc + q, dy0 + r)
+      float* sp = &sm.sp[hb][0][jj];
+      sp[0 * CH] = M00;
+      sp[1 * CH] = fmaf(dxc, M00, M10);
+      sp[2 * CH] = fmaf(dy0, M00, M01);
+      sp[3 * CH] = fmaf(dxc, fmaf(dxc, M00, 2.0f * M10), M20);
+      sp[4 * CH] = fmaf(dxc, fmaf(dy0, M00, M01), fmaf(dy0, M10, M11));
+      sp[5 * CH] = fmaf(dy0, fmaf(dy0, M00, 2.0f * M01), M02);
     }
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += NT) {
-      float m[6];
+      float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      const unsigned hm = sm.hmask[j];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        float acc = 0.f;
+      for (int hb = 0; hb < NH; ++hb)
+        if ((hm >> hb) & 1u) {
 #pragma unroll
-        for (int w = 0; w < NW; ++w) acc += sm.sp[w][k][j];
-        m[k] = acc;
-      }
+          for (int k = 0; k < 6; ++k) m[k] += sm.sp[hb][k][j];
+        }
       const float4 g0 = sm.s0[j], g1 = sm.s1[j], g2 = sm.s2[j];
       const float at = g0.z;
       const float C00 = g1.w, C01 = g2.z, C11 = g0.w;
