@@ -5,8 +5,9 @@ Workload (one step = the whole hot path): 500k Gaussians in a 1024 x 1024 x 256
 light-sheet-shaped volume (z-scale 3x the xy-scale, log-normal intensities),
 sigma_z = 3; each step renders a random batch of 16 of the 256 slices
 (K-pre, pair binning, radix sort, K-range, K-fwd), takes the MSE against the
-same slices of a seeded 256-slice target stack (K-loss), and runs the backward
-(re-binning, K-bwd, K-bwd-pre) to gradients of all 11 parameters per Gaussian.
+same slices of a seeded 256-slice target stack (K-loss), runs the backward
+(K-bwd on the forward's bins, K-bwd-pre) to gradients of all 11 parameters per
+Gaussian, and applies the Adam update with the paper's learning rates.
 Inputs are synthetic (seeded); the target stack is rendered once, untimed,
 from a second seeded set of the same distribution.
 
@@ -38,7 +39,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+bwd Gaussian-pixel evals/s"
 UNIT = "evals/s"
 WORKLOAD = {"workload": "microscopy fit step: 500k Gaussians, 1024x1024x256 volume, sigma_z=3, "
-                        "random batch of 16 slices per step, fwd + MSE + bwd",
+                        "random batch of 16 slices per step, fwd + MSE + bwd + Adam update",
             "n_gaussians": 500_000, "slice_hw": [1024, 1024], "n_planes": 256, "slices_per_step": 16,
             "sigma_z": 3.0, "eps": 1e-6, "l2": "flushed between steps (256 MiB write)"}
 N, H, W, DEPTH, S, SIGMA = 500_000, 1024, 1024, 256, 16, 3.0
@@ -301,8 +302,13 @@ def run_native(args, rank, world):
     g, gs, target = make_workload(B, synth, torch, dev, ctx)
     batches = step_batches(synth, rank, args.warmup + args.steps)
     zs = [synth.slice_positions(b) for b in batches]
-    evals = [B.gp_count_evals(ctx, gs, z, H, W, SIGMA) for z in zs]
-    log(f"setup {time.perf_counter() - t_setup:.1f}s; evals/step (fwd) ~{np.mean(evals):.3e}")
+    # a second context counts the algorithmic evaluations of every step on the
+    # parameters that step renders (the Adam update moves them between steps)
+    cctx = B.Context(dev_index, deterministic=args.det, tile=args.tile)
+    evals0 = [B.gp_count_evals(cctx, gs, z, H, W, SIGMA) for z in zs]  # initial parameters (e2e loop)
+    log(f"setup {time.perf_counter() - t_setup:.1f}s; evals/step (fwd) ~{np.mean(evals0):.3e}")
+    host_params = [t.cpu().pin_memory() for t in (gs.mu, gs.scale, gs.quat, gs.alpha)]
+    opt = B.Adam(ctx, gs, total_steps=30000, mu_extent=float(max(H, W)))
     I = torch.empty(S, H, W, device=dev)
     G = torch.empty(S, H, W, device=dev)
     loss = torch.zeros(1, device=dev)
@@ -314,6 +320,7 @@ def run_native(args, rank, world):
         B.gp_render_slices(ctx, gs, zs[k], H, W, SIGMA, out=I)
         B.gp_mse_grad(ctx, I, target, t_index=batches[k], dL_dI=G, loss=loss)
         B.gp_render_backward(ctx, gs, zs[k], H, W, SIGMA, G, grads=grads)
+        opt.step(gs, grads)
 
     for k in range(args.warmup):
         flush.zero_()
@@ -337,11 +344,15 @@ def run_native(args, rank, world):
     torch.cuda.synchronize()
     launches0 = int(B.lib.gp_launch_count())
     clocks.start()
-    evs = []
+    evs, ev_steps = [], []
+    count_launches = 0
     wall0 = time.perf_counter()
     tw0 = time.time()
     for k in range(args.warmup, args.warmup + args.steps):
         flush.zero_()
+        lc = int(B.lib.gp_launch_count())
+        ev_steps.append(B.gp_count_evals(cctx, gs, zs[k], H, W, SIGMA))  # outside the timed events
+        count_launches += int(B.lib.gp_launch_count()) - lc
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         step(k)
@@ -353,12 +364,11 @@ def run_native(args, rank, world):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    launches = int(B.lib.gp_launch_count()) - launches0
+    launches = int(B.lib.gp_launch_count()) - launches0 - count_launches
     phases = ctx.timing_read()
     ctx.timing(False)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     t_total = sum(step_ms) * 1e-3
-    ev_steps = evals[args.warmup:]
     my_evals = 2.0 * sum(ev_steps)
     t_total, tot_evals = reduce_timing(t_total, my_evals, device=dev if dist else None)
     value = tot_evals / t_total
@@ -377,15 +387,16 @@ def run_native(args, rank, world):
     traffic, traffic_note = recorded_traffic(f"k_raster_{dom}_blk") if default_cfg else \
         (None, "recorded for the default configuration only")
 
-    # end to end through host buffers: parameters and the batch's target slices
-    # in (pinned host -> device), loss and gradients out (device -> pinned host)
-    host_params = [t.cpu().pin_memory() for t in (gs.mu, gs.scale, gs.quat, gs.alpha)]
-    host_target = target[:S].cpu().pin_memory()
-    host_grads = [torch.empty(t.shape, pin_memory=True) for t in grads]
+    # end to end through host buffers: every step uploads the parameters and the
+    # batch's 16 target slices (pinned host -> device), runs the step (render,
+    # loss, backward, Adam) and reads back the loss and the updated parameters
+    # (device -> pinned host)
+    host_stack = target.cpu().pin_memory()
+    host_out = [torch.empty(t.shape, pin_memory=True) for t in (gs.mu, gs.scale, gs.quat, gs.alpha)]
     host_loss = torch.empty(1, pin_memory=True)
     tgt_dev = torch.empty(S, H, W, device=dev)
-    h2d = sum(t.numel() * 4 for t in host_params) + host_target.numel() * 4
-    d2h = sum(t.numel() * 4 for t in host_grads) + 4
+    h2d = sum(t.numel() * 4 for t in host_params) + S * H * W * 4
+    d2h = sum(t.numel() * 4 for t in host_out) + 4
     e2e_ms = []
     for k in range(args.warmup, args.warmup + args.steps):
         flush.zero_()
@@ -393,17 +404,20 @@ def run_native(args, rank, world):
         e0.record(stream)
         for d, h in zip((gs.mu, gs.scale, gs.quat, gs.alpha), host_params):
             d.copy_(h, non_blocking=True)
-        tgt_dev.copy_(host_target, non_blocking=True)
+        for j, si in enumerate(batches[k]):
+            tgt_dev[j].copy_(host_stack[int(si)], non_blocking=True)
         B.gp_render_slices(ctx, gs, zs[k], H, W, SIGMA, out=I)
         B.gp_mse_grad(ctx, I, tgt_dev, dL_dI=G, loss=loss)
         B.gp_render_backward(ctx, gs, zs[k], H, W, SIGMA, G, grads=grads)
-        for h, d in zip(host_grads, grads):
+        opt.step(gs, grads)
+        for h, d in zip(host_out, (gs.mu, gs.scale, gs.quat, gs.alpha)):
             h.copy_(d, non_blocking=True)
         host_loss.copy_(loss, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_value = world * my_evals / (sum(e2e_ms) * 1e-3)
+    # every e2e step renders the initial parameters again (uploaded each step)
+    e2e_value = world * 2.0 * sum(evals0[args.warmup:]) / (sum(e2e_ms) * 1e-3)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -350,6 +350,45 @@ GP_API gp_status gp_serve_stats_get(gp_server* server, gp_serve_stats* out);
 /* Stops the workers after their current requests; still-queued requests are dropped. */
 GP_API gp_status gp_serve_close(gp_server* server);
 
+/* ------------------------------------------------------------- fit loop
+ * The parameter update of the fit loop (Sec. 5.1: Adam for 30k iterations with
+ * initial learning rates 6e-4 position, 2e-2 intensity, 2e-3 scale, 1e-3
+ * rotation, each decaying exponentially to 0.1 of its initial value):
+ *     lr_t = lr_0 * final_ratio^(k / total_steps),  k = min(t - 1, total_steps),
+ *     m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+ *     theta <- theta - lr_t (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+ * With log_scale_logit_alpha (default 1) the scale and the intensity are
+ * optimised as log s and logit alpha (the Gaussian-splatting parameterisation
+ * the paper builds on; the renderer still reads linear s and alpha, which the
+ * step writes back), so s stays positive and alpha in (0, 1).  The position
+ * rate is multiplied by mu_extent (rates relative to the scene extent). */
+typedef struct {
+  float lr_mu, lr_scale, lr_quat, lr_alpha;
+  float mu_extent;          /* default 1 */
+  float lr_final_ratio;     /* default 0.1 */
+  int64_t total_steps;      /* default 30000 */
+  float beta1, beta2, eps;  /* defaults 0.9, 0.999, 1e-15 */
+  int log_scale_logit_alpha;
+} gp_adam_cfg;
+
+/* Fills *cfg with the defaults above (the paper's rates).  GP_ERR_ARG if NULL. */
+GP_API gp_status gp_adam_default(gp_adam_cfg* cfg);
+/* Floats of optimiser state for n Gaussians (DEVICE, caller-owned): 26 n,
+ * laid out [26][n] -- first moments (11 rows: mu xyz, scale xyz, quat wxyz,
+ * alpha), second moments (11 rows), raw log s (3 rows) and logit alpha. */
+GP_API int64_t gp_adam_state_floats(int64_t n);
+/* Zeroes the moments and sets the raw parameters from the current scale and
+ * alpha (alpha clamped to [1e-6, 1 - 1e-6] before the logit).  Asynchronous. */
+GP_API gp_status gp_adam_init(gp_ctx* ctx, const gp_adam_cfg* cfg, int64_t n, const float* scale,
+                              const float* alpha, float* state, void* stream);
+/* Step t (1, 2, ...): updates mu [3n], scale [3n], quat [4n] (16-byte aligned)
+ * and alpha [n] in place (DEVICE) from the gradients d_* (DEVICE, as written by
+ * gp_render_backward) and the state.  GP_ERR_ARG for t < 1, bad rates or NULL
+ * pointers.  Asynchronous on `stream`. */
+GP_API gp_status gp_adam_step(gp_ctx* ctx, const gp_adam_cfg* cfg, int64_t t, int64_t n, float* mu, float* scale,
+                              float* quat, float* alpha, const float* d_mu, const float* d_scale,
+                              const float* d_quat, const float* d_alpha, float* state, void* stream);
+
 /* Phase timing.  When enabled, every call records a CUDA event pair on its
  * stream around each phase below; gp_timing_read synchronises those events,
  * returns the summed milliseconds and launch counts per phase since the last
@@ -361,7 +400,8 @@ GP_API gp_status gp_serve_close(gp_server* server);
 #define GP_PHASE_LOSS 4       /* K-loss */
 #define GP_PHASE_VOX_FWD 5    /* voxelizer forward rasteriser */
 #define GP_PHASE_VOX_BWD 6    /* voxelizer backward rasteriser + gradient finish */
-#define GP_NUM_PHASES 7
+#define GP_PHASE_OPT 7        /* gp_adam_step */
+#define GP_NUM_PHASES 8
 GP_API gp_status gp_timing_enable(gp_ctx* ctx, int enable);
 GP_API gp_status gp_timing_read(gp_ctx* ctx, double* ms /* [GP_NUM_PHASES] */,
                                 int64_t* launches /* [GP_NUM_PHASES] */,

@@ -37,12 +37,12 @@ EXPORTS = (
     "gp_batch_plan", "gp_batch_run", "gp_batch_wait", "gp_batch_info", "gp_batch_destroy",
     "gp_serve_open", "gp_serve_load_set", "gp_serve_submit", "gp_serve_poll", "gp_serve_stats_get",
     "gp_serve_close", "gp_view_from_axis", "gp_render_slices_view", "gp_render_backward_view",
-    "gp_count_evals_view",
+    "gp_count_evals_view", "gp_adam_default", "gp_adam_state_floats", "gp_adam_init", "gp_adam_step",
 )
 GP_REQ_SLICE, GP_REQ_STACK, GP_REQ_VOXELIZE = 0, 1, 2
 GP_BATCH_AUTOTUNE = 1
-GP_NUM_PHASES = 7
-PHASES = ("bin", "fwd", "bwd", "bwd_pre", "loss", "vox_fwd", "vox_bwd")
+GP_NUM_PHASES = 8
+PHASES = ("bin", "fwd", "bwd", "bwd_pre", "loss", "vox_fwd", "vox_bwd", "opt")
 
 
 class GPError(RuntimeError):
@@ -83,6 +83,13 @@ class gp_batch_item(ctypes.Structure):
                 ("out", ctypes.c_void_p), ("target", ctypes.c_void_p), ("dL_dI", ctypes.c_void_p),
                 ("d_mu", ctypes.c_void_p), ("d_scale", ctypes.c_void_p), ("d_quat", ctypes.c_void_p),
                 ("d_alpha", ctypes.c_void_p), ("loss", ctypes.c_void_p), ("view", ctypes.c_void_p)]
+
+
+class gp_adam_cfg(ctypes.Structure):
+    _fields_ = [("lr_mu", ctypes.c_float), ("lr_scale", ctypes.c_float), ("lr_quat", ctypes.c_float),
+                ("lr_alpha", ctypes.c_float), ("mu_extent", ctypes.c_float), ("lr_final_ratio", ctypes.c_float),
+                ("total_steps", ctypes.c_int64), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("log_scale_logit_alpha", ctypes.c_int)]
 
 
 class gp_serve_cfg(ctypes.Structure):
@@ -151,6 +158,10 @@ def _load():
         "gp_render_slices_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, P, P],
         "gp_render_backward_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, P, P, P, P, P, P],
         "gp_count_evals_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, ctypes.POINTER(I64)],
+        "gp_adam_default": [ctypes.POINTER(gp_adam_cfg)],
+        "gp_adam_state_floats": [I64],
+        "gp_adam_init": [P, ctypes.POINTER(gp_adam_cfg), I64, P, P, P, P],
+        "gp_adam_step": [P, ctypes.POINTER(gp_adam_cfg), I64, I64, P, P, P, P, P, P, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -160,6 +171,7 @@ def _load():
     lib.gp_workspace_bytes.restype = I64
     lib.gp_launch_count.restype = I64
     lib.gp_fma_probe_threads.restype = I64
+    lib.gp_adam_state_floats.restype = I64
     return lib
 
 
@@ -546,6 +558,37 @@ def gp_exp2_eval(ctx, x, mode=GP_EXP_POLY, y=None, stream=None):
     st = lib.gp_exp2_eval(ctx.h, _dev(x, "x"), _dev(y, "y", shape=x.shape), x.numel(), int(mode), _stream(stream))
     ctx.check(st, "gp_exp2_eval")
     return y
+
+
+class Adam:
+    """The fit loop's parameter update on the device (gp_adam_*): Adam with the
+    paper's learning rates, decaying exponentially, on log s and logit alpha by
+    default.  Owns its [26, n] state tensor; step() updates a GaussianSet in place."""
+
+    def __init__(self, ctx, gs, total_steps=30000, mu_extent=1.0, log_scale_logit_alpha=True, **rates):
+        self.ctx = ctx
+        self.cfg = gp_adam_cfg()
+        lib.gp_adam_default(ctypes.byref(self.cfg))
+        self.cfg.total_steps = int(total_steps)
+        self.cfg.mu_extent = float(mu_extent)
+        self.cfg.log_scale_logit_alpha = int(bool(log_scale_logit_alpha))
+        for k, v in rates.items():
+            setattr(self.cfg, k, float(v))
+        self.n = gs.n
+        self.state = torch.empty(int(lib.gp_adam_state_floats(self.n)), device=gs.alpha.device)
+        self.t = 0
+        ctx.check(lib.gp_adam_init(ctx.h, ctypes.byref(self.cfg), self.n, _dev(gs.scale, "scale"),
+                                   _dev(gs.alpha, "alpha"), _dev(self.state, "state"), _stream(None)),
+                  "gp_adam_init")
+
+    def step(self, gs, grads, stream=None):
+        self.t += 1
+        d_mu, d_s, d_q, d_a = grads
+        self.ctx.check(lib.gp_adam_step(self.ctx.h, ctypes.byref(self.cfg), self.t, self.n, _dev(gs.mu, "mu"),
+                                        _dev(gs.scale, "scale"), _dev(gs.quat, "quat"), _dev(gs.alpha, "alpha"),
+                                        _dev(d_mu, "d_mu"), _dev(d_s, "d_scale"), _dev(d_q, "d_quat"),
+                                        _dev(d_a, "d_alpha"), _dev(self.state, "state"), _stream(stream)),
+                       "gp_adam_step")
 
 
 class SliceRender(torch.autograd.Function):
