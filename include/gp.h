@@ -172,14 +172,28 @@ GP_API gp_status gp_render_backward_view(gp_ctx* ctx, const gp_set* set, const g
 GP_API gp_status gp_count_evals_view(gp_ctx* ctx, const gp_set* set, const gp_view* view, const float* z, int S,
                                      int H, int W, float sigma_z, int64_t* evals);
 
-/* Mean squared error of a rendered stack against target slices (the loss the
- * operator is driven with here; the paper's L1 + D-SSIM of Eq. 11 is not
- * built).  I: [S][H][W] DEVICE.  T: DEVICE target stack of at least
+/* Mean squared error of a rendered stack against target slices (the
+ * benchmarked fit step's loss; the paper's own L1 + D-SSIM is
+ * gp_l1_dssim_grad).  I: [S][H][W] DEVICE.  T: DEVICE target stack of at least
  * max(t_index)+1 slices of H*W.  t_index: HOST array of S slice indices into T,
  * or NULL for T[s] = slice s.  Writes dL/dI = 2 (I - T) / (S H W) (DEVICE) and,
  * if loss != NULL, L = mean (I - T)^2 into loss[0] (DEVICE, fp32). */
 GP_API gp_status gp_mse_grad(gp_ctx* ctx, const float* I, const float* T, const int* t_index,
                       int S, int H, int W, float* dL_dI, float* loss, void* stream);
+
+/* The paper's photometric loss (Eq. 11, lambda = 0.2 in Sec. 5.1):
+ *     L = L1 + lambda (1 - SSIM),   L1 = mean |I - T|,
+ * SSIM the mean over pixels and slices of the per-slice structural similarity
+ * (Wang et al. 2004: 11 x 11 Gaussian window of standard deviation 1.5,
+ * C1 = 0.01^2, C2 = 0.03^2 for data range 1, zero padding at the borders).
+ * I, T, t_index and dL_dI as in gp_mse_grad; dL/dI is fully overwritten (the
+ * L1 term takes sign(0) = 0).  If loss != NULL, writes (L, L1, mean SSIM) into
+ * loss[0..2] (DEVICE, fp32; sums taken in double in a fixed order).  Scratch:
+ * 12 bytes per pixel in the context's workspace.  GP_ERR_ARG for S < 0, H or W
+ * <= 0, lambda < 0 or non-finite, NULL pointers, a negative index, S > 65535 or
+ * S*H*W > 2^31.  Asynchronous on `stream`. */
+GP_API gp_status gp_l1_dssim_grad(gp_ctx* ctx, const float* I, const float* T, const int* t_index, int S, int H,
+                                  int W, float lambda, float* dL_dI, float* loss, void* stream);
 
 /* Allocation-free variant of gp_mse_grad (the paper has no counterpart: this is a
  * deployment convenience).  For callers that must not allocate device memory:

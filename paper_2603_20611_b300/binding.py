@@ -38,6 +38,7 @@ EXPORTS = (
     "gp_serve_open", "gp_serve_load_set", "gp_serve_submit", "gp_serve_poll", "gp_serve_stats_get",
     "gp_serve_close", "gp_view_from_axis", "gp_render_slices_view", "gp_render_backward_view",
     "gp_count_evals_view", "gp_adam_default", "gp_adam_state_floats", "gp_adam_init", "gp_adam_step",
+    "gp_l1_dssim_grad",
 )
 GP_REQ_SLICE, GP_REQ_STACK, GP_REQ_VOXELIZE = 0, 1, 2
 GP_BATCH_AUTOTUNE = 1
@@ -159,6 +160,7 @@ def _load():
         "gp_render_backward_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, P, P, P, P, P, P],
         "gp_count_evals_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, ctypes.POINTER(I64)],
         "gp_adam_default": [ctypes.POINTER(gp_adam_cfg)],
+        "gp_l1_dssim_grad": [P, P, P, P, I, I, I, F, P, P, P],
         "gp_adam_state_floats": [I64],
         "gp_adam_init": [P, ctypes.POINTER(gp_adam_cfg), I64, P, P, P, P],
         "gp_adam_step": [P, ctypes.POINTER(gp_adam_cfg), I64, I64, P, P, P, P, P, P, P, P, P, P],
@@ -356,6 +358,27 @@ def gp_mse_grad(ctx, I, T, t_index=None, dL_dI=None, loss=None, stream=None):
                          _dev(dL_dI, "dL_dI", shape=(S, H, W)),
                          None if loss is None else _dev(loss, "loss", shape=(1,)), _stream(stream))
     ctx.check(st, "gp_mse_grad")
+    return dL_dI, loss
+
+
+def gp_l1_dssim_grad(ctx, I, T, t_index=None, lam=0.2, dL_dI=None, loss=None, stream=None):
+    """The paper's loss L1 + lam (1 - SSIM) and dL/dI; loss (3 floats, device)
+    receives (L, L1, mean SSIM)."""
+    S, H, W = I.shape
+    if dL_dI is None:
+        dL_dI = torch.empty_like(I)
+    tid = None
+    if t_index is not None:
+        tid = np.ascontiguousarray(np.asarray(t_index, np.int32).reshape(-1))
+        if tid.shape[0] != S or T.dim() != 3 or T.shape[1:] != I.shape[1:] or int(tid.max(initial=0)) >= T.shape[0]:
+            raise ValueError("t_index needs one in-range entry per slice")
+    elif tuple(T.shape) != tuple(I.shape):
+        raise ValueError("T must match I when t_index is None")
+    st = lib.gp_l1_dssim_grad(ctx.h, _dev(I, "I"), _dev(T, "T"),
+                              None if tid is None else tid.ctypes.data_as(ctypes.c_void_p), S, H, W, float(lam),
+                              _dev(dL_dI, "dL_dI", shape=(S, H, W)),
+                              None if loss is None else _dev(loss, "loss", shape=(3,)), _stream(stream))
+    ctx.check(st, "gp_l1_dssim_grad")
     return dL_dI, loss
 
 
