@@ -302,6 +302,40 @@ GP_API gp_status gp_batch_info(gp_plan* plan, int64_t* pair_capacity, int* tile,
                                int* bwd_chunk, int64_t* device_bytes);
 GP_API gp_status gp_batch_destroy(gp_plan* plan);
 
+/* ---------------------------------------------------------------- codec
+ * The paper's storage path (Sec. 4, "Quantization and compression"): Gaussians
+ * in Morton (Z-order) of their quantised positions; positions normalised to
+ * the bounding box at pos_bits (1..15, typically 14) bits per axis; scales
+ * log-transformed and quantised to 12 bits over [ln min s, ln max s] (round to
+ * nearest in the log domain); quaternions normalised, folded to w >= 0 and
+ * quantised to 12 bits per component over [-1, 1]; intensities clamped to
+ * [0, 1] and quantised to 12 bits; each of the 11 attribute streams (x y z,
+ * s0 s1 s2, qw qx qy qz, alpha) holds the first code and then the differences
+ * of consecutive codes, zigzag-mapped (d >= 0 -> 2d, d < 0 -> -2d - 1) to
+ * uint16.  The entropy stage (LZMA) runs on the host over these streams.
+ * Affine quantisations round with separately rounded fp32 operations,
+ * code = floor((v - lo) * ((2^B - 1) / (hi - lo)) + 0.5) clamped; decoding
+ * returns the Gaussians in Morton order. */
+typedef struct {
+  int64_t n;
+  int pos_bits;
+  float lo[3], hi[3];           /* position bounding box */
+  double log_s_min, log_s_max;  /* scale range (natural logarithms) */
+} gp_codec_header;
+
+/* Encodes a set (DEVICE parameters; scale_mod is not applied) into streams
+ * (DEVICE uint16 [11][n], caller-owned) and fills *header (HOST).  If order is
+ * non-NULL (DEVICE uint32 [n]) it receives the input index of each encoded
+ * Gaussian.  Synchronous (one readback of the bounding box).  GP_ERR_ARG for
+ * pos_bits outside 1..15, NULL pointers, or a set with a non-finite parameter
+ * or a scale <= 0. */
+GP_API gp_status gp_encode(gp_ctx* ctx, const gp_set* set, int pos_bits, gp_codec_header* header,
+                           uint16_t* streams, uint32_t* order, void* stream);
+/* Decodes streams (DEVICE [11][n]) into mu [3n], scale [3n], quat [4n]
+ * (16-byte aligned) and alpha [n] (DEVICE, caller-owned).  Asynchronous. */
+GP_API gp_status gp_decode(gp_ctx* ctx, const gp_codec_header* header, const uint16_t* streams, float* mu,
+                           float* scale, float* quat, float* alpha, void* stream);
+
 /* ------------------------------------------------------------------- serving
  * A request loop over resident Gaussian sets (deployment form; the paper has no
  * server).  Requests -- one slice, a stack of slices, or a voxelize -- enter a
@@ -355,6 +389,11 @@ typedef struct gp_server gp_server;
 GP_API gp_status gp_serve_open(gp_ctx* ctx, const gp_serve_cfg* cfg, gp_server** out);
 /* Registers a resident set (caller keeps its device memory valid); returns its id. */
 GP_API gp_status gp_serve_load_set(gp_server* server, const gp_set* set, int* set_id);
+/* Decodes an encoded set (gp_encode's header and DEVICE streams) into device
+ * memory owned by the server (freed by gp_serve_close) and registers it;
+ * returns its id.  Synchronous. */
+GP_API gp_status gp_serve_load_encoded(gp_server* server, const gp_codec_header* header, const uint16_t* streams,
+                                       float scale_mod, int* set_id);
 /* Queues a request (validated here: GP_ERR_ARG) and returns its ticket. */
 GP_API gp_status gp_serve_submit(gp_server* server, const gp_request* req, uint64_t* ticket);
 /* Waits up to timeout_ms for the ticket: GP_OK with *out filled (once per

@@ -8,7 +8,9 @@ no fallback: if the shared library is missing the import fails loudly.
 from __future__ import annotations
 
 import ctypes
+import lzma
 import os
+import struct
 
 import numpy as np
 import torch
@@ -38,7 +40,7 @@ EXPORTS = (
     "gp_serve_open", "gp_serve_load_set", "gp_serve_submit", "gp_serve_poll", "gp_serve_stats_get",
     "gp_serve_close", "gp_view_from_axis", "gp_render_slices_view", "gp_render_backward_view",
     "gp_count_evals_view", "gp_adam_default", "gp_adam_state_floats", "gp_adam_init", "gp_adam_step",
-    "gp_l1_dssim_grad",
+    "gp_l1_dssim_grad", "gp_encode", "gp_decode", "gp_serve_load_encoded",
 )
 GP_REQ_SLICE, GP_REQ_STACK, GP_REQ_VOXELIZE = 0, 1, 2
 GP_BATCH_AUTOTUNE = 1
@@ -84,6 +86,11 @@ class gp_batch_item(ctypes.Structure):
                 ("out", ctypes.c_void_p), ("target", ctypes.c_void_p), ("dL_dI", ctypes.c_void_p),
                 ("d_mu", ctypes.c_void_p), ("d_scale", ctypes.c_void_p), ("d_quat", ctypes.c_void_p),
                 ("d_alpha", ctypes.c_void_p), ("loss", ctypes.c_void_p), ("view", ctypes.c_void_p)]
+
+
+class gp_codec_header(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("pos_bits", ctypes.c_int), ("lo", ctypes.c_float * 3),
+                ("hi", ctypes.c_float * 3), ("log_s_min", ctypes.c_double), ("log_s_max", ctypes.c_double)]
 
 
 class gp_adam_cfg(ctypes.Structure):
@@ -161,6 +168,9 @@ def _load():
         "gp_count_evals_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, ctypes.POINTER(I64)],
         "gp_adam_default": [ctypes.POINTER(gp_adam_cfg)],
         "gp_l1_dssim_grad": [P, P, P, P, I, I, I, F, P, P, P],
+        "gp_encode": [P, SP, I, ctypes.POINTER(gp_codec_header), P, P, P],
+        "gp_decode": [P, ctypes.POINTER(gp_codec_header), P, P, P, P, P, P],
+        "gp_serve_load_encoded": [P, ctypes.POINTER(gp_codec_header), P, F, ctypes.POINTER(I)],
         "gp_adam_state_floats": [I64],
         "gp_adam_init": [P, ctypes.POINTER(gp_adam_cfg), I64, P, P, P, P],
         "gp_adam_step": [P, ctypes.POINTER(gp_adam_cfg), I64, I64, P, P, P, P, P, P, P, P, P, P],
@@ -492,6 +502,16 @@ class Server:
             raise GPError(st, "gp_serve_load_set")
         return sid.value
 
+    def load_encoded(self, hdr, streams, scale_mod=1.0):
+        """Registers a set decoded by the server from gp_encode output (the server owns the memory)."""
+        sid = ctypes.c_int()
+        sc = streams.contiguous()
+        st = lib.gp_serve_load_encoded(self.h, ctypes.byref(hdr), _dev(sc, "streams", torch.int16), float(scale_mod),
+                                       ctypes.byref(sid))
+        if st != GP_OK:
+            raise GPError(st, "gp_serve_load_encoded")
+        return sid.value
+
     def submit(self, kind, set_id, out, z=None, H=0, W=0, sigma_z=1.0, axis=2, X=0, Y=0, Z=0, view=None):
         r = gp_request()
         r.kind, r.set_id = int(kind), int(set_id)
@@ -581,6 +601,55 @@ def gp_exp2_eval(ctx, x, mode=GP_EXP_POLY, y=None, stream=None):
     st = lib.gp_exp2_eval(ctx.h, _dev(x, "x"), _dev(y, "y", shape=x.shape), x.numel(), int(mode), _stream(stream))
     ctx.check(st, "gp_exp2_eval")
     return y
+
+
+def gp_encode(ctx, gs, pos_bits=14, stream=None):
+    """(header, streams [11, n] int16 tensor holding uint16 codes, order [n] int32
+    tensor) of the paper's codec; streams are zigzag deltas in Morton order."""
+    hdr = gp_codec_header()
+    n = gs.n
+    dev = gs.alpha.device
+    streams = torch.empty(11, max(n, 1), dtype=torch.int16, device=dev)
+    order = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    ctx.check(lib.gp_encode(ctx.h, ctypes.byref(gs.c()), int(pos_bits), ctypes.byref(hdr),
+                            _dev(streams, "streams", torch.int16), _dev(order, "order", torch.int32),
+                            _stream(stream)), "gp_encode")
+    return hdr, streams[:, :n], order[:n]
+
+
+def gp_decode(ctx, hdr, streams, scale_mod=1.0, stream=None):
+    """GaussianSet decoded from a header and device streams (Morton order)."""
+    n = int(hdr.n)
+    dev = streams.device
+    quat = torch.empty(n, 4, device=dev)
+    gs = GaussianSet(torch.empty(n, 3, device=dev), torch.empty(n, 3, device=dev), quat,
+                     torch.empty(n, device=dev), scale_mod)
+    st = streams.contiguous()
+    ctx.check(lib.gp_decode(ctx.h, ctypes.byref(hdr), _dev(st, "streams", torch.int16), _dev(gs.mu, "mu"),
+                            _dev(gs.scale, "scale"), _dev(gs.quat, "quat"), _dev(gs.alpha, "alpha"),
+                            _stream(stream)), "gp_decode")
+    return gs
+
+
+_CODEC_HDR = struct.Struct("<qi3f3f2d")
+
+
+def encode_bytes(ctx, gs, pos_bits=14):
+    """The whole storage path: device quantisation and delta streams, then LZMA
+    on the host over the header and the little-endian uint16 streams."""
+    hdr, streams, _ = gp_encode(ctx, gs, pos_bits)
+    raw = _CODEC_HDR.pack(hdr.n, hdr.pos_bits, *hdr.lo, *hdr.hi, hdr.log_s_min, hdr.log_s_max)
+    body = streams.cpu().numpy().astype("<i2").tobytes()
+    return lzma.compress(raw + body)
+
+
+def decode_bytes(ctx, blob, device="cuda", scale_mod=1.0):
+    """Inverse of encode_bytes: LZMA on the host, then the device decode."""
+    raw = lzma.decompress(blob)
+    n, bits, lx, ly, lz, hx, hy, hz, l0, l1 = _CODEC_HDR.unpack_from(raw)
+    hdr = gp_codec_header(n, bits, (ctypes.c_float * 3)(lx, ly, lz), (ctypes.c_float * 3)(hx, hy, hz), l0, l1)
+    streams = torch.from_numpy(np.frombuffer(raw, "<i2", offset=_CODEC_HDR.size).reshape(11, n).copy()).to(device)
+    return hdr, gp_decode(ctx, hdr, streams, scale_mod)
 
 
 class Adam:

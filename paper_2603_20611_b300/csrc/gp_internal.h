@@ -49,6 +49,7 @@ struct BinBufs {
   DevBuf accum;      // backward: per-Gaussian accumulators
   DevBuf partial;    // backward, deterministic mode: per-pair partials
   DevBuf loss_tmp;
+  DevBuf codec;      // encode / decode scratch
 };
 
 // Adds k to the process-wide count of kernels this library launched.

@@ -410,7 +410,7 @@ gp_status gp_destroy(gp_ctx* ctx) {
   BinBufs& b = c->b;
   DevBuf* all[] = {&b.rec, &b.counts, &b.offsets, &b.total, &b.keys, &b.vals, &b.keys_alt, &b.vals_alt,
                    &b.emit_gid, &b.ranges, &b.scan_tmp, &b.sort_tmp, &b.zs, &b.zorder, &b.zorig,
-                   &b.accum, &b.partial, &b.loss_tmp};
+                   &b.accum, &b.partial, &b.loss_tmp, &b.codec};
   for (DevBuf* d : all) ws_release(c, *d);
   for (auto& e : c->events) {
     cudaEventDestroy(e.start);

@@ -57,6 +57,7 @@ struct gp_server {
   int device = 0;
   gp_serve_cfg cfg{};
   std::vector<gp_set> sets;
+  std::vector<void*> owned;  // device memory of sets decoded by the server
   std::vector<Worker> workers;
   std::mutex mu;
   std::condition_variable cv_work;   // workers wait for requests
@@ -301,6 +302,39 @@ gp_status gp_serve_load_set(gp_server* s, const gp_set* set, int* set_id) {
   return GP_OK;
 }
 
+gp_status gp_serve_load_encoded(gp_server* s, const gp_codec_header* header, const uint16_t* streams,
+                                float scale_mod, int* set_id) {
+  if (!s || !header || !set_id || header->n < 0 || !(scale_mod > 0.0f)) return GP_ERR_ARG;
+  const int64_t n = header->n;
+  gp_set set{};
+  set.n = n;
+  set.scale_mod = scale_mod;
+  void* mem = nullptr;
+  if (n > 0) {
+    if (cudaSetDevice(s->device) != cudaSuccess || cudaMalloc(&mem, (size_t)n * 11 * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return GP_ERR_OOM;
+    }
+    float* base = (float*)mem;  // quat first: 16-byte aligned
+    set.quat = base;
+    set.mu = base + 4 * n;
+    set.scale = base + 7 * n;
+    set.alpha = base + 10 * n;
+    gp_status st = gp_decode(s->owner, header, streams, (float*)set.mu, (float*)set.scale, (float*)set.quat,
+                             (float*)set.alpha, nullptr);
+    if (st == GP_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) st = GP_ERR_CUDA;
+    if (st != GP_OK) {
+      cudaFree(mem);
+      return st;
+    }
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->sets.push_back(set);
+  if (mem) s->owned.push_back(mem);
+  *set_id = (int)s->sets.size() - 1;
+  return GP_OK;
+}
+
 gp_status gp_serve_submit(gp_server* s, const gp_request* r, uint64_t* ticket) {
   if (!s || !ticket) return GP_ERR_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -379,6 +413,7 @@ gp_status gp_serve_close(gp_server* s) {
     }
     s->pending.clear();
   }
+  for (void* m : s->owned) cudaFree(m);
   delete s;
   return GP_OK;
 }
