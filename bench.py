@@ -178,6 +178,21 @@ def recorded_traffic(kernel):
     return None, "kernel not in the capture"
 
 
+def oblique_view(Wd, Hd, Dd, seed=8080):
+    """Seeded rotation R and translation t putting the volume centre at the image
+    centre on plane z_c = 0 (camera x_c = R x + t)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    q = rng.standard_normal(4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                  [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                  [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+    c = np.array([Wd / 2.0, Hd / 2.0, Dd / 2.0])
+    t = np.array([Wd / 2.0, Hd / 2.0, 0.0]) - R @ c
+    return R.astype(np.float32), t.astype(np.float32)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -302,10 +317,16 @@ def run_native(args, rank, world):
     g, gs, target = make_workload(B, synth, torch, dev, ctx)
     batches = step_batches(synth, rank, args.warmup + args.steps)
     zs = [synth.slice_positions(b) for b in batches]
+    view = None
+    if args.view == "oblique":
+        # a seeded rotation through the volume's centre; plane s sits at
+        # (s + 1/2) - DEPTH/2 along the rotated normal
+        view = oblique_view(W, H, DEPTH)
+        zs = [z - DEPTH / 2.0 for z in zs]
     # a second context counts the algorithmic evaluations of every step on the
     # parameters that step renders (the Adam update moves them between steps)
     cctx = B.Context(dev_index, deterministic=args.det, tile=args.tile)
-    evals0 = [B.gp_count_evals(cctx, gs, z, H, W, SIGMA) for z in zs]  # initial parameters (e2e loop)
+    evals0 = [B.gp_count_evals(cctx, gs, z, H, W, SIGMA, view=view) for z in zs]  # initial parameters (e2e loop)
     log(f"setup {time.perf_counter() - t_setup:.1f}s; evals/step (fwd) ~{np.mean(evals0):.3e}")
     host_params = [t.cpu().pin_memory() for t in (gs.mu, gs.scale, gs.quat, gs.alpha)]
     opt = B.Adam(ctx, gs, total_steps=30000, mu_extent=float(max(H, W)))
@@ -325,9 +346,9 @@ def run_native(args, rank, world):
             B.gp_mse_grad(ctx, I, T, t_index=t_index, dL_dI=G, loss=loss)
 
     def step(k):
-        B.gp_render_slices(ctx, gs, zs[k], H, W, SIGMA, out=I)
+        B.gp_render_slices(ctx, gs, zs[k], H, W, SIGMA, out=I, view=view)
         loss_grad(target, batches[k])
-        B.gp_render_backward(ctx, gs, zs[k], H, W, SIGMA, G, grads=grads)
+        B.gp_render_backward(ctx, gs, zs[k], H, W, SIGMA, G, grads=grads, view=view)
         opt.step(gs, grads)
 
     for k in range(args.warmup):
@@ -359,7 +380,7 @@ def run_native(args, rank, world):
     for k in range(args.warmup, args.warmup + args.steps):
         flush.zero_()
         lc = int(B.lib.gp_launch_count())
-        ev_steps.append(B.gp_count_evals(cctx, gs, zs[k], H, W, SIGMA))  # outside the timed events
+        ev_steps.append(B.gp_count_evals(cctx, gs, zs[k], H, W, SIGMA, view=view))  # outside the timed events
         count_launches += int(B.lib.gp_launch_count()) - lc
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -414,9 +435,9 @@ def run_native(args, rank, world):
             d.copy_(h, non_blocking=True)
         for j, si in enumerate(batches[k]):
             tgt_dev[j].copy_(host_stack[int(si)], non_blocking=True)
-        B.gp_render_slices(ctx, gs, zs[k], H, W, SIGMA, out=I)
+        B.gp_render_slices(ctx, gs, zs[k], H, W, SIGMA, out=I, view=view)
         loss_grad(tgt_dev, None)
-        B.gp_render_backward(ctx, gs, zs[k], H, W, SIGMA, G, grads=grads)
+        B.gp_render_backward(ctx, gs, zs[k], H, W, SIGMA, G, grads=grads, view=view)
         opt.step(gs, grads)
         for h, d in zip(host_out, (gs.mu, gs.scale, gs.quat, gs.alpha)):
             h.copy_(d, non_blocking=True)
@@ -438,6 +459,7 @@ def run_native(args, rank, world):
                 "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(WORKLOAD, exp=args.exp, deterministic=bool(args.det), tile=args.tile, loss=args.loss,
+                               view=args.view,
                                backward_bins="re-binned" if args.rebin else "reused from the step's forward",
                                parallelism="replicas" if world > 1 else "single"),
                 "slices_per_s": world * S * args.steps / t_total,
@@ -636,6 +658,62 @@ def run_serving(args):
     return 0
 
 
+def run_codec(args):
+    """Encode (device quantisation, Morton sort, delta streams) and decode of the
+    500k-Gaussian microscopy set, timed with CUDA events; throughput in
+    Gaussians/s and algorithmic bytes (44 B of parameters + 22 B of streams per
+    Gaussian) against the measured HBM copy bandwidth.  The host LZMA stage is
+    timed separately (wall clock)."""
+    import torch
+    from paper_2603_20611_b300 import binding as B
+    from paper_2603_20611_b300 import synth
+    torch.cuda.set_device(0)
+    ctx = B.Context(0)
+    g = microscopy_set(synth, 1002)
+    gs = B.GaussianSet.from_numpy(g, "cuda:0")
+    stream = torch.cuda.current_stream()
+    hdr, streams, _ = B.gp_encode(ctx, gs)
+    out = B.gp_decode(ctx, hdr, streams)
+    for _ in range(args.warmup):
+        B.gp_encode(ctx, gs)
+        B.gp_decode(ctx, hdr, streams)
+    torch.cuda.synchronize()
+    enc_ms, dec_ms = [], []
+    for _ in range(args.steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        hdr, streams, _ = B.gp_encode(ctx, gs)  # synchronous (bounding-box readback)
+        e1.record(stream)
+        B.gp_decode(ctx, hdr, streams)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        enc_ms.append(e0.elapsed_time(e1))
+        dec_ms.append(e1.elapsed_time(e2))
+    t0 = time.perf_counter()
+    blob = B.encode_bytes(ctx, gs)
+    t_host = time.perf_counter() - t0
+    n = g.n
+    peaks = measured_peaks() or {}
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    e_ms, d_ms = float(np.median(enc_ms)), float(np.median(dec_ms))
+    line = {"metric": "codec Gaussians/s (encode + decode on the device)", "value": n / ((e_ms + d_ms) * 1e-3),
+            "unit": "Gaussians/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": e_ms + d_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/u16", "data": "synthetic",
+            "config": {"workload": "codec of the 500k-Gaussian microscopy set: 14-bit positions, 12-bit log "
+                                   "scales, quaternions and intensities, Morton order, zigzag deltas", "n": n},
+            "encode_ms": e_ms, "decode_ms": d_ms,
+            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": hbm,
+                         "encode_achieved": n * 66 / (e_ms * 1e-3) / 1e9,
+                         "decode_achieved": n * 66 / (d_ms * 1e-3) / 1e9,
+                         "algorithmic_bytes_per_gaussian": 66},
+            "host_lzma": {"seconds": t_host, "bytes": len(blob), "raw_param_bytes": n * 44,
+                          "ratio_vs_fp32_params": n * 44 / len(blob)}}
+    line["roofline"]["frac"] = line["roofline"]["decode_achieved"] / hbm
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -654,7 +732,9 @@ def main():
     ap.add_argument("--ref-px", type=int, default=2048)
     ap.add_argument("--ref-gauss", type=int, default=0, help="0 = twice the oracle's threads")
     ap.add_argument("--case", default="microscopy", choices=["microscopy", "small"])
-    ap.add_argument("--workload", default="fit", choices=["fit", "batched", "serving"])
+    ap.add_argument("--workload", default="fit", choices=["fit", "batched", "serving", "codec"])
+    ap.add_argument("--view", default="axis", choices=["axis", "oblique"],
+                    help="fit step on axis-aligned planes, or on a seeded oblique stack through the centre")
     ap.add_argument("--rates", default="10,30,100,300,1000")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-requests", type=int, default=400)
@@ -672,6 +752,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "codec":
+        return run_codec(args)
     return run_native(args, rank, world)
 
 
