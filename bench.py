@@ -658,6 +658,103 @@ def run_serving(args):
     return 0
 
 
+def speckle_blob_volume(torch, dev, shape, seed=2003, n_blobs=16):
+    """Ultrasound-shaped target [Z, Y, X] on the device: Rayleigh(1) speckle times
+    a sum of 16 isotropic blobs (std U(20, 80) voxels, centres uniform), scaled
+    to [0, 1]; seeded."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    Z, Y, X = shape
+    z = torch.arange(Z, device=dev, dtype=torch.float32) + 0.5
+    y = torch.arange(Y, device=dev, dtype=torch.float32) + 0.5
+    x = torch.arange(X, device=dev, dtype=torch.float32) + 0.5
+    env = torch.zeros(shape, device=dev)
+    for _ in range(n_blobs):
+        c = torch.rand(3, generator=g, device=dev) * torch.tensor([X, Y, Z], device=dev, dtype=torch.float32)
+        sd = 20.0 + 60.0 * torch.rand(1, generator=g, device=dev)
+        gz = torch.exp(-0.5 * ((z - c[2]) / sd) ** 2)
+        gy = torch.exp(-0.5 * ((y - c[1]) / sd) ** 2)
+        gx = torch.exp(-0.5 * ((x - c[0]) / sd) ** 2)
+        env += gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    u = torch.rand(shape, generator=g, device=dev).clamp_(min=1e-12)
+    vol = torch.sqrt(-2.0 * torch.log(u)) * env  # Rayleigh(1) speckle
+    return vol / vol.max()
+
+
+def run_ultrasound(args):
+    """The ultrasound-shaped configuration: 200k Gaussians in 512^3, sigma_z = 5,
+    against a speckle-times-blobs target.  --workload ultrasound renders all 512
+    slices of 512^2 (forward + MSE + backward); --workload voxelize runs the
+    voxelizer (Eq. 12) over the 512^3 grid forward + MSE + backward.  Metric:
+    algorithmic evaluations (forward + backward) per second."""
+    import torch
+    from paper_2603_20611_b300 import binding as B
+    from paper_2603_20611_b300 import synth
+    torch.cuda.set_device(0)
+    dev = "cuda:0"
+    ctx = B.Context(0, reuse_bins=True)  # the backward takes the forward's bins (parameters unchanged)
+    g = synth.ultrasound()
+    gs = B.GaussianSet.from_numpy(g, dev)
+    D = 512
+    target = speckle_blob_volume(torch, dev, (D, D, D))
+    stream = torch.cuda.current_stream()
+    grads = (torch.empty(g.n, 3, device=dev), torch.empty(g.n, 3, device=dev), torch.empty(g.n, 4, device=dev),
+             torch.empty(g.n, device=dev))
+    out = torch.empty(D, D, D, device=dev)
+    G = torch.empty_like(out)
+    loss = torch.zeros(1, device=dev)
+    z = synth.slice_positions(range(D))
+    if args.workload == "ultrasound":
+        evals = B.gp_count_evals(ctx, gs, z, D, D, 5.0)
+
+        def step():
+            B.gp_render_slices(ctx, gs, z, D, D, 5.0, out=out)
+            B.gp_mse_grad(ctx, out, target, dL_dI=G, loss=loss)
+            B.gp_render_backward(ctx, gs, z, D, D, 5.0, G, grads=grads)
+        fwd_phase, bwd_phase, ops = "fwd", "bwd", OPS_PER_EVAL["bwd"]
+        name = "ultrasound slice stack: 200k Gaussians, 512^3, sigma_z = 5, all 512 slices, fwd + MSE + bwd"
+    else:
+        evals = B.gp_count_vox_evals(ctx, gs, D, D, D)
+
+        def step():
+            B.gp_voxelize(ctx, gs, D, D, D, vol=out)
+            B.gp_mse_grad(ctx, out, target, dL_dI=G, loss=loss)
+            B.gp_voxelize_backward(ctx, gs, D, D, D, G, grads=grads)
+        fwd_phase, bwd_phase, ops = "vox_fwd", "vox_bwd", None
+        name = "ultrasound voxelize: 200k Gaussians, 512^3 grid, Eq. 12 fwd + MSE + bwd"
+    flush = torch.empty(64 * 1024 * 1024, device=dev)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ctx.timing(True)
+    ctx.timing_read()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    phases = ctx.timing_read()
+    ctx.timing(False)
+    t = float(np.mean(ms))
+    line = {"metric": METRIC, "value": 2.0 * evals / (t * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name, "n_gaussians": g.n, "l2": "flushed between steps (256 MiB write)"},
+            "evals_fwd_per_step": evals,
+            "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[2]}}
+    if ops:
+        bwd_s = phases[bwd_phase][0] * 1e-3 / max(phases[bwd_phase][2], 1)
+        line["roofline"] = {"bound": "alu", "kernel": "k_raster_bwd", "achieved": evals * ops / bwd_s / 1e12,
+                            "unit": "Tinst/s (FP32+INT lane instructions)", "ops_per_eval": ops}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_codec(args):
     """Encode (device quantisation, Morton sort, delta streams) and decode of the
     500k-Gaussian microscopy set, timed with CUDA events; throughput in
@@ -732,7 +829,8 @@ def main():
     ap.add_argument("--ref-px", type=int, default=2048)
     ap.add_argument("--ref-gauss", type=int, default=0, help="0 = twice the oracle's threads")
     ap.add_argument("--case", default="microscopy", choices=["microscopy", "small"])
-    ap.add_argument("--workload", default="fit", choices=["fit", "batched", "serving", "codec"])
+    ap.add_argument("--workload", default="fit", choices=["fit", "batched", "serving", "codec", "ultrasound",
+                                                           "voxelize"])
     ap.add_argument("--view", default="axis", choices=["axis", "oblique"],
                     help="fit step on axis-aligned planes, or on a seeded oblique stack through the centre")
     ap.add_argument("--rates", default="10,30,100,300,1000")
@@ -754,6 +852,8 @@ def main():
         return run_serving(args)
     if args.workload == "codec":
         return run_codec(args)
+    if args.workload in ("ultrasound", "voxelize"):
+        return run_ultrasound(args)
     return run_native(args, rank, world)
 
 

@@ -237,6 +237,11 @@ GP_API gp_status gp_voxelize_backward(gp_ctx* ctx, const gp_set* set, int X, int
                                const float* dL_dV, float* d_mu, float* d_scale,
                                float* d_quat, float* d_alpha, void* stream);
 
+/* Number of (voxel, Gaussian) evaluations inside the culling ellipsoid
+ * (x - mu)^T Sigma^-1 (x - mu) <= 2 ln(1/eps), voxel centres in the X x Y x Z
+ * grid: the algorithmic work of gp_voxelize (Eq. 12).  Synchronous. */
+GP_API gp_status gp_count_vox_evals(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, int64_t* evals);
+
 /* Diagnostics of the last gp_render_slices / gp_render_backward / gp_voxelize
  * on ctx: number of (Gaussian, slice, tile) pairs binned and of pixel
  * evaluations issued (pairs x tile pixels). */

@@ -241,3 +241,30 @@ def mse(I, T):
     g = np.zeros_like(I)
     L = _load().orc_mse(I.size, _ptr(I), _ptr(T), _ptr(g))
     return float(L), g
+
+
+def count_vox_evals(mu, scale, quat, alpha, X, Y, Z, eps=1e-6, scale_mod=1.0):
+    """Voxel centres inside each Gaussian's culling ellipsoid (x - mu)^T Sigma^-1
+    (x - mu) <= 2 ln(1/eps) within the X x Y x Z grid: the algorithmic work of
+    Eq. 12 under that culling (FP64 brute force over each bounding box)."""
+    mu = np.asarray(mu, np.float64).reshape(-1, 3)
+    sc = np.asarray(scale, np.float64).reshape(-1, 3) * scale_mod
+    q = np.asarray(quat, np.float64).reshape(-1, 4)
+    k2 = 2.0 * np.log(1.0 / eps)
+    total = 0
+    for i in range(mu.shape[0]):
+        w, x, y, z = q[i] / np.linalg.norm(q[i])
+        R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                      [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+        S = R @ np.diag(sc[i] ** 2) @ R.T
+        K = np.linalg.inv(S)
+        h = np.sqrt(k2 * np.diag(S))
+        lo = np.maximum(np.ceil(mu[i] - h - 0.5), 0).astype(int)
+        hi = np.minimum(np.floor(mu[i] + h - 0.5), np.array([X, Y, Z]) - 1).astype(int)
+        if np.any(hi < lo):
+            continue
+        g = np.stack(np.meshgrid(*[np.arange(lo[a], hi[a] + 1) + 0.5 for a in range(3)], indexing="ij"), -1)
+        d = g - mu[i]
+        total += int((np.einsum("...i,ij,...j->...", d, K, d) <= k2).sum())
+    return total

@@ -40,7 +40,7 @@ EXPORTS = (
     "gp_serve_open", "gp_serve_load_set", "gp_serve_submit", "gp_serve_poll", "gp_serve_stats_get",
     "gp_serve_close", "gp_view_from_axis", "gp_render_slices_view", "gp_render_backward_view",
     "gp_count_evals_view", "gp_adam_default", "gp_adam_state_floats", "gp_adam_init", "gp_adam_step",
-    "gp_l1_dssim_grad", "gp_encode", "gp_decode", "gp_serve_load_encoded",
+    "gp_l1_dssim_grad", "gp_encode", "gp_decode", "gp_serve_load_encoded", "gp_count_vox_evals",
 )
 GP_REQ_SLICE, GP_REQ_STACK, GP_REQ_VOXELIZE = 0, 1, 2
 GP_BATCH_AUTOTUNE = 1
@@ -169,6 +169,7 @@ def _load():
         "gp_adam_default": [ctypes.POINTER(gp_adam_cfg)],
         "gp_l1_dssim_grad": [P, P, P, P, I, I, I, F, P, P, P],
         "gp_encode": [P, SP, I, ctypes.POINTER(gp_codec_header), P, P, P],
+        "gp_count_vox_evals": [P, SP, I, I, I, ctypes.POINTER(I64)],
         "gp_decode": [P, ctypes.POINTER(gp_codec_header), P, P, P, P, P, P],
         "gp_serve_load_encoded": [P, ctypes.POINTER(gp_codec_header), P, F, ctypes.POINTER(I)],
         "gp_adam_state_floats": [I64],
@@ -592,6 +593,12 @@ def gp_count_evals(ctx, gs, z, H, W, sigma_z, axis=2, view=None):
         st = lib.gp_count_evals(ctx.h, ctypes.byref(gs.c()), zp, z.shape[0], H, W, float(sigma_z), axis,
                                 ctypes.byref(out))
     ctx.check(st, "gp_count_evals")
+    return int(out.value)
+
+
+def gp_count_vox_evals(ctx, gs, X, Y, Z):
+    out = ctypes.c_int64()
+    ctx.check(lib.gp_count_vox_evals(ctx.h, ctypes.byref(gs.c()), X, Y, Z, ctypes.byref(out)), "gp_count_vox_evals")
     return int(out.value)
 
 

@@ -644,6 +644,25 @@ gp_status gp_voxelize(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, float
   return GP_OK;
 }
 
+gp_status gp_count_vox_evals(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, int64_t* evals) {
+  if (!ctx || !evals) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+  GP_TRY(check_set(c, set));
+  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  cudaStream_t st = 0;
+  VoxArgs a;
+  uint32_t P = 0;
+  const uint32_t* vals = nullptr;
+  GP_TRY(bin_voxels(c, set, X, Y, Z, st, &a, &P, &vals));
+  unsigned long long* d = (unsigned long long*)c->b.total.ptr + 1;
+  GP_CUDA(c, cudaMemsetAsync(d, 0, 8, st), "count");
+  launch_vox_count(a, (const VoxRec*)c->b.rec.ptr, d, st);
+  GP_CUDA(c, cudaMemcpyAsync(c->h_total, d, 8, cudaMemcpyDeviceToHost, st), "count readback");
+  GP_CUDA(c, cudaStreamSynchronize(st), "count readback");
+  *evals = (int64_t)*c->h_total;
+  return GP_OK;
+}
+
 gp_status gp_voxelize_backward(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, const float* dL_dV,
                                float* d_mu, float* d_scale, float* d_quat, float* d_alpha, void* stream) {
   if (!ctx) return GP_ERR_ARG;

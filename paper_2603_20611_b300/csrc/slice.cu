@@ -269,6 +269,22 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_slice_emit(SliceArgs a1, Batch
     if (BATCH) a = b.args[find_item(b.gstart, b.n_items, i)];
   }
   const uint32_t T = (uint32_t)(a.TX * a.TY);
+  if (wend - wstart > 2ull * EMIT_WIN) {
+    // many pairs per warp (Gaussians spanning many planes): one enumeration
+    // with direct stores (each thread's run is contiguous) instead of one
+    // enumeration per window
+    if (mine) {
+      unsigned long long e = my0;
+      for_each_pair(a, r, [&](int j, int tile) {
+        if (e < wend) {
+          keys[e] = a.key_base + (uint32_t)a.zorder[j] * T + (uint32_t)tile;
+          emit_gid[e] = (uint32_t)i;
+        }
+        ++e;
+      });
+    }
+    return;
+  }
   for (unsigned long long wb = wstart; wb < wend; wb += EMIT_WIN) {
     const unsigned long long we = wb + EMIT_WIN;
     if (mine && my1 > wb && my0 < we) {

@@ -392,6 +392,49 @@ __global__ void __launch_bounds__(VPRE_THREADS) k_vox_bwd_pre(VoxArgs a, const f
   d_alpha[i] = ga;
 }
 
+// Algorithmic work of a voxelize: the voxel centres inside each Gaussian's
+// culling ellipsoid d^T Sigma^-1 d <= 2 ln(1/eps), clipped to the grid.  One
+// warp per Gaussian; each lane takes (y, z) rows of the bounding box and counts
+// the row's x interval in closed form (double precision).  Added into *out.
+__global__ void __launch_bounds__(256) k_vox_count(VoxArgs a, const VoxRec* __restrict__ rec,
+                                                   unsigned long long* __restrict__ out) {
+  const int g = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (g >= a.n) return;
+  const VoxRec r = rec[g];
+  if (r.r3.y == 0.0f) return;
+  const double mx = r.r0.x, my = r.r0.y, mz = r.r0.z;
+  const double K00 = r.r1.x, K01 = r.r1.y, K02 = r.r1.z, K11 = r.r1.w, K12 = r.r2.x, K22 = r.r2.y;
+  const double hy = r.r2.w, hz = r.r3.x, k2 = a.k2;
+  const int y0 = max(0, (int)ceil(my - hy - 0.5)), y1 = min(a.Y - 1, (int)floor(my + hy - 0.5));
+  const int z0 = max(0, (int)ceil(mz - hz - 0.5)), z1 = min(a.Z - 1, (int)floor(mz + hz - 0.5));
+  unsigned long long cnt = 0;
+  if (y1 >= y0 && z1 >= z0) {
+    const int ny = y1 - y0 + 1;
+    const int rows = ny * (z1 - z0 + 1);
+    for (int i = lane; i < rows; i += 32) {
+      const double dy = (y0 + i % ny) + 0.5 - my, dz = (z0 + i / ny) + 0.5 - mz;
+      const double b = K01 * dy + K02 * dz;
+      const double c = K11 * dy * dy + 2.0 * K12 * dy * dz + K22 * dz * dz;
+      const double disc = b * b - K00 * (c - k2);
+      if (disc < 0.0) continue;
+      const double sq = sqrt(disc);
+      const long long x0 = max(0LL, (long long)ceil(mx + (-b - sq) / K00 - 0.5));
+      const long long x1 = min((long long)a.X - 1, (long long)floor(mx + (-b + sq) / K00 - 0.5));
+      if (x1 >= x0) cnt += (unsigned long long)(x1 - x0 + 1);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0 && cnt) atomicAdd(out, cnt);
+}
+
+void launch_vox_count(const VoxArgs& a, const VoxRec* rec, unsigned long long* out, cudaStream_t st) {
+  if (a.n <= 0) return;
+  k_vox_count<<<ceil_div(a.n, 8), 256, 0, st>>>(a, rec, out);
+  note_launch();
+}
+
 void launch_vox_bwd_pre(const VoxArgs& a, const float* accum, float* d_mu, float* d_scale, float* d_quat,
                         float* d_alpha, cudaStream_t st) {
   if (a.n <= 0) return;

@@ -32,6 +32,7 @@ cudaError_t launch_vox_bwd(const VoxArgs& a, bool deterministic, const VoxRec* r
                            float4* partial, cudaStream_t st);
 void launch_vox_det_reduce(int n, const unsigned long long* offsets, const unsigned long long* counts,
                            const float4* partial, float* accum, cudaStream_t st);
+void launch_vox_count(const VoxArgs& a, const VoxRec* rec, unsigned long long* out, cudaStream_t st);
 void launch_vox_bwd_pre(const VoxArgs& a, const float* accum, float* d_mu, float* d_scale, float* d_quat,
                         float* d_alpha, cudaStream_t st);
 

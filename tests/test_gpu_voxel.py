@@ -61,3 +61,14 @@ def test_voxelize_serving_size_sampled(ctx):
     ref = oracle.voxelize_points(*orc(g), idx[:, 0] + 0.5, idx[:, 1] + 0.5, idx[:, 2] + 0.5)
     got = np32(vol[torch.from_numpy(idx[:, 2]), torch.from_numpy(idx[:, 1]), torch.from_numpy(idx[:, 0])])
     assert_forward_close(got, ref, "voxelize 256^3 sampled")
+
+
+def test_voxel_eval_count_matches_oracle():
+    """gp_count_vox_evals (double-precision row intervals) against the oracle's
+    brute-force lattice count; only voxels within rounding of an ellipsoid's
+    boundary may differ."""
+    c = B.Context(0)
+    g = synth.small(seed=77, n=300, extent=(40, 36, 28))
+    got = B.gp_count_vox_evals(c, dev_set(g), 40, 36, 28)
+    ref = oracle.count_vox_evals(g.mu, g.scale, g.quat, g.alpha, 40, 36, 28)
+    assert ref > 0 and abs(got - ref) <= 1e-4 * ref

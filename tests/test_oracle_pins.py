@@ -442,3 +442,19 @@ def test_count_evals_brute_force():
             q = Ki[0, 0] * dx * dx + 2 * Ki[0, 1] * dx * dy + Ki[1, 1] * dy * dy
             count += int((q <= k2).sum())
     assert oracle.count_evals(g.mu, g.scale, g.quat, g.alpha, z, H, W, sig, eps=eps) == count
+
+
+def test_voxel_count_lattice_points():
+    """The voxel-evaluation count is a lattice-point count: a tiny isotropic
+    Gaussian on a voxel centre covers that voxel only; with radius k s in
+    (1, sqrt 2) it also covers the 6 face neighbours; a large ball holds about
+    its volume (4/3) pi (k s)^3 of points."""
+    k = math.sqrt(2 * math.log(1e6))
+    one = lambda s, m: oracle.count_vox_evals([m], [(s, s, s)], [(1, 0, 0, 0)], [1.0], 40, 40, 40)
+    assert one(0.1, (10.5, 10.5, 10.5)) == 1
+    assert one(1.2 / k, (10.5, 10.5, 10.5)) == 7
+    n = one(3.0, (20.5, 20.5, 20.5))
+    assert n == pytest.approx(4.0 / 3.0 * math.pi * (3.0 * k) ** 3, rel=0.02)
+    # clipped by the grid: a ball centred on a corner voxel keeps about an eighth
+    c = one(3.0, (0.5, 0.5, 0.5))
+    assert c == pytest.approx(n / 8, rel=0.15)
