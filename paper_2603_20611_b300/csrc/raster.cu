@@ -211,18 +211,20 @@ __device__ __forceinline__ bool rect_hit(float4 g0, float4 g1, float4 gc, float 
   return m <= k2;
 }
 
-// Shared memory of the backward body.  The tile's dL/dI is held with rows
-// padded to TILE + 4 floats (16-byte aligned rows).
+// Shared memory of the backward body.  The tile's dL/dI is held half-block by
+// half-block (4 rows of 8 pixels each), the half-blocks 36 floats apart: the
+// 16-byte loads of the same row and column by lanes working on different
+// half-blocks then fall in different banks.
 template <int TILE, int CH>
 struct BwdSmem {
   static constexpr int NW = (TILE / 8) * (TILE / 8);
   static constexpr int NH = 2 * NW;  // 8 x 4 half-blocks per tile
-  static constexpr int GS = TILE + 4;
+  static constexpr int HBS = 36;     // floats per half-block (32 + 4 of padding)
   float4 s0[CH], s1[CH], s2[CH], sc[CH];
   uint32_t sg[CH];
-  alignas(16) float G[TILE * GS];
+  alignas(16) float G[NH * HBS];
   int units[NW][CH * NH / NW];  // per warp: the hit (Gaussian, half-block) pairs it tested, (j << 4) | hb
-  int nunits[NW + 1];           // their counts, then offsets
+  int nunits[NW];               // their counts
   unsigned char hmask[CH];      // per Gaussian: which half-blocks were hit (bit hb)
   float sp[NH][6][CH];          // per (half-block, Gaussian): the six pixel moments
 };
@@ -245,7 +247,7 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
                                          float4* __restrict__ partial, BwdSmem<TILE, CH>& sm) {
   constexpr int NW = BwdSmem<TILE, CH>::NW;
   constexpr int NH = BwdSmem<TILE, CH>::NH;
-  constexpr int GS = BwdSmem<TILE, CH>::GS;
+  constexpr int HBS = BwdSmem<TILE, CH>::HBS;
   constexpr int NT = NW * 32;
   constexpr int ROUNDS = CH * NH / NT;  // test rounds per chunk
   static_assert((CH * NH) % NT == 0 && NH <= 8 && (NH & (NH - 1)) == 0, "tile / chunk shape");
@@ -257,11 +259,13 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
   const float zsv = a.zorig[s];
-  // the tile's dL/dI (zero outside the image)
+  // the tile's dL/dI (zero outside the image), half-block-major
   for (int i = threadIdx.x; i < TILE * TILE; i += NT) {
     const int yy = i / TILE, xx = i - yy * TILE;
     const int py = ty * TILE + yy, px = tx * TILE + xx;
-    sm.G[yy * GS + xx] = (py < a.H && px < a.W) ? a.dL_dI[((int64_t)s * a.H + py) * a.W + px] : 0.0f;
+    const int hb = 2 * ((yy >> 3) * (TILE / 8) + (xx >> 3)) + ((yy >> 2) & 1);
+    sm.G[hb * HBS + (yy & 3) * 8 + (xx & 7)] =
+        (py < a.H && px < a.W) ? a.dL_dI[((int64_t)s * a.H + py) * a.W + px] : 0.0f;
   }
   for (uint32_t base = rg.x; base < rg.y; base += CH) {
     const int cnt = (int)min((uint32_t)CH, rg.y - base);
@@ -297,23 +301,20 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
     }
     if (lane == 0) sm.nunits[warp] = nu;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int off = 0;
+    // every thread forms the offsets of the NW per-warp lists itself
+    int offs[NW + 1];
+    offs[0] = 0;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        const int c = sm.nunits[w];
-        sm.nunits[w] = off;
-        off += c;
-      }
-      sm.nunits[NW] = off;
-    }
-    __syncthreads();
-    const int total = sm.nunits[NW];
+    for (int w = 0; w < NW; ++w) offs[w + 1] = offs[w] + sm.nunits[w];
+    const int total = offs[NW];
     for (int u = threadIdx.x; u < total; u += NT) {
       int w = 0;
 #pragma unroll
-      for (int k = 1; k < NW; ++k) w += (u >= sm.nunits[k]);
-      const int code = sm.units[w][u - sm.nunits[w]];
+      for (int k = 1; k < NW; ++k) w += (u >= offs[k]);
+      int base_w = offs[0];
+#pragma unroll
+      for (int k = 1; k < NW; ++k) base_w = (w == k) ? offs[k] : base_w;
+      const int code = sm.units[w][u - base_w];
       const int jj = code >> 4, hb = code & 15;
       const float4 g0 = sm.s0[jj], g1 = sm.s1[jj];
       const float c0 = g1.x, c1 = g1.y, c2 = g1.z;
@@ -326,15 +327,15 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
       const float B0 = fmaf(2.0f * c0, dxc, c1 * dy0);
       const float2 C2 = make_float2(c0, c0);
       float M00 = 0.f, M10 = 0.f, M20 = 0.f, M01 = 0.f, M11 = 0.f, M02 = 0.f;
-      const float* Gr = sm.G + hby * GS + hbx;
+      const float* Gr = sm.G + hb * HBS;
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const float rf = (float)r;
         const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
         const float B = fmaf(c1, rf, B0);
         const float2 A2 = make_float2(A, A), B2 = make_float2(B, B);
-        const float4 ga = *reinterpret_cast<const float4*>(Gr + r * GS);
-        const float4 gb = *reinterpret_cast<const float4*>(Gr + r * GS + 4);
+        const float4 ga = *reinterpret_cast<const float4*>(Gr + r * 8);
+        const float4 gb = *reinterpret_cast<const float4*>(Gr + r * 8 + 4);
         const float2 Gp[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w), make_float2(gb.x, gb.y),
                               make_float2(gb.z, gb.w)};
         float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
