@@ -9,6 +9,7 @@ namespace gp {
 
 // log2(e) as an fp32 literal of the mathematical constant.
 constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kExpFloor = -125.0f;  // 2^-125 ~ 2.4e-38: below fp32 resolution of any sum
 
 // ---------------------------------------------------------------- exp2
 // 2^x = 2^n 2^f, n = round(x), f = x - n in [-1/2, 1/2]; 2^f by a degree-6
@@ -79,7 +80,17 @@ __device__ __forceinline__ float2 exp2_sel2(float2 x) {
   else return exp2_poly2(x);
 }
 
-constexpr float kExpFloor = -125.0f;  // 2^-125 ~ 2.4e-38: below fp32 resolution of any sum
+// Exponentials of two consecutive samples (2p, 2p + 1) of a row: e = A + B q +
+// C q^2 floored at kExpFloor, two samples per packed fp32x2 instruction (each
+// rounded as the scalar form rounds it).
+template <int EXPM>
+__device__ __forceinline__ float2 pair_exp2(float2 C2, float2 B2, float2 A2, float2 q) {
+  float2 e = __ffma2_rn(__ffma2_rn(C2, q, B2), q, A2);
+  e.x = fmaxf(e.x, kExpFloor);
+  e.y = fmaxf(e.y, kExpFloor);
+  return exp2_sel2<EXPM>(e);
+}
+
 
 // ---------------------------------------------------------------- records
 // Per-Gaussian slice-invariant record of the slice renderer (camera frame of the

@@ -35,17 +35,6 @@
 
 namespace gp {
 
-// Exponentials of pixels (2p, 2p + 1) of a row: e = A + B q + C q^2 floored at
-// kExpFloor, two pixels per packed fp32x2 instruction (each pixel rounded as the
-// scalar form rounds it).
-template <int EXPM>
-__device__ __forceinline__ float2 pair_exp2(float2 C2, float2 B2, float2 A2, float2 q) {
-  float2 e = __ffma2_rn(__ffma2_rn(C2, q, B2), q, A2);
-  e.x = fmaxf(e.x, kExpFloor);
-  e.y = fmaxf(e.y, kExpFloor);
-  return exp2_sel2<EXPM>(e);
-}
-
 // Staging of one Gaussian for one (slice, tile):
 //   s0 = (mu_2d,x - x0, mu_2d,y - y0, a~, C11)
 //   s1 = (c0, c1, c2, C00)     e = c0 dx^2 + c1 dx dy + c2 dy^2 = -log2(e)/2 d^T C d

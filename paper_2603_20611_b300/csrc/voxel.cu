@@ -7,13 +7,15 @@
 //   K-vpre   per Gaussian: record (mu, alpha, K = Sigma^-1, bounding box of the
 //            ellipsoid (x-mu)^T K (x-mu) <= 2 ln(1/eps)) + number of tiles
 //   K-vemit  tile keys with emission indices
-//   K-vfwd   one 64-thread CTA per tile; each thread owns one (x, y) column of
-//            eight voxels, so the x/y part of the quadratic form is computed once
-//            per Gaussian and each voxel costs two FMAs plus the exponential
-//   K-vbwd   ten moments per (Gaussian, tile) (sum G E, sum G E d_i,
-//            sum G E d_i d_j), warp-reduced, summed over the two warps in a
-//            fixed order, then atomically added per Gaussian (or stored per pair
-//            for the deterministic ordered reduction)
+//   K-vfwd   one 64-thread CTA per tile; each warp owns an 8 x 4 x 8 half and
+//            skips the Gaussians whose ellipsoid misses it (both shadows tested);
+//            a lane owns a row of 8 voxels along x, whose exponent is a quadratic
+//            in the x offset, two voxels per packed fp32x2 instruction
+//   K-vbwd   one Gaussian per lane over the warp's half: ten moments
+//            (sum G E, sum G E d_i, sum G E d_i d_j) from per-row sums, no
+//            cross-lane reduction; the two halves summed in a fixed order, then
+//            atomically added per Gaussian (or stored per pair for the
+//            deterministic ordered reduction)
 //   K-vbwd-pre  moments -> dL/d(mu, scale, quat, alpha)
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -132,68 +134,118 @@ void launch_vox_emit(const VoxArgs& a, const VoxRec* rec, const unsigned long lo
   note_launch();
 }
 
-// Staging: mean relative to the tile origin (exact), alpha, and the quadratic
-// form pre-scaled to base 2 with doubled off-diagonals:
-//   e = q0 dx^2 + q1 dy^2 + q2 dz^2 + q3 dx dy + q4 dx dz + q5 dy dz.
-__device__ __forceinline__ void vstage(const VoxRec* __restrict__ rec, uint32_t g, float ox, float oy, float oz,
-                                       float4& s0, float4& s1, float2& s2) {
+// Staging of one Gaussian for one 8^3 tile:
+//   s0 = (mu - tile origin (x, y, z), alpha)
+//   s1 = (q_xx, q_yy, q_zz, q_xy), s2 = (q_xz, q_yz): the exponent in base 2,
+//        e = q_xx dx^2 + q_yy dy^2 + q_zz dz^2 + q_xy dx dy + q_xz dx dz + q_yz dy dz
+//        = -log2(e)/2 d^T K d (off-diagonals doubled), K = Sigma^-1
+//   h0 = (C00, C01, C11, 1/C00), h1 = (1/C11, D00, D01, D11), h2 = (1/D00, 1/D11):
+//        the shadows of the culling ellipsoid on the xy plane (conic C, the Schur
+//        complement of K_zz) and on the xz plane (conic D, the complement of K_yy).
+struct VoxStage {
+  float4 s0, s1, h0, h1;
+  float4 s2h2;  // (q_xz, q_yz, 1/D00, 1/D11)
+};
+
+__device__ __forceinline__ VoxStage vstage(const VoxRec* __restrict__ rec, uint32_t g, float ox, float oy,
+                                           float oz) {
   const float4* rp = reinterpret_cast<const float4*>(rec + g);
   const float4 r0 = __ldg(rp), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2);
+  const float K00 = r1.x, K01 = r1.y, K02 = r1.z, K11 = r1.w, K12 = r2.x, K22 = r2.y;
   const float h = -0.5f * kLog2e;
-  s0 = make_float4(r0.x - ox, r0.y - oy, r0.z - oz, r0.w);
-  s1 = make_float4(h * r1.x, h * r1.w, h * r2.y, 2.0f * h * r1.y);  // q0 (xx), q1 (yy), q2 (zz), q3 (xy)
-  s2 = make_float2(2.0f * h * r1.z, 2.0f * h * r2.x);                // q4 (xz), q5 (yz)
+  VoxStage v;
+  v.s0 = make_float4(r0.x - ox, r0.y - oy, r0.z - oz, r0.w);
+  v.s1 = make_float4(h * K00, h * K11, h * K22, 2.0f * h * K01);
+  const float iz = 1.0f / K22, iy = 1.0f / K11;
+  const float C00 = K00 - K02 * K02 * iz, C01 = K01 - K02 * K12 * iz, C11 = K11 - K12 * K12 * iz;
+  const float D00 = K00 - K01 * K01 * iy, D01 = K02 - K01 * K12 * iy, D11 = K22 - K12 * K12 * iy;
+  v.h0 = make_float4(C00, C01, C11, 1.0f / C00);
+  v.h1 = make_float4(1.0f / C11, D00, D01, D11);
+  v.s2h2 = make_float4(2.0f * h * K02, 2.0f * h * K12, 1.0f / D00, 1.0f / D11);
+  return v;
 }
 
+// Does the culling ellipsoid reach the box [0.5, 7.5] x [y0, y1] x [0.5, 7.5]
+// (voxel centres, tile-relative)?  Both of its shadows must reach the box's
+// (conservative: an exact box test would cost a 3-D quadratic program).
+__device__ __forceinline__ bool vox_box_hit(const VoxStage& v, float y0, float y1, float k2) {
+  return ellipse_hits_rect(v.s0.x, v.s0.y, v.h0.x, v.h0.y, v.h0.z, v.h0.w, v.h1.x, k2, 0.5f, 7.5f, y0, y1) &&
+         ellipse_hits_rect(v.s0.x, v.s0.z, v.h1.y, v.h1.z, v.h1.w, v.s2h2.z, v.s2h2.w, k2, 0.5f, 7.5f, 0.5f, 7.5f);
+}
+
+// Row coefficients along x for the row (dy, dz): e = A + B q + C q^2 with
+// q = x - 4 the offset from the tile's centre column and dxc = 4 - mu_x.
+__device__ __forceinline__ void vrow(const float4& s1, float qxz, float qyz, float dxc, float dy, float dz, float& A,
+                                     float& B) {
+  const float lin = fmaf(s1.w, dy, qxz * dz);  // q_xy dy + q_xz dz
+  B = fmaf(2.0f * s1.x, dxc, lin);
+  A = fmaf(dxc, fmaf(s1.x, dxc, lin), fmaf(s1.y * dy, dy, fmaf(s1.z * dz, dz, qyz * dy * dz)));
+}
+
+struct VoxFwdSmem {
+  VoxStage st[VCH];
+  int hits[VNT / 32][VCH];
+};
+
+// Forward: one 64-thread CTA per 8^3 tile; warp w owns the 8 x 4 x 8 half with
+// y in [4w, 4w + 4); lane (yl, z) owns the row of 8 voxels along x at y = 4w + yl
+// and z, two voxels per packed instruction.  Each staged Gaussian is tested
+// against the warp's half (its xy and xz shadows), and the hits are applied in
+// chunk order (bitwise reproducible sums).
+template <int EXPM>
 __global__ void __launch_bounds__(VNT) k_vox_fwd(VoxArgs a, const VoxRec* __restrict__ rec,
                                                  const uint32_t* __restrict__ vals,
                                                  const uint32_t* __restrict__ emit_gid,
                                                  const uint2* __restrict__ ranges, float* __restrict__ vol) {
-  __shared__ float4 s0[VCH], s1[VCH];
-  __shared__ float2 s2[VCH];
+  __shared__ VoxFwdSmem sm;
   const int tile = blockIdx.x;
   const int tx = tile % a.TX, ty = (tile / a.TX) % a.TY, tz = tile / (a.TX * a.TY);
   const uint2 rg = ranges[tile];
-  const int lx = threadIdx.x & 7, ly = threadIdx.x >> 3;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int yl = lane & 3, zl = lane >> 2;
   const float ox = (float)(tx * VOX_TILE), oy = (float)(ty * VOX_TILE), oz = (float)(tz * VOX_TILE);
-  const float px = (float)lx + 0.5f, py = (float)ly + 0.5f;
-  float acc[VOX_TILE];
+  const float py = (float)(4 * warp + yl) + 0.5f, pz = (float)zl + 0.5f;
+  const float y0 = (float)(4 * warp) + 0.5f;
+  int* hits = sm.hits[warp];
+  float2 acc[4];
 #pragma unroll
-  for (int k = 0; k < VOX_TILE; ++k) acc[k] = 0.f;
+  for (int p = 0; p < 4; ++p) acc[p] = make_float2(0.f, 0.f);
   for (uint32_t base = rg.x; base < rg.y; base += VCH) {
     const int cnt = (int)min((uint32_t)VCH, rg.y - base);
-    for (int j = threadIdx.x; j < cnt; j += VNT) {
-      uint32_t g = emit_gid[vals[base + j]];
-      float4 a0, a1;
-      float2 a2;
-      vstage(rec, g, ox, oy, oz, a0, a1, a2);
-      s0[j] = a0;
-      s1[j] = a1;
-      s2[j] = a2;
-    }
+    for (int j = threadIdx.x; j < cnt; j += VNT) sm.st[j] = vstage(rec, emit_gid[vals[base + j]], ox, oy, oz);
     __syncthreads();
-    for (int j = 0; j < cnt; ++j) {
-      const float4 g0 = s0[j], g1 = s1[j];
-      const float2 g2 = s2[j];
-      const float dx = px - g0.x, dy = py - g0.y;
-      const float bxy = fmaf(dx, fmaf(g1.x, dx, g1.w * dy), g1.y * dy * dy);
-      const float lin = fmaf(g2.x, dx, g2.y * dy);
+    int nh = 0;
+    for (int jb = 0; jb < cnt; jb += 32) {
+      const int j = jb + lane;
+      const bool hit = j < cnt && vox_box_hit(sm.st[j], y0, y0 + 3.0f, a.k2);
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (hit) hits[nh + __popc(m & ((1u << lane) - 1u))] = j;
+      nh += __popc(m);
+    }
+    __syncwarp();
+    for (int h = 0; h < nh; ++h) {
+      const VoxStage& v = sm.st[hits[h]];
+      const float4 g0 = v.s0, g1 = v.s1;
+      float A, B;
+      vrow(g1, v.s2h2.x, v.s2h2.y, 4.0f - g0.x, py - g0.y, pz - g0.z, A, B);
+      const float2 C2 = make_float2(g1.x, g1.x), B2 = make_float2(B, B), A2 = make_float2(A, A);
+      const float2 al2 = make_float2(g0.w, g0.w);
 #pragma unroll
-      for (int k = 0; k < VOX_TILE; ++k) {
-        const float dz = ((float)k + 0.5f) - g0.z;
-        float e = fmaf(dz, fmaf(g1.z, dz, lin), bxy);
-        e = fmaxf(e, kExpFloor);
-        acc[k] = fmaf(g0.w, exp2_poly(e), acc[k]);
+      for (int p = 0; p < 4; ++p) {
+        const float2 q = make_float2((float)(2 * p) - 3.5f, (float)(2 * p + 1) - 3.5f);
+        acc[p] = __ffma2_rn(al2, pair_exp2<EXPM>(C2, B2, A2, q), acc[p]);
       }
     }
     __syncthreads();
   }
-  const int x = tx * VOX_TILE + lx, y = ty * VOX_TILE + ly;
-  if (x < a.X && y < a.Y) {
+  const int y = ty * VOX_TILE + 4 * warp + yl, z = tz * VOX_TILE + zl;
+  if (y < a.Y && z < a.Z) {
+    float* o = vol + ((int64_t)z * a.Y + y) * a.X + tx * VOX_TILE;
+    const int xr = a.X - tx * VOX_TILE;  // voxels of this row inside the volume
 #pragma unroll
-    for (int k = 0; k < VOX_TILE; ++k) {
-      const int z = tz * VOX_TILE + k;
-      if (z < a.Z) vol[((int64_t)z * a.Y + y) * a.X + x] = acc[k];
+    for (int p = 0; p < 4; ++p) {
+      if (2 * p < xr) o[2 * p] = acc[p].x;
+      if (2 * p + 1 < xr) o[2 * p + 1] = acc[p].y;
     }
   }
 }
@@ -202,19 +254,29 @@ cudaError_t launch_vox_fwd(const VoxArgs& a, const VoxRec* rec, const uint32_t* 
                            const uint2* ranges, float* vol, cudaStream_t st) {
   int64_t tiles = (int64_t)a.TX * a.TY * a.TZ;
   if (tiles == 0) return cudaSuccess;
-  k_vox_fwd<<<(unsigned)tiles, VNT, 0, st>>>(a, rec, vals, emit_gid, ranges, vol);
+  k_vox_fwd<GP_EXP_POLY><<<(unsigned)tiles, VNT, 0, st>>>(a, rec, vals, emit_gid, ranges, vol);
   note_launch();
   return cudaGetLastError();
 }
 
-__device__ __forceinline__ float vwarp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
+struct VoxBwdSmem {
+  VoxStage st[VCH];
+  uint32_t sg[VCH];
+  alignas(16) float G[VOX_TILE][VOX_TILE][VOX_TILE];  // the tile's dL/dV [z][y][x], zero outside the volume
+  int hits[VNT / 32][VCH];
+  unsigned hmask[VNT / 32][VCH / 32];
+  float sp[VNT / 32][VACC][VCH];
+};
 
-// Moment layout: 0 sum G E, 1..3 sum G E (dx, dy, dz),
-//                4..9 sum G E (dx dx, dy dy, dz dz, dx dy, dx dz, dy dz).
+// Backward: warp w owns the same 8 x 4 x 8 half as in the forward.  Each lane
+// takes one hit Gaussian at a time and sums, over the half's 128 voxels (16 rows
+// of 8 along x, two voxels per packed instruction, dL/dV read from shared memory
+// as broadcasts), the ten moments
+//     sum G E {1, dx, dy, dz, dx^2, dy^2, dz^2, dx dy, dx dz, dy dz}
+// (E the Gaussian's exponential, G = dL/dV, d = voxel - mu) from per-row sums
+// about the centre column; no lane shares a Gaussian, so nothing is reduced
+// across lanes.  The two halves' moments are added in a fixed order and folded
+// into the Gaussian's accumulators (atomics) or a per-pair partial.
 template <bool DET>
 __global__ void __launch_bounds__(VNT) k_vox_bwd(VoxArgs a, const VoxRec* __restrict__ rec,
                                                  const uint32_t* __restrict__ vals,
@@ -222,81 +284,113 @@ __global__ void __launch_bounds__(VNT) k_vox_bwd(VoxArgs a, const VoxRec* __rest
                                                  const uint2* __restrict__ ranges, const float* __restrict__ dL_dV,
                                                  float* __restrict__ accum, float4* __restrict__ partial) {
   constexpr int NW = VNT / 32;
-  __shared__ float4 s0[VCH], s1[VCH];
-  __shared__ float2 s2[VCH];
-  __shared__ uint32_t sg[VCH];
-  __shared__ float sp[NW][VACC][VCH];
+  __shared__ VoxBwdSmem sm;
   const int tile = blockIdx.x;
   const uint2 rg = ranges[tile];
-  if (rg.y <= rg.x) return;
+  if (rg.y <= rg.x) return;  // uniform over the CTA
   const int tx = tile % a.TX, ty = (tile / a.TX) % a.TY, tz = tile / (a.TX * a.TY);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int lx = threadIdx.x & 7, ly = threadIdx.x >> 3;
   const float ox = (float)(tx * VOX_TILE), oy = (float)(ty * VOX_TILE), oz = (float)(tz * VOX_TILE);
-  const float px = (float)lx + 0.5f, py = (float)ly + 0.5f;
-  const int x = tx * VOX_TILE + lx, y = ty * VOX_TILE + ly;
-  float G[VOX_TILE];
-#pragma unroll
-  for (int k = 0; k < VOX_TILE; ++k) {
-    const int z = tz * VOX_TILE + k;
-    G[k] = (x < a.X && y < a.Y && z < a.Z) ? dL_dV[((int64_t)z * a.Y + y) * a.X + x] : 0.f;
+  const float y0 = (float)(4 * warp) + 0.5f;
+  for (int i = threadIdx.x; i < VOX_TILE * VOX_TILE * VOX_TILE; i += VNT) {
+    const int xx = i & 7, yy = (i >> 3) & 7, zz = i >> 6;
+    const int x = tx * VOX_TILE + xx, y = ty * VOX_TILE + yy, z = tz * VOX_TILE + zz;
+    sm.G[zz][yy][xx] = (x < a.X && y < a.Y && z < a.Z) ? dL_dV[((int64_t)z * a.Y + y) * a.X + x] : 0.f;
   }
+  int* hits = sm.hits[warp];
   for (uint32_t base = rg.x; base < rg.y; base += VCH) {
     const int cnt = (int)min((uint32_t)VCH, rg.y - base);
     for (int j = threadIdx.x; j < cnt; j += VNT) {
-      uint32_t g = emit_gid[vals[base + j]];
-      float4 a0, a1;
-      float2 a2;
-      vstage(rec, g, ox, oy, oz, a0, a1, a2);
-      s0[j] = a0;
-      s1[j] = a1;
-      s2[j] = a2;
-      sg[j] = g;
+      const uint32_t g = emit_gid[vals[base + j]];
+      sm.st[j] = vstage(rec, g, ox, oy, oz);
+      sm.sg[j] = g;
     }
     __syncthreads();
-    for (int j = 0; j < cnt; ++j) {
-      const float4 g0 = s0[j], g1 = s1[j];
-      const float2 g2 = s2[j];
-      const float dx = px - g0.x, dy = py - g0.y;
-      const float bxy = fmaf(dx, fmaf(g1.x, dx, g1.w * dy), g1.y * dy * dy);
-      const float lin = fmaf(g2.x, dx, g2.y * dy);
-      float c0 = 0.f, cz = 0.f, czz = 0.f;
+    int nh = 0;
+    for (int jb = 0; jb < VCH; jb += 32) {
+      const int j = jb + lane;
+      const bool hit = j < cnt && vox_box_hit(sm.st[j], y0, y0 + 3.0f, a.k2);
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (hit) hits[nh + __popc(m & ((1u << lane) - 1u))] = j;
+      if (lane == 0) sm.hmask[warp][jb >> 5] = m;
+      nh += __popc(m);
+    }
+    __syncwarp();
+    for (int u0 = 0; u0 < nh; u0 += 32) {
+      const int u = u0 + lane;
+      if (u >= nh) break;
+      const int jj = hits[u];
+      const VoxStage& v = sm.st[jj];
+      const float4 g0 = v.s0, g1 = v.s1;
+      const float dxc = 4.0f - g0.x;
+      const float2 C2 = make_float2(g1.x, g1.x);
+      float T0 = 0.f, T1 = 0.f, T2 = 0.f, Y0 = 0.f, Y1 = 0.f, Z0 = 0.f, Z1 = 0.f, YY = 0.f, ZZ = 0.f, YZ = 0.f;
+      for (int zz = 0; zz < VOX_TILE; ++zz) {
+        const float dz = ((float)zz + 0.5f) - g0.z;
 #pragma unroll
-      for (int k = 0; k < VOX_TILE; ++k) {
-        const float dz = ((float)k + 0.5f) - g0.z;
-        float e = fmaf(dz, fmaf(g1.z, dz, lin), bxy);
-        e = fmaxf(e, kExpFloor);
-        const float gE = G[k] * exp2_poly(e);
-        c0 += gE;
-        const float t = gE * dz;
-        cz += t;
-        czz = fmaf(t, dz, czz);
+        for (int yl = 0; yl < 4; ++yl) {
+          const float dy = (float)(4 * warp + yl) + 0.5f - g0.y;
+          float A, B;
+          vrow(g1, v.s2h2.x, v.s2h2.y, dxc, dy, dz, A, B);
+          const float2 A2 = make_float2(A, A), B2 = make_float2(B, B);
+          const float4 ga = *reinterpret_cast<const float4*>(&sm.G[zz][4 * warp + yl][0]);
+          const float4 gb = *reinterpret_cast<const float4*>(&sm.G[zz][4 * warp + yl][4]);
+          const float2 Gp[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w), make_float2(gb.x, gb.y),
+                                make_float2(gb.z, gb.w)};
+          float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const float qa = (float)(2 * p) - 3.5f, qb = (float)(2 * p + 1) - 3.5f;
+            const float2 q = make_float2(qa, qb);
+            const float2 gE = __fmul2_rn(Gp[p], pair_exp2<GP_EXP_POLY>(C2, B2, A2, q));
+            P0 = __fadd2_rn(P0, gE);
+            P1 = __ffma2_rn(q, gE, P1);
+            P2 = __ffma2_rn(make_float2(qa * qa, qb * qb), gE, P2);
+          }
+          const float S0 = P0.x + P0.y, S1 = P1.x + P1.y, S2 = P2.x + P2.y;
+          T0 += S0;
+          T1 += S1;
+          T2 += S2;
+          Y0 = fmaf(dy, S0, Y0);
+          Y1 = fmaf(dy, S1, Y1);
+          Z0 = fmaf(dz, S0, Z0);
+          Z1 = fmaf(dz, S1, Z1);
+          YY = fmaf(dy * dy, S0, YY);
+          ZZ = fmaf(dz * dz, S0, ZZ);
+          YZ = fmaf(dy * dz, S0, YZ);
+        }
       }
-      float m[VACC] = {c0, c0 * dx, c0 * dy, cz, c0 * dx * dx, c0 * dy * dy, czz, c0 * dx * dy, cz * dx, cz * dy};
-#pragma unroll
-      for (int k = 0; k < VACC; ++k) m[k] = vwarp_sum(m[k]);
-      if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < VACC; ++k) sp[warp][k][j] = m[k];
-      }
+      // moments in d = (dxc + q, dy, dz)
+      float* sp = &sm.sp[warp][0][jj];
+      sp[0 * VCH] = T0;
+      sp[1 * VCH] = fmaf(dxc, T0, T1);
+      sp[2 * VCH] = Y0;
+      sp[3 * VCH] = Z0;
+      sp[4 * VCH] = fmaf(dxc, fmaf(dxc, T0, 2.0f * T1), T2);
+      sp[5 * VCH] = YY;
+      sp[6 * VCH] = ZZ;
+      sp[7 * VCH] = fmaf(dxc, Y0, Y1);
+      sp[8 * VCH] = fmaf(dxc, Z0, Z1);
+      sp[9 * VCH] = YZ;
     }
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += VNT) {
       float m[VACC];
 #pragma unroll
-      for (int k = 0; k < VACC; ++k) {
-        float s = 0.f;
+      for (int k = 0; k < VACC; ++k) m[k] = 0.f;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) s += sp[w][k][j];
-        m[k] = s;
-      }
+      for (int w = 0; w < NW; ++w)
+        if ((sm.hmask[w][j >> 5] >> (j & 31)) & 1u) {
+#pragma unroll
+          for (int k = 0; k < VACC; ++k) m[k] += sm.sp[w][k][j];
+        }
       if constexpr (DET) {
         const size_t e = vals[base + j];
         partial[3 * e] = make_float4(m[0], m[1], m[2], m[3]);
         partial[3 * e + 1] = make_float4(m[4], m[5], m[6], m[7]);
         partial[3 * e + 2] = make_float4(m[8], m[9], 0.f, 0.f);
       } else {
-        float* A = accum + (size_t)sg[j] * VACC;
+        float* A = accum + (size_t)sm.sg[j] * VACC;
 #pragma unroll
         for (int k = 0; k < VACC; ++k) atomicAdd(A + k, m[k]);
       }
