@@ -63,31 +63,57 @@ __global__ void __launch_bounds__(kThreads) k_ssim_stats(SsimArgs p, const float
     sT[r][c] = in ? Tp[(int64_t)y * p.W + x] : 0.0f;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kWS * kTS; i += kThreads) {
-    const int r = i / kTS, c = i - r * kTS;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+  // horizontal window sums: a thread takes 8 consecutive outputs of one row from
+  // 18 staged values of each image (a sliding window held in registers)
+  for (int i = threadIdx.x; i < kWS * (kTS / 8); i += kThreads) {
+    const int r = i / (kTS / 8), c0 = (i - r * (kTS / 8)) * 8;
+    float u[18], v[18];
 #pragma unroll
-    for (int k = 0; k < 11; ++k) {
-      const float wk = p.w[k], u = sI[r][c + k], v = sT[r][c + k];
-      a0 = fmaf(wk, u, a0);
-      a1 = fmaf(wk, v, a1);
-      a2 = fmaf(wk * u, u, a2);
-      a3 = fmaf(wk * v, v, a3);
-      a4 = fmaf(wk * u, v, a4);
+    for (int k = 0; k < 18; ++k) {
+      u[k] = sI[r][c0 + k];
+      v[k] = sT[r][c0 + k];
     }
-    hs[0][r][c] = a0; hs[1][r][c] = a1; hs[2][r][c] = a2; hs[3][r][c] = a3; hs[4][r][c] = a4;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 11; ++k) {
+        const float wk = p.w[k], uu = u[o + k], vv = v[o + k];
+        a0 = fmaf(wk, uu, a0);
+        a1 = fmaf(wk, vv, a1);
+        a2 = fmaf(wk * uu, uu, a2);
+        a3 = fmaf(wk * vv, vv, a3);
+        a4 = fmaf(wk * uu, vv, a4);
+      }
+      hs[0][r][c0 + o] = a0; hs[1][r][c0 + o] = a1; hs[2][r][c0 + o] = a2; hs[3][r][c0 + o] = a3;
+      hs[4][r][c0 + o] = a4;
+    }
   }
   __syncthreads();
   double ssim_acc = 0.0, l1_acc = 0.0;
-  for (int i = threadIdx.x; i < kTS * kTS; i += kThreads) {
-    const int y = i / kTS, x = i - y * kTS;
+  // vertical window sums: a thread takes 4 consecutive outputs of one column
+  for (int i = threadIdx.x; i < kTS * (kTS / 4); i += kThreads) {
+    const int x = i % kTS, yb = (i / kTS) * 4;
+    float mm[4][5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      float col[14];
+#pragma unroll
+      for (int k = 0; k < 14; ++k) col[k] = hs[q][yb + k][x];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) acc = fmaf(p.w[k], col[o + k], acc);
+        mm[o][q] = acc;
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+    const int y = yb + o;
     const int gy = y0 + y, gx = x0 + x;
     if (!in_img(p, gy, gx)) continue;
-    float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < 11; ++k)
-#pragma unroll
-      for (int q = 0; q < 5; ++q) m[q] = fmaf(p.w[k], hs[q][y + k][x], m[q]);
+    const float* m = mm[o];
     const float mI = m[0], mT = m[1];
     const float sII = m[2] - mI * mI, sTT = m[3] - mT * mT, sIT = m[4] - mI * mT;
     const float A = fmaf(2.0f * mI, mT, p.c1), Bv = fmaf(2.0f, sIT, p.c2);
@@ -97,13 +123,14 @@ __global__ void __launch_bounds__(kThreads) k_ssim_stats(SsimArgs p, const float
     const float dS_dmI = 2.0f * mT * Bv * inv_CD - Sv * 2.0f * mI / Cv;
     const float dS_dsII = -Sv / D;
     const float dS_dsIT = 2.0f * A * inv_CD;
-    const int64_t o = (int64_t)s * HW + (int64_t)gy * p.W + gx;
+    const int64_t off = (int64_t)s * HW + (int64_t)gy * p.W + gx;
     const int64_t plane = (int64_t)p.S * HW;
-    dS[o] = dS_dmI - 2.0f * mI * dS_dsII - mT * dS_dsIT;  // dS/dm_I (all paths)
-    dS[plane + o] = dS_dsII;                              // dS/dm_II
-    dS[2 * plane + o] = dS_dsIT;                          // dS/dm_IT
+    dS[off] = dS_dmI - 2.0f * mI * dS_dsII - mT * dS_dsIT;  // dS/dm_I (all paths)
+    dS[plane + off] = dS_dsII;                              // dS/dm_II
+    dS[2 * plane + off] = dS_dsIT;                          // dS/dm_IT
     ssim_acc += (double)Sv;
     l1_acc += (double)fabsf(sI[y + kHalo][x + kHalo] - sT[y + kHalo][x + kHalo]);
+    }
   }
   // block sums in a fixed order
 #pragma unroll
@@ -146,34 +173,53 @@ __global__ void __launch_bounds__(kThreads) k_ssim_grad(SsimArgs p, const float*
     for (int q = 0; q < 3; ++q) sA[q][r][c] = in ? dS[q * plane + o] : 0.0f;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kWS * kTS; i += kThreads) {
-    const int r = i / kTS, c = i - r * kTS;
-    float a[3] = {0.f, 0.f, 0.f};
+  for (int i = threadIdx.x; i < 3 * kWS * (kTS / 8); i += kThreads) {
+    const int q = i / (kWS * (kTS / 8));
+    const int rr = i - q * (kWS * (kTS / 8));
+    const int r = rr / (kTS / 8), c0 = (rr - r * (kTS / 8)) * 8;
+    float u[18];
 #pragma unroll
-    for (int k = 0; k < 11; ++k)
+    for (int k = 0; k < 18; ++k) u[k] = sA[q][r][c0 + k];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) a[q] = fmaf(p.w[k], sA[q][r][c + k], a[q]);
+    for (int o = 0; o < 8; ++o) {
+      float acc = 0.f;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) hs[q][r][c] = a[q];
+      for (int k = 0; k < 11; ++k) acc = fmaf(p.w[k], u[o + k], acc);
+      hs[q][r][c0 + o] = acc;
+    }
   }
   __syncthreads();
   const float* Ip = I + (int64_t)s * HW;
   const float* Tp = T + (int64_t)(tidx ? tidx[s] : s) * HW;
-  for (int i = threadIdx.x; i < kTS * kTS; i += kThreads) {
-    const int y = i / kTS, x = i - y * kTS;
+  for (int i = threadIdx.x; i < kTS * (kTS / 4); i += kThreads) {
+    const int x = i % kTS, yb = (i / kTS) * 4;
+    float cc[4][3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      float col[14];
+#pragma unroll
+      for (int k = 0; k < 14; ++k) col[k] = hs[q][yb + k][x];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) acc = fmaf(p.w[k], col[o + k], acc);
+        cc[o][q] = acc;
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+    const int y = yb + o;
     const int gy = y0 + y, gx = x0 + x;
     if (!in_img(p, gy, gx)) continue;
-    float c[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < 11; ++k)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) c[q] = fmaf(p.w[k], hs[q][y + k][x], c[q]);
+    const float* c = cc[o];
     const int64_t off = (int64_t)gy * p.W + gx;
     const float iv = Ip[off], tv = Tp[off];
     const float d = iv - tv;
     const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
     const float dssim = fmaf(2.0f * iv, c[1], fmaf(tv, c[2], c[0]));
     dL_dI[(int64_t)s * HW + off] = p.inv_n * fmaf(-p.lam, dssim, sgn);
+    }
   }
 }
 
