@@ -67,6 +67,14 @@ def microscopy_set(synth, seed):
 # form 2 + clamp 1 + exp2 11 + accumulate 1; backward = the same 15 up to the
 # exponential + 5 moment updates (g = G E, 2 sums, 1 product, 1 FMA).
 OPS_PER_EVAL = {"fwd": 16, "bwd": 20}
+# The row-factored form (GP_EXP_POLY_ROW) does its exponentials per row of 8
+# pixels: per row 2 exp2 (22) + 2 clamps + the larger end's exponent 1 + powers
+# r^2..r^7 6 + row coefficients 4, then forward 7 scalings by L + 8 accumulates
+# (50 per row), backward 7 products r^j 2^(C q^2) + 8 products with dL/dI +
+# 24 moment updates + 3 pair sums + 3 products with L + 6 row-moment updates
+# (84 per row), i.e. 50/8 and 84/8 lane instructions per evaluation.
+OPS_PER_EVAL_ROW = {"fwd": 6.25, "bwd": 10.5}
+EXP_MODES = {"poly": 0, "hw": 1, "row": 3}
 
 
 def log(*a):
@@ -318,7 +326,7 @@ def run_native(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    ctx = B.Context(dev_index, exp_mode=B.GP_EXP_HW if args.exp == "hw" else B.GP_EXP_POLY,
+    ctx = B.Context(dev_index, exp_mode=EXP_MODES[args.exp],
                     deterministic=args.det, tile=args.tile, fwd_px=args.fwd_px, bwd_px=args.bwd_px,
                     reuse_bins=not args.rebin)
     stream = torch.cuda.current_stream()
@@ -416,7 +424,8 @@ def run_native(args, rank, world):
     dom = "bwd" if phases["bwd"][0] >= phases["fwd"][0] else "fwd"
     ms_dom, _, calls_dom = phases[dom]
     avg_launch_s = ms_dom * 1e-3 / max(calls_dom, 1)
-    alg_ops_per_launch = float(np.mean(ev_steps)) * OPS_PER_EVAL[dom]
+    ops_table = OPS_PER_EVAL_ROW if args.exp == "row" else OPS_PER_EVAL
+    alg_ops_per_launch = float(np.mean(ev_steps)) * ops_table[dom]
     achieved = alg_ops_per_launch / avg_launch_s / 1e12
     peak = fp32_peak / 1e12
     nominal = 148 * 128 * 2.032e9 / 1e12
@@ -479,7 +488,7 @@ def run_native(args, rank, world):
                              "unit": "Tinst/s (FP32+INT lane instructions)", "frac": achieved / peak,
                              "traffic": traffic, "traffic_note": traffic_note,
                              "peak_kind": "measured FMA probe, burst, same run",
-                             "nominal_peak_2032mhz": nominal, "ops_per_eval": OPS_PER_EVAL[dom]},
+                             "nominal_peak_2032mhz": nominal, "ops_per_eval": ops_table[dom]},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "ms_per_step": float(np.mean(e2e_ms))},
@@ -826,7 +835,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--exp", default="poly", choices=["poly", "hw"])
+    ap.add_argument("--exp", default="poly", choices=sorted(EXP_MODES),
+                    help="exponential: poly (default), hw (SFU ex2.approx) or row (poly, factored per pixel row)")
     ap.add_argument("--det", action="store_true")
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--fwd-px", type=int, default=0)

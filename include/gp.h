@@ -75,12 +75,20 @@ typedef struct gp_ctx gp_ctx;
 #define GP_EXP_HW 1    /* the SFU ex2.approx instruction (benchmarked alternative) */
 #define GP_EXP_POLY_PACKED 2  /* gp_exp2_eval only: GP_EXP_POLY in the packed two-value form
                                  the rasterisers use (bitwise equal to GP_EXP_POLY) */
+#define GP_EXP_POLY_ROW 3     /* GP_EXP_POLY, with the Gaussian factored along each row of 8
+                                 pixels: exp2 of the row's linear part at its larger end and of
+                                 the per-pixel step, powers of the step by multiplication, and
+                                 the quadratic part 2^(c q^2) once per Gaussian and tile, so a
+                                 row costs two exp2 instead of eight (relative error of a few
+                                 ulp per pixel instead of about 2).  Block-culled rasterisers
+                                 only (fwd_px = bwd_px = 0); Gaussians narrower than about 0.3
+                                 pixel fall back to one exp2 per pixel. */
 
 typedef struct {
   float eps;              /* culling bound: truncated mass per pair <= eps (default 1e-6) */
   int deterministic;      /* 1: backward reduces per-pair partials in a fixed order
                              (bitwise repeatable); 0: warp-reduced atomics (default 0) */
-  int exp_mode;           /* GP_EXP_POLY (default) or GP_EXP_HW */
+  int exp_mode;           /* GP_EXP_POLY (default), GP_EXP_HW or GP_EXP_POLY_ROW */
   int tile;               /* screen tile side in pixels: 16 (default) or 8 */
   int fwd_px;             /* forward rasteriser: 0 (default) = block-culled kernel (16x16
                              tiles; 8x8 tiles use one pixel per thread), or the per-thread
@@ -475,6 +483,13 @@ GP_API int64_t gp_launch_count(void);
  * Used to measure the FP32 lane-instruction peak at the clocks in force. */
 GP_API int64_t gp_fma_probe_threads(gp_ctx* ctx);
 GP_API gp_status gp_fma_probe(gp_ctx* ctx, int iters, float* out, void* stream);
+/* The same probe in one of three instruction forms: mode 0 = 8 scalar FFMA
+ * chains (gp_fma_probe), 1 = 8 packed fp32x2 FFMA2 chains, 2 = 4 FFMA2 + 8 FFMA
+ * chains.  gp_fma_probe_lane_fmas(mode) gives the lane FMAs per thread and
+ * iteration (8, 16, 16; 0 for a bad mode).  GP_ERR_ARG for a bad mode, iters
+ * <= 0 or a NULL out. */
+GP_API gp_status gp_fma_probe_mode(gp_ctx* ctx, int mode, int iters, float* out, void* stream);
+GP_API int gp_fma_probe_lane_fmas(int mode);
 
 #ifdef __cplusplus
 }

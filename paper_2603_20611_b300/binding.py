@@ -29,6 +29,7 @@ GP_ERR_STATE = -6
 GP_EXP_POLY = 0
 GP_EXP_HW = 1
 GP_EXP_POLY_PACKED = 2
+GP_EXP_POLY_ROW = 3
 
 # Every symbol include/gp.h declares (checked by the CPU ABI test).
 EXPORTS = (
@@ -41,6 +42,7 @@ EXPORTS = (
     "gp_serve_close", "gp_view_from_axis", "gp_render_slices_view", "gp_render_backward_view",
     "gp_count_evals_view", "gp_adam_default", "gp_adam_state_floats", "gp_adam_init", "gp_adam_step",
     "gp_l1_dssim_grad", "gp_encode", "gp_decode", "gp_serve_load_encoded", "gp_count_vox_evals",
+    "gp_fma_probe_mode", "gp_fma_probe_lane_fmas",
 )
 GP_REQ_SLICE, GP_REQ_STACK, GP_REQ_VOXELIZE = 0, 1, 2
 GP_BATCH_AUTOTUNE = 1
@@ -149,6 +151,8 @@ def _load():
         "gp_launch_count": [],
         "gp_fma_probe_threads": [P],
         "gp_fma_probe": [P, I, P, P],
+        "gp_fma_probe_mode": [P, I, I, P, P],
+        "gp_fma_probe_lane_fmas": [I],
         "gp_mse_grad_noalloc": [P, P, P, I, I, I, P, P, P],
         "gp_batch_plan": [P, ctypes.POINTER(gp_batch_item), I, I, ctypes.POINTER(P)],
         "gp_batch_run": [P, P],
@@ -261,13 +265,15 @@ class Context:
         self.check(lib.gp_timing_read(self.h, ms, ln, cl), "gp_timing_read")
         return {PHASES[k]: (ms[k], ln[k], cl[k]) for k in range(GP_NUM_PHASES)}
 
-    def fma_probe(self, iters, out=None, stream=None):
+    def fma_probe(self, iters, out=None, stream=None, mode=0):
+        """Launch the FP32-pipe probe; returns (out, lane FMAs it performs).
+        mode 0: scalar FFMA chains, 1: packed FFMA2 chains, 2: both mixed."""
         n = int(lib.gp_fma_probe_threads(self.h))
         if out is None:
             out = torch.empty(n, device=f"cuda:{self.device}")
-        self.check(lib.gp_fma_probe(self.h, int(iters), _dev(out, "out", shape=(n,)), _stream(stream)),
-                   "gp_fma_probe")
-        return out, n * int(iters) * 8
+        self.check(lib.gp_fma_probe_mode(self.h, int(mode), int(iters), _dev(out, "out", shape=(n,)),
+                                         _stream(stream)), "gp_fma_probe_mode")
+        return out, n * int(iters) * int(lib.gp_fma_probe_lane_fmas(int(mode)))
 
     def last_counts(self):
         p, e = ctypes.c_int64(), ctypes.c_int64()

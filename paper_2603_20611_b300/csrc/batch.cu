@@ -277,8 +277,8 @@ static gp_status alloc_pairs(gp_plan* p, uint32_t cap, uint32_t n_keys) {
 
 static void set_ctas(gp_plan* p) {
   const int sm = p->c->sm_count;
-  p->ctas_f = std::max(1, raster_batch_ctas_per_sm(p->tile, p->fchunk, false)) * sm;
-  p->ctas_b = std::max(1, raster_batch_ctas_per_sm(p->tile, p->bchunk, true)) * sm;
+  p->ctas_f = std::max(1, raster_batch_ctas_per_sm(p->tile, p->fchunk, false, p->c->cfg.exp_mode)) * sm;
+  p->ctas_b = std::max(1, raster_batch_ctas_per_sm(p->tile, p->bchunk, true, p->c->cfg.exp_mode)) * sm;
 }
 
 static gp_status capture(gp_plan* p) {

@@ -56,7 +56,8 @@ struct BinBufs {
 void note_launch(int k = 1);
 int64_t launch_count();
 int64_t fma_probe_threads(int sm_count);
-void launch_fma_probe(int sm_count, int iters, float* out, cudaStream_t st);
+int fma_probe_lane_fmas(int mode);
+void launch_fma_probe(int sm_count, int mode, int iters, float* out, cudaStream_t st);
 
 struct PhaseEvent {
   int phase;

@@ -62,6 +62,62 @@ __device__ __forceinline__ float edge_q(float cf, float c01, float cv, float inv
   return fmaf(cf * dfix, dfix, fmaf(2.0f * c01 * dfix, t, cv * t * t));
 }
 
+// ---- row factorisation (GP_EXP_POLY_ROW)
+// Along a row the exponent is e(q) = A + B q + C q^2 (C < 0), q = p - 3.5 for
+// the pixels p = 0..7.  With j the pixel's distance in pixels from the row's end
+// where the linear part A + B q is larger (j = 7 - p if B >= 0, j = p if not),
+//     2^e(q) = 2^(A + 3.5 |B|) * (2^-|B|)^j * 2^(C q^2),
+// i.e. two exp2 per row (L = 2^(A + 3.5|B|), r = 2^-|B|), powers of r by
+// multiplication and four per-Gaussian values 2^(C q^2), q^2 in {1/4, 9/4,
+// 25/4, 49/4}.  Every factor but L is <= 1, and since e(q) <= 0 for all real q,
+// A + 3.5 |B| <= 12.25 |C|: with |C| <= 8 L stays below 2^98 and 2^(C q^2)
+// above 2^-98, so no factor overflows and a factor underflows only where the
+// product is below 2^-51.  Narrower Gaussians (C < kRowMinC, a conditional
+// standard deviation under 0.3 pixel) take the per-pixel exp2.
+constexpr float kRowMinC = -8.0f;
+
+template <int EXPM>
+constexpr bool row_factored() { return EXPM == GP_EXP_POLY_ROW; }
+
+// 2^(c q^2) for q = 3.5, 2.5, 1.5, 0.5 (fa) and 0.5, 1.5, 2.5, 3.5 (fb), times s.
+__device__ __forceinline__ void row_quad_factors(float c, float s, float4& fa, float4& fb) {
+  const float2 e01 = exp2_poly2(make_float2(fmaxf(0.25f * c, kExpFloor), fmaxf(2.25f * c, kExpFloor)));
+  const float2 e23 = exp2_poly2(make_float2(fmaxf(6.25f * c, kExpFloor), fmaxf(12.25f * c, kExpFloor)));
+  const float2 s01 = __fmul2_rn(e01, make_float2(s, s)), s23 = __fmul2_rn(e23, make_float2(s, s));
+  fa = make_float4(s23.y, s23.x, s01.y, s01.x);
+  fb = make_float4(s01.x, s01.y, s23.x, s23.y);
+}
+
+// L and r^0..r^7 of one row, as the pairs (r^0, r^1) ... (r^6, r^7) scaled by
+// L (forward) or not (backward, which applies L to the row's sums).
+struct RowPowers {
+  float L;
+  float2 p01, p23, p45, p67;
+};
+
+__device__ __forceinline__ RowPowers row_powers(float A, float aB, bool scale_by_L) {
+  const float2 ex = exp2_poly2(make_float2(fmaxf(fmaf(3.5f, aB, A), kExpFloor), fmaxf(-aB, kExpFloor)));
+  const float r = ex.y, r2 = r * r;
+  const float2 r23 = make_float2(r2, r2 * r);
+  const float2 r45 = __fmul2_rn(make_float2(r2, r2), r23);          // r^4, r^5
+  const float2 r67 = __fmul2_rn(make_float2(r45.x, r45.x), r23);    // r^6, r^7
+  RowPowers w;
+  w.L = ex.x;
+  if (scale_by_L) {
+    const float2 L2 = make_float2(ex.x, ex.x);
+    w.p01 = make_float2(ex.x, ex.x * r);
+    w.p23 = __fmul2_rn(L2, r23);
+    w.p45 = __fmul2_rn(L2, r45);
+    w.p67 = __fmul2_rn(L2, r67);
+  } else {
+    w.p01 = make_float2(1.0f, r);
+    w.p23 = r23;
+    w.p45 = r45;
+    w.p67 = r67;
+  }
+  return w;
+}
+
 // Ballot of the Gaussians jb..jb+31 whose culling ellipse d^T C d <= k2 touches
 // this warp's block (pixel centres [bx + .5, bx + 7.5] x [by + .5, by + 7.5]):
 // the minimum of the quadratic form over the block rectangle, taken at the
@@ -93,9 +149,10 @@ __device__ __forceinline__ int block_hits(const float4* __restrict__ s0, const f
 }
 
 // Shared memory of the forward body.
-template <int TILE, int CH>
+template <int TILE, int CH, bool RF = false>
 struct FwdSmem {
   float4 s0[CH], s1[CH], sc[CH];
+  float4 fa[RF ? CH : 1], fb[RF ? CH : 1];   // row factorisation: a~ 2^(C q^2) per pixel column
   int hitlist[(TILE / 8) * (TILE / 8)][CH];  // per warp: the chunk's Gaussians that hit its block
 };
 
@@ -103,8 +160,10 @@ struct FwdSmem {
 template <int TILE, int CH, int EXPM>
 __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, const SliceRec* __restrict__ rec,
                                          const uint32_t* __restrict__ vals, const uint32_t* __restrict__ emit_gid,
-                                         const uint2* __restrict__ ranges, FwdSmem<TILE, CH>& sm) {
+                                         const uint2* __restrict__ ranges,
+                                         FwdSmem<TILE, CH, row_factored<EXPM>()>& sm) {
   constexpr int NT = (TILE / 8) * (TILE / 8) * 32;
+  constexpr bool RF = row_factored<EXPM>();
   const int T = a.TX * a.TY;
   const int s = local_key / T, t = local_key - s * T;
   const int ty = t / a.TX, tx = t - ty * a.TX;
@@ -128,6 +187,12 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
       sm.s0[j] = a0;
       sm.s1[j] = a1;
       sm.sc[j] = a3;
+      if constexpr (RF) {
+        float4 fa, fb;
+        row_quad_factors(a1.x, a0.z, fa, fb);
+        sm.fa[j] = fa;
+        sm.fb[j] = fb;
+      }
     }
     __syncthreads();
     // test the whole chunk first, so that the hits are taken four at a time
@@ -145,14 +210,29 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
         const float dxc = cxb - g0.x;
         const float A = fmaf(dxc, fmaf(g1.x, dxc, u), g1.z * dy * dy);
         const float Bq = fmaf(2.0f * g1.x, dxc, u);
-        const float2 C2 = make_float2(g1.x, g1.x), B2 = make_float2(Bq, Bq), A2 = make_float2(A, A);
-        const float2 at2 = make_float2(g0.z, g0.z);
-        // two pixels per packed instruction; each lane of a pair is rounded as
-        // the scalar form would round it
+        if (RF && g1.x >= kRowMinC) {
+          // pixel p takes L r^j a~ 2^(C q^2), j = 7 - p when B >= 0 and p otherwise
+          const RowPowers w = row_powers(A, fabsf(Bq), true);
+          const bool rev = Bq >= 0.0f;
+          const float4 fa = sm.fa[jj], fb = sm.fb[jj];
+          const float2 W0 = rev ? make_float2(w.p67.y, w.p67.x) : w.p01;
+          const float2 W1 = rev ? make_float2(w.p45.y, w.p45.x) : w.p23;
+          const float2 W2 = rev ? make_float2(w.p23.y, w.p23.x) : w.p45;
+          const float2 W3 = rev ? make_float2(w.p01.y, w.p01.x) : w.p67;
+          acc[0] = __ffma2_rn(W0, make_float2(fa.x, fa.y), acc[0]);
+          acc[1] = __ffma2_rn(W1, make_float2(fa.z, fa.w), acc[1]);
+          acc[2] = __ffma2_rn(W2, make_float2(fb.x, fb.y), acc[2]);
+          acc[3] = __ffma2_rn(W3, make_float2(fb.z, fb.w), acc[3]);
+        } else {
+          const float2 C2 = make_float2(g1.x, g1.x), B2 = make_float2(Bq, Bq), A2 = make_float2(A, A);
+          const float2 at2 = make_float2(g0.z, g0.z);
+          // two pixels per packed instruction; each lane of a pair is rounded as
+          // the scalar form would round it
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const float2 q = make_float2((float)(2 * p) - 3.5f, (float)(2 * p + 1) - 3.5f);
-          acc[p] = __ffma2_rn(at2, pair_exp2<EXPM>(C2, B2, A2, q), acc[p]);
+          for (int p = 0; p < 4; ++p) {
+            const float2 q = make_float2((float)(2 * p) - 3.5f, (float)(2 * p + 1) - 3.5f);
+            acc[p] = __ffma2_rn(at2, pair_exp2<EXPM>(C2, B2, A2, q), acc[p]);
+          }
         }
       }
       __syncwarp();
@@ -204,14 +284,16 @@ __device__ __forceinline__ bool rect_hit(float4 g0, float4 g1, float4 gc, float 
 // half-block (4 rows of 8 pixels each), the half-blocks 36 floats apart: the
 // 16-byte loads of the same row and column by lanes working on different
 // half-blocks then fall in different banks.
-template <int TILE, int CH>
+template <int TILE, int CH, bool RF = false>
 struct BwdSmem {
   static constexpr int NW = (TILE / 8) * (TILE / 8);
   static constexpr int NH = 2 * NW;  // 8 x 4 half-blocks per tile
   static constexpr int HBS = 36;     // floats per half-block (32 + 4 of padding)
   float4 s0[CH], s1[CH], s2[CH], sc[CH];
+  float4 fa[RF ? CH : 1], fb[RF ? CH : 1];  // row factorisation: 2^(C q^2) per pixel column
   uint32_t sg[CH];
   alignas(16) float G[NH * HBS];
+  alignas(16) float Grev[RF ? NH * HBS : 4];  // row factorisation: G with each row of 8 reversed
   int units[NW][CH * NH / NW];  // per warp: the hit (Gaussian, half-block) pairs it tested, (j << 4) | hb
   int nunits[NW];               // their counts
   unsigned char hmask[CH];      // per Gaussian: which half-blocks were hit (bit hb)
@@ -233,10 +315,12 @@ template <int TILE, int CH, int EXPM, bool DET>
 __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, const SliceRec* __restrict__ rec,
                                          const uint32_t* __restrict__ vals, const uint32_t* __restrict__ emit_gid,
                                          const uint2* __restrict__ ranges, float* __restrict__ accum,
-                                         float4* __restrict__ partial, BwdSmem<TILE, CH>& sm) {
-  constexpr int NW = BwdSmem<TILE, CH>::NW;
-  constexpr int NH = BwdSmem<TILE, CH>::NH;
-  constexpr int HBS = BwdSmem<TILE, CH>::HBS;
+                                         float4* __restrict__ partial,
+                                         BwdSmem<TILE, CH, row_factored<EXPM>()>& sm) {
+  constexpr bool RF = row_factored<EXPM>();
+  constexpr int NW = BwdSmem<TILE, CH, RF>::NW;
+  constexpr int NH = BwdSmem<TILE, CH, RF>::NH;
+  constexpr int HBS = BwdSmem<TILE, CH, RF>::HBS;
   constexpr int NT = NW * 32;
   constexpr int ROUNDS = CH * NH / NT;  // test rounds per chunk
   static_assert((CH * NH) % NT == 0 && NH <= 8 && (NH & (NH - 1)) == 0, "tile / chunk shape");
@@ -253,8 +337,9 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
     const int yy = i / TILE, xx = i - yy * TILE;
     const int py = ty * TILE + yy, px = tx * TILE + xx;
     const int hb = 2 * ((yy >> 3) * (TILE / 8) + (xx >> 3)) + ((yy >> 2) & 1);
-    sm.G[hb * HBS + (yy & 3) * 8 + (xx & 7)] =
-        (py < a.H && px < a.W) ? a.dL_dI[((int64_t)s * a.H + py) * a.W + px] : 0.0f;
+    const float gv = (py < a.H && px < a.W) ? a.dL_dI[((int64_t)s * a.H + py) * a.W + px] : 0.0f;
+    sm.G[hb * HBS + (yy & 3) * 8 + (xx & 7)] = gv;
+    if constexpr (RF) sm.Grev[hb * HBS + (yy & 3) * 8 + (7 - (xx & 7))] = gv;
   }
   for (uint32_t base = rg.x; base < rg.y; base += CH) {
     const int cnt = (int)min((uint32_t)CH, rg.y - base);
@@ -267,6 +352,12 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
       sm.s2[j] = a2;
       sm.sc[j] = a3;
       sm.sg[j] = g;
+      if constexpr (RF) {
+        float4 fa, fb;
+        row_quad_factors(a1.x, 1.0f, fa, fb);
+        sm.fa[j] = fa;
+        sm.fb[j] = fb;
+      }
     }
     __syncthreads();
     // test every (Gaussian, half-block) pair; pair i = j * NH + hb, so the NH
@@ -317,33 +408,75 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
       const float2 C2 = make_float2(c0, c0);
       float M00 = 0.f, M10 = 0.f, M20 = 0.f, M01 = 0.f, M11 = 0.f, M02 = 0.f;
       const float* Gr = sm.G + hb * HBS;
+      if (RF && c0 >= kRowMinC) {
+        // rows in the factored form, summed over j (the distance from the row's
+        // larger end): the pixel of j has q = j - 3.5 when B < 0 and 3.5 - j
+        // when B >= 0, whose dL/dI the reversed copy of the tile supplies
+        const float4 fa = sm.fa[jj], fb = sm.fb[jj];
+        const float2 F01 = make_float2(fa.x, fa.y), F23 = make_float2(fa.z, fa.w);
+        const float2 F45 = make_float2(fb.x, fb.y), F67 = make_float2(fb.z, fb.w);
+        const float* Grv = sm.Grev + hb * HBS;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const float rf = (float)r;
-        const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
-        const float B = fmaf(c1, rf, B0);
-        const float2 A2 = make_float2(A, A), B2 = make_float2(B, B);
-        const float4 ga = *reinterpret_cast<const float4*>(Gr + r * 8);
-        const float4 gb = *reinterpret_cast<const float4*>(Gr + r * 8 + 4);
-        const float2 Gp[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w), make_float2(gb.x, gb.y),
-                              make_float2(gb.z, gb.w)};
-        float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
+        for (int r = 0; r < 4; ++r) {
+          const float rf = (float)r;
+          const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
+          const float B = fmaf(c1, rf, B0);
+          const RowPowers w = row_powers(A, fabsf(B), false);
+          const bool rev = B >= 0.0f;
+          const float* Gj = (rev ? Grv : Gr) + r * 8;
+          const float4 ga = *reinterpret_cast<const float4*>(Gj);
+          const float4 gb = *reinterpret_cast<const float4*>(Gj + 4);
+          const float2 gE[4] = {__fmul2_rn(make_float2(ga.x, ga.y), __fmul2_rn(w.p01, F01)),
+                                __fmul2_rn(make_float2(ga.z, ga.w), __fmul2_rn(w.p23, F23)),
+                                __fmul2_rn(make_float2(gb.x, gb.y), __fmul2_rn(w.p45, F45)),
+                                __fmul2_rn(make_float2(gb.z, gb.w), __fmul2_rn(w.p67, F67))};
+          float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const float qa = (float)(2 * p) - 3.5f, qb = (float)(2 * p + 1) - 3.5f;
-          const float2 q = make_float2(qa, qb);
-          const float2 gE = __fmul2_rn(Gp[p], pair_exp2<EXPM>(C2, B2, A2, q));
-          P0 = __fadd2_rn(P0, gE);
-          P1 = __ffma2_rn(q, gE, P1);
-          P2 = __ffma2_rn(make_float2(qa * qa, qb * qb), gE, P2);
+          for (int p = 0; p < 4; ++p) {
+            const float qa = (float)(2 * p) - 3.5f, qb = (float)(2 * p + 1) - 3.5f;
+            P0 = __fadd2_rn(P0, gE[p]);
+            P1 = __ffma2_rn(make_float2(qa, qb), gE[p], P1);
+            P2 = __ffma2_rn(make_float2(qa * qa, qb * qb), gE[p], P2);
+          }
+          const float S0 = w.L * (P0.x + P0.y);
+          const float S1 = (rev ? -w.L : w.L) * (P1.x + P1.y);
+          const float S2 = w.L * (P2.x + P2.y);
+          M00 += S0;
+          M10 += S1;
+          M20 += S2;
+          M01 = fmaf(rf, S0, M01);
+          M11 = fmaf(rf, S1, M11);
+          M02 = fmaf(rf * rf, S0, M02);
         }
-        const float S0 = P0.x + P0.y, S1 = P1.x + P1.y, S2 = P2.x + P2.y;
-        M00 += S0;
-        M10 += S1;
-        M20 += S2;
-        M01 = fmaf(rf, S0, M01);
-        M11 = fmaf(rf, S1, M11);
-        M02 = fmaf(rf * rf, S0, M02);
+      } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float rf = (float)r;
+          const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
+          const float B = fmaf(c1, rf, B0);
+          const float2 A2 = make_float2(A, A), B2 = make_float2(B, B);
+          const float4 ga = *reinterpret_cast<const float4*>(Gr + r * 8);
+          const float4 gb = *reinterpret_cast<const float4*>(Gr + r * 8 + 4);
+          const float2 Gp[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w), make_float2(gb.x, gb.y),
+                                make_float2(gb.z, gb.w)};
+          float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const float qa = (float)(2 * p) - 3.5f, qb = (float)(2 * p + 1) - 3.5f;
+            const float2 q = make_float2(qa, qb);
+            const float2 gE = __fmul2_rn(Gp[p], pair_exp2<EXPM>(C2, B2, A2, q));
+            P0 = __fadd2_rn(P0, gE);
+            P1 = __ffma2_rn(q, gE, P1);
+            P2 = __ffma2_rn(make_float2(qa * qa, qb * qb), gE, P2);
+          }
+          const float S0 = P0.x + P0.y, S1 = P1.x + P1.y, S2 = P2.x + P2.y;
+          M00 += S0;
+          M10 += S1;
+          M20 += S2;
+          M01 = fmaf(rf, S0, M01);
+          M11 = fmaf(rf, S1, M11);
+          M02 = fmaf(rf * rf, S0, M02);
+        }
       }
       // moments in d = (dxc + q, dy0 + r)
       float* sp = &sm.sp[hb][0][jj];
@@ -403,16 +536,16 @@ template <int TILE, int CH, int EXPM>
 __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? 12 : 32) k_raster_fwd_blk(
     SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges) {
-  __shared__ FwdSmem<TILE, CH> sm;
+  __shared__ FwdSmem<TILE, CH, row_factored<EXPM>()> sm;
   fwd_tile<TILE, CH, EXPM>(a, blockIdx.x, rec, vals, emit_gid, ranges, sm);
 }
 
 template <int TILE, int CH, int EXPM, bool DET>
-__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? 10 : 32) k_raster_bwd_blk(
-    SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
-    const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, float* __restrict__ accum,
-    float4* __restrict__ partial) {
-  __shared__ BwdSmem<TILE, CH> sm;
+__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? (row_factored<EXPM>() ? 8 : 10) : 32)
+    k_raster_bwd_blk(SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
+                     const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges,
+                     float* __restrict__ accum, float4* __restrict__ partial) {
+  __shared__ BwdSmem<TILE, CH, row_factored<EXPM>()> sm;
   bwd_tile<TILE, CH, EXPM, DET>(a, blockIdx.x, rec, vals, emit_gid, ranges, accum, partial, sm);
 }
 
@@ -436,7 +569,7 @@ template <int TILE, int CH, int EXPM>
 __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32) k_raster_fwd_persist(
     BatchItems b, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, unsigned* __restrict__ work) {
-  __shared__ FwdSmem<TILE, CH> sm;
+  __shared__ FwdSmem<TILE, CH, row_factored<EXPM>()> sm;
   __shared__ uint32_t next;
   for (;;) {
     if (threadIdx.x == 0) next = atomicAdd(work, (unsigned)KEY_CHUNK);
@@ -459,7 +592,7 @@ __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32) k_raster_bwd_per
     BatchItems b, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, float* __restrict__ accum,
     float4* __restrict__ partial, unsigned* __restrict__ work) {
-  __shared__ BwdSmem<TILE, CH> sm;
+  __shared__ BwdSmem<TILE, CH, row_factored<EXPM>()> sm;
   __shared__ uint32_t next;
   for (;;) {
     if (threadIdx.x == 0) next = atomicAdd(work, (unsigned)KEY_CHUNK);
@@ -486,6 +619,8 @@ static cudaError_t fwd_blk(const SliceArgs& a, int exp_mode, const SliceRec* rec
   constexpr int NT = (TILE / 8) * (TILE / 8) * 32;
   if (exp_mode == GP_EXP_HW)
     k_raster_fwd_blk<TILE, CH, GP_EXP_HW><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges);
+  else if (exp_mode == GP_EXP_POLY_ROW)
+    k_raster_fwd_blk<TILE, CH, GP_EXP_POLY_ROW><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges);
   else
     k_raster_fwd_blk<TILE, CH, GP_EXP_POLY><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges);
   note_launch();
@@ -511,6 +646,9 @@ static cudaError_t bwd_blk(const SliceArgs& a, int exp_mode, bool det, const Sli
   if (exp_mode == GP_EXP_HW) {
     if (det) k_raster_bwd_blk<TILE, CH, GP_EXP_HW, true><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
     else k_raster_bwd_blk<TILE, CH, GP_EXP_HW, false><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+  } else if (exp_mode == GP_EXP_POLY_ROW) {
+    if (det) k_raster_bwd_blk<TILE, CH, GP_EXP_POLY_ROW, true><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+    else k_raster_bwd_blk<TILE, CH, GP_EXP_POLY_ROW, false><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
   } else {
     if (det) k_raster_bwd_blk<TILE, CH, GP_EXP_POLY, true><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
     else k_raster_bwd_blk<TILE, CH, GP_EXP_POLY, false><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
@@ -537,6 +675,8 @@ static cudaError_t fwd_persist(const BatchItems& b, int ctas, int exp_mode, cons
   constexpr int NT = (TILE / 8) * (TILE / 8) * 32;
   if (exp_mode == GP_EXP_HW)
     k_raster_fwd_persist<TILE, CH, GP_EXP_HW><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, work);
+  else if (exp_mode == GP_EXP_POLY_ROW)
+    k_raster_fwd_persist<TILE, CH, GP_EXP_POLY_ROW><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, work);
   else
     k_raster_fwd_persist<TILE, CH, GP_EXP_POLY><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, work);
   note_launch();
@@ -551,6 +691,9 @@ static cudaError_t bwd_persist(const BatchItems& b, int ctas, int exp_mode, bool
   if (exp_mode == GP_EXP_HW) {
     if (det) k_raster_bwd_persist<TILE, CH, GP_EXP_HW, true><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work);
     else k_raster_bwd_persist<TILE, CH, GP_EXP_HW, false><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work);
+  } else if (exp_mode == GP_EXP_POLY_ROW) {
+    if (det) k_raster_bwd_persist<TILE, CH, GP_EXP_POLY_ROW, true><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work);
+    else k_raster_bwd_persist<TILE, CH, GP_EXP_POLY_ROW, false><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work);
   } else {
     if (det) k_raster_bwd_persist<TILE, CH, GP_EXP_POLY, true><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work);
     else k_raster_bwd_persist<TILE, CH, GP_EXP_POLY, false><<<ctas, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work);
@@ -584,17 +727,22 @@ cudaError_t launch_raster_bwd_batch(const BatchItems& b, int tile, int chunk, in
 }
 
 // Resident CTAs per SM of a persistent kernel (occupancy calculator).
-int raster_batch_ctas_per_sm(int tile, int chunk, bool backward) {
+int raster_batch_ctas_per_sm(int tile, int chunk, bool backward, int exp_mode) {
   int n = 0;
   cudaError_t e = cudaErrorInvalidValue;
+  const bool row = exp_mode == GP_EXP_POLY_ROW;
 #define GP_OCC_F(T, C)                                                                                       \
   if (!backward && tile == T && chunk == C)                                                                  \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd_persist<T, C, GP_EXP_POLY>,          \
-                                                      (T / 8) * (T / 8) * 32, 0);
+    e = row ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd_persist<T, C, GP_EXP_POLY_ROW>, \
+                                                            (T / 8) * (T / 8) * 32, 0)                       \
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd_persist<T, C, GP_EXP_POLY>,     \
+                                                            (T / 8) * (T / 8) * 32, 0);
 #define GP_OCC_B(T, C)                                                                                       \
   if (backward && tile == T && chunk == C)                                                                   \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_bwd_persist<T, C, GP_EXP_POLY, false>,   \
-                                                      (T / 8) * (T / 8) * 32, 0);
+    e = row ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                                 \
+                  &n, k_raster_bwd_persist<T, C, GP_EXP_POLY_ROW, false>, (T / 8) * (T / 8) * 32, 0)        \
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                                 \
+                  &n, k_raster_bwd_persist<T, C, GP_EXP_POLY, false>, (T / 8) * (T / 8) * 32, 0);
   GP_OCC_F(16, 64) GP_OCC_F(16, 128) GP_OCC_F(16, 256) GP_OCC_F(8, 64) GP_OCC_F(8, 128) GP_OCC_F(8, 256)
   GP_OCC_B(16, 32) GP_OCC_B(16, 64) GP_OCC_B(16, 128) GP_OCC_B(8, 32) GP_OCC_B(8, 64) GP_OCC_B(8, 128)
 #undef GP_OCC_F

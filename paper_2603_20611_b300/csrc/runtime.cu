@@ -377,7 +377,8 @@ gp_status gp_create(gp_ctx** out, int device, const gp_config* cfg) {
     c = *cfg;
     if (!(c.eps > 0.0f && c.eps < 1.0f)) return GP_ERR_ARG;
     if (c.tile != 8 && c.tile != 16) return GP_ERR_ARG;
-    if (c.exp_mode != GP_EXP_POLY && c.exp_mode != GP_EXP_HW) return GP_ERR_ARG;
+    if (c.exp_mode != GP_EXP_POLY && c.exp_mode != GP_EXP_HW && c.exp_mode != GP_EXP_POLY_ROW) return GP_ERR_ARG;
+    if (c.exp_mode == GP_EXP_POLY_ROW && (c.fwd_px != 0 || c.bwd_px != 0)) return GP_ERR_ARG;
     if (c.workspace_limit < 0) return GP_ERR_ARG;
     if (c.fwd_px < 0 || (c.fwd_px > 0 && !fwd_px_supported(c.tile, c.fwd_px))) return GP_ERR_ARG;
     if (c.bwd_px < 0 || (c.bwd_px > 0 && !bwd_px_supported(c.tile, c.bwd_px))) return GP_ERR_ARG;
@@ -731,13 +732,19 @@ int64_t gp_launch_count(void) { return launch_count(); }
 
 int64_t gp_fma_probe_threads(gp_ctx* ctx) { return ctx ? fma_probe_threads(ctx->impl.sm_count) : 0; }
 
-gp_status gp_fma_probe(gp_ctx* ctx, int iters, float* out, void* stream) {
+gp_status gp_fma_probe_mode(gp_ctx* ctx, int mode, int iters, float* out, void* stream) {
   if (!ctx) return GP_ERR_ARG;
   Ctx* c = &ctx->impl;
-  if (iters <= 0 || !out) return set_err(c, GP_ERR_ARG, "bad probe arguments");
+  if (iters <= 0 || !out || mode < 0 || mode > 2) return set_err(c, GP_ERR_ARG, "bad probe arguments");
   GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
-  launch_fma_probe(c->sm_count, iters, out, (cudaStream_t)stream);
+  launch_fma_probe(c->sm_count, mode, iters, out, (cudaStream_t)stream);
   return cuda_err(c, cudaGetLastError(), "fma probe");
 }
+
+gp_status gp_fma_probe(gp_ctx* ctx, int iters, float* out, void* stream) {
+  return gp_fma_probe_mode(ctx, 0, iters, out, stream);
+}
+
+int gp_fma_probe_lane_fmas(int mode) { return (mode >= 0 && mode <= 2) ? fma_probe_lane_fmas(mode) : 0; }
 
 }  // extern "C"

@@ -61,7 +61,7 @@ cudaError_t launch_raster_bwd_batch(const BatchItems& b, int tile, int chunk, in
                                     const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
                                     const uint2* ranges, float* accum, float4* partial, unsigned* work,
                                     cudaStream_t st);
-int raster_batch_ctas_per_sm(int tile, int chunk, bool backward);
+int raster_batch_ctas_per_sm(int tile, int chunk, bool backward, int exp_mode);
 
 // K-pre: records + per-Gaussian pair counts.
 void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st);
