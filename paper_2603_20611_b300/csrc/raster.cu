@@ -295,9 +295,7 @@ struct BwdSmem {
   alignas(16) float G[NH * HBS];
   alignas(16) float Grev[RF ? NH * HBS : 4];  // row factorisation: G with each row of 8 reversed
   int units[NW][CH * NH / NW];  // per warp: the hit (Gaussian, half-block) pairs it tested, (j << 4) | hb
-  int nunits[NW];               // their counts
-  unsigned char hmask[CH];      // per Gaussian: which half-blocks were hit (bit hb)
-  float sp[NH][6][CH];          // per (half-block, Gaussian): the six pixel moments
+  float acc[6][CH];             // per Gaussian: the six pixel moments summed over its half-blocks
 };
 
 // Backward of one (slice s, tile t) of item a.  The tile is cut into 8 x 4
@@ -322,8 +320,9 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
   constexpr int NH = BwdSmem<TILE, CH, RF>::NH;
   constexpr int HBS = BwdSmem<TILE, CH, RF>::HBS;
   constexpr int NT = NW * 32;
-  constexpr int ROUNDS = CH * NH / NT;  // test rounds per chunk
-  static_assert((CH * NH) % NT == 0 && NH <= 8 && (NH & (NH - 1)) == 0, "tile / chunk shape");
+  constexpr int CW = CH / NW;  // Gaussians per warp chunk
+  static_assert(CW * NH == CH * NH / NW && CW * NH % 32 == 0 && NH <= 8 && (NH & (NH - 1)) == 0,
+                "tile / chunk shape");
   const uint2 rg = ranges[a.key_base + (uint32_t)local_key];
   if (rg.y <= rg.x) return;  // uniform over the CTA
   const int T = a.TX * a.TY;
@@ -341,10 +340,18 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
     sm.G[hb * HBS + (yy & 3) * 8 + (xx & 7)] = gv;
     if constexpr (RF) sm.Grev[hb * HBS + (yy & 3) * 8 + (7 - (xx & 7))] = gv;
   }
-  for (uint32_t base = rg.x; base < rg.y; base += CH) {
-    const int cnt = (int)min((uint32_t)CH, rg.y - base);
-    for (int j = threadIdx.x; j < cnt; j += NT) {
-      const uint32_t g = emit_gid[vals[base + j]];
+  __syncthreads();
+  // From here on every warp works alone on its own chunks of the list: it
+  // stages CW Gaussians into its own slots, tests them against all NH
+  // half-blocks, evaluates the hits and folds them, so a Gaussian's units
+  // never leave the warp and warps need no block-wide barrier.
+  const int slot0 = warp * CW;
+  int* units = sm.units[warp];
+  for (uint32_t base = rg.x + (uint32_t)slot0; base < rg.y; base += CH) {
+    const int cnt = (int)min((uint32_t)CW, rg.y - base);
+    for (int jl = lane; jl < cnt; jl += 32) {
+      const int j = slot0 + jl;
+      const uint32_t g = emit_gid[vals[base + jl]];
       float4 a0, a1, a2, a3;
       stage_blk<EXPM>(rec, g, zsv, x0, y0, a0, a1, a2, a3);
       sm.s0[j] = a0;
@@ -352,6 +359,8 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
       sm.s2[j] = a2;
       sm.sc[j] = a3;
       sm.sg[j] = g;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) sm.acc[k][j] = 0.0f;
       if constexpr (RF) {
         float4 fa, fb;
         row_quad_factors(a1.x, 1.0f, fa, fb);
@@ -359,144 +368,153 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
         sm.fb[j] = fb;
       }
     }
-    __syncthreads();
-    // test every (Gaussian, half-block) pair; pair i = j * NH + hb, so the NH
-    // tests of one Gaussian sit in NH consecutive lanes
+    __syncwarp();
+    // test every (Gaussian, half-block) pair of the warp's chunk; pair i =
+    // jl * NH + hb, so the NH tests of one Gaussian sit in NH consecutive lanes
     int nu = 0;
-    int* units = sm.units[warp];
+    const int rounds = (cnt * NH + 31) / 32;
 #pragma unroll 1
-    for (int r = 0; r < ROUNDS; ++r) {
-      const int i = (r * NW + warp) * 32 + lane;
-      const int j = i / NH, hb = i & (NH - 1);
+    for (int r = 0; r < rounds; ++r) {
+      const int i = r * 32 + lane;
+      const int jl = i / NH, hb = i & (NH - 1);
+      const int j = slot0 + jl;
       bool hit = false;
-      if (j < cnt) {
+      if (jl < cnt) {
         const float bxf = (float)(((hb >> 1) % (TILE / 8)) * 8);
         const float byf = (float)(((hb >> 1) / (TILE / 8)) * 8 + 4 * (hb & 1));
         hit = rect_hit(sm.s0[j], sm.s1[j], sm.sc[j], bxf + 0.5f, bxf + 7.5f, byf + 0.5f, byf + 3.5f, a.k2);
       }
       const unsigned m = __ballot_sync(0xffffffffu, hit);
       if (hit) units[nu + __popc(m & ((1u << lane) - 1u))] = (j << 4) | hb;
-      if ((lane & (NH - 1)) == 0 && j < CH) sm.hmask[j] = (unsigned char)((m >> lane) & ((1u << NH) - 1u));
       nu += __popc(m);
     }
-    if (lane == 0) sm.nunits[warp] = nu;
-    __syncthreads();
-    // every thread forms the offsets of the NW per-warp lists itself
-    int offs[NW + 1];
-    offs[0] = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) offs[w + 1] = offs[w] + sm.nunits[w];
-    const int total = offs[NW];
-    for (int u = threadIdx.x; u < total; u += NT) {
-      int w = 0;
-#pragma unroll
-      for (int k = 1; k < NW; ++k) w += (u >= offs[k]);
-      int base_w = offs[0];
-#pragma unroll
-      for (int k = 1; k < NW; ++k) base_w = (w == k) ? offs[k] : base_w;
-      const int code = sm.units[w][u - base_w];
+    __syncwarp();
+    // units in rounds of 32; the units of one Gaussian are consecutive (the
+    // list is Gaussian-major), so after each round a segmented scan over the
+    // lanes sums them and the segment's last lane adds the sum to the
+    // Gaussian's accumulators (a fixed order: the sums are reproducible)
+    for (int u0 = 0; u0 < nu; u0 += 32) {
+      const int u = u0 + lane;
+      const bool valid = u < nu;
+      const int code = valid ? units[u] : -16;  // an idle lane is its own segment, Gaussian -1
       const int jj = code >> 4, hb = code & 15;
-      const float4 g0 = sm.s0[jj], g1 = sm.s1[jj];
-      const float c0 = g1.x, c1 = g1.y, c2 = g1.z;
-      const int hbx = ((hb >> 1) % (TILE / 8)) * 8, hby = ((hb >> 1) / (TILE / 8)) * 8 + 4 * (hb & 1);
-      const float dxc = (float)hbx + 4.0f - g0.x, dy0 = (float)hby + 0.5f - g0.y;
-      // row r of the half-block: exponent A(r) + B(r) q + c0 q^2 along the row,
-      // q the offset from the half-block's centre column
-      const float A0 = fmaf(dxc, fmaf(c0, dxc, c1 * dy0), c2 * dy0 * dy0);
-      const float A1 = fmaf(c1, dxc, 2.0f * c2 * dy0);
-      const float B0 = fmaf(2.0f * c0, dxc, c1 * dy0);
-      const float2 C2 = make_float2(c0, c0);
-      float M00 = 0.f, M10 = 0.f, M20 = 0.f, M01 = 0.f, M11 = 0.f, M02 = 0.f;
-      const float* Gr = sm.G + hb * HBS;
-      if (RF && c0 >= kRowMinC) {
-        // rows in the factored form, summed over j (the distance from the row's
-        // larger end): the pixel of j has q = j - 3.5 when B < 0 and 3.5 - j
-        // when B >= 0, whose dL/dI the reversed copy of the tile supplies
-        const float4 fa = sm.fa[jj], fb = sm.fb[jj];
-        const float2 F01 = make_float2(fa.x, fa.y), F23 = make_float2(fa.z, fa.w);
-        const float2 F45 = make_float2(fb.x, fb.y), F67 = make_float2(fb.z, fb.w);
-        const float* Grv = sm.Grev + hb * HBS;
+      float mom[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (valid) {
+        const float4 g0 = sm.s0[jj], g1 = sm.s1[jj];
+        const float c0 = g1.x, c1 = g1.y, c2 = g1.z;
+        const int hbx = ((hb >> 1) % (TILE / 8)) * 8, hby = ((hb >> 1) / (TILE / 8)) * 8 + 4 * (hb & 1);
+        const float dxc = (float)hbx + 4.0f - g0.x, dy0 = (float)hby + 0.5f - g0.y;
+        // row r of the half-block: exponent A(r) + B(r) q + c0 q^2 along the row,
+        // q the offset from the half-block's centre column
+        const float A0 = fmaf(dxc, fmaf(c0, dxc, c1 * dy0), c2 * dy0 * dy0);
+        const float A1 = fmaf(c1, dxc, 2.0f * c2 * dy0);
+        const float B0 = fmaf(2.0f * c0, dxc, c1 * dy0);
+        const float2 C2 = make_float2(c0, c0);
+        float M00 = 0.f, M10 = 0.f, M20 = 0.f, M01 = 0.f, M11 = 0.f, M02 = 0.f;
+        const float* Gr = sm.G + hb * HBS;
+        if (RF && c0 >= kRowMinC) {
+          // rows in the factored form, summed over j (the distance from the row's
+          // larger end): the pixel of j has q = j - 3.5 when B < 0 and 3.5 - j
+          // when B >= 0, whose dL/dI the reversed copy of the tile supplies
+          const float4 fa = sm.fa[jj], fb = sm.fb[jj];
+          const float2 F01 = make_float2(fa.x, fa.y), F23 = make_float2(fa.z, fa.w);
+          const float2 F45 = make_float2(fb.x, fb.y), F67 = make_float2(fb.z, fb.w);
+          const float* Grv = sm.Grev + hb * HBS;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const float rf = (float)r;
-          const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
-          const float B = fmaf(c1, rf, B0);
-          const RowPowers w = row_powers(A, fabsf(B), false);
-          const bool rev = B >= 0.0f;
-          const float* Gj = (rev ? Grv : Gr) + r * 8;
-          const float4 ga = *reinterpret_cast<const float4*>(Gj);
-          const float4 gb = *reinterpret_cast<const float4*>(Gj + 4);
-          const float2 gE[4] = {__fmul2_rn(make_float2(ga.x, ga.y), __fmul2_rn(w.p01, F01)),
-                                __fmul2_rn(make_float2(ga.z, ga.w), __fmul2_rn(w.p23, F23)),
-                                __fmul2_rn(make_float2(gb.x, gb.y), __fmul2_rn(w.p45, F45)),
-                                __fmul2_rn(make_float2(gb.z, gb.w), __fmul2_rn(w.p67, F67))};
-          float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
+          for (int r = 0; r < 4; ++r) {
+            const float rf = (float)r;
+            const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
+            const float B = fmaf(c1, rf, B0);
+            const RowPowers w = row_powers(A, fabsf(B), false);
+            const bool rev = B >= 0.0f;
+            const float* Gj = (rev ? Grv : Gr) + r * 8;
+            const float4 ga = *reinterpret_cast<const float4*>(Gj);
+            const float4 gb = *reinterpret_cast<const float4*>(Gj + 4);
+            const float2 gE[4] = {__fmul2_rn(make_float2(ga.x, ga.y), __fmul2_rn(w.p01, F01)),
+                                  __fmul2_rn(make_float2(ga.z, ga.w), __fmul2_rn(w.p23, F23)),
+                                  __fmul2_rn(make_float2(gb.x, gb.y), __fmul2_rn(w.p45, F45)),
+                                  __fmul2_rn(make_float2(gb.z, gb.w), __fmul2_rn(w.p67, F67))};
+            float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const float qa = (float)(2 * p) - 3.5f, qb = (float)(2 * p + 1) - 3.5f;
-            P0 = __fadd2_rn(P0, gE[p]);
-            P1 = __ffma2_rn(make_float2(qa, qb), gE[p], P1);
-            P2 = __ffma2_rn(make_float2(qa * qa, qb * qb), gE[p], P2);
+            for (int p = 0; p < 4; ++p) {
+              const float qa = (float)(2 * p) - 3.5f, qb = (float)(2 * p + 1) - 3.5f;
+              P0 = __fadd2_rn(P0, gE[p]);
+              P1 = __ffma2_rn(make_float2(qa, qb), gE[p], P1);
+              P2 = __ffma2_rn(make_float2(qa * qa, qb * qb), gE[p], P2);
+            }
+            const float S0 = w.L * (P0.x + P0.y);
+            const float S1 = (rev ? -w.L : w.L) * (P1.x + P1.y);
+            const float S2 = w.L * (P2.x + P2.y);
+            M00 += S0;
+            M10 += S1;
+            M20 += S2;
+            M01 = fmaf(rf, S0, M01);
+            M11 = fmaf(rf, S1, M11);
+            M02 = fmaf(rf * rf, S0, M02);
           }
-          const float S0 = w.L * (P0.x + P0.y);
-          const float S1 = (rev ? -w.L : w.L) * (P1.x + P1.y);
-          const float S2 = w.L * (P2.x + P2.y);
-          M00 += S0;
-          M10 += S1;
-          M20 += S2;
-          M01 = fmaf(rf, S0, M01);
-          M11 = fmaf(rf, S1, M11);
-          M02 = fmaf(rf * rf, S0, M02);
+        } else {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const float rf = (float)r;
+            const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
+            const float B = fmaf(c1, rf, B0);
+            const float2 A2 = make_float2(A, A), B2 = make_float2(B, B);
+            const float4 ga = *reinterpret_cast<const float4*>(Gr + r * 8);
+            const float4 gb = *reinterpret_cast<const float4*>(Gr + r * 8 + 4);
+            const float2 Gp[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w), make_float2(gb.x, gb.y),
+                                  make_float2(gb.z, gb.w)};
+            float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+              const float qa = (float)(2 * p) - 3.5f, qb = (float)(2 * p + 1) - 3.5f;
+              const float2 q = make_float2(qa, qb);
+              const float2 gE = __fmul2_rn(Gp[p], pair_exp2<EXPM>(C2, B2, A2, q));
+              P0 = __fadd2_rn(P0, gE);
+              P1 = __ffma2_rn(q, gE, P1);
+              P2 = __ffma2_rn(make_float2(qa * qa, qb * qb), gE, P2);
+            }
+            const float S0 = P0.x + P0.y, S1 = P1.x + P1.y, S2 = P2.x + P2.y;
+            M00 += S0;
+            M10 += S1;
+            M20 += S2;
+            M01 = fmaf(rf, S0, M01);
+            M11 = fmaf(rf, S1, M11);
+            M02 = fmaf(rf * rf, S0, M02);
+          }
         }
-      } else {
+        // moments in d = (dxc + q, dy0 + r)
+        mom[0] = M00;
+        mom[1] = fmaf(dxc, M00, M10);
+        mom[2] = fmaf(dy0, M00, M01);
+        mom[3] = fmaf(dxc, fmaf(dxc, M00, 2.0f * M10), M20);
+        mom[4] = fmaf(dxc, fmaf(dy0, M00, M01), fmaf(dy0, M10, M11));
+        mom[5] = fmaf(dy0, fmaf(dy0, M00, 2.0f * M01), M02);
+      }
+      // segmented inclusive scan: a Gaussian has at most NH units, so offsets
+      // 1, 2, ..., NH / 2 reach the whole segment
+      const int jprev = __shfl_up_sync(0xffffffffu, jj, 1);
+      const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || jprev != jj);
+      const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const float rf = (float)r;
-          const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
-          const float B = fmaf(c1, rf, B0);
-          const float2 A2 = make_float2(A, A), B2 = make_float2(B, B);
-          const float4 ga = *reinterpret_cast<const float4*>(Gr + r * 8);
-          const float4 gb = *reinterpret_cast<const float4*>(Gr + r * 8 + 4);
-          const float2 Gp[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w), make_float2(gb.x, gb.y),
-                                make_float2(gb.z, gb.w)};
-          float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
+      for (int o = 1; o < NH; o <<= 1) {
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const float qa = (float)(2 * p) - 3.5f, qb = (float)(2 * p + 1) - 3.5f;
-            const float2 q = make_float2(qa, qb);
-            const float2 gE = __fmul2_rn(Gp[p], pair_exp2<EXPM>(C2, B2, A2, q));
-            P0 = __fadd2_rn(P0, gE);
-            P1 = __ffma2_rn(q, gE, P1);
-            P2 = __ffma2_rn(make_float2(qa * qa, qb * qb), gE, P2);
-          }
-          const float S0 = P0.x + P0.y, S1 = P1.x + P1.y, S2 = P2.x + P2.y;
-          M00 += S0;
-          M10 += S1;
-          M20 += S2;
-          M01 = fmaf(rf, S0, M01);
-          M11 = fmaf(rf, S1, M11);
-          M02 = fmaf(rf * rf, S0, M02);
+        for (int k = 0; k < 6; ++k) {
+          const float t = __shfl_up_sync(0xffffffffu, mom[k], o);
+          if (lane - o >= start) mom[k] += t;
         }
       }
-      // moments in d = (dxc + q, dy0 + r)
-      float* sp = &sm.sp[hb][0][jj];
-      sp[0 * CH] = M00;
-      sp[1 * CH] = fmaf(dxc, M00, M10);
-      sp[2 * CH] = fmaf(dy0, M00, M01);
-      sp[3 * CH] = fmaf(dxc, fmaf(dxc, M00, 2.0f * M10), M20);
-      sp[4 * CH] = fmaf(dxc, fmaf(dy0, M00, M01), fmaf(dy0, M10, M11));
-      sp[5 * CH] = fmaf(dy0, fmaf(dy0, M00, 2.0f * M01), M02);
+      const int jnext = __shfl_down_sync(0xffffffffu, jj, 1);
+      if (valid && (lane == 31 || u + 1 == nu || jnext != jj)) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sm.acc[k][jj] += mom[k];
+      }
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < cnt; j += NT) {
-      float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      const unsigned hm = sm.hmask[j];
+    __syncwarp();
+    for (int jl = lane; jl < cnt; jl += 32) {
+      const int j = slot0 + jl;
+      float m[6];
 #pragma unroll
-      for (int hb = 0; hb < NH; ++hb)
-        if ((hm >> hb) & 1u) {
-#pragma unroll
-          for (int k = 0; k < 6; ++k) m[k] += sm.sp[hb][k][j];
-        }
+      for (int k = 0; k < 6; ++k) m[k] = sm.acc[k][j];
       const float4 g0 = sm.s0[j], g1 = sm.s1[j], g2 = sm.s2[j];
       const float at = g0.z;
       const float C00 = g1.w, C01 = g2.z, C11 = g0.w;
@@ -509,7 +527,7 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
       const float gc11 = -0.5f * at * m[5];
       const float d = g2.x, w = g2.y;
       if constexpr (DET) {
-        const uint32_t e = vals[base + j];
+        const uint32_t e = vals[base + jl];
         partial[2 * (size_t)e] = make_float4(g_at, gmx, gmy, gc00);
         partial[2 * (size_t)e + 1] = make_float4(gc01, gc11, d, w);
       } else {
@@ -527,7 +545,7 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
         atomicAdd(A + 9, gc11);
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -663,8 +681,8 @@ cudaError_t launch_raster_bwd_blocked(const SliceArgs& a, int exp_mode, bool det
   if ((int64_t)a.S * a.TX * a.TY == 0) return cudaSuccess;
   SliceArgs b = a;
   b.dL_dI = dL_dI;
-  if (a.tile == 16) return bwd_blk<16, 64>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
-  if (a.tile == 8) return bwd_blk<8, 64>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
+  if (a.tile == 16) return bwd_blk<16, 128>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
+  if (a.tile == 8) return bwd_blk<8, 32>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
   return cudaErrorInvalidValue;
 }
 
