@@ -35,14 +35,56 @@
 
 namespace gp {
 
+// Cells of a TILE x TILE tile (bands of BH pixel rows by columns of 8 pixels)
+// whose pixel centres the culling ellipse d^T C d <= k2 touches, as a bit mask:
+// band b, column c is bit b * (TILE / 8) + c for 8-row bands (the 8 x 8
+// blocks) and 2 (b / 2 * (TILE / 8) + c) + b % 2 for 4-row bands (the 8 x 4
+// half-blocks, so the two halves of a block are adjacent bits).  Over a band's
+// pixel-centre heights the ellipse spans x in [xmin, xmax]: its chord at height
+// dy (from the centre) is centred on -s dy, s = C01 / C00, with half-width
+// sqrt((k2 - D dy^2) / C00), D = C11 - C01^2 / C00 = k2 / ry^2 (ry the
+// ellipse's half-height), and its right (left) end is furthest out at the
+// height dyt of the rightmost point (-dyt), clamped to the band.  A cell is
+// touched iff its column's pixel centres meet [xmin, xmax]; the interval is
+// widened by 1e-3 pixel so that rounding only ever adds cells (an extra cell
+// adds pixels where every term is below eps).
+//   r2 = (C00, C01, C11, rx), r3 = (ry, valid, 1/C00, 1/C11); (mx, my) the
+//   tile-relative centre.
+constexpr float kCellTol = 1e-3f;
+
+template <int TILE, int BH>
+__device__ __forceinline__ unsigned ellipse_cells(float4 r2, float4 r3, float mx, float my, float k2) {
+  const float ry = r3.x, inv00 = r3.z;
+  const float s = r2.y * inv00;
+  const float D = k2 / (ry * ry);
+  const float dyt = -r2.y * r3.w * r2.w;
+  unsigned m = 0u;
+#pragma unroll
+  for (int b = 0; b < TILE / BH; ++b) {
+    const float dya = fmaxf((float)(b * BH) + 0.5f - my, -ry);
+    const float dyb = fminf((float)(b * BH + BH) - 0.5f - my, ry);
+    if (dya <= dyb) {
+      const float dM = fminf(fmaxf(dyt, dya), dyb), dm = fminf(fmaxf(-dyt, dya), dyb);
+      const float xmax = fmaf(-s, dM, mx) + sqrtf(fmaxf((k2 - D * dM * dM) * inv00, 0.0f)) + kCellTol;
+      const float xmin = fmaf(-s, dm, mx) - sqrtf(fmaxf((k2 - D * dm * dm) * inv00, 0.0f)) - kCellTol;
+#pragma unroll
+      for (int c = 0; c < TILE / 8; ++c) {
+        const int bit = BH == 8 ? b * (TILE / 8) + c : 2 * ((b >> 1) * (TILE / 8) + c) + (b & 1);
+        if (xmin <= (float)(8 * c) + 7.5f && xmax >= (float)(8 * c) + 0.5f) m |= 1u << bit;
+      }
+    }
+  }
+  return m;
+}
+
 // Staging of one Gaussian for one (slice, tile):
 //   s0 = (mu_2d,x - x0, mu_2d,y - y0, a~, C11)
 //   s1 = (c0, c1, c2, C00)     e = c0 dx^2 + c1 dx dy + c2 dy^2 = -log2(e)/2 d^T C d
 //   s2 = (delta, opacity_r, C01, 0)    (backward)
-//   sc = (C01, 1/C00, 1/C11, 0)        block test
-template <int EXPM>
-__device__ __forceinline__ void stage_blk(const SliceRec* __restrict__ rec, uint32_t g, float zsv, float x0,
-                                          float y0, float4& s0, float4& s1, float4& s2, float4& sc) {
+// and the mask of the cells (bands of BH rows) its culling ellipse touches.
+template <int EXPM, int TILE, int BH>
+__device__ __forceinline__ unsigned stage_blk(const SliceRec* __restrict__ rec, uint32_t g, float zsv, float x0,
+                                              float y0, float k2, float4& s0, float4& s1, float4& s2) {
   const float4* rp = reinterpret_cast<const float4*>(rec + g);
   const float4 r0 = __ldg(rp), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3);
   const float d = r0.z - zsv;
@@ -53,13 +95,7 @@ __device__ __forceinline__ void stage_blk(const SliceRec* __restrict__ rec, uint
   s0 = make_float4(mxr, myr, r1.z * w, C11);
   s1 = make_float4(-0.5f * kLog2e * C00, -kLog2e * C01, -0.5f * kLog2e * C11, C00);
   s2 = make_float4(d, w, C01, 0.0f);
-  sc = make_float4(C01, r3.z, r3.w, 0.0f);
-}
-
-// min over the segment of the quadratic form along one block edge
-__device__ __forceinline__ float edge_q(float cf, float c01, float cv, float inv_v, float dfix, float lo, float hi) {
-  const float t = fminf(fmaxf(-c01 * dfix * inv_v, lo), hi);
-  return fmaf(cf * dfix, dfix, fmaf(2.0f * c01 * dfix, t, cv * t * t));
+  return ellipse_cells<TILE, BH>(r2, r3, mxr, myr, k2);
 }
 
 // ---- row factorisation (GP_EXP_POLY_ROW)
@@ -118,41 +154,12 @@ __device__ __forceinline__ RowPowers row_powers(float A, float aB, bool scale_by
   return w;
 }
 
-// Ballot of the Gaussians jb..jb+31 whose culling ellipse d^T C d <= k2 touches
-// this warp's block (pixel centres [bx + .5, bx + 7.5] x [by + .5, by + 7.5]):
-// the minimum of the quadratic form over the block rectangle, taken at the
-// centre if it lies inside and otherwise on the nearest of the four edges.
-// Their chunk indices are compacted into list[0..n) (list points past the hits
-// already found in this chunk).  Returns n.
-__device__ __forceinline__ int block_hits(const float4* __restrict__ s0, const float4* __restrict__ s1,
-                                          const float4* __restrict__ sc, int jb, int cnt, float bx, float by,
-                                          float k2, int lane, int* list) {
-  const int j = jb + lane;
-  bool hit = false;
-  if (j < cnt) {
-    const float4 g0 = s0[j], g1 = s1[j], gc = sc[j];
-    const float C00 = g1.w, C01 = gc.x, C11 = g0.w;
-    const float xl = bx + 0.5f - g0.x, xh = bx + 7.5f - g0.x;
-    const float yl = by + 0.5f - g0.y, yh = by + 7.5f - g0.y;
-    if (xl <= 0.0f && xh >= 0.0f && yl <= 0.0f && yh >= 0.0f) {
-      hit = true;
-    } else {
-      float m = fminf(edge_q(C00, C01, C11, gc.z, xl, yl, yh), edge_q(C00, C01, C11, gc.z, xh, yl, yh));
-      m = fminf(m, fminf(edge_q(C11, C01, C00, gc.y, yl, xl, xh), edge_q(C11, C01, C00, gc.y, yh, xl, xh)));
-      hit = m <= k2;
-    }
-  }
-  const unsigned msk = __ballot_sync(0xffffffffu, hit);
-  if (hit) list[__popc(msk & ((1u << lane) - 1u))] = j;
-  __syncwarp();
-  return __popc(msk);
-}
-
 // Shared memory of the forward body.
 template <int TILE, int CH, bool RF = false>
 struct FwdSmem {
-  float4 s0[CH], s1[CH], sc[CH];
+  float4 s0[CH], s1[CH];
   float4 fa[RF ? CH : 1], fb[RF ? CH : 1];   // row factorisation: a~ 2^(C q^2) per pixel column
+  unsigned char bmask[CH];                   // per Gaussian: the 8 x 8 blocks its ellipse touches
   int hitlist[(TILE / 8) * (TILE / 8)][CH];  // per warp: the chunk's Gaussians that hit its block
 };
 
@@ -182,11 +189,11 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
   for (uint32_t base = rg.x; base < rg.y; base += CH) {
     const int cnt = (int)min((uint32_t)CH, rg.y - base);
     for (int j = threadIdx.x; j < cnt; j += NT) {
-      float4 a0, a1, a2, a3;
-      stage_blk<EXPM>(rec, emit_gid[vals[base + j]], zsv, x0, y0, a0, a1, a2, a3);
+      float4 a0, a1, a2;
+      sm.bmask[j] = (unsigned char)stage_blk<EXPM, TILE, 8>(rec, emit_gid[vals[base + j]], zsv, x0, y0, a.k2, a0,
+                                                            a1, a2);
       sm.s0[j] = a0;
       sm.s1[j] = a1;
-      sm.sc[j] = a3;
       if constexpr (RF) {
         float4 fa, fb;
         row_quad_factors(a1.x, a0.z, fa, fb);
@@ -198,7 +205,14 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
     // test the whole chunk first, so that the hits are taken four at a time
     // with at most one partly idle round per chunk
     int nh = 0;
-    for (int jb = 0; jb < cnt; jb += 32) nh += block_hits(sm.s0, sm.s1, sm.sc, jb, cnt, bx, by, a.k2, lane, list + nh);
+    for (int jb = 0; jb < cnt; jb += 32) {
+      const int j = jb + lane;
+      const bool hit = j < cnt && ((sm.bmask[j] >> warp) & 1u);
+      const unsigned msk = __ballot_sync(0xffffffffu, hit);
+      if (hit) list[nh + __popc(msk & ((1u << lane) - 1u))] = j;
+      nh += __popc(msk);
+    }
+    __syncwarp();
     {
       for (int h = grp; h < nh; h += 4) {
         const int jj = list[h];
@@ -268,18 +282,6 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
 
 constexpr int ACC10 = 10;
 
-// Rectangle test of one staged Gaussian (as block_hits): does its culling
-// ellipse touch the pixel centres [x0, x1] x [y0, y1] (tile-relative)?
-__device__ __forceinline__ bool rect_hit(float4 g0, float4 g1, float4 gc, float x0, float x1, float y0, float y1,
-                                         float k2) {
-  const float C00 = g1.w, C01 = gc.x, C11 = g0.w;
-  const float xl = x0 - g0.x, xh = x1 - g0.x, yl = y0 - g0.y, yh = y1 - g0.y;
-  if (xl <= 0.0f && xh >= 0.0f && yl <= 0.0f && yh >= 0.0f) return true;
-  float m = fminf(edge_q(C00, C01, C11, gc.z, xl, yl, yh), edge_q(C00, C01, C11, gc.z, xh, yl, yh));
-  m = fminf(m, fminf(edge_q(C11, C01, C00, gc.y, yl, xl, xh), edge_q(C11, C01, C00, gc.y, yh, xl, xh)));
-  return m <= k2;
-}
-
 // Shared memory of the backward body.  The tile's dL/dI is held half-block by
 // half-block (4 rows of 8 pixels each), the half-blocks 36 floats apart: the
 // 16-byte loads of the same row and column by lanes working on different
@@ -289,7 +291,7 @@ struct BwdSmem {
   static constexpr int NW = (TILE / 8) * (TILE / 8);
   static constexpr int NH = 2 * NW;  // 8 x 4 half-blocks per tile
   static constexpr int HBS = 36;     // floats per half-block (32 + 4 of padding)
-  float4 s0[CH], s1[CH], s2[CH], sc[CH];
+  float4 s0[CH], s1[CH], s2[CH];
   float4 fa[RF ? CH : 1], fb[RF ? CH : 1];  // row factorisation: 2^(C q^2) per pixel column
   uint32_t sg[CH];
   alignas(16) float G[NH * HBS];
@@ -342,51 +344,52 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
   }
   __syncthreads();
   // From here on every warp works alone on its own chunks of the list: it
-  // stages CW Gaussians into its own slots, tests them against all NH
-  // half-blocks, evaluates the hits and folds them, so a Gaussian's units
-  // never leave the warp and warps need no block-wide barrier.
+  // stages CW Gaussians into its own slots with the half-blocks each one's
+  // ellipse touches, evaluates those units and folds them, so a Gaussian's
+  // units never leave the warp and warps need no block-wide barrier.
   const int slot0 = warp * CW;
   int* units = sm.units[warp];
   for (uint32_t base = rg.x + (uint32_t)slot0; base < rg.y; base += CH) {
     const int cnt = (int)min((uint32_t)CW, rg.y - base);
-    for (int jl = lane; jl < cnt; jl += 32) {
-      const int j = slot0 + jl;
-      const uint32_t g = emit_gid[vals[base + jl]];
-      float4 a0, a1, a2, a3;
-      stage_blk<EXPM>(rec, g, zsv, x0, y0, a0, a1, a2, a3);
-      sm.s0[j] = a0;
-      sm.s1[j] = a1;
-      sm.s2[j] = a2;
-      sm.sc[j] = a3;
-      sm.sg[j] = g;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) sm.acc[k][j] = 0.0f;
-      if constexpr (RF) {
-        float4 fa, fb;
-        row_quad_factors(a1.x, 1.0f, fa, fb);
-        sm.fa[j] = fa;
-        sm.fb[j] = fb;
-      }
-    }
-    __syncwarp();
-    // test every (Gaussian, half-block) pair of the warp's chunk; pair i =
-    // jl * NH + hb, so the NH tests of one Gaussian sit in NH consecutive lanes
+    // stage the chunk and list its (Gaussian, half-block) units, Gaussian-major
+    // with half-blocks ascending: a warp scan of the units per Gaussian gives
+    // each lane where to write its own
     int nu = 0;
-    const int rounds = (cnt * NH + 31) / 32;
-#pragma unroll 1
-    for (int r = 0; r < rounds; ++r) {
-      const int i = r * 32 + lane;
-      const int jl = i / NH, hb = i & (NH - 1);
+    for (int jl0 = 0; jl0 < cnt; jl0 += 32) {
+      const int jl = jl0 + lane;
       const int j = slot0 + jl;
-      bool hit = false;
+      unsigned hm = 0u;
       if (jl < cnt) {
-        const float bxf = (float)(((hb >> 1) % (TILE / 8)) * 8);
-        const float byf = (float)(((hb >> 1) / (TILE / 8)) * 8 + 4 * (hb & 1));
-        hit = rect_hit(sm.s0[j], sm.s1[j], sm.sc[j], bxf + 0.5f, bxf + 7.5f, byf + 0.5f, byf + 3.5f, a.k2);
+        const uint32_t g = emit_gid[vals[base + jl]];
+        float4 a0, a1, a2;
+        hm = stage_blk<EXPM, TILE, 4>(rec, g, zsv, x0, y0, a.k2, a0, a1, a2);
+        sm.s0[j] = a0;
+        sm.s1[j] = a1;
+        sm.s2[j] = a2;
+        sm.sg[j] = g;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sm.acc[k][j] = 0.0f;
+        if constexpr (RF) {
+          float4 fa, fb;
+          row_quad_factors(a1.x, 1.0f, fa, fb);
+          sm.fa[j] = fa;
+          sm.fb[j] = fb;
+        }
       }
-      const unsigned m = __ballot_sync(0xffffffffu, hit);
-      if (hit) units[nu + __popc(m & ((1u << lane) - 1u))] = (j << 4) | hb;
-      nu += __popc(m);
+      const int c = __popc(hm);
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int sh = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += sh;
+      }
+      int at = nu + incl - c;
+      while (hm) {
+        const int hb = __ffs(hm) - 1;
+        hm &= hm - 1u;
+        units[at++] = (j << 4) | hb;
+      }
+      nu += __shfl_sync(0xffffffffu, incl, 31);
     }
     __syncwarp();
     // units in rounds of 32; the units of one Gaussian are consecutive (the
