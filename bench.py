@@ -77,6 +77,21 @@ OPS_PER_EVAL_ROW = {"fwd": 6.25, "bwd": 10.5}
 EXP_MODES = {"poly": 0, "hw": 1, "row": 3}
 
 
+def fp32_probe_peak(ctx, stream, reps=5, iters=20000):
+    """FP32 lane instructions per second of the FMA probe: best of reps launches."""
+    import torch
+    ctx.fma_probe(2000)
+    best = 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, lanes = ctx.fma_probe(iters)
+        e1.record(stream)
+        e1.synchronize()
+        best = max(best, lanes / (e0.elapsed_time(e1) * 1e-3))
+    return best
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -372,15 +387,10 @@ def run_native(args, rank, world):
         flush.zero_()
         step(k)
     torch.cuda.synchronize()
-    # FP32-pipe peak at the clocks in force (burst, just before the timed region)
-    ctx.fma_probe(2000)
-    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    pe0.record(stream)
-    ctx.fma_probe(20000)
-    pe1.record(stream)
-    torch.cuda.synchronize()
-    n_thr = int(B.lib.gp_fma_probe_threads(ctx.h))
-    fp32_peak = n_thr * 20000 * 8 / (pe0.elapsed_time(pe1) * 1e-3)  # lane instructions / s
+    # FP32-pipe peak at the clocks in force (burst, just before the timed region):
+    # the best of five probe launches, so that one launch slowed by the host or a
+    # clock transition does not lower the denominator
+    fp32_peak = fp32_probe_peak(ctx, stream)
 
     clocks = ClockSampler(dev_index)
     ctx.timing(True)
@@ -487,7 +497,7 @@ def run_native(args, rank, world):
                 "roofline": {"bound": "alu", "kernel": f"k_raster_{dom}", "achieved": achieved, "peak": peak,
                              "unit": "Tinst/s (FP32+INT lane instructions)", "frac": achieved / peak,
                              "traffic": traffic, "traffic_note": traffic_note,
-                             "peak_kind": "measured FMA probe, burst, same run",
+                             "peak_kind": "measured FMA probe, best of 5 bursts, same run",
                              "nominal_peak_2032mhz": nominal, "ops_per_eval": ops_table[dom]},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
