@@ -562,7 +562,7 @@ __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? 12 
 }
 
 template <int TILE, int CH, int EXPM, bool DET>
-__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? (row_factored<EXPM>() ? 8 : 10) : 32)
+__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? (row_factored<EXPM>() ? 9 : 10) : 32)
     k_raster_bwd_blk(SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
                      const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges,
                      float* __restrict__ accum, float4* __restrict__ partial) {
