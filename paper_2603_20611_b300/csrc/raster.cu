@@ -2,30 +2,32 @@
 // K-fwd and K-bwd), sm_103a; plain (one CTA per tile) and persistent (a work
 // queue over every tile of a batch of renders) launches share the tile bodies.
 //
-// A CTA owns one (slice, tile) and its binned Gaussian list; its warps own the
-// 8x8 blocks of the tile (four for 16x16 tiles, one for 8x8).  Per round the CTA stages a chunk
-// of Gaussians in shared memory (16-byte loads of the 64-byte records, mu_2d
-// and a~ of this slice computed once per Gaussian).  Each warp then tests 32
-// staged Gaussians at a time against its block -- lane l tests Gaussian l with
-//     min over the block's pixel-centre rectangle of d^T Sigma_2d^-1 d  >  k^2
-// (k^2 = 2 ln(1/eps)), i.e. every pixel of the block lies outside the culling
-// ellipse -- and compacts the hits with a ballot.  The warp's four
-// 8-lane groups then take four hits at a time; lane r of a group evaluates row r
-// of the block (8 pixels), so the per-Gaussian terms (row offset, shared part
-// of the quadratic form) are paid once per 8 pixels and the backward's
-// per-Gaussian reductions are 8-lane trees.
+// A CTA owns one (slice, tile) and its binned Gaussian list.  Gaussians are
+// staged in shared memory in chunks (16-byte loads of the 64-byte records, mu_2d
+// and a~ of this slice computed once per Gaussian), and at staging each one's
+// culling ellipse d^T Sigma_2d^-1 d <= k^2 (k^2 = 2 ln(1/eps)) is turned into a
+// mask of the tile's cells it touches, from its x-extent over each band of
+// pixel rows.
 //
-// Forward: each lane keeps 8 partial sums per group; the four groups are added
-// in a fixed shuffle tree at the end, so results are bitwise reproducible.
-// Along a row the exponent is a quadratic in the pixel offset q from the block's
-// centre column, evaluated with two FMAs per pixel.
-// Backward: six pixel moments per (Gaussian, block) -- sum G E, sum G E dx,
-// sum G E dy, sum G E dx^2, sum G E dx dy, sum G E dy^2 with E the Gaussian's
-// exponential and G = dL/dI, formed from three row sums about the centre
-// column -- reduced over the group's 8 rows by a transposed butterfly, stored per warp,
-// summed over the 4 warps in a fixed order, then folded into the 10
-// accumulators of the Gaussian (atomics) or written as a per-pair partial
-// (deterministic mode).
+// Forward: the warps own the 8x8 blocks of the tile (four for 16x16 tiles, one
+// for 8x8).  Per chunk each warp compacts the staged Gaussians whose mask has
+// its block; its four 8-lane groups take four of them at a time, lane r of a
+// group evaluating row r of the block (8 pixels): along a row the exponent is a
+// quadratic in the pixel offset q from the block's centre column, two pixels
+// per packed fp32x2 instruction.  Each lane keeps 8 partial sums per group; the
+// four groups are added in a fixed shuffle tree at the end, so results are
+// bitwise reproducible.
+// Backward: after the tile's dL/dI is in shared memory every warp works on its
+// own chunks of the list without block barriers.  The unit of work is a
+// (Gaussian, 8x4 half-block) pair the mask marks; one lane evaluates a unit's
+// 32 pixels and forms its six moments sum G E {1, dx, dy, dx^2, dx dy, dy^2}
+// (E the Gaussian's exponential, G = dL/dI).  The unit list is Gaussian-major,
+// so a segmented scan over the lanes sums each Gaussian's units into its six
+// accumulators in a fixed order; the accumulators are then folded into the 10
+// per-Gaussian sums (atomics) or written as a per-pair partial (deterministic
+// mode).
+// GP_EXP_POLY_ROW factors the exponential along each row (two exp2 per 8
+// pixels, see row_powers) in both kernels.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
