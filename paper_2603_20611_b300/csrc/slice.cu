@@ -329,23 +329,45 @@ void launch_slice_emit_batch(const BatchItems& b, const SliceRec* rec, const uns
 }
 
 // ------------------------------------------------------------ K-range
-__global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long long* __restrict__ n_dev,
-                         uint32_t cap, uint32_t nkeys, uint2* __restrict__ ranges) {
-  unsigned long long nn = *n_dev;
-  uint32_t n = nn < cap ? (uint32_t)nn : cap;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    uint32_t k = keys[i];
-    if (k >= nkeys) continue;  // cannot happen for emitted keys; keeps the store in bounds
-    if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
-    if (i + 1 == n || keys[i + 1] != k) ranges[k].y = i + 1;
+// Each thread takes four consecutive sorted keys (one 16-byte load; the key
+// array is 16-byte aligned and a vector that would run past cap is read key by
+// key) and its neighbours' last and first keys by shuffle, so every key is
+// loaded once.
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ keys,
+                                                const unsigned long long* __restrict__ n_dev, uint32_t cap,
+                                                uint32_t nkeys, uint2* __restrict__ ranges) {
+  const unsigned long long nn = *n_dev;
+  const uint32_t n = nn < cap ? (uint32_t)nn : cap;
+  const uint32_t i0 = 4u * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int lane = threadIdx.x & 31;
+  uint32_t k[4];
+  if (i0 + 4u <= cap) {
+    const uint4 v = *reinterpret_cast<const uint4*>(keys + i0);
+    k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) k[j] = i0 + (uint32_t)j < cap ? keys[i0 + j] : 0xffffffffu;
+  }
+  uint32_t prev = __shfl_up_sync(0xffffffffu, k[3], 1);
+  uint32_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
+  if (lane == 0) prev = (i0 > 0u && i0 - 1u < n) ? keys[i0 - 1u] : 0xffffffffu;
+  if (lane == 31) next = i0 + 4u < n ? keys[i0 + 4u] : 0xffffffffu;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t i = i0 + (uint32_t)j;
+    const uint32_t kj = k[j];
+    if (i >= n || kj >= nkeys) continue;  // kj >= nkeys cannot happen for emitted keys; keeps the store in bounds
+    const uint32_t before = j == 0 ? prev : k[j - 1], after = j == 3 ? next : k[j + 1];
+    if (i == 0u || before != kj) ranges[kj].x = i;
+    if (i + 1u == n || after != kj) ranges[kj].y = i + 1u;
   }
 }
 
 void launch_ranges(const uint32_t* keys, const unsigned long long* n_dev, uint32_t cap, uint32_t nkeys,
                    uint2* ranges, cudaStream_t st) {
   if (cap == 0) return;
-  int blocks = (int)std::min<int64_t>(((int64_t)cap + 255) / 256, 148 * 16);
-  k_ranges<<<blocks, 256, 0, st>>>(keys, n_dev, cap, nkeys, ranges);
+  const int64_t threads = ((int64_t)cap + 3) / 4;
+  k_ranges<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(keys, n_dev, cap, nkeys, ranges);
   note_launch();
 }
 

@@ -157,6 +157,10 @@ __device__ __forceinline__ uint32_t load_count(const unsigned long long* n_dev, 
   return n < cap ? (uint32_t)n : cap;
 }
 
+// Keys are read as 16-byte vectors, all four loads of a thread issued before
+// its shared-memory atomics (the tile's first key is a multiple of 4096, so
+// with a 16-byte aligned key array every vector is aligned; a vector that
+// would run past cap is read key by key).
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __restrict__ keys,
                                                             const unsigned long long* __restrict__ n_dev,
                                                             uint32_t cap, int shift,
@@ -167,10 +171,27 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __res
   uint32_t n = load_count(n_dev, cap);
   uint32_t base = blockIdx.x * RS_TILE;
   if (base < n) {
-#pragma unroll 4
-    for (int r = 0; r < RS_ROUNDS; ++r) {
-      uint32_t i = base + r * RS_THREADS + threadIdx.x;
-      if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 0xffu], 1u);
+    constexpr int NV = RS_ROUNDS / 4;  // 16-byte vectors per thread
+    uint4 v[NV];
+#pragma unroll
+    for (int r = 0; r < NV; ++r) {
+      const uint32_t i = base + 4u * (uint32_t)(r * RS_THREADS + threadIdx.x);
+      if (i + 4u <= cap) {
+        v[r] = *reinterpret_cast<const uint4*>(keys + i);
+      } else {
+        v[r].x = i < cap ? keys[i] : 0u;
+        v[r].y = i + 1u < cap ? keys[i + 1u] : 0u;
+        v[r].z = i + 2u < cap ? keys[i + 2u] : 0u;
+        v[r].w = i + 3u < cap ? keys[i + 3u] : 0u;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NV; ++r) {
+      const uint32_t i = base + 4u * (uint32_t)(r * RS_THREADS + threadIdx.x);
+      const uint32_t k4[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (i + (uint32_t)q < n) atomicAdd(&cnt[(k4[q] >> shift) & 0xffu], 1u);
     }
   }
   __syncthreads();
@@ -187,7 +208,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __res
 constexpr int RS_PER_WARP = RS_TILE / RS_WARPS;     // 512 keys
 constexpr int RS_ROUNDS_W = RS_PER_WARP / 32;       // 16 rounds
 
-__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
+__global__ void __launch_bounds__(RS_THREADS, 4) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const unsigned long long* __restrict__ n_dev, uint32_t cap, int shift,
     const uint32_t* __restrict__ hist, int nb) {
@@ -284,6 +305,7 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                              cudaStream_t st, bool* result_in_alt) {
   *result_in_alt = false;
   if (cap == 0 || bits <= 0) return cudaSuccess;
+  if ((((uintptr_t)keys) | ((uintptr_t)keys_alt)) & 15u) return cudaErrorMisalignedAddress;
   int nb = (int)((cap + RS_TILE - 1) / RS_TILE);
   uint32_t* hist = (uint32_t*)temp;
   int64_t nh = (int64_t)RS_BINS * nb;
