@@ -234,7 +234,15 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_scatter(
     key[r] = valid ? kin[i] : 0u;
     val[r] = valid ? (vin ? vin[i] : i) : 0u;  // no input values: the identity
     const uint32_t d = valid ? ((key[r] >> shift) & 0xffu) : (RS_BINS + lane);
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    // lanes holding the same digit: one ballot per digit bit (and one for
+    // validity; an invalid lane's low bits are its lane number, so it is alone)
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+      const bool bit = (d >> b) & 1u;
+      const uint32_t m = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? m : ~m;
+    }
     uint32_t c = 0u;
     if (valid) c = wcnt[warp][d];
     rank[r] = valid ? c + __popc(peers & lt_mask) : 0xffffffffu;
