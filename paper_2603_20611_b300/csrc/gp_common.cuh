@@ -104,15 +104,6 @@ struct __align__(16) SliceRec {
   float4 r0, r1, r2, r3;
 };
 
-// Per-Gaussian record of the voxelizer (world frame), 64 bytes:
-//   r0 = (mu_x, mu_y, mu_z, alpha)
-//   r1 = (K00, K01, K02, K11)             K = Sigma^-1
-//   r2 = (K12, K22, hx, hy)               h = k sqrt(diag Sigma): bounding box
-//   r3 = (hz, valid, 0, 0)
-struct __align__(16) VoxRec {
-  float4 r0, r1, r2, r3;
-};
-
 // ------------------------------------------------------------ rotations
 // Rotation matrix of q/|q|, q = (w, x, y, z).
 __device__ __forceinline__ void quat_rot(float4 q, float R[3][3], float qn[4], float& qnorm) {

@@ -84,9 +84,11 @@ __device__ __forceinline__ unsigned ellipse_cells(float4 r2, float4 r3, float mx
 //   s1 = (c0, c1, c2, C00)     e = c0 dx^2 + c1 dx dy + c2 dy^2 = -log2(e)/2 d^T C d
 //   s2 = (delta, opacity_r, C01, 0)    (backward)
 // and the mask of the cells (bands of BH rows) its culling ellipse touches.
+// On a voxelizer plane (vox) the culling ellipse is the plane's section of the
+// 3D one, d^T C d <= k2 - delta^2 / Sigma_zz (its extents scaled to match).
 template <int EXPM, int TILE, int BH>
 __device__ __forceinline__ unsigned stage_blk(const SliceRec* __restrict__ rec, uint32_t g, float zsv, float x0,
-                                              float y0, float k2, float4& s0, float4& s1, float4& s2) {
+                                              float y0, float k2, bool vox, float4& s0, float4& s1, float4& s2) {
   const float4* rp = reinterpret_cast<const float4*>(rec + g);
   const float4 r0 = __ldg(rp), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3);
   const float d = r0.z - zsv;
@@ -97,6 +99,13 @@ __device__ __forceinline__ unsigned stage_blk(const SliceRec* __restrict__ rec, 
   s0 = make_float4(mxr, myr, r1.z * w, C11);
   s1 = make_float4(-0.5f * kLog2e * C00, -kLog2e * C01, -0.5f * kLog2e * C11, C00);
   s2 = make_float4(d, w, C01, 0.0f);
+  if (vox) {
+    const float k2e = k2 - d * d * r0.w;
+    if (!(k2e > 0.0f)) return 0u;
+    const float f = sqrtf(k2e / k2);
+    return ellipse_cells<TILE, BH>(make_float4(r2.x, r2.y, r2.z, r2.w * f), make_float4(r3.x * f, r3.y, r3.z, r3.w),
+                                   mxr, myr, k2e);
+  }
   return ellipse_cells<TILE, BH>(r2, r3, mxr, myr, k2);
 }
 
@@ -192,8 +201,8 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
     const int cnt = (int)min((uint32_t)CH, rg.y - base);
     for (int j = threadIdx.x; j < cnt; j += NT) {
       float4 a0, a1, a2;
-      sm.bmask[j] = (unsigned char)stage_blk<EXPM, TILE, 8>(rec, emit_gid[vals[base + j]], zsv, x0, y0, a.k2, a0,
-                                                            a1, a2);
+      sm.bmask[j] = (unsigned char)stage_blk<EXPM, TILE, 8>(rec, emit_gid[vals[base + j]], zsv, x0, y0, a.k2, a.vox != 0,
+                                                            a0, a1, a2);
       sm.s0[j] = a0;
       sm.s1[j] = a1;
       if constexpr (RF) {
@@ -364,7 +373,7 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
       if (jl < cnt) {
         const uint32_t g = emit_gid[vals[base + jl]];
         float4 a0, a1, a2;
-        hm = stage_blk<EXPM, TILE, 4>(rec, g, zsv, x0, y0, a.k2, a0, a1, a2);
+        hm = stage_blk<EXPM, TILE, 4>(rec, g, zsv, x0, y0, a.k2, a.vox != 0, a0, a1, a2);
         sm.s0[j] = a0;
         sm.s1[j] = a1;
         sm.s2[j] = a2;

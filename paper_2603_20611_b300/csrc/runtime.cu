@@ -1,7 +1,8 @@
 // runtime.cu -- C ABI of the slice projection library: context, workspace pool,
 // argument checking and the host sequencing of the render / backward /
 // voxelize pipelines.  Every arithmetic step runs in the kernels of slice.cu,
-// voxel.cu and sort.cu.
+// raster.cu and sort.cu (the voxelizer is the slice path over the grid's
+// z-planes with sigma_z = 0 and amplitude alpha).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -16,7 +17,6 @@
 
 #include "gp_internal.h"
 #include "slice.cuh"
-#include "voxel.cuh"
 
 namespace gp {
 
@@ -183,12 +183,14 @@ static gp_status scan_counts(Ctx* c, int n, cudaStream_t st, uint32_t* P) {
 // one count readback, K-emit, radix sort, K-range.  On return the context's
 // buffers hold the records, the sorted emission indices and the tile ranges,
 // and *a describes the launch.
+// vox: the planes of the voxelizer (Eq. 12): sigma_z = 0 and amplitude alpha.
 static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, int H, int W, float sigma_z,
                             const View& view, cudaStream_t st, SliceArgs* a, uint32_t* pairs_out,
-                            const uint32_t** sorted_vals) {
+                            const uint32_t** sorted_vals, bool vox = false) {
   if (S < 0 || H <= 0 || W <= 0) return set_err(c, GP_ERR_ARG, "need S >= 0, H > 0, W > 0");
   if (S > 0 && !z) return set_err(c, GP_ERR_ARG, "z is NULL");
-  if (!(sigma_z > 0.0f) || !isfinite(sigma_z)) return set_err(c, GP_ERR_ARG, "sigma_z must be in (0, inf)");
+  if (vox) sigma_z = 0.0f;
+  else if (!(sigma_z > 0.0f) || !isfinite(sigma_z)) return set_err(c, GP_ERR_ARG, "sigma_z must be in (0, inf)");
   if ((int64_t)S * H * W > (int64_t)INT32_MAX) return set_err(c, GP_ERR_ARG, "S*H*W exceeds 2^31");
   for (int s = 0; s < S; ++s)
     if (!isfinite(z[s])) return set_err(c, GP_ERR_ARG, "z contains a non-finite value");
@@ -218,6 +220,7 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
   A = SliceArgs{};
   A.mu = set->mu; A.scale = set->scale; A.quat = set->quat; A.alpha = set->alpha;
   A.n = n; A.mod = set->scale_mod; A.sigma2 = sigma_z * sigma_z;
+  A.vox = vox ? 1 : 0;
   memcpy(A.Rc, view.R, sizeof(A.Rc));
   memcpy(A.tc, view.t, sizeof(A.tc));
   A.k2 = 2.0f * logf(1.0f / c->cfg.eps);
@@ -272,48 +275,6 @@ static bool bins_match(const Ctx* c, const gp_set* set, const float* z, int S, i
   for (int s = 0; s < S; ++s)
     if (k.z[s] != z[s]) return false;
   return true;
-}
-
-// Bins the voxelizer's (Gaussian, 8^3 tile) pairs: K-vpre, scan, count
-// readback, K-vemit, radix sort, K-range.
-static gp_status bin_voxels(Ctx* c, const gp_set* set, int X, int Y, int Z, cudaStream_t st, VoxArgs* a,
-                            uint32_t* pairs_out, const uint32_t** sorted_vals) {
-  if (X <= 0 || Y <= 0 || Z <= 0) return set_err(c, GP_ERR_ARG, "need X, Y, Z > 0");
-  if ((int64_t)X * Y * Z > (int64_t)INT32_MAX * 4) return set_err(c, GP_ERR_ARG, "volume too large");
-  PhaseTimer timer(c, GP_PHASE_BIN, st);
-  const int TX = ceil_div(X, VOX_TILE), TY = ceil_div(Y, VOX_TILE), TZ = ceil_div(Z, VOX_TILE);
-  const int64_t nkeys = (int64_t)TX * TY * TZ;
-  BinBufs& b = c->b;
-  const int n = (int)set->n;
-  VoxArgs& A = *a;
-  A.mu = set->mu; A.scale = set->scale; A.quat = set->quat; A.alpha = set->alpha;
-  A.n = n; A.mod = set->scale_mod; A.k2 = 2.0f * logf(1.0f / c->cfg.eps);
-  A.X = X; A.Y = Y; A.Z = Z; A.TX = TX; A.TY = TY; A.TZ = TZ;
-  GP_TRY(ws_reserve(c, b.rec, (size_t)std::max(n, 1) * sizeof(VoxRec)));
-  GP_TRY(ws_reserve(c, b.counts, (size_t)std::max(n, 1) * 8));
-  GP_TRY(ws_reserve(c, b.offsets, (size_t)std::max(n, 1) * 8));
-  GP_TRY(ws_reserve(c, b.total, 64));
-  GP_TRY(ws_reserve(c, b.scan_tmp, (size_t)scan_temp_bytes(std::max(n, 1))));
-  GP_TRY(ws_reserve(c, b.ranges, (size_t)nkeys * 8));
-  GP_CUDA(c, cudaMemsetAsync(b.ranges.ptr, 0, (size_t)nkeys * 8, st), "memset ranges");
-  uint32_t P = 0;
-  if (n > 0) {
-    launch_vox_pre(A, (VoxRec*)b.rec.ptr, (unsigned long long*)b.counts.ptr, st);
-    GP_TRY(scan_counts(c, n, st, &P));
-  }
-  *sorted_vals = nullptr;
-  if (P > 0) {
-    GP_TRY(reserve_pairs(c, P));
-    launch_vox_emit(A, (const VoxRec*)b.rec.ptr, (const unsigned long long*)b.offsets.ptr,
-                    (const unsigned long long*)b.counts.ptr, (uint32_t*)b.keys.ptr,
-                    (uint32_t*)b.vals.ptr, (uint32_t*)b.emit_gid.ptr, st);
-    GP_TRY(sort_and_range(c, P, nkeys, st, sorted_vals));
-  }
-  *pairs_out = P;
-  c->last_pairs = P;
-  c->last_issued = (int64_t)P * VOX_TILE * VOX_TILE * VOX_TILE;
-  c->bin_key.valid = false;  // the slice binning's buffers now hold voxel pairs
-  return cuda_err(c, cudaGetLastError(), "voxel binning kernels");
 }
 
 static gp_status check_grads(Ctx* c, int64_t n, float* d_mu, float* d_scale, float* d_quat, float* d_alpha) {
@@ -438,7 +399,7 @@ gp_status gp_last_counts(gp_ctx* ctx, int64_t* pairs, int64_t* issued) {
 }
 
 static gp_status render_impl(gp_ctx* ctx, const gp_set* set, const View& view, const float* z, int S, int H,
-                             int W, float sigma_z, float* out, void* stream) {
+                             int W, float sigma_z, float* out, void* stream, bool vox = false) {
   Ctx* c = &ctx->impl;
   GP_TRY(check_set(c, set));
   if (!out && S > 0) return set_err(c, GP_ERR_ARG, "out is NULL");
@@ -447,13 +408,13 @@ static gp_status render_impl(gp_ctx* ctx, const gp_set* set, const View& view, c
   SliceArgs a;
   uint32_t P = 0;
   const uint32_t* vals = nullptr;
-  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals));
+  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals, vox));
   if (S == 0) return GP_OK;
   if (P == 0) {
     GP_CUDA(c, cudaMemsetAsync(out, 0, (size_t)S * H * W * 4, st), "clear out");
     return GP_OK;
   }
-  PhaseTimer timer(c, GP_PHASE_FWD, st);
+  PhaseTimer timer(c, vox ? GP_PHASE_VOX_FWD : GP_PHASE_FWD, st);
   GP_CUDA(c, launch_raster_fwd(a, fwd_px(c), c->cfg.exp_mode, (const SliceRec*)c->b.rec.ptr, vals,
                                (const uint32_t*)c->b.emit_gid.ptr, (const uint2*)c->b.ranges.ptr, out, st),
           "raster forward");
@@ -462,7 +423,7 @@ static gp_status render_impl(gp_ctx* ctx, const gp_set* set, const View& view, c
 
 static gp_status backward_impl(gp_ctx* ctx, const gp_set* set, const View& view, const float* z, int S, int H,
                                int W, float sigma_z, const float* dL_dI, float* d_mu, float* d_scale,
-                               float* d_quat, float* d_alpha, void* stream) {
+                               float* d_quat, float* d_alpha, void* stream, bool vox = false) {
   Ctx* c = &ctx->impl;
   GP_TRY(check_set(c, set));
   const int n = (int)set->n;
@@ -473,12 +434,13 @@ static gp_status backward_impl(gp_ctx* ctx, const gp_set* set, const View& view,
   SliceArgs a;
   uint32_t P = 0;
   const uint32_t* vals = nullptr;
+  if (vox) sigma_z = 0.0f;  // the key of voxelizer bins (slices never have sigma_z = 0)
   if (c->cfg.reuse_bins && S > 0 && z && bins_match(c, set, z, S, H, W, sigma_z, view)) {
     memcpy(&a, c->bin_args, sizeof(SliceArgs));
     P = c->bin_pairs;
     vals = c->bin_vals;
   } else {
-    GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals));
+    GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals, vox));
   }
   if (n == 0) return GP_OK;
   BinBufs& b = c->b;
@@ -490,14 +452,14 @@ static gp_status backward_impl(gp_ctx* ctx, const gp_set* set, const View& view,
     GP_CUDA(c, cudaMemsetAsync(b.accum.ptr, 0, (size_t)n * 10 * 4, st), "clear accumulators");
   }
   if (P > 0) {
-    PhaseTimer timer(c, GP_PHASE_BWD, st);
+    PhaseTimer timer(c, vox ? GP_PHASE_VOX_BWD : GP_PHASE_BWD, st);
     GP_CUDA(c, launch_raster_bwd(a, bwd_px(c), c->cfg.exp_mode, det, (const SliceRec*)b.rec.ptr, vals,
                                  (const uint32_t*)b.emit_gid.ptr, (const uint2*)b.ranges.ptr, dL_dI,
                                  (float*)b.accum.ptr, (float4*)b.partial.ptr, st),
             "raster backward");
   }
   {
-    PhaseTimer timer(c, GP_PHASE_BWD_PRE, st);
+    PhaseTimer timer(c, vox ? GP_PHASE_VOX_BWD : GP_PHASE_BWD_PRE, st);
     if (det)
       launch_det_reduce(n, (const unsigned long long*)b.offsets.ptr, (const unsigned long long*)b.counts.ptr,
                         (const float4*)b.partial.ptr, (float*)b.accum.ptr, st);
@@ -533,7 +495,7 @@ gp_status gp_mse_grad(gp_ctx* ctx, const float* I, const float* T, const int* t_
 }
 
 static gp_status count_impl(gp_ctx* ctx, const gp_set* set, const View& view, const float* z, int S, int H,
-                            int W, float sigma_z, int64_t* evals) {
+                            int W, float sigma_z, int64_t* evals, bool vox = false) {
   Ctx* c = &ctx->impl;
   GP_TRY(check_set(c, set));
   GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
@@ -541,7 +503,7 @@ static gp_status count_impl(gp_ctx* ctx, const gp_set* set, const View& view, co
   SliceArgs a;
   uint32_t P = 0;
   const uint32_t* vals = nullptr;
-  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals));
+  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals, vox));
   unsigned long long* d = (unsigned long long*)c->b.total.ptr + 1;
   GP_CUDA(c, cudaMemsetAsync(d, 0, 8, st), "count");
   if (set->n > 0 && S > 0) launch_count_evals(a, (const SliceRec*)c->b.rec.ptr, d, st);
@@ -623,77 +585,49 @@ gp_status gp_exp2_eval(gp_ctx* ctx, const float* x, float* y, int64_t n, int mod
   return cuda_err(c, cudaGetLastError(), "exp2 eval");
 }
 
+// The voxelizer (Eq. 12) runs as a stack of Z planes through the slice path:
+// on the plane z the Gaussian is alpha exp(-delta^2 / 2 Sigma_zz) exp(-d^T
+// Sigma_2d^-1 d / 2) with Sigma_2d the conditional covariance, i.e. the slice
+// operator with sigma_z = 0 and amplitude alpha; voxel (ix, iy, iz) is pixel
+// (ix, iy) of plane iz + 1/2, and the [Z, Y, X] volume is the [S, H, W] stack.
+static gp_status vox_planes(Ctx* c, int X, int Y, int Z, std::vector<float>& z) {
+  if (X <= 0 || Y <= 0 || Z <= 0) return set_err(c, GP_ERR_ARG, "need X, Y, Z > 0");
+  z.resize(Z);
+  for (int k = 0; k < Z; ++k) z[k] = (float)k + 0.5f;
+  return GP_OK;
+}
+
 gp_status gp_voxelize(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, float* vol, void* stream) {
   if (!ctx) return GP_ERR_ARG;
   Ctx* c = &ctx->impl;
-  GP_TRY(check_set(c, set));
   if (!vol) return set_err(c, GP_ERR_ARG, "vol is NULL");
-  cudaStream_t st = (cudaStream_t)stream;
-  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
-  VoxArgs a;
-  uint32_t P = 0;
-  const uint32_t* vals = nullptr;
-  GP_TRY(bin_voxels(c, set, X, Y, Z, st, &a, &P, &vals));
-  if (P == 0) {
-    GP_CUDA(c, cudaMemsetAsync(vol, 0, (size_t)X * Y * Z * 4, st), "clear vol");
-    return GP_OK;
-  }
-  PhaseTimer timer(c, GP_PHASE_VOX_FWD, st);
-  GP_CUDA(c, launch_vox_fwd(a, (const VoxRec*)c->b.rec.ptr, vals, (const uint32_t*)c->b.emit_gid.ptr,
-                            (const uint2*)c->b.ranges.ptr, vol, st),
-          "voxelize forward");
-  return GP_OK;
+  std::vector<float> z;
+  GP_TRY(vox_planes(c, X, Y, Z, z));
+  View v;
+  axis_view(2, &v);
+  return render_impl(ctx, set, v, z.data(), Z, Y, X, 0.0f, vol, stream, true);
 }
 
 gp_status gp_count_vox_evals(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, int64_t* evals) {
   if (!ctx || !evals) return GP_ERR_ARG;
   Ctx* c = &ctx->impl;
-  GP_TRY(check_set(c, set));
-  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
-  cudaStream_t st = 0;
-  VoxArgs a;
-  uint32_t P = 0;
-  const uint32_t* vals = nullptr;
-  GP_TRY(bin_voxels(c, set, X, Y, Z, st, &a, &P, &vals));
-  unsigned long long* d = (unsigned long long*)c->b.total.ptr + 1;
-  GP_CUDA(c, cudaMemsetAsync(d, 0, 8, st), "count");
-  launch_vox_count(a, (const VoxRec*)c->b.rec.ptr, d, st);
-  GP_CUDA(c, cudaMemcpyAsync(c->h_total, d, 8, cudaMemcpyDeviceToHost, st), "count readback");
-  GP_CUDA(c, cudaStreamSynchronize(st), "count readback");
-  *evals = (int64_t)*c->h_total;
-  return GP_OK;
+  std::vector<float> z;
+  GP_TRY(vox_planes(c, X, Y, Z, z));
+  View v;
+  axis_view(2, &v);
+  return count_impl(ctx, set, v, z.data(), Z, Y, X, 0.0f, evals, true);
 }
 
 gp_status gp_voxelize_backward(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, const float* dL_dV,
                                float* d_mu, float* d_scale, float* d_quat, float* d_alpha, void* stream) {
   if (!ctx) return GP_ERR_ARG;
   Ctx* c = &ctx->impl;
-  GP_TRY(check_set(c, set));
-  const int n = (int)set->n;
-  GP_TRY(check_grads(c, n, d_mu, d_scale, d_quat, d_alpha));
   if (!dL_dV) return set_err(c, GP_ERR_ARG, "dL_dV is NULL");
-  cudaStream_t st = (cudaStream_t)stream;
-  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
-  VoxArgs a;
-  uint32_t P = 0;
-  const uint32_t* vals = nullptr;
-  GP_TRY(bin_voxels(c, set, X, Y, Z, st, &a, &P, &vals));
-  if (n == 0) return GP_OK;
-  BinBufs& b = c->b;
-  GP_TRY(ws_reserve(c, b.accum, (size_t)n * 10 * 4));
-  const bool det = c->cfg.deterministic != 0;
-  if (det) GP_TRY(ws_reserve(c, b.partial, (size_t)std::max<uint32_t>(P, 1) * 48));
-  else GP_CUDA(c, cudaMemsetAsync(b.accum.ptr, 0, (size_t)n * 10 * 4, st), "clear accumulators");
-  PhaseTimer timer(c, GP_PHASE_VOX_BWD, st);
-  if (P > 0)
-    GP_CUDA(c, launch_vox_bwd(a, det, (const VoxRec*)b.rec.ptr, vals, (const uint32_t*)b.emit_gid.ptr,
-                              (const uint2*)b.ranges.ptr, dL_dV, (float*)b.accum.ptr, (float4*)b.partial.ptr, st),
-            "voxelize backward");
-  if (det)
-    launch_vox_det_reduce(n, (const unsigned long long*)b.offsets.ptr, (const unsigned long long*)b.counts.ptr,
-                          (const float4*)b.partial.ptr, (float*)b.accum.ptr, st);
-  launch_vox_bwd_pre(a, (const float*)b.accum.ptr, d_mu, d_scale, d_quat, d_alpha, st);
-  return cuda_err(c, cudaGetLastError(), "voxelize backward kernels");
+  std::vector<float> z;
+  GP_TRY(vox_planes(c, X, Y, Z, z));
+  View v;
+  axis_view(2, &v);
+  return backward_impl(ctx, set, v, z.data(), Z, Y, X, 0.0f, dL_dV, d_mu, d_scale, d_quat, d_alpha, stream, true);
 }
 
 gp_status gp_timing_enable(gp_ctx* ctx, int enable) {

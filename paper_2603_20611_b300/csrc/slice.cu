@@ -80,17 +80,31 @@ __device__ __forceinline__ void plane_range(const SliceArgs& a, const SliceRec& 
   hi = upper_bound_f(a.zs, a.S, __fadd_rn(mz, zr));
 }
 
-// mu_2d on sorted plane j and the clamped range of tile rows the ellipse spans.
+// mu_2d on sorted plane j, the culling ellipse on it and the clamped range of
+// tile rows the ellipse spans.  On a slice the ellipse is d^T C d <= k2 on every
+// plane the pair reaches; on a voxelizer plane the cut is the 3D one,
+// d^T C d + delta^2 / Sigma_zz <= k2, so the plane's ellipse is d^T C d <= k2 -
+// delta^2 / Sigma_zz, its half-extents rx, ry scaled by sqrt(k2e / k2).
 struct PlaneBox {
   float mx, my;
+  float k2e, rxe, rye;  // the plane's squared radius and half-extents
   int ty0, ty1;
 };
 
 __device__ __forceinline__ PlaneBox plane_box(const SliceArgs& a, const SliceRec& r, int j) {
   PlaneBox b;
   const float inv_tile = 1.0f / (float)a.tile;
-  const float ry = r.r3.x;
   const float d = __fsub_rn(r.r0.z, a.zs[j]);
+  b.k2e = a.k2;
+  b.rxe = r.r2.w;
+  b.rye = r.r3.x;
+  if (a.vox) {
+    b.k2e = fmaxf(__fsub_rn(a.k2, __fmul_rn(__fmul_rn(d, d), r.r0.w)), 0.0f);
+    const float f = __fsqrt_rn(__fdiv_rn(b.k2e, a.k2));
+    b.rxe = __fmul_rn(b.rxe, f);
+    b.rye = __fmul_rn(b.rye, f);
+  }
+  const float ry = b.rye;
   b.mx = __fsub_rn(r.r0.x, __fmul_rn(r.r1.x, d));
   b.my = __fsub_rn(r.r0.y, __fmul_rn(r.r1.y, d));
   b.ty0 = max(0, clamp_tile(__fmul_rn(__fsub_rn(__fsub_rn(b.my, ry), 0.5f), inv_tile), a.TY));
@@ -107,7 +121,7 @@ __device__ __forceinline__ PlaneBox plane_box(const SliceArgs& a, const SliceRec
 // [xmin, xmax].  Explicit roundings keep the count and the emission identical.
 __device__ __forceinline__ bool row_tiles(const SliceArgs& a, const SliceRec& r, const PlaneBox& b, int ty,
                                           int* lo, int* hi) {
-  const float c00 = r.r2.x, c01 = r.r2.y, c11 = r.r2.z, rx = r.r2.w, ry = r.r3.x;
+  const float c00 = r.r2.x, c01 = r.r2.y, c11 = r.r2.z, rx = b.rxe, ry = b.rye, k2 = b.k2e;
   const float inv00 = r.r3.z, inv11 = r.r3.w;
   const float y0 = (float)(ty * a.tile) + 0.5f;
   const float y1 = (float)(min((ty + 1) * a.tile, a.H)) - 0.5f;
@@ -119,8 +133,8 @@ __device__ __forceinline__ bool row_tiles(const SliceArgs& a, const SliceRec& r,
   const float dyt = -__fmul_rn(__fmul_rn(c01, inv11), rx);
   const float dM = fminf(fmaxf(dyt, dya), dyb);
   const float dm = fminf(fmaxf(-dyt, dya), dyb);
-  const float wM = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(a.k2, __fmul_rn(D, __fmul_rn(dM, dM))), inv00), 0.0f));
-  const float wm = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(a.k2, __fmul_rn(D, __fmul_rn(dm, dm))), inv00), 0.0f));
+  const float wM = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(k2, __fmul_rn(D, __fmul_rn(dM, dM))), inv00), 0.0f));
+  const float wm = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(k2, __fmul_rn(D, __fmul_rn(dm, dm))), inv00), 0.0f));
   const float xmax = __fadd_rn(__fsub_rn(b.mx, __fmul_rn(s, dM)), wM);
   const float xmin = __fsub_rn(__fsub_rn(b.mx, __fmul_rn(s, dm)), wm);
   const float inv_tile = 1.0f / (float)a.tile;
@@ -190,7 +204,9 @@ __device__ __forceinline__ void slice_pre_one(const SliceArgs& a, int i, int ig,
   float idet = 1.0f / det;
   SliceRec r;
   r.r0 = make_float4(mux, muy, muz, iv);
-  r.r1 = make_float4(ax, ay, a.alpha[i] / sqrtf(det), sqrtf(a.k2 * v));
+  // amplitude: alpha / sqrt(det Sigma_2d) on a slice (Eq. 9); alpha on a voxelizer plane, where the
+  // Gaussian on the plane z is alpha exp(-delta^2 / 2 Sigma_zz) exp(-d^T Sigma_2d^-1 d / 2) (Eq. 12)
+  r.r1 = make_float4(ax, ay, a.vox ? a.alpha[i] : a.alpha[i] / sqrtf(det), sqrtf(a.k2 * v));
   r.r2 = make_float4(syy * idet, -sxy * idet, sxx * idet, sqrtf(a.k2 * sxx));
   r.r3 = make_float4(sqrtf(a.k2 * syy), valid ? 1.0f : 0.0f, det / syy, det / sxx);
   rec[ig] = r;
@@ -739,13 +755,14 @@ __device__ __forceinline__ void slice_bwd_pre_one(const SliceArgs& a, int i, int
   float gmu[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, galpha = 0.f;
   if (valid) {
     float idet = 1.0f / det, sq = sqrtf(det);
-    float A = a.alpha[i] / sq;
+    // amplitude A = alpha / sqrt(det) (slices) or alpha (voxelizer planes, no det term)
+    float A = a.vox ? a.alpha[i] : a.alpha[i] / sq;
     float C00 = syy * idet, C01 = -sxy * idet, C11 = sxx * idet;
     const float S1x = acc[0], S1y = acc[1], S2x = acc[2], S2y = acc[3];
     const float T0 = acc[4], T1 = acc[5], T2 = acc[6];
     const float G00 = acc[7], G01 = 0.5f * acc[8], G11 = acc[9];
-    galpha = T0 / sq;
-    float gdet = -0.5f * T0 * A * idet;
+    galpha = a.vox ? T0 : T0 / sq;
+    float gdet = a.vox ? 0.0f : -0.5f * T0 * A * idet;
     // dL/dSigma_2d = -C Gc C + gdet det C  (symmetric)
     float CG00 = C00 * G00 + C01 * G01, CG01 = C00 * G01 + C01 * G11;
     float CG10 = C01 * G00 + C11 * G01, CG11 = C01 * G01 + C11 * G11;
@@ -896,6 +913,23 @@ __global__ void __launch_bounds__(PRE_THREADS) k_count_evals(SliceArgs a, const 
       float mx = r.r0.x - r.r1.x * d, my = r.r0.y - r.r1.y * d;
       int ty = tile / a.TX, tx = tile - ty * a.TX;
       int xa = tx * a.tile, xb = min((tx + 1) * a.tile, a.W);
+      if (a.vox) {
+        // voxelizer plane: the section of the 3D ellipsoid, d^T C d <= k2 - delta^2 / Sigma_zz,
+        // in double precision (the count is compared with an FP64 lattice count)
+        const double dd = (double)r.r0.z - (double)a.zs[j];
+        const double k2e = (double)a.k2 - dd * dd * (double)r.r0.w;
+        const double mxd = (double)r.r0.x - (double)r.r1.x * dd, myd = (double)r.r0.y - (double)r.r1.y * dd;
+        for (int y = ty * a.tile; y < min((ty + 1) * a.tile, a.H); ++y) {
+          const double dy = (double)y + 0.5 - myd;
+          const double disc = (double)c01 * c01 * dy * dy - (double)c00 * ((double)c11 * dy * dy - k2e);
+          if (!(disc >= 0.0)) continue;
+          const double sq = sqrt(disc);
+          const double lo = mxd + (-(double)c01 * dy - sq) / c00, hi = mxd + (-(double)c01 * dy + sq) / c00;
+          int x0 = max(xa, (int)ceil(lo - 0.5)), x1 = min(xb - 1, (int)floor(hi - 0.5));
+          if (x1 >= x0) cnt += (unsigned long long)(x1 - x0 + 1);
+        }
+        return;
+      }
       for (int y = ty * a.tile; y < min((ty + 1) * a.tile, a.H); ++y) {
         float dy = (float)y + 0.5f - my;
         float disc = c01 * c01 * dy * dy - c00 * (c11 * dy * dy - a.k2);

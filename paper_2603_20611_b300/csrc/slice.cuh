@@ -19,6 +19,7 @@ struct SliceArgs {
   float tc[3];
   float sigma2;   // sigma_z^2
   float k2;       // 2 ln(1/eps): squared Mahalanobis culling radius
+  int vox;        // 1: voxelizer planes (Eq. 12): sigma_z = 0 and amplitude alpha, not alpha/sqrt(det Sigma_2d)
   const float* zs;      // [S] plane positions sorted ascending
   const int* zorder;    // [S] slice index of sorted position j
   const float* zorig;   // [S] plane position of slice index s
