@@ -72,3 +72,77 @@ def test_voxel_eval_count_matches_oracle():
     got = B.gp_count_vox_evals(c, dev_set(g), 40, 36, 28)
     ref = oracle.count_vox_evals(g.mu, g.scale, g.quat, g.alpha, 40, 36, 28)
     assert ref > 0 and abs(got - ref) <= 1e-4 * ref
+
+
+# ------------------------------------------------ the plane-stack voxelizer
+
+def test_voxelize_matches_the_voxelizer_limit_of_the_slice_operator(ctx):
+    """Pin P4 on the device: each z-plane of the volume is the slice of that
+    plane at sigma_z -> 0 times sqrt(det Sigma_cond) (the slice operator's
+    amplitude alpha / sqrt(det Sigma_2d) against the voxelizer's alpha), here
+    checked through the oracle's slice render at a tiny sigma_z for a single
+    Gaussian."""
+    g = synth.small(seed=45, n=1, extent=(24, 20, 12))
+    vol = np32(B.gp_voxelize(ctx, dev_set(g), 24, 20, 12))
+    z = synth.slice_positions(range(12))
+    sl = oracle.render(*orc(g), z, 20, 24, 1e-4)
+    # sqrt(det Sigma_2d) of the conditional covariance at sigma_z -> 0
+    w, x, y, zq = g.quat[0].astype(np.float64) / np.linalg.norm(g.quat[0].astype(np.float64))
+    R = np.array([[1 - 2 * (y * y + zq * zq), 2 * (x * y - w * zq), 2 * (x * zq + w * y)],
+                  [2 * (x * y + w * zq), 1 - 2 * (x * x + zq * zq), 2 * (y * zq - w * x)],
+                  [2 * (x * zq - w * y), 2 * (y * zq + w * x), 1 - 2 * (x * x + y * y)]])
+    S = R @ np.diag(g.scale[0].astype(np.float64) ** 2) @ R.T
+    cond = S[:2, :2] - np.outer(S[:2, 2], S[:2, 2]) / S[2, 2]
+    assert_forward_close(vol, sl * np.sqrt(np.linalg.det(cond)), "voxelize = slice limit")
+
+
+def test_voxelize_single_plane_and_thin_grids(ctx):
+    g = synth.small(seed=46, n=150, extent=(19, 23, 1))
+    for X, Y, Z in ((19, 23, 1), (1, 23, 5), (19, 1, 3)):
+        vol = B.gp_voxelize(ctx, dev_set(g), X, Y, Z)
+        assert_forward_close(np32(vol), oracle.voxelize(*orc(g), X, Y, Z), f"grid {X}x{Y}x{Z}")
+
+
+def test_voxelize_row_factored():
+    c = B.Context(0, exp_mode=B.GP_EXP_POLY_ROW)
+    g = synth.small(seed=47, n=400, extent=(37, 29, 21))
+    vol = B.gp_voxelize(c, dev_set(g), 37, 29, 21)
+    assert_forward_close(np32(vol), oracle.voxelize(*orc(g), 37, 29, 21), "voxelize row-factored")
+    G = synth.random_field(9, (21, 29, 37))
+    grads = B.gp_voxelize_backward(c, dev_set(g), 37, 29, 21, torch.from_numpy(G).cuda())
+    assert_grads_close(grads, oracle.voxelize_backward(*orc(g), 37, 29, 21, G), "voxelize backward row-factored")
+
+
+def test_voxelizer_and_slice_bins_are_never_shared():
+    """With bin reuse on, a voxelize after a slice render of the same planes,
+    and a slice backward after a voxelize, must each bin again (different
+    amplitude and culling): both match the oracle; and the voxelize backward
+    right after its forward reuses the bins bitwise (deterministic mode)."""
+    c = B.Context(0, reuse_bins=True, deterministic=True)
+    plain = B.Context(0, deterministic=True)
+    g = synth.small(seed=48, n=300, extent=(26, 22, 14))
+    gs = dev_set(g)
+    z = synth.slice_positions(range(14))
+    G = torch.from_numpy(synth.random_field(10, (14, 22, 26))).cuda()
+    B.gp_render_slices(c, gs, z, 22, 26, 1.5)
+    gv = B.gp_voxelize_backward(c, gs, 26, 22, 14, G)
+    assert_grads_close(gv, oracle.voxelize_backward(*orc(g), 26, 22, 14, G.cpu().numpy()), "vox after slices")
+    B.gp_voxelize(c, gs, 26, 22, 14)
+    gsl = B.gp_render_backward(c, gs, z, 22, 26, 1.5, G)
+    assert_grads_close(gsl, oracle.render_backward(*orc(g), z, 22, 26, 1.5, G.cpu().numpy()), "slices after vox")
+    B.gp_voxelize(c, gs, 26, 22, 14)
+    reused = [t.clone() for t in B.gp_voxelize_backward(c, gs, 26, 22, 14, G)]
+    fresh = B.gp_voxelize_backward(plain, gs, 26, 22, 14, G)
+    for a, b in zip(reused, fresh):
+        assert torch.equal(a, b)
+
+
+def test_voxelize_bad_arguments(ctx):
+    import ctypes
+    g = dev_set(synth.small(seed=49, n=10, extent=(8, 8, 8)))
+    s = g.c()
+    vol = torch.empty(8, 8, 8, device="cuda")
+    for X, Y, Z in ((0, 8, 8), (8, 8, -1), (8, -3, 8)):
+        st = B.lib.gp_voxelize(ctx.h, ctypes.byref(s), X, Y, Z, ctypes.c_void_p(vol.data_ptr()), None)
+        assert st == B.GP_ERR_ARG, (X, Y, Z, st)
+    torch.cuda.synchronize()
