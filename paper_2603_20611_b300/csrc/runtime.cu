@@ -221,6 +221,12 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
   A.mu = set->mu; A.scale = set->scale; A.quat = set->quat; A.alpha = set->alpha;
   A.n = n; A.mod = set->scale_mod; A.sigma2 = sigma_z * sigma_z;
   A.vox = vox ? 1 : 0;
+  // a warp per Gaussian in K-pre / K-emit when the sigma_z blur alone makes a
+  // Gaussian reach 32 or more of the call's planes (their mean spacing)
+  if (S >= 64) {
+    const float span = zs[S - 1] - zs[0];
+    A.warp_pairs = span > 0.0f && 2.0f * sqrtf(2.0f * logf(1.0f / c->cfg.eps)) * sigma_z >= 32.0f * span / (float)(S - 1);
+  }
   memcpy(A.Rc, view.R, sizeof(A.Rc));
   memcpy(A.tc, view.t, sizeof(A.tc));
   A.k2 = 2.0f * logf(1.0f / c->cfg.eps);

@@ -44,6 +44,12 @@ namespace gp {
 
 constexpr int PRE_THREADS = 256;
 
+// Calls whose Gaussians each reach tens of planes (the host sets warp_pairs)
+// count and emit with a warp per Gaussian, the lanes taking its planes; other
+// calls keep a thread per Gaussian.  Both enumerate the same pairs in the same
+// order.
+__host__ __device__ inline bool warp_per_gaussian(const SliceArgs& a) { return a.warp_pairs != 0; }
+
 // ------------------------------------------------------------ K-pre
 __device__ __forceinline__ int lower_bound_f(const float* __restrict__ v, int n, float x) {
   int lo = 0, hi = n;
@@ -164,25 +170,30 @@ __device__ __forceinline__ void for_each_pair(const SliceArgs& a, const SliceRec
   }
 }
 
-// Number of pairs of one Gaussian (same enumeration, whole runs at a time).
+// Number of pairs of one Gaussian on sorted plane j (same enumeration, whole
+// runs at a time).
+__device__ __forceinline__ unsigned plane_pairs(const SliceArgs& a, const SliceRec& r, int j) {
+  const PlaneBox b = plane_box(a, r, j);
+  unsigned c = 0;
+  for (int ty = b.ty0; ty <= b.ty1; ++ty) {
+    int lo, hi;
+    if (row_tiles(a, r, b, ty, &lo, &hi)) c += (unsigned)(hi - lo + 1);
+  }
+  return c;
+}
+
+// Number of pairs of one Gaussian.
 __device__ __forceinline__ unsigned long long count_pairs(const SliceArgs& a, const SliceRec& r) {
   if (r.r3.y == 0.0f) return 0;
   int plo, phi;
   plane_range(a, r, plo, phi);
   unsigned long long c = 0;
-  for (int j = plo; j < phi; ++j) {
-    const PlaneBox b = plane_box(a, r, j);
-    for (int ty = b.ty0; ty <= b.ty1; ++ty) {
-      int lo, hi;
-      if (row_tiles(a, r, b, ty, &lo, &hi)) c += (unsigned long long)(hi - lo + 1);
-    }
-  }
+  for (int j = plo; j < phi; ++j) c += plane_pairs(a, r, j);
   return c;
 }
 
-// Record and pair count of Gaussian i of item a, stored at batch-wide index ig.
-__device__ __forceinline__ void slice_pre_one(const SliceArgs& a, int i, int ig, SliceRec* __restrict__ rec,
-                                              unsigned long long* __restrict__ counts) {
+// Record of Gaussian i of item a.
+__device__ __forceinline__ SliceRec make_record(const SliceArgs& a, int i) {
   float4 q = reinterpret_cast<const float4*>(a.quat)[i];
   float R[3][3], qn[4], qnorm;
   quat_rot(q, R, qn, qnorm);
@@ -209,6 +220,13 @@ __device__ __forceinline__ void slice_pre_one(const SliceArgs& a, int i, int ig,
   r.r1 = make_float4(ax, ay, a.vox ? a.alpha[i] : a.alpha[i] / sqrtf(det), sqrtf(a.k2 * v));
   r.r2 = make_float4(syy * idet, -sxy * idet, sxx * idet, sqrtf(a.k2 * sxx));
   r.r3 = make_float4(sqrtf(a.k2 * syy), valid ? 1.0f : 0.0f, det / syy, det / sxx);
+  return r;
+}
+
+// Record and pair count of Gaussian i of item a, stored at batch-wide index ig.
+__device__ __forceinline__ void slice_pre_one(const SliceArgs& a, int i, int ig, SliceRec* __restrict__ rec,
+                                              unsigned long long* __restrict__ counts) {
+  const SliceRec r = make_record(a, i);
   rec[ig] = r;
   counts[ig] = count_pairs(a, r);
 }
@@ -217,6 +235,29 @@ __global__ void __launch_bounds__(PRE_THREADS) k_slice_pre(SliceArgs a, SliceRec
                                                            unsigned long long* __restrict__ counts) {
   const int i = blockIdx.x * PRE_THREADS + threadIdx.x;
   if (i < a.n) slice_pre_one(a, i, i, rec, counts);
+}
+
+// K-pre with a warp per Gaussian, for calls with many planes: the lanes count
+// the Gaussian's planes (a stride of 32), summed by a warp reduction.  Same
+// record and count as k_slice_pre.
+constexpr int PRE_WARPS = 8;
+
+__global__ void __launch_bounds__(PRE_WARPS * 32) k_slice_pre_warp(SliceArgs a, SliceRec* __restrict__ rec,
+                                                                   unsigned long long* __restrict__ counts) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * PRE_WARPS + (threadIdx.x >> 5);
+  if (i >= a.n) return;  // uniform over the warp
+  const SliceRec r = make_record(a, i);
+  if (lane == 0) rec[i] = r;
+  unsigned long long c = 0;
+  if (r.r3.y != 0.0f) {
+    int plo, phi;
+    plane_range(a, r, plo, phi);
+    for (int j = plo + lane; j < phi; j += 32) c += plane_pairs(a, r, j);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) counts[i] = c;
 }
 
 // Item owning batch-wide index x of a prefix table t[0..n] (t[0] = 0).
@@ -247,7 +288,10 @@ void launch_slice_pre_batch(const BatchItems& b, SliceRec* rec, unsigned long lo
 
 void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
   if (a.n <= 0) return;
-  k_slice_pre<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, counts);
+  if (warp_per_gaussian(a))
+    k_slice_pre_warp<<<ceil_div(a.n, PRE_WARPS), PRE_WARPS * 32, 0, st>>>(a, rec, counts);
+  else
+    k_slice_pre<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, counts);
   note_launch();
 }
 
@@ -323,11 +367,60 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_slice_emit(SliceArgs a1, Batch
   }
 }
 
+// K-emit with a warp per Gaussian (calls with many planes): the lanes take 32
+// of the Gaussian's planes at a time, a warp scan of their pair counts gives
+// each lane the start of its plane's run, so the Gaussian's pairs leave as one
+// contiguous run in the same order as the thread-per-Gaussian emission.
+__global__ void __launch_bounds__(PRE_WARPS * 32) k_slice_emit_warp(SliceArgs a, const SliceRec* __restrict__ rec,
+                                                                    const unsigned long long* __restrict__ offsets,
+                                                                    uint32_t* __restrict__ keys,
+                                                                    uint32_t* __restrict__ emit_gid) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * PRE_WARPS + (threadIdx.x >> 5);
+  if (i >= a.n) return;  // uniform over the warp
+  const SliceRec r = rec[i];
+  if (r.r3.y == 0.0f) return;
+  const uint32_t T = (uint32_t)(a.TX * a.TY);
+  unsigned long long base = offsets[i];
+  int plo, phi;
+  plane_range(a, r, plo, phi);
+  for (int j0 = plo; j0 < phi; j0 += 32) {
+    const int j = j0 + lane;
+    const unsigned c = j < phi ? plane_pairs(a, r, j) : 0u;
+    unsigned incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (j < phi) {
+      unsigned long long e = base + (incl - c);
+      const PlaneBox b = plane_box(a, r, j);
+      const uint32_t kb = a.key_base + (uint32_t)a.zorder[j] * T;
+      for (int ty = b.ty0; ty <= b.ty1; ++ty) {
+        int lo, hi;
+        if (!row_tiles(a, r, b, ty, &lo, &hi)) continue;
+        for (int tx = lo; tx <= hi; ++tx) {
+          keys[e] = kb + (uint32_t)(ty * a.TX + tx);
+          emit_gid[e] = (uint32_t)i;
+          ++e;
+        }
+      }
+    }
+    base += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
 void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* offsets,
                        const unsigned long long* counts, uint32_t* keys, uint32_t* vals, uint32_t* emit_gid,
                        cudaStream_t st) {
   (void)vals;  // the sort generates the identity values itself
   if (a.n <= 0) return;
+  if (warp_per_gaussian(a)) {
+    k_slice_emit_warp<<<ceil_div(a.n, PRE_WARPS), PRE_WARPS * 32, 0, st>>>(a, rec, offsets, keys, emit_gid);
+    note_launch();
+    return;
+  }
   BatchItems none{};
   k_slice_emit<false><<<ceil_div(a.n, EMIT_THREADS), EMIT_THREADS, 0, st>>>(a, none, a.n, rec, offsets, counts,
                                                                             ~0ull, keys, emit_gid);
