@@ -131,3 +131,45 @@ def test_batch_overflow_is_reported_not_faulted():
     plan2.run()
     plan2.wait()
     plan2.close()
+
+
+def test_batched_workload_full_size_sampled():
+    """The batched benchmark workload itself (64 uneven sets, 1k-200k Gaussians,
+    128^2-1024^2 slices, 8-64 planes, sigma_z in [1, 6]) in its benchmarked
+    launch configuration (one autotuned plan): for six items, the smallest, the
+    largest and four others, forward on 256 sampled pixels and the gradients of
+    8 sampled Gaussians against the oracle."""
+    ctx = B.Context(0)
+    raw = synth.batched()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4004)
+    items = []
+    for bi in raw:
+        S = len(bi.z)
+        gs = dev_set(bi.gs)
+        items.append({"gs": gs, "z": bi.z, "H": bi.H, "W": bi.W, "sigma_z": bi.sigma_z, "axis": 2,
+                      "out": torch.empty(S, bi.H, bi.W, device="cuda"),
+                      "dL_dI": torch.randn(S, bi.H, bi.W, device="cuda", generator=gen),
+                      "grads": (torch.empty(gs.n, 3, device="cuda"), torch.empty(gs.n, 3, device="cuda"),
+                                torch.empty(gs.n, 4, device="cuda"), torch.empty(gs.n, device="cuda"))})
+    plan = B.BatchPlan(ctx, items, autotune=True)
+    plan.run()
+    plan.wait()
+    sizes = [bi.gs.n for bi in raw]
+    pick = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 5, 17, 33, 50})
+    rng = np.random.Generator(np.random.PCG64(77))
+    for k in pick:
+        bi, it = raw[k], items[k]
+        g, S = bi.gs, len(bi.z)
+        ps = rng.integers(0, S, 256).astype(np.int32)
+        iy, ix = rng.integers(0, bi.H, 256), rng.integers(0, bi.W, 256)
+        ref = oracle.render_points(g.mu, g.scale, g.quat, g.alpha, bi.z, bi.sigma_z, ps, ix + 0.5, iy + 0.5)
+        got = np32(it["out"][torch.from_numpy(ps).long(), torch.from_numpy(iy), torch.from_numpy(ix)])
+        assert_forward_close(got, ref, f"batched item {k} ({g.n} Gaussians, {S} x {bi.H}^2)")
+        near = np.where(np.min(np.abs(g.mu[:, 2][:, None] - bi.z[None, :]), axis=1) < 3.0 * bi.sigma_z + 3.0)[0]
+        sel = np.sort(rng.choice(near, min(8, near.size), replace=False))
+        og = oracle.render_backward(g.mu[sel], g.scale[sel], g.quat[sel], g.alpha[sel], bi.z, bi.H, bi.W,
+                                    bi.sigma_z, it["dL_dI"].cpu().numpy())
+        sub = [t[torch.from_numpy(sel).long().cuda()] for t in it["grads"]]
+        assert_grads_close(sub, og, f"batched item {k} grads")
+    plan.close()
