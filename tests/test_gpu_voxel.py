@@ -146,3 +146,25 @@ def test_voxelize_bad_arguments(ctx):
         st = B.lib.gp_voxelize(ctx.h, ctypes.byref(s), X, Y, Z, ctypes.c_void_p(vol.data_ptr()), None)
         assert st == B.GP_ERR_ARG, (X, Y, Z, st)
     torch.cuda.synchronize()
+
+
+def test_voxelize_ultrasound_full_size_sampled():
+    """The voxelize benchmark's workload in its launch configuration: 200k
+    Gaussians of the ultrasound set on the 512^3 grid, forward on 512 sampled
+    voxels, backward against a random dL/dV on 8 sampled Gaussians."""
+    c = B.Context(0, reuse_bins=True)
+    g = synth.ultrasound()
+    gs = dev_set(g)
+    vol = B.gp_voxelize(c, gs, 512, 512, 512)
+    rng = np.random.Generator(np.random.PCG64(52))
+    idx = rng.integers(0, 512, (512, 3))
+    ref = oracle.voxelize_points(*orc(g), idx[:, 0] + 0.5, idx[:, 1] + 0.5, idx[:, 2] + 0.5)
+    got = np32(vol[torch.from_numpy(idx[:, 2]), torch.from_numpy(idx[:, 1]), torch.from_numpy(idx[:, 0])])
+    assert_forward_close(got, ref, "voxelize 512^3 sampled")
+    del vol
+    G = torch.randn(512, 512, 512, device="cuda", generator=torch.Generator(device="cuda").manual_seed(53))
+    grads = B.gp_voxelize_backward(c, gs, 512, 512, 512, G)
+    sel = np.sort(rng.choice(g.n, 8, replace=False))
+    og = oracle.voxelize_backward(g.mu[sel], g.scale[sel], g.quat[sel], g.alpha[sel], 512, 512, 512, G.cpu().numpy())
+    sub = [t[torch.from_numpy(sel).long().cuda()] for t in grads]
+    assert_grads_close(sub, og, "voxelize 512^3 sampled grads")
