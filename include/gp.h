@@ -96,12 +96,12 @@ typedef struct {
   int bwd_px;             /* backward rasteriser: 0 (default) = block-culled kernel, or the
                              per-thread kernel (16: 2, 4, 8 pixels per thread; 8: 2) */
   int64_t workspace_limit;/* max device bytes of library scratch, 0 = no limit */
-  int reuse_bins;         /* 1: gp_render_backward reuses the binning of the immediately
-                             preceding gp_render_slices on this context when called with the
-                             same set pointers, n, scale_mod, planes, image size, sigma_z and
-                             axis; the caller guarantees the parameter VALUES are unchanged
-                             in between (true inside one forward/backward step).  0 (default):
-                             the backward always re-bins. */
+  int reuse_bins;         /* 1: gp_render_backward (gp_voxelize_backward) reuses the binning of
+                             the immediately preceding gp_render_slices (gp_voxelize) on this
+                             context when called with the same set pointers, n, scale_mod,
+                             planes, image size, sigma_z and axis (grid); the caller guarantees
+                             the parameter VALUES are unchanged in between (true inside one
+                             forward/backward step).  0 (default): the backward always re-bins. */
 } gp_config;
 
 /* Fills *cfg with the defaults above.  Returns GP_ERR_ARG if cfg is NULL. */
@@ -233,14 +233,20 @@ GP_API gp_status gp_mse_grad_noalloc(const float* I, const float* T, const int* 
 
 /* Differentiable voxelizer (Sec. 4.3 "Differentiable Voxelization", Eq. 12):
  * V(x) = sum_i alpha_i exp(-1/2 (x - mu_i)^T Sigma_i^-1 (x - mu_i)) on the
- * X x Y x Z voxel grid, written to vol (DEVICE, [Z][Y][X], overwritten).
- * Binned to 8^3 voxel tiles; each Gaussian visits the tiles inside the bounding
- * box of its ellipsoid (x - mu)^T Sigma^-1 (x - mu) <= 2 ln(1/eps). */
+ * X x Y x Z voxel grid (voxel centres at index + 1/2), written to vol (DEVICE,
+ * [Z][Y][X], overwritten).  Rendered as the stack of the grid's z-planes
+ * through the slice path: on a plane the term factors into alpha exp(-delta^2 /
+ * 2 Sigma_zz) exp(-1/2 d^T Sigma_2d^-1 d) with Sigma_2d the conditional
+ * covariance, i.e. the slice operator with sigma_z = 0 and amplitude alpha.
+ * Each plane is culled by its section of the ellipsoid (x - mu)^T Sigma^-1
+ * (x - mu) <= 2 ln(1/eps).  GP_ERR_ARG for X, Y or Z <= 0, more than 2^31
+ * voxels or a NULL vol. */
 GP_API gp_status gp_voxelize(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, float* vol,
                       void* stream);
 
 /* Backward of gp_voxelize given dL/dV (DEVICE [Z][Y][X]); gradients as in
- * gp_render_backward (overwritten). */
+ * gp_render_backward (overwritten).  With reuse_bins it reuses the binning of
+ * an immediately preceding gp_voxelize of the same set and grid. */
 GP_API gp_status gp_voxelize_backward(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z,
                                const float* dL_dV, float* d_mu, float* d_scale,
                                float* d_quat, float* d_alpha, void* stream);
