@@ -748,7 +748,7 @@ def run_ultrasound(args):
     dev = "cuda:0"
     # the backward takes the forward's bins (parameters unchanged); --exp picks the
     # rasterisers' exponential (the voxelizer always evaluates exp2 per voxel)
-    ctx = B.Context(0, reuse_bins=True, exp_mode=EXP_MODES[args.exp])
+    ctx = B.Context(0, reuse_bins=True, exp_mode=EXP_MODES[args.exp], tile=args.tile)
     g = synth.ultrasound()
     gs = B.GaussianSet.from_numpy(g, dev)
     D = 512
