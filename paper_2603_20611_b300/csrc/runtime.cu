@@ -227,6 +227,9 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
     const float span = zs[S - 1] - zs[0];
     A.warp_pairs = span > 0.0f && 2.0f * sqrtf(2.0f * logf(1.0f / c->cfg.eps)) * sigma_z >= 32.0f * span / (float)(S - 1);
   }
+  // otherwise 4 lanes per Gaussian on dense stacks (planes at most 2 apart, at
+  // least 8 of them), where a Gaussian's own extent reaches several planes
+  if (!A.warp_pairs && S >= 8) A.group_pairs = (zs[S - 1] - zs[0]) <= 2.0f * (float)(S - 1);
   memcpy(A.Rc, view.R, sizeof(A.Rc));
   memcpy(A.tc, view.t, sizeof(A.tc));
   A.k2 = 2.0f * logf(1.0f / c->cfg.eps);

@@ -43,6 +43,7 @@
 namespace gp {
 
 constexpr int PRE_THREADS = 256;
+constexpr int kPairGroup = 4;  // lanes per Gaussian of the grouped K-pre / K-emit
 
 // Calls whose Gaussians each reach tens of planes (the host sets warp_pairs)
 // count and emit with a warp per Gaussian, the lanes taking its planes; other
@@ -127,7 +128,7 @@ __device__ __forceinline__ PlaneBox plane_box(const SliceArgs& a, const SliceRec
 // [xmin, xmax].  Explicit roundings keep the count and the emission identical.
 __device__ __forceinline__ bool row_tiles(const SliceArgs& a, const SliceRec& r, const PlaneBox& b, int ty,
                                           int* lo, int* hi) {
-  const float c00 = r.r2.x, c01 = r.r2.y, c11 = r.r2.z, rx = b.rxe, ry = b.rye, k2 = b.k2e;
+  const float c01 = r.r2.y, c11 = r.r2.z, rx = b.rxe, ry = b.rye, k2 = b.k2e;
   const float inv00 = r.r3.z, inv11 = r.r3.w;
   const float y0 = (float)(ty * a.tile) + 0.5f;
   const float y1 = (float)(min((ty + 1) * a.tile, a.H)) - 0.5f;
@@ -237,6 +238,40 @@ __global__ void __launch_bounds__(PRE_THREADS) k_slice_pre(SliceArgs a, SliceRec
   if (i < a.n) slice_pre_one(a, i, i, rec, counts);
 }
 
+// K-pre split in two for calls whose Gaussians reach a few planes each: the
+// records (a thread per Gaussian), then the counts with a group of L lanes per
+// Gaussian, the lanes taking its planes (a stride of L).  Loop bounds are made
+// uniform over the warp (groups of one warp reach different numbers of planes)
+// so that the group shuffles run with every lane present.
+__global__ void __launch_bounds__(PRE_THREADS) k_slice_rec(SliceArgs a, SliceRec* __restrict__ rec) {
+  const int i = blockIdx.x * PRE_THREADS + threadIdx.x;
+  if (i < a.n) rec[i] = make_record(a, i);
+}
+
+template <int L>
+__global__ void __launch_bounds__(PRE_THREADS) k_slice_count_grp(SliceArgs a, const SliceRec* __restrict__ rec,
+                                                                 unsigned long long* __restrict__ counts) {
+  const int sub = threadIdx.x & (L - 1);
+  const int i = (int)((blockIdx.x * (unsigned)PRE_THREADS + threadIdx.x) / L);
+  const bool live = i < a.n;
+  SliceRec r{};
+  int plo = 0, phi = 0;
+  if (live) {
+    r = rec[i];
+    if (r.r3.y != 0.0f) plane_range(a, r, plo, phi);
+  }
+  const int np = phi - plo;
+  const int npmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)np);
+  unsigned c = 0;
+  for (int t0 = 0; t0 < npmax; t0 += L) {
+    const int t = t0 + sub;
+    if (t < np) c += plane_pairs(a, r, plo + t);
+  }
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o, L);
+  if (sub == 0 && live) counts[i] = c;
+}
+
 // K-pre with a warp per Gaussian, for calls with many planes: the lanes count
 // the Gaussian's planes (a stride of 32), summed by a warp reduction.  Same
 // record and count as k_slice_pre.
@@ -288,11 +323,17 @@ void launch_slice_pre_batch(const BatchItems& b, SliceRec* rec, unsigned long lo
 
 void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
   if (a.n <= 0) return;
-  if (warp_per_gaussian(a))
+  if (warp_per_gaussian(a)) {
     k_slice_pre_warp<<<ceil_div(a.n, PRE_WARPS), PRE_WARPS * 32, 0, st>>>(a, rec, counts);
-  else
+    note_launch();
+  } else if (a.group_pairs) {
+    k_slice_rec<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec);
+    k_slice_count_grp<kPairGroup><<<ceil_div(a.n, PRE_THREADS / kPairGroup), PRE_THREADS, 0, st>>>(a, rec, counts);
+    note_launch(2);
+  } else {
     k_slice_pre<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, counts);
-  note_launch();
+    note_launch();
+  }
 }
 
 // ------------------------------------------------------------ K-emit
@@ -411,6 +452,84 @@ __global__ void __launch_bounds__(PRE_WARPS * 32) k_slice_emit_warp(SliceArgs a,
   }
 }
 
+// K-emit with a group of L lanes per Gaussian (the grouped K-pre's calls): the
+// lanes take the Gaussian's planes, a group scan of their pair counts places
+// each plane's run, and the warp's Gaussians (32 / L, consecutive, so their
+// runs are one contiguous stretch) are gathered in a shared-memory window of
+// GRP_WIN pairs and written with coalesced stores.  A warp with more pairs than
+// the window stores directly.  Same pairs, same order as k_slice_emit.
+constexpr int GRP_WIN = 512;
+
+template <int L>
+__global__ void __launch_bounds__(EMIT_THREADS) k_slice_emit_grp(SliceArgs a, const SliceRec* __restrict__ rec,
+                                                                 const unsigned long long* __restrict__ offsets,
+                                                                 const unsigned long long* __restrict__ counts,
+                                                                 uint32_t* __restrict__ keys,
+                                                                 uint32_t* __restrict__ emit_gid) {
+  __shared__ uint32_t wkey[EMIT_THREADS / 32][GRP_WIN];
+  __shared__ uint32_t wgid[EMIT_THREADS / 32][GRP_WIN];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane & (L - 1);
+  const int gw = (int)((blockIdx.x * (unsigned)EMIT_THREADS + threadIdx.x) >> 5);  // global warp
+  const int i0 = gw * (32 / L);
+  if (i0 >= a.n) return;  // whole warp past the end
+  const int i = i0 + lane / L;
+  const bool live = i < a.n;
+  const int ilast = min(i0 + 32 / L - 1, a.n - 1);
+  const unsigned long long wstart = offsets[i0];
+  const unsigned long long wcount = offsets[ilast] + counts[ilast] - wstart;
+  const bool window = wcount <= (unsigned long long)GRP_WIN;
+  SliceRec r{};
+  int plo = 0, phi = 0;
+  if (live) {
+    r = rec[i];
+    if (r.r3.y != 0.0f) plane_range(a, r, plo, phi);
+  }
+  const int np = phi - plo;
+  const int npmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)np);
+  const uint32_t T = (uint32_t)(a.TX * a.TY);
+  unsigned long long run = live ? offsets[i] : 0ull;  // where the group's next round of planes starts
+  for (int t0 = 0; t0 < npmax; t0 += L) {
+    const int t = t0 + sub;
+    const bool mine = t < np;
+    const int j = plo + t;
+    const unsigned c = mine ? plane_pairs(a, r, j) : 0u;
+    unsigned incl = c;
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xffffffffu, incl, o, L);
+      if (sub >= o) incl += v;
+    }
+    if (mine && c) {
+      unsigned long long e = run + (incl - c);
+      const PlaneBox b = plane_box(a, r, j);
+      const uint32_t kb = (uint32_t)a.zorder[j] * T;
+      for (int ty = b.ty0; ty <= b.ty1; ++ty) {
+        int lo, hi;
+        if (!row_tiles(a, r, b, ty, &lo, &hi)) continue;
+        for (int tx = lo; tx <= hi; ++tx) {
+          const uint32_t key = kb + (uint32_t)(ty * a.TX + tx);
+          if (window) {
+            wkey[warp][e - wstart] = key;
+            wgid[warp][e - wstart] = (uint32_t)i;
+          } else {
+            keys[e] = key;
+            emit_gid[e] = (uint32_t)i;
+          }
+          ++e;
+        }
+      }
+    }
+    run += __shfl_sync(0xffffffffu, incl, L - 1, L);
+  }
+  if (window) {
+    __syncwarp();
+    for (int k = lane; k < (int)wcount; k += 32) {
+      keys[wstart + k] = wkey[warp][k];
+      emit_gid[wstart + k] = wgid[warp][k];
+    }
+  }
+}
+
 void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* offsets,
                        const unsigned long long* counts, uint32_t* keys, uint32_t* vals, uint32_t* emit_gid,
                        cudaStream_t st) {
@@ -418,6 +537,12 @@ void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned l
   if (a.n <= 0) return;
   if (warp_per_gaussian(a)) {
     k_slice_emit_warp<<<ceil_div(a.n, PRE_WARPS), PRE_WARPS * 32, 0, st>>>(a, rec, offsets, keys, emit_gid);
+    note_launch();
+    return;
+  }
+  if (a.group_pairs) {
+    k_slice_emit_grp<kPairGroup><<<ceil_div(a.n, EMIT_THREADS / kPairGroup), EMIT_THREADS, 0, st>>>(
+        a, rec, offsets, counts, keys, emit_gid);
     note_launch();
     return;
   }
