@@ -296,7 +296,10 @@ constexpr int ACC10 = 10;
 // Shared memory of the backward body.  The tile's dL/dI is held half-block by
 // half-block (4 rows of 8 pixels each), the half-blocks 36 floats apart: the
 // 16-byte loads of the same row and column by lanes working on different
-// half-blocks then fall in different banks.
+// half-blocks then fall in different banks.  A row is stored as its pixels
+// 0, 1, 2, 3, 7, 6, 5, 4 (each pixel of the first half followed, four places on,
+// by its mirror about the row's centre), or in order with a reversed copy
+// beside it under the row factorisation.
 template <int TILE, int CH, bool RF = false>
 struct BwdSmem {
   static constexpr int NW = (TILE / 8) * (TILE / 8);
@@ -313,15 +316,15 @@ struct BwdSmem {
 
 // Backward of one (slice s, tile t) of item a.  The tile is cut into 8 x 4
 // half-blocks; every (staged Gaussian, half-block) pair whose ellipse touches
-// the half-block is a unit of work, and the CTA's threads take the units of a
-// chunk round-robin, so all warps get the same share whatever the Gaussians'
-// layout.  A thread sums, over its unit's 32 pixels, the six moments
+// the half-block is a unit of work.  Each warp takes its own chunks of the
+// tile's list and evaluates their units one per lane: a lane sums, over its
+// unit's 32 pixels, the six moments
 //     sum G E {1, dx, dy, dx^2, dx dy, dy^2}      (E the Gaussian's exponential,
 // G = dL/dI, d = pixel - mu_2d), row by row with two pixels per packed
-// instruction; no unit is shared, so nothing is reduced across lanes.  The
-// per-half-block moments of a Gaussian are summed in a fixed order and folded
-// into its 10 accumulators (atomics) or written as a per-pair partial
-// (deterministic mode).
+// instruction and a row's pixels in mirrored couples.  The per-half-block
+// moments of a Gaussian are summed in a fixed order and folded into its 10
+// accumulators (atomics) or written as a per-pair partial (deterministic
+// mode).
 template <int TILE, int CH, int EXPM, bool DET>
 __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, const SliceRec* __restrict__ rec,
                                          const uint32_t* __restrict__ vals, const uint32_t* __restrict__ emit_gid,
@@ -350,7 +353,8 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
     const int py = ty * TILE + yy, px = tx * TILE + xx;
     const int hb = 2 * ((yy >> 3) * (TILE / 8) + (xx >> 3)) + ((yy >> 2) & 1);
     const float gv = (py < a.H && px < a.W) ? a.dL_dI[((int64_t)s * a.H + py) * a.W + px] : 0.0f;
-    sm.G[hb * HBS + (yy & 3) * 8 + (xx & 7)] = gv;
+    const int cx = xx & 7;
+    sm.G[hb * HBS + (yy & 3) * 8 + ((RF || cx < 4) ? cx : 11 - cx)] = gv;
     if constexpr (RF) sm.Grev[hb * HBS + (yy & 3) * 8 + (7 - (xx & 7))] = gv;
   }
   __syncthreads();
@@ -467,34 +471,62 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
             M02 = fmaf(rf * rf, S0, M02);
           }
         } else {
+          // per-pixel exponentials, the pixels of a row taken in mirrored couples
+          // (q, -q): with X = G E at the q < 0 pixels and Y at their mirrors,
+          //     sum G E = X + Y,  sum q G E = q (X + Y) - 2 q Y,  sum q^2 G E = q^2 (X + Y).
+          // Rows run bottom-up with running sums P, so the row-weighted moments
+          // are sums of P's snapshots: sum_r r S_r = s3 + (s3 + s2) + (s3 + s2 + s1)
+          // and sum_r r^2 S_r = 5 s3 + 3 (s3 + s2) + (s3 + s2 + s1) (s_r the row sums).
+          const float* Gm = RF ? sm.Grev + hb * HBS : Gr + 4;  // the row's pixels 7, 6, 5, 4
+          float2 P0, P1, P2, T0, T1, U0;
 #pragma unroll
-          for (int r = 0; r < 4; ++r) {
+          for (int r = 3; r >= 0; --r) {
             const float rf = (float)r;
             const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
             const float B = fmaf(c1, rf, B0);
-            const float2 A2 = make_float2(A, A), B2 = make_float2(B, B);
-            const float4 ga = *reinterpret_cast<const float4*>(Gr + r * 8);
-            const float4 gb = *reinterpret_cast<const float4*>(Gr + r * 8 + 4);
-            const float2 Gp[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w), make_float2(gb.x, gb.y),
-                                  make_float2(gb.z, gb.w)};
-            float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
+            const float2 A2 = make_float2(A, A), B2 = make_float2(B, B), Bn2 = make_float2(-B, -B);
+            const float4 gx = *reinterpret_cast<const float4*>(Gr + r * 8);
+            const float4 gy = *reinterpret_cast<const float4*>(Gm + r * 8);
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              const float qa = (float)(2 * p) - 3.5f, qb = (float)(2 * p + 1) - 3.5f;
-              const float2 q = make_float2(qa, qb);
-              const float2 gE = __fmul2_rn(Gp[p], pair_exp2<EXPM>(C2, B2, A2, q));
-              P0 = __fadd2_rn(P0, gE);
-              P1 = __ffma2_rn(q, gE, P1);
-              P2 = __ffma2_rn(make_float2(qa * qa, qb * qb), gE, P2);
+            for (int k = 0; k < 2; ++k) {
+              const float qa = (float)(2 * k) - 3.5f, qb = qa + 1.0f;
+              const float2 q = make_float2(qa, qb), q2 = make_float2(qa * qa, qb * qb);
+              const float2 GX = k == 0 ? make_float2(gx.x, gx.y) : make_float2(gx.z, gx.w);
+              const float2 GY = k == 0 ? make_float2(gy.x, gy.y) : make_float2(gy.z, gy.w);
+              // e(-q) = (C q - B) q + A
+              const float2 Y = __fmul2_rn(GY, pair_exp2<EXPM>(C2, Bn2, A2, q));
+              const float2 XY = __ffma2_rn(GX, pair_exp2<EXPM>(C2, B2, A2, q), Y);
+              if (r == 3 && k == 0) {
+                P0 = XY;
+                P1 = __fmul2_rn(q, XY);
+                P2 = __fmul2_rn(q2, XY);
+              } else {
+                P0 = __fadd2_rn(P0, XY);
+                P1 = __ffma2_rn(q, XY, P1);
+                P2 = __ffma2_rn(q2, XY, P2);
+              }
+              P1 = __ffma2_rn(make_float2(-2.0f * qa, -2.0f * qb), Y, P1);
             }
-            const float S0 = P0.x + P0.y, S1 = P1.x + P1.y, S2 = P2.x + P2.y;
-            M00 += S0;
-            M10 += S1;
-            M20 += S2;
-            M01 = fmaf(rf, S0, M01);
-            M11 = fmaf(rf, S1, M11);
-            M02 = fmaf(rf * rf, S0, M02);
+            if (r == 3) {
+              T0 = P0;
+              T1 = P1;
+              U0 = __fmul2_rn(make_float2(5.0f, 5.0f), P0);
+            } else if (r == 2) {
+              T0 = __fadd2_rn(T0, P0);
+              T1 = __fadd2_rn(T1, P1);
+              U0 = __ffma2_rn(make_float2(3.0f, 3.0f), P0, U0);
+            } else if (r == 1) {
+              T0 = __fadd2_rn(T0, P0);
+              T1 = __fadd2_rn(T1, P1);
+              U0 = __fadd2_rn(U0, P0);
+            }
           }
+          M00 = P0.x + P0.y;
+          M10 = P1.x + P1.y;
+          M20 = P2.x + P2.y;
+          M01 = T0.x + T0.y;
+          M11 = T1.x + T1.y;
+          M02 = U0.x + U0.y;
         }
         // moments in d = (dxc + q, dy0 + r)
         mom[0] = M00;
@@ -598,7 +630,7 @@ __device__ __forceinline__ int find_item_k(const T* __restrict__ t, int n, T x) 
 }
 
 template <int TILE, int CH, int EXPM>
-__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32) k_raster_fwd_persist(
+__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? 12 : 32) k_raster_fwd_persist(
     BatchItems b, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, unsigned* __restrict__ work) {
   __shared__ FwdSmem<TILE, CH, row_factored<EXPM>()> sm;
@@ -620,7 +652,8 @@ __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32) k_raster_fwd_per
 }
 
 template <int TILE, int CH, int EXPM, bool DET>
-__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32) k_raster_bwd_persist(
+__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? (row_factored<EXPM>() ? 9 : 10) : 32)
+    k_raster_bwd_persist(
     BatchItems b, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, float* __restrict__ accum,
     float4* __restrict__ partial, unsigned* __restrict__ work) {
