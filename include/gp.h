@@ -66,6 +66,7 @@ typedef int gp_status;
 #define GP_ERR_TIMEOUT (-4)   /* a bounded wait ran out */
 #define GP_ERR_OVERFLOW (-5)  /* a preplanned buffer was too small; re-plan */
 #define GP_ERR_STATE (-6)     /* call not valid in the object's current state */
+#define GP_ERR_CANCELLED (-7) /* gp_serve_poll result: the request was cancelled while queued */
 
 typedef struct gp_ctx gp_ctx;
 
@@ -95,7 +96,10 @@ typedef struct {
                              kernel with this many pixels per thread (16: 1, 2, 4; 8: 1, 2) */
   int bwd_px;             /* backward rasteriser: 0 (default) = block-culled kernel, or the
                              per-thread kernel (16: 2, 4, 8 pixels per thread; 8: 2) */
-  int64_t workspace_limit;/* max device bytes of library scratch, 0 = no limit */
+  int64_t workspace_limit;/* max device bytes of library scratch, 0 = no limit.  A call that
+                             would pass it (or whose cudaMalloc fails) returns GP_ERR_OOM
+                             after freeing the context's whole workspace, so later calls
+                             that fit still run. */
   int reuse_bins;         /* 1: gp_render_backward (gp_voxelize_backward) reuses the binning of
                              the immediately preceding gp_render_slices (gp_voxelize) on this
                              context when called with the same set pointers, n, scale_mod,
@@ -388,6 +392,8 @@ typedef struct {
   int X, Y, Z;      /* voxelize */
   float* out;       /* DEVICE [S][H][W] or [Z][Y][X] */
   const gp_view* view;  /* HOST, copied at submit; NULL = the view of `axis` (slice / stack) */
+  double timeout_ms;    /* queue deadline: a request not started within timeout_ms of its
+                           submit is dropped with result status GP_ERR_TIMEOUT; 0 = none */
 } gp_request;
 
 typedef struct {
@@ -400,6 +406,7 @@ typedef struct {
 typedef struct {
   int64_t submitted, completed, failed, batches, admission_waits, pending, inflight_bytes;
   int64_t inflight_requests, max_inflight_requests;  /* admitted and not finished; its maximum */
+  int64_t expired, cancelled;  /* dropped from the queue by their deadline / by gp_serve_cancel */
 } gp_serve_stats;
 
 typedef struct gp_server gp_server;
@@ -416,8 +423,16 @@ GP_API gp_status gp_serve_load_encoded(gp_server* server, const gp_codec_header*
 /* Queues a request (validated here: GP_ERR_ARG) and returns its ticket. */
 GP_API gp_status gp_serve_submit(gp_server* server, const gp_request* req, uint64_t* ticket);
 /* Waits up to timeout_ms for the ticket: GP_OK with *out filled (once per
- * ticket), or GP_PENDING if it is still queued or running. */
+ * ticket), or GP_PENDING if it is still queued or running.  out->status is the
+ * request's own outcome: GP_OK, an error of its run, GP_ERR_TIMEOUT (its queue
+ * deadline passed before it started), GP_ERR_CANCELLED, or GP_ERR_STATE (still
+ * queued when the server closed).  Requests past their deadline are dropped
+ * by the workers and by poll / stats calls, without waiting for a worker. */
 GP_API gp_status gp_serve_poll(gp_server* server, uint64_t ticket, int timeout_ms, gp_result* out);
+/* Removes a request that is still queued; its poll result then has status
+ * GP_ERR_CANCELLED.  GP_ERR_STATE if it has started or finished (it runs to
+ * completion), GP_ERR_ARG for a ticket never issued. */
+GP_API gp_status gp_serve_cancel(gp_server* server, uint64_t ticket);
 GP_API gp_status gp_serve_stats_get(gp_server* server, gp_serve_stats* out);
 /* Stops the workers after their current requests; still-queued requests are dropped. */
 GP_API gp_status gp_serve_close(gp_server* server);

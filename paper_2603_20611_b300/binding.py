@@ -26,6 +26,7 @@ GP_ERR_CUDA = -3
 GP_ERR_TIMEOUT = -4
 GP_ERR_OVERFLOW = -5
 GP_ERR_STATE = -6
+GP_ERR_CANCELLED = -7
 GP_EXP_POLY = 0
 GP_EXP_HW = 1
 GP_EXP_POLY_PACKED = 2
@@ -38,7 +39,7 @@ EXPORTS = (
     "gp_last_counts", "gp_count_evals", "gp_exp2_eval", "gp_timing_enable", "gp_timing_read",
     "gp_launch_count", "gp_fma_probe_threads", "gp_fma_probe", "gp_mse_grad_noalloc",
     "gp_batch_plan", "gp_batch_run", "gp_batch_wait", "gp_batch_info", "gp_batch_destroy",
-    "gp_serve_open", "gp_serve_load_set", "gp_serve_submit", "gp_serve_poll", "gp_serve_stats_get",
+    "gp_serve_open", "gp_serve_load_set", "gp_serve_submit", "gp_serve_poll", "gp_serve_cancel", "gp_serve_stats_get",
     "gp_serve_close", "gp_view_from_axis", "gp_render_slices_view", "gp_render_backward_view",
     "gp_count_evals_view", "gp_adam_default", "gp_adam_state_floats", "gp_adam_init", "gp_adam_step",
     "gp_l1_dssim_grad", "gp_encode", "gp_decode", "gp_serve_load_encoded", "gp_count_vox_evals",
@@ -111,7 +112,7 @@ class gp_request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("set_id", ctypes.c_int), ("z", ctypes.c_void_p), ("S", ctypes.c_int),
                 ("H", ctypes.c_int), ("W", ctypes.c_int), ("sigma_z", ctypes.c_float), ("axis", ctypes.c_int),
                 ("X", ctypes.c_int), ("Y", ctypes.c_int), ("Z", ctypes.c_int), ("out", ctypes.c_void_p),
-                ("view", ctypes.c_void_p)]
+                ("view", ctypes.c_void_p), ("timeout_ms", ctypes.c_double)]
 
 
 class gp_result(ctypes.Structure):
@@ -122,7 +123,7 @@ class gp_result(ctypes.Structure):
 class gp_serve_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "batches", "admission_waits",
                                               "pending", "inflight_bytes", "inflight_requests",
-                                              "max_inflight_requests")]
+                                              "max_inflight_requests", "expired", "cancelled")]
 
 
 def _load():
@@ -164,6 +165,7 @@ def _load():
         "gp_serve_load_set": [P, SP, ctypes.POINTER(I)],
         "gp_serve_submit": [P, ctypes.POINTER(gp_request), ctypes.POINTER(ctypes.c_uint64)],
         "gp_serve_poll": [P, ctypes.c_uint64, I, ctypes.POINTER(gp_result)],
+        "gp_serve_cancel": [P, ctypes.c_uint64],
         "gp_serve_stats_get": [P, ctypes.POINTER(gp_serve_stats)],
         "gp_serve_close": [P],
         "gp_view_from_axis": [I, ctypes.POINTER(gp_view)],
@@ -519,7 +521,10 @@ class Server:
             raise GPError(st, "gp_serve_load_encoded")
         return sid.value
 
-    def submit(self, kind, set_id, out, z=None, H=0, W=0, sigma_z=1.0, axis=2, X=0, Y=0, Z=0, view=None):
+    def submit(self, kind, set_id, out, z=None, H=0, W=0, sigma_z=1.0, axis=2, X=0, Y=0, Z=0, view=None,
+               timeout_ms=0.0):
+        """Queues a request; timeout_ms > 0 drops it (status GP_ERR_TIMEOUT) if it
+        has not started that long after the submit."""
         r = gp_request()
         r.kind, r.set_id = int(kind), int(set_id)
         zz = None
@@ -528,6 +533,7 @@ class Server:
             r.z, r.S = zz.ctypes.data_as(ctypes.c_void_p).value, zz.shape[0]
         r.H, r.W, r.sigma_z, r.axis = int(H), int(W), float(sigma_z), int(axis)
         r.X, r.Y, r.Z = int(X), int(Y), int(Z)
+        r.timeout_ms = float(timeout_ms)
         r.out = _dev(out, "out").value
         v = None
         if view is not None:
@@ -551,6 +557,13 @@ class Server:
         self._outs.pop(ticket, None)
         return {"status": res.status, "latency_ms": res.latency_ms, "queue_ms": res.queue_ms,
                 "batch_size": res.batch_size}
+
+    def cancel(self, ticket):
+        """Removes a still-queued request (its poll status becomes GP_ERR_CANCELLED);
+        GPError with GP_ERR_STATE once it has started."""
+        st = lib.gp_serve_cancel(self.h, ctypes.c_uint64(ticket))
+        if st != GP_OK:
+            raise GPError(st, "gp_serve_cancel")
 
     def stats(self):
         s = gp_serve_stats()

@@ -502,6 +502,7 @@ gp_status gp_batch_plan(gp_ctx* ctx, const gp_batch_item* items, int n, int flag
 
 gp_status gp_batch_run(gp_plan* p, void* stream) {
   if (!p || !p->exec) return GP_ERR_ARG;
+  gp::NvtxRange range("gp:batch_run");
   cudaError_t e = cudaGraphLaunch(p->exec, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_err(p->c, e, "graph launch");
   return GP_OK;

@@ -34,6 +34,7 @@ struct Ctx;
 // Ensures buf holds at least `bytes`; grows by 1.25x.  Returns GP_OK or GP_ERR_OOM.
 gp_status ws_reserve(Ctx* c, DevBuf& buf, size_t bytes);
 void ws_release(Ctx* c, DevBuf& buf);
+void ws_release_all(Ctx* c);
 
 // Buffers of one binned render (slice renderer or voxelizer).
 struct BinBufs {
@@ -107,13 +108,26 @@ struct Ctx {
 
 gp_status set_err(Ctx* c, gp_status st, const std::string& msg);
 
-// Records an event pair around a phase on stream st when timing is enabled.
+// A named NVTX range on the calling host thread for the object's lifetime (a
+// no-op unless a profiler is attached), so the phases of every call show up on
+// an nsys / ncu timeline.
+class NvtxRange {
+ public:
+  explicit NvtxRange(const char* name);
+  ~NvtxRange();
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Records an event pair around a phase on stream st when timing is enabled,
+// inside an NVTX range named after the phase.
 class PhaseTimer {
  public:
   PhaseTimer(Ctx* c, int phase, cudaStream_t st);
   ~PhaseTimer();
 
  private:
+  NvtxRange range_;
   Ctx* c_;
   int phase_;
   cudaStream_t st_;

@@ -15,10 +15,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gp_internal.h"
 #include "slice.cuh"
 
 namespace gp {
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
+
+static const char* phase_range_name(int phase) {
+  static const char* const names[] = {"gp:bin", "gp:fwd", "gp:bwd", "gp:bwd_pre",
+                                      "gp:loss", "gp:vox_fwd", "gp:vox_bwd", "gp:opt"};
+  return phase >= 0 && phase < (int)(sizeof(names) / sizeof(names[0])) ? names[phase] : "gp:phase";
+}
 
 static std::atomic<int64_t> g_launches{0};
 void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -38,7 +49,8 @@ static cudaEvent_t pooled_event(Ctx* c) {
   return e;
 }
 
-PhaseTimer::PhaseTimer(Ctx* c, int phase, cudaStream_t st) : c_(c), phase_(phase), st_(st) {
+PhaseTimer::PhaseTimer(Ctx* c, int phase, cudaStream_t st)
+    : range_(phase_range_name(phase)), c_(c), phase_(phase), st_(st) {
   if (!c->timing) return;
   start_ = pooled_event(c);
   if (start_ && cudaEventRecord(start_, st) != cudaSuccess) {
@@ -73,6 +85,22 @@ gp_status cuda_err(Ctx* c, cudaError_t e, const char* where) {
   return set_err(c, GP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Frees every workspace buffer of the context (and forgets the binning they
+// held).  cudaFree waits for the work already queued on the device, so this is
+// safe while kernels of the failing call are still in flight.
+void ws_release_all(Ctx* c) {
+  BinBufs& b = c->b;
+  DevBuf* all[] = {&b.rec, &b.counts, &b.offsets, &b.total, &b.keys, &b.vals, &b.keys_alt, &b.vals_alt,
+                   &b.emit_gid, &b.ranges, &b.scan_tmp, &b.sort_tmp, &b.zs, &b.zorder, &b.zorig,
+                   &b.accum, &b.partial, &b.loss_tmp, &b.codec};
+  for (DevBuf* d : all) ws_release(c, *d);
+  c->bin_key.valid = false;
+}
+
+// Grows buf to at least `bytes` (by 25 % steps).  A request past the
+// context's workspace limit, or a failed cudaMalloc, frees the whole workspace
+// before it returns GP_ERR_OOM (every caller then returns the error at once),
+// so the context is left empty and later calls that fit still run.
 gp_status ws_reserve(Ctx* c, DevBuf& buf, size_t bytes) {
   if (bytes <= buf.bytes) return GP_OK;
   size_t want = std::max(bytes, (size_t)(buf.bytes * 1.25));
@@ -80,8 +108,10 @@ gp_status ws_reserve(Ctx* c, DevBuf& buf, size_t bytes) {
   int64_t limit = c->cfg.workspace_limit;
   if (limit > 0 && c->ws_bytes - (int64_t)buf.bytes + (int64_t)want > limit) {
     want = (bytes + 255) & ~(size_t)255;
-    if (c->ws_bytes - (int64_t)buf.bytes + (int64_t)want > limit)
+    if (c->ws_bytes - (int64_t)buf.bytes + (int64_t)want > limit) {
+      ws_release_all(c);
       return set_err(c, GP_ERR_OOM, "workspace limit exceeded (" + std::to_string(limit) + " bytes)");
+    }
   }
   if (buf.ptr) {
     cudaError_t e = cudaFree(buf.ptr);
@@ -94,6 +124,7 @@ gp_status ws_reserve(Ctx* c, DevBuf& buf, size_t bytes) {
   if (e != cudaSuccess) {
     buf.ptr = nullptr;
     cudaGetLastError();
+    ws_release_all(c);
     return set_err(c, GP_ERR_OOM, "cudaMalloc of " + std::to_string(want) + " bytes failed");
   }
   buf.bytes = want;
@@ -378,11 +409,7 @@ gp_status gp_destroy(gp_ctx* ctx) {
   Ctx* c = &ctx->impl;
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
-  BinBufs& b = c->b;
-  DevBuf* all[] = {&b.rec, &b.counts, &b.offsets, &b.total, &b.keys, &b.vals, &b.keys_alt, &b.vals_alt,
-                   &b.emit_gid, &b.ranges, &b.scan_tmp, &b.sort_tmp, &b.zs, &b.zorder, &b.zorig,
-                   &b.accum, &b.partial, &b.loss_tmp, &b.codec};
-  for (DevBuf* d : all) ws_release(c, *d);
+  ws_release_all(c);
   for (auto& e : c->events) {
     cudaEventDestroy(e.start);
     cudaEventDestroy(e.stop);

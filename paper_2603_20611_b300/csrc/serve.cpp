@@ -105,6 +105,35 @@ int64_t free_device_bytes(int device) {
   return (int64_t)f;
 }
 
+// Result of a request that leaves the queue without running (deadline passed,
+// cancelled).  Caller holds s->mu.
+void drop_locked(gp_server* s, const Request& q, gp_status st, Clock::time_point now) {
+  gp_result res{};
+  res.status = st;
+  res.latency_ms = ms_between(q.submitted, now);
+  res.queue_ms = res.latency_ms;
+  res.batch_size = 0;
+  s->done[q.ticket] = res;
+  s->stats.completed += 1;
+  s->stats.failed += 1;
+  if (st == GP_ERR_TIMEOUT) s->stats.expired += 1;
+  if (st == GP_ERR_CANCELLED) s->stats.cancelled += 1;
+  s->cv_done.notify_all();
+}
+
+// Drops the queued requests whose deadline has passed.  Caller holds s->mu.
+void expire_locked(gp_server* s) {
+  const Clock::time_point now = Clock::now();
+  for (auto it = s->pending.begin(); it != s->pending.end();) {
+    if (it->r.timeout_ms > 0.0 && ms_between(it->submitted, now) > it->r.timeout_ms) {
+      drop_locked(s, *it, GP_ERR_TIMEOUT, now);
+      it = s->pending.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
 void finish(gp_server* s, const std::vector<Request>& reqs, gp_status st, Clock::time_point started) {
   const Clock::time_point now = Clock::now();
   std::lock_guard<std::mutex> lk(s->mu);
@@ -181,6 +210,7 @@ void worker_loop(gp_server* s, int wi) {
       int64_t budget = 0;
       for (;;) {
         if (s->stop) return;
+        expire_locked(s);
         if (!s->pending.empty()) {
           // admission: the oldest request first; it runs if its estimate fits in
           // the memory budget (always, when nothing else is in flight)
@@ -214,6 +244,7 @@ void worker_loop(gp_server* s, int wi) {
       s->stats.max_inflight_requests = std::max(s->stats.max_inflight_requests, s->stats.inflight_requests);
     }
     const Clock::time_point started = Clock::now();
+    gp::NvtxRange range(batch[0].r.kind == GP_REQ_VOXELIZE ? "gp:serve_voxelize" : "gp:serve_slices");
     gp_status st;
     if (batch[0].r.kind == GP_REQ_VOXELIZE) {
       const gp_request& r = batch[0].r;
@@ -232,7 +263,7 @@ void worker_loop(gp_server* s, int wi) {
 gp_status check_request(gp_server* s, const gp_request* r) {
   if (!r) return GP_ERR_ARG;
   if (r->set_id < 0 || r->set_id >= (int)s->sets.size()) return GP_ERR_ARG;
-  if (!r->out) return GP_ERR_ARG;
+  if (!r->out || !(r->timeout_ms >= 0.0)) return GP_ERR_ARG;
   if (r->kind == GP_REQ_VOXELIZE) {
     if (r->X <= 0 || r->Y <= 0 || r->Z <= 0) return GP_ERR_ARG;
     return GP_OK;
@@ -366,6 +397,7 @@ gp_status gp_serve_poll(gp_server* s, uint64_t ticket, int timeout_ms, gp_result
   if (ticket >= s->next_ticket) return GP_ERR_ARG;
   const auto deadline = Clock::now() + std::chrono::milliseconds(std::max(timeout_ms, 0));
   for (;;) {
+    expire_locked(s);
     auto it = s->done.find(ticket);
     if (it != s->done.end()) {
       *out = it->second;
@@ -373,13 +405,29 @@ gp_status gp_serve_poll(gp_server* s, uint64_t ticket, int timeout_ms, gp_result
       return GP_OK;
     }
     if (timeout_ms <= 0 || Clock::now() >= deadline) return GP_PENDING;
-    s->cv_done.wait_until(lk, deadline);
+    // wake at least every 5 ms, so that a queued request's deadline is seen
+    s->cv_done.wait_until(lk, std::min(deadline, Clock::now() + std::chrono::milliseconds(5)));
   }
+}
+
+gp_status gp_serve_cancel(gp_server* s, uint64_t ticket) {
+  if (!s || ticket == 0) return GP_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (ticket >= s->next_ticket) return GP_ERR_ARG;
+  for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
+    if (it->ticket == ticket) {
+      drop_locked(s, *it, GP_ERR_CANCELLED, Clock::now());
+      s->pending.erase(it);
+      return GP_OK;
+    }
+  }
+  return GP_ERR_STATE;
 }
 
 gp_status gp_serve_stats_get(gp_server* s, gp_serve_stats* out) {
   if (!s || !out) return GP_ERR_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
+  expire_locked(s);
   *out = s->stats;
   out->pending = (int64_t)s->pending.size();
   out->inflight_bytes = s->inflight_bytes;

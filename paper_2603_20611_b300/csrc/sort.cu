@@ -10,11 +10,12 @@
 //   1. k_radix_hist     per 4096-key tile: 256-bin histogram (shared atomics),
 //                       stored digit-major hist[d * nb + b];
 //   2. exclusive scan   of hist -> global scatter base of (digit, tile);
-//   3. k_radix_scatter  per tile, 16 rounds of 256 keys in input order: warp
-//                       match_any gives each key its rank among equal digits in
-//                       its warp, a per-digit prefix over the 8 warps gives the
-//                       rank in the round, and a running per-digit count the rank
-//                       in the tile -> stable positions.
+//   3. k_radix_scatter  per tile, each warp ranks its own 512 keys in 16 rounds
+//                       of 32 (nine ballots give each key the lanes holding the
+//                       same digit, a running per-warp digit count the rest), a
+//                       per-digit prefix over the 8 warps gives tile-local
+//                       positions -> a stable local sort in shared memory, then
+//                       each digit's run is stored contiguously.
 // Only ceil(bits / 8) passes run; bits is the number of live key bits.
 // Counts are read from device memory (n_dev) with a host-side capacity bound on
 // the grid, so the same launches serve a preplanned (graph-captured) binning.
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __res
 
 // Stable scatter of one 4096-key tile.  Warp w owns the tile's keys
 // [w * 512, (w + 1) * 512) and ranks them in 16 rounds of 32 against its own
-// per-digit counters (match_any gives the rank among equal digits in a round),
+// per-digit counters (nine ballots give the rank among equal digits in a round),
 // keeping key, value and rank in registers.  A block-wide pass turns the
 // per-warp counts into tile-local digit offsets; the keys are first placed in
 // shared memory in digit order (a stable local sort), and then written out in

@@ -134,3 +134,72 @@ def test_bad_requests_are_rejected():
     with pytest.raises(B.GPError):
         srv.poll(12345)
     srv.close()
+
+
+def _busy_server(ctx, n_long=3):
+    """One worker and a 1-byte budget, so requests run one at a time, and n_long
+    stacks of a 500k-Gaussian set in front (each several milliseconds): whatever
+    is submitted next waits in the queue behind them."""
+    g = synth.microscopy(seed=1002, n=500_000, extent=(1024, 1024, 256))
+    gs = dev_set(g)
+    srv = B.Server(ctx, workers=1, hbm_budget_bytes=1)
+    sid = srv.load_set(gs)
+    z = (np.arange(64, dtype=np.float32) * 4.0 + 0.5)
+    outs = [torch.empty(64, 1024, 1024, device="cuda") for _ in range(n_long)]
+    long_t = [srv.submit(B.GP_REQ_STACK, sid, o, z=z, H=1024, W=1024, sigma_z=3.0) for o in outs]
+    return srv, sid, gs, long_t, outs
+
+
+def test_cancel_and_queue_deadline():
+    ctx = B.Context(0)
+    srv, sid, gs, long_t, _ = _busy_server(ctx)
+    out = torch.full((1, 64, 64), float("nan"), device="cuda")
+    z = np.array([10.5], np.float32)
+    t_cancel = srv.submit(B.GP_REQ_SLICE, sid, torch.empty(1, 64, 64, device="cuda"), z=z, H=64, W=64, sigma_z=3.0)
+    srv.cancel(t_cancel)  # still queued behind the long stacks
+    t_late = srv.submit(B.GP_REQ_SLICE, sid, torch.empty(1, 64, 64, device="cuda"), z=z, H=64, W=64, sigma_z=3.0,
+                        timeout_ms=2.0)
+    t_ok = srv.submit(B.GP_REQ_SLICE, sid, out, z=z, H=64, W=64, sigma_z=3.0, timeout_ms=60_000.0)
+    assert _wait(srv, t_cancel)["status"] == B.GP_ERR_CANCELLED
+    assert _wait(srv, t_late)["status"] == B.GP_ERR_TIMEOUT
+    assert _wait(srv, t_ok)["status"] == B.GP_OK
+    assert all(_wait(srv, t)["status"] == B.GP_OK for t in long_t)
+    assert torch.equal(out, B.gp_render_slices(ctx, gs, z, 64, 64, 3.0))  # the request behind them is right
+    # a finished request cannot be cancelled, an unknown ticket is an argument error
+    with pytest.raises(B.GPError) as ei:
+        srv.cancel(t_ok)
+    assert ei.value.status == B.GP_ERR_STATE
+    with pytest.raises(B.GPError) as ei:
+        srv.cancel(10 ** 9)
+    assert ei.value.status == B.GP_ERR_ARG
+    st = srv.stats()
+    assert st["cancelled"] == 1 and st["expired"] == 1 and st["failed"] == 2 and st["pending"] == 0
+    assert st["completed"] == len(long_t) + 3
+    with pytest.raises(B.GPError) as ei:  # a negative deadline is rejected at submit
+        srv.submit(B.GP_REQ_SLICE, sid, out, z=z, H=64, W=64, sigma_z=3.0, timeout_ms=-1.0)
+    assert ei.value.status == B.GP_ERR_ARG
+    srv.close()
+
+
+def test_workspace_limit_reports_oom_and_leaves_the_context_usable():
+    """A call whose scratch would pass the context's workspace limit fails with
+    GP_ERR_OOM and frees the context's workspace; smaller calls on the same
+    context still run and are right."""
+    g = synth.small(seed=74, n=3000, extent=(96, 96, 48))
+    gs = dev_set(g)
+    z = synth.slice_positions(range(8))
+    free = B.Context(0)
+    ref = B.gp_render_slices(free, gs, z, 96, 96, 2.0)
+    need = free.workspace_bytes()
+    assert need > 0
+    ctx = B.Context(0, workspace_limit=need // 4)
+    with pytest.raises(B.GPError) as ei:
+        B.gp_render_slices(ctx, gs, z, 96, 96, 2.0)
+    assert ei.value.status == B.GP_ERR_OOM and "workspace limit" in str(ei.value)
+    assert ctx.workspace_bytes() == 0
+    small = dev_set(synth.small(seed=75, n=20, extent=(16, 16, 8)))
+    zs = synth.slice_positions(range(2))
+    got = B.gp_render_slices(ctx, small, zs, 16, 16, 2.0)
+    assert torch.equal(got, B.gp_render_slices(free, small, zs, 16, 16, 2.0))
+    big = B.Context(0, workspace_limit=4 * need)
+    assert torch.equal(B.gp_render_slices(big, gs, z, 96, 96, 2.0), ref)

@@ -61,3 +61,40 @@ def test_reference_arm_is_silent_on_other_ranks():
     p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2"],
                        env=env, capture_output=True, text=True, timeout=120)
     assert p.returncode == 0 and p.stdout.strip() == ""
+
+
+def _rank_dies_main(rank, port, out_dir):
+    import datetime
+
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=2, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)  # a rank that fails between steps, before the measurement's reduction
+    try:
+        replicas.reduce_timing(0.5, 1.0e9)
+        outcome = "returned"
+    except Exception as e:  # the survivor learns of it from the process group
+        outcome = "error " + type(e).__name__
+    with open(os.path.join(out_dir, "r0.txt"), "w") as f:
+        f.write(outcome)
+    os._exit(0)
+
+
+def test_a_dead_rank_surfaces_as_an_error_not_a_hang(tmp_path):
+    """A rank that exits before the reduction makes the other rank's reduction
+    raise within the process group's timeout instead of waiting forever."""
+    import time
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_rank_dies_main, args=(r, port, str(tmp_path))) for r in range(2)]
+    t0 = time.monotonic()
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(not p.is_alive() for p in procs)
+    assert procs[1].exitcode == 3 and procs[0].exitcode == 0
+    assert (tmp_path / "r0.txt").read_text().startswith("error")
+    assert time.monotonic() - t0 < 120
