@@ -77,19 +77,30 @@ OPS_PER_EVAL_ROW = {"fwd": 6.25, "bwd": 10.5}
 EXP_MODES = {"poly": 0, "hw": 1, "row": 3}
 
 
-def fp32_probe_peak(ctx, stream, reps=5, iters=20000):
-    """FP32 lane instructions per second of the FMA probe: best of reps launches."""
+def fp32_probe_peak(ctx, stream, reps=5, iters=20000, mode=0):
+    """Lane instructions per second of the throughput probe (mode 0: FP32 FMA,
+    3: SFU ex2): best of reps launches."""
     import torch
-    ctx.fma_probe(2000)
+    ctx.fma_probe(2000, mode=mode)
     best = 0.0
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, lanes = ctx.fma_probe(iters)
+        _, lanes = ctx.fma_probe(iters, mode=mode)
         e1.record(stream)
         e1.synchronize()
         best = max(best, lanes / (e0.elapsed_time(e1) * 1e-3))
     return best
+
+
+def sfu_roofline(sfu_peak, evals_per_launch, launch_s):
+    """The SFU side of the GP_EXP_HW variant's roofline: one ex2.approx per
+    algorithmic evaluation against the measured ex2 rate (probe mode 3)."""
+    if not sfu_peak:
+        return {}
+    achieved = evals_per_launch / launch_s / 1e12
+    return {"sfu": {"achieved": achieved, "peak": sfu_peak / 1e12, "unit": "T ex2/s",
+                    "frac": achieved * 1e12 / sfu_peak, "peak_kind": "measured ex2.approx probe, best of 5"}}
 
 
 def log(*a):
@@ -391,6 +402,7 @@ def run_native(args, rank, world):
     # the best of five probe launches, so that one launch slowed by the host or a
     # clock transition does not lower the denominator
     fp32_peak = fp32_probe_peak(ctx, stream)
+    sfu_peak = fp32_probe_peak(ctx, stream, mode=3) if args.exp == "hw" else None
 
     clocks = ClockSampler(dev_index)
     ctx.timing(True)
@@ -523,7 +535,8 @@ def run_native(args, rank, world):
                              "unit": "Tinst/s (FP32+INT lane instructions)", "frac": achieved / peak,
                              "traffic": traffic, "traffic_note": traffic_note,
                              "peak_kind": "measured FMA probe, best of 5 bursts, same run",
-                             "nominal_peak_2032mhz": nominal, "ops_per_eval": ops_table[dom]},
+                             "nominal_peak_2032mhz": nominal, "ops_per_eval": ops_table[dom],
+                             **sfu_roofline(sfu_peak, float(np.mean(ev_steps)), avg_launch_s)},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "ms_per_step": float(np.mean(e2e_ms)),
@@ -788,6 +801,7 @@ def run_ultrasound(args):
         step()
     torch.cuda.synchronize()
     fp32_peak = fp32_probe_peak(ctx, stream)
+    sfu_peak = fp32_probe_peak(ctx, stream, mode=3) if args.exp == "hw" and ops else None
     ctx.timing(True)
     ctx.timing_read()
     ms = []
@@ -815,7 +829,8 @@ def run_ultrasound(args):
         line["roofline"] = {"bound": "alu", "kernel": "k_raster_bwd", "achieved": achieved,
                             "peak": fp32_peak / 1e12, "frac": achieved / (fp32_peak / 1e12),
                             "unit": "Tinst/s (FP32+INT lane instructions)", "ops_per_eval": ops,
-                            "peak_kind": "measured FMA probe, best of 5 bursts, same run"}
+                            "peak_kind": "measured FMA probe, best of 5 bursts, same run",
+                            **sfu_roofline(sfu_peak, evals, bwd_s)}
     print(json.dumps(line), flush=True)
     return 0
 

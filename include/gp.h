@@ -504,11 +504,12 @@ GP_API int64_t gp_launch_count(void);
  * Used to measure the FP32 lane-instruction peak at the clocks in force. */
 GP_API int64_t gp_fma_probe_threads(gp_ctx* ctx);
 GP_API gp_status gp_fma_probe(gp_ctx* ctx, int iters, float* out, void* stream);
-/* The same probe in one of three instruction forms: mode 0 = 8 scalar FFMA
+/* The same probe in one of four instruction forms: mode 0 = 8 scalar FFMA
  * chains (gp_fma_probe), 1 = 8 packed fp32x2 FFMA2 chains, 2 = 4 FFMA2 + 8 FFMA
- * chains.  gp_fma_probe_lane_fmas(mode) gives the lane FMAs per thread and
- * iteration (8, 16, 16; 0 for a bad mode).  GP_ERR_ARG for a bad mode, iters
- * <= 0 or a NULL out. */
+ * chains, 3 = 8 chains of the SFU ex2.approx instruction (the SFU rate).
+ * gp_fma_probe_lane_fmas(mode) gives the lane operations per thread and
+ * iteration (8, 16, 16, 8; 0 for a bad mode).  GP_ERR_ARG for a bad mode,
+ * iters <= 0 or a NULL out. */
 GP_API gp_status gp_fma_probe_mode(gp_ctx* ctx, int mode, int iters, float* out, void* stream);
 GP_API int gp_fma_probe_lane_fmas(int mode);
 

@@ -268,8 +268,9 @@ class Context:
         return {PHASES[k]: (ms[k], ln[k], cl[k]) for k in range(GP_NUM_PHASES)}
 
     def fma_probe(self, iters, out=None, stream=None, mode=0):
-        """Launch the FP32-pipe probe; returns (out, lane FMAs it performs).
-        mode 0: scalar FFMA chains, 1: packed FFMA2 chains, 2: both mixed."""
+        """Launch the throughput probe; returns (out, lane operations it performs).
+        mode 0: scalar FFMA chains, 1: packed FFMA2 chains, 2: both mixed,
+        3: chains of the SFU ex2.approx instruction."""
         n = int(lib.gp_fma_probe_threads(self.h))
         if out is None:
             out = torch.empty(n, device=f"cuda:{self.device}")

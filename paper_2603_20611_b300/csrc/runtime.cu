@@ -705,7 +705,7 @@ int64_t gp_fma_probe_threads(gp_ctx* ctx) { return ctx ? fma_probe_threads(ctx->
 gp_status gp_fma_probe_mode(gp_ctx* ctx, int mode, int iters, float* out, void* stream) {
   if (!ctx) return GP_ERR_ARG;
   Ctx* c = &ctx->impl;
-  if (iters <= 0 || !out || mode < 0 || mode > 2) return set_err(c, GP_ERR_ARG, "bad probe arguments");
+  if (iters <= 0 || !out || mode < 0 || mode > 3) return set_err(c, GP_ERR_ARG, "bad probe arguments");
   GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   launch_fma_probe(c->sm_count, mode, iters, out, (cudaStream_t)stream);
   return cuda_err(c, cudaGetLastError(), "fma probe");
@@ -715,6 +715,6 @@ gp_status gp_fma_probe(gp_ctx* ctx, int iters, float* out, void* stream) {
   return gp_fma_probe_mode(ctx, 0, iters, out, stream);
 }
 
-int gp_fma_probe_lane_fmas(int mode) { return (mode >= 0 && mode <= 2) ? fma_probe_lane_fmas(mode) : 0; }
+int gp_fma_probe_lane_fmas(int mode) { return (mode >= 0 && mode <= 3) ? fma_probe_lane_fmas(mode) : 0; }
 
 }  // extern "C"
