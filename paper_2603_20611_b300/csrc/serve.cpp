@@ -81,8 +81,11 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 int64_t estimate_bytes(const gp_server* s, const gp_request& r) {
   const gp_set& g = s->sets[r.set_id];
   if (r.kind == GP_REQ_VOXELIZE) {
-    const int64_t tiles = (int64_t)((r.X + 7) / 8) * ((r.Y + 7) / 8) * ((r.Z + 7) / 8);
-    return g.n * 64 + tiles * 8 + g.n * 8 * 20;  // records + ranges + ~8 tiles per Gaussian of pair buffers
+    // the voxelizer bins the grid's Z planes of 16 x 16 tiles: records + tile
+    // ranges + pair buffers (20 B per pair; a Gaussian of std 1.5 voxels
+    // reaches ~16 planes and ~2 tiles on each)
+    const int64_t tiles = (int64_t)((r.X + 15) / 16) * ((r.Y + 15) / 16) * r.Z;
+    return g.n * 64 + tiles * 8 + g.n * 32 * 20;
   }
   const int64_t px = (int64_t)r.S * r.H * r.W;
   return px * 4 + g.n * 64 + g.n * 24 * 20;  // staging + records + pair buffers
