@@ -227,13 +227,19 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_scatter(
   __syncthreads();
   const uint32_t lt_mask = (1u << lane) - 1u;
   const uint32_t base = tile0 + warp * RS_PER_WARP;
-  uint32_t key[RS_ROUNDS_W], val[RS_ROUNDS_W], rank[RS_ROUNDS_W];
+  uint32_t key[RS_ROUNDS_W], rank[RS_ROUNDS_W];
+  // every key load of the thread first: the ranking rounds below are separated
+  // by __syncwarp, which would otherwise hold each round's load back until the
+  // previous round is done (the values are read only at the placement)
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS_W; ++r) {
+    const uint32_t i = base + r * 32 + lane;
+    key[r] = i < n ? kin[i] : 0u;
+  }
 #pragma unroll
   for (int r = 0; r < RS_ROUNDS_W; ++r) {
     const uint32_t i = base + r * 32 + lane;
     const bool valid = i < n;
-    key[r] = valid ? kin[i] : 0u;
-    val[r] = valid ? (vin ? vin[i] : i) : 0u;  // no input values: the identity
     const uint32_t d = valid ? ((key[r] >> shift) & 0xffu) : (RS_BINS + lane);
     // lanes holding the same digit: one ballot per digit bit (and one for
     // validity; an invalid lane's low bits are its lane number, so it is alone)
@@ -286,10 +292,11 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_scatter(
 #pragma unroll
   for (int r = 0; r < RS_ROUNDS_W; ++r) {
     if (rank[r] != 0xffffffffu) {
+      const uint32_t i = base + r * 32 + lane;
       const uint32_t d = (key[r] >> shift) & 0xffu;
       const uint32_t lp = dlocal[d] + wcnt[warp][d] + rank[r];
       skey[lp] = key[r];
-      sval[lp] = val[r];
+      sval[lp] = vin ? vin[i] : i;  // no input values: the identity
     }
   }
   __syncthreads();
