@@ -513,6 +513,20 @@ GP_API gp_status gp_fma_probe(gp_ctx* ctx, int iters, float* out, void* stream);
 GP_API gp_status gp_fma_probe_mode(gp_ctx* ctx, int mode, int iters, float* out, void* stream);
 GP_API int gp_fma_probe_lane_fmas(int mode);
 
+/* ------------------------------------------------ bounds-checked debug build
+ * The library also builds as libgaussianpile_check.so (-DGP_CHECK), in place
+ * of a memory sanitizer: its kernels check their shared- and global-memory
+ * indices, skip an out-of-range access and record the first one per source
+ * file, and gp_render_*, gp_voxelize* and gp_batch_wait then wait for their
+ * stream and return GP_ERR_STATE with the file, check site and index in
+ * gp_last_error.  gp_check_enabled() is 1 in that build and 0 in the default
+ * one.  gp_check_selftest fails one check on purpose in a kernel that touches
+ * no memory and returns what the checked build reports (GP_ERR_STATE naming
+ * site 99, index 5); in the default build it launches nothing and returns
+ * GP_ERR_STATE ("not a bounds-checked build"). */
+GP_API int gp_check_enabled(void);
+GP_API gp_status gp_check_selftest(gp_ctx* ctx, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

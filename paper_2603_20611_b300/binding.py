@@ -16,7 +16,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgaussianpile.so")
+# GP_LIBRARY=check selects the bounds-checked debug build (see build.py)
+LIB_PATH = os.path.join(_HERE, "libgaussianpile_check.so" if os.environ.get("GP_LIBRARY") == "check"
+                        else "libgaussianpile.so")
 
 GP_OK = 0
 GP_PENDING = 1
@@ -43,7 +45,7 @@ EXPORTS = (
     "gp_serve_close", "gp_view_from_axis", "gp_render_slices_view", "gp_render_backward_view",
     "gp_count_evals_view", "gp_adam_default", "gp_adam_state_floats", "gp_adam_init", "gp_adam_step",
     "gp_l1_dssim_grad", "gp_encode", "gp_decode", "gp_serve_load_encoded", "gp_count_vox_evals",
-    "gp_fma_probe_mode", "gp_fma_probe_lane_fmas",
+    "gp_fma_probe_mode", "gp_fma_probe_lane_fmas", "gp_check_enabled", "gp_check_selftest",
 )
 GP_REQ_SLICE, GP_REQ_STACK, GP_REQ_VOXELIZE = 0, 1, 2
 GP_BATCH_AUTOTUNE = 1
@@ -154,6 +156,8 @@ def _load():
         "gp_fma_probe": [P, I, P, P],
         "gp_fma_probe_mode": [P, I, I, P, P],
         "gp_fma_probe_lane_fmas": [I],
+        "gp_check_enabled": [],
+        "gp_check_selftest": [P, P],
         "gp_mse_grad_noalloc": [P, P, P, I, I, I, P, P, P],
         "gp_batch_plan": [P, ctypes.POINTER(gp_batch_item), I, I, ctypes.POINTER(P)],
         "gp_batch_run": [P, P],

@@ -513,7 +513,7 @@ gp_status gp_batch_wait(gp_plan* p, void* stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_err(p->c, e, "batch wait");
   if (*p->h_flag) return set_err(p->c, GP_ERR_OVERFLOW, "batch pairs exceeded the planned buffers; re-plan");
-  return GP_OK;
+  return check_after(p->c, (cudaStream_t)stream);
 }
 
 gp_status gp_batch_info(gp_plan* p, int64_t* pair_capacity, int* tile, int* fwd_chunk, int* bwd_chunk,

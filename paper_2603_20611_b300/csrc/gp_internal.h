@@ -108,6 +108,20 @@ struct Ctx {
 
 gp_status set_err(Ctx* c, gp_status st, const std::string& msg);
 
+// Bounds-checked build (-DGP_CHECK): the first failed index check of each
+// translation unit, read and cleared ((site << 40) | index, 0 = none), and a
+// kernel that fails one check on purpose (it touches no memory).
+#ifdef GP_CHECK
+unsigned long long check_read_raster();
+unsigned long long check_read_slice();
+unsigned long long check_read_sort();
+void launch_check_selftest(cudaStream_t st);
+#endif
+// In the bounds-checked build: waits for st and returns GP_ERR_STATE, naming
+// the file, site and index, if a kernel skipped an out-of-range access.
+// GP_OK otherwise, and always in the default build (no wait).
+gp_status check_after(Ctx* c, cudaStream_t st);
+
 // A named NVTX range on the calling host thread for the object's lifetime (a
 // no-op unless a profiler is attached), so the phases of every call show up on
 // an nsys / ncu timeline.

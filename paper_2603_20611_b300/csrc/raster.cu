@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gp_check.cuh"
 #include "gp_common.cuh"
 #include "gp_internal.h"
 #include "slice.cuh"
@@ -185,6 +186,7 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
   const int T = a.TX * a.TY;
   const int s = local_key / T, t = local_key - s * T;
   const int ty = t / a.TX, tx = t - ty * a.TX;
+  if (!GP_IN_RANGE(6, local_key, T * a.S)) return;
   const uint2 rg = ranges[a.key_base + (uint32_t)local_key];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane >> 3, row = lane & 7;
@@ -201,8 +203,10 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
     const int cnt = (int)min((uint32_t)CH, rg.y - base);
     for (int j = threadIdx.x; j < cnt; j += NT) {
       float4 a0, a1, a2;
-      sm.bmask[j] = (unsigned char)stage_blk<EXPM, TILE, 8>(rec, emit_gid[vals[base + j]], zsv, x0, y0, a.k2, a.vox != 0,
-                                                            a0, a1, a2);
+      const uint32_t g = emit_gid[vals[base + j]];
+      sm.bmask[j] = GP_IN_RANGE(5, (int64_t)g - a.gbase, a.n)
+                        ? (unsigned char)stage_blk<EXPM, TILE, 8>(rec, g, zsv, x0, y0, a.k2, a.vox != 0, a0, a1, a2)
+                        : (unsigned char)0;
       sm.s0[j] = a0;
       sm.s1[j] = a1;
       if constexpr (RF) {
@@ -220,7 +224,8 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
       const int j = jb + lane;
       const bool hit = j < cnt && ((sm.bmask[j] >> warp) & 1u);
       const unsigned msk = __ballot_sync(0xffffffffu, hit);
-      if (hit) list[nh + __popc(msk & ((1u << lane) - 1u))] = j;
+      const int at = nh + __popc(msk & ((1u << lane) - 1u));
+      if (hit && GP_IN_RANGE(4, at, CH)) list[at] = j;
       nh += __popc(msk);
     }
     __syncwarp();
@@ -339,9 +344,10 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
   constexpr int CW = CH / NW;  // Gaussians per warp chunk
   static_assert(CW * NH == CH * NH / NW && CW * NH % 32 == 0 && NH <= 8 && (NH & (NH - 1)) == 0,
                 "tile / chunk shape");
+  const int T = a.TX * a.TY;
+  if (!GP_IN_RANGE(6, local_key, T * a.S)) return;
   const uint2 rg = ranges[a.key_base + (uint32_t)local_key];
   if (rg.y <= rg.x) return;  // uniform over the CTA
-  const int T = a.TX * a.TY;
   const int s = local_key / T, t = local_key - s * T;
   const int ty = t / a.TX, tx = t - ty * a.TX;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -377,7 +383,8 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
       if (jl < cnt) {
         const uint32_t g = emit_gid[vals[base + jl]];
         float4 a0, a1, a2;
-        hm = stage_blk<EXPM, TILE, 4>(rec, g, zsv, x0, y0, a.k2, a.vox != 0, a0, a1, a2);
+        if (GP_IN_RANGE(5, (int64_t)g - a.gbase, a.n))
+          hm = stage_blk<EXPM, TILE, 4>(rec, g, zsv, x0, y0, a.k2, a.vox != 0, a0, a1, a2);
         sm.s0[j] = a0;
         sm.s1[j] = a1;
         sm.s2[j] = a2;
@@ -402,7 +409,8 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
       while (hm) {
         const int hb = __ffs(hm) - 1;
         hm &= hm - 1u;
-        units[at++] = (j << 4) | hb;
+        if (GP_IN_RANGE(1, at, CW * NH)) units[at] = (j << 4) | hb;
+        ++at;
       }
       nu += __shfl_sync(0xffffffffu, incl, 31);
     }
@@ -416,8 +424,9 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
       const bool valid = u < nu;
       const int code = valid ? units[u] : -16;  // an idle lane is its own segment, Gaussian -1
       const int jj = code >> 4, hb = code & 15;
+      const bool ok = valid && GP_IN_RANGE(2, jj - slot0, CW) && GP_IN_RANGE(3, hb, NH);
       float mom[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (valid) {
+      if (ok) {
         const float4 g0 = sm.s0[jj], g1 = sm.s1[jj];
         const float c0 = g1.x, c1 = g1.y, c2 = g1.z;
         const int hbx = ((hb >> 1) % (TILE / 8)) * 8, hby = ((hb >> 1) / (TILE / 8)) * 8 + 4 * (hb & 1);
@@ -550,7 +559,7 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
         }
       }
       const int jnext = __shfl_down_sync(0xffffffffu, jj, 1);
-      if (valid && (lane == 31 || u + 1 == nu || jnext != jj)) {
+      if (ok && (lane == 31 || u + 1 == nu || jnext != jj)) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) sm.acc[k][jj] += mom[k];
       }
@@ -818,5 +827,15 @@ int raster_batch_ctas_per_sm(int tile, int chunk, bool backward, int exp_mode) {
   }
   return n;
 }
+
+GP_CHECK_READER(check_read_raster)
+
+#ifdef GP_CHECK
+__global__ void k_check_selftest(int i, int n) {
+  if (threadIdx.x == 0) (void)GP_IN_RANGE(99, i, n);
+}
+
+void launch_check_selftest(cudaStream_t st) { k_check_selftest<<<1, 32, 0, st>>>(5, 4); }
+#endif
 
 }  // namespace gp

@@ -152,6 +152,23 @@ void ws_release(Ctx* c, DevBuf& buf) {
     if (_e != cudaSuccess) return cuda_err(c, _e, where);  \
   } while (0)
 
+gp_status check_after(Ctx* c, cudaStream_t st) {
+#ifdef GP_CHECK
+  GP_CUDA(c, cudaStreamSynchronize(st), "bounds check");
+  const char* files[] = {"raster.cu", "slice.cu", "sort.cu"};
+  const unsigned long long words[] = {check_read_raster(), check_read_slice(), check_read_sort()};
+  for (int k = 0; k < 3; ++k)
+    if (words[k])
+      return set_err(c, GP_ERR_STATE, std::string("bounds check failed in ") + files[k] + " at site " +
+                                           std::to_string(words[k] >> 40) + ", index " +
+                                           std::to_string((long long)(words[k] & ((1ull << 40) - 1ull))));
+#else
+  (void)c;
+  (void)st;
+#endif
+  return GP_OK;
+}
+
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 static gp_status check_set(Ctx* c, const gp_set* s) {
@@ -448,13 +465,15 @@ static gp_status render_impl(gp_ctx* ctx, const gp_set* set, const View& view, c
   if (S == 0) return GP_OK;
   if (P == 0) {
     GP_CUDA(c, cudaMemsetAsync(out, 0, (size_t)S * H * W * 4, st), "clear out");
-    return GP_OK;
+    return check_after(c, st);
   }
-  PhaseTimer timer(c, vox ? GP_PHASE_VOX_FWD : GP_PHASE_FWD, st);
-  GP_CUDA(c, launch_raster_fwd(a, fwd_px(c), c->cfg.exp_mode, (const SliceRec*)c->b.rec.ptr, vals,
-                               (const uint32_t*)c->b.emit_gid.ptr, (const uint2*)c->b.ranges.ptr, out, st),
-          "raster forward");
-  return GP_OK;
+  {
+    PhaseTimer timer(c, vox ? GP_PHASE_VOX_FWD : GP_PHASE_FWD, st);
+    GP_CUDA(c, launch_raster_fwd(a, fwd_px(c), c->cfg.exp_mode, (const SliceRec*)c->b.rec.ptr, vals,
+                                 (const uint32_t*)c->b.emit_gid.ptr, (const uint2*)c->b.ranges.ptr, out, st),
+            "raster forward");
+  }
+  return check_after(c, st);
 }
 
 static gp_status backward_impl(gp_ctx* ctx, const gp_set* set, const View& view, const float* z, int S, int H,
@@ -501,7 +520,8 @@ static gp_status backward_impl(gp_ctx* ctx, const gp_set* set, const View& view,
                         (const float4*)b.partial.ptr, (float*)b.accum.ptr, st);
     launch_slice_bwd_pre(a, (const float*)b.accum.ptr, d_mu, d_scale, d_quat, d_alpha, st);
   }
-  return cuda_err(c, cudaGetLastError(), "backward kernels");
+  GP_TRY(cuda_err(c, cudaGetLastError(), "backward kernels"));
+  return check_after(c, st);
 }
 
 gp_status gp_mse_grad(gp_ctx* ctx, const float* I, const float* T, const int* t_index, int S, int H, int W,
@@ -716,5 +736,27 @@ gp_status gp_fma_probe(gp_ctx* ctx, int iters, float* out, void* stream) {
 }
 
 int gp_fma_probe_lane_fmas(int mode) { return (mode >= 0 && mode <= 3) ? fma_probe_lane_fmas(mode) : 0; }
+
+int gp_check_enabled(void) {
+#ifdef GP_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+gp_status gp_check_selftest(gp_ctx* ctx, void* stream) {
+  if (!ctx) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+#ifdef GP_CHECK
+  GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  launch_check_selftest((cudaStream_t)stream);
+  GP_CUDA(c, cudaGetLastError(), "check selftest");
+  return check_after(c, (cudaStream_t)stream);
+#else
+  (void)stream;
+  return set_err(c, GP_ERR_STATE, "not a bounds-checked build");
+#endif
+}
 
 }  // extern "C"

@@ -36,6 +36,7 @@
 
 #include <algorithm>
 
+#include "gp_check.cuh"
 #include "gp_common.cuh"
 #include "gp_internal.h"
 #include "slice.cuh"
@@ -166,7 +167,8 @@ __device__ __forceinline__ void for_each_pair(const SliceArgs& a, const SliceRec
     for (int ty = b.ty0; ty <= b.ty1; ++ty) {
       int lo, hi;
       if (!row_tiles(a, r, b, ty, &lo, &hi)) continue;
-      for (int tx = lo; tx <= hi; ++tx) f(j, ty * a.TX + tx);
+      for (int tx = lo; tx <= hi; ++tx)
+        if (GP_IN_RANGE(7, tx, a.TX) && GP_IN_RANGE(8, ty, a.TY)) f(j, ty * a.TX + tx);
     }
   }
 }
@@ -442,8 +444,10 @@ __global__ void __launch_bounds__(PRE_WARPS * 32) k_slice_emit_warp(SliceArgs a,
         int lo, hi;
         if (!row_tiles(a, r, b, ty, &lo, &hi)) continue;
         for (int tx = lo; tx <= hi; ++tx) {
-          keys[e] = kb + (uint32_t)(ty * a.TX + tx);
-          emit_gid[e] = (uint32_t)i;
+          if (GP_IN_RANGE(7, tx, a.TX) && GP_IN_RANGE(8, ty, a.TY)) {
+            keys[e] = kb + (uint32_t)(ty * a.TX + tx);
+            emit_gid[e] = (uint32_t)i;
+          }
           ++e;
         }
       }
@@ -508,9 +512,12 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_slice_emit_grp(SliceArgs a, co
         if (!row_tiles(a, r, b, ty, &lo, &hi)) continue;
         for (int tx = lo; tx <= hi; ++tx) {
           const uint32_t key = kb + (uint32_t)(ty * a.TX + tx);
-          if (window) {
-            wkey[warp][e - wstart] = key;
-            wgid[warp][e - wstart] = (uint32_t)i;
+          if (!(GP_IN_RANGE(7, tx, a.TX) && GP_IN_RANGE(8, ty, a.TY))) {
+          } else if (window) {
+            if (GP_IN_RANGE(12, e - wstart, GRP_WIN)) {
+              wkey[warp][e - wstart] = key;
+              wgid[warp][e - wstart] = (uint32_t)i;
+            }
           } else {
             keys[e] = key;
             emit_gid[e] = (uint32_t)i;
@@ -590,7 +597,11 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
   for (int j = 0; j < 4; ++j) {
     const uint32_t i = i0 + (uint32_t)j;
     const uint32_t kj = k[j];
-    if (i >= n || kj >= nkeys) continue;  // kj >= nkeys cannot happen for emitted keys; keeps the store in bounds
+    if (i >= n) continue;
+    if (kj >= nkeys) {  // cannot happen for emitted keys; keeps the store in bounds
+      (void)GP_IN_RANGE(9, kj, nkeys);
+      continue;
+    }
     const uint32_t before = j == 0 ? prev : k[j - 1], after = j == 3 ? next : k[j + 1];
     if (i == 0u || before != kj) ranges[kj].x = i;
     if (i + 1u == n || after != kj) ranges[kj].y = i + 1u;
@@ -1191,5 +1202,7 @@ void launch_exp2_eval(const float* x, float* y, int64_t n, int mode, cudaStream_
   k_exp2_eval<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n, mode);
   note_launch();
 }
+
+GP_CHECK_READER(check_read_slice)
 
 }  // namespace gp

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gp_check.cuh"
 #include "gp_internal.h"
 
 namespace gp {
@@ -295,8 +296,10 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_scatter(
       const uint32_t i = base + r * 32 + lane;
       const uint32_t d = (key[r] >> shift) & 0xffu;
       const uint32_t lp = dlocal[d] + wcnt[warp][d] + rank[r];
-      skey[lp] = key[r];
-      sval[lp] = vin ? vin[i] : i;  // no input values: the identity
+      if (GP_IN_RANGE(11, lp, RS_TILE)) {
+        skey[lp] = key[r];
+        sval[lp] = vin ? vin[i] : i;  // no input values: the identity
+      }
     }
   }
   __syncthreads();
@@ -305,8 +308,10 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_scatter(
     const uint32_t k = skey[lp];
     const uint32_t d = (k >> shift) & 0xffu;
     const uint32_t pos = dglobal[d] + (lp - dlocal[d]);
-    kout[pos] = k;
-    vout[pos] = sval[lp];
+    if (GP_IN_RANGE(10, pos, n)) {
+      kout[pos] = k;
+      vout[pos] = sval[lp];
+    }
   }
 }
 
@@ -339,5 +344,7 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
   }
   return cudaGetLastError();
 }
+
+GP_CHECK_READER(check_read_sort)
 
 }  // namespace gp

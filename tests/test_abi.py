@@ -33,6 +33,18 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def test_bounds_checked_variant_exports_the_same_symbols():
+    """The -DGP_CHECK build of the same sources: same ABI, and it says which
+    build it is (the default one says 0)."""
+    path = os.path.join(os.path.dirname(b.LIB_PATH), "libgaussianpile_check.so")
+    assert os.path.exists(path), "build() makes the bounds-checked variant too"
+    chk = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(chk, name), name
+    assert chk.gp_check_enabled() == 1
+    assert ctypes.CDLL(os.path.join(os.path.dirname(b.LIB_PATH), "libgaussianpile.so")).gp_check_enabled() == 0
+
+
 def test_config_defaults():
     cfg = b.gp_config()
     assert b.lib.gp_config_default(ctypes.byref(cfg)) == b.GP_OK
