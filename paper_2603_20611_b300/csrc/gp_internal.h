@@ -16,11 +16,12 @@ template <typename T>
 cudaError_t exclusive_scan(const T* in, T* out, int64_t n, unsigned long long* total, void* temp,
                            cudaStream_t st);
 int64_t radix_temp_bytes(int64_t cap);
-// The first pass takes the identity 0..n-1 as input values (vals is not read);
-// later passes ping-pong between vals and vals_alt.
+// The first pass takes first_vals as input values, or the identity 0..n-1 when
+// it is NULL (vals is not read); later passes ping-pong between vals and
+// vals_alt.
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                              const unsigned long long* n_dev, uint32_t cap, int bits, void* temp,
-                             cudaStream_t st, bool* result_in_alt);
+                             cudaStream_t st, bool* result_in_alt, const uint32_t* first_vals = nullptr);
 
 // --------------------------------------------------------------- workspace
 // A grow-only device buffer.
@@ -93,6 +94,7 @@ struct Ctx {
   BinKey bin_key;          // what b.rec / b.ranges / the sorted values describe
   uint32_t bin_pairs = 0;
   const uint32_t* bin_vals = nullptr;
+  bool bin_gid_vals = false;  // the sorted values are Gaussian ids (else emission indices)
   char bin_args[256];      // the SliceArgs of that binning (opaque here)
   bool timing = false;
   std::vector<PhaseEvent> events;

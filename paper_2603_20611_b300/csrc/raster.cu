@@ -203,7 +203,8 @@ __device__ __forceinline__ void fwd_tile(const SliceArgs& a, int local_key, cons
     const int cnt = (int)min((uint32_t)CH, rg.y - base);
     for (int j = threadIdx.x; j < cnt; j += NT) {
       float4 a0, a1, a2;
-      const uint32_t g = emit_gid[vals[base + j]];
+      const uint32_t v = vals[base + j];
+      const uint32_t g = emit_gid ? emit_gid[v] : v;  // sorted values: emission indices, or Gaussian ids
       sm.bmask[j] = GP_IN_RANGE(5, (int64_t)g - a.gbase, a.n)
                         ? (unsigned char)stage_blk<EXPM, TILE, 8>(rec, g, zsv, x0, y0, a.k2, a.vox != 0, a0, a1, a2)
                         : (unsigned char)0;
@@ -381,7 +382,8 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
       const int j = slot0 + jl;
       unsigned hm = 0u;
       if (jl < cnt) {
-        const uint32_t g = emit_gid[vals[base + jl]];
+        const uint32_t v = vals[base + jl];
+        const uint32_t g = emit_gid ? emit_gid[v] : v;  // sorted values: emission indices, or Gaussian ids
         float4 a0, a1, a2;
         if (GP_IN_RANGE(5, (int64_t)g - a.gbase, a.n))
           hm = stage_blk<EXPM, TILE, 4>(rec, g, zsv, x0, y0, a.k2, a.vox != 0, a0, a1, a2);

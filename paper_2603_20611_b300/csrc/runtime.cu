@@ -185,15 +185,19 @@ static int tile_of(const Ctx* c) { return c->cfg.tile == 8 ? 8 : 16; }
 static int fwd_px(const Ctx* c) { return c->cfg.fwd_px; }
 static int bwd_px(const Ctx* c) { return c->cfg.bwd_px; }
 
-// Sorts the sorted keys' pairs after emission; shared tail of both binnings.
-static gp_status sort_and_range(Ctx* c, uint32_t P, int64_t nkeys, cudaStream_t st, const uint32_t** sorted_vals) {
+// Sorts the emitted (key, value) pairs and finds the tile ranges.  The values
+// are the Gaussian ids when first_vals is the emission-to-Gaussian map (the
+// rasterisers then read them directly), or the emission indices when it is
+// NULL (the deterministic backward indexes its per-pair partials by them).
+static gp_status sort_and_range(Ctx* c, uint32_t P, int64_t nkeys, cudaStream_t st, const uint32_t** sorted_vals,
+                                const uint32_t* first_vals) {
   BinBufs& b = c->b;
   int bits = 1;
   while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)nkeys) ++bits;
   bool in_alt = false;
   GP_CUDA(c, radix_sort_pairs((uint32_t*)b.keys.ptr, (uint32_t*)b.vals.ptr, (uint32_t*)b.keys_alt.ptr,
                               (uint32_t*)b.vals_alt.ptr, (const unsigned long long*)b.total.ptr, P, bits,
-                              b.sort_tmp.ptr, st, &in_alt),
+                              b.sort_tmp.ptr, st, &in_alt, first_vals),
           "radix sort");
   const uint32_t* sk = (const uint32_t*)(in_alt ? b.keys_alt.ptr : b.keys.ptr);
   *sorted_vals = (const uint32_t*)(in_alt ? b.vals_alt.ptr : b.vals.ptr);
@@ -303,7 +307,9 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
     GP_TRY(reserve_pairs(c, P));
     launch_slice_emit(A, (const SliceRec*)b.rec.ptr, (const unsigned long long*)b.offsets.ptr,
                       (const unsigned long long*)b.counts.ptr, (uint32_t*)b.keys.ptr, (uint32_t*)b.vals.ptr, (uint32_t*)b.emit_gid.ptr, st);
-    GP_TRY(sort_and_range(c, P, nkeys, st, sorted_vals));
+    c->bin_gid_vals = c->cfg.deterministic == 0;
+    GP_TRY(sort_and_range(c, P, nkeys, st, sorted_vals,
+                          c->bin_gid_vals ? (const uint32_t*)b.emit_gid.ptr : nullptr));
   }
   *pairs_out = P;
   c->last_pairs = P;
@@ -470,7 +476,8 @@ static gp_status render_impl(gp_ctx* ctx, const gp_set* set, const View& view, c
   {
     PhaseTimer timer(c, vox ? GP_PHASE_VOX_FWD : GP_PHASE_FWD, st);
     GP_CUDA(c, launch_raster_fwd(a, fwd_px(c), c->cfg.exp_mode, (const SliceRec*)c->b.rec.ptr, vals,
-                                 (const uint32_t*)c->b.emit_gid.ptr, (const uint2*)c->b.ranges.ptr, out, st),
+                                 c->bin_gid_vals ? nullptr : (const uint32_t*)c->b.emit_gid.ptr,
+                                 (const uint2*)c->b.ranges.ptr, out, st),
             "raster forward");
   }
   return check_after(c, st);
@@ -509,7 +516,8 @@ static gp_status backward_impl(gp_ctx* ctx, const gp_set* set, const View& view,
   if (P > 0) {
     PhaseTimer timer(c, vox ? GP_PHASE_VOX_BWD : GP_PHASE_BWD, st);
     GP_CUDA(c, launch_raster_bwd(a, bwd_px(c), c->cfg.exp_mode, det, (const SliceRec*)b.rec.ptr, vals,
-                                 (const uint32_t*)b.emit_gid.ptr, (const uint2*)b.ranges.ptr, dL_dI,
+                                 c->bin_gid_vals ? nullptr : (const uint32_t*)b.emit_gid.ptr,
+                                 (const uint2*)b.ranges.ptr, dL_dI,
                                  (float*)b.accum.ptr, (float4*)b.partial.ptr, st),
             "raster backward");
   }

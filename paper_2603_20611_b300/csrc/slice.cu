@@ -664,7 +664,8 @@ __global__ void __launch_bounds__(TILE* TILE / PX) k_raster_fwd(SliceArgs a, con
   for (uint32_t base = rg.x; base < rg.y; base += FWD_CHUNK) {
     const int cnt = (int)min((uint32_t)FWD_CHUNK, rg.y - base);
     for (int j = threadIdx.x; j < cnt; j += NT) {
-      uint32_t g = emit_gid[vals[base + j]];
+      const uint32_t v = vals[base + j];
+      uint32_t g = emit_gid ? emit_gid[v] : v;
       float d, w, c11;
       float4 a0, a1;
       stage_gaussian<EXPM>(rec, g, zsv, x0, y0, a0, a1, d, w, c11);
@@ -788,7 +789,8 @@ __global__ void __launch_bounds__(TILE* TILE / PX) k_raster_bwd(
   for (uint32_t base = rg.x; base < rg.y; base += CH) {
     const int cnt = (int)min((uint32_t)CH, rg.y - base);
     for (int j = threadIdx.x; j < cnt; j += NT) {
-      uint32_t g = emit_gid[vals[base + j]];
+      const uint32_t v = vals[base + j];
+      uint32_t g = emit_gid ? emit_gid[v] : v;
       float d, w, c11;
       float4 a0, a1;
       stage_gaussian<EXPM>(rec, g, zsv, x0, y0, a0, a1, d, w, c11);

@@ -323,7 +323,7 @@ int64_t radix_temp_bytes(int64_t cap) {
 
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                              const unsigned long long* n_dev, uint32_t cap, int bits, void* temp,
-                             cudaStream_t st, bool* result_in_alt) {
+                             cudaStream_t st, bool* result_in_alt, const uint32_t* first_vals) {
   *result_in_alt = false;
   if (cap == 0 || bits <= 0) return cudaSuccess;
   if ((((uintptr_t)keys) | ((uintptr_t)keys_alt)) & 15u) return cudaErrorMisalignedAddress;
@@ -336,7 +336,7 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
     k_radix_hist<<<nb, RS_THREADS, 0, st>>>(ki, n_dev, cap, shift, hist, nb);
     cudaError_t e = exclusive_scan<uint32_t>(hist, hist, nh, nullptr, stemp, st);
     if (e != cudaSuccess) return e;
-    k_radix_scatter<<<nb, RS_THREADS, 0, st>>>(ki, shift == 0 ? nullptr : vi, ko, vo, n_dev, cap, shift, hist, nb);
+    k_radix_scatter<<<nb, RS_THREADS, 0, st>>>(ki, shift == 0 ? first_vals : vi, ko, vo, n_dev, cap, shift, hist, nb);
     note_launch(2);
     uint32_t* tk = ki; ki = ko; ko = tk;
     uint32_t* tv = vi; vi = vo; vo = tv;
