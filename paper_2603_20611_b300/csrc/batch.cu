@@ -185,8 +185,10 @@ static gp_status enqueue_binning(gp_plan* p, cudaStream_t st) {
   int bits = 1;
   while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)p->n_keys) ++bits;
   bool in_alt = false;
+  // values: Gaussian ids (read directly by the rasterisers), or the emission
+  // indices by which the deterministic backward addresses its partials
   GP_CUDAB(p, radix_sort_pairs(p->keys, p->vals, p->keys_alt, p->vals_alt, p->total, p->cap, bits, p->sort_tmp, st,
-                               &in_alt),
+                               &in_alt, p->det ? nullptr : p->emit_gid),
            "batch sort");
   p->sk = in_alt ? p->keys_alt : p->keys;
   p->sv = in_alt ? p->vals_alt : p->vals;
@@ -203,7 +205,7 @@ static gp_status enqueue_forward(gp_plan* p, cudaStream_t st) {
   }
   GP_CUDAB(p, cudaMemsetAsync(p->work, 0, sizeof(unsigned), st), "memset work");
   GP_CUDAB(p, launch_raster_fwd_batch(batch_view(p), p->tile, p->fchunk, p->ctas_f, p->c->cfg.exp_mode, p->rec, p->sv,
-                                      p->emit_gid, p->ranges, p->work, st),
+                                      p->det ? p->emit_gid : nullptr, p->ranges, p->work, st),
            "batch forward");
   return GP_OK;
 }
@@ -226,7 +228,7 @@ static gp_status enqueue_backward(gp_plan* p, cudaStream_t st) {
   if (p->cap > 0) {
     GP_CUDAB(p, cudaMemsetAsync(p->work + 1, 0, sizeof(unsigned), st), "memset work");
     GP_CUDAB(p, launch_raster_bwd_batch(b, p->tile, p->bchunk, p->ctas_b, p->c->cfg.exp_mode, p->det, p->rec, p->sv,
-                                        p->emit_gid, p->ranges, p->accum, p->partial, p->work + 1, st),
+                                        p->det ? p->emit_gid : nullptr, p->ranges, p->accum, p->partial, p->work + 1, st),
              "batch backward");
   }
   if (p->det) launch_det_reduce_n(p->n_gauss, p->offsets, p->counts, p->partial, p->accum, p->cap, st);
