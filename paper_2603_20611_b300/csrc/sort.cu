@@ -4,7 +4,9 @@
 // The renderer's binning (the "binned to screen tiles" step of the operator)
 // needs the Gaussians of every (slice, tile) contiguous and, inside a tile, in
 // ascending emission (= Gaussian id) order so that sums are reproducible.  Keys
-// are emitted in that order, so a STABLE sort on the key alone suffices.
+// are emitted in that order, so a STABLE sort on the key alone suffices.  The
+// values carried along are the identity (emission indices) or the caller's
+// first-pass values (the Gaussian ids).
 //
 // Radix sort, per 8-bit digit pass:
 //   1. k_radix_hist     per 4096-key tile: 256-bin histogram (shared atomics),
@@ -203,7 +205,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __res
 // Stable scatter of one 4096-key tile.  Warp w owns the tile's keys
 // [w * 512, (w + 1) * 512) and ranks them in 16 rounds of 32 against its own
 // per-digit counters (nine ballots give the rank among equal digits in a round),
-// keeping key, value and rank in registers.  A block-wide pass turns the
+// keeping key and rank in registers (the value is read at the placement).  A
+// block-wide pass turns the
 // per-warp counts into tile-local digit offsets; the keys are first placed in
 // shared memory in digit order (a stable local sort), and then written out in
 // that order, so each digit's run leaves the block as contiguous stores.
