@@ -607,8 +607,8 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
 }
 
 // ------------------------------------------------------------ plain kernels
-template <int TILE, int CH, int EXPM>
-__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? 12 : 32) k_raster_fwd_blk(
+template <int TILE, int CH, int EXPM, bool DENSE>
+__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? (DENSE ? 8 : 12) : 32) k_raster_fwd_blk(
     SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges) {
   __shared__ FwdSmem<TILE, CH, row_factored<EXPM>()> sm;
@@ -616,7 +616,7 @@ __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? 12 
 }
 
 template <int TILE, int CH, int EXPM, bool DET>
-__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? (row_factored<EXPM>() ? 9 : 10) : 32)
+__global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? 9 : 32)
     k_raster_bwd_blk(SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
                      const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges,
                      float* __restrict__ accum, float4* __restrict__ partial) {
@@ -688,28 +688,34 @@ __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? (ro
 }
 
 // ------------------------------------------------------------ launchers
-template <int TILE, int CH>
+template <int TILE, int CH, bool DENSE>
 static cudaError_t fwd_blk(const SliceArgs& a, int exp_mode, const SliceRec* rec, const uint32_t* vals,
                            const uint32_t* emit_gid, const uint2* ranges, cudaStream_t st) {
   const int64_t tiles = (int64_t)a.S * a.TX * a.TY;
   constexpr int NT = (TILE / 8) * (TILE / 8) * 32;
   if (exp_mode == GP_EXP_HW)
-    k_raster_fwd_blk<TILE, CH, GP_EXP_HW><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges);
+    k_raster_fwd_blk<TILE, CH, GP_EXP_HW, DENSE><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges);
   else if (exp_mode == GP_EXP_POLY_ROW)
-    k_raster_fwd_blk<TILE, CH, GP_EXP_POLY_ROW><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges);
+    k_raster_fwd_blk<TILE, CH, GP_EXP_POLY_ROW, DENSE><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges);
   else
-    k_raster_fwd_blk<TILE, CH, GP_EXP_POLY><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges);
+    k_raster_fwd_blk<TILE, CH, GP_EXP_POLY, DENSE><<<(unsigned)tiles, NT, 0, st>>>(a, rec, vals, emit_gid, ranges);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_raster_fwd_blocked(const SliceArgs& a, int exp_mode, const SliceRec* rec, const uint32_t* vals,
-                                      const uint32_t* emit_gid, const uint2* ranges, float* out, cudaStream_t st) {
-  if ((int64_t)a.S * a.TX * a.TY == 0) return cudaSuccess;
+                                      const uint32_t* emit_gid, const uint2* ranges, float* out, cudaStream_t st,
+                                      uint32_t pairs) {
+  const int64_t tiles = (int64_t)a.S * a.TX * a.TY;
+  if (tiles == 0) return cudaSuccess;
   SliceArgs b = a;
   b.out = out;
-  if (a.tile == 16) return fwd_blk<16, 128>(b, exp_mode, rec, vals, emit_gid, ranges, st);
-  if (a.tile == 8) return fwd_blk<8, 64>(b, exp_mode, rec, vals, emit_gid, ranges, st);
+  if (a.tile == 16) {
+    if ((int64_t)pairs >= (int64_t)kDenseTilePairs * tiles)
+      return fwd_blk<16, 128, true>(b, exp_mode, rec, vals, emit_gid, ranges, st);
+    return fwd_blk<16, 128, false>(b, exp_mode, rec, vals, emit_gid, ranges, st);
+  }
+  if (a.tile == 8) return fwd_blk<8, 64, false>(b, exp_mode, rec, vals, emit_gid, ranges, st);
   return cudaErrorInvalidValue;
 }
 

@@ -477,7 +477,7 @@ static gp_status render_impl(gp_ctx* ctx, const gp_set* set, const View& view, c
     PhaseTimer timer(c, vox ? GP_PHASE_VOX_FWD : GP_PHASE_FWD, st);
     GP_CUDA(c, launch_raster_fwd(a, fwd_px(c), c->cfg.exp_mode, (const SliceRec*)c->b.rec.ptr, vals,
                                  c->bin_gid_vals ? nullptr : (const uint32_t*)c->b.emit_gid.ptr,
-                                 (const uint2*)c->b.ranges.ptr, out, st),
+                                 (const uint2*)c->b.ranges.ptr, out, st, P),
             "raster forward");
   }
   return check_after(c, st);

@@ -718,8 +718,8 @@ bool fwd_px_supported(int tile, int px) {
 
 cudaError_t launch_raster_fwd(const SliceArgs& a, int px, int exp_mode, const SliceRec* rec,
                               const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
-                              float* out, cudaStream_t st) {
-  if (px == 0) return launch_raster_fwd_blocked(a, exp_mode, rec, vals, emit_gid, ranges, out, st);
+                              float* out, cudaStream_t st, uint32_t pairs) {
+  if (px == 0) return launch_raster_fwd_blocked(a, exp_mode, rec, vals, emit_gid, ranges, out, st, pairs);
   if (a.tile == 16) {
     switch (px) {
       case 1: return fwd_dispatch<16, 1>(a, exp_mode, rec, vals, emit_gid, ranges, out, st);

@@ -76,9 +76,11 @@ void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned l
 void launch_ranges(const uint32_t* keys, const unsigned long long* n_dev, uint32_t cap, uint32_t nkeys,
                    uint2* ranges, cudaStream_t st);
 // K-fwd.
+// pairs: the binned (Gaussian, slice, tile) pairs, which choose the occupancy
+// of the default forward (see launch_raster_fwd_blocked).
 cudaError_t launch_raster_fwd(const SliceArgs& a, int px, int exp_mode, const SliceRec* rec,
                               const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
-                              float* out, cudaStream_t st);
+                              float* out, cudaStream_t st, uint32_t pairs);
 // K-bwd-raster; atomic mode adds into accum [n][10] (zeroed), deterministic mode
 // writes per-pair partials [pairs][8].
 cudaError_t launch_raster_bwd(const SliceArgs& a, int px, int exp_mode, bool deterministic,
@@ -100,9 +102,14 @@ void launch_count_evals(const SliceArgs& a, const SliceRec* rec, unsigned long l
                         cudaStream_t st);
 void launch_exp2_eval(const float* x, float* y, int64_t n, int mode, cudaStream_t st);
 
-// Block-culled rasterisers (raster.cu), the default for 16 x 16 tiles.
+// Block-culled rasterisers (raster.cu), the default for 16 x 16 tiles.  The
+// forward runs at 8 CTAs per SM (more registers, more exponentials in flight)
+// when the tiles hold kDenseTilePairs or more pairs on average, else at 12
+// (sparse tiles, as on voxelizer planes, are latency-bound).
+constexpr uint32_t kDenseTilePairs = 48;
 cudaError_t launch_raster_fwd_blocked(const SliceArgs& a, int exp_mode, const SliceRec* rec, const uint32_t* vals,
-                                      const uint32_t* emit_gid, const uint2* ranges, float* out, cudaStream_t st);
+                                      const uint32_t* emit_gid, const uint2* ranges, float* out, cudaStream_t st,
+                                      uint32_t pairs);
 cudaError_t launch_raster_bwd_blocked(const SliceArgs& a, int exp_mode, bool det, const SliceRec* rec,
                                       const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
                                       const float* dL_dI, float* accum, float4* partial, cudaStream_t st);
