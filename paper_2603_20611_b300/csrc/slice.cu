@@ -43,7 +43,7 @@
 
 namespace gp {
 
-constexpr int PRE_THREADS = 256;
+constexpr int PRE_THREADS = 128;
 constexpr int kPairGroup = 4;  // lanes per Gaussian of the grouped K-pre / K-emit
 
 // Calls whose Gaussians each reach tens of planes (the host sets warp_pairs)
