@@ -28,6 +28,11 @@
 // mode).
 // GP_EXP_POLY_ROW factors the exponential along each row (two exp2 per 8
 // pixels, see row_powers) in both kernels.
+// The sorted list values are Gaussian ids (emit_gid == nullptr) or, in the
+// deterministic mode, emission indices mapped through emit_gid.  The forward is
+// built twice, for 8 CTAs per SM on dense tiles (more registers, more
+// exponentials in flight) and 12 on sparse ones; the launcher picks by the
+// mean number of pairs per tile.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
