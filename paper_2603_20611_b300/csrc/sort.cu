@@ -205,15 +205,14 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __res
 // Stable scatter of one 4096-key tile.  Warp w owns the tile's keys
 // [w * 512, (w + 1) * 512) and ranks them in 16 rounds of 32 against its own
 // per-digit counters (nine ballots give the rank among equal digits in a round),
-// keeping key and rank in registers (the value is read at the placement).  A
-// block-wide pass turns the
+// keeping key, value and rank in registers.  A block-wide pass turns the
 // per-warp counts into tile-local digit offsets; the keys are first placed in
 // shared memory in digit order (a stable local sort), and then written out in
 // that order, so each digit's run leaves the block as contiguous stores.
 constexpr int RS_PER_WARP = RS_TILE / RS_WARPS;     // 512 keys
 constexpr int RS_ROUNDS_W = RS_PER_WARP / 32;       // 16 rounds
 
-__global__ void __launch_bounds__(RS_THREADS, 4) k_radix_scatter(
+__global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const unsigned long long* __restrict__ n_dev, uint32_t cap, int shift,
     const uint32_t* __restrict__ hist, int nb) {
@@ -231,14 +230,16 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_scatter(
   __syncthreads();
   const uint32_t lt_mask = (1u << lane) - 1u;
   const uint32_t base = tile0 + warp * RS_PER_WARP;
-  uint32_t key[RS_ROUNDS_W], rank[RS_ROUNDS_W];
-  // every key load of the thread first: the ranking rounds below are separated
-  // by __syncwarp, which would otherwise hold each round's load back until the
-  // previous round is done (the values are read only at the placement)
+  uint32_t key[RS_ROUNDS_W], val[RS_ROUNDS_W], rank[RS_ROUNDS_W];
+  // every load of the thread first (keys and values, held in registers: 3 CTAs
+  // per SM with 80 registers beat 4 with the values read at the placement): the
+  // ranking rounds below are separated by __syncwarp, which would otherwise
+  // hold each round's load back until the previous round is done
 #pragma unroll
   for (int r = 0; r < RS_ROUNDS_W; ++r) {
     const uint32_t i = base + r * 32 + lane;
     key[r] = i < n ? kin[i] : 0u;
+    val[r] = i < n ? (vin ? vin[i] : i) : 0u;  // no input values: the identity
   }
 #pragma unroll
   for (int r = 0; r < RS_ROUNDS_W; ++r) {
@@ -296,12 +297,11 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_scatter(
 #pragma unroll
   for (int r = 0; r < RS_ROUNDS_W; ++r) {
     if (rank[r] != 0xffffffffu) {
-      const uint32_t i = base + r * 32 + lane;
       const uint32_t d = (key[r] >> shift) & 0xffu;
       const uint32_t lp = dlocal[d] + wcnt[warp][d] + rank[r];
       if (GP_IN_RANGE(11, lp, RS_TILE)) {
         skey[lp] = key[r];
-        sval[lp] = vin ? vin[i] : i;  // no input values: the identity
+        sval[lp] = val[r];
       }
     }
   }
