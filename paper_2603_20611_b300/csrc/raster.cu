@@ -171,6 +171,27 @@ __device__ __forceinline__ RowPowers row_powers(float A, float aB, bool scale_by
   return w;
 }
 
+// The backward's powers of one row in mirrored couples: L, (r^0, r^1),
+// (r^2, r^3) for the distances 0..3 from the row's larger end, and (r^7, r^6),
+// (r^5, r^4) for their mirrors 7..4.
+struct RowCouplePowers {
+  float L;
+  float2 p01, p23, p76, p54;
+};
+
+__device__ __forceinline__ RowCouplePowers row_couple_powers(float A, float aB) {
+  const float2 ex = exp2_poly2(make_float2(fmaxf(fmaf(3.5f, aB, A), kExpFloor), fmaxf(-aB, kExpFloor)));
+  const float r = ex.y, r2 = r * r, r3 = r2 * r, r4 = r2 * r2;
+  const float2 r32 = make_float2(r3, r2);
+  RowCouplePowers w;
+  w.L = ex.x;
+  w.p01 = make_float2(1.0f, r);
+  w.p23 = make_float2(r2, r3);
+  w.p54 = __fmul2_rn(make_float2(r2, r2), r32);
+  w.p76 = __fmul2_rn(make_float2(r4, r4), r32);
+  return w;
+}
+
 // Shared memory of the forward body.
 template <int TILE, int CH, bool RF = false>
 struct FwdSmem {
@@ -317,7 +338,7 @@ struct BwdSmem {
   static constexpr int NH = 2 * NW;  // 8 x 4 half-blocks per tile
   static constexpr int HBS = 36;     // floats per half-block (32 + 4 of padding)
   float4 s0[CH], s1[CH], s2[CH];
-  float4 fa[RF ? CH : 1], fb[RF ? CH : 1];  // row factorisation: 2^(C q^2) per pixel column
+  float4 fa[RF ? CH : 1];  // row factorisation: 2^(C q^2), |q| = 3.5, 2.5, 1.5, 0.5
   uint32_t sg[CH];
   alignas(16) float G[NH * HBS];
   alignas(16) float Grev[RF ? NH * HBS : 4];  // row factorisation: G with each row of 8 reversed
@@ -401,8 +422,7 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
         if constexpr (RF) {
           float4 fa, fb;
           row_quad_factors(a1.x, 1.0f, fa, fb);
-          sm.fa[j] = fa;
-          sm.fb[j] = fb;
+          sm.fa[j] = fa;  // the couples use 2^(C q^2) in the order |q| = 3.5, 2.5, 1.5, 0.5 only
         }
       }
       const int c = __popc(hm);
@@ -447,34 +467,41 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
         float M00 = 0.f, M10 = 0.f, M20 = 0.f, M01 = 0.f, M11 = 0.f, M02 = 0.f;
         const float* Gr = sm.G + hb * HBS;
         if (RF && c0 >= kRowMinC) {
-          // rows in the factored form, summed over j (the distance from the row's
-          // larger end): the pixel of j has q = j - 3.5 when B < 0 and 3.5 - j
-          // when B >= 0, whose dL/dI the reversed copy of the tile supplies
-          const float4 fa = sm.fa[jj], fb = sm.fb[jj];
-          const float2 F01 = make_float2(fa.x, fa.y), F23 = make_float2(fa.z, fa.w);
-          const float2 F45 = make_float2(fb.x, fb.y), F67 = make_float2(fb.z, fb.w);
+          // rows in the factored form, over j (the distance from the row's
+          // larger end), in mirrored couples (j, 7 - j): the pixel of j has
+          // q = j - 3.5 when B < 0 and 3.5 - j when B >= 0, so in that frame a
+          // couple is (q, -q) as in the per-pixel form below.  The near half
+          // (j = 0..3) comes from the tile's dL/dI in the row's order, the far
+          // half (j = 7..4) from the reversed copy, or the other way round.
+          const float4 fa = sm.fa[jj];
+          const float2 F0 = make_float2(fa.x, fa.y), F1 = make_float2(fa.z, fa.w);  // 2^(C q^2), |q| = 3.5, 2.5 / 1.5, 0.5
           const float* Grv = sm.Grev + hb * HBS;
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
             const float rf = (float)r;
             const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
             const float B = fmaf(c1, rf, B0);
-            const RowPowers w = row_powers(A, fabsf(B), false);
+            const RowCouplePowers w = row_couple_powers(A, fabsf(B));
             const bool rev = B >= 0.0f;
-            const float* Gj = (rev ? Grv : Gr) + r * 8;
-            const float4 ga = *reinterpret_cast<const float4*>(Gj);
-            const float4 gb = *reinterpret_cast<const float4*>(Gj + 4);
-            const float2 gE[4] = {__fmul2_rn(make_float2(ga.x, ga.y), __fmul2_rn(w.p01, F01)),
-                                  __fmul2_rn(make_float2(ga.z, ga.w), __fmul2_rn(w.p23, F23)),
-                                  __fmul2_rn(make_float2(gb.x, gb.y), __fmul2_rn(w.p45, F45)),
-                                  __fmul2_rn(make_float2(gb.z, gb.w), __fmul2_rn(w.p67, F67))};
-            float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              const float qa = (float)(2 * p) - 3.5f, qb = (float)(2 * p + 1) - 3.5f;
-              P0 = __fadd2_rn(P0, gE[p]);
-              P1 = __ffma2_rn(make_float2(qa, qb), gE[p], P1);
-              P2 = __ffma2_rn(make_float2(qa * qa, qb * qb), gE[p], P2);
+            const float4 gn = *reinterpret_cast<const float4*>((rev ? Grv : Gr) + r * 8);  // j = 0, 1, 2, 3
+            const float4 gf = *reinterpret_cast<const float4*>((rev ? Gr : Grv) + r * 8);  // j = 7, 6, 5, 4
+            // sum G E = X + Y, sum q G E = q (X + Y) - 2 q Y, sum q^2 G E = q^2 (X + Y)
+            // couple 0: j = (0, 1) with (7, 6), q = (-3.5, -2.5)
+            float2 P0, P1, P2;
+            {
+              const float2 Y = __fmul2_rn(make_float2(gf.x, gf.y), __fmul2_rn(w.p76, F0));
+              const float2 XY = __ffma2_rn(make_float2(gn.x, gn.y), __fmul2_rn(w.p01, F0), Y);
+              P0 = XY;
+              P1 = __ffma2_rn(make_float2(7.0f, 5.0f), Y, __fmul2_rn(make_float2(-3.5f, -2.5f), XY));
+              P2 = __fmul2_rn(make_float2(12.25f, 6.25f), XY);
+            }
+            // couple 1: j = (2, 3) with (5, 4), q = (-1.5, -0.5)
+            {
+              const float2 Y = __fmul2_rn(make_float2(gf.z, gf.w), __fmul2_rn(w.p54, F1));
+              const float2 XY = __ffma2_rn(make_float2(gn.z, gn.w), __fmul2_rn(w.p23, F1), Y);
+              P0 = __fadd2_rn(P0, XY);
+              P1 = __ffma2_rn(make_float2(3.0f, 1.0f), Y, __ffma2_rn(make_float2(-1.5f, -0.5f), XY, P1));
+              P2 = __ffma2_rn(make_float2(2.25f, 0.25f), XY, P2);
             }
             const float S0 = w.L * (P0.x + P0.y);
             const float S1 = (rev ? -w.L : w.L) * (P1.x + P1.y);
