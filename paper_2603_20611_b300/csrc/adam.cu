@@ -30,15 +30,16 @@ struct AdamStep {
   int act;          // log-scale / logit-alpha parameterisation
 };
 
-__device__ __forceinline__ float adam_one(float theta, float g, float* __restrict__ m, float* __restrict__ v,
-                                          const AdamStep& p, float lr) {
-  const float mm = fmaf(p.b1, *m, (1.0f - p.b1) * g);
-  const float vv = fmaf(p.b2, *v, (1.0f - p.b2) * g * g);
-  *m = mm;
-  *v = vv;
-  return theta - lr * (mm * p.inv_bc1) / fmaf(sqrtf(vv), p.inv_sbc2, p.eps);
+// One Adam update of parameter theta with gradient g; m and v in, updated.
+__device__ __forceinline__ float adam_one(float theta, float g, float& m, float& v, const AdamStep& p, float lr) {
+  m = fmaf(p.b1, m, (1.0f - p.b1) * g);
+  v = fmaf(p.b2, v, (1.0f - p.b2) * g * g);
+  return theta - lr * (m * p.inv_bc1) / fmaf(sqrtf(v), p.inv_sbc2, p.eps);
 }
 
+// Every load of a Gaussian first, then the updates, then every store: the 26
+// state rows share one base pointer, so stores to one row would otherwise hold
+// back the loads of the next.
 __global__ void __launch_bounds__(kAdamThreads) k_adam(AdamStep p, int64_t n, float* __restrict__ mu,
                                                       float* __restrict__ scale, float* __restrict__ quat,
                                                       float* __restrict__ alpha, const float* __restrict__ d_mu,
@@ -47,52 +48,69 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam(AdamStep p, int64_t n, fl
                                                       const float* __restrict__ d_alpha, float* __restrict__ st) {
   const int64_t i = (int64_t)blockIdx.x * kAdamThreads + threadIdx.x;
   if (i >= n) return;
-  float* M = st;            // rows 0..10
-  float* V = st + 11 * n;   // rows 11..21
-  float* RAW = st + 22 * n; // rows 22..25
-  // positions
+  // parameters and gradients in the order mu xyz, scale xyz, quat wxyz, alpha
+  float th[11], g[11], m[11], v[11], raw[4];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    float* x = mu + 3 * i + k;
-    *x = adam_one(*x, d_mu[3 * i + k], M + k * n + i, V + k * n + i, p, p.lr[0]);
+    th[k] = mu[3 * i + k];
+    g[k] = d_mu[3 * i + k];
+    th[3 + k] = scale[3 * i + k];
+    g[3 + k] = d_scale[3 * i + k];
   }
+  const float4 q = reinterpret_cast<const float4*>(quat)[i];
+  const float4 gq = reinterpret_cast<const float4*>(d_quat)[i];
+  th[6] = q.x; th[7] = q.y; th[8] = q.z; th[9] = q.w;
+  g[6] = gq.x; g[7] = gq.y; g[8] = gq.z; g[9] = gq.w;
+  th[10] = alpha[i];
+  g[10] = d_alpha[i];
+#pragma unroll
+  for (int k = 0; k < 11; ++k) {
+    m[k] = st[(int64_t)k * n + i];          // rows 0..10
+    v[k] = st[(int64_t)(11 + k) * n + i];   // rows 11..21
+  }
+  if (p.act) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) raw[k] = st[(int64_t)(22 + k) * n + i];  // raw log s xyz, raw logit alpha
+  }
+  // positions
+#pragma unroll
+  for (int k = 0; k < 3; ++k) th[k] = adam_one(th[k], g[k], m[k], v[k], p, p.lr[0]);
   // scales: raw log s (gradient through s = exp(raw)) or linear s
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const int r = 3 + k;
-    const float s = scale[3 * i + k];
-    const float g = d_scale[3 * i + k];
     if (p.act) {
-      float* raw = RAW + k * n + i;
-      const float nr = adam_one(*raw, g * s, M + r * n + i, V + r * n + i, p, p.lr[1]);
-      *raw = nr;
-      scale[3 * i + k] = expf(nr);
+      raw[k] = adam_one(raw[k], g[3 + k] * th[3 + k], m[3 + k], v[3 + k], p, p.lr[1]);
+      th[3 + k] = expf(raw[k]);
     } else {
-      scale[3 * i + k] = adam_one(s, g, M + r * n + i, V + r * n + i, p, p.lr[1]);
+      th[3 + k] = adam_one(th[3 + k], g[3 + k], m[3 + k], v[3 + k], p, p.lr[1]);
     }
   }
   // quaternion (normalised inside the renderer, optimised as it is)
-  {
-    float4 q = reinterpret_cast<float4*>(quat)[i];
-    const float4 gq = reinterpret_cast<const float4*>(d_quat)[i];
-    q.x = adam_one(q.x, gq.x, M + 6 * n + i, V + 6 * n + i, p, p.lr[2]);
-    q.y = adam_one(q.y, gq.y, M + 7 * n + i, V + 7 * n + i, p, p.lr[2]);
-    q.z = adam_one(q.z, gq.z, M + 8 * n + i, V + 8 * n + i, p, p.lr[2]);
-    q.w = adam_one(q.w, gq.w, M + 9 * n + i, V + 9 * n + i, p, p.lr[2]);
-    reinterpret_cast<float4*>(quat)[i] = q;
-  }
+#pragma unroll
+  for (int k = 6; k < 10; ++k) th[k] = adam_one(th[k], g[k], m[k], v[k], p, p.lr[2]);
   // intensity: raw logit (gradient through a = sigmoid(raw)) or linear
-  {
-    const float a = alpha[i];
-    const float g = d_alpha[i];
-    if (p.act) {
-      float* raw = RAW + 3 * n + i;
-      const float nr = adam_one(*raw, g * a * (1.0f - a), M + 10 * n + i, V + 10 * n + i, p, p.lr[3]);
-      *raw = nr;
-      alpha[i] = 1.0f / (1.0f + expf(-nr));
-    } else {
-      alpha[i] = adam_one(a, g, M + 10 * n + i, V + 10 * n + i, p, p.lr[3]);
-    }
+  if (p.act) {
+    const float a = th[10];
+    raw[3] = adam_one(raw[3], g[10] * a * (1.0f - a), m[10], v[10], p, p.lr[3]);
+    th[10] = 1.0f / (1.0f + expf(-raw[3]));
+  } else {
+    th[10] = adam_one(th[10], g[10], m[10], v[10], p, p.lr[3]);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    mu[3 * i + k] = th[k];
+    scale[3 * i + k] = th[3 + k];
+  }
+  reinterpret_cast<float4*>(quat)[i] = make_float4(th[6], th[7], th[8], th[9]);
+  alpha[i] = th[10];
+#pragma unroll
+  for (int k = 0; k < 11; ++k) {
+    st[(int64_t)k * n + i] = m[k];
+    st[(int64_t)(11 + k) * n + i] = v[k];
+  }
+  if (p.act) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) st[(int64_t)(22 + k) * n + i] = raw[k];
   }
 }
 
