@@ -227,8 +227,9 @@ GP_API gp_status gp_l1_dssim_grad(gp_ctx* ctx, const float* I, const float* T, c
  * address cannot be obtained.
  *
  * The first call on a device looks up the scratch's device address with
- * cudaGetSymbolAddress (once per device, thread-safe); make that first call
- * before any stream capture.  Every call shares the one array, and each call
+ * cudaGetSymbolAddress (once per device, thread-safe; a failed lookup returns
+ * GP_ERR_CUDA and is not remembered, so the next call tries again); make that
+ * first call before any stream capture.  Every call shares the one array, and each call
  * overwrites what it reads, so nothing carries over between calls; but calls
  * whose work overlaps on the GPU (different streams, or different host threads
  * without ordering) race on it and must be serialised by the caller. */
@@ -369,8 +370,13 @@ GP_API gp_status gp_decode(gp_ctx* ctx, const gp_codec_header* header, const uin
  * worker taking a slice/stack request also takes every pending request for the
  * same set, view, image size and sigma_z (up to max_batch_slices planes) and
  * renders them in one call; results are bitwise the same alone and in a batch.
+ * A worker taking a voxelize request also takes every pending voxelize request
+ * for the same set and grid (up to max_batch_slices requests): they ask for the
+ * same volume, which it voxelizes once and copies to each output.
  * Outputs are caller-owned device buffers that must stay valid until the
- * request completes.  submit / poll / stats may be called from any thread. */
+ * request completes.  submit / poll / stats / load may be called from any
+ * thread; a request keeps a copy of its set's descriptor from its submit, so
+ * sets may be registered while requests run. */
 #define GP_REQ_SLICE 0     /* one plane: S must be 1 */
 #define GP_REQ_STACK 1     /* S planes */
 #define GP_REQ_VOXELIZE 2  /* X x Y x Z volume */

@@ -11,7 +11,13 @@
 // staging stack, then copies each request's planes to that request's output.
 // Every (plane, tile) list and every tile's summation order depend only on the
 // set and the plane, so a request's result is bitwise the same alone and in a
-// batch.  Voxelize requests run one at a time per worker.
+// batch.  Pending voxelize requests for the same set and grid ask for the same
+// volume: a worker takes them together, voxelizes once and copies the volume to
+// each of their outputs.
+//
+// A request carries its own copy of the set's descriptor (pointers, count,
+// scale modifier), taken under the lock when it is submitted, so a worker never
+// reads the server's set table, which a concurrent load may grow.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -36,6 +42,7 @@ using Clock = std::chrono::steady_clock;
 struct Request {
   uint64_t ticket;
   gp_request r;
+  gp_set set{};          // the set's descriptor as registered (a copy)
   std::vector<float> z;  // copy of the plane positions
   gp::View view{};       // slice orientation (the request's view, or its axis's)
   Clock::time_point submitted;
@@ -78,8 +85,7 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 
 // Device bytes a request may add while it runs (workspace and staging), a
 // conservative estimate used for admission.
-int64_t estimate_bytes(const gp_server* s, const gp_request& r) {
-  const gp_set& g = s->sets[r.set_id];
+int64_t estimate_bytes(const gp_set& g, const gp_request& r) {
   if (r.kind == GP_REQ_VOXELIZE) {
     // the voxelizer bins the grid's Z planes of 16 x 16 tiles: records + tile
     // ranges + pair buffers (20 B per pair; a Gaussian of std 1.5 voxels
@@ -93,6 +99,8 @@ int64_t estimate_bytes(const gp_server* s, const gp_request& r) {
 
 bool same_batch(const Request& qa, const Request& qb) {
   const gp_request &a = qa.r, &b = qb.r;
+  if (a.kind == GP_REQ_VOXELIZE || b.kind == GP_REQ_VOXELIZE)
+    return a.kind == b.kind && a.set_id == b.set_id && a.X == b.X && a.Y == b.Y && a.Z == b.Z;
   return (a.kind == GP_REQ_SLICE || a.kind == GP_REQ_STACK) && (b.kind == GP_REQ_SLICE || b.kind == GP_REQ_STACK) &&
          a.set_id == b.set_id && gp::same_view(qa.view, qb.view) && a.H == b.H && a.W == b.W &&
          a.sigma_z == b.sigma_z;
@@ -182,7 +190,7 @@ gp_status run_slices(gp_server* s, Worker& w, std::vector<Request>& batch) {
   gp_view v;
   memcpy(v.R, batch[0].view.R, sizeof(v.R));
   memcpy(v.t, batch[0].view.t, sizeof(v.t));
-  gp_status st = gp_render_slices_view(w.ctx, &s->sets[r0.set_id], &v, z.data(), S, r0.H, r0.W, r0.sigma_z, dst,
+  gp_status st = gp_render_slices_view(w.ctx, &batch[0].set, &v, z.data(), S, r0.H, r0.W, r0.sigma_z, dst,
                                        w.stream);
   if (st != GP_OK) return st;
   if (batch.size() > 1) {
@@ -196,6 +204,24 @@ gp_status run_slices(gp_server* s, Worker& w, std::vector<Request>& batch) {
       off += n;
     }
   }
+  if (cudaStreamSynchronize(w.stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GP_ERR_CUDA;
+  }
+  return GP_OK;
+}
+
+// Voxelize requests of one set and grid: one volume, copied to every output.
+gp_status run_voxelize(Worker& w, std::vector<Request>& batch) {
+  const gp_request& r0 = batch[0].r;
+  gp_status st = gp_voxelize(w.ctx, &batch[0].set, r0.X, r0.Y, r0.Z, r0.out, w.stream);
+  if (st != GP_OK) return st;
+  const size_t bytes = (size_t)r0.X * r0.Y * r0.Z * 4;
+  for (size_t i = 1; i < batch.size(); ++i)
+    if (cudaMemcpyAsync(batch[i].r.out, r0.out, bytes, cudaMemcpyDeviceToDevice, w.stream) != cudaSuccess) {
+      cudaGetLastError();
+      return GP_ERR_CUDA;
+    }
   if (cudaStreamSynchronize(w.stream) != cudaSuccess) {
     cudaGetLastError();
     return GP_ERR_CUDA;
@@ -242,6 +268,19 @@ void worker_loop(gp_server* s, int wi) {
             ++it;
           }
         }
+      } else {
+        // the same volume again: no workspace beyond the first request's, but
+        // like a slice it joins only while the memory in flight is in budget
+        for (auto it = s->pending.begin(); it != s->pending.end();) {
+          if ((int)batch.size() < s->cfg.max_batch_slices && same_batch(batch[0], *it) &&
+              s->inflight_bytes <= budget) {
+            it->est_bytes = 0;
+            batch.push_back(std::move(*it));
+            it = s->pending.erase(it);
+          } else {
+            ++it;
+          }
+        }
       }
       s->stats.inflight_requests += (int64_t)batch.size();
       s->stats.max_inflight_requests = std::max(s->stats.max_inflight_requests, s->stats.inflight_requests);
@@ -250,12 +289,7 @@ void worker_loop(gp_server* s, int wi) {
     gp::NvtxRange range(batch[0].r.kind == GP_REQ_VOXELIZE ? "gp:serve_voxelize" : "gp:serve_slices");
     gp_status st;
     if (batch[0].r.kind == GP_REQ_VOXELIZE) {
-      const gp_request& r = batch[0].r;
-      st = gp_voxelize(w.ctx, &s->sets[r.set_id], r.X, r.Y, r.Z, r.out, w.stream);
-      if (st == GP_OK && cudaStreamSynchronize(w.stream) != cudaSuccess) {
-        cudaGetLastError();
-        st = GP_ERR_CUDA;
-      }
+      st = run_voxelize(w, batch);
     } else {
       st = run_slices(s, w, batch);
     }
@@ -385,8 +419,9 @@ gp_status gp_serve_submit(gp_server* s, const gp_request* r, uint64_t* ticket) {
       gp::axis_view(r->axis, &q.view);
   }
   q.r.view = nullptr;  // the caller's view need not outlive the submit
+  q.set = s->sets[r->set_id];
   q.submitted = Clock::now();
-  q.est_bytes = estimate_bytes(s, *r);
+  q.est_bytes = estimate_bytes(q.set, *r);
   *ticket = q.ticket;
   s->pending.push_back(std::move(q));
   s->stats.submitted += 1;

@@ -49,28 +49,101 @@ def _wait(srv, t):
     raise AssertionError("request did not complete")
 
 
+def _long_stacks(srv, n, sid, planes):
+    """n stacks of `planes` planes of 1024^2 of a 500k-Gaussian set (several ms each)."""
+    z = (np.arange(planes, dtype=np.float32) * 4.0 + 0.5)
+    outs = [torch.empty(planes, 1024, 1024, device="cuda") for _ in range(n)]
+    return [srv.submit(B.GP_REQ_STACK, sid, o, z=z, H=1024, W=1024, sigma_z=3.0) for o in outs], outs
+
+
 def test_results_alone_equal_results_in_the_mix():
     ctx = B.Context(0)
     sets = [dev_set(g) for g in _sets()]
+    big = dev_set(synth.microscopy(seed=1002, n=500_000, extent=(1024, 1024, 256)))
     rng = np.random.Generator(np.random.PCG64(5))
     reqs = _requests(rng, 24)
     srv = B.Server(ctx, workers=3, max_batch_slices=32)
     ids = [srv.load_set(g) for g in sets]
     assert ids == [0, 1]
+    big_id = srv.load_set(big)
     alone = []
     for r in reqs:
         out = torch.full(r["shape"], float("nan"), device="cuda")
         res = _wait(srv, _submit(srv, r, out))
-        assert res["status"] == B.GP_OK
+        assert res["status"] == B.GP_OK and res["batch_size"] == 1
         alone.append(out)
+    # three long stacks occupy the three workers while the mix is queued behind
+    # them, so the mix is taken in batches and runs concurrently on the workers
+    long_t, _ = _long_stacks(srv, 3, big_id, 32)
     outs = [torch.full(r["shape"], float("nan"), device="cuda") for r in reqs]
     tickets = [_submit(srv, r, o) for r, o in zip(reqs, outs)]
     results = [_wait(srv, t) for t in tickets]
+    assert all(_wait(srv, t)["status"] == B.GP_OK for t in long_t)
     assert all(res["status"] == B.GP_OK for res in results)
     for a, b in zip(alone, outs):
         assert torch.equal(a, b)
+    assert max(res["batch_size"] for res in results) > 1, "the mix was never batched"
     st = srv.stats()
-    assert st["completed"] == 2 * len(reqs) and st["failed"] == 0
+    assert st["max_inflight_requests"] > 1, "requests never overlapped"
+    assert st["batches"] < st["completed"]
+    assert st["completed"] == 2 * len(reqs) + len(long_t) and st["failed"] == 0
+    srv.close()
+
+
+def test_voxelize_requests_of_one_set_and_grid_are_batched():
+    ctx = B.Context(0)
+    a, b = [dev_set(g) for g in _sets()]
+    big = dev_set(synth.microscopy(seed=1002, n=500_000, extent=(1024, 1024, 256)))
+    srv = B.Server(ctx, workers=1, max_batch_slices=64)
+    ia, ib, ibig = srv.load_set(a), srv.load_set(b), srv.load_set(big)
+    long_t, _ = _long_stacks(srv, 2, ibig, 64)  # the worker is busy while the rest queue up
+    same = [torch.full((24, 36, 40), float("nan"), device="cuda") for _ in range(5)]
+    t_same = [srv.submit(B.GP_REQ_VOXELIZE, ia, o, X=40, Y=36, Z=24) for o in same]
+    other_grid = torch.full((24, 36, 48), float("nan"), device="cuda")
+    other_set = torch.full((24, 36, 40), float("nan"), device="cuda")
+    t_grid = srv.submit(B.GP_REQ_VOXELIZE, ia, other_grid, X=48, Y=36, Z=24)
+    t_set = srv.submit(B.GP_REQ_VOXELIZE, ib, other_set, X=40, Y=36, Z=24)
+    res = [_wait(srv, t) for t in t_same]
+    r_grid, r_set = _wait(srv, t_grid), _wait(srv, t_set)
+    assert all(_wait(srv, t)["status"] == B.GP_OK for t in long_t)
+    assert all(r["status"] == B.GP_OK for r in res + [r_grid, r_set])
+    assert [r["batch_size"] for r in res] == [5] * 5
+    assert r_grid["batch_size"] == 1 and r_set["batch_size"] == 1
+    ref = B.gp_voxelize(ctx, a, 40, 36, 24)
+    for o in same:
+        assert torch.equal(o, ref)
+    assert torch.equal(other_grid, B.gp_voxelize(ctx, a, 48, 36, 24))
+    assert torch.equal(other_set, B.gp_voxelize(ctx, b, 40, 36, 24))
+    srv.close()
+
+
+def test_loading_sets_while_requests_run():
+    """Registering sets grows the server's set table while workers render
+    requests of earlier sets: every result is still right."""
+    import threading
+    ctx = B.Context(0)
+    g = _sets()[0]
+    gs = dev_set(g)
+    srv = B.Server(ctx, workers=3, max_batch_slices=8)
+    sid = srv.load_set(gs)
+    rng = np.random.Generator(np.random.PCG64(8))
+    zs = [rng.uniform(0, 48, int(rng.integers(1, 4))).astype(np.float32) for _ in range(60)]
+    outs = [torch.full((len(z), 96, 96), float("nan"), device="cuda") for z in zs]
+    extra = [dev_set(synth.small(seed=300 + k, n=10, extent=(16, 16, 8))) for k in range(4)]
+    loaded = []
+
+    def loader():
+        for k in range(400):
+            loaded.append(srv.load_set(extra[k % 4]))
+
+    th = threading.Thread(target=loader)
+    th.start()
+    tickets = [srv.submit(B.GP_REQ_STACK, sid, o, z=z, H=96, W=96, sigma_z=2.0) for z, o in zip(zs, outs)]
+    th.join()
+    assert all(_wait(srv, t)["status"] == B.GP_OK for t in tickets)
+    assert sorted(loaded) == list(range(1, 401))
+    for z, o in zip(zs, outs):
+        assert torch.equal(o, B.gp_render_slices(ctx, gs, z, 96, 96, 2.0))
     srv.close()
 
 
