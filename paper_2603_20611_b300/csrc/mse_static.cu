@@ -13,8 +13,9 @@
 // The array lives in the library's device module, so every GPU that loads the
 // library holds it (about 1.06 MiB) until the process exits.  In host code the
 // array's name is only a host-side stand-in, so its device address is looked up
-// with cudaGetSymbolAddress once per device, with that device current, on the
-// first call made on that device.
+// with cudaGetSymbolAddress on the first call made on each device, with that
+// device current.  Only a successful lookup is kept: after a failed one (for
+// example under an error left by earlier work) the next call tries again.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,11 +33,24 @@ constexpr int kNoallocMaxDevices = 64;
 static __device__ __align__(256) float g_noalloc_scratch[kNoallocPartials + kNoallocIndex];
 
 struct NoallocDevice {
-  std::once_flag once;
-  float* ptr = nullptr;
-  cudaError_t err = cudaSuccess;
+  std::mutex mu;
+  float* ptr = nullptr;  // set once the lookup has succeeded
 };
 static NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
+
+// The scratch's device address on the current device `dev`, or nullptr.
+static float* noalloc_scratch(int dev) {
+  NoallocDevice& d = g_noalloc_dev[dev];
+  std::lock_guard<std::mutex> lk(d.mu);
+  if (!d.ptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) == cudaSuccess)
+      d.ptr = (float*)p;
+    else
+      cudaGetLastError();
+  }
+  return d.ptr;
+}
 
 }  // namespace gp
 
@@ -60,18 +74,12 @@ extern "C" GP_API gp_status gp_mse_grad_noalloc(const float* I, const float* T, 
     cudaGetLastError();
     return GP_ERR_CUDA;
   }
-  NoallocDevice& d = g_noalloc_dev[dev];
-  std::call_once(d.once, [&]() {
-    void* p = nullptr;
-    d.err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    d.ptr = d.err == cudaSuccess ? (float*)p : nullptr;
-    if (d.err != cudaSuccess) cudaGetLastError();
-  });
-  if (d.err != cudaSuccess || !d.ptr) return GP_ERR_CUDA;
+  float* scratch = noalloc_scratch(dev);
+  if (!scratch) return GP_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
   const int* tid = nullptr;
   if (t_index) {
-    int* dst = (int*)(d.ptr + kNoallocPartials);
+    int* dst = (int*)(scratch + kNoallocPartials);
     if (cudaMemcpyAsync(dst, t_index, (size_t)S * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess) {
       cudaGetLastError();
       return GP_ERR_CUDA;
@@ -80,7 +88,7 @@ extern "C" GP_API gp_status gp_mse_grad_noalloc(const float* I, const float* T, 
   }
   // every partial the final reduction reads is written first by the per-slice
   // kernel of this call, so nothing has to be cleared
-  launch_mse(I, T, tid, S, HW, dL_dI, loss, d.ptr, st);
+  launch_mse(I, T, tid, S, HW, dL_dI, loss, scratch, st);
   if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
   return GP_OK;
 }
