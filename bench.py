@@ -16,9 +16,14 @@ ALGORITHMIC evaluations (pixels inside each pair's culling ellipse,
 d^T Sigma_2d^-1 d <= 2 ln(1/eps), on slices with opacity_r >= eps), twice per
 step (forward and backward).  Also reported: slices/s, per-phase times, the
 roofline of the dominant kernel, an end-to-end figure through host buffers,
-and the FP64 oracle timed on host cores on a bounded sample.
+and the FP64 oracle timed on host cores on a bounded sample.  At N = 1 the
+line also carries the batched form ("batched": 64 uneven sets in one autotuned
+graph launch against 64 plain render + backward calls) and the served form
+("serving": a seeded Poisson request stream at two offered rates, served with
+continuous batching and replayed through sequential plain calls), each with
+its own clocks, after the fit step's timed region.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--fit-only]
 """
 from __future__ import annotations
 
@@ -180,10 +185,14 @@ def summarise_clocks(text, window=None):
             "power_w_max": max(pw) if pw else None}
 
 
-# Per-launch DRAM traffic of the rasterisers, from a full-size ncu capture of
-# the default configuration (single-pass dram__bytes metrics), keyed by a hash
-# of the kernels' sources so that a changed kernel reports null.
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_raster_traffic_microscopy_fit_step.md")
+# Per-launch DRAM traffic of the rasterisers on this workload, from an ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), kept as data in
+# profiles/raster_traffic.json with a hash of the kernels' sources, so that a
+# changed kernel reports null.  A capture beyond gpu__time_duration is taken on
+# one kernel and one or two launches of the quarter-size case (--case small,
+# -k regex:k_raster_bwd_blk -s <warm-up launches> -c 2, --clock-control none)
+# and scaled to a full launch by the binned pairs ("scale").
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "raster_traffic.json")
 KERNEL_SOURCES = ("paper_2603_20611_b300/csrc/raster.cu", "paper_2603_20611_b300/csrc/gp_common.cuh",
                   "paper_2603_20611_b300/csrc/slice.cuh")
 
@@ -200,16 +209,14 @@ def recorded_traffic(kernel):
     """(bytes per launch, note) for `kernel` ('k_raster_fwd_blk' / 'k_raster_bwd_blk')."""
     if not os.path.exists(TRAFFIC_FILE):
         return None, "no capture recorded"
-    want = kernel_source_hash()
     with open(TRAFFIC_FILE) as f:
-        for line in f:
-            c = [x.strip() for x in line.strip().strip("|").split("|")]
-            if len(c) >= 5 and c[0] == kernel:
-                if c[1] != want:
-                    return None, "stale: the kernel sources changed since the capture"
-                return float(c[2]) + float(c[3]), ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
-                                                   "full-size capture of the default configuration")
-    return None, "kernel not in the capture"
+        rec = json.load(f).get("kernels", {}).get(kernel)
+    if rec is None:
+        return None, "kernel not in the capture"
+    if rec["source_hash"] != kernel_source_hash():
+        return None, "stale: the kernel sources changed since the capture"
+    return (rec["dram_read_bytes"] + rec["dram_write_bytes"]) * rec.get("scale", 1.0), \
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch: " + rec["note"]
 
 
 def oblique_view(Wd, Hd, Dd, seed=8080):
@@ -542,6 +549,14 @@ def run_native(args, rank, world):
                         "ms_per_step": float(np.mean(e2e_ms)),
                         "overlap": "uploads and readbacks on two copy streams, two device buffer sets"},
                 "gpu_launches": launches, "clocks": clk, "wall_s_timed": wall}
+        if world == 1 and not args.fit_only:
+            # the batched and served forms against their plain launches (after
+            # the headline's timed region; their own CUDA-event and wall clocks)
+            del target, host_stack, bufs
+            torch.cuda.empty_cache()
+            line["batched"] = batched_comparison(max(5, min(args.steps, 20)), 3)
+            line["serving"] = serving_comparison([float(r) for r in args.fit_rates.split(",")],
+                                                 args.serve_requests, args.serve_workers)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -550,23 +565,22 @@ def run_native(args, rank, world):
 
 # ------------------------------------------------------------ batched workload
 
-def run_batched(args):
+def batched_comparison(steps, warmup):
     """64 uneven sets (1k-200k Gaussians, 128^2-1024^2 slices, 8-64 planes,
     sigma_z in [1, 6]) forward + backward against seeded upstream gradients:
-    one autotuned graph launch per step versus 64 plain render + backward calls."""
+    one autotuned graph launch per step against 64 plain render + backward
+    calls, both timed with CUDA events on the launching stream."""
     import torch
     from paper_2603_20611_b300 import binding as B
     from paper_2603_20611_b300 import synth
-    torch.cuda.set_device(0)
-    dev = "cuda:0"
-    ctx = B.Context(0)
+    dev = f"cuda:{torch.cuda.current_device()}"
+    ctx = B.Context(torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     gen = torch.Generator(device=dev)
     gen.manual_seed(4004)
     t0 = time.perf_counter()
-    raw = synth.batched()
     items, evals = [], 0
-    for bi in raw:
+    for bi in synth.batched():
         gs = B.GaussianSet.from_numpy(bi.gs, dev)
         S = len(bi.z)
         it = {"gs": gs, "z": bi.z, "H": bi.H, "W": bi.W, "sigma_z": bi.sigma_z, "axis": 2,
@@ -588,142 +602,235 @@ def run_batched(args):
             B.gp_render_backward(ctx, it["gs"], it["z"], it["H"], it["W"], it["sigma_z"], it["dL_dI"],
                                  grads=it["grads"])
 
-    def timed(fn, steps):
+    def timed(fn, n):
         evs = []
-        for _ in range(steps):
+        for _ in range(n):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()
             e1.record(stream)
             evs.append((e0, e1))
         torch.cuda.synchronize()
-        return [a.elapsed_time(b) for a, b in evs]
+        return [x.elapsed_time(y) for x, y in evs]
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plan.run()
         plain_step()
     plan.wait()
     torch.cuda.synchronize()
-    b_ms = timed(lambda: plan.run(), args.steps)
+    b_ms = timed(lambda: plan.run(), steps)
     plan.wait()
-    p_ms = timed(plain_step, args.steps)
+    p_ms = timed(plain_step, steps)
     info = plan.info()
-    work_gb = sum(2 * it["out"].numel() * 4 for it in items) / 1e9  # images + dL/dI
-    line = {"metric": METRIC, "value": 2.0 * evals / (np.mean(b_ms) * 1e-3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(b_ms)),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batched: 64 sets, N log-uniform in [1k, 200k], square slices of side in "
-                                   "{128, 256, 512, 1024}, 8-64 planes, sigma_z ~ U(1, 6), fwd + bwd against "
-                                   "seeded dL/dI; one autotuned graph launch per step",
-                       "n_items": len(items), "n_gaussians": int(sum(it["gs"].n for it in items)),
-                       "l2": f"not flushed: every step writes and reads {work_gb:.1f} GB of images and "
-                             f"gradients, {work_gb * 1e3 / 126:.0f}x the 126 MB L2",
-                       "autotuned": info},
-            "plain_launches": {"value": 2.0 * evals / (np.mean(p_ms) * 1e-3), "ms_per_step": float(np.mean(p_ms)),
-                               "launch": "64 x (gp_render_slices + gp_render_backward)"},
-            "speedup_vs_plain": float(np.mean(p_ms) / np.mean(b_ms)),
-            "slices_per_s": sum(len(it["z"]) for it in items) / (np.mean(b_ms) * 1e-3)}
-    print(json.dumps(line), flush=True)
     plan.close()
+    work_gb = sum(2 * it["out"].numel() * 4 for it in items) / 1e9  # images + dL/dI
+    return {"workload": "64 sets, N log-uniform in [1k, 200k], square slices of side in {128, 256, 512, 1024}, "
+                        "8-64 planes, sigma_z ~ U(1, 6), fwd + bwd against seeded dL/dI; one autotuned graph "
+                        "launch per step",
+            "n_items": len(items), "n_gaussians": int(sum(it["gs"].n for it in items)),
+            "evals_fwd_per_step": float(evals), "steps": steps, "warmup": warmup,
+            "ms_per_step": float(np.mean(b_ms)), "value": 2.0 * evals / (np.mean(b_ms) * 1e-3), "unit": UNIT,
+            "slices_per_s": sum(len(it["z"]) for it in items) / (np.mean(b_ms) * 1e-3),
+            "plain": {"ms_per_step": float(np.mean(p_ms)), "value": 2.0 * evals / (np.mean(p_ms) * 1e-3),
+                      "launch": "64 x (gp_render_slices + gp_render_backward) on one stream"},
+            "speedup_vs_plain": float(np.mean(p_ms) / np.mean(b_ms)),
+            "autotuned": info,
+            "l2": f"not flushed: every step writes and reads {work_gb:.1f} GB of images and gradients, "
+                  f"{work_gb * 1e3 / 126:.0f}x the 126 MB L2"}
+
+
+def run_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = batched_comparison(args.steps, args.warmup)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched: " + r["workload"], "n_items": r["n_items"],
+                       "n_gaussians": r["n_gaussians"], "l2": r["l2"], "autotuned": r["autotuned"]},
+            "plain_launches": r["plain"], "speedup_vs_plain": r["speedup_vs_plain"],
+            "slices_per_s": r["slices_per_s"]}
+    print(json.dumps(line), flush=True)
     return 0
 
 
 # ------------------------------------------------------------- serving workload
 
-def run_serving(args):
-    """8 resident sets (50k-2M Gaussians in 1024^3), Poisson arrivals at swept
-    rates; each request is a random axis-aligned slice (side 256-1024, random
-    axis), a 16-slice 512^2 stack, or a 256^3 voxelize.  Reports throughput and
-    p50 / p99 latency per rate."""
+SERVE_KINDS = ("slice", "stack", "voxelize")
+
+
+def serving_stream(rate, n, n_sets, seed):
+    """A seeded request stream: Poisson arrival offsets (s) and, per request, its
+    kind (a slice of side 256-1024 on a random axis, a 16-slice 512^2 stack, or
+    a 256^3 voxelize), set and parameters."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+    reqs = []
+    for kind in rng.choice(3, n):
+        sid = int(rng.integers(0, n_sets))
+        if kind == 2:
+            reqs.append({"kind": 2, "set": sid})
+        elif kind == 0:
+            side = int(rng.integers(256, 1025))
+            reqs.append({"kind": 0, "set": sid, "side": side, "axis": int(rng.integers(0, 3)),
+                         "z": np.array([rng.uniform(0, 1024)], np.float32)})
+        else:
+            z0 = rng.uniform(0, 1024 - 16)
+            reqs.append({"kind": 1, "set": sid, "z": (z0 + np.arange(16)).astype(np.float32)})
+    return arrivals, reqs
+
+
+def _latency_summary(lat_ms, n, wall):
+    a = np.asarray(lat_ms)
+    return {"requests": n, "throughput_req_per_s": n / wall, "p50_ms": float(np.percentile(a, 50)),
+            "p99_ms": float(np.percentile(a, 99)), "mean_ms": float(a.mean())}
+
+
+def serve_served(B, srv, pools, arrivals, reqs):
+    """The stream through the server: each request is submitted at its arrival
+    time (once an output buffer of its kind is free, as a client with a bounded
+    number of outstanding requests would); latency runs from the arrival to the
+    completion the server reports."""
     import threading
+    kinds = (B.GP_REQ_SLICE, B.GP_REQ_STACK, B.GP_REQ_VOXELIZE)
+    free = {k: list(range(len(v))) for k, v in pools.items()}
+    lock = threading.Lock()
+    lat, pend, batch = [], {}, []
+    done_evt = threading.Event()
+
+    def poller():
+        while not (done_evt.is_set() and not pend):
+            with lock:
+                items = list(pend.items())
+            if not items:
+                time.sleep(0.0005)
+                continue
+            for t, (kind, slot, lag_ms) in items:
+                res = srv.poll(t, timeout_ms=0)
+                if res is not None:
+                    with lock:
+                        lat.append(lag_ms + res["latency_ms"])
+                        batch.append(res["batch_size"])
+                        free[kind].append(slot)
+                        del pend[t]
+            time.sleep(0.0002)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for at, r in zip(arrivals, reqs):
+        while time.perf_counter() - t0 < at:
+            time.sleep(min(0.0005, max(0.0, at - (time.perf_counter() - t0))))
+        kind = kinds[r["kind"]]
+        while True:
+            with lock:
+                if free[kind]:
+                    slot = free[kind].pop()
+                    break
+            time.sleep(0.0002)
+        buf = pools[kind][slot]
+        lag_ms = (time.perf_counter() - t0 - at) * 1e3
+        if r["kind"] == 2:
+            t = srv.submit(kind, r["set"], buf, X=256, Y=256, Z=256)
+        elif r["kind"] == 0:
+            sd = r["side"]
+            t = srv.submit(kind, r["set"], buf[:sd * sd], z=r["z"], H=sd, W=sd, sigma_z=3.0, axis=r["axis"])
+        else:
+            t = srv.submit(kind, r["set"], buf, z=r["z"], H=512, W=512, sigma_z=3.0, axis=2)
+        with lock:
+            pend[t] = (kind, slot, lag_ms)
+    done_evt.set()
+    th.join()
+    wall = time.perf_counter() - t0
+    out = _latency_summary(lat, len(reqs), wall)
+    out["mean_batch_size"] = float(np.mean(batch))
+    return out
+
+
+def serve_plain(B, ctx, sets, bufs, arrivals, reqs, stream):
+    """The same stream through sequential plain calls (gp_render_slices /
+    gp_voxelize) on one stream, each waited for before the next starts;
+    latency runs from the arrival to the end of the call."""
+    lat = []
+    t0 = time.perf_counter()
+    for at, r in zip(arrivals, reqs):
+        while time.perf_counter() - t0 < at:
+            time.sleep(min(0.0005, max(0.0, at - (time.perf_counter() - t0))))
+        gs = sets[r["set"]]
+        if r["kind"] == 2:
+            B.gp_voxelize(ctx, gs, 256, 256, 256, vol=bufs[2])
+        elif r["kind"] == 0:
+            sd = r["side"]
+            B.gp_render_slices(ctx, gs, r["z"], sd, sd, 3.0, r["axis"], out=bufs[0][:sd * sd].view(1, sd, sd))
+        else:
+            B.gp_render_slices(ctx, gs, r["z"], 512, 512, 3.0, 2, out=bufs[1].view(16, 512, 512))
+        stream.synchronize()
+        lat.append((time.perf_counter() - t0 - at) * 1e3)
+    return _latency_summary(lat, len(reqs), time.perf_counter() - t0)
+
+
+def serving_comparison(rates, n_requests, workers):
+    """8 resident sets (50k-2M Gaussians in 1024^3); for each offered rate a
+    seeded Poisson stream of n_requests requests, served (continuous batching
+    on `workers` workers) and replayed through sequential plain calls."""
     import torch
     from paper_2603_20611_b300 import binding as B
     from paper_2603_20611_b300 import synth
-    torch.cuda.set_device(0)
-    dev = "cuda:0"
-    ctx = B.Context(0)
+    dev_i = torch.cuda.current_device()
+    dev = f"cuda:{dev_i}"
+    ctx = B.Context(dev_i)
+    pctx = B.Context(dev_i)
+    stream = torch.cuda.current_stream()
     sets = [B.GaussianSet.from_numpy(g, dev) for g in synth.serving_sets()]
-    srv = B.Server(ctx, workers=args.serve_workers, max_batch_slices=64)
+    srv = B.Server(ctx, workers=workers, max_batch_slices=64)
     for g in sets:
         srv.load_set(g)
     pools = {B.GP_REQ_SLICE: [torch.empty(1024 * 1024, device=dev) for _ in range(48)],
              B.GP_REQ_STACK: [torch.empty(16 * 512 * 512, device=dev) for _ in range(48)],
              B.GP_REQ_VOXELIZE: [torch.empty(256 ** 3, device=dev) for _ in range(24)]}
-    rng = np.random.Generator(np.random.PCG64(5005))
-    rates = [float(r) for r in args.rates.split(",")]
+    bufs = [torch.empty(1024 * 1024, device=dev), torch.empty(16 * 512 * 512, device=dev),
+            torch.empty(256, 256, 256, device=dev)]
+    # warm-up: every kind on every set through both arms (workspaces grow once)
+    arr_w, req_w = serving_stream(1e6, 48, len(sets), 5004)
+    serve_served(B, srv, pools, arr_w, req_w)
+    serve_plain(B, pctx, sets, bufs, arr_w, req_w, stream)
     per_rate = []
-    for rate in rates:
-        n_req = int(max(20, min(args.serve_requests, rate * args.serve_seconds)))
-        free = {k: list(range(len(v))) for k, v in pools.items()}
-        lock = threading.Lock()
-        lat, pend = [], {}
-        done_evt = threading.Event()
-
-        def poller():
-            while not (done_evt.is_set() and not pend):
-                with lock:
-                    items = list(pend.items())
-                if not items:
-                    time.sleep(0.0005)
-                    continue
-                for t, (kind, slot) in items:
-                    res = srv.poll(t, timeout_ms=0)
-                    if res is not None:
-                        with lock:
-                            lat.append(res["latency_ms"])
-                            free[kind].append(slot)
-                            del pend[t]
-                time.sleep(0.0002)
-
-        th = threading.Thread(target=poller)
-        th.start()
-        t0 = time.perf_counter()
-        next_t = t0
-        kinds = rng.choice(3, n_req)
-        for i in range(n_req):
-            next_t += rng.exponential(1.0 / rate)
-            while time.perf_counter() < next_t:
-                time.sleep(min(0.0005, max(0.0, next_t - time.perf_counter())))
-            kind = [B.GP_REQ_SLICE, B.GP_REQ_STACK, B.GP_REQ_VOXELIZE][int(kinds[i])]
-            while True:
-                with lock:
-                    if free[kind]:
-                        slot = free[kind].pop()
-                        break
-                time.sleep(0.0002)
-            buf = pools[kind][slot]
-            sid = int(rng.integers(0, len(sets)))
-            if kind == B.GP_REQ_VOXELIZE:
-                t = srv.submit(kind, sid, buf, X=256, Y=256, Z=256)
-            elif kind == B.GP_REQ_SLICE:
-                side = int(rng.integers(256, 1025))
-                axis = int(rng.integers(0, 3))
-                z = np.array([rng.uniform(0, 1024)], np.float32)
-                t = srv.submit(kind, sid, buf[:side * side], z=z, H=side, W=side, sigma_z=3.0, axis=axis)
-            else:
-                z0 = rng.uniform(0, 1024 - 16)
-                z = (z0 + np.arange(16)).astype(np.float32)
-                t = srv.submit(kind, sid, buf, z=z, H=512, W=512, sigma_z=3.0, axis=2)
-            with lock:
-                pend[t] = (kind, slot)
-        done_evt.set()
-        th.join()
-        wall = time.perf_counter() - t0
-        lat_a = np.array(lat)
-        per_rate.append({"offered_req_per_s": rate, "requests": n_req, "throughput_req_per_s": n_req / wall,
-                         "p50_ms": float(np.percentile(lat_a, 50)), "p99_ms": float(np.percentile(lat_a, 99)),
-                         "mean_ms": float(lat_a.mean())})
-        log(f"rate {rate}: {per_rate[-1]}")
-    st = srv.stats()
+    for k, rate in enumerate(rates):
+        arrivals, reqs = serving_stream(rate, n_requests, len(sets), 5005 + k)
+        st0 = srv.stats()
+        served = serve_served(B, srv, pools, arrivals, reqs)
+        st1 = srv.stats()
+        served["batches"] = st1["batches"] - st0["batches"]
+        plain = serve_plain(B, pctx, sets, bufs, arrivals, reqs, stream)
+        per_rate.append({"offered_req_per_s": rate, "served": served, "plain": plain,
+                         "throughput_vs_plain": served["throughput_req_per_s"] / plain["throughput_req_per_s"],
+                         "p99_vs_plain": served["p99_ms"] / plain["p99_ms"]})
+        log(f"serving rate {rate}: served {served['throughput_req_per_s']:.0f} req/s p50 {served['p50_ms']:.2f} "
+            f"p99 {served['p99_ms']:.2f} ms; plain {plain['throughput_req_per_s']:.0f} req/s "
+            f"p50 {plain['p50_ms']:.2f} p99 {plain['p99_ms']:.2f} ms")
+    stats = srv.stats()
     srv.close()
-    best = max(per_rate, key=lambda r: r["throughput_req_per_s"])
-    line = {"metric": "served requests/s with p50/p99 latency", "value": best["throughput_req_per_s"],
+    return {"workload": "8 resident sets of 50k-2M Gaussians in 1024^3; Poisson arrivals; requests uniform over "
+                        "{1 slice 256^2-1024^2 on a random axis, 16-slice 512^2 stack, 256^3 voxelize}",
+            "workers": workers, "per_rate": per_rate, "server_stats": stats,
+            "plain": "the same seeded request stream through sequential gp_render_slices / gp_voxelize calls on "
+                     "one stream, each finished before the next starts",
+            "latency": "from the request's arrival time to its completion, in both arms"}
+
+
+def run_serving(args):
+    import torch
+    torch.cuda.set_device(0)
+    rates = [float(r) for r in args.rates.split(",")]
+    r = serving_comparison(rates, args.serve_requests, args.serve_workers)
+    best = max(r["per_rate"], key=lambda x: x["served"]["throughput_req_per_s"])
+    line = {"metric": "served requests/s with p50/p99 latency", "value": best["served"]["throughput_req_per_s"],
             "unit": "req/s", "n_gpus": 1, "steps": len(rates), "warmup": 0, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serving: 8 resident sets of 50k-2M Gaussians in 1024^3; Poisson arrivals; "
-                                   "requests uniform over {1 slice 256^2-1024^2 on a random axis, 16-slice 512^2 "
-                                   "stack, 256^3 voxelize}", "workers": args.serve_workers},
-            "per_rate": per_rate, "server_stats": st}
+            "config": {"workload": "serving: " + r["workload"], "workers": r["workers"],
+                       "requests_per_rate": args.serve_requests},
+            "per_rate": r["per_rate"], "plain": r["plain"], "latency": r["latency"],
+            "server_stats": r["server_stats"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -918,10 +1025,13 @@ def main():
                                                            "voxelize"])
     ap.add_argument("--view", default="axis", choices=["axis", "oblique"],
                     help="fit step on axis-aligned planes, or on a seeded oblique stack through the centre")
-    ap.add_argument("--rates", default="10,30,100,300,1000")
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--rates", default="1000,3000,10000,30000")
+    ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--fit-only", action="store_true",
+                    help="the fit step alone, without the batched and served comparisons")
+    ap.add_argument("--fit-rates", default="3000,30000",
+                    help="offered request rates of the served comparison attached to the fit-step line")
     args = ap.parse_args()
     if args.case == "small":
         use_small_case()
