@@ -80,6 +80,17 @@ OPS_PER_EVAL = {"fwd": 16, "bwd": 20}
 # (84 per row), i.e. 50/8 and 84/8 lane instructions per evaluation.
 OPS_PER_EVAL_ROW = {"fwd": 6.25, "bwd": 10.5}
 EXP_MODES = {"poly": 0, "hw": 1, "row": 3}
+RASTER_FORMS = {"auto": 0, "block": 1, "rows": 2}
+
+
+def pass_roofline(evals, evaluated, ops, launch_s, peak, kernel):
+    """Roofline figures of one rasteriser pass: algorithmic lane instructions per
+    second against the measured FP32 peak, and the evaluated pixels per
+    algorithmic evaluation."""
+    achieved = evals * ops / launch_s / 1e12
+    return {"kernel": kernel, "achieved": achieved, "peak": peak / 1e12, "frac": achieved / (peak / 1e12),
+            "ops_per_eval": ops, "launch_ms": launch_s * 1e3,
+            "evaluated_per_algorithmic": (evaluated / evals) if evals else None}
 
 
 def fp32_probe_peak(ctx, stream, reps=5, iters=20000, mode=0):
@@ -361,7 +372,7 @@ def run_native(args, rank, world):
         dist.init_process_group("nccl")
     ctx = B.Context(dev_index, exp_mode=EXP_MODES[args.exp],
                     deterministic=args.det, tile=args.tile, fwd_px=args.fwd_px, bwd_px=args.bwd_px,
-                    reuse_bins=not args.rebin)
+                    reuse_bins=not args.rebin, raster=RASTER_FORMS[args.raster])
     stream = torch.cuda.current_stream()
     t_setup = time.perf_counter()
     g, gs, target = make_workload(B, synth, torch, dev, ctx)
@@ -375,8 +386,12 @@ def run_native(args, rank, world):
         zs = [z - DEPTH / 2.0 for z in zs]
     # a second context counts the algorithmic evaluations of every step on the
     # parameters that step renders (the Adam update moves them between steps)
-    cctx = B.Context(dev_index, deterministic=args.det, tile=args.tile)
+    cctx = B.Context(dev_index, deterministic=args.det, tile=args.tile, exp_mode=EXP_MODES[args.exp],
+                     raster=RASTER_FORMS[args.raster])
     evals0 = [B.gp_count_evals(cctx, gs, z, H, W, SIGMA, view=view) for z in zs]  # initial parameters (e2e loop)
+    # pixels the rasterisers evaluate on the first timed step (initial parameters)
+    evaluated = B.gp_count_evaluated(cctx, gs, zs[args.warmup], H, W, SIGMA, view=view)
+    evaluated_ratio = [e / max(evals0[args.warmup], 1) for e in evaluated]
     log(f"setup {time.perf_counter() - t_setup:.1f}s; evals/step (fwd) ~{np.mean(evals0):.3e}")
     host_params = [t.cpu().pin_memory() for t in (gs.mu, gs.scale, gs.quat, gs.alpha)]
     opt = B.Adam(ctx, gs, total_steps=30000, mu_extent=float(max(H, W)))
@@ -449,8 +464,12 @@ def run_native(args, rank, world):
     value = tot_evals / t_total
     pairs, issued = ctx.last_counts()
 
-    # roofline of the dominant kernel (the larger of the two rasterisers)
+    # roofline of the dominant kernel (the larger of the two rasterisers), and of both passes
     dom = "bwd" if phases["bwd"][0] >= phases["fwd"][0] else "fwd"
+    ops_t = OPS_PER_EVAL_ROW if args.exp == "row" else OPS_PER_EVAL
+    passes = {p: pass_roofline(float(np.mean(ev_steps)), float(np.mean(ev_steps)) * evaluated_ratio[i], ops_t[p],
+                               phases[p][0] * 1e-3 / max(phases[p][2], 1), fp32_peak, f"k_raster_{p}")
+              for i, p in enumerate(("fwd", "bwd"))}
     ms_dom, _, calls_dom = phases[dom]
     avg_launch_s = ms_dom * 1e-3 / max(calls_dom, 1)
     ops_table = OPS_PER_EVAL_ROW if args.exp == "row" else OPS_PER_EVAL
@@ -536,7 +555,9 @@ def run_native(args, rank, world):
                                parallelism="replicas" if world > 1 else "single"),
                 "slices_per_s": world * S * args.steps / t_total,
                 "evals_fwd_per_step": float(np.mean(ev_steps)),
-                "issued_evals_last_call": issued, "pairs_last_call": pairs,
+                "pairs_last_call": pairs, "tile_pixels_last_call": issued,
+                "evaluated_per_algorithmic": {"fwd": evaluated_ratio[0], "bwd": evaluated_ratio[1]},
+                "rasteriser": args.raster, "passes": passes,
                 "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[2]},
                 "roofline": {"bound": "alu", "kernel": f"k_raster_{dom}", "achieved": achieved, "peak": peak,
                              "unit": "Tinst/s (FP32+INT lane instructions)", "frac": achieved / peak,
@@ -871,7 +892,8 @@ def run_ultrasound(args):
     dev = "cuda:0"
     # the backward takes the forward's bins (parameters unchanged); --exp picks the
     # rasterisers' exponential (the voxelizer always evaluates exp2 per voxel)
-    ctx = B.Context(0, reuse_bins=True, exp_mode=EXP_MODES[args.exp], tile=args.tile)
+    ctx = B.Context(0, reuse_bins=True, exp_mode=EXP_MODES[args.exp], tile=args.tile,
+                    raster=RASTER_FORMS[args.raster])
     g = synth.ultrasound()
     gs = B.GaussianSet.from_numpy(g, dev)
     D = 512
@@ -885,6 +907,7 @@ def run_ultrasound(args):
     z = synth.slice_positions(range(D))
     if args.workload == "ultrasound":
         evals = B.gp_count_evals(ctx, gs, z, D, D, 5.0)
+        evaluated = B.gp_count_evaluated(ctx, gs, z, D, D, 5.0)
 
         def step():
             B.gp_render_slices(ctx, gs, z, D, D, 5.0, out=out)
@@ -895,12 +918,14 @@ def run_ultrasound(args):
         name = "ultrasound slice stack: 200k Gaussians, 512^3, sigma_z = 5, all 512 slices, fwd + MSE + bwd"
     else:
         evals = B.gp_count_vox_evals(ctx, gs, D, D, D)
+        evaluated = B.gp_count_vox_evaluated(ctx, gs, D, D, D)
 
         def step():
             B.gp_voxelize(ctx, gs, D, D, D, vol=out)
             B.gp_mse_grad(ctx, out, target, dL_dI=G, loss=loss)
             B.gp_voxelize_backward(ctx, gs, D, D, D, G, grads=grads)
-        fwd_phase, bwd_phase, ops = "vox_fwd", "vox_bwd", None
+        fwd_phase, bwd_phase = "vox_fwd", "vox_bwd"
+        ops = OPS_PER_EVAL["bwd"]  # the voxelizer planes run the slice rasterisers with per-pixel exp2
         name = "ultrasound voxelize: 200k Gaussians, 512^3 grid, Eq. 12 fwd + MSE + bwd"
     flush = torch.empty(64 * 1024 * 1024, device=dev)
     for _ in range(args.warmup):
@@ -928,10 +953,16 @@ def run_ultrasound(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": name, "n_gaussians": g.n, "l2": "flushed between steps (256 MiB write)",
                        "exp": args.exp if args.workload == "ultrasound" else "poly"},
-            "evals_fwd_per_step": evals,
+            "evals_fwd_per_step": evals, "rasteriser": args.raster,
             "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[2]}}
+    ops_t = OPS_PER_EVAL_ROW if (args.exp == "row" and args.workload == "ultrasound") else OPS_PER_EVAL
+    # one rasteriser launch per step and pass (the voxelizer's backward phase also
+    # holds its small gradient-finish kernel)
+    line["passes"] = {p: pass_roofline(evals, evals * (evaluated[i] / max(evals, 1)), ops_t[p],
+                                       phases[ph][0] * 1e-3 / args.steps, fp32_peak, f"k_raster_{p}")
+                      for i, (p, ph) in enumerate((("fwd", fwd_phase), ("bwd", bwd_phase)))}
     if ops:
-        bwd_s = phases[bwd_phase][0] * 1e-3 / max(phases[bwd_phase][2], 1)
+        bwd_s = phases[bwd_phase][0] * 1e-3 / args.steps
         achieved = evals * ops / bwd_s / 1e12
         line["roofline"] = {"bound": "alu", "kernel": "k_raster_bwd", "achieved": achieved,
                             "peak": fp32_peak / 1e12, "frac": achieved / (fp32_peak / 1e12),
@@ -1012,6 +1043,8 @@ def main():
                     help="exponential: poly (default), hw (SFU ex2.approx) or row (poly, factored per pixel row)")
     ap.add_argument("--det", action="store_true")
     ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--raster", default="auto", choices=sorted(RASTER_FORMS),
+                    help="rasteriser form: auto (row units on voxelizer planes, block-culled on slices), block or rows")
     ap.add_argument("--fwd-px", type=int, default=0)
     ap.add_argument("--bwd-px", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -85,6 +85,18 @@ typedef struct gp_ctx gp_ctx;
                                  only (fwd_px = bwd_px = 0); Gaussians narrower than about 0.3
                                  pixel fall back to one exp2 per pixel. */
 
+/* Form of the default rasterisers (fwd_px = bwd_px = 0), GP_EXP_POLY / GP_EXP_HW. */
+#define GP_RASTER_AUTO 0   /* row units for the forward, and for the backward on voxelizer planes;
+                              block-culled for the backward on slice planes (default) */
+#define GP_RASTER_BLOCK 1  /* block-culled: four warps per 16 x 16 tile, each Gaussian evaluated
+                              over the 8 x 8 blocks (forward) / 8 x 4 half-blocks (backward) its
+                              culling ellipse touches */
+#define GP_RASTER_ROWS 2   /* row units: one warp per tile, each Gaussian evaluated over the 8-pixel
+                              row segments its culling ellipse touches */
+#define GP_RASTER_PIXELS 3 /* (batch plans' report only) one thread per group of pixels of a tile,
+                              every staged Gaussian evaluated at every pixel: the fwd_px / bwd_px
+                              kernels */
+
 typedef struct {
   float eps;              /* culling bound: truncated mass per pair <= eps (default 1e-6) */
   int deterministic;      /* 1: backward reduces per-pair partials in a fixed order
@@ -106,6 +118,8 @@ typedef struct {
                              planes, image size, sigma_z and axis (grid); the caller guarantees
                              the parameter VALUES are unchanged in between (true inside one
                              forward/backward step).  0 (default): the backward always re-bins. */
+  int raster;             /* GP_RASTER_AUTO (default), GP_RASTER_BLOCK or GP_RASTER_ROWS; the
+                             row-factored exponential (GP_EXP_POLY_ROW) is block-culled only */
 } gp_config;
 
 /* Fills *cfg with the defaults above.  Returns GP_ERR_ARG if cfg is NULL. */
@@ -261,6 +275,20 @@ GP_API gp_status gp_voxelize_backward(gp_ctx* ctx, const gp_set* set, int X, int
  * grid: the algorithmic work of gp_voxelize (Eq. 12).  Synchronous. */
 GP_API gp_status gp_count_vox_evals(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, int64_t* evals);
 
+/* Pixels (or voxels) the context's default rasterisers (fwd_px = bwd_px = 0)
+ * evaluate for a render or a voxelize, *fwd for the forward and *bwd for the
+ * backward, with the same culling tests the kernels stage with (Sec. 4.2, the
+ * eps reading above): the row-unit form evaluates 8 pixels per (Gaussian,
+ * plane, screen tile, 8-pixel column band, pixel row) whose segment of pixel
+ * centres the culling ellipse meets; the block-culled form 64 per 8 x 8 block
+ * (forward) and 32 per 8 x 4 half-block (backward) the ellipse touches.
+ * Divided by gp_count_evals / gp_count_vox_evals it gives the evaluations
+ * spent per algorithmic one.  Synchronous.  GP_ERR_ARG as in the render calls. */
+GP_API gp_status gp_count_evaluated_view(gp_ctx* ctx, const gp_set* set, const gp_view* view, const float* z,
+                                         int S, int H, int W, float sigma_z, int64_t* fwd, int64_t* bwd);
+GP_API gp_status gp_count_vox_evaluated(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, int64_t* fwd,
+                                        int64_t* bwd);
+
 /* Diagnostics of the last gp_render_slices / gp_render_backward / gp_voxelize
  * on ctx: number of (Gaussian, slice, tile) pairs binned and of pixel
  * evaluations issued (pairs x tile pixels). */
@@ -321,9 +349,16 @@ GP_API gp_status gp_batch_plan(gp_ctx* ctx, const gp_batch_item* items, int n, i
 GP_API gp_status gp_batch_run(gp_plan* plan, void* stream);
 /* Synchronises `stream`; GP_ERR_OVERFLOW if the last run outgrew the plan. */
 GP_API gp_status gp_batch_wait(gp_plan* plan, void* stream);
-/* Chosen configuration and memory of a plan (any pointer may be NULL). */
-GP_API gp_status gp_batch_info(gp_plan* plan, int64_t* pair_capacity, int* tile, int* fwd_chunk,
-                               int* bwd_chunk, int64_t* device_bytes);
+/* Chosen configuration and memory of a plan. */
+typedef struct {
+  int64_t pair_capacity;   /* binned (Gaussian, slice, tile) pairs the plan's buffers hold */
+  int64_t device_bytes;    /* device memory the plan owns */
+  int tile;                /* screen tile side */
+  int fwd_raster, bwd_raster;  /* GP_RASTER_BLOCK, GP_RASTER_ROWS or GP_RASTER_PIXELS */
+  int fwd_chunk, bwd_chunk;    /* block-culled form: Gaussians per staging round (else 0) */
+  int fwd_px, bwd_px;          /* per-thread form: pixels per thread (else 0) */
+} gp_batch_config;
+GP_API gp_status gp_batch_info(gp_plan* plan, gp_batch_config* out);
 GP_API gp_status gp_batch_destroy(gp_plan* plan);
 
 /* ---------------------------------------------------------------- codec

@@ -46,8 +46,10 @@ EXPORTS = (
     "gp_count_evals_view", "gp_adam_default", "gp_adam_state_floats", "gp_adam_init", "gp_adam_step",
     "gp_l1_dssim_grad", "gp_encode", "gp_decode", "gp_serve_load_encoded", "gp_count_vox_evals",
     "gp_fma_probe_mode", "gp_fma_probe_lane_fmas", "gp_check_enabled", "gp_check_selftest",
+    "gp_count_evaluated_view", "gp_count_vox_evaluated",
 )
 GP_REQ_SLICE, GP_REQ_STACK, GP_REQ_VOXELIZE = 0, 1, 2
+GP_RASTER_AUTO, GP_RASTER_BLOCK, GP_RASTER_ROWS, GP_RASTER_PIXELS = 0, 1, 2, 3
 GP_BATCH_AUTOTUNE = 1
 GP_NUM_PHASES = 8
 PHASES = ("bin", "fwd", "bwd", "bwd_pre", "loss", "vox_fwd", "vox_bwd", "opt")
@@ -62,7 +64,7 @@ class GPError(RuntimeError):
 class gp_config(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("deterministic", ctypes.c_int), ("exp_mode", ctypes.c_int),
                 ("tile", ctypes.c_int), ("fwd_px", ctypes.c_int), ("bwd_px", ctypes.c_int),
-                ("workspace_limit", ctypes.c_int64), ("reuse_bins", ctypes.c_int)]
+                ("workspace_limit", ctypes.c_int64), ("reuse_bins", ctypes.c_int), ("raster", ctypes.c_int)]
 
 
 class gp_set(ctypes.Structure):
@@ -91,6 +93,12 @@ class gp_batch_item(ctypes.Structure):
                 ("out", ctypes.c_void_p), ("target", ctypes.c_void_p), ("dL_dI", ctypes.c_void_p),
                 ("d_mu", ctypes.c_void_p), ("d_scale", ctypes.c_void_p), ("d_quat", ctypes.c_void_p),
                 ("d_alpha", ctypes.c_void_p), ("loss", ctypes.c_void_p), ("view", ctypes.c_void_p)]
+
+
+class gp_batch_config(ctypes.Structure):
+    _fields_ = [("pair_capacity", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("tile", ctypes.c_int),
+                ("fwd_raster", ctypes.c_int), ("bwd_raster", ctypes.c_int), ("fwd_chunk", ctypes.c_int),
+                ("bwd_chunk", ctypes.c_int), ("fwd_px", ctypes.c_int), ("bwd_px", ctypes.c_int)]
 
 
 class gp_codec_header(ctypes.Structure):
@@ -162,8 +170,7 @@ def _load():
         "gp_batch_plan": [P, ctypes.POINTER(gp_batch_item), I, I, ctypes.POINTER(P)],
         "gp_batch_run": [P, P],
         "gp_batch_wait": [P, P],
-        "gp_batch_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
-                          ctypes.POINTER(I64)],
+        "gp_batch_info": [P, ctypes.POINTER(gp_batch_config)],
         "gp_batch_destroy": [P],
         "gp_serve_open": [P, ctypes.POINTER(gp_serve_cfg), ctypes.POINTER(P)],
         "gp_serve_load_set": [P, SP, ctypes.POINTER(I)],
@@ -176,6 +183,9 @@ def _load():
         "gp_render_slices_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, P, P],
         "gp_render_backward_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, P, P, P, P, P, P],
         "gp_count_evals_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, ctypes.POINTER(I64)],
+        "gp_count_evaluated_view": [P, SP, ctypes.POINTER(gp_view), P, I, I, I, F, ctypes.POINTER(I64),
+                                    ctypes.POINTER(I64)],
+        "gp_count_vox_evaluated": [P, SP, I, I, I, ctypes.POINTER(I64), ctypes.POINTER(I64)],
         "gp_adam_default": [ctypes.POINTER(gp_adam_cfg)],
         "gp_l1_dssim_grad": [P, P, P, P, I, I, I, F, P, P, P],
         "gp_encode": [P, SP, I, ctypes.POINTER(gp_codec_header), P, P, P],
@@ -226,13 +236,15 @@ class Context:
     """Owns a gp_ctx (device workspace pool) on one CUDA device."""
 
     def __init__(self, device=0, eps=1e-6, deterministic=False, exp_mode=GP_EXP_POLY, tile=16,
-                 fwd_px=0, bwd_px=0, workspace_limit=0, reuse_bins=False):
+                 fwd_px=0, bwd_px=0, workspace_limit=0, reuse_bins=False, raster=None):
         cfg = gp_config()
         lib.gp_config_default(ctypes.byref(cfg))
         cfg.eps, cfg.deterministic, cfg.exp_mode = float(eps), int(bool(deterministic)), int(exp_mode)
         cfg.tile, cfg.fwd_px, cfg.bwd_px = int(tile), int(fwd_px), int(bwd_px)
         cfg.workspace_limit = int(workspace_limit)
         cfg.reuse_bins = int(bool(reuse_bins))
+        if raster is not None:
+            cfg.raster = int(raster)
         self.device = int(device)
         self.cfg = cfg
         h = ctypes.c_void_p()
@@ -476,12 +488,13 @@ class BatchPlan:
             raise GPError(st, "gp_batch_wait: " + lib.gp_last_error(self.ctx.h).decode(errors="replace"))
 
     def info(self):
-        cap, b = ctypes.c_int64(), ctypes.c_int64()
-        t, f, bw = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        self.ctx.check(lib.gp_batch_info(self.h, ctypes.byref(cap), ctypes.byref(t), ctypes.byref(f),
-                                         ctypes.byref(bw), ctypes.byref(b)), "gp_batch_info")
-        return {"pair_capacity": cap.value, "tile": t.value, "fwd_chunk": f.value, "bwd_chunk": bw.value,
-                "device_bytes": b.value}
+        c = gp_batch_config()
+        self.ctx.check(lib.gp_batch_info(self.h, ctypes.byref(c)), "gp_batch_info")
+        form = {GP_RASTER_BLOCK: "block", GP_RASTER_ROWS: "rows", GP_RASTER_PIXELS: "pixels"}
+        return {"pair_capacity": c.pair_capacity, "tile": c.tile,
+                "fwd_raster": form.get(c.fwd_raster, c.fwd_raster), "fwd_chunk": c.fwd_chunk, "fwd_px": c.fwd_px,
+                "bwd_raster": form.get(c.bwd_raster, c.bwd_raster), "bwd_chunk": c.bwd_chunk, "bwd_px": c.bwd_px,
+                "device_bytes": c.device_bytes}
 
     def close(self):
         if getattr(self, "h", None):
@@ -624,6 +637,30 @@ def gp_count_vox_evals(ctx, gs, X, Y, Z):
     out = ctypes.c_int64()
     ctx.check(lib.gp_count_vox_evals(ctx.h, ctypes.byref(gs.c()), X, Y, Z, ctypes.byref(out)), "gp_count_vox_evals")
     return int(out.value)
+
+
+def gp_count_evaluated(ctx, gs, z, H, W, sigma_z, axis=2, view=None):
+    """(forward, backward) pixels the context's default rasterisers evaluate for this render."""
+    z = _host_f32(z)
+    out, outb = ctypes.c_int64(), ctypes.c_int64()
+    if view is not None:
+        v = make_view(view)
+    else:
+        v = gp_view()
+        if lib.gp_view_from_axis(int(axis), ctypes.byref(v)) != GP_OK:
+            raise ValueError("axis must be 0, 1 or 2")
+    st = lib.gp_count_evaluated_view(ctx.h, ctypes.byref(gs.c()), ctypes.byref(v), z.ctypes.data_as(ctypes.c_void_p),
+                                     z.shape[0], H, W, float(sigma_z), ctypes.byref(out), ctypes.byref(outb))
+    ctx.check(st, "gp_count_evaluated_view")
+    return int(out.value), int(outb.value)
+
+
+def gp_count_vox_evaluated(ctx, gs, X, Y, Z):
+    """(forward, backward) voxels the context's default rasterisers evaluate for a voxelize."""
+    out, outb = ctypes.c_int64(), ctypes.c_int64()
+    ctx.check(lib.gp_count_vox_evaluated(ctx.h, ctypes.byref(gs.c()), X, Y, Z, ctypes.byref(out),
+                                         ctypes.byref(outb)), "gp_count_vox_evaluated")
+    return int(out.value), int(outb.value)
 
 
 def gp_exp2_eval(ctx, x, mode=GP_EXP_POLY, y=None, stream=None):

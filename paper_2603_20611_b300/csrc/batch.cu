@@ -14,8 +14,13 @@
 // bounds) and raises a flag that gp_batch_wait reports as GP_ERR_OVERFLOW.
 //
 // The autotuner (GP_BATCH_AUTOTUNE) times the plan's own workload for each tile
-// side (8, 16) and staging chunk (forward 64/128/256, backward 32/64/128
-// Gaussians per round) and keeps the fastest combination.
+// side (8, 16) and, for the forward and the backward separately, each
+// rasteriser form: block-culled (four warps per tile, 8 x 8 / 8 x 4 cells) at
+// each staging chunk (forward 64/128/256, backward 32/64/128 Gaussians per
+// round); row units (one warp per tile, 8-pixel row segments); and one thread
+// per pixel group at each number of pixels per thread (forward 1/2/4,
+// backward 2/4/8 on 16 x 16 tiles; 1/2 and 2 on 8 x 8), and keeps the fastest
+// combination.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -47,6 +52,9 @@ struct gp_plan {
   std::vector<View> views;  // per item, copied at plan time (item.view is not kept)
   int flags = 0;
   int tile = 16, fchunk = 128, bchunk = 64, ctas_f = 0, ctas_b = 0;
+  // forward / backward rasteriser form (GP_RASTER_BLOCK, _ROWS or _PIXELS) and, for the per-thread
+  // form, pixels per thread
+  int fform = GP_RASTER_BLOCK, bform = GP_RASTER_BLOCK, fpx = 0, bpx = 0;
   bool any_fwd = false, any_bwd = false, det = false;
   int n_gauss = 0;
   uint32_t n_keys = 0;
@@ -204,7 +212,13 @@ static gp_status enqueue_forward(gp_plan* p, cudaStream_t st) {
     return GP_OK;
   }
   GP_CUDAB(p, cudaMemsetAsync(p->work, 0, sizeof(unsigned), st), "memset work");
-  GP_CUDAB(p, launch_raster_fwd_batch(batch_view(p), p->tile, p->fchunk, p->ctas_f, p->c->cfg.exp_mode, p->rec, p->sv,
+  if (p->fform == GP_RASTER_PIXELS) {
+    GP_CUDAB(p, launch_raster_fwd_px_batch(batch_view(p), p->tile, p->fpx, p->c->cfg.exp_mode, p->rec, p->sv,
+                                           p->det ? p->emit_gid : nullptr, p->ranges, st),
+             "batch forward");
+    return GP_OK;
+  }
+  GP_CUDAB(p, launch_raster_fwd_batch(batch_view(p), p->fform == GP_RASTER_ROWS, p->tile, p->fchunk, p->ctas_f, p->c->cfg.exp_mode, p->rec, p->sv,
                                       p->det ? p->emit_gid : nullptr, p->ranges, p->work, st),
            "batch forward");
   return GP_OK;
@@ -227,7 +241,12 @@ static gp_status enqueue_backward(gp_plan* p, cudaStream_t st) {
   if (!p->det) GP_CUDAB(p, cudaMemsetAsync(p->accum, 0, (size_t)p->n_gauss * 10 * 4, st), "clear accumulators");
   if (p->cap > 0) {
     GP_CUDAB(p, cudaMemsetAsync(p->work + 1, 0, sizeof(unsigned), st), "memset work");
-    GP_CUDAB(p, launch_raster_bwd_batch(b, p->tile, p->bchunk, p->ctas_b, p->c->cfg.exp_mode, p->det, p->rec, p->sv,
+    if (p->bform == GP_RASTER_PIXELS)
+      GP_CUDAB(p, launch_raster_bwd_px_batch(b, p->tile, p->bpx, p->c->cfg.exp_mode, p->det, p->rec, p->sv,
+                                             p->det ? p->emit_gid : nullptr, p->ranges, p->accum, p->partial, st),
+               "batch backward");
+    else
+    GP_CUDAB(p, launch_raster_bwd_batch(b, p->bform == GP_RASTER_ROWS, p->tile, p->bchunk, p->ctas_b, p->c->cfg.exp_mode, p->det, p->rec, p->sv,
                                         p->det ? p->emit_gid : nullptr, p->ranges, p->accum, p->partial, p->work + 1, st),
              "batch backward");
   }
@@ -279,8 +298,10 @@ static gp_status alloc_pairs(gp_plan* p, uint32_t cap, uint32_t n_keys) {
 
 static void set_ctas(gp_plan* p) {
   const int sm = p->c->sm_count;
-  p->ctas_f = std::max(1, raster_batch_ctas_per_sm(p->tile, p->fchunk, false, p->c->cfg.exp_mode)) * sm;
-  p->ctas_b = std::max(1, raster_batch_ctas_per_sm(p->tile, p->bchunk, true, p->c->cfg.exp_mode)) * sm;
+  p->ctas_f = std::max(1, raster_batch_ctas_per_sm(p->fform == GP_RASTER_ROWS, p->tile, p->fchunk, false,
+                                                   p->c->cfg.exp_mode)) * sm;
+  p->ctas_b = std::max(1, raster_batch_ctas_per_sm(p->bform == GP_RASTER_ROWS, p->tile, p->bchunk, true,
+                                                   p->c->cfg.exp_mode)) * sm;
 }
 
 static gp_status capture(gp_plan* p) {
@@ -326,9 +347,29 @@ static double time_phase(gp_plan* p, F&& f, int reps) {
   return ms;
 }
 
+// One rasteriser configuration of a pass: form, staging chunk (block-culled)
+// or pixels per thread (per-thread).
+struct PassCfg {
+  int form, chunk, px;
+};
+
+static std::vector<PassCfg> pass_candidates(const gp_plan* p, bool backward) {
+  std::vector<PassCfg> c;
+  for (int ch : backward ? std::vector<int>{32, 64, 128} : std::vector<int>{64, 128, 256})
+    c.push_back({GP_RASTER_BLOCK, ch, 0});
+  if (p->c->cfg.exp_mode == GP_EXP_POLY_ROW) return c;  // block-culled only
+  c.push_back({GP_RASTER_ROWS, backward ? p->bchunk : p->fchunk, 0});
+  std::vector<int> pxs;
+  if (p->tile == 16) pxs = backward ? std::vector<int>{2, 4, 8} : std::vector<int>{1, 2, 4};
+  else pxs = backward ? std::vector<int>{2} : std::vector<int>{1, 2};
+  for (int px : pxs) c.push_back({GP_RASTER_PIXELS, backward ? p->bchunk : p->fchunk, px});
+  return c;
+}
+
 static gp_status autotune(gp_plan* p, const std::vector<int>& tiles, const std::vector<uint32_t>& caps) {
   double best = 1e30;
-  int bt = p->tile, bf = p->fchunk, bb = p->bchunk;
+  int bt = p->tile;
+  PassCfg bf{p->fform, p->fchunk, p->fpx}, bb{p->bform, p->bchunk, p->bpx};
   for (size_t t = 0; t < tiles.size(); ++t) {
     GP_TRYB(build_layout(p, tiles[t]));
     p->cap = caps[t];
@@ -336,32 +377,40 @@ static gp_status autotune(gp_plan* p, const std::vector<int>& tiles, const std::
     GP_TRYB(enqueue_binning(p, p->cap_stream));  // also leaves the binning for the timings below
     const double t_bin = time_phase(p, [&] { enqueue_binning(p, p->cap_stream); }, 2);
     double t_f = 0.0, t_b = 0.0;
-    int cf = p->fchunk, cb = p->bchunk;
+    PassCfg cf{p->fform, p->fchunk, p->fpx}, cb{p->bform, p->bchunk, p->bpx};
     if (p->any_fwd) {
       t_f = 1e30;
-      for (int ch : {64, 128, 256}) {
-        p->fchunk = ch;
+      for (const PassCfg& k : pass_candidates(p, false)) {
+        p->fform = k.form;
+        p->fchunk = k.chunk;
+        p->fpx = k.px;
         set_ctas(p);
         const double ms = time_phase(p, [&] { enqueue_forward(p, p->cap_stream); }, 2);
-        if (ms < t_f) { t_f = ms; cf = ch; }
+        if (ms < t_f) { t_f = ms; cf = k; }
       }
     }
     if (p->any_bwd) {
       enqueue_loss(p, p->cap_stream);
       t_b = 1e30;
-      for (int ch : {32, 64, 128}) {
-        p->bchunk = ch;
+      for (const PassCfg& k : pass_candidates(p, true)) {
+        p->bform = k.form;
+        p->bchunk = k.chunk;
+        p->bpx = k.px;
         set_ctas(p);
         const double ms = time_phase(p, [&] { enqueue_backward(p, p->cap_stream); }, 2);
-        if (ms < t_b) { t_b = ms; cb = ch; }
+        if (ms < t_b) { t_b = ms; cb = k; }
       }
     }
     const double tot = t_bin + t_f + t_b;
     if (tot < best) { best = tot; bt = tiles[t]; bf = cf; bb = cb; }
   }
   GP_CUDAB(p, cudaStreamSynchronize(p->cap_stream), "autotune");
-  p->fchunk = bf;
-  p->bchunk = bb;
+  p->fform = bf.form;
+  p->fchunk = bf.chunk;
+  p->fpx = bf.px;
+  p->bform = bb.form;
+  p->bchunk = bb.chunk;
+  p->bpx = bb.px;
   for (size_t t = 0; t < tiles.size(); ++t)
     if (tiles[t] == bt) p->cap = caps[t];
   return build_layout(p, bt);
@@ -407,6 +456,13 @@ static gp_status plan_build(gp_plan* p) {
   p->gstart[n] = (int)gs;
   p->n_gauss = (int)gs;
   p->det = c->cfg.deterministic != 0;
+  // forms without autotuning: as the plain calls choose them on slice planes
+  const bool rows_ok = c->cfg.exp_mode != GP_EXP_POLY_ROW;
+  p->fform = (c->cfg.raster != GP_RASTER_BLOCK && rows_ok) ? GP_RASTER_ROWS : GP_RASTER_BLOCK;
+  p->bform = (c->cfg.raster == GP_RASTER_ROWS && rows_ok) ? GP_RASTER_ROWS : GP_RASTER_BLOCK;
+  // a context with a per-thread rasteriser keeps it
+  if (c->cfg.fwd_px > 0) { p->fform = GP_RASTER_PIXELS; p->fpx = c->cfg.fwd_px; }
+  if (c->cfg.bwd_px > 0) { p->bform = GP_RASTER_PIXELS; p->bpx = c->cfg.bwd_px; }
   // fixed allocations
   GP_TRYB(plan_alloc(p, (void**)&p->d_args, sizeof(SliceArgs) * n));
   GP_TRYB(plan_alloc(p, (void**)&p->d_gstart, sizeof(int) * (n + 1)));
@@ -518,14 +574,17 @@ gp_status gp_batch_wait(gp_plan* p, void* stream) {
   return check_after(p->c, (cudaStream_t)stream);
 }
 
-gp_status gp_batch_info(gp_plan* p, int64_t* pair_capacity, int* tile, int* fwd_chunk, int* bwd_chunk,
-                        int64_t* device_bytes) {
-  if (!p) return GP_ERR_ARG;
-  if (pair_capacity) *pair_capacity = p->cap;
-  if (tile) *tile = p->tile;
-  if (fwd_chunk) *fwd_chunk = p->fchunk;
-  if (bwd_chunk) *bwd_chunk = p->bchunk;
-  if (device_bytes) *device_bytes = p->bytes;
+gp_status gp_batch_info(gp_plan* p, gp_batch_config* out) {
+  if (!p || !out) return GP_ERR_ARG;
+  out->pair_capacity = p->cap;
+  out->device_bytes = p->bytes;
+  out->tile = p->tile;
+  out->fwd_raster = p->fform;
+  out->bwd_raster = p->bform;
+  out->fwd_chunk = p->fform == GP_RASTER_BLOCK ? p->fchunk : 0;
+  out->bwd_chunk = p->bform == GP_RASTER_BLOCK ? p->bchunk : 0;
+  out->fwd_px = p->fform == GP_RASTER_PIXELS ? p->fpx : 0;
+  out->bwd_px = p->bform == GP_RASTER_PIXELS ? p->bpx : 0;
   return GP_OK;
 }
 

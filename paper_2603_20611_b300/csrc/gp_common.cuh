@@ -92,6 +92,137 @@ __device__ __forceinline__ float2 pair_exp2(float2 C2, float2 B2, float2 A2, flo
 }
 
 
+
+// ------------------------------------------------------------ row units
+// Culling cells are widened by this many pixels so that rounding only ever
+// adds cells (an extra cell adds pixels where every term is below eps).
+constexpr float kCellTol = 1e-3f;
+
+// Rows [lo, hi] (tile-relative, lo > hi when none) whose pixel-centre segment
+// x in [xa, xb] (tile-relative) the ellipse d^T C d <= k2 meets; (mx, my) the
+// tile-relative centre, rx / ry its half-extents, inv00 = 1 / C00, inv11 =
+// 1 / C11.  At dx from the centre the ellipse's vertical chord is centred on
+// -(C01 / C11) dx with half-height h(dx) = sqrt((k2 / C11)(1 - dx^2 / rx^2)).
+// The upper edge -(C01/C11) dx + h(dx) is concave, so over the strip it is
+// highest at the strip point nearest the ellipse's topmost point, dx_t =
+// -(C01 / C00) ry; the lower edge, convex, is lowest nearest -dx_t.  The range
+// is widened by kCellTol so that rounding only ever adds rows; that widening
+// also covers the approximate reciprocal and square roots (a few ulp).
+__device__ __forceinline__ void band_rows(float C01, float inv00, float inv11, float rx, float ry, float k2,
+                                          float mx, float my, float xa, float xb, int nrows, int& lo, int& hi) {
+  const float u0 = xa - mx, u1 = xb - mx;
+  lo = 1;
+  hi = 0;
+  if (!(u0 <= rx + kCellTol && u1 >= -rx - kCellTol)) return;
+  const float s = C01 * inv11;
+  const float kk = k2 * inv11;
+  const float irx2 = __fdividef(1.0f, rx * rx);
+  const float xt = -C01 * inv00 * ry;
+  const float xtop = fminf(fmaxf(xt, u0), u1), xbot = fminf(fmaxf(-xt, u0), u1);
+  const float ttop = kk * fmaf(-xtop * xtop, irx2, 1.0f), tbot = kk * fmaf(-xbot * xbot, irx2, 1.0f);
+  const float htop = ttop > 0.0f ? ttop * rsqrtf(ttop) : 0.0f;
+  const float hbot = tbot > 0.0f ? tbot * rsqrtf(tbot) : 0.0f;
+  const float ymax = fmaf(-s, xtop, htop), ymin = fmaf(-s, xbot, -hbot);
+  // pixel row y has its centres at height y + 0.5
+  lo = max(0, __float2int_ru(my + ymin - 0.5f - kCellTol));
+  hi = min(nrows - 1, __float2int_rd(my + ymax - 0.5f + kCellTol));
+}
+
+// Cells of a TILE x TILE tile (bands of BH pixel rows by columns of 8 pixels)
+// whose pixel centres the culling ellipse d^T C d <= k2 touches, as a bit mask:
+// band b, column c is bit b * (TILE / 8) + c for 8-row bands (the 8 x 8
+// blocks) and 2 (b / 2 * (TILE / 8) + c) + b % 2 for 4-row bands (the 8 x 4
+// half-blocks, so the two halves of a block are adjacent bits).  Over a band's
+// pixel-centre heights the ellipse spans x in [xmin, xmax]: its chord at height
+// dy (from the centre) is centred on -s dy, s = C01 / C00, with half-width
+// sqrt((k2 - D dy^2) / C00), D = C11 - C01^2 / C00 = k2 / ry^2 (ry the
+// ellipse's half-height), and its right (left) end is furthest out at the
+// height dyt of the rightmost point (-dyt), clamped to the band.  A cell is
+// touched iff its column's pixel centres meet [xmin, xmax]; the interval is
+// widened by 1e-3 pixel so that rounding only ever adds cells (an extra cell
+// adds pixels where every term is below eps).
+//   r2 = (C00, C01, C11, rx), r3 = (ry, valid, 1/C00, 1/C11); (mx, my) the
+//   tile-relative centre.
+template <int TILE, int BH>
+__device__ __forceinline__ unsigned ellipse_cells(float4 r2, float4 r3, float mx, float my, float k2) {
+  const float ry = r3.x, inv00 = r3.z;
+  const float s = r2.y * inv00;
+  const float D = k2 / (ry * ry);
+  const float dyt = -r2.y * r3.w * r2.w;
+  unsigned m = 0u;
+#pragma unroll
+  for (int b = 0; b < TILE / BH; ++b) {
+    const float dya = fmaxf((float)(b * BH) + 0.5f - my, -ry);
+    const float dyb = fminf((float)(b * BH + BH) - 0.5f - my, ry);
+    if (dya <= dyb) {
+      const float dM = fminf(fmaxf(dyt, dya), dyb), dm = fminf(fmaxf(-dyt, dya), dyb);
+      const float xmax = fmaf(-s, dM, mx) + sqrtf(fmaxf((k2 - D * dM * dM) * inv00, 0.0f)) + kCellTol;
+      const float xmin = fmaf(-s, dm, mx) - sqrtf(fmaxf((k2 - D * dm * dm) * inv00, 0.0f)) - kCellTol;
+#pragma unroll
+      for (int c = 0; c < TILE / 8; ++c) {
+        const int bit = BH == 8 ? b * (TILE / 8) + c : 2 * ((b >> 1) * (TILE / 8) + c) + (b & 1);
+        if (xmin <= (float)(8 * c) + 7.5f && xmax >= (float)(8 * c) + 0.5f) m |= 1u << bit;
+      }
+    }
+  }
+  return m;
+}
+
+// The row units of one (Gaussian, plane, tile): bit c * TILE + y is set when
+// the culling ellipse meets the pixel-centre segment of column band c (pixels
+// 8c .. 8c + 7) of tile row y.  r0, r2, r3: the Gaussian's record; d its
+// offset from the plane; (mx, my) its tile-relative centre on the plane;
+// nrows / nbands: the tile's rows and column bands inside the image.  On a
+// voxelizer plane the ellipse is the plane's section of the 3D one, d^T C d <=
+// k2 - delta^2 / Sigma_zz (its extents scaled to match).
+template <int TILE>
+__device__ __forceinline__ unsigned row_unit_mask(float4 r0, float4 r2, float4 r3, float d, float mx, float my,
+                                                  float k2, bool vox, int nrows, int nbands) {
+  float ke = k2, rx = r2.w, ry = r3.x;
+  if (vox) {
+    ke = k2 - d * d * r0.w;
+    if (!(ke > 0.0f)) return 0u;
+    const float f = sqrtf(ke / k2);
+    rx *= f;
+    ry *= f;
+  }
+  unsigned mask = 0u;
+#pragma unroll
+  for (int c = 0; c < TILE / 8; ++c) {
+    if (c >= nbands) break;
+    int lo, hi;
+    band_rows(r2.y, r3.z, r3.w, rx, ry, ke, mx, my, (float)(8 * c) + 0.5f, (float)(8 * c) + 7.5f, nrows, lo, hi);
+    if (lo <= hi) mask |= ((0xffffffffu >> (31 - (hi - lo))) << lo) << (c * TILE);
+  }
+  return mask;
+}
+
+// The culling cells of one (Gaussian, plane, tile) for the block-culled
+// rasterisers: ellipse_cells with, on a voxelizer plane, the plane's section
+// of the 3D ellipsoid (k2 - delta^2 / Sigma_zz, extents scaled to match).
+template <int TILE, int BH>
+__device__ __forceinline__ unsigned plane_cells(float4 r0, float4 r2, float4 r3, float d, float mx, float my,
+                                                float k2, bool vox) {
+  if (vox) {
+    const float k2e = k2 - d * d * r0.w;
+    if (!(k2e > 0.0f)) return 0u;
+    const float f = sqrtf(k2e / k2);
+    return ellipse_cells<TILE, BH>(make_float4(r2.x, r2.y, r2.z, r2.w * f), make_float4(r3.x * f, r3.y, r3.z, r3.w),
+                                   mx, my, k2e);
+  }
+  return ellipse_cells<TILE, BH>(r2, r3, mx, my, k2);
+}
+// Exponentials 2^(base + B q) of a couple's two pixels (base = A + C q^2): the
+// mirrored pixels q and -q of a row share base, so one packed instruction
+// finishes each exponent.
+template <int EXPM>
+__device__ __forceinline__ float2 couple_exp2(float2 B2, float2 q, float2 base) {
+  float2 e = __ffma2_rn(B2, q, base);
+  e.x = fmaxf(e.x, kExpFloor);
+  e.y = fmaxf(e.y, kExpFloor);
+  return exp2_sel2<EXPM>(e);
+}
+
 // ---------------------------------------------------------------- records
 // Per-Gaussian slice-invariant record of the slice renderer (camera frame of the
 // slice axis), 64 bytes:

@@ -36,54 +36,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "gp_check.cuh"
 #include "gp_common.cuh"
 #include "gp_internal.h"
 #include "slice.cuh"
 
 namespace gp {
-
-// Cells of a TILE x TILE tile (bands of BH pixel rows by columns of 8 pixels)
-// whose pixel centres the culling ellipse d^T C d <= k2 touches, as a bit mask:
-// band b, column c is bit b * (TILE / 8) + c for 8-row bands (the 8 x 8
-// blocks) and 2 (b / 2 * (TILE / 8) + c) + b % 2 for 4-row bands (the 8 x 4
-// half-blocks, so the two halves of a block are adjacent bits).  Over a band's
-// pixel-centre heights the ellipse spans x in [xmin, xmax]: its chord at height
-// dy (from the centre) is centred on -s dy, s = C01 / C00, with half-width
-// sqrt((k2 - D dy^2) / C00), D = C11 - C01^2 / C00 = k2 / ry^2 (ry the
-// ellipse's half-height), and its right (left) end is furthest out at the
-// height dyt of the rightmost point (-dyt), clamped to the band.  A cell is
-// touched iff its column's pixel centres meet [xmin, xmax]; the interval is
-// widened by 1e-3 pixel so that rounding only ever adds cells (an extra cell
-// adds pixels where every term is below eps).
-//   r2 = (C00, C01, C11, rx), r3 = (ry, valid, 1/C00, 1/C11); (mx, my) the
-//   tile-relative centre.
-constexpr float kCellTol = 1e-3f;
-
-template <int TILE, int BH>
-__device__ __forceinline__ unsigned ellipse_cells(float4 r2, float4 r3, float mx, float my, float k2) {
-  const float ry = r3.x, inv00 = r3.z;
-  const float s = r2.y * inv00;
-  const float D = k2 / (ry * ry);
-  const float dyt = -r2.y * r3.w * r2.w;
-  unsigned m = 0u;
-#pragma unroll
-  for (int b = 0; b < TILE / BH; ++b) {
-    const float dya = fmaxf((float)(b * BH) + 0.5f - my, -ry);
-    const float dyb = fminf((float)(b * BH + BH) - 0.5f - my, ry);
-    if (dya <= dyb) {
-      const float dM = fminf(fmaxf(dyt, dya), dyb), dm = fminf(fmaxf(-dyt, dya), dyb);
-      const float xmax = fmaf(-s, dM, mx) + sqrtf(fmaxf((k2 - D * dM * dM) * inv00, 0.0f)) + kCellTol;
-      const float xmin = fmaf(-s, dm, mx) - sqrtf(fmaxf((k2 - D * dm * dm) * inv00, 0.0f)) - kCellTol;
-#pragma unroll
-      for (int c = 0; c < TILE / 8; ++c) {
-        const int bit = BH == 8 ? b * (TILE / 8) + c : 2 * ((b >> 1) * (TILE / 8) + c) + (b & 1);
-        if (xmin <= (float)(8 * c) + 7.5f && xmax >= (float)(8 * c) + 0.5f) m |= 1u << bit;
-      }
-    }
-  }
-  return m;
-}
 
 // Staging of one Gaussian for one (slice, tile):
 //   s0 = (mu_2d,x - x0, mu_2d,y - y0, a~, C11)
@@ -105,14 +65,7 @@ __device__ __forceinline__ unsigned stage_blk(const SliceRec* __restrict__ rec, 
   s0 = make_float4(mxr, myr, r1.z * w, C11);
   s1 = make_float4(-0.5f * kLog2e * C00, -kLog2e * C01, -0.5f * kLog2e * C11, C00);
   s2 = make_float4(d, w, C01, 0.0f);
-  if (vox) {
-    const float k2e = k2 - d * d * r0.w;
-    if (!(k2e > 0.0f)) return 0u;
-    const float f = sqrtf(k2e / k2);
-    return ellipse_cells<TILE, BH>(make_float4(r2.x, r2.y, r2.z, r2.w * f), make_float4(r3.x * f, r3.y, r3.z, r3.w),
-                                   mxr, myr, k2e);
-  }
-  return ellipse_cells<TILE, BH>(r2, r3, mxr, myr, k2);
+  return plane_cells<TILE, BH>(r0, r2, r3, d, mxr, myr, k2, vox);
 }
 
 // ---- row factorisation (GP_EXP_POLY_ROW)
@@ -638,7 +591,42 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
   }
 }
 
+}  // namespace gp
+
+#include "raster_rows.cuh"
+
+namespace gp {
+
 // ------------------------------------------------------------ plain kernels
+// Row-unit kernels (the default for per-pixel exponentials): one warp per tile.
+constexpr int kRowCtasPerSm = 24;
+
+template <int TILE, int EXPM>
+__global__ void __launch_bounds__(32, kRowCtasPerSm) k_raster_fwd_rows(SliceArgs a, const SliceRec* __restrict__ rec,
+                                                                       const uint32_t* __restrict__ vals,
+                                                                       const uint32_t* __restrict__ emit_gid,
+                                                                       const uint2* __restrict__ ranges) {
+  if constexpr (TILE == 16) {
+    __shared__ OwnFwdSmem sm;
+    fwd_tile_owner<EXPM>(a, blockIdx.x, rec, vals, emit_gid, ranges, sm);
+  } else {
+    __shared__ RowFwdSmem<TILE> sm;
+    fwd_tile_rows<TILE, EXPM>(a, blockIdx.x, rec, vals, emit_gid, ranges, sm);
+  }
+}
+
+template <int TILE, int EXPM, bool DET>
+__global__ void __launch_bounds__(32, kRowCtasPerSm) k_raster_bwd_rows(SliceArgs a, const SliceRec* __restrict__ rec,
+                                                                       const uint32_t* __restrict__ vals,
+                                                                       const uint32_t* __restrict__ emit_gid,
+                                                                       const uint2* __restrict__ ranges,
+                                                                       float* __restrict__ accum,
+                                                                       float4* __restrict__ partial) {
+  __shared__ RowBwdSmem<TILE> sm;
+  bwd_tile_rows<TILE, EXPM, DET>(a, blockIdx.x, rec, vals, emit_gid, ranges, accum, partial, sm);
+}
+
+// Block-culled kernels (the row-factored exponential's): four warps per 16 x 16 tile.
 template <int TILE, int CH, int EXPM, bool DENSE>
 __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? (DENSE ? 8 : 12) : 32) k_raster_fwd_blk(
     SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
@@ -662,15 +650,6 @@ __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? 9 :
 // by binary search over the items' key starts.
 constexpr int KEY_CHUNK = 8;
 
-template <typename T>
-__device__ __forceinline__ int find_item_k(const T* __restrict__ t, int n, T x) {
-  int lo = 0, hi = n;
-  while (hi - lo > 1) {
-    const int m = (lo + hi) >> 1;
-    if (t[m] <= x) lo = m; else hi = m;
-  }
-  return lo;
-}
 
 template <int TILE, int CH, int EXPM>
 __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? 12 : 32) k_raster_fwd_persist(
@@ -719,7 +698,84 @@ __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? (ro
   }
 }
 
+// Persistent row-unit kernels: one warp per CTA takes chunks of keys.
+template <int TILE, int EXPM>
+__global__ void __launch_bounds__(32, kRowCtasPerSm) k_raster_fwd_rows_persist(
+    BatchItems b, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, unsigned* __restrict__ work) {
+  using Smem = typename std::conditional<TILE == 16, OwnFwdSmem, RowFwdSmem<TILE>>::type;
+  __shared__ Smem sm;
+  for (;;) {
+    uint32_t k0 = 0;
+    if (threadIdx.x == 0) k0 = atomicAdd(work, (unsigned)KEY_CHUNK);
+    k0 = __shfl_sync(0xffffffffu, k0, 0);
+    if (k0 >= b.n_keys) break;
+    const uint32_t k1 = min(k0 + (uint32_t)KEY_CHUNK, b.n_keys);
+    for (uint32_t key = k0; key < k1; ++key) {
+      const int it = find_item_k(b.kstart, b.n_items, key);
+      const SliceArgs a = b.args[it];
+      if (a.out) {
+        if constexpr (TILE == 16)
+          fwd_tile_owner<EXPM>(a, (int)(key - b.kstart[it]), rec, vals, emit_gid, ranges, sm);
+        else
+          fwd_tile_rows<TILE, EXPM>(a, (int)(key - b.kstart[it]), rec, vals, emit_gid, ranges, sm);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+template <int TILE, int EXPM, bool DET>
+__global__ void __launch_bounds__(32, kRowCtasPerSm) k_raster_bwd_rows_persist(
+    BatchItems b, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, float* __restrict__ accum,
+    float4* __restrict__ partial, unsigned* __restrict__ work) {
+  __shared__ RowBwdSmem<TILE> sm;
+  for (;;) {
+    uint32_t k0 = 0;
+    if (threadIdx.x == 0) k0 = atomicAdd(work, (unsigned)KEY_CHUNK);
+    k0 = __shfl_sync(0xffffffffu, k0, 0);
+    if (k0 >= b.n_keys) break;
+    const uint32_t k1 = min(k0 + (uint32_t)KEY_CHUNK, b.n_keys);
+    for (uint32_t key = k0; key < k1; ++key) {
+      const int it = find_item_k(b.kstart, b.n_items, key);
+      const SliceArgs a = b.args[it];
+      if (a.dL_dI) bwd_tile_rows<TILE, EXPM, DET>(a, (int)(key - b.kstart[it]), rec, vals, emit_gid, ranges, accum,
+                                                  partial, sm);
+      __syncwarp();
+    }
+  }
+}
+
 // ------------------------------------------------------------ launchers
+template <int TILE>
+static cudaError_t fwd_rows(const SliceArgs& a, int exp_mode, const SliceRec* rec, const uint32_t* vals,
+                            const uint32_t* emit_gid, const uint2* ranges, cudaStream_t st) {
+  const unsigned tiles = (unsigned)((int64_t)a.S * a.TX * a.TY);
+  if (exp_mode == GP_EXP_HW)
+    k_raster_fwd_rows<TILE, GP_EXP_HW><<<tiles, 32, 0, st>>>(a, rec, vals, emit_gid, ranges);
+  else
+    k_raster_fwd_rows<TILE, GP_EXP_POLY><<<tiles, 32, 0, st>>>(a, rec, vals, emit_gid, ranges);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int TILE>
+static cudaError_t bwd_rows(const SliceArgs& a, int exp_mode, bool det, const SliceRec* rec, const uint32_t* vals,
+                            const uint32_t* emit_gid, const uint2* ranges, float* accum, float4* partial,
+                            cudaStream_t st) {
+  const unsigned g = (unsigned)((int64_t)a.S * a.TX * a.TY);
+  if (exp_mode == GP_EXP_HW) {
+    if (det) k_raster_bwd_rows<TILE, GP_EXP_HW, true><<<g, 32, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+    else k_raster_bwd_rows<TILE, GP_EXP_HW, false><<<g, 32, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+  } else {
+    if (det) k_raster_bwd_rows<TILE, GP_EXP_POLY, true><<<g, 32, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+    else k_raster_bwd_rows<TILE, GP_EXP_POLY, false><<<g, 32, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <int TILE, int CH, bool DENSE>
 static cudaError_t fwd_blk(const SliceArgs& a, int exp_mode, const SliceRec* rec, const uint32_t* vals,
                            const uint32_t* emit_gid, const uint2* ranges, cudaStream_t st) {
@@ -735,13 +791,23 @@ static cudaError_t fwd_blk(const SliceArgs& a, int exp_mode, const SliceRec* rec
   return cudaGetLastError();
 }
 
-cudaError_t launch_raster_fwd_blocked(const SliceArgs& a, int exp_mode, const SliceRec* rec, const uint32_t* vals,
-                                      const uint32_t* emit_gid, const uint2* ranges, float* out, cudaStream_t st,
-                                      uint32_t pairs) {
+bool raster_rows_form(const SliceArgs& a, int raster, int exp_mode, bool backward) {
+  if (exp_mode == GP_EXP_POLY_ROW) return false;
+  return raster == GP_RASTER_ROWS || (raster == GP_RASTER_AUTO && (!backward || a.vox != 0));
+}
+
+cudaError_t launch_raster_fwd_blocked(const SliceArgs& a, int raster, int exp_mode, const SliceRec* rec,
+                                      const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges, float* out,
+                                      cudaStream_t st, uint32_t pairs) {
   const int64_t tiles = (int64_t)a.S * a.TX * a.TY;
   if (tiles == 0) return cudaSuccess;
   SliceArgs b = a;
   b.out = out;
+  if (raster_rows_form(a, raster, exp_mode, false)) {
+    if (a.tile == 16) return fwd_rows<16>(b, exp_mode, rec, vals, emit_gid, ranges, st);
+    if (a.tile == 8) return fwd_rows<8>(b, exp_mode, rec, vals, emit_gid, ranges, st);
+    return cudaErrorInvalidValue;
+  }
   if (a.tile == 16) {
     if ((int64_t)pairs >= (int64_t)kDenseTilePairs * tiles)
       return fwd_blk<16, 128, true>(b, exp_mode, rec, vals, emit_gid, ranges, st);
@@ -771,12 +837,17 @@ static cudaError_t bwd_blk(const SliceArgs& a, int exp_mode, bool det, const Sli
   return cudaGetLastError();
 }
 
-cudaError_t launch_raster_bwd_blocked(const SliceArgs& a, int exp_mode, bool det, const SliceRec* rec,
+cudaError_t launch_raster_bwd_blocked(const SliceArgs& a, int raster, int exp_mode, bool det, const SliceRec* rec,
                                       const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
                                       const float* dL_dI, float* accum, float4* partial, cudaStream_t st) {
   if ((int64_t)a.S * a.TX * a.TY == 0) return cudaSuccess;
   SliceArgs b = a;
   b.dL_dI = dL_dI;
+  if (raster_rows_form(a, raster, exp_mode, true)) {
+    if (a.tile == 16) return bwd_rows<16>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
+    if (a.tile == 8) return bwd_rows<8>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
+    return cudaErrorInvalidValue;
+  }
   if (a.tile == 16) return bwd_blk<16, 128>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
   if (a.tile == 8) return bwd_blk<8, 32>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
   return cudaErrorInvalidValue;
@@ -816,10 +887,21 @@ static cudaError_t bwd_persist(const BatchItems& b, int ctas, int exp_mode, bool
   return cudaGetLastError();
 }
 
-cudaError_t launch_raster_fwd_batch(const BatchItems& b, int tile, int chunk, int ctas, int exp_mode,
+cudaError_t launch_raster_fwd_batch(const BatchItems& b, bool rows, int tile, int chunk, int ctas, int exp_mode,
                                     const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
                                     const uint2* ranges, unsigned* work, cudaStream_t st) {
   if (b.n_keys == 0) return cudaSuccess;
+  if (rows && exp_mode != GP_EXP_POLY_ROW) {
+#define GP_FWD_R(T, E) \
+  if (tile == T && exp_mode == E) {                                                              \
+    k_raster_fwd_rows_persist<T, E><<<ctas, 32, 0, st>>>(b, rec, vals, emit_gid, ranges, work);  \
+    note_launch();                                                                               \
+    return cudaGetLastError();                                                                   \
+  }
+    GP_FWD_R(16, GP_EXP_POLY) GP_FWD_R(16, GP_EXP_HW) GP_FWD_R(8, GP_EXP_POLY) GP_FWD_R(8, GP_EXP_HW)
+#undef GP_FWD_R
+    return cudaErrorInvalidValue;
+  }
 #define GP_FWD_P(T, C) \
   if (tile == T && chunk == C) return fwd_persist<T, C>(b, ctas, exp_mode, rec, vals, emit_gid, ranges, work, st);
   GP_FWD_P(16, 64) GP_FWD_P(16, 128) GP_FWD_P(16, 256) GP_FWD_P(8, 64) GP_FWD_P(8, 128) GP_FWD_P(8, 256)
@@ -827,11 +909,25 @@ cudaError_t launch_raster_fwd_batch(const BatchItems& b, int tile, int chunk, in
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_raster_bwd_batch(const BatchItems& b, int tile, int chunk, int ctas, int exp_mode, bool det,
+cudaError_t launch_raster_bwd_batch(const BatchItems& b, bool rows, int tile, int chunk, int ctas, int exp_mode, bool det,
                                     const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
                                     const uint2* ranges, float* accum, float4* partial, unsigned* work,
                                     cudaStream_t st) {
   if (b.n_keys == 0) return cudaSuccess;
+  if (rows && exp_mode != GP_EXP_POLY_ROW) {
+#define GP_BWD_R(T, E)                                                                                         \
+  if (tile == T && exp_mode == E) {                                                                            \
+    if (det)                                                                                                   \
+      k_raster_bwd_rows_persist<T, E, true><<<ctas, 32, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work);  \
+    else                                                                                                       \
+      k_raster_bwd_rows_persist<T, E, false><<<ctas, 32, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work); \
+    note_launch();                                                                                             \
+    return cudaGetLastError();                                                                                 \
+  }
+    GP_BWD_R(16, GP_EXP_POLY) GP_BWD_R(16, GP_EXP_HW) GP_BWD_R(8, GP_EXP_POLY) GP_BWD_R(8, GP_EXP_HW)
+#undef GP_BWD_R
+    return cudaErrorInvalidValue;
+  }
 #define GP_BWD_P(T, C)                                                                                       \
   if (tile == T && chunk == C)                                                                               \
     return bwd_persist<T, C>(b, ctas, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, work, st);
@@ -841,10 +937,23 @@ cudaError_t launch_raster_bwd_batch(const BatchItems& b, int tile, int chunk, in
 }
 
 // Resident CTAs per SM of a persistent kernel (occupancy calculator).
-int raster_batch_ctas_per_sm(int tile, int chunk, bool backward, int exp_mode) {
+int raster_batch_ctas_per_sm(bool rows, int tile, int chunk, bool backward, int exp_mode) {
   int n = 0;
   cudaError_t e = cudaErrorInvalidValue;
   const bool row = exp_mode == GP_EXP_POLY_ROW;
+  if (rows && !row) {  // the row-unit kernels (one warp per CTA; the chunk is fixed at 32 Gaussians)
+    if (tile == 16)
+      e = backward ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_bwd_rows_persist<16, GP_EXP_POLY, false>, 32, 0)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd_rows_persist<16, GP_EXP_POLY>, 32, 0);
+    else if (tile == 8)
+      e = backward ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_bwd_rows_persist<8, GP_EXP_POLY, false>, 32, 0)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd_rows_persist<8, GP_EXP_POLY>, 32, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return n;
+  }
 #define GP_OCC_F(T, C)                                                                                       \
   if (!backward && tile == T && chunk == C)                                                                  \
     e = row ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd_persist<T, C, GP_EXP_POLY_ROW>, \

@@ -389,6 +389,7 @@ gp_status gp_config_default(gp_config* cfg) {
   cfg->bwd_px = 0;
   cfg->workspace_limit = 0;
   cfg->reuse_bins = 0;
+  cfg->raster = GP_RASTER_AUTO;
   return GP_OK;
 }
 
@@ -406,6 +407,8 @@ gp_status gp_create(gp_ctx** out, int device, const gp_config* cfg) {
     if (c.workspace_limit < 0) return GP_ERR_ARG;
     if (c.fwd_px < 0 || (c.fwd_px > 0 && !fwd_px_supported(c.tile, c.fwd_px))) return GP_ERR_ARG;
     if (c.bwd_px < 0 || (c.bwd_px > 0 && !bwd_px_supported(c.tile, c.bwd_px))) return GP_ERR_ARG;
+    if (c.raster != GP_RASTER_AUTO && c.raster != GP_RASTER_BLOCK && c.raster != GP_RASTER_ROWS) return GP_ERR_ARG;
+    if (c.exp_mode == GP_EXP_POLY_ROW && c.raster == GP_RASTER_ROWS) return GP_ERR_ARG;
   }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -475,7 +478,7 @@ static gp_status render_impl(gp_ctx* ctx, const gp_set* set, const View& view, c
   }
   {
     PhaseTimer timer(c, vox ? GP_PHASE_VOX_FWD : GP_PHASE_FWD, st);
-    GP_CUDA(c, launch_raster_fwd(a, fwd_px(c), c->cfg.exp_mode, (const SliceRec*)c->b.rec.ptr, vals,
+    GP_CUDA(c, launch_raster_fwd(a, fwd_px(c), c->cfg.raster, c->cfg.exp_mode, (const SliceRec*)c->b.rec.ptr, vals,
                                  c->bin_gid_vals ? nullptr : (const uint32_t*)c->b.emit_gid.ptr,
                                  (const uint2*)c->b.ranges.ptr, out, st, P),
             "raster forward");
@@ -515,7 +518,7 @@ static gp_status backward_impl(gp_ctx* ctx, const gp_set* set, const View& view,
   }
   if (P > 0) {
     PhaseTimer timer(c, vox ? GP_PHASE_VOX_BWD : GP_PHASE_BWD, st);
-    GP_CUDA(c, launch_raster_bwd(a, bwd_px(c), c->cfg.exp_mode, det, (const SliceRec*)b.rec.ptr, vals,
+    GP_CUDA(c, launch_raster_bwd(a, bwd_px(c), c->cfg.raster, c->cfg.exp_mode, det, (const SliceRec*)b.rec.ptr, vals,
                                  c->bin_gid_vals ? nullptr : (const uint32_t*)b.emit_gid.ptr,
                                  (const uint2*)b.ranges.ptr, dL_dI,
                                  (float*)b.accum.ptr, (float4*)b.partial.ptr, st),
@@ -558,8 +561,11 @@ gp_status gp_mse_grad(gp_ctx* ctx, const float* I, const float* T, const int* t_
   return cuda_err(c, cudaGetLastError(), "mse");
 }
 
+// units: count the pixels the context's default rasterisers evaluate,
+// evals[0] forward and evals[1] backward, instead of the algorithmic
+// evaluations (evals[0]).
 static gp_status count_impl(gp_ctx* ctx, const gp_set* set, const View& view, const float* z, int S, int H,
-                            int W, float sigma_z, int64_t* evals, bool vox = false) {
+                            int W, float sigma_z, int64_t* evals, bool vox = false, bool units = false) {
   Ctx* c = &ctx->impl;
   GP_TRY(check_set(c, set));
   GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
@@ -569,11 +575,18 @@ static gp_status count_impl(gp_ctx* ctx, const gp_set* set, const View& view, co
   const uint32_t* vals = nullptr;
   GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals, vox));
   unsigned long long* d = (unsigned long long*)c->b.total.ptr + 1;
-  GP_CUDA(c, cudaMemsetAsync(d, 0, 8, st), "count");
-  if (set->n > 0 && S > 0) launch_count_evals(a, (const SliceRec*)c->b.rec.ptr, d, st);
-  GP_CUDA(c, cudaMemcpyAsync(c->h_total, d, 8, cudaMemcpyDeviceToHost, st), "count readback");
+  GP_CUDA(c, cudaMemsetAsync(d, 0, 16, st), "count");
+  if (set->n > 0 && S > 0) {
+    if (units)
+      launch_count_units(a, (const SliceRec*)c->b.rec.ptr, raster_rows_form(a, c->cfg.raster, c->cfg.exp_mode, false),
+                         raster_rows_form(a, c->cfg.raster, c->cfg.exp_mode, true), d, st);
+    else
+      launch_count_evals(a, (const SliceRec*)c->b.rec.ptr, d, st);
+  }
+  GP_CUDA(c, cudaMemcpyAsync(c->h_total, d, 16, cudaMemcpyDeviceToHost, st), "count readback");
   GP_CUDA(c, cudaStreamSynchronize(st), "count readback");
-  *evals = (int64_t)*c->h_total;
+  evals[0] = (int64_t)c->h_total[0];
+  if (units) evals[1] = (int64_t)c->h_total[1];
   return GP_OK;
 }
 
@@ -638,6 +651,19 @@ gp_status gp_count_evals_view(gp_ctx* ctx, const gp_set* set, const gp_view* vie
   return count_impl(ctx, set, v, z, S, H, W, sigma_z, evals);
 }
 
+gp_status gp_count_evaluated_view(gp_ctx* ctx, const gp_set* set, const gp_view* view, const float* z, int S,
+                                  int H, int W, float sigma_z, int64_t* fwd, int64_t* bwd) {
+  if (!ctx || !fwd || !bwd) return GP_ERR_ARG;
+  View v;
+  if (!check_view(view, &v))
+    return set_err(&ctx->impl, GP_ERR_ARG, "view must be finite with R orthonormal to 1e-3");
+  int64_t e[2] = {0, 0};
+  GP_TRY(count_impl(ctx, set, v, z, S, H, W, sigma_z, e, false, true));
+  *fwd = e[0];
+  *bwd = e[1];
+  return GP_OK;
+}
+
 gp_status gp_exp2_eval(gp_ctx* ctx, const float* x, float* y, int64_t n, int mode, void* stream) {
   if (!ctx) return GP_ERR_ARG;
   Ctx* c = &ctx->impl;
@@ -680,6 +706,20 @@ gp_status gp_count_vox_evals(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z
   View v;
   axis_view(2, &v);
   return count_impl(ctx, set, v, z.data(), Z, Y, X, 0.0f, evals, true);
+}
+
+gp_status gp_count_vox_evaluated(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, int64_t* fwd, int64_t* bwd) {
+  if (!ctx || !fwd || !bwd) return GP_ERR_ARG;
+  Ctx* c = &ctx->impl;
+  std::vector<float> z;
+  GP_TRY(vox_planes(c, X, Y, Z, z));
+  View v;
+  axis_view(2, &v);
+  int64_t e[2] = {0, 0};
+  GP_TRY(count_impl(ctx, set, v, z.data(), Z, Y, X, 0.0f, e, true, true));
+  *fwd = e[0];
+  *bwd = e[1];
+  return GP_OK;
 }
 
 gp_status gp_voxelize_backward(gp_ctx* ctx, const gp_set* set, int X, int Y, int Z, const float* dL_dV,

@@ -639,20 +639,19 @@ __device__ __forceinline__ void stage_gaussian(const SliceRec* __restrict__ rec,
   c11 = r2.z;
 }
 
+// Per-thread forward of one (slice, tile) key of item a (local_key counts the
+// item's own keys; ranges are batch-wide).
 template <int TILE, int PX, int EXPM>
-__global__ void __launch_bounds__(TILE* TILE / PX) k_raster_fwd(SliceArgs a, const SliceRec* __restrict__ rec,
-                                                               const uint32_t* __restrict__ vals,
-                                                               const uint32_t* __restrict__ emit_gid,
-                                                               const uint2* __restrict__ ranges,
-                                                               float* __restrict__ out) {
+__device__ __forceinline__ void fwd_tile_px(const SliceArgs& a, int local_key, const SliceRec* __restrict__ rec,
+                                            const uint32_t* __restrict__ vals, const uint32_t* __restrict__ emit_gid,
+                                            const uint2* __restrict__ ranges, float* __restrict__ out) {
   constexpr int NT = TILE * TILE / PX;
   constexpr int SEGS = TILE / PX;
   __shared__ float4 s0[FWD_CHUNK], s1[FWD_CHUNK];
   const int T = a.TX * a.TY;
-  const int tile_id = blockIdx.x;
-  const int s = tile_id / T, t = tile_id - s * T;
+  const int s = local_key / T, t = local_key - s * T;
   const int ty = t / a.TX, tx = t - ty * a.TX;
-  const uint2 rg = ranges[tile_id];
+  const uint2 rg = ranges[a.key_base + (uint32_t)local_key];
   const int row = threadIdx.x / SEGS, seg = threadIdx.x - row * SEGS;
   const float pyr = (float)row + 0.5f;
   const float px0 = (float)(seg * PX) + 0.5f;
@@ -698,6 +697,26 @@ __global__ void __launch_bounds__(TILE* TILE / PX) k_raster_fwd(SliceArgs a, con
   }
 }
 
+template <int TILE, int PX, int EXPM>
+__global__ void __launch_bounds__(TILE* TILE / PX) k_raster_fwd(SliceArgs a, const SliceRec* __restrict__ rec,
+                                                               const uint32_t* __restrict__ vals,
+                                                               const uint32_t* __restrict__ emit_gid,
+                                                               const uint2* __restrict__ ranges,
+                                                               float* __restrict__ out) {
+  fwd_tile_px<TILE, PX, EXPM>(a, blockIdx.x, rec, vals, emit_gid, ranges, out);
+}
+
+template <int TILE, int PX, int EXPM>
+__global__ void __launch_bounds__(TILE* TILE / PX) k_raster_fwd_px_batch(BatchItems b, const SliceRec* __restrict__ rec,
+                                                                        const uint32_t* __restrict__ vals,
+                                                                        const uint32_t* __restrict__ emit_gid,
+                                                                        const uint2* __restrict__ ranges) {
+  const uint32_t key = blockIdx.x;
+  const int it = find_item_k(b.kstart, b.n_items, key);
+  const SliceArgs a = b.args[it];
+  if (a.out) fwd_tile_px<TILE, PX, EXPM>(a, (int)(key - b.kstart[it]), rec, vals, emit_gid, ranges, a.out);
+}
+
 template <int TILE, int PX>
 static cudaError_t fwd_dispatch(const SliceArgs& a, int exp_mode, const SliceRec* rec, const uint32_t* vals,
                                 const uint32_t* emit_gid, const uint2* ranges, float* out, cudaStream_t st) {
@@ -712,14 +731,39 @@ static cudaError_t fwd_dispatch(const SliceArgs& a, int exp_mode, const SliceRec
   return cudaGetLastError();
 }
 
+template <int TILE, int PX>
+static cudaError_t fwd_px_batch(const BatchItems& b, int exp_mode, const SliceRec* rec, const uint32_t* vals,
+                                const uint32_t* emit_gid, const uint2* ranges, cudaStream_t st) {
+  constexpr int NT = TILE * TILE / PX;
+  if (exp_mode == GP_EXP_HW)
+    k_raster_fwd_px_batch<TILE, PX, GP_EXP_HW><<<b.n_keys, NT, 0, st>>>(b, rec, vals, emit_gid, ranges);
+  else
+    k_raster_fwd_px_batch<TILE, PX, GP_EXP_POLY><<<b.n_keys, NT, 0, st>>>(b, rec, vals, emit_gid, ranges);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raster_fwd_px_batch(const BatchItems& b, int tile, int px, int exp_mode, const SliceRec* rec,
+                                       const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
+                                       cudaStream_t st) {
+  if (b.n_keys == 0) return cudaSuccess;
+  if (exp_mode == GP_EXP_POLY_ROW) return cudaErrorInvalidValue;
+  if (tile == 16 && px == 1) return fwd_px_batch<16, 1>(b, exp_mode, rec, vals, emit_gid, ranges, st);
+  if (tile == 16 && px == 2) return fwd_px_batch<16, 2>(b, exp_mode, rec, vals, emit_gid, ranges, st);
+  if (tile == 16 && px == 4) return fwd_px_batch<16, 4>(b, exp_mode, rec, vals, emit_gid, ranges, st);
+  if (tile == 8 && px == 1) return fwd_px_batch<8, 1>(b, exp_mode, rec, vals, emit_gid, ranges, st);
+  if (tile == 8 && px == 2) return fwd_px_batch<8, 2>(b, exp_mode, rec, vals, emit_gid, ranges, st);
+  return cudaErrorInvalidValue;
+}
+
 bool fwd_px_supported(int tile, int px) {
   return px == 0 || (tile == 16 ? (px == 1 || px == 2 || px == 4) : (tile == 8 ? (px == 1 || px == 2) : false));
 }
 
-cudaError_t launch_raster_fwd(const SliceArgs& a, int px, int exp_mode, const SliceRec* rec,
+cudaError_t launch_raster_fwd(const SliceArgs& a, int px, int raster, int exp_mode, const SliceRec* rec,
                               const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
                               float* out, cudaStream_t st, uint32_t pairs) {
-  if (px == 0) return launch_raster_fwd_blocked(a, exp_mode, rec, vals, emit_gid, ranges, out, st, pairs);
+  if (px == 0) return launch_raster_fwd_blocked(a, raster, exp_mode, rec, vals, emit_gid, ranges, out, st, pairs);
   if (a.tile == 16) {
     switch (px) {
       case 1: return fwd_dispatch<16, 1>(a, exp_mode, rec, vals, emit_gid, ranges, out, st);
@@ -753,10 +797,10 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 template <int TILE, int PX, int EXPM, bool DET>
-__global__ void __launch_bounds__(TILE* TILE / PX) k_raster_bwd(
-    SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
-    const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges,
-    const float* __restrict__ dL_dI, float* __restrict__ accum, float4* __restrict__ partial) {
+__device__ __forceinline__ void bwd_tile_px(const SliceArgs& a, int local_key, const SliceRec* __restrict__ rec,
+                                            const uint32_t* __restrict__ vals, const uint32_t* __restrict__ emit_gid,
+                                            const uint2* __restrict__ ranges, const float* __restrict__ dL_dI,
+                                            float* __restrict__ accum, float4* __restrict__ partial) {
   constexpr int NT = TILE * TILE / PX;
   constexpr int SEGS = TILE / PX;
   constexpr int NW = NT / 32;
@@ -766,10 +810,9 @@ __global__ void __launch_bounds__(TILE* TILE / PX) k_raster_bwd(
   __shared__ uint32_t sg[CH];          // Gaussian id
   __shared__ float sp[NW][6][CH];      // per-warp moments
   const int T = a.TX * a.TY;
-  const int tile_id = blockIdx.x;
-  const int s = tile_id / T, t = tile_id - s * T;
+  const int s = local_key / T, t = local_key - s * T;
   const int ty = t / a.TX, tx = t - ty * a.TX;
-  const uint2 rg = ranges[tile_id];
+  const uint2 rg = ranges[a.key_base + (uint32_t)local_key];
   if (rg.y <= rg.x) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int row = threadIdx.x / SEGS, seg = threadIdx.x - row * SEGS;
@@ -873,6 +916,27 @@ __global__ void __launch_bounds__(TILE* TILE / PX) k_raster_bwd(
   }
 }
 
+template <int TILE, int PX, int EXPM, bool DET>
+__global__ void __launch_bounds__(TILE* TILE / PX) k_raster_bwd(
+    SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges,
+    const float* __restrict__ dL_dI, float* __restrict__ accum, float4* __restrict__ partial) {
+  bwd_tile_px<TILE, PX, EXPM, DET>(a, blockIdx.x, rec, vals, emit_gid, ranges, dL_dI, accum, partial);
+}
+
+template <int TILE, int PX, int EXPM, bool DET>
+__global__ void __launch_bounds__(TILE* TILE / PX) k_raster_bwd_px_batch(
+    BatchItems b, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, float* __restrict__ accum,
+    float4* __restrict__ partial) {
+  const uint32_t key = blockIdx.x;
+  const int it = find_item_k(b.kstart, b.n_items, key);
+  const SliceArgs a = b.args[it];
+  if (a.dL_dI)
+    bwd_tile_px<TILE, PX, EXPM, DET>(a, (int)(key - b.kstart[it]), rec, vals, emit_gid, ranges, a.dL_dI, accum,
+                                     partial);
+}
+
 template <int TILE, int PX>
 static cudaError_t bwd_dispatch(const SliceArgs& a, int exp_mode, bool det, const SliceRec* rec,
                                 const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
@@ -892,15 +956,45 @@ static cudaError_t bwd_dispatch(const SliceArgs& a, int exp_mode, bool det, cons
   return cudaGetLastError();
 }
 
+template <int TILE, int PX>
+static cudaError_t bwd_px_batch(const BatchItems& b, int exp_mode, bool det, const SliceRec* rec,
+                                const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges, float* accum,
+                                float4* partial, cudaStream_t st) {
+  constexpr int NT = TILE * TILE / PX;
+  const unsigned g = b.n_keys;
+  if (exp_mode == GP_EXP_HW) {
+    if (det) k_raster_bwd_px_batch<TILE, PX, GP_EXP_HW, true><<<g, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial);
+    else k_raster_bwd_px_batch<TILE, PX, GP_EXP_HW, false><<<g, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial);
+  } else {
+    if (det) k_raster_bwd_px_batch<TILE, PX, GP_EXP_POLY, true><<<g, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial);
+    else k_raster_bwd_px_batch<TILE, PX, GP_EXP_POLY, false><<<g, NT, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial);
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raster_bwd_px_batch(const BatchItems& b, int tile, int px, int exp_mode, bool det,
+                                       const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
+                                       const uint2* ranges, float* accum, float4* partial, cudaStream_t st) {
+  if (b.n_keys == 0) return cudaSuccess;
+  if (exp_mode == GP_EXP_POLY_ROW) return cudaErrorInvalidValue;
+  if (tile == 16 && px == 2) return bwd_px_batch<16, 2>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
+  if (tile == 16 && px == 4) return bwd_px_batch<16, 4>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
+  if (tile == 16 && px == 8) return bwd_px_batch<16, 8>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
+  if (tile == 8 && px == 2) return bwd_px_batch<8, 2>(b, exp_mode, det, rec, vals, emit_gid, ranges, accum, partial, st);
+  return cudaErrorInvalidValue;
+}
+
 bool bwd_px_supported(int tile, int px) {
   return px == 0 || (tile == 16 ? (px == 2 || px == 4 || px == 8) : (tile == 8 ? px == 2 : false));
 }
 
-cudaError_t launch_raster_bwd(const SliceArgs& a, int px, int exp_mode, bool det, const SliceRec* rec,
+cudaError_t launch_raster_bwd(const SliceArgs& a, int px, int raster, int exp_mode, bool det, const SliceRec* rec,
                               const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
                               const float* dL_dI, float* accum, float4* partial, cudaStream_t st) {
   if (px == 0)
-    return launch_raster_bwd_blocked(a, exp_mode, det, rec, vals, emit_gid, ranges, dL_dI, accum, partial, st);
+    return launch_raster_bwd_blocked(a, raster, exp_mode, det, rec, vals, emit_gid, ranges, dL_dI, accum, partial,
+                                     st);
   if (a.tile == 16) {
     switch (px) {
       case 2: return bwd_dispatch<16, 2>(a, exp_mode, det, rec, vals, emit_gid, ranges, dL_dI, accum, partial, st);
@@ -1181,6 +1275,54 @@ __global__ void __launch_bounds__(PRE_THREADS) k_count_evals(SliceArgs a, const 
 void launch_count_evals(const SliceArgs& a, const SliceRec* rec, unsigned long long* out, cudaStream_t st) {
   if (a.n <= 0) return;
   k_count_evals<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, out);
+  note_launch();
+}
+
+// Pixels the default rasterisers evaluate, out[0] forward and out[1]
+// backward: row units (rows): 8 per (Gaussian, plane, tile, column band,
+// pixel row) whose segment of pixel centres the culling ellipse meets;
+// block-culled: 64 per 8 x 8 block (forward) and 32 per 8 x 4 half-block
+// (backward) the ellipse touches -- the same tests the kernels stage with.
+template <int TILE>
+__global__ void __launch_bounds__(PRE_THREADS) k_count_units(SliceArgs a, const SliceRec* __restrict__ rec,
+                                                             bool rows_f, bool rows_b,
+                                                             unsigned long long* __restrict__ out) {
+  int i = blockIdx.x * PRE_THREADS + threadIdx.x;
+  unsigned long long cnt = 0, cntb = 0;
+  if (i < a.n) {
+    const SliceRec r = rec[i];
+    for_each_pair(a, r, [&](int j, int tile) {
+      const int ty = tile / a.TX, tx = tile - ty * a.TX;
+      const float x0 = (float)(tx * TILE), y0 = (float)(ty * TILE);
+      const float d = r.r0.z - a.zs[j];
+      const float mx = (r.r0.x - x0) - r.r1.x * d, my = (r.r0.y - y0) - r.r1.y * d;
+      const int nrows = min(TILE, a.H - ty * TILE), nbands = min(TILE / 8, (a.W - tx * TILE + 7) >> 3);
+      const unsigned long long units =
+          (rows_f || rows_b)
+              ? 8ull * (unsigned)__popc(row_unit_mask<TILE>(r.r0, r.r2, r.r3, d, mx, my, a.k2, a.vox != 0, nrows,
+                                                             nbands))
+              : 0ull;
+      cnt += rows_f ? units : 64ull * (unsigned)__popc(plane_cells<TILE, 8>(r.r0, r.r2, r.r3, d, mx, my, a.k2,
+                                                                            a.vox != 0));
+      cntb += rows_b ? units : 32ull * (unsigned)__popc(plane_cells<TILE, 4>(r.r0, r.r2, r.r3, d, mx, my, a.k2,
+                                                                             a.vox != 0));
+    });
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    cntb += __shfl_xor_sync(0xffffffffu, cntb, o);
+  }
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+  if ((threadIdx.x & 31) == 0 && cntb) atomicAdd(out + 1, cntb);
+}
+
+void launch_count_units(const SliceArgs& a, const SliceRec* rec, bool rows_f, bool rows_b, unsigned long long* out,
+                        cudaStream_t st) {
+  if (a.tile == 8)
+    k_count_units<8><<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, rows_f, rows_b, out);
+  else
+    k_count_units<16><<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, rows_f, rows_b, out);
   note_launch();
 }
 

@@ -57,14 +57,34 @@ void launch_det_reduce_n(int n, const unsigned long long* offsets, const unsigne
                          const float4* partial, float* accum, unsigned long long cap, cudaStream_t st);
 // Persistent block-culled rasterisers over every (item, slice, tile) key of a
 // batch: CTAs take chunks of keys from *work (zeroed before each launch).
-cudaError_t launch_raster_fwd_batch(const BatchItems& b, int tile, int chunk, int ctas, int exp_mode,
+cudaError_t launch_raster_fwd_batch(const BatchItems& b, bool rows, int tile, int chunk, int ctas, int exp_mode,
                                     const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
                                     const uint2* ranges, unsigned* work, cudaStream_t st);
-cudaError_t launch_raster_bwd_batch(const BatchItems& b, int tile, int chunk, int ctas, int exp_mode, bool det,
+cudaError_t launch_raster_bwd_batch(const BatchItems& b, bool rows, int tile, int chunk, int ctas, int exp_mode, bool det,
                                     const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
                                     const uint2* ranges, float* accum, float4* partial, unsigned* work,
                                     cudaStream_t st);
-int raster_batch_ctas_per_sm(int tile, int chunk, bool backward, int exp_mode);
+int raster_batch_ctas_per_sm(bool rows, int tile, int chunk, bool backward, int exp_mode);
+
+// The item of batch key x: the last k with t[k] <= x (t ascending, t[0] = 0).
+template <typename T>
+__device__ __forceinline__ int find_item_k(const T* __restrict__ t, int n, T x) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int m = (lo + hi) >> 1;
+    if (t[m] <= x) lo = m; else hi = m;
+  }
+  return lo;
+}
+
+// Per-thread rasterisers over every (item, slice, tile) key of a batch (one
+// CTA per key): px pixels per thread, as gp_config.fwd_px / bwd_px.
+cudaError_t launch_raster_fwd_px_batch(const BatchItems& b, int tile, int px, int exp_mode, const SliceRec* rec,
+                                       const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
+                                       cudaStream_t st);
+cudaError_t launch_raster_bwd_px_batch(const BatchItems& b, int tile, int px, int exp_mode, bool det,
+                                       const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
+                                       const uint2* ranges, float* accum, float4* partial, cudaStream_t st);
 
 // K-pre: records + per-Gaussian pair counts.
 void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st);
@@ -78,12 +98,14 @@ void launch_ranges(const uint32_t* keys, const unsigned long long* n_dev, uint32
 // K-fwd.
 // pairs: the binned (Gaussian, slice, tile) pairs, which choose the occupancy
 // of the default forward (see launch_raster_fwd_blocked).
-cudaError_t launch_raster_fwd(const SliceArgs& a, int px, int exp_mode, const SliceRec* rec,
+// px > 0: the per-thread kernel; px = 0: the default kernels of form `raster`
+// (GP_RASTER_*).
+cudaError_t launch_raster_fwd(const SliceArgs& a, int px, int raster, int exp_mode, const SliceRec* rec,
                               const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
                               float* out, cudaStream_t st, uint32_t pairs);
 // K-bwd-raster; atomic mode adds into accum [n][10] (zeroed), deterministic mode
 // writes per-pair partials [pairs][8].
-cudaError_t launch_raster_bwd(const SliceArgs& a, int px, int exp_mode, bool deterministic,
+cudaError_t launch_raster_bwd(const SliceArgs& a, int px, int raster, int exp_mode, bool deterministic,
                               const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
                               const uint2* ranges, const float* dL_dI, float* accum, float4* partial,
                               cudaStream_t st);
@@ -100,6 +122,10 @@ int mse_tmp_floats(int S, int64_t HW);
 // Algorithmic evaluation count (pixels inside the culling ellipse), added into *out.
 void launch_count_evals(const SliceArgs& a, const SliceRec* rec, unsigned long long* out,
                         cudaStream_t st);
+// Pixels the default rasterisers of the given form evaluate, added into out[0]
+// (forward) and out[1] (backward).
+void launch_count_units(const SliceArgs& a, const SliceRec* rec, bool rows_f, bool rows_b, unsigned long long* out,
+                        cudaStream_t st);
 void launch_exp2_eval(const float* x, float* y, int64_t n, int mode, cudaStream_t st);
 
 // Block-culled rasterisers (raster.cu), the default for 16 x 16 tiles.  The
@@ -107,10 +133,14 @@ void launch_exp2_eval(const float* x, float* y, int64_t n, int mode, cudaStream_
 // when the tiles hold kDenseTilePairs or more pairs on average, else at 12
 // (sparse tiles, as on voxelizer planes, are latency-bound).
 constexpr uint32_t kDenseTilePairs = 48;
-cudaError_t launch_raster_fwd_blocked(const SliceArgs& a, int exp_mode, const SliceRec* rec, const uint32_t* vals,
+// Row units when raster is GP_RASTER_ROWS, or GP_RASTER_AUTO for the forward
+// and for the backward on voxelizer planes (a.vox), with a per-pixel
+// exponential; block-culled otherwise.
+bool raster_rows_form(const SliceArgs& a, int raster, int exp_mode, bool backward);
+cudaError_t launch_raster_fwd_blocked(const SliceArgs& a, int raster, int exp_mode, const SliceRec* rec, const uint32_t* vals,
                                       const uint32_t* emit_gid, const uint2* ranges, float* out, cudaStream_t st,
                                       uint32_t pairs);
-cudaError_t launch_raster_bwd_blocked(const SliceArgs& a, int exp_mode, bool det, const SliceRec* rec,
+cudaError_t launch_raster_bwd_blocked(const SliceArgs& a, int raster, int exp_mode, bool det, const SliceRec* rec,
                                       const uint32_t* vals, const uint32_t* emit_gid, const uint2* ranges,
                                       const float* dL_dI, float* accum, float4* partial, cudaStream_t st);
 

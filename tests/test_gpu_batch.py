@@ -53,6 +53,7 @@ def test_batch_matches_plain_and_oracle(autotune):
     plan.wait()
     info = plan.info()
     assert info["tile"] in (8, 16) and info["pair_capacity"] > 0
+    assert info["fwd_raster"] in ("block", "rows", "pixels") and info["bwd_raster"] in ("block", "rows", "pixels")
     plain = B.Context(0, tile=info["tile"])
     for k, (it, g) in enumerate(zip(items, meta)):
         ref_img = B.gp_render_slices(plain, it["gs"], it["z"], it["H"], it["W"], it["sigma_z"], it["axis"])
@@ -172,4 +173,50 @@ def test_batched_workload_full_size_sampled():
                                     bi.sigma_z, it["dL_dI"].cpu().numpy())
         sub = [t[torch.from_numpy(sel).long().cuda()] for t in it["grads"]]
         assert_grads_close(sub, og, f"batched item {k} grads")
+    plan.close()
+
+
+def test_batch_row_units_match_plain_row_units_and_oracle():
+    """A plan of a row-unit context (no autotuning) runs the persistent row-unit
+    rasterisers; its images and gradients equal the plain row-unit calls'
+    bitwise (same per-tile lists and summation order) and the oracle's."""
+    ctx = B.Context(0, raster=B.GP_RASTER_ROWS)
+    items, meta = _items(seed=11, n=5)
+    plan = B.BatchPlan(ctx, items)
+    plan.run()
+    plan.wait()
+    info = plan.info()
+    assert info["fwd_raster"] == "rows" and info["bwd_raster"] == "rows"
+    plain = B.Context(0, raster=B.GP_RASTER_ROWS)
+    for k, (it, g) in enumerate(zip(items, meta)):
+        ref_img = B.gp_render_slices(plain, it["gs"], it["z"], it["H"], it["W"], it["sigma_z"], it["axis"])
+        assert torch.equal(it["out"], ref_img), k
+        o = oracle.render(g.mu, g.scale, g.quat, g.alpha, it["z"], it["H"], it["W"], it["sigma_z"], axis=it["axis"])
+        assert_forward_close(np32(it["out"]), o, f"batch item {k}")
+        og = oracle.render_backward(g.mu, g.scale, g.quat, g.alpha, it["z"], it["H"], it["W"], it["sigma_z"],
+                                    it["dL_dI"].cpu().numpy(), axis=it["axis"])
+        assert_grads_close(it["grads"], og, f"batch item {k}")
+    plan.close()
+
+
+def test_batch_per_thread_forms_match_plain_calls_and_oracle():
+    """A plan of a context with per-thread rasterisers (2 pixels per thread
+    forward, 4 backward) runs them over every batch key; images equal the plain
+    per-thread calls' bitwise and both passes meet the oracle's parity bars."""
+    ctx = B.Context(0, fwd_px=2, bwd_px=4)
+    items, meta = _items(seed=12, n=4)
+    plan = B.BatchPlan(ctx, items)
+    plan.run()
+    plan.wait()
+    info = plan.info()
+    assert (info["fwd_raster"], info["fwd_px"], info["bwd_raster"], info["bwd_px"]) == ("pixels", 2, "pixels", 4)
+    plain = B.Context(0, fwd_px=2, bwd_px=4)
+    for k, (it, g) in enumerate(zip(items, meta)):
+        ref_img = B.gp_render_slices(plain, it["gs"], it["z"], it["H"], it["W"], it["sigma_z"], it["axis"])
+        assert torch.equal(it["out"], ref_img), k
+        o = oracle.render(g.mu, g.scale, g.quat, g.alpha, it["z"], it["H"], it["W"], it["sigma_z"], axis=it["axis"])
+        assert_forward_close(np32(it["out"]), o, f"batch item {k}")
+        og = oracle.render_backward(g.mu, g.scale, g.quat, g.alpha, it["z"], it["H"], it["W"], it["sigma_z"],
+                                    it["dL_dI"].cpu().numpy(), axis=it["axis"])
+        assert_grads_close(it["grads"], og, f"batch item {k}")
     plan.close()

@@ -2,7 +2,8 @@
 set sizes from 1 to 500 Gaussians, images from 1 x 1 to 70 x 70 (never tile
 multiples by construction), 1 to 6 planes anywhere in and beyond the volume,
 sigma_z from 0.3 to 6, scale modifiers, all three axes and oblique views, both
-tile sizes, the three exponentials and both backward modes.
+tile sizes, the three exponentials, both backward modes and both rasteriser
+forms (odd cases: row units).
 
 Every case checks the forward and every gradient.  The device culls terms
 below eps = 1e-6 of their pair (the culling reading), the oracle culls none,
@@ -57,7 +58,8 @@ def _oblique(rng):
 
 
 def _run(g, z, H, W, cfg, view, G, eps):
-    c = B.Context(0, tile=cfg["tile"], exp_mode=cfg["exp"], deterministic=cfg["det"], eps=eps)
+    c = B.Context(0, tile=cfg["tile"], exp_mode=cfg["exp"], deterministic=cfg["det"], eps=eps,
+                  raster=cfg["raster"])
     gs = dev_set(g, cfg["mod"])
     Gd = torch.from_numpy(G).cuda()
     if cfg["view"] < 3:
@@ -82,6 +84,8 @@ def _within_bars(ref, gref, b, gb):
 @pytest.mark.parametrize("k", range(N_CASES))
 def test_random_configuration(k):
     g, z, H, W, cfg, rng = _case(k)
+    # odd cases take the row-unit rasterisers, even ones the default forms
+    cfg["raster"] = B.GP_RASTER_ROWS if (k % 2 and cfg["exp"] != B.GP_EXP_POLY_ROW) else B.GP_RASTER_AUTO
     o = (g.mu, g.scale, g.quat, g.alpha)
     G = synth.random_field(9200 + k, (len(z), H, W))
     if cfg["view"] < 3:
