@@ -139,8 +139,8 @@ __device__ __forceinline__ void band_rows(float C01, float inv00, float inv11, f
 // ellipse's half-height), and its right (left) end is furthest out at the
 // height dyt of the rightmost point (-dyt), clamped to the band.  A cell is
 // touched iff its column's pixel centres meet [xmin, xmax]; the interval is
-// widened by 1e-3 pixel so that rounding only ever adds cells (an extra cell
-// adds pixels where every term is below eps).
+// widened by 1e-3 pixel so that rounding and the approximate square roots only
+// ever add cells (an extra cell adds pixels where every term is below eps).
 //   r2 = (C00, C01, C11, rx), r3 = (ry, valid, 1/C00, 1/C11); (mx, my) the
 //   tile-relative centre.
 template <int TILE, int BH>
@@ -156,8 +156,9 @@ __device__ __forceinline__ unsigned ellipse_cells(float4 r2, float4 r3, float mx
     const float dyb = fminf((float)(b * BH + BH) - 0.5f - my, ry);
     if (dya <= dyb) {
       const float dM = fminf(fmaxf(dyt, dya), dyb), dm = fminf(fmaxf(-dyt, dya), dyb);
-      const float xmax = fmaf(-s, dM, mx) + sqrtf(fmaxf((k2 - D * dM * dM) * inv00, 0.0f)) + kCellTol;
-      const float xmin = fmaf(-s, dm, mx) - sqrtf(fmaxf((k2 - D * dm * dm) * inv00, 0.0f)) - kCellTol;
+      const float tM = (k2 - D * dM * dM) * inv00, tm = (k2 - D * dm * dm) * inv00;
+      const float xmax = fmaf(-s, dM, mx) + (tM > 0.0f ? tM * rsqrtf(tM) : 0.0f) + kCellTol;
+      const float xmin = fmaf(-s, dm, mx) - (tm > 0.0f ? tm * rsqrtf(tm) : 0.0f) - kCellTol;
 #pragma unroll
       for (int c = 0; c < TILE / 8; ++c) {
         const int bit = BH == 8 ? b * (TILE / 8) + c : 2 * ((b >> 1) * (TILE / 8) + c) + (b & 1);

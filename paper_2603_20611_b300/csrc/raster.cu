@@ -489,9 +489,10 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
               const float2 q = make_float2(qa, qb), q2 = make_float2(qa * qa, qb * qb);
               const float2 GX = k == 0 ? make_float2(gx.x, gx.y) : make_float2(gx.z, gx.w);
               const float2 GY = k == 0 ? make_float2(gy.x, gy.y) : make_float2(gy.z, gy.w);
-              // e(-q) = (C q - B) q + A
-              const float2 Y = __fmul2_rn(GY, pair_exp2<EXPM>(C2, Bn2, A2, q));
-              const float2 XY = __ffma2_rn(GX, pair_exp2<EXPM>(C2, B2, A2, q), Y);
+              // e(+-q) = (A + C q^2) +- B q
+              const float2 base = __ffma2_rn(C2, q2, A2);
+              const float2 Y = __fmul2_rn(GY, couple_exp2<EXPM>(Bn2, q, base));
+              const float2 XY = __ffma2_rn(GX, couple_exp2<EXPM>(B2, q, base), Y);
               if (r == 3 && k == 0) {
                 P0 = XY;
                 P1 = __fmul2_rn(q, XY);
