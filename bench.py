@@ -586,7 +586,7 @@ def run_native(args, rank, world):
 
 # ------------------------------------------------------------ batched workload
 
-def batched_comparison(steps, warmup):
+def batched_comparison(steps, warmup, n_sets=64):
     """64 uneven sets (1k-200k Gaussians, 128^2-1024^2 slices, 8-64 planes,
     sigma_z in [1, 6]) forward + backward against seeded upstream gradients:
     one autotuned graph launch per step against 64 plain render + backward
@@ -601,7 +601,7 @@ def batched_comparison(steps, warmup):
     gen.manual_seed(4004)
     t0 = time.perf_counter()
     items, evals = [], 0
-    for bi in synth.batched():
+    for bi in synth.batched(n_sets=n_sets):
         gs = B.GaussianSet.from_numpy(bi.gs, dev)
         S = len(bi.z)
         it = {"gs": gs, "z": bi.z, "H": bi.H, "W": bi.W, "sigma_z": bi.sigma_z, "axis": 2,
@@ -645,7 +645,7 @@ def batched_comparison(steps, warmup):
     info = plan.info()
     plan.close()
     work_gb = sum(2 * it["out"].numel() * 4 for it in items) / 1e9  # images + dL/dI
-    return {"workload": "64 sets, N log-uniform in [1k, 200k], square slices of side in {128, 256, 512, 1024}, "
+    return {"workload": f"{n_sets} sets, N log-uniform in [1k, 200k], square slices of side in {{128, 256, 512, 1024}}, "
                         "8-64 planes, sigma_z ~ U(1, 6), fwd + bwd against seeded dL/dI; one autotuned graph "
                         "launch per step",
             "n_items": len(items), "n_gaussians": int(sum(it["gs"].n for it in items)),
@@ -663,7 +663,8 @@ def batched_comparison(steps, warmup):
 def run_batched(args):
     import torch
     torch.cuda.set_device(0)
-    r = batched_comparison(args.steps, args.warmup)
+    # --case small: the first 12 of the sets (a few GB on the device, for profiler captures)
+    r = batched_comparison(args.steps, args.warmup, n_sets=12 if args.case == "small" else 64)
     line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",

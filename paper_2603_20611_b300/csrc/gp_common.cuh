@@ -216,13 +216,24 @@ __device__ __forceinline__ unsigned plane_cells(float4 r0, float4 r2, float4 r3,
 // Exponentials 2^(base + B q) of a couple's two pixels (base = A + C q^2): the
 // mirrored pixels q and -q of a row share base, so one packed instruction
 // finishes each exponent.
-template <int EXPM>
+// FLOOR = false drops the floor where the caller knows every exponent is above
+// kExpUnfloored.
+template <int EXPM, bool FLOOR = true>
 __device__ __forceinline__ float2 couple_exp2(float2 B2, float2 q, float2 base) {
   float2 e = __ffma2_rn(B2, q, base);
-  e.x = fmaxf(e.x, kExpFloor);
-  e.y = fmaxf(e.y, kExpFloor);
+  if constexpr (FLOOR) {
+    e.x = fmaxf(e.x, kExpFloor);
+    e.y = fmaxf(e.y, kExpFloor);
+  }
   return exp2_sel2<EXPM>(e);
 }
+
+// Exponents at or above this need no floor in exp2_poly (a margin of one over
+// kExpFloor covers the rounding between a bound and the exponents it bounds).
+// Along a row or over a cell the exponent A + B q + C q^2 (+ row terms) is a
+// concave quadratic, so it is smallest at a corner: a unit whose corners are
+// all above kExpUnfloored can skip the per-pixel floor.
+constexpr float kExpUnfloored = kExpFloor + 1.0f;
 
 // ---------------------------------------------------------------- records
 // Per-Gaussian slice-invariant record of the slice renderer (camera frame of the

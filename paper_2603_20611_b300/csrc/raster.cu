@@ -474,56 +474,68 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
           // are sums of P's snapshots: sum_r r S_r = s3 + (s3 + s2) + (s3 + s2 + s1)
           // and sum_r r^2 S_r = 5 s3 + 3 (s3 + s2) + (s3 + s2 + s1) (s_r the row sums).
           const float* Gm = RF ? sm.Grev + hb * HBS : Gr + 4;  // the row's pixels 7, 6, 5, 4
-          float2 P0, P1, P2, T0, T1, U0;
-#pragma unroll
-          for (int r = 3; r >= 0; --r) {
-            const float rf = (float)r;
-            const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
-            const float B = fmaf(c1, rf, B0);
-            const float2 A2 = make_float2(A, A), B2 = make_float2(B, B), Bn2 = make_float2(-B, -B);
-            const float4 gx = *reinterpret_cast<const float4*>(Gr + r * 8);
-            const float4 gy = *reinterpret_cast<const float4*>(Gm + r * 8);
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-              const float qa = (float)(2 * k) - 3.5f, qb = qa + 1.0f;
-              const float2 q = make_float2(qa, qb), q2 = make_float2(qa * qa, qb * qb);
-              const float2 GX = k == 0 ? make_float2(gx.x, gx.y) : make_float2(gx.z, gx.w);
-              const float2 GY = k == 0 ? make_float2(gy.x, gy.y) : make_float2(gy.z, gy.w);
-              // e(+-q) = (A + C q^2) +- B q
-              const float2 base = __ffma2_rn(C2, q2, A2);
-              const float2 Y = __fmul2_rn(GY, couple_exp2<EXPM>(Bn2, q, base));
-              const float2 XY = __ffma2_rn(GX, couple_exp2<EXPM>(B2, q, base), Y);
-              if (r == 3 && k == 0) {
-                P0 = XY;
-                P1 = __fmul2_rn(q, XY);
-                P2 = __fmul2_rn(q2, XY);
-              } else {
-                P0 = __fadd2_rn(P0, XY);
-                P1 = __ffma2_rn(q, XY, P1);
-                P2 = __ffma2_rn(q2, XY, P2);
+          // the exponent is concave in (q, r): if its four corners are above
+          // kExpUnfloored, so is every pixel, and the pixels need no floor
+          const float Bl = fmaf(c1, 3.0f, B0), Al = fmaf(fmaf(c2, 3.0f, A1), 3.0f, A0);
+          const float emin = fminf(fmaf(-3.5f, fabsf(B0), fmaf(12.25f, c0, A0)),
+                                   fmaf(-3.5f, fabsf(Bl), fmaf(12.25f, c0, Al)));
+          auto rows = [&](auto floor_tag) {
+            constexpr bool FL = decltype(floor_tag)::value;
+            float2 P0, P1, P2, T0, T1, U0;
+  #pragma unroll
+            for (int r = 3; r >= 0; --r) {
+              const float rf = (float)r;
+              const float A = fmaf(fmaf(c2, rf, A1), rf, A0);
+              const float B = fmaf(c1, rf, B0);
+              const float2 A2 = make_float2(A, A), B2 = make_float2(B, B), Bn2 = make_float2(-B, -B);
+              const float4 gx = *reinterpret_cast<const float4*>(Gr + r * 8);
+              const float4 gy = *reinterpret_cast<const float4*>(Gm + r * 8);
+  #pragma unroll
+              for (int k = 0; k < 2; ++k) {
+                const float qa = (float)(2 * k) - 3.5f, qb = qa + 1.0f;
+                const float2 q = make_float2(qa, qb), q2 = make_float2(qa * qa, qb * qb);
+                const float2 GX = k == 0 ? make_float2(gx.x, gx.y) : make_float2(gx.z, gx.w);
+                const float2 GY = k == 0 ? make_float2(gy.x, gy.y) : make_float2(gy.z, gy.w);
+                // e(+-q) = (A + C q^2) +- B q
+                const float2 base = __ffma2_rn(C2, q2, A2);
+                const float2 Y = __fmul2_rn(GY, couple_exp2<EXPM, FL>(Bn2, q, base));
+                const float2 XY = __ffma2_rn(GX, couple_exp2<EXPM, FL>(B2, q, base), Y);
+                if (r == 3 && k == 0) {
+                  P0 = XY;
+                  P1 = __fmul2_rn(q, XY);
+                  P2 = __fmul2_rn(q2, XY);
+                } else {
+                  P0 = __fadd2_rn(P0, XY);
+                  P1 = __ffma2_rn(q, XY, P1);
+                  P2 = __ffma2_rn(q2, XY, P2);
+                }
+                P1 = __ffma2_rn(make_float2(-2.0f * qa, -2.0f * qb), Y, P1);
               }
-              P1 = __ffma2_rn(make_float2(-2.0f * qa, -2.0f * qb), Y, P1);
+              if (r == 3) {
+                T0 = P0;
+                T1 = P1;
+                U0 = __fmul2_rn(make_float2(5.0f, 5.0f), P0);
+              } else if (r == 2) {
+                T0 = __fadd2_rn(T0, P0);
+                T1 = __fadd2_rn(T1, P1);
+                U0 = __ffma2_rn(make_float2(3.0f, 3.0f), P0, U0);
+              } else if (r == 1) {
+                T0 = __fadd2_rn(T0, P0);
+                T1 = __fadd2_rn(T1, P1);
+                U0 = __fadd2_rn(U0, P0);
+              }
             }
-            if (r == 3) {
-              T0 = P0;
-              T1 = P1;
-              U0 = __fmul2_rn(make_float2(5.0f, 5.0f), P0);
-            } else if (r == 2) {
-              T0 = __fadd2_rn(T0, P0);
-              T1 = __fadd2_rn(T1, P1);
-              U0 = __ffma2_rn(make_float2(3.0f, 3.0f), P0, U0);
-            } else if (r == 1) {
-              T0 = __fadd2_rn(T0, P0);
-              T1 = __fadd2_rn(T1, P1);
-              U0 = __fadd2_rn(U0, P0);
-            }
-          }
-          M00 = P0.x + P0.y;
-          M10 = P1.x + P1.y;
-          M20 = P2.x + P2.y;
-          M01 = T0.x + T0.y;
-          M11 = T1.x + T1.y;
-          M02 = U0.x + U0.y;
+            M00 = P0.x + P0.y;
+            M10 = P1.x + P1.y;
+            M20 = P2.x + P2.y;
+            M01 = T0.x + T0.y;
+            M11 = T1.x + T1.y;
+            M02 = U0.x + U0.y;
+          };
+          if (__all_sync(__activemask(), emin >= kExpUnfloored))
+            rows(std::false_type{});
+          else
+            rows(std::true_type{});
         }
         // moments in d = (dxc + q, dy0 + r)
         mom[0] = M00;
