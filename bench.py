@@ -83,6 +83,15 @@ EXP_MODES = {"poly": 0, "hw": 1, "row": 3}
 RASTER_FORMS = {"auto": 0, "block": 1, "rows": 2}
 
 
+def raster_kernel(pass_, raster, exp, vox=False):
+    """Name of the kernel a rasteriser pass runs on this configuration."""
+    if exp == "row" or raster == "block":
+        return f"k_raster_{pass_}_blk"
+    if raster == "rows" or pass_ == "fwd" or vox:
+        return f"k_raster_{pass_}_rows"
+    return f"k_raster_{pass_}_blk"
+
+
 def pass_roofline(evals, evaluated, ops, launch_s, peak, kernel):
     """Roofline figures of one rasteriser pass: algorithmic lane instructions per
     second against the measured FP32 peak, and the evaluated pixels per
@@ -468,7 +477,8 @@ def run_native(args, rank, world):
     dom = "bwd" if phases["bwd"][0] >= phases["fwd"][0] else "fwd"
     ops_t = OPS_PER_EVAL_ROW if args.exp == "row" else OPS_PER_EVAL
     passes = {p: pass_roofline(float(np.mean(ev_steps)), float(np.mean(ev_steps)) * evaluated_ratio[i], ops_t[p],
-                               phases[p][0] * 1e-3 / max(phases[p][2], 1), fp32_peak, f"k_raster_{p}")
+                               phases[p][0] * 1e-3 / max(phases[p][2], 1), fp32_peak,
+                               raster_kernel(p, args.raster, args.exp))
               for i, p in enumerate(("fwd", "bwd"))}
     ms_dom, _, calls_dom = phases[dom]
     avg_launch_s = ms_dom * 1e-3 / max(calls_dom, 1)
@@ -478,8 +488,9 @@ def run_native(args, rank, world):
     peak = fp32_peak / 1e12
     nominal = 148 * 128 * 2.032e9 / 1e12
     default_cfg = (args.exp == "poly" and not args.det and args.tile == 16 and args.fwd_px == 0
-                   and args.bwd_px == 0 and args.case == "microscopy")
-    traffic, traffic_note = recorded_traffic(f"k_raster_{dom}_blk") if default_cfg else \
+                   and args.bwd_px == 0 and args.case == "microscopy" and args.raster == "auto")
+    dom_kernel = raster_kernel(dom, args.raster, args.exp)
+    traffic, traffic_note = recorded_traffic(dom_kernel) if default_cfg else \
         (None, "recorded for the default configuration only")
 
     # end to end through host buffers: every step uploads the parameters and the
@@ -559,7 +570,7 @@ def run_native(args, rank, world):
                 "evaluated_per_algorithmic": {"fwd": evaluated_ratio[0], "bwd": evaluated_ratio[1]},
                 "rasteriser": args.raster, "passes": passes,
                 "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[2]},
-                "roofline": {"bound": "alu", "kernel": f"k_raster_{dom}", "achieved": achieved, "peak": peak,
+                "roofline": {"bound": "alu", "kernel": dom_kernel, "achieved": achieved, "peak": peak,
                              "unit": "Tinst/s (FP32+INT lane instructions)", "frac": achieved / peak,
                              "traffic": traffic, "traffic_note": traffic_note,
                              "peak_kind": "measured FMA probe, best of 5 bursts, same run",
@@ -960,12 +971,15 @@ def run_ultrasound(args):
     # one rasteriser launch per step and pass (the voxelizer's backward phase also
     # holds its small gradient-finish kernel)
     line["passes"] = {p: pass_roofline(evals, evals * (evaluated[i] / max(evals, 1)), ops_t[p],
-                                       phases[ph][0] * 1e-3 / args.steps, fp32_peak, f"k_raster_{p}")
+                                       phases[ph][0] * 1e-3 / args.steps, fp32_peak,
+                                       raster_kernel(p, args.raster, args.exp, args.workload == "voxelize"))
                       for i, (p, ph) in enumerate((("fwd", fwd_phase), ("bwd", bwd_phase)))}
     if ops:
         bwd_s = phases[bwd_phase][0] * 1e-3 / args.steps
         achieved = evals * ops / bwd_s / 1e12
-        line["roofline"] = {"bound": "alu", "kernel": "k_raster_bwd", "achieved": achieved,
+        line["roofline"] = {"bound": "alu", "kernel": raster_kernel("bwd", args.raster, args.exp,
+                                                                    args.workload == "voxelize"),
+                            "achieved": achieved,
                             "peak": fp32_peak / 1e12, "frac": achieved / (fp32_peak / 1e12),
                             "unit": "Tinst/s (FP32+INT lane instructions)", "ops_per_eval": ops,
                             "peak_kind": "measured FMA probe, best of 5 bursts, same run",
