@@ -214,7 +214,7 @@ def summarise_clocks(text, window=None):
 # and scaled to a full launch by the binned pairs ("scale").
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "raster_traffic.json")
 KERNEL_SOURCES = ("paper_2603_20611_b300/csrc/raster.cu", "paper_2603_20611_b300/csrc/gp_common.cuh",
-                  "paper_2603_20611_b300/csrc/slice.cuh")
+                  "paper_2603_20611_b300/csrc/slice.cuh", "paper_2603_20611_b300/csrc/raster_rows.cuh")
 
 
 def kernel_source_hash():
@@ -226,7 +226,7 @@ def kernel_source_hash():
 
 
 def recorded_traffic(kernel):
-    """(bytes per launch, note) for `kernel` ('k_raster_fwd_blk' / 'k_raster_bwd_blk')."""
+    """(bytes per launch, note) for `kernel` (e.g. 'k_raster_fwd_rows', 'k_raster_bwd_blk')."""
     if not os.path.exists(TRAFFIC_FILE):
         return None, "no capture recorded"
     with open(TRAFFIC_FILE) as f:
@@ -664,7 +664,7 @@ def batched_comparison(steps, warmup, n_sets=64):
             "ms_per_step": float(np.mean(b_ms)), "value": 2.0 * evals / (np.mean(b_ms) * 1e-3), "unit": UNIT,
             "slices_per_s": sum(len(it["z"]) for it in items) / (np.mean(b_ms) * 1e-3),
             "plain": {"ms_per_step": float(np.mean(p_ms)), "value": 2.0 * evals / (np.mean(p_ms) * 1e-3),
-                      "launch": "64 x (gp_render_slices + gp_render_backward) on one stream"},
+                      "launch": f"{len(items)} x (gp_render_slices + gp_render_backward) on one stream"},
             "speedup_vs_plain": float(np.mean(p_ms) / np.mean(b_ms)),
             "autotuned": info,
             "l2": f"not flushed: every step writes and reads {work_gb:.1f} GB of images and gradients, "
