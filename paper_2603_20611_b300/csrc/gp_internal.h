@@ -23,6 +23,12 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                              const unsigned long long* n_dev, uint32_t cap, int bits, void* temp,
                              cudaStream_t st, bool* result_in_alt, const uint32_t* first_vals = nullptr);
 
+// Copies up to three small host arrays of 32-bit words to the device in stream
+// order.  Up to 720 words in all travel as the arguments of one kernel launch
+// (no copy-engine operation, no staging of pageable memory); larger arrays go
+// by cudaMemcpyAsync.
+cudaError_t put_words(cudaStream_t st, int k, uint32_t* const* dst, const void* const* src, const int* n);
+
 // --------------------------------------------------------------- workspace
 // A grow-only device buffer.
 struct DevBuf {

@@ -80,7 +80,9 @@ extern "C" GP_API gp_status gp_mse_grad_noalloc(const float* I, const float* T, 
   const int* tid = nullptr;
   if (t_index) {
     int* dst = (int*)(scratch + kNoallocPartials);
-    if (cudaMemcpyAsync(dst, t_index, (size_t)S * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    uint32_t* d1[1] = {(uint32_t*)dst};
+    const void* s1[1] = {t_index};
+    if (put_words(st, 1, d1, s1, &S) != cudaSuccess) {
       cudaGetLastError();
       return GP_ERR_CUDA;
     }

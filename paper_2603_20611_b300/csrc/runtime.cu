@@ -169,6 +169,46 @@ gp_status check_after(Ctx* c, cudaStream_t st) {
   return GP_OK;
 }
 
+constexpr int kPutWords = 720;
+struct PutArgs {
+  uint32_t* dst[3];
+  int n[3];
+  uint32_t w[kPutWords];
+};
+
+__global__ void k_put_words(PutArgs p) {
+  int o = 0;
+  for (int s = 0; s < 3; ++s) {
+    for (int i = threadIdx.x; i < p.n[s]; i += blockDim.x) p.dst[s][i] = p.w[o + i];
+    o += p.n[s];
+  }
+}
+
+cudaError_t put_words(cudaStream_t st, int k, uint32_t* const* dst, const void* const* src, const int* n) {
+  int tot = 0;
+  for (int s = 0; s < k; ++s) tot += n[s];
+  if (k <= 3 && tot <= kPutWords) {
+    if (tot == 0) return cudaSuccess;
+    PutArgs p{};
+    int o = 0;
+    for (int s = 0; s < k; ++s) {
+      p.dst[s] = dst[s];
+      p.n[s] = n[s];
+      memcpy(p.w + o, src[s], (size_t)n[s] * 4);
+      o += n[s];
+    }
+    k_put_words<<<1, 256, 0, st>>>(p);
+    note_launch();
+    return cudaGetLastError();
+  }
+  for (int s = 0; s < k; ++s) {
+    if (n[s] == 0) continue;
+    cudaError_t e = cudaMemcpyAsync(dst[s], src[s], (size_t)n[s] * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 static gp_status check_set(Ctx* c, const gp_set* s) {
@@ -264,24 +304,16 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
   GP_TRY(ws_reserve(c, b.zorder, (size_t)std::max(S, 1) * 4));
   GP_TRY(ws_reserve(c, b.zorig, (size_t)std::max(S, 1) * 4));
   if (S > 0) {
-    GP_CUDA(c, cudaMemcpyAsync(b.zs.ptr, zs.data(), S * 4, cudaMemcpyHostToDevice, st), "upload z");
-    GP_CUDA(c, cudaMemcpyAsync(b.zorder.ptr, order.data(), S * 4, cudaMemcpyHostToDevice, st), "upload z");
-    GP_CUDA(c, cudaMemcpyAsync(b.zorig.ptr, z, S * 4, cudaMemcpyHostToDevice, st), "upload z");
+    uint32_t* dst[3] = {(uint32_t*)b.zs.ptr, (uint32_t*)b.zorder.ptr, (uint32_t*)b.zorig.ptr};
+    const void* src[3] = {zs.data(), order.data(), z};
+    const int cnt[3] = {S, S, S};
+    GP_CUDA(c, put_words(st, 3, dst, src, cnt), "upload z");
   }
   SliceArgs& A = *a;
   A = SliceArgs{};
   A.mu = set->mu; A.scale = set->scale; A.quat = set->quat; A.alpha = set->alpha;
   A.n = n; A.mod = set->scale_mod; A.sigma2 = sigma_z * sigma_z;
   A.vox = vox ? 1 : 0;
-  // a warp per Gaussian in K-pre / K-emit when the sigma_z blur alone makes a
-  // Gaussian reach 32 or more of the call's planes (their mean spacing)
-  if (S >= 64) {
-    const float span = zs[S - 1] - zs[0];
-    A.warp_pairs = span > 0.0f && 2.0f * sqrtf(2.0f * logf(1.0f / c->cfg.eps)) * sigma_z >= 32.0f * span / (float)(S - 1);
-  }
-  // otherwise 4 lanes per Gaussian on dense stacks (planes at most 2 apart, at
-  // least 8 of them), where a Gaussian's own extent reaches several planes
-  if (!A.warp_pairs && S >= 8) A.group_pairs = (zs[S - 1] - zs[0]) <= 2.0f * (float)(S - 1);
   memcpy(A.Rc, view.R, sizeof(A.Rc));
   memcpy(A.tc, view.t, sizeof(A.tc));
   A.k2 = 2.0f * logf(1.0f / c->cfg.eps);
@@ -553,7 +585,9 @@ gp_status gp_mse_grad(gp_ctx* ctx, const float* I, const float* T, const int* t_
     for (int s = 0; s < S; ++s)
       if (t_index[s] < 0) return set_err(c, GP_ERR_ARG, "negative target slice index");
     int* dst = (int*)((char*)b.loss_tmp.ptr + tmp_bytes);
-    GP_CUDA(c, cudaMemcpyAsync(dst, t_index, (size_t)S * 4, cudaMemcpyHostToDevice, st), "upload t_index");
+    uint32_t* d1[1] = {(uint32_t*)dst};
+    const void* s1[1] = {t_index};
+    GP_CUDA(c, put_words(st, 1, d1, s1, &S), "upload t_index");
     tid = dst;
   }
   PhaseTimer timer(c, GP_PHASE_LOSS, st);

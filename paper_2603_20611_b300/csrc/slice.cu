@@ -17,9 +17,12 @@
 //
 // Pipeline of one render:
 //   K-pre     per Gaussian: record + number of (slice, tile) pairs it touches
+//             (a warp per 32 Gaussians, their work dealt out by plane and by
+//             tile row)
 //   scan      exclusive scan of the counts (sort.cu)
-//   K-emit    keys (slice * T + tile) with emission indices as values
-//   sort      stable radix sort on the live key bits (sort.cu)
+//   K-emit    keys (slice * T + tile) with Gaussian ids as values, in Gaussian
+//             order (the same warp-balanced enumeration)
+//   sort      stable one-sweep radix sort on the live key bits (sort.cu)
 //   K-range   [start, end) of every (slice, tile)
 //   K-fwd     one CTA per (slice, tile): stage the tile's Gaussians in shared
 //             memory with 16-byte loads, every thread accumulates PX pixels of
@@ -44,13 +47,6 @@
 namespace gp {
 
 constexpr int PRE_THREADS = 128;
-constexpr int kPairGroup = 4;  // lanes per Gaussian of the grouped K-pre / K-emit
-
-// Calls whose Gaussians each reach tens of planes (the host sets warp_pairs)
-// count and emit with a warp per Gaussian, the lanes taking its planes; other
-// calls keep a thread per Gaussian.  Both enumerate the same pairs in the same
-// order.
-__host__ __device__ inline bool warp_per_gaussian(const SliceArgs& a) { return a.warp_pairs != 0; }
 
 // ------------------------------------------------------------ K-pre
 __device__ __forceinline__ int lower_bound_f(const float* __restrict__ v, int n, float x) {
@@ -173,28 +169,6 @@ __device__ __forceinline__ void for_each_pair(const SliceArgs& a, const SliceRec
   }
 }
 
-// Number of pairs of one Gaussian on sorted plane j (same enumeration, whole
-// runs at a time).
-__device__ __forceinline__ unsigned plane_pairs(const SliceArgs& a, const SliceRec& r, int j) {
-  const PlaneBox b = plane_box(a, r, j);
-  unsigned c = 0;
-  for (int ty = b.ty0; ty <= b.ty1; ++ty) {
-    int lo, hi;
-    if (row_tiles(a, r, b, ty, &lo, &hi)) c += (unsigned)(hi - lo + 1);
-  }
-  return c;
-}
-
-// Number of pairs of one Gaussian.
-__device__ __forceinline__ unsigned long long count_pairs(const SliceArgs& a, const SliceRec& r) {
-  if (r.r3.y == 0.0f) return 0;
-  int plo, phi;
-  plane_range(a, r, plo, phi);
-  unsigned long long c = 0;
-  for (int j = plo; j < phi; ++j) c += plane_pairs(a, r, j);
-  return c;
-}
-
 // Record of Gaussian i of item a.
 __device__ __forceinline__ SliceRec make_record(const SliceArgs& a, int i) {
   float4 q = reinterpret_cast<const float4*>(a.quat)[i];
@@ -226,77 +200,6 @@ __device__ __forceinline__ SliceRec make_record(const SliceArgs& a, int i) {
   return r;
 }
 
-// Record and pair count of Gaussian i of item a, stored at batch-wide index ig.
-__device__ __forceinline__ void slice_pre_one(const SliceArgs& a, int i, int ig, SliceRec* __restrict__ rec,
-                                              unsigned long long* __restrict__ counts) {
-  const SliceRec r = make_record(a, i);
-  rec[ig] = r;
-  counts[ig] = count_pairs(a, r);
-}
-
-__global__ void __launch_bounds__(PRE_THREADS) k_slice_pre(SliceArgs a, SliceRec* __restrict__ rec,
-                                                           unsigned long long* __restrict__ counts) {
-  const int i = blockIdx.x * PRE_THREADS + threadIdx.x;
-  if (i < a.n) slice_pre_one(a, i, i, rec, counts);
-}
-
-// K-pre split in two for calls whose Gaussians reach a few planes each: the
-// records (a thread per Gaussian), then the counts with a group of L lanes per
-// Gaussian, the lanes taking its planes (a stride of L).  Loop bounds are made
-// uniform over the warp (groups of one warp reach different numbers of planes)
-// so that the group shuffles run with every lane present.
-__global__ void __launch_bounds__(PRE_THREADS) k_slice_rec(SliceArgs a, SliceRec* __restrict__ rec) {
-  const int i = blockIdx.x * PRE_THREADS + threadIdx.x;
-  if (i < a.n) rec[i] = make_record(a, i);
-}
-
-template <int L>
-__global__ void __launch_bounds__(PRE_THREADS) k_slice_count_grp(SliceArgs a, const SliceRec* __restrict__ rec,
-                                                                 unsigned long long* __restrict__ counts) {
-  const int sub = threadIdx.x & (L - 1);
-  const int i = (int)((blockIdx.x * (unsigned)PRE_THREADS + threadIdx.x) / L);
-  const bool live = i < a.n;
-  SliceRec r{};
-  int plo = 0, phi = 0;
-  if (live) {
-    r = rec[i];
-    if (r.r3.y != 0.0f) plane_range(a, r, plo, phi);
-  }
-  const int np = phi - plo;
-  const int npmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)np);
-  unsigned c = 0;
-  for (int t0 = 0; t0 < npmax; t0 += L) {
-    const int t = t0 + sub;
-    if (t < np) c += plane_pairs(a, r, plo + t);
-  }
-#pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o, L);
-  if (sub == 0 && live) counts[i] = c;
-}
-
-// K-pre with a warp per Gaussian, for calls with many planes: the lanes count
-// the Gaussian's planes (a stride of 32), summed by a warp reduction.  Same
-// record and count as k_slice_pre.
-constexpr int PRE_WARPS = 8;
-
-__global__ void __launch_bounds__(PRE_WARPS * 32) k_slice_pre_warp(SliceArgs a, SliceRec* __restrict__ rec,
-                                                                   unsigned long long* __restrict__ counts) {
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * PRE_WARPS + (threadIdx.x >> 5);
-  if (i >= a.n) return;  // uniform over the warp
-  const SliceRec r = make_record(a, i);
-  if (lane == 0) rec[i] = r;
-  unsigned long long c = 0;
-  if (r.r3.y != 0.0f) {
-    int plo, phi;
-    plane_range(a, r, plo, phi);
-    for (int j = plo + lane; j < phi; j += 32) c += plane_pairs(a, r, j);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if (lane == 0) counts[i] = c;
-}
-
 // Item owning batch-wide index x of a prefix table t[0..n] (t[0] = 0).
 template <typename T>
 __device__ __forceinline__ int find_item(const T* __restrict__ t, int n, T x) {
@@ -308,233 +211,202 @@ __device__ __forceinline__ int find_item(const T* __restrict__ t, int n, T x) {
   return lo;
 }
 
-__global__ void __launch_bounds__(PRE_THREADS) k_slice_pre_batch(BatchItems b, SliceRec* __restrict__ rec,
-                                                                 unsigned long long* __restrict__ counts) {
-  const int ig = blockIdx.x * PRE_THREADS + threadIdx.x;
-  if (ig >= b.n_gauss) return;
-  const int k = find_item(b.gstart, b.n_items, ig);
-  const SliceArgs a = b.args[k];
-  slice_pre_one(a, ig - b.gstart[k], ig, rec, counts);
+// ------------------------------------------------------------ K-pre / K-emit
+// Both are warp-balanced.  With a thread per Gaussian a warp waits for its
+// largest Gaussian: on the microscopy fit step (500k Gaussians, 16 of 256
+// planes) a warp's largest Gaussian has 3.7x the mean pair count and 3.0x the
+// mean number of tile rows.  Here a warp takes 32 consecutive Gaussians and
+// deals their work out in two stages: the (Gaussian, plane) items 32 at a
+// time, then those items' tile rows 32 at a time, each lane finding its item
+// (row) by a binary search over the warp's prefix counts in shared memory.
+// K-pre adds each row's tile count to its Gaussian's count; K-emit places each
+// row's pairs by a warp scan of the row counts, so the pairs leave in the order
+// of for_each_pair (Gaussian, plane, tile row, tile column) and the counts and
+// the emission agree by construction.
+constexpr int BAL_WARPS = 4;
+
+struct BalSmem {
+  SliceRec rec[32];  // the warp's records
+  int item0[33];     // exclusive prefix of the lanes' plane counts
+  int plo[32];       // each lane's first sorted plane
+  int row0[33];      // exclusive prefix of the current items' tile-row counts
+  int owner[32], j[32], ty0[32];
+  float mx[32], my[32], k2e[32], rxe[32], rye[32];
+  unsigned cnt[32];  // K-pre: pairs of each lane's Gaussian
+};
+
+// m in [0, 32) with pre[m] <= x < pre[m + 1], for pre ascending, pre[0] <= x < pre[32].
+__device__ __forceinline__ int bal_slot(const int* pre, int x) {
+  int lo = 0, hi = 32;
+  while (hi - lo > 1) {
+    const int m = (lo + hi) >> 1;
+    if (pre[m] <= x) lo = m; else hi = m;
+  }
+  return lo;
 }
 
-void launch_slice_pre_batch(const BatchItems& b, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
-  if (b.n_gauss <= 0) return;
-  k_slice_pre_batch<<<ceil_div(b.n_gauss, PRE_THREADS), PRE_THREADS, 0, st>>>(b, rec, counts);
-  note_launch();
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// One warp over the Gaussians of one item whose batch-wide indices are
+// i0 + [lane_lo, lane_hi) (local index = batch-wide index - gbase0).  K-pre
+// (EMIT false): make the records, store them and the pair counts.  K-emit (EMIT
+// true): read the records and write the pairs (keys and batch-wide Gaussian
+// ids) from offsets[i0 + lane_lo] on, never at or past `cap`.
+template <bool EMIT>
+__device__ __forceinline__ void bal_warp(const SliceArgs& a, int i0, int lane_lo, int lane_hi, int gbase0,
+                                         BalSmem& sm, SliceRec* __restrict__ rec,
+                                         unsigned long long* __restrict__ counts,
+                                         const unsigned long long* __restrict__ offsets, unsigned long long cap,
+                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ emit_gid) {
+  const int lane = threadIdx.x & 31;
+  const int i = i0 + lane;
+  const bool live = lane >= lane_lo && lane < lane_hi;
+  SliceRec r{};
+  if (live) {
+    if (EMIT) {
+      r = rec[i];
+    } else {
+      r = make_record(a, i - gbase0);
+      rec[i] = r;
+    }
+  }
+  int plo = 0, phi = 0;
+  if (live && r.r3.y != 0.0f) plane_range(a, r, plo, phi);
+  sm.rec[lane] = r;
+  sm.plo[lane] = plo;
+  const int iincl = warp_incl_scan(phi - plo, lane);
+  sm.item0[lane + 1] = iincl;
+  if (lane == 0) sm.item0[0] = 0;
+  if (!EMIT) sm.cnt[lane] = 0u;
+  const int n_items = __shfl_sync(0xffffffffu, iincl, 31);
+  unsigned long long e0 = 0ull, e_end = 0ull;  // the lanes' run of the output, as K-pre counted it
+  if (EMIT) {
+    e0 = offsets[i0 + lane_lo];
+    e_end = min(offsets[i0 + lane_hi - 1] + counts[i0 + lane_hi - 1], cap);
+  }
+  const uint32_t T = (uint32_t)(a.TX * a.TY);
+  __syncwarp();
+  for (int c0 = 0; c0 < n_items; c0 += 32) {
+    const int k = c0 + lane;
+    int ny = 0;
+    if (k < n_items) {
+      const int o = bal_slot(sm.item0, k);
+      const int j = sm.plo[o] + (k - sm.item0[o]);
+      const PlaneBox b = plane_box(a, sm.rec[o], j);
+      ny = max(b.ty1 - b.ty0 + 1, 0);
+      sm.owner[lane] = o;
+      sm.j[lane] = j;
+      sm.ty0[lane] = b.ty0;
+      sm.mx[lane] = b.mx;
+      sm.my[lane] = b.my;
+      sm.k2e[lane] = b.k2e;
+      sm.rxe[lane] = b.rxe;
+      sm.rye[lane] = b.rye;
+    }
+    const int rincl = warp_incl_scan(ny, lane);
+    sm.row0[lane + 1] = rincl;
+    if (lane == 0) sm.row0[0] = 0;
+    const int n_rows = __shfl_sync(0xffffffffu, rincl, 31);
+    __syncwarp();
+    for (int q0 = 0; q0 < n_rows; q0 += 32) {
+      const int q = q0 + lane;
+      int lo = 0, hi = -1, o = 0, m = 0, ty = 0;
+      if (q < n_rows) {
+        m = bal_slot(sm.row0, q);
+        o = sm.owner[m];
+        ty = sm.ty0[m] + (q - sm.row0[m]);
+        PlaneBox b;
+        b.mx = sm.mx[m];
+        b.my = sm.my[m];
+        b.k2e = sm.k2e[m];
+        b.rxe = sm.rxe[m];
+        b.rye = sm.rye[m];
+        if (!row_tiles(a, sm.rec[o], b, ty, &lo, &hi)) {
+          lo = 0;
+          hi = -1;
+        }
+      }
+      const int c = hi - lo + 1;  // pairs of this tile row (0 if none)
+      if (!EMIT) {
+        if (c > 0) atomicAdd(&sm.cnt[o], (unsigned)c);
+      } else {
+        const int cincl = warp_incl_scan(c, lane);
+        unsigned long long e = e0 + (unsigned long long)(cincl - c);
+        if (c > 0) {
+          const uint32_t kb = a.key_base + (uint32_t)a.zorder[sm.j[m]] * T + (uint32_t)(ty * a.TX);
+          const uint32_t gid = (uint32_t)(i0 + o);
+          for (int tx = lo; tx <= hi; ++tx, ++e) {
+            if (e < e_end && GP_IN_RANGE(7, tx, a.TX) && GP_IN_RANGE(8, ty, a.TY)) {
+              keys[e] = kb + (uint32_t)tx;
+              emit_gid[e] = gid;
+            }
+          }
+        }
+        e0 += (unsigned long long)__shfl_sync(0xffffffffu, cincl, 31);
+      }
+    }
+    __syncwarp();  // the next items overwrite this round's item arrays
+  }
+  if (!EMIT && live) counts[i] = sm.cnt[lane];
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(BAL_WARPS * 32) k_slice_bal(SliceArgs a, SliceRec* __restrict__ rec,
+                                                              unsigned long long* __restrict__ counts,
+                                                              const unsigned long long* __restrict__ offsets,
+                                                              uint32_t* __restrict__ keys,
+                                                              uint32_t* __restrict__ emit_gid) {
+  __shared__ BalSmem sm[BAL_WARPS];
+  const int w = threadIdx.x >> 5;
+  const int i0 = (blockIdx.x * BAL_WARPS + w) * 32;
+  if (i0 >= a.n) return;  // uniform over the warp
+  bal_warp<EMIT>(a, i0, 0, min(32, a.n - i0), 0, sm[w], rec, counts, offsets, ~0ull, keys, emit_gid);
+}
+
+// Batched form: the warp's 32 batch-wide Gaussians, one item at a time (items
+// own contiguous ranges of Gaussians, so each one's share is a lane range).
+template <bool EMIT>
+__global__ void __launch_bounds__(BAL_WARPS * 32) k_slice_bal_batch(BatchItems b, SliceRec* __restrict__ rec,
+                                                                    unsigned long long* __restrict__ counts,
+                                                                    const unsigned long long* __restrict__ offsets,
+                                                                    unsigned long long cap,
+                                                                    uint32_t* __restrict__ keys,
+                                                                    uint32_t* __restrict__ emit_gid) {
+  __shared__ BalSmem sm[BAL_WARPS];
+  const int w = threadIdx.x >> 5;
+  const int i0 = (blockIdx.x * BAL_WARPS + w) * 32;
+  if (i0 >= b.n_gauss) return;  // uniform over the warp
+  const int nl = min(32, b.n_gauss - i0);
+  for (int l = 0; l < nl;) {  // uniform over the warp
+    const int k = find_item(b.gstart, b.n_items, i0 + l);
+    const int g0 = b.gstart[k];
+    const int lh = min(nl, b.gstart[k + 1] - i0);
+    const SliceArgs a = b.args[k];
+    bal_warp<EMIT>(a, i0, l, lh, g0, sm[w], rec, counts, offsets, cap, keys, emit_gid);
+    __syncwarp();
+    l = lh;
+  }
 }
 
 void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
   if (a.n <= 0) return;
-  if (warp_per_gaussian(a)) {
-    k_slice_pre_warp<<<ceil_div(a.n, PRE_WARPS), PRE_WARPS * 32, 0, st>>>(a, rec, counts);
-    note_launch();
-  } else if (a.group_pairs) {
-    k_slice_rec<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec);
-    k_slice_count_grp<kPairGroup><<<ceil_div(a.n, PRE_THREADS / kPairGroup), PRE_THREADS, 0, st>>>(a, rec, counts);
-    note_launch(2);
-  } else {
-    k_slice_pre<<<ceil_div(a.n, PRE_THREADS), PRE_THREADS, 0, st>>>(a, rec, counts);
-    note_launch();
-  }
+  k_slice_bal<false><<<ceil_div(a.n, BAL_WARPS * 32), BAL_WARPS * 32, 0, st>>>(a, rec, counts, nullptr, nullptr,
+                                                                               nullptr);
+  note_launch();
 }
 
-// ------------------------------------------------------------ K-emit
-// One thread per Gaussian, enumerating exactly as K-pre counted.  The 32
-// Gaussians of a warp own one contiguous run of the output (their offsets are
-// consecutive), so the warp gathers its pairs in a shared-memory window and
-// writes the window with coalesced stores.
-constexpr int EMIT_THREADS = 128;
-constexpr int EMIT_WIN = 1024;  // pairs per warp window
-
-template <bool BATCH>
-__global__ void __launch_bounds__(EMIT_THREADS) k_slice_emit(SliceArgs a1, BatchItems b, int n,
-                                                             const SliceRec* __restrict__ rec,
-                                                             const unsigned long long* __restrict__ offsets,
-                                                             const unsigned long long* __restrict__ counts,
-                                                             unsigned long long cap, uint32_t* __restrict__ keys,
-                                                             uint32_t* __restrict__ emit_gid) {
-  __shared__ uint32_t wkey[EMIT_THREADS / 32][EMIT_WIN];
-  __shared__ uint32_t wgid[EMIT_THREADS / 32][EMIT_WIN];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i = blockIdx.x * EMIT_THREADS + threadIdx.x;
-  const int i0 = i - lane;
-  if (i0 >= n) return;  // whole warp past the end
-  const int ilast = min(i0 + 31, n - 1);
-  const unsigned long long wstart = offsets[i0];
-  const unsigned long long wend = min(offsets[ilast] + counts[ilast], cap);
-  const bool mine = i < n;
-  const unsigned long long my0 = mine ? offsets[i] : 0ull;
-  const unsigned long long my1 = mine ? my0 + counts[i] : 0ull;
-  SliceRec r;
-  SliceArgs a = a1;
-  if (mine) {
-    r = rec[i];
-    if (BATCH) a = b.args[find_item(b.gstart, b.n_items, i)];
-  }
-  const uint32_t T = (uint32_t)(a.TX * a.TY);
-  if (wend - wstart > 2ull * EMIT_WIN) {
-    // many pairs per warp (Gaussians spanning many planes): one enumeration
-    // with direct stores (each thread's run is contiguous) instead of one
-    // enumeration per window
-    if (mine) {
-      unsigned long long e = my0;
-      for_each_pair(a, r, [&](int j, int tile) {
-        if (e < wend) {
-          keys[e] = a.key_base + (uint32_t)a.zorder[j] * T + (uint32_t)tile;
-          emit_gid[e] = (uint32_t)i;
-        }
-        ++e;
-      });
-    }
-    return;
-  }
-  for (unsigned long long wb = wstart; wb < wend; wb += EMIT_WIN) {
-    const unsigned long long we = wb + EMIT_WIN;
-    if (mine && my1 > wb && my0 < we) {
-      unsigned long long e = my0;
-      for_each_pair(a, r, [&](int j, int tile) {
-        if (e >= wb && e < we && e < my1) {
-          wkey[warp][e - wb] = a.key_base + (uint32_t)a.zorder[j] * T + (uint32_t)tile;
-          wgid[warp][e - wb] = (uint32_t)i;
-        }
-        ++e;
-      });
-    }
-    __syncwarp();
-    const int cnt = (int)min((unsigned long long)EMIT_WIN, wend - wb);
-    for (int k = lane; k < cnt; k += 32) {
-      keys[wb + k] = wkey[warp][k];
-      emit_gid[wb + k] = wgid[warp][k];
-    }
-    __syncwarp();
-  }
-}
-
-// K-emit with a warp per Gaussian (calls with many planes): the lanes take 32
-// of the Gaussian's planes at a time, a warp scan of their pair counts gives
-// each lane the start of its plane's run, so the Gaussian's pairs leave as one
-// contiguous run in the same order as the thread-per-Gaussian emission.
-__global__ void __launch_bounds__(PRE_WARPS * 32) k_slice_emit_warp(SliceArgs a, const SliceRec* __restrict__ rec,
-                                                                    const unsigned long long* __restrict__ offsets,
-                                                                    uint32_t* __restrict__ keys,
-                                                                    uint32_t* __restrict__ emit_gid) {
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * PRE_WARPS + (threadIdx.x >> 5);
-  if (i >= a.n) return;  // uniform over the warp
-  const SliceRec r = rec[i];
-  if (r.r3.y == 0.0f) return;
-  const uint32_t T = (uint32_t)(a.TX * a.TY);
-  unsigned long long base = offsets[i];
-  int plo, phi;
-  plane_range(a, r, plo, phi);
-  for (int j0 = plo; j0 < phi; j0 += 32) {
-    const int j = j0 + lane;
-    const unsigned c = j < phi ? plane_pairs(a, r, j) : 0u;
-    unsigned incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    if (j < phi) {
-      unsigned long long e = base + (incl - c);
-      const PlaneBox b = plane_box(a, r, j);
-      const uint32_t kb = a.key_base + (uint32_t)a.zorder[j] * T;
-      for (int ty = b.ty0; ty <= b.ty1; ++ty) {
-        int lo, hi;
-        if (!row_tiles(a, r, b, ty, &lo, &hi)) continue;
-        for (int tx = lo; tx <= hi; ++tx) {
-          if (GP_IN_RANGE(7, tx, a.TX) && GP_IN_RANGE(8, ty, a.TY)) {
-            keys[e] = kb + (uint32_t)(ty * a.TX + tx);
-            emit_gid[e] = (uint32_t)i;
-          }
-          ++e;
-        }
-      }
-    }
-    base += __shfl_sync(0xffffffffu, incl, 31);
-  }
-}
-
-// K-emit with a group of L lanes per Gaussian (the grouped K-pre's calls): the
-// lanes take the Gaussian's planes, a group scan of their pair counts places
-// each plane's run, and the warp's Gaussians (32 / L, consecutive, so their
-// runs are one contiguous stretch) are gathered in a shared-memory window of
-// GRP_WIN pairs and written with coalesced stores.  A warp with more pairs than
-// the window stores directly.  Same pairs, same order as k_slice_emit.
-constexpr int GRP_WIN = 512;
-
-template <int L>
-__global__ void __launch_bounds__(EMIT_THREADS) k_slice_emit_grp(SliceArgs a, const SliceRec* __restrict__ rec,
-                                                                 const unsigned long long* __restrict__ offsets,
-                                                                 const unsigned long long* __restrict__ counts,
-                                                                 uint32_t* __restrict__ keys,
-                                                                 uint32_t* __restrict__ emit_gid) {
-  __shared__ uint32_t wkey[EMIT_THREADS / 32][GRP_WIN];
-  __shared__ uint32_t wgid[EMIT_THREADS / 32][GRP_WIN];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane & (L - 1);
-  const int gw = (int)((blockIdx.x * (unsigned)EMIT_THREADS + threadIdx.x) >> 5);  // global warp
-  const int i0 = gw * (32 / L);
-  if (i0 >= a.n) return;  // whole warp past the end
-  const int i = i0 + lane / L;
-  const bool live = i < a.n;
-  const int ilast = min(i0 + 32 / L - 1, a.n - 1);
-  const unsigned long long wstart = offsets[i0];
-  const unsigned long long wcount = offsets[ilast] + counts[ilast] - wstart;
-  const bool window = wcount <= (unsigned long long)GRP_WIN;
-  SliceRec r{};
-  int plo = 0, phi = 0;
-  if (live) {
-    r = rec[i];
-    if (r.r3.y != 0.0f) plane_range(a, r, plo, phi);
-  }
-  const int np = phi - plo;
-  const int npmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)np);
-  const uint32_t T = (uint32_t)(a.TX * a.TY);
-  unsigned long long run = live ? offsets[i] : 0ull;  // where the group's next round of planes starts
-  for (int t0 = 0; t0 < npmax; t0 += L) {
-    const int t = t0 + sub;
-    const bool mine = t < np;
-    const int j = plo + t;
-    const unsigned c = mine ? plane_pairs(a, r, j) : 0u;
-    unsigned incl = c;
-#pragma unroll
-    for (int o = 1; o < L; o <<= 1) {
-      const unsigned v = __shfl_up_sync(0xffffffffu, incl, o, L);
-      if (sub >= o) incl += v;
-    }
-    if (mine && c) {
-      unsigned long long e = run + (incl - c);
-      const PlaneBox b = plane_box(a, r, j);
-      const uint32_t kb = (uint32_t)a.zorder[j] * T;
-      for (int ty = b.ty0; ty <= b.ty1; ++ty) {
-        int lo, hi;
-        if (!row_tiles(a, r, b, ty, &lo, &hi)) continue;
-        for (int tx = lo; tx <= hi; ++tx) {
-          const uint32_t key = kb + (uint32_t)(ty * a.TX + tx);
-          if (!(GP_IN_RANGE(7, tx, a.TX) && GP_IN_RANGE(8, ty, a.TY))) {
-          } else if (window) {
-            if (GP_IN_RANGE(12, e - wstart, GRP_WIN)) {
-              wkey[warp][e - wstart] = key;
-              wgid[warp][e - wstart] = (uint32_t)i;
-            }
-          } else {
-            keys[e] = key;
-            emit_gid[e] = (uint32_t)i;
-          }
-          ++e;
-        }
-      }
-    }
-    run += __shfl_sync(0xffffffffu, incl, L - 1, L);
-  }
-  if (window) {
-    __syncwarp();
-    for (int k = lane; k < (int)wcount; k += 32) {
-      keys[wstart + k] = wkey[warp][k];
-      emit_gid[wstart + k] = wgid[warp][k];
-    }
-  }
+void launch_slice_pre_batch(const BatchItems& b, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
+  if (b.n_gauss <= 0) return;
+  k_slice_bal_batch<false><<<ceil_div(b.n_gauss, BAL_WARPS * 32), BAL_WARPS * 32, 0, st>>>(
+      b, rec, counts, nullptr, 0ull, nullptr, nullptr);
+  note_launch();
 }
 
 void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* offsets,
@@ -542,20 +414,8 @@ void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned l
                        cudaStream_t st) {
   (void)vals;  // the sort generates the identity values itself
   if (a.n <= 0) return;
-  if (warp_per_gaussian(a)) {
-    k_slice_emit_warp<<<ceil_div(a.n, PRE_WARPS), PRE_WARPS * 32, 0, st>>>(a, rec, offsets, keys, emit_gid);
-    note_launch();
-    return;
-  }
-  if (a.group_pairs) {
-    k_slice_emit_grp<kPairGroup><<<ceil_div(a.n, EMIT_THREADS / kPairGroup), EMIT_THREADS, 0, st>>>(
-        a, rec, offsets, counts, keys, emit_gid);
-    note_launch();
-    return;
-  }
-  BatchItems none{};
-  k_slice_emit<false><<<ceil_div(a.n, EMIT_THREADS), EMIT_THREADS, 0, st>>>(a, none, a.n, rec, offsets, counts,
-                                                                            ~0ull, keys, emit_gid);
+  k_slice_bal<true><<<ceil_div(a.n, BAL_WARPS * 32), BAL_WARPS * 32, 0, st>>>(
+      a, const_cast<SliceRec*>(rec), const_cast<unsigned long long*>(counts), offsets, keys, emit_gid);
   note_launch();
 }
 
@@ -563,12 +423,10 @@ void launch_slice_emit_batch(const BatchItems& b, const SliceRec* rec, const uns
                              const unsigned long long* counts, uint32_t cap, uint32_t* keys, uint32_t* emit_gid,
                              cudaStream_t st) {
   if (b.n_gauss <= 0) return;
-  SliceArgs none{};
-  k_slice_emit<true><<<ceil_div(b.n_gauss, EMIT_THREADS), EMIT_THREADS, 0, st>>>(none, b, b.n_gauss, rec, offsets,
-                                                                                 counts, cap, keys, emit_gid);
+  k_slice_bal_batch<true><<<ceil_div(b.n_gauss, BAL_WARPS * 32), BAL_WARPS * 32, 0, st>>>(
+      b, const_cast<SliceRec*>(rec), const_cast<unsigned long long*>(counts), offsets, cap, keys, emit_gid);
   note_launch();
 }
-
 // ------------------------------------------------------------ K-range
 // Each thread takes four consecutive sorted keys (one 16-byte load; the key
 // array is 16-byte aligned and a vector that would run past cap is read key by

@@ -20,8 +20,6 @@ struct SliceArgs {
   float sigma2;   // sigma_z^2
   float k2;       // 2 ln(1/eps): squared Mahalanobis culling radius
   int vox;        // 1: voxelizer planes (Eq. 12): sigma_z = 0 and amplitude alpha, not alpha/sqrt(det Sigma_2d)
-  int warp_pairs; // 1: K-pre / K-emit take a warp per Gaussian (its pairs span many planes)
-  int group_pairs;// 1: K-pre / K-emit take 4 lanes per Gaussian (its pairs span a few planes)
   const float* zs;      // [S] plane positions sorted ascending
   const int* zorder;    // [S] slice index of sorted position j
   const float* zorig;   // [S] plane position of slice index s

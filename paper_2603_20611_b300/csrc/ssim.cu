@@ -285,8 +285,9 @@ gp_status gp_l1_dssim_grad(gp_ctx* ctx, const float* I, const float* T, const in
     for (int s = 0; s < S; ++s)
       if (t_index[s] < 0) return set_err(c, GP_ERR_ARG, "negative target slice index");
     tid = (int*)(base + ds_bytes + part_bytes);
-    if (cudaMemcpyAsync(tid, t_index, (size_t)S * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
-      return cuda_err(c, cudaGetLastError(), "upload t_index");
+    uint32_t* d1[1] = {(uint32_t*)tid};
+    const void* s1[1] = {t_index};
+    if (put_words(st, 1, d1, s1, &S) != cudaSuccess) return cuda_err(c, cudaGetLastError(), "upload t_index");
   }
   SsimArgs p;
   double w[11], sum = 0.0;
