@@ -111,6 +111,14 @@ struct Ctx {
   BinBufs b;
   unsigned long long* h_total = nullptr;  // pinned readback slot
   int64_t last_pairs = 0, last_issued = 0;
+  // Speculative binning: the pairs were emitted and sorted into the buffers'
+  // capacity (bin_cap pairs) before their count came back.  The count's copy
+  // to h_total runs on side_st after scan_ev (the scan's end); bin_ev follows
+  // it, and the call checks it once its rasteriser is queued.
+  bool bin_pending = false;
+  uint32_t bin_cap = 0;
+  cudaEvent_t bin_ev = nullptr, scan_ev = nullptr;
+  cudaStream_t side_st = nullptr;
   int sm_count = 148;
 };
 

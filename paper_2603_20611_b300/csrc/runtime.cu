@@ -271,14 +271,58 @@ static gp_status scan_counts(Ctx* c, int n, cudaStream_t st, uint32_t* P) {
   return GP_OK;
 }
 
+// Pairs the context's pair buffers (and the sort's scratch) hold, 0 if none.
+static uint32_t pair_capacity(Ctx* c) {
+  const BinBufs& b = c->b;
+  size_t bytes = std::min({b.keys.bytes, b.vals.bytes, b.keys_alt.bytes, b.vals_alt.bytes, b.emit_gid.bytes});
+  uint32_t cap = (uint32_t)std::min<size_t>(bytes / 4, (size_t)INT32_MAX - 1);
+  while (cap > 0 && (size_t)radix_temp_bytes(cap) > b.sort_tmp.bytes) cap -= std::max<uint32_t>(cap / 64, 1);
+  return cap;
+}
+
+// Completes a speculative binning (see bin_slices): waits for the pair count's
+// copy and sets the binned pair count, or sets *redo when the pairs did not
+// fit the buffers the emission and sort were sized by (the caller then bins
+// again without speculation and repeats its rasteriser).
+static gp_status finish_bin(Ctx* c, bool* redo) {
+  *redo = false;
+  if (!c->bin_pending) return GP_OK;
+  c->bin_pending = false;
+  GP_CUDA(c, cudaEventSynchronize(c->bin_ev), "pair count readback");
+  const unsigned long long tot = *c->h_total;
+  if (tot >= (unsigned long long)INT32_MAX) {
+    c->bin_key.valid = false;
+    return set_err(c, GP_ERR_OVERFLOW, "more than 2^31 binned pairs in one call; split the call");
+  }
+  if (tot > c->bin_cap) {
+    c->bin_key.valid = false;
+    *redo = true;
+    return GP_OK;
+  }
+  c->bin_pairs = (uint32_t)tot;
+  c->last_pairs = (int64_t)tot;
+  c->last_issued = (int64_t)tot * c->bin_key.tile * c->bin_key.tile;
+  return GP_OK;
+}
+
 // Bins the set's (Gaussian, slice, tile) pairs of a slice stack: K-pre, scan,
 // one count readback, K-emit, radix sort, K-range.  On return the context's
 // buffers hold the records, the sorted emission indices and the tile ranges,
 // and *a describes the launch.
 // vox: the planes of the voxelizer (Eq. 12): sigma_z = 0 and amplitude alpha.
+// speculate: when the context already holds pair buffers, emit and sort into
+// their capacity without waiting for the pair count (the sort and the tile
+// ranges take the count from device memory); the count's copy is then pending,
+// *pairs_out is the capacity, and the caller queues its rasteriser and calls
+// finish_bin, so the host's wait for the count overlaps the device's work
+// instead of stalling the device between the scan and the emission.
 static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, int H, int W, float sigma_z,
                             const View& view, cudaStream_t st, SliceArgs* a, uint32_t* pairs_out,
-                            const uint32_t** sorted_vals, bool vox = false) {
+                            const uint32_t** sorted_vals, bool vox = false, bool speculate = false) {
+  if (c->bin_pending) {  // an earlier speculative binning whose caller failed before finishing it
+    c->bin_pending = false;
+    GP_CUDA(c, cudaEventSynchronize(c->bin_ev), "pair count readback");
+  }
   if (S < 0 || H <= 0 || W <= 0) return set_err(c, GP_ERR_ARG, "need S >= 0, H > 0, W > 0");
   if (S > 0 && !z) return set_err(c, GP_ERR_ARG, "z is NULL");
   if (vox) sigma_z = 0.0f;
@@ -327,22 +371,50 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
   GP_TRY(ws_reserve(c, b.ranges, (size_t)std::max<int64_t>(nkeys, 1) * 8));
   GP_CUDA(c, cudaMemsetAsync(b.ranges.ptr, 0, (size_t)std::max<int64_t>(nkeys, 1) * 8, st), "memset ranges");
   uint32_t P = 0;
+  bool spec = false;
   if (n > 0 && S > 0) {
     launch_slice_pre(A, (SliceRec*)b.rec.ptr, (unsigned long long*)b.counts.ptr, st);
-    GP_TRY(scan_counts(c, n, st, &P));
+    // the speculative capacity: the buffers' capacity, but at most a quarter
+    // more than the last binning's count (the sort's grids and scans are sized
+    // by it)
+    uint32_t cap = speculate ? pair_capacity(c) : 0u;
+    if (cap > 0 && c->last_pairs > 0)
+      cap = (uint32_t)std::min<int64_t>(cap, std::max<int64_t>(c->last_pairs + c->last_pairs / 4, 4096));
+    if (cap > 0) {
+      GP_CUDA(c, exclusive_scan<unsigned long long>((unsigned long long*)b.counts.ptr,
+                                                    (unsigned long long*)b.offsets.ptr, n,
+                                                    (unsigned long long*)b.total.ptr, b.scan_tmp.ptr, st),
+              "pair scan");
+      // the count's copy runs on the context's side stream as soon as the scan
+      // is done, beside the emission and the sort
+      GP_CUDA(c, cudaEventRecord(c->scan_ev, st), "pair count readback");
+      GP_CUDA(c, cudaStreamWaitEvent(c->side_st, c->scan_ev, 0), "pair count readback");
+      GP_CUDA(c, cudaMemcpyAsync(c->h_total, b.total.ptr, 8, cudaMemcpyDeviceToHost, c->side_st),
+              "pair count readback");
+      GP_CUDA(c, cudaEventRecord(c->bin_ev, c->side_st), "pair count readback");
+      c->bin_pending = true;
+      P = cap;
+      spec = true;
+    } else {
+      GP_TRY(scan_counts(c, n, st, &P));
+    }
   } else if (n > 0) {
     GP_CUDA(c, cudaMemsetAsync(b.counts.ptr, 0, (size_t)n * 8, st), "clear counts");
     GP_CUDA(c, cudaMemsetAsync(b.offsets.ptr, 0, (size_t)n * 8, st), "clear offsets");
   }
   *sorted_vals = nullptr;
   if (P > 0) {
-    GP_TRY(reserve_pairs(c, P));
+    // an eighth more than this call needs, so that the next calls' counts
+    // usually fit the buffers a speculative binning is sized by
+    if (!spec) GP_TRY(reserve_pairs(c, (uint32_t)std::min<uint64_t>((uint64_t)P + P / 8, (uint64_t)INT32_MAX - 1)));
     launch_slice_emit(A, (const SliceRec*)b.rec.ptr, (const unsigned long long*)b.offsets.ptr,
-                      (const unsigned long long*)b.counts.ptr, (uint32_t*)b.keys.ptr, (uint32_t*)b.vals.ptr, (uint32_t*)b.emit_gid.ptr, st);
+                      (const unsigned long long*)b.counts.ptr, (uint32_t*)b.keys.ptr, (uint32_t*)b.vals.ptr,
+                      (uint32_t*)b.emit_gid.ptr, st, P);
     c->bin_gid_vals = c->cfg.deterministic == 0;
     GP_TRY(sort_and_range(c, P, nkeys, st, sorted_vals,
                           c->bin_gid_vals ? (const uint32_t*)b.emit_gid.ptr : nullptr));
   }
+  if (spec) c->bin_cap = P;
   *pairs_out = P;
   c->last_pairs = P;
   c->last_issued = (int64_t)P * tile * tile;
@@ -457,6 +529,16 @@ gp_status gp_create(gp_ctx** out, int device, const gp_config* cfg) {
     delete ctx;
     return GP_ERR_OOM;
   }
+  if (cudaEventCreateWithFlags(&ctx->impl.bin_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->impl.scan_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->impl.side_st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->impl.bin_ev) cudaEventDestroy(ctx->impl.bin_ev);
+    if (ctx->impl.scan_ev) cudaEventDestroy(ctx->impl.scan_ev);
+    cudaFreeHost(ctx->impl.h_total);
+    delete ctx;
+    return GP_ERR_CUDA;
+  }
   cudaDeviceGetAttribute(&ctx->impl.sm_count, cudaDevAttrMultiProcessorCount, device);
   *out = ctx;
   return GP_OK;
@@ -474,6 +556,9 @@ gp_status gp_destroy(gp_ctx* ctx) {
   }
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   if (c->h_total) cudaFreeHost(c->h_total);
+  if (c->bin_ev) cudaEventDestroy(c->bin_ev);
+  if (c->scan_ev) cudaEventDestroy(c->scan_ev);
+  if (c->side_st) cudaStreamDestroy(c->side_st);
   delete ctx;
   return GP_OK;
 }
@@ -502,18 +587,25 @@ static gp_status render_impl(gp_ctx* ctx, const gp_set* set, const View& view, c
   SliceArgs a;
   uint32_t P = 0;
   const uint32_t* vals = nullptr;
-  GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals, vox));
-  if (S == 0) return GP_OK;
-  if (P == 0) {
-    GP_CUDA(c, cudaMemsetAsync(out, 0, (size_t)S * H * W * 4, st), "clear out");
-    return check_after(c, st);
-  }
-  {
-    PhaseTimer timer(c, vox ? GP_PHASE_VOX_FWD : GP_PHASE_FWD, st);
-    GP_CUDA(c, launch_raster_fwd(a, fwd_px(c), c->cfg.raster, c->cfg.exp_mode, (const SliceRec*)c->b.rec.ptr, vals,
-                                 c->bin_gid_vals ? nullptr : (const uint32_t*)c->b.emit_gid.ptr,
-                                 (const uint2*)c->b.ranges.ptr, out, st, P),
-            "raster forward");
+  // the first attempt bins speculatively; a count that overflowed the buffers
+  // is binned again with its readback, and the forward repeated
+  for (int attempt = 0;; ++attempt) {
+    GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals, vox, attempt == 0));
+    if (S == 0) return GP_OK;
+    if (P == 0) {
+      GP_CUDA(c, cudaMemsetAsync(out, 0, (size_t)S * H * W * 4, st), "clear out");
+      return check_after(c, st);
+    }
+    {
+      PhaseTimer timer(c, vox ? GP_PHASE_VOX_FWD : GP_PHASE_FWD, st);
+      GP_CUDA(c, launch_raster_fwd(a, fwd_px(c), c->cfg.raster, c->cfg.exp_mode, (const SliceRec*)c->b.rec.ptr, vals,
+                                   c->bin_gid_vals ? nullptr : (const uint32_t*)c->b.emit_gid.ptr,
+                                   (const uint2*)c->b.ranges.ptr, out, st, P),
+              "raster forward");
+    }
+    bool redo = false;
+    GP_TRY(finish_bin(c, &redo));
+    if (!redo) break;
   }
   return check_after(c, st);
 }
@@ -532,38 +624,49 @@ static gp_status backward_impl(gp_ctx* ctx, const gp_set* set, const View& view,
   uint32_t P = 0;
   const uint32_t* vals = nullptr;
   if (vox) sigma_z = 0.0f;  // the key of voxelizer bins (slices never have sigma_z = 0)
-  if (c->cfg.reuse_bins && S > 0 && z && bins_match(c, set, z, S, H, W, sigma_z, view)) {
-    memcpy(&a, c->bin_args, sizeof(SliceArgs));
-    P = c->bin_pairs;
-    vals = c->bin_vals;
-  } else {
-    GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals, vox));
+  const bool reuse = c->cfg.reuse_bins && S > 0 && z && bins_match(c, set, z, S, H, W, sigma_z, view);
+  // a fresh binning is speculative on the first attempt (see render_impl)
+  for (int attempt = 0;; ++attempt) {
+    if (reuse) {
+      memcpy(&a, c->bin_args, sizeof(SliceArgs));
+      P = c->bin_pairs;
+      vals = c->bin_vals;
+    } else {
+      GP_TRY(bin_slices(c, set, z, S, H, W, sigma_z, view, st, &a, &P, &vals, vox, attempt == 0));
+    }
+    if (n == 0) {
+      bool redo = false;
+      GP_TRY(finish_bin(c, &redo));
+      return GP_OK;
+    }
+    BinBufs& b = c->b;
+    GP_TRY(ws_reserve(c, b.accum, (size_t)n * 10 * 4));
+    const bool det = c->cfg.deterministic != 0;
+    if (det) {
+      GP_TRY(ws_reserve(c, b.partial, (size_t)std::max<uint32_t>(P, 1) * 32));
+    } else {
+      GP_CUDA(c, cudaMemsetAsync(b.accum.ptr, 0, (size_t)n * 10 * 4, st), "clear accumulators");
+    }
+    if (P > 0) {
+      PhaseTimer timer(c, vox ? GP_PHASE_VOX_BWD : GP_PHASE_BWD, st);
+      GP_CUDA(c, launch_raster_bwd(a, bwd_px(c), c->cfg.raster, c->cfg.exp_mode, det, (const SliceRec*)b.rec.ptr,
+                                   vals, c->bin_gid_vals ? nullptr : (const uint32_t*)b.emit_gid.ptr,
+                                   (const uint2*)b.ranges.ptr, dL_dI,
+                                   (float*)b.accum.ptr, (float4*)b.partial.ptr, st),
+              "raster backward");
+    }
+    {
+      PhaseTimer timer(c, vox ? GP_PHASE_VOX_BWD : GP_PHASE_BWD_PRE, st);
+      if (det)
+        launch_det_reduce(n, (const unsigned long long*)b.offsets.ptr, (const unsigned long long*)b.counts.ptr,
+                          (const float4*)b.partial.ptr, (float*)b.accum.ptr, st);
+      launch_slice_bwd_pre(a, (const float*)b.accum.ptr, d_mu, d_scale, d_quat, d_alpha, st);
+    }
+    GP_TRY(cuda_err(c, cudaGetLastError(), "backward kernels"));
+    bool redo = false;
+    GP_TRY(finish_bin(c, &redo));
+    if (!redo) break;
   }
-  if (n == 0) return GP_OK;
-  BinBufs& b = c->b;
-  GP_TRY(ws_reserve(c, b.accum, (size_t)n * 10 * 4));
-  const bool det = c->cfg.deterministic != 0;
-  if (det) {
-    GP_TRY(ws_reserve(c, b.partial, (size_t)std::max<uint32_t>(P, 1) * 32));
-  } else {
-    GP_CUDA(c, cudaMemsetAsync(b.accum.ptr, 0, (size_t)n * 10 * 4, st), "clear accumulators");
-  }
-  if (P > 0) {
-    PhaseTimer timer(c, vox ? GP_PHASE_VOX_BWD : GP_PHASE_BWD, st);
-    GP_CUDA(c, launch_raster_bwd(a, bwd_px(c), c->cfg.raster, c->cfg.exp_mode, det, (const SliceRec*)b.rec.ptr, vals,
-                                 c->bin_gid_vals ? nullptr : (const uint32_t*)b.emit_gid.ptr,
-                                 (const uint2*)b.ranges.ptr, dL_dI,
-                                 (float*)b.accum.ptr, (float4*)b.partial.ptr, st),
-            "raster backward");
-  }
-  {
-    PhaseTimer timer(c, vox ? GP_PHASE_VOX_BWD : GP_PHASE_BWD_PRE, st);
-    if (det)
-      launch_det_reduce(n, (const unsigned long long*)b.offsets.ptr, (const unsigned long long*)b.counts.ptr,
-                        (const float4*)b.partial.ptr, (float*)b.accum.ptr, st);
-    launch_slice_bwd_pre(a, (const float*)b.accum.ptr, d_mu, d_scale, d_quat, d_alpha, st);
-  }
-  GP_TRY(cuda_err(c, cudaGetLastError(), "backward kernels"));
   return check_after(c, st);
 }
 

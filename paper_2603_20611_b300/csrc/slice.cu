@@ -361,13 +361,14 @@ template <bool EMIT>
 __global__ void __launch_bounds__(BAL_WARPS * 32) k_slice_bal(SliceArgs a, SliceRec* __restrict__ rec,
                                                               unsigned long long* __restrict__ counts,
                                                               const unsigned long long* __restrict__ offsets,
+                                                              unsigned long long cap,
                                                               uint32_t* __restrict__ keys,
                                                               uint32_t* __restrict__ emit_gid) {
   __shared__ BalSmem sm[BAL_WARPS];
   const int w = threadIdx.x >> 5;
   const int i0 = (blockIdx.x * BAL_WARPS + w) * 32;
   if (i0 >= a.n) return;  // uniform over the warp
-  bal_warp<EMIT>(a, i0, 0, min(32, a.n - i0), 0, sm[w], rec, counts, offsets, ~0ull, keys, emit_gid);
+  bal_warp<EMIT>(a, i0, 0, min(32, a.n - i0), 0, sm[w], rec, counts, offsets, cap, keys, emit_gid);
 }
 
 // Batched form: the warp's 32 batch-wide Gaussians, one item at a time (items
@@ -397,8 +398,8 @@ __global__ void __launch_bounds__(BAL_WARPS * 32) k_slice_bal_batch(BatchItems b
 
 void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
   if (a.n <= 0) return;
-  k_slice_bal<false><<<ceil_div(a.n, BAL_WARPS * 32), BAL_WARPS * 32, 0, st>>>(a, rec, counts, nullptr, nullptr,
-                                                                               nullptr);
+  k_slice_bal<false><<<ceil_div(a.n, BAL_WARPS * 32), BAL_WARPS * 32, 0, st>>>(a, rec, counts, nullptr, 0ull,
+                                                                               nullptr, nullptr);
   note_launch();
 }
 
@@ -411,11 +412,11 @@ void launch_slice_pre_batch(const BatchItems& b, SliceRec* rec, unsigned long lo
 
 void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* offsets,
                        const unsigned long long* counts, uint32_t* keys, uint32_t* vals, uint32_t* emit_gid,
-                       cudaStream_t st) {
+                       cudaStream_t st, unsigned long long cap) {
   (void)vals;  // the sort generates the identity values itself
   if (a.n <= 0) return;
   k_slice_bal<true><<<ceil_div(a.n, BAL_WARPS * 32), BAL_WARPS * 32, 0, st>>>(
-      a, const_cast<SliceRec*>(rec), const_cast<unsigned long long*>(counts), offsets, keys, emit_gid);
+      a, const_cast<SliceRec*>(rec), const_cast<unsigned long long*>(counts), offsets, cap, keys, emit_gid);
   note_launch();
 }
 

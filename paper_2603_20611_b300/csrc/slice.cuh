@@ -86,10 +86,11 @@ cudaError_t launch_raster_bwd_px_batch(const BatchItems& b, int tile, int px, in
 
 // K-pre: records + per-Gaussian pair counts.
 void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st);
-// K-emit: (slice, tile) keys, identity values, emission -> Gaussian id.
+// K-emit: (slice, tile) keys, identity values, emission -> Gaussian id; no
+// pair at or past index cap is written.
 void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* offsets,
                        const unsigned long long* counts, uint32_t* keys, uint32_t* vals, uint32_t* emit_gid,
-                       cudaStream_t st);
+                       cudaStream_t st, unsigned long long cap = ~0ull);
 // K-range: [start, end) of each key in the sorted key list; ranges must be zeroed.
 void launch_ranges(const uint32_t* keys, const unsigned long long* n_dev, uint32_t cap, uint32_t nkeys,
                    uint2* ranges, cudaStream_t st);
