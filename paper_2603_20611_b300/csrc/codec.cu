@@ -21,7 +21,13 @@
 // (__fsub_rn / __fmul_rn / __fadd_rn / __fdiv_rn / __fsqrt_rn: no contraction),
 // except the scale code, which counts the double-precision thresholds
 // exp(L0 + (k - 1/2) D), k = 1..4095, not above the scale (round to nearest in
-// the log domain without a device logarithm).
+// the log domain without a device logarithm).  The device compares the fp32
+// scale with each threshold's ceiling in fp32 (the smallest float not below
+// it), which takes exactly the double comparison's decision for every fp32
+// scale.  The 11 codes of a Gaussian are kept together (32 bytes) so that the
+// Morton-order gather reads two 16-byte vectors per Gaussian; decoded scales
+// come from a 4096-entry table of exp(L0 + c D) computed in double on the
+// device.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -39,17 +45,19 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kScaleLevels = 4095;  // 12-bit codes 0..4095
 
+constexpr int kCodeStride = 16;      // uint16 slots per Gaussian in the code buffer (11 used)
+
 struct QuantArgs {
   float lo[3], inv[3];
   int top;          // 2^B - 1
   int bits;
   int scale_range;  // 0: all scales equal (codes 0)
-  const double* th; // kScaleLevels thresholds
+  const float* th;  // kScaleLevels thresholds, each rounded up to fp32
 };
 
 struct DequantArgs {
   float lo[3], step[3];
-  double L0, D;
+  const float* scale_of;  // decoded scale of each 12-bit code
 };
 
 __device__ __forceinline__ void mm_merge(float* a, const float* b) {
@@ -116,12 +124,36 @@ __global__ void __launch_bounds__(kThreads) k_codec_minmax(const float* __restri
   }
 }
 
-__global__ void k_codec_minmax_final(const float* __restrict__ part, int nb, float* __restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// the blocks' partials merged by one block (min and max are exact, so the
+// order of the merge does not matter)
+__global__ void __launch_bounds__(kThreads) k_codec_minmax_final(const float* __restrict__ part, int nb,
+                                                                float* __restrict__ out) {
   float m[8];
-  for (int k = 0; k < 8; ++k) m[k] = part[k];
-  for (int b = 1; b < nb; ++b) mm_merge(m, part + 8 * b);
-  for (int k = 0; k < 8; ++k) out[k] = m[k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    m[2 * k] = INFINITY;
+    m[2 * k + 1] = -INFINITY;
+  }
+  for (int b = threadIdx.x; b < nb; b += kThreads) mm_merge(m, part + 8 * b);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float v = __shfl_xor_sync(0xffffffffu, m[k], o);
+      m[k] = (k & 1) ? fmaxf(m[k], v) : fminf(m[k], v);
+    }
+  }
+  __shared__ float sm[kThreads / 32][8];
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sm[threadIdx.x >> 5][k] = m[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kThreads / 32; ++w) mm_merge(sm[0], sm[w]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) out[k] = sm[0][k];
+  }
 }
 
 __device__ __forceinline__ int q_affine(float v, float lo, float inv, int top) {
@@ -144,24 +176,25 @@ __global__ void __launch_bounds__(kThreads) k_codec_quant(QuantArgs p, const flo
                                                          uint32_t* __restrict__ khi) {
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i >= n) return;
+  uint32_t cw[kCodeStride / 2] = {};  // the Gaussian's codes, two per word (code 2m in the low half)
   int pc[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    pc[k] = q_affine(mu[3 * i + k], p.lo[k], p.inv[k], p.top);
-    codes[(int64_t)k * n + i] = (uint16_t)pc[k];
-  }
+  for (int k = 0; k < 3; ++k) pc[k] = q_affine(mu[3 * i + k], p.lo[k], p.inv[k], p.top);
   unsigned long long key = 0;
   for (int j = 0; j < p.bits; ++j)
 #pragma unroll
     for (int a = 0; a < 3; ++a) key |= (unsigned long long)((pc[a] >> j) & 1) << (3 * j + a);
   klo[i] = (uint32_t)key;
   khi[i] = (uint32_t)(key >> 32);
+  int c11[11];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) c11[k] = pc[k];
   // scales: number of thresholds not above s
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     int c = 0;
     if (p.scale_range) {
-      const double sv = (double)scale[3 * i + k];
+      const float sv = scale[3 * i + k];
       int lo = 0, hi = kScaleLevels;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -170,7 +203,7 @@ __global__ void __launch_bounds__(kThreads) k_codec_quant(QuantArgs p, const flo
       }
       c = lo;
     }
-    codes[(int64_t)(3 + k) * n + i] = (uint16_t)c;
+    c11[3 + k] = c;
   }
   // quaternion: normalised (w, x, y, z summed in order), folded to w >= 0
   const float4 q = reinterpret_cast<const float4*>(quat)[i];
@@ -191,15 +224,27 @@ __global__ void __launch_bounds__(kThreads) k_codec_quant(QuantArgs p, const flo
     for (int k = 0; k < 4; ++k) c4[k] = -c4[k];
   }
 #pragma unroll
-  for (int k = 0; k < 4; ++k) codes[(int64_t)(6 + k) * n + i] = (uint16_t)q_12(__fmul_rn(__fadd_rn(c4[k], 1.0f), 2047.5f));
+  for (int k = 0; k < 4; ++k) c11[6 + k] = q_12(__fmul_rn(__fadd_rn(c4[k], 1.0f), 2047.5f));
   const float a = fminf(fmaxf(alpha[i], 0.0f), 1.0f);
-  codes[(int64_t)10 * n + i] = (uint16_t)q_12(__fmul_rn(a, 4095.0f));
+  c11[10] = q_12(__fmul_rn(a, 4095.0f));
+#pragma unroll
+  for (int k = 0; k < 11; ++k) cw[k >> 1] |= (uint32_t)(uint16_t)c11[k] << (16 * (k & 1));
+  uint4* dst = reinterpret_cast<uint4*>(codes + (size_t)i * kCodeStride);
+  dst[0] = make_uint4(cw[0], cw[1], cw[2], cw[3]);
+  dst[1] = make_uint4(cw[4], cw[5], cw[6], cw[7]);
 }
 
 __global__ void k_codec_gather_u32(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx, int64_t n,
                                    uint32_t* __restrict__ dst) {
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i < n) dst[i] = src[idx[i]];
+}
+
+__device__ __forceinline__ void load_codes(const uint16_t* __restrict__ codes, uint32_t g, uint32_t* w) {
+  const uint4* src = reinterpret_cast<const uint4*>(codes + (size_t)g * kCodeStride);
+  const uint4 a = src[0], b = src[1];
+  w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+  w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
 }
 
 __global__ void __launch_bounds__(kThreads) k_codec_delta(const uint16_t* __restrict__ codes,
@@ -209,15 +254,23 @@ __global__ void __launch_bounds__(kThreads) k_codec_delta(const uint16_t* __rest
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i >= n) return;
   const uint32_t cur = order[i];
-  const uint32_t prv = i > 0 ? order[i - 1] : 0u;
+  uint32_t wc[8], wp[8] = {};
+  load_codes(codes, cur, wc);
+  if (i > 0) load_codes(codes, order[i - 1], wp);
 #pragma unroll
   for (int a = 0; a < 11; ++a) {
-    const int c = codes[(int64_t)a * n + cur];
-    const int b = i > 0 ? (int)codes[(int64_t)a * n + prv] : 0;
+    const int c = (int)((wc[a >> 1] >> (16 * (a & 1))) & 0xffffu);
+    const int b = (int)((wp[a >> 1] >> (16 * (a & 1))) & 0xffffu);
     const int d = c - b;
     streams[(int64_t)a * n + i] = (uint16_t)(d >= 0 ? 2 * d : -2 * d - 1);
   }
   if (order_out) order_out[i] = cur;
+}
+
+// decoded scale of every 12-bit code: exp(L0 + c D) in double, rounded to fp32
+__global__ void k_codec_scale_table(double L0, double D, float* __restrict__ table) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c <= kScaleLevels) table[c] = (float)exp(L0 + (double)c * D);
 }
 
 __global__ void __launch_bounds__(kThreads) k_codec_unzig(const uint16_t* __restrict__ streams, int64_t total,
@@ -244,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_codec_dequant(DequantArgs p, const
 #pragma unroll
   for (int k = 0; k < 3; ++k) mu[3 * i + k] = __fadd_rn(p.lo[k], __fmul_rn((float)c[k], p.step[k]));
 #pragma unroll
-  for (int k = 0; k < 3; ++k) scale[3 * i + k] = (float)exp(p.L0 + (double)c[3 + k] * p.D);
+  for (int k = 0; k < 3; ++k) scale[3 * i + k] = p.scale_of[min(max(c[3 + k], 0), kScaleLevels)];
   float4 q;
   q.x = __fsub_rn(__fdiv_rn((float)c[6], 2047.5f), 1.0f);
   q.y = __fsub_rn(__fdiv_rn((float)c[7], 2047.5f), 1.0f);
@@ -291,14 +344,14 @@ gp_status gp_encode(gp_ctx* ctx, const gp_set* set, int pos_bits, gp_codec_heade
   const int nb = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 4 * (int64_t)c->sm_count);
   // scratch: codes | klo | khi | vals (4 buffers) | gather | th | part | mm | bad | n_dev
   const size_t o_codes = 0;
-  const size_t o_klo = o_codes + align256((size_t)11 * n * 2);
+  const size_t o_klo = o_codes + align256((size_t)kCodeStride * n * 2);
   const size_t o_khi = o_klo + align256((size_t)n * 4);
   const size_t o_k2 = o_khi + align256((size_t)n * 4);
   const size_t o_v1 = o_k2 + align256((size_t)n * 4);
   const size_t o_v2 = o_v1 + align256((size_t)n * 4);
   const size_t o_g = o_v2 + align256((size_t)n * 4);
   const size_t o_th = o_g + align256((size_t)n * 4);
-  const size_t o_part = o_th + align256((size_t)kScaleLevels * 8);
+  const size_t o_part = o_th + align256((size_t)kScaleLevels * 4);
   const size_t o_mm = o_part + align256((size_t)nb * 32);
   const size_t o_nd = o_mm + 256;
   const size_t total = o_nd + 256;
@@ -313,7 +366,7 @@ gp_status gp_encode(gp_ctx* ctx, const gp_set* set, int pos_bits, gp_codec_heade
   uint32_t* v1 = (uint32_t*)(base + o_v1);
   uint32_t* v2 = (uint32_t*)(base + o_v2);
   uint32_t* g = (uint32_t*)(base + o_g);
-  double* th = (double*)(base + o_th);
+  float* th = (float*)(base + o_th);
   float* part = (float*)(base + o_part);
   float* mm = (float*)(base + o_mm);
   unsigned* bad = (unsigned*)(base + o_mm + 32);  // read back with the 8 floats before it
@@ -321,7 +374,7 @@ gp_status gp_encode(gp_ctx* ctx, const gp_set* set, int pos_bits, gp_codec_heade
   // bounding box, scale range, argument check
   if (cudaMemsetAsync(bad, 0, 4, st) != cudaSuccess) return cuda_err(c, cudaGetLastError(), "codec memset");
   k_codec_minmax<<<nb, kThreads, 0, st>>>(set->mu, set->scale, set->quat, set->alpha, n, part, bad);
-  k_codec_minmax_final<<<1, 32, 0, st>>>(part, nb, mm);
+  k_codec_minmax_final<<<1, kThreads, 0, st>>>(part, nb, mm);
   note_launch(2);
   float h[9];
   if (cudaMemcpyAsync(h, mm, 36, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -346,10 +399,17 @@ gp_status gp_encode(gp_ctx* ctx, const gp_set* set, int pos_bits, gp_codec_heade
   qa.scale_range = header->log_s_max > header->log_s_min ? 1 : 0;
   qa.th = th;
   if (qa.scale_range) {
-    std::vector<double> t(kScaleLevels);
+    // each threshold's fp32 ceiling: for an fp32 scale s, t <= (double)s exactly
+    // when ceil32(t) <= s
+    std::vector<float> t(kScaleLevels);
     const double D = (header->log_s_max - header->log_s_min) / (double)kScaleLevels;
-    for (int k = 1; k <= kScaleLevels; ++k) t[k - 1] = exp(header->log_s_min + ((double)k - 0.5) * D);
-    if (cudaMemcpyAsync(th, t.data(), t.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    for (int k = 1; k <= kScaleLevels; ++k) {
+      const double tk = exp(header->log_s_min + ((double)k - 0.5) * D);
+      float f = (float)tk;
+      if ((double)f < tk) f = nextafterf(f, INFINITY);
+      t[k - 1] = f;
+    }
+    if (cudaMemcpyAsync(th, t.data(), t.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return cuda_err(c, cudaGetLastError(), "codec thresholds");
   }
   const unsigned grid = (unsigned)((n + kThreads - 1) / kThreads);
@@ -403,10 +463,14 @@ gp_status gp_decode(gp_ctx* ctx, const gp_codec_header* header, const uint16_t* 
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t tot = 11 * n;
   BinBufs& b = c->b;
-  CODEC_TRY(ws_reserve(c, b.codec, 2 * align256((size_t)tot * 4)));
+  CODEC_TRY(ws_reserve(c, b.codec, 2 * align256((size_t)tot * 4) + align256((kScaleLevels + 1) * 4)));
   CODEC_TRY(ws_reserve(c, b.scan_tmp, (size_t)scan_temp_bytes(tot)));
   uint32_t* d = (uint32_t*)b.codec.ptr;
   uint32_t* ex = (uint32_t*)((char*)b.codec.ptr + align256((size_t)tot * 4));
+  float* scale_of = (float*)((char*)b.codec.ptr + 2 * align256((size_t)tot * 4));
+  k_codec_scale_table<<<(kScaleLevels + 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(
+      header->log_s_min, (header->log_s_max - header->log_s_min) / (double)kScaleLevels, scale_of);
+  note_launch();
   k_codec_unzig<<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, st>>>(streams, tot, d);
   note_launch();
   cudaError_t e = exclusive_scan<uint32_t>(d, ex, tot, nullptr, b.scan_tmp.ptr, st);
@@ -417,8 +481,7 @@ gp_status gp_decode(gp_ctx* ctx, const gp_codec_header* header, const uint16_t* 
     p.lo[k] = header->lo[k];
     p.step[k] = (header->hi[k] - header->lo[k]) / top;
   }
-  p.L0 = header->log_s_min;
-  p.D = (header->log_s_max - header->log_s_min) / (double)kScaleLevels;
+  p.scale_of = scale_of;
   k_codec_dequant<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(p, d, ex, n, mu, scale, quat,
                                                                                    alpha);
   note_launch();

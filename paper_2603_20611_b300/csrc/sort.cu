@@ -11,8 +11,10 @@
 // Radix sort, per 8-bit digit pass:
 //   1. k_radix_hist     per 4096-key tile: 256-bin histogram (shared atomics),
 //                       stored digit-major hist[d * nb + b];
-//   2. exclusive scan   of hist -> global scatter base of (digit, tile);
-//   3. k_radix_scatter  per tile, each warp ranks its own 512 keys in 16 rounds
+//   2. k_radix_colscan  one CTA per digit: exclusive scan of the digit's row
+//                       over the tiles (in place) and the digit's total;
+//   3. k_radix_scatter  per tile: the digits' global starts (a scan of the 256
+//                       totals plus the tile's row entry); each warp ranks its own 512 keys in 16 rounds
 //                       of 32 (nine ballots give each key the lanes holding the
 //                       same digit, a running per-warp digit count the rest), a
 //                       per-digit prefix over the 8 warps gives tile-local
@@ -202,6 +204,36 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __res
   hist[(size_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
 }
 
+// Exclusive scan of each digit's row of the digit-major histogram over the
+// tiles, in place, one CTA per digit, and the digit's total.
+constexpr int CS_THREADS = 512;
+constexpr int CS_ITEMS = 8;
+
+__global__ void __launch_bounds__(CS_THREADS) k_radix_colscan(uint32_t* __restrict__ hist, int nb,
+                                                               uint32_t* __restrict__ dtot) {
+  __shared__ uint32_t sw[CS_THREADS / 32 + 1];
+  uint32_t* row = hist + (size_t)blockIdx.x * nb;
+  uint32_t carry = 0;
+  for (int base = 0; base < nb; base += CS_THREADS * CS_ITEMS) {
+    const int i0 = base + threadIdx.x * CS_ITEMS;
+    uint32_t v[CS_ITEMS], sum = 0;
+#pragma unroll
+    for (int k = 0; k < CS_ITEMS; ++k) {
+      v[k] = i0 + k < nb ? row[i0 + k] : 0u;
+      sum += v[k];
+    }
+    uint32_t tot;
+    uint32_t run = carry + block_exclusive_scan<uint32_t, CS_THREADS>(sum, sw, &tot);
+#pragma unroll
+    for (int k = 0; k < CS_ITEMS; ++k) {
+      if (i0 + k < nb) row[i0 + k] = run;
+      run += v[k];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
+}
+
 // Stable scatter of one 4096-key tile.  Warp w owns the tile's keys
 // [w * 512, (w + 1) * 512) and ranks them in 16 rounds of 32 against its own
 // per-digit counters (nine ballots give the rank among equal digits in a round),
@@ -215,12 +247,12 @@ constexpr int RS_ROUNDS_W = RS_PER_WARP / 32;       // 16 rounds
 __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const unsigned long long* __restrict__ n_dev, uint32_t cap, int shift,
-    const uint32_t* __restrict__ hist, int nb) {
+    const uint32_t* __restrict__ hist, int nb, const uint32_t* __restrict__ dtot) {
   __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
   __shared__ uint32_t dlocal[RS_BINS];   // tile-local start of each digit
   __shared__ uint32_t dglobal[RS_BINS];  // global start of each digit of this tile
   __shared__ uint32_t skey[RS_TILE], sval[RS_TILE];
-  __shared__ uint32_t swarp[RS_WARPS + 1];
+  __shared__ uint32_t swarp[RS_WARPS + 1], sgw[RS_WARPS];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t n = load_count(n_dev, cap);
   const uint32_t tile0 = blockIdx.x * RS_TILE;
@@ -271,27 +303,39 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(
     wcnt[w][t] = tot;
     tot += c;
   }
-  dglobal[t] = hist[(size_t)t * nb + blockIdx.x];
-  // exclusive scan of the digit totals over the 256 digits (warp scans + warp sums)
-  uint32_t inc = tot;
+  // exclusive scans over the 256 digits (warp scans + warp sums): the tile's
+  // digit totals (tile-local starts) and the digits' totals over all keys
+  // (where each digit starts in the output)
+  const uint32_t g = dtot[t];
+  uint32_t inc = tot, ginc = g;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += u;
+    const uint32_t gu = __shfl_up_sync(0xffffffffu, ginc, o);
+    if (lane >= o) {
+      inc += u;
+      ginc += gu;
+    }
   }
-  if (lane == 31) swarp[warp] = inc;
+  if (lane == 31) {
+    swarp[warp] = inc;
+    sgw[warp] = ginc;
+  }
   __syncthreads();
   if (t == 0) {
-    uint32_t run = 0;
+    uint32_t run = 0, grun = 0;
     for (int w = 0; w < RS_WARPS; ++w) {
-      const uint32_t c = swarp[w];
+      const uint32_t c = swarp[w], gc = sgw[w];
       swarp[w] = run;
+      sgw[w] = grun;
       run += c;
+      grun += gc;
     }
     swarp[RS_WARPS] = run;
   }
   __syncthreads();
   dlocal[t] = swarp[warp] + inc - tot;
+  dglobal[t] = sgw[warp] + ginc - g + hist[(size_t)t * nb + blockIdx.x];
   __syncthreads();
   // local stable placement in digit order
 #pragma unroll
@@ -321,7 +365,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(
 int64_t radix_temp_bytes(int64_t cap) {
   int64_t nb = (cap + RS_TILE - 1) / RS_TILE;
   int64_t hist = (int64_t)RS_BINS * nb;
-  return ((hist * 4 + 255) / 256) * 256 + scan_temp_bytes(hist) + 64;
+  return ((hist * 4 + 255) / 256) * 256 + RS_BINS * 4;
 }
 
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
@@ -333,14 +377,14 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
   int nb = (int)((cap + RS_TILE - 1) / RS_TILE);
   uint32_t* hist = (uint32_t*)temp;
   int64_t nh = (int64_t)RS_BINS * nb;
-  void* stemp = (char*)temp + ((nh * 4 + 255) / 256) * 256;
+  uint32_t* dtot = (uint32_t*)((char*)temp + ((nh * 4 + 255) / 256) * 256);
   uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
   for (int shift = 0; shift < bits; shift += 8) {
     k_radix_hist<<<nb, RS_THREADS, 0, st>>>(ki, n_dev, cap, shift, hist, nb);
-    cudaError_t e = exclusive_scan<uint32_t>(hist, hist, nh, nullptr, stemp, st);
-    if (e != cudaSuccess) return e;
-    k_radix_scatter<<<nb, RS_THREADS, 0, st>>>(ki, shift == 0 ? first_vals : vi, ko, vo, n_dev, cap, shift, hist, nb);
-    note_launch(2);
+    k_radix_colscan<<<RS_BINS, CS_THREADS, 0, st>>>(hist, nb, dtot);
+    k_radix_scatter<<<nb, RS_THREADS, 0, st>>>(ki, shift == 0 ? first_vals : vi, ko, vo, n_dev, cap, shift, hist, nb,
+                                               dtot);
+    note_launch(3);
     uint32_t* tk = ki; ki = ko; ko = tk;
     uint32_t* tv = vi; vi = vo; vo = tv;
     *result_in_alt = !*result_in_alt;

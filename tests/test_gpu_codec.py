@@ -45,6 +45,28 @@ def test_encode_is_bit_exact(ctx, bits):
     _check_encode(ctx, g, bits)
 
 
+def test_scale_codes_at_their_thresholds(ctx):
+    """Scales placed on the fp32 values around the codec's double-precision
+    thresholds exp(L0 + (k - 1/2) D) (the float nearest each one and its two
+    neighbours): the device's codes, decided without double arithmetic, equal
+    the oracle's double comparisons."""
+    g = synth.small(seed=430, n=3000, extent=(64, 64, 32))
+    s = g.scale.astype(np.float32).copy()
+    lo, hi = np.float32(0.25), np.float32(12.0)
+    s[0, 0], s[1, 1] = lo, hi  # fixes L0 and L1
+    L0, L1 = float(np.log(np.float64(lo))), float(np.log(np.float64(hi)))
+    th = oc.scale_thresholds(L0, L1)
+    rng = np.random.default_rng(5)
+    ks = rng.choice(th.size, 900, replace=False)
+    f = th[ks].astype(np.float32)
+    cand = np.concatenate([f, np.nextafter(f, np.float32(np.inf)), np.nextafter(f, np.float32(0))])
+    cand = np.clip(cand, lo, hi)
+    flat = s.reshape(-1)
+    flat[10:10 + cand.size] = cand  # after the two fixed entries (flat indices 0 and 4)
+    g2 = synth.GaussianSet(g.mu, flat.reshape(s.shape), g.quat, g.alpha, g.extent)
+    _check_encode(ctx, g2, 12)
+
+
 def test_decode_matches_oracle(ctx):
     g = synth.small(seed=420, n=2500, extent=(64, 64, 32))
     hdr, streams = _check_encode(ctx, g, 14)
