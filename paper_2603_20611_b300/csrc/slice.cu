@@ -429,31 +429,37 @@ void launch_slice_emit_batch(const BatchItems& b, const SliceRec* rec, const uns
   note_launch();
 }
 // ------------------------------------------------------------ K-range
-// Each thread takes four consecutive sorted keys (one 16-byte load; the key
-// array is 16-byte aligned and a vector that would run past cap is read key by
-// key) and its neighbours' last and first keys by shuffle, so every key is
+// Each thread takes RG_KEYS consecutive sorted keys (16-byte loads; the key
+// array is 16-byte aligned and a vector that would run past the count is read
+// key by key) and its neighbours' boundary keys by shuffle, so every key is
 // loaded once.
+constexpr int RG_KEYS = 16;
+
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ keys,
                                                 const unsigned long long* __restrict__ n_dev, uint32_t cap,
                                                 uint32_t nkeys, uint2* __restrict__ ranges) {
   const unsigned long long nn = *n_dev;
   const uint32_t n = nn < cap ? (uint32_t)nn : cap;
-  const uint32_t i0 = 4u * (blockIdx.x * blockDim.x + threadIdx.x);
+  const uint32_t i0 = (uint32_t)RG_KEYS * (blockIdx.x * blockDim.x + threadIdx.x);
   const int lane = threadIdx.x & 31;
-  uint32_t k[4];
-  if (i0 + 4u <= cap) {
-    const uint4 v = *reinterpret_cast<const uint4*>(keys + i0);
-    k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
-  } else {
+  uint32_t k[RG_KEYS];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) k[j] = i0 + (uint32_t)j < cap ? keys[i0 + j] : 0xffffffffu;
+  for (int v = 0; v < RG_KEYS / 4; ++v) {
+    const uint32_t j = i0 + 4u * (uint32_t)v;
+    if (j + 4u <= n) {
+      const uint4 q = *reinterpret_cast<const uint4*>(keys + j);
+      k[4 * v] = q.x; k[4 * v + 1] = q.y; k[4 * v + 2] = q.z; k[4 * v + 3] = q.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) k[4 * v + q] = j + (uint32_t)q < n ? keys[j + q] : 0xffffffffu;
+    }
   }
-  uint32_t prev = __shfl_up_sync(0xffffffffu, k[3], 1);
+  uint32_t prev = __shfl_up_sync(0xffffffffu, k[RG_KEYS - 1], 1);
   uint32_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
   if (lane == 0) prev = (i0 > 0u && i0 - 1u < n) ? keys[i0 - 1u] : 0xffffffffu;
-  if (lane == 31) next = i0 + 4u < n ? keys[i0 + 4u] : 0xffffffffu;
+  if (lane == 31) next = i0 + (uint32_t)RG_KEYS < n ? keys[i0 + RG_KEYS] : 0xffffffffu;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < RG_KEYS; ++j) {
     const uint32_t i = i0 + (uint32_t)j;
     const uint32_t kj = k[j];
     if (i >= n) continue;
@@ -461,7 +467,7 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
       (void)GP_IN_RANGE(9, kj, nkeys);
       continue;
     }
-    const uint32_t before = j == 0 ? prev : k[j - 1], after = j == 3 ? next : k[j + 1];
+    const uint32_t before = j == 0 ? prev : k[j - 1], after = j == RG_KEYS - 1 ? next : k[j + 1];
     if (i == 0u || before != kj) ranges[kj].x = i;
     if (i + 1u == n || after != kj) ranges[kj].y = i + 1u;
   }
@@ -470,7 +476,7 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
 void launch_ranges(const uint32_t* keys, const unsigned long long* n_dev, uint32_t cap, uint32_t nkeys,
                    uint2* ranges, cudaStream_t st) {
   if (cap == 0) return;
-  const int64_t threads = ((int64_t)cap + 3) / 4;
+  const int64_t threads = ((int64_t)cap + RG_KEYS - 1) / RG_KEYS;
   k_ranges<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(keys, n_dev, cap, nkeys, ranges);
   note_launch();
 }
