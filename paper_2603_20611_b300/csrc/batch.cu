@@ -72,6 +72,7 @@ struct gp_plan {
   float* d_z = nullptr;  // per item: sorted positions, order (as int), positions by index
   SliceRec* rec = nullptr;
   unsigned long long *counts = nullptr, *offsets = nullptr, *total = nullptr;
+  unsigned long long *wsum = nullptr, *woff = nullptr;  // per warp of 32 Gaussians: pair total, its scan
   uint32_t *keys = nullptr, *vals = nullptr, *keys_alt = nullptr, *vals_alt = nullptr, *emit_gid = nullptr;
   const uint32_t *sk = nullptr, *sv = nullptr;  // sorted keys / values (one of the two ping-pong buffers)
   uint2* ranges = nullptr;
@@ -185,11 +186,12 @@ static gp_status build_layout(gp_plan* p, int tile) {
 static gp_status enqueue_binning(gp_plan* p, cudaStream_t st) {
   const BatchItems b = batch_view(p);
   GP_CUDAB(p, cudaMemsetAsync(p->ranges, 0, (size_t)std::max<uint32_t>(p->n_keys, 1) * 8, st), "memset ranges");
-  launch_slice_pre_batch(b, p->rec, p->counts, st);
-  GP_CUDAB(p, exclusive_scan<unsigned long long>(p->counts, p->offsets, p->n_gauss, p->total, p->scan_tmp, st),
+  launch_slice_pre_batch(b, p->rec, p->counts, p->wsum, st);
+  GP_CUDAB(p, exclusive_scan<unsigned long long>(p->wsum, p->woff, ceil_div(p->n_gauss, 32), p->total, p->scan_tmp,
+                                                 st),
            "batch scan");
   if (p->cap == 0) return GP_OK;
-  launch_slice_emit_batch(b, p->rec, p->offsets, p->counts, p->cap, p->keys, p->emit_gid, st);
+  launch_slice_emit_batch(b, p->rec, p->woff, p->counts, p->offsets, p->cap, p->keys, p->emit_gid, st);
   int bits = 1;
   while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)p->n_keys) ++bits;
   bool in_alt = false;
@@ -269,8 +271,9 @@ static gp_status enqueue_all(gp_plan* p, cudaStream_t st) {
 // Pairs the batch bins with the current layout (one count, read back).
 static gp_status count_pairs_now(gp_plan* p, unsigned long long* tot) {
   cudaStream_t st = p->cap_stream;
-  launch_slice_pre_batch(batch_view(p), p->rec, p->counts, st);
-  GP_CUDAB(p, exclusive_scan<unsigned long long>(p->counts, p->offsets, p->n_gauss, p->total, p->scan_tmp, st),
+  launch_slice_pre_batch(batch_view(p), p->rec, p->counts, p->wsum, st);
+  GP_CUDAB(p, exclusive_scan<unsigned long long>(p->wsum, p->woff, ceil_div(p->n_gauss, 32), p->total, p->scan_tmp,
+                                                 st),
            "batch scan");
   GP_CUDAB(p, cudaMemcpyAsync(p->h_flag + 2, p->total, 8, cudaMemcpyDeviceToHost, st), "count readback");
   GP_CUDAB(p, cudaStreamSynchronize(st), "count readback");
@@ -471,6 +474,8 @@ static gp_status plan_build(gp_plan* p) {
   GP_TRYB(plan_alloc(p, (void**)&p->rec, sizeof(SliceRec) * std::max<int64_t>(gs, 1)));
   GP_TRYB(plan_alloc(p, (void**)&p->counts, 8 * std::max<int64_t>(gs, 1)));
   GP_TRYB(plan_alloc(p, (void**)&p->offsets, 8 * std::max<int64_t>(gs, 1)));
+  GP_TRYB(plan_alloc(p, (void**)&p->wsum, 8 * std::max<int64_t>((gs + 31) / 32, 1)));
+  GP_TRYB(plan_alloc(p, (void**)&p->woff, 8 * std::max<int64_t>((gs + 31) / 32, 1)));
   GP_TRYB(plan_alloc(p, (void**)&p->total, 64));
   GP_TRYB(plan_alloc(p, &p->scan_tmp, (size_t)scan_temp_bytes(std::max<int64_t>(gs, 1))));
   GP_TRYB(plan_alloc(p, (void**)&p->accum, 40 * std::max<int64_t>(gs, 1)));

@@ -47,7 +47,8 @@ void ws_release_all(Ctx* c);
 struct BinBufs {
   DevBuf rec;        // per-Gaussian record (64 B)
   DevBuf counts;     // per-Gaussian pair count (uint64)
-  DevBuf offsets;    // exclusive scan of counts (uint64)
+  DevBuf offsets;    // exclusive scan of counts (uint64), written by K-emit
+  DevBuf wsum, woff; // per warp of 32 Gaussians: pair total and its exclusive scan (uint64)
   DevBuf total;      // pair total (uint64) + spare slots
   DevBuf keys, vals, keys_alt, vals_alt;  // uint32
   DevBuf emit_gid;   // emission index -> Gaussian id (uint32)

@@ -256,12 +256,17 @@ static gp_status reserve_pairs(Ctx* c, uint32_t P) {
   return GP_OK;
 }
 
-// Scan of the per-Gaussian counts and the one host readback of the total.
+// Scan of the per-warp pair totals (K-emit derives each Gaussian's offset).
+static cudaError_t scan_warp_totals(Ctx* c, int n, cudaStream_t st) {
+  BinBufs& b = c->b;
+  return exclusive_scan<unsigned long long>((unsigned long long*)b.wsum.ptr, (unsigned long long*)b.woff.ptr,
+                                            ceil_div(n, 32), (unsigned long long*)b.total.ptr, b.scan_tmp.ptr, st);
+}
+
+// The scan and the one host readback of the total.
 static gp_status scan_counts(Ctx* c, int n, cudaStream_t st, uint32_t* P) {
   BinBufs& b = c->b;
-  GP_CUDA(c, exclusive_scan<unsigned long long>((unsigned long long*)b.counts.ptr, (unsigned long long*)b.offsets.ptr,
-                                                n, (unsigned long long*)b.total.ptr, b.scan_tmp.ptr, st),
-          "pair scan");
+  GP_CUDA(c, scan_warp_totals(c, n, st), "pair scan");
   GP_CUDA(c, cudaMemcpyAsync(c->h_total, b.total.ptr, 8, cudaMemcpyDeviceToHost, st), "pair count readback");
   GP_CUDA(c, cudaStreamSynchronize(st), "pair count readback");
   unsigned long long tot = *c->h_total;
@@ -366,6 +371,8 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
   GP_TRY(ws_reserve(c, b.rec, (size_t)std::max(n, 1) * sizeof(SliceRec)));
   GP_TRY(ws_reserve(c, b.counts, (size_t)std::max(n, 1) * 8));
   GP_TRY(ws_reserve(c, b.offsets, (size_t)std::max(n, 1) * 8));
+  GP_TRY(ws_reserve(c, b.wsum, (size_t)std::max(ceil_div(n, 32), 1) * 8));
+  GP_TRY(ws_reserve(c, b.woff, (size_t)std::max(ceil_div(n, 32), 1) * 8));
   GP_TRY(ws_reserve(c, b.total, 64));
   GP_TRY(ws_reserve(c, b.scan_tmp, (size_t)scan_temp_bytes(std::max(n, 1))));
   GP_TRY(ws_reserve(c, b.ranges, (size_t)std::max<int64_t>(nkeys, 1) * 8));
@@ -373,7 +380,7 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
   uint32_t P = 0;
   bool spec = false;
   if (n > 0 && S > 0) {
-    launch_slice_pre(A, (SliceRec*)b.rec.ptr, (unsigned long long*)b.counts.ptr, st);
+    launch_slice_pre(A, (SliceRec*)b.rec.ptr, (unsigned long long*)b.counts.ptr, (unsigned long long*)b.wsum.ptr, st);
     // the speculative capacity: the buffers' capacity, but at most a quarter
     // more than the last binning's count (the sort's grids and scans are sized
     // by it)
@@ -381,10 +388,7 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
     if (cap > 0 && c->last_pairs > 0)
       cap = (uint32_t)std::min<int64_t>(cap, std::max<int64_t>(c->last_pairs + c->last_pairs / 4, 4096));
     if (cap > 0) {
-      GP_CUDA(c, exclusive_scan<unsigned long long>((unsigned long long*)b.counts.ptr,
-                                                    (unsigned long long*)b.offsets.ptr, n,
-                                                    (unsigned long long*)b.total.ptr, b.scan_tmp.ptr, st),
-              "pair scan");
+      GP_CUDA(c, scan_warp_totals(c, n, st), "pair scan");
       // the count's copy runs on the context's side stream as soon as the scan
       // is done, beside the emission and the sort
       GP_CUDA(c, cudaEventRecord(c->scan_ev, st), "pair count readback");
@@ -407,9 +411,9 @@ static gp_status bin_slices(Ctx* c, const gp_set* set, const float* z, int S, in
     // an eighth more than this call needs, so that the next calls' counts
     // usually fit the buffers a speculative binning is sized by
     if (!spec) GP_TRY(reserve_pairs(c, (uint32_t)std::min<uint64_t>((uint64_t)P + P / 8, (uint64_t)INT32_MAX - 1)));
-    launch_slice_emit(A, (const SliceRec*)b.rec.ptr, (const unsigned long long*)b.offsets.ptr,
-                      (const unsigned long long*)b.counts.ptr, (uint32_t*)b.keys.ptr, (uint32_t*)b.vals.ptr,
-                      (uint32_t*)b.emit_gid.ptr, st, P);
+    launch_slice_emit(A, (const SliceRec*)b.rec.ptr, (const unsigned long long*)b.woff.ptr,
+                      (const unsigned long long*)b.counts.ptr, (unsigned long long*)b.offsets.ptr,
+                      (uint32_t*)b.keys.ptr, (uint32_t*)b.emit_gid.ptr, st, P);
     c->bin_gid_vals = c->cfg.deterministic == 0;
     GP_TRY(sort_and_range(c, P, nkeys, st, sorted_vals,
                           c->bin_gid_vals ? (const uint32_t*)b.emit_gid.ptr : nullptr));

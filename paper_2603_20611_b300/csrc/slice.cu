@@ -225,24 +225,26 @@ __device__ __forceinline__ int find_item(const T* __restrict__ t, int n, T x) {
 // the emission agree by construction.
 constexpr int BAL_WARPS = 4;
 
+template <bool EMIT>
 struct BalSmem {
   SliceRec rec[32];  // the warp's records
   int item0[33];     // exclusive prefix of the lanes' plane counts
   int plo[32];       // each lane's first sorted plane
   int row0[33];      // exclusive prefix of the current items' tile-row counts
-  int owner[32], j[32], ty0[32];
+  int owner[32], ty0[32];
   float mx[32], my[32], k2e[32], rxe[32], rye[32];
   unsigned cnt[32];  // K-pre: pairs of each lane's Gaussian
+  int iown[32];      // the lane owning each item of the current round
+  int rown[32];      // the item slot owning each tile row of the current round
+  uint32_t kb[32];    // K-emit: the key of each current item's plane and tile (0, 0)
 };
 
-// m in [0, 32) with pre[m] <= x < pre[m + 1], for pre ascending, pre[0] <= x < pre[32].
-__device__ __forceinline__ int bal_slot(const int* pre, int x) {
-  int lo = 0, hi = 32;
-  while (hi - lo > 1) {
-    const int m = (lo + hi) >> 1;
-    if (pre[m] <= x) lo = m; else hi = m;
-  }
-  return lo;
+// Marks the slots [c0, c0 + 32) of a round that this lane's run [b, e) of a
+// warp-wide sequence covers with the lane's index (each slot is covered by
+// exactly one lane), so that a lane finds the owner of its slot with one load.
+__device__ __forceinline__ void bal_mark(int* own, int b, int e, int c0, int lane) {
+  const int s = max(b, c0) - c0, t = min(e, c0 + 32) - c0;
+  for (int p = s; p < t; ++p) own[p] = lane;
 }
 
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
@@ -258,13 +260,13 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 // i0 + [lane_lo, lane_hi) (local index = batch-wide index - gbase0).  K-pre
 // (EMIT false): make the records, store them and the pair counts.  K-emit (EMIT
 // true): read the records and write the pairs (keys and batch-wide Gaussian
-// ids) from offsets[i0 + lane_lo] on, never at or past `cap`.
+// ids) from index e0 on, never at or past e_end.
 template <bool EMIT>
 __device__ __forceinline__ void bal_warp(const SliceArgs& a, int i0, int lane_lo, int lane_hi, int gbase0,
-                                         BalSmem& sm, SliceRec* __restrict__ rec,
-                                         unsigned long long* __restrict__ counts,
-                                         const unsigned long long* __restrict__ offsets, unsigned long long cap,
-                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ emit_gid) {
+                                         BalSmem<EMIT>& sm, SliceRec* __restrict__ rec,
+                                         unsigned long long* __restrict__ counts, unsigned long long e0,
+                                         unsigned long long e_end, uint32_t* __restrict__ keys,
+                                         uint32_t* __restrict__ emit_gid) {
   const int lane = threadIdx.x & 31;
   const int i = i0 + lane;
   const bool live = lane >= lane_lo && lane < lane_hi;
@@ -281,28 +283,25 @@ __device__ __forceinline__ void bal_warp(const SliceArgs& a, int i0, int lane_lo
   if (live && r.r3.y != 0.0f) plane_range(a, r, plo, phi);
   sm.rec[lane] = r;
   sm.plo[lane] = plo;
-  const int iincl = warp_incl_scan(phi - plo, lane);
+  const int iincl = warp_incl_scan(phi - plo, lane), iexcl = iincl - (phi - plo);
   sm.item0[lane + 1] = iincl;
   if (lane == 0) sm.item0[0] = 0;
   if (!EMIT) sm.cnt[lane] = 0u;
   const int n_items = __shfl_sync(0xffffffffu, iincl, 31);
-  unsigned long long e0 = 0ull, e_end = 0ull;  // the lanes' run of the output, as K-pre counted it
-  if (EMIT) {
-    e0 = offsets[i0 + lane_lo];
-    e_end = min(offsets[i0 + lane_hi - 1] + counts[i0 + lane_hi - 1], cap);
-  }
   const uint32_t T = (uint32_t)(a.TX * a.TY);
   __syncwarp();
   for (int c0 = 0; c0 < n_items; c0 += 32) {
     const int k = c0 + lane;
     int ny = 0;
+    bal_mark(sm.iown, iexcl, iincl, c0, lane);
+    __syncwarp();
     if (k < n_items) {
-      const int o = bal_slot(sm.item0, k);
+      const int o = sm.iown[lane];
       const int j = sm.plo[o] + (k - sm.item0[o]);
       const PlaneBox b = plane_box(a, sm.rec[o], j);
       ny = max(b.ty1 - b.ty0 + 1, 0);
       sm.owner[lane] = o;
-      sm.j[lane] = j;
+      if (EMIT) sm.kb[lane] = a.key_base + (uint32_t)a.zorder[j] * T;
       sm.ty0[lane] = b.ty0;
       sm.mx[lane] = b.mx;
       sm.my[lane] = b.my;
@@ -314,12 +313,14 @@ __device__ __forceinline__ void bal_warp(const SliceArgs& a, int i0, int lane_lo
     sm.row0[lane + 1] = rincl;
     if (lane == 0) sm.row0[0] = 0;
     const int n_rows = __shfl_sync(0xffffffffu, rincl, 31);
-    __syncwarp();
     for (int q0 = 0; q0 < n_rows; q0 += 32) {
       const int q = q0 + lane;
       int lo = 0, hi = -1, o = 0, m = 0, ty = 0;
+      __syncwarp();  // the last round's owners are read
+      bal_mark(sm.rown, rincl - ny, rincl, q0, lane);
+      __syncwarp();
       if (q < n_rows) {
-        m = bal_slot(sm.row0, q);
+        m = sm.rown[lane];
         o = sm.owner[m];
         ty = sm.ty0[m] + (q - sm.row0[m]);
         PlaneBox b;
@@ -340,7 +341,7 @@ __device__ __forceinline__ void bal_warp(const SliceArgs& a, int i0, int lane_lo
         const int cincl = warp_incl_scan(c, lane);
         unsigned long long e = e0 + (unsigned long long)(cincl - c);
         if (c > 0) {
-          const uint32_t kb = a.key_base + (uint32_t)a.zorder[sm.j[m]] * T + (uint32_t)(ty * a.TX);
+          const uint32_t kb = sm.kb[m] + (uint32_t)(ty * a.TX);
           const uint32_t gid = (uint32_t)(i0 + o);
           for (int tx = lo; tx <= hi; ++tx, ++e) {
             if (e < e_end && GP_IN_RANGE(7, tx, a.TX) && GP_IN_RANGE(8, ty, a.TY)) {
@@ -357,18 +358,66 @@ __device__ __forceinline__ void bal_warp(const SliceArgs& a, int i0, int lane_lo
   if (!EMIT && live) counts[i] = sm.cnt[lane];
 }
 
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// The warp's pair counts: K-pre's per-warp total (wsum) after the warp's
+// bal_warp calls have written its lanes' counts, or K-emit's placement from
+// the scan of those totals (wsum = their exclusive scan): each Gaussian's
+// offset (written out, the deterministic backward reads them) and a lane
+// range's run [e0, e_end) of the output.
+struct WarpRun {
+  unsigned long long base, incl, cnt;
+};
+
+template <bool EMIT>
+__device__ __forceinline__ WarpRun warp_run(const unsigned long long* __restrict__ counts,
+                                            unsigned long long* __restrict__ wsum,
+                                            unsigned long long* __restrict__ offsets, int wg, int i0, int nl,
+                                            int lane) {
+  WarpRun w{0ull, 0ull, 0ull};
+  if (EMIT) {
+    w.cnt = lane < nl ? counts[i0 + lane] : 0ull;
+    w.incl = warp_incl_scan_u64(w.cnt, lane);
+    w.base = wsum[wg];
+    if (lane < nl) offsets[i0 + lane] = w.base + w.incl - w.cnt;
+  }
+  return w;
+}
+
+__device__ __forceinline__ void warp_total(const unsigned long long* __restrict__ counts,
+                                           unsigned long long* __restrict__ wsum, int wg, int i0, int nl,
+                                           int lane) {
+  unsigned long long c = lane < nl ? counts[i0 + lane] : 0ull;  // this lane's own store
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) wsum[wg] = c;
+}
+
 template <bool EMIT>
 __global__ void __launch_bounds__(BAL_WARPS * 32) k_slice_bal(SliceArgs a, SliceRec* __restrict__ rec,
                                                               unsigned long long* __restrict__ counts,
-                                                              const unsigned long long* __restrict__ offsets,
+                                                              unsigned long long* __restrict__ wsum,
+                                                              unsigned long long* __restrict__ offsets,
                                                               unsigned long long cap,
                                                               uint32_t* __restrict__ keys,
                                                               uint32_t* __restrict__ emit_gid) {
-  __shared__ BalSmem sm[BAL_WARPS];
-  const int w = threadIdx.x >> 5;
-  const int i0 = (blockIdx.x * BAL_WARPS + w) * 32;
+  __shared__ BalSmem<EMIT> sm[BAL_WARPS];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wg = blockIdx.x * BAL_WARPS + w;
+  const int i0 = wg * 32;
   if (i0 >= a.n) return;  // uniform over the warp
-  bal_warp<EMIT>(a, i0, 0, min(32, a.n - i0), 0, sm[w], rec, counts, offsets, cap, keys, emit_gid);
+  const int nl = min(32, a.n - i0);
+  const WarpRun wr = warp_run<EMIT>(counts, wsum, offsets, wg, i0, nl, lane);
+  const unsigned long long end = __shfl_sync(0xffffffffu, wr.incl, 31);
+  bal_warp<EMIT>(a, i0, 0, nl, 0, sm[w], rec, counts, wr.base, min(wr.base + end, cap), keys, emit_gid);
+  if (!EMIT) warp_total(counts, wsum, wg, i0, nl, lane);
 }
 
 // Batched form: the warp's 32 batch-wide Gaussians, one item at a time (items
@@ -376,58 +425,68 @@ __global__ void __launch_bounds__(BAL_WARPS * 32) k_slice_bal(SliceArgs a, Slice
 template <bool EMIT>
 __global__ void __launch_bounds__(BAL_WARPS * 32) k_slice_bal_batch(BatchItems b, SliceRec* __restrict__ rec,
                                                                     unsigned long long* __restrict__ counts,
-                                                                    const unsigned long long* __restrict__ offsets,
+                                                                    unsigned long long* __restrict__ wsum,
+                                                                    unsigned long long* __restrict__ offsets,
                                                                     unsigned long long cap,
                                                                     uint32_t* __restrict__ keys,
                                                                     uint32_t* __restrict__ emit_gid) {
-  __shared__ BalSmem sm[BAL_WARPS];
-  const int w = threadIdx.x >> 5;
-  const int i0 = (blockIdx.x * BAL_WARPS + w) * 32;
+  __shared__ BalSmem<EMIT> sm[BAL_WARPS];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wg = blockIdx.x * BAL_WARPS + w;
+  const int i0 = wg * 32;
   if (i0 >= b.n_gauss) return;  // uniform over the warp
   const int nl = min(32, b.n_gauss - i0);
+  const WarpRun wr = warp_run<EMIT>(counts, wsum, offsets, wg, i0, nl, lane);
   for (int l = 0; l < nl;) {  // uniform over the warp
     const int k = find_item(b.gstart, b.n_items, i0 + l);
     const int g0 = b.gstart[k];
     const int lh = min(nl, b.gstart[k + 1] - i0);
     const SliceArgs a = b.args[k];
-    bal_warp<EMIT>(a, i0, l, lh, g0, sm[w], rec, counts, offsets, cap, keys, emit_gid);
+    const unsigned long long e0 = wr.base + __shfl_sync(0xffffffffu, wr.incl - wr.cnt, l);
+    const unsigned long long e1 = wr.base + __shfl_sync(0xffffffffu, wr.incl, lh - 1);
+    bal_warp<EMIT>(a, i0, l, lh, g0, sm[w], rec, counts, e0, min(e1, cap), keys, emit_gid);
     __syncwarp();
     l = lh;
   }
+  if (!EMIT) warp_total(counts, wsum, wg, i0, nl, lane);
 }
 
-void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
+void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, unsigned long long* wsum,
+                      cudaStream_t st) {
   if (a.n <= 0) return;
-  k_slice_bal<false><<<ceil_div(a.n, BAL_WARPS * 32), BAL_WARPS * 32, 0, st>>>(a, rec, counts, nullptr, 0ull,
+  k_slice_bal<false><<<ceil_div(a.n, BAL_WARPS * 32), BAL_WARPS * 32, 0, st>>>(a, rec, counts, wsum, nullptr, 0ull,
                                                                                nullptr, nullptr);
   note_launch();
 }
 
-void launch_slice_pre_batch(const BatchItems& b, SliceRec* rec, unsigned long long* counts, cudaStream_t st) {
+void launch_slice_pre_batch(const BatchItems& b, SliceRec* rec, unsigned long long* counts, unsigned long long* wsum,
+                            cudaStream_t st) {
   if (b.n_gauss <= 0) return;
   k_slice_bal_batch<false><<<ceil_div(b.n_gauss, BAL_WARPS * 32), BAL_WARPS * 32, 0, st>>>(
-      b, rec, counts, nullptr, 0ull, nullptr, nullptr);
+      b, rec, counts, wsum, nullptr, 0ull, nullptr, nullptr);
   note_launch();
 }
 
-void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* offsets,
-                       const unsigned long long* counts, uint32_t* keys, uint32_t* vals, uint32_t* emit_gid,
-                       cudaStream_t st, unsigned long long cap) {
-  (void)vals;  // the sort generates the identity values itself
+void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* woff,
+                       const unsigned long long* counts, unsigned long long* offsets, uint32_t* keys,
+                       uint32_t* emit_gid, cudaStream_t st, unsigned long long cap) {
   if (a.n <= 0) return;
   k_slice_bal<true><<<ceil_div(a.n, BAL_WARPS * 32), BAL_WARPS * 32, 0, st>>>(
-      a, const_cast<SliceRec*>(rec), const_cast<unsigned long long*>(counts), offsets, cap, keys, emit_gid);
+      a, const_cast<SliceRec*>(rec), const_cast<unsigned long long*>(counts), const_cast<unsigned long long*>(woff),
+      offsets, cap, keys, emit_gid);
   note_launch();
 }
 
-void launch_slice_emit_batch(const BatchItems& b, const SliceRec* rec, const unsigned long long* offsets,
-                             const unsigned long long* counts, uint32_t cap, uint32_t* keys, uint32_t* emit_gid,
-                             cudaStream_t st) {
+void launch_slice_emit_batch(const BatchItems& b, const SliceRec* rec, const unsigned long long* woff,
+                             const unsigned long long* counts, unsigned long long* offsets, uint32_t cap,
+                             uint32_t* keys, uint32_t* emit_gid, cudaStream_t st) {
   if (b.n_gauss <= 0) return;
   k_slice_bal_batch<true><<<ceil_div(b.n_gauss, BAL_WARPS * 32), BAL_WARPS * 32, 0, st>>>(
-      b, const_cast<SliceRec*>(rec), const_cast<unsigned long long*>(counts), offsets, cap, keys, emit_gid);
+      b, const_cast<SliceRec*>(rec), const_cast<unsigned long long*>(counts), const_cast<unsigned long long*>(woff),
+      offsets, cap, keys, emit_gid);
   note_launch();
 }
+
 // ------------------------------------------------------------ K-range
 // Each thread takes RG_KEYS consecutive sorted keys (16-byte loads; the key
 // array is 16-byte aligned and a vector that would run past the count is read

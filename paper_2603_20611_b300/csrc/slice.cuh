@@ -46,10 +46,11 @@ struct BatchItems {
   uint32_t n_keys;    // kstart[n_items]
 };
 
-void launch_slice_pre_batch(const BatchItems& b, SliceRec* rec, unsigned long long* counts, cudaStream_t st);
-void launch_slice_emit_batch(const BatchItems& b, const SliceRec* rec, const unsigned long long* offsets,
-                             const unsigned long long* counts, uint32_t cap, uint32_t* keys, uint32_t* emit_gid,
-                             cudaStream_t st);
+void launch_slice_pre_batch(const BatchItems& b, SliceRec* rec, unsigned long long* counts, unsigned long long* wsum,
+                            cudaStream_t st);
+void launch_slice_emit_batch(const BatchItems& b, const SliceRec* rec, const unsigned long long* woff,
+                             const unsigned long long* counts, unsigned long long* offsets, uint32_t cap,
+                             uint32_t* keys, uint32_t* emit_gid, cudaStream_t st);
 void launch_slice_bwd_pre_batch(const BatchItems& b, const float* accum, cudaStream_t st);
 void launch_det_reduce_n(int n, const unsigned long long* offsets, const unsigned long long* counts,
                          const float4* partial, float* accum, unsigned long long cap, cudaStream_t st);
@@ -84,13 +85,15 @@ cudaError_t launch_raster_bwd_px_batch(const BatchItems& b, int tile, int px, in
                                        const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
                                        const uint2* ranges, float* accum, float4* partial, cudaStream_t st);
 
-// K-pre: records + per-Gaussian pair counts.
-void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, cudaStream_t st);
-// K-emit: (slice, tile) keys, identity values, emission -> Gaussian id; no
-// pair at or past index cap is written.
-void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* offsets,
-                       const unsigned long long* counts, uint32_t* keys, uint32_t* vals, uint32_t* emit_gid,
-                       cudaStream_t st, unsigned long long cap = ~0ull);
+// K-pre: records, per-Gaussian pair counts and per-warp (32 Gaussians) totals.
+void launch_slice_pre(const SliceArgs& a, SliceRec* rec, unsigned long long* counts, unsigned long long* wsum,
+                      cudaStream_t st);
+// K-emit: (slice, tile) keys and Gaussian ids, placed by woff (the exclusive
+// scan of K-pre's per-warp totals); writes each Gaussian's offset into offsets;
+// no pair at or past index cap is written.
+void launch_slice_emit(const SliceArgs& a, const SliceRec* rec, const unsigned long long* woff,
+                       const unsigned long long* counts, unsigned long long* offsets, uint32_t* keys,
+                       uint32_t* emit_gid, cudaStream_t st, unsigned long long cap = ~0ull);
 // K-range: [start, end) of each key in the sorted key list; ranges must be zeroed.
 void launch_ranges(const uint32_t* keys, const unsigned long long* n_dev, uint32_t cap, uint32_t nkeys,
                    uint2* ranges, cudaStream_t st);
