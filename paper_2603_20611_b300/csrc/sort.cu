@@ -130,6 +130,33 @@ int64_t scan_temp_bytes(int64_t n) {
   return (nb + 1) * (int64_t)sizeof(unsigned long long);
 }
 
+// One block scans a short array (up to SCAN_ONE items) in a single launch.
+constexpr int SCAN_ONE_THREADS = 1024;
+constexpr int SCAN_ONE_ITEMS = 16;
+constexpr int64_t SCAN_ONE = (int64_t)SCAN_ONE_THREADS * SCAN_ONE_ITEMS;
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_ONE_THREADS) k_scan_one(const T* __restrict__ in, T* __restrict__ out,
+                                                               int n, unsigned long long* __restrict__ total) {
+  __shared__ unsigned long long sw[SCAN_ONE_THREADS / 32 + 1];
+  const int base = threadIdx.x * SCAN_ONE_ITEMS;
+  T v[SCAN_ONE_ITEMS];
+  unsigned long long s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ONE_ITEMS; ++k) {
+    v[k] = base + k < n ? in[base + k] : T(0);
+    s += (unsigned long long)v[k];
+  }
+  unsigned long long tot;
+  unsigned long long run = block_exclusive_scan<unsigned long long, SCAN_ONE_THREADS>(s, sw, &tot);
+#pragma unroll
+  for (int k = 0; k < SCAN_ONE_ITEMS; ++k) {
+    if (base + k < n) out[base + k] = (T)run;
+    run += (unsigned long long)v[k];
+  }
+  if (threadIdx.x == 0 && total) *total = tot;
+}
+
 template <typename T>
 cudaError_t exclusive_scan(const T* in, T* out, int64_t n, unsigned long long* total, void* temp,
                            cudaStream_t st) {
@@ -138,6 +165,11 @@ cudaError_t exclusive_scan(const T* in, T* out, int64_t n, unsigned long long* t
   if (nb == 0) {
     if (total) return cudaMemsetAsync(total, 0, sizeof(unsigned long long), st);
     return cudaSuccess;
+  }
+  if (n <= SCAN_ONE) {
+    k_scan_one<T><<<1, SCAN_ONE_THREADS, 0, st>>>(in, out, (int)n, total);
+    note_launch();
+    return cudaGetLastError();
   }
   k_scan_reduce<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, part);
   k_scan_partials<<<1, 1024, 0, st>>>(part, (int)nb, total);
