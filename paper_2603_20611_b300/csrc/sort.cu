@@ -130,31 +130,38 @@ int64_t scan_temp_bytes(int64_t n) {
   return (nb + 1) * (int64_t)sizeof(unsigned long long);
 }
 
-// One block scans a short array (up to SCAN_ONE items) in a single launch.
-constexpr int SCAN_ONE_THREADS = 1024;
-constexpr int SCAN_ONE_ITEMS = 16;
-constexpr int64_t SCAN_ONE = (int64_t)SCAN_ONE_THREADS * SCAN_ONE_ITEMS;
+// Short arrays (up to SCAN_SMALL_TILES tiles) in one launch: every block first
+// sums all the items before its tile (coalesced; the redundant reads are a few
+// tiles at most), then scans its own tile as k_scan_down does.
+constexpr int SCAN_SMALL_TILES = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(SCAN_ONE_THREADS) k_scan_one(const T* __restrict__ in, T* __restrict__ out,
-                                                               int n, unsigned long long* __restrict__ total) {
-  __shared__ unsigned long long sw[SCAN_ONE_THREADS / 32 + 1];
-  const int base = threadIdx.x * SCAN_ONE_ITEMS;
-  T v[SCAN_ONE_ITEMS];
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_small(const T* __restrict__ in, T* __restrict__ out,
+                                                              int64_t n, unsigned long long* __restrict__ total) {
+  __shared__ unsigned long long sw[SCAN_THREADS / 32 + 1];
+  const int64_t tile0 = (int64_t)blockIdx.x * SCAN_TILE;
+  unsigned long long c = 0;
+  for (int64_t i = threadIdx.x; i < tile0; i += SCAN_THREADS) c += (unsigned long long)in[i];
+  unsigned long long carry;
+  block_exclusive_scan<unsigned long long, SCAN_THREADS>(c, sw, &carry);
+  const int64_t base = tile0 + (int64_t)threadIdx.x * SCAN_ITEMS;
+  T v[SCAN_ITEMS];
   unsigned long long s = 0;
 #pragma unroll
-  for (int k = 0; k < SCAN_ONE_ITEMS; ++k) {
-    v[k] = base + k < n ? in[base + k] : T(0);
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int64_t i = base + k;
+    v[k] = i < n ? in[i] : T(0);
     s += (unsigned long long)v[k];
   }
   unsigned long long tot;
-  unsigned long long run = block_exclusive_scan<unsigned long long, SCAN_ONE_THREADS>(s, sw, &tot);
+  unsigned long long run = carry + block_exclusive_scan<unsigned long long, SCAN_THREADS>(s, sw, &tot);
 #pragma unroll
-  for (int k = 0; k < SCAN_ONE_ITEMS; ++k) {
-    if (base + k < n) out[base + k] = (T)run;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int64_t i = base + k;
+    if (i < n) out[i] = (T)run;
     run += (unsigned long long)v[k];
   }
-  if (threadIdx.x == 0 && total) *total = tot;
+  if (total && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) *total = carry + tot;
 }
 
 template <typename T>
@@ -166,8 +173,8 @@ cudaError_t exclusive_scan(const T* in, T* out, int64_t n, unsigned long long* t
     if (total) return cudaMemsetAsync(total, 0, sizeof(unsigned long long), st);
     return cudaSuccess;
   }
-  if (n <= SCAN_ONE) {
-    k_scan_one<T><<<1, SCAN_ONE_THREADS, 0, st>>>(in, out, (int)n, total);
+  if (nb <= SCAN_SMALL_TILES) {
+    k_scan_small<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, total);
     note_launch();
     return cudaGetLastError();
   }
