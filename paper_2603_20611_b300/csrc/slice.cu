@@ -67,6 +67,9 @@ __device__ __forceinline__ int upper_bound_f(const float* __restrict__ v, int n,
   return lo;
 }
 
+// 1 / tile for the power-of-two tile sides (exact, without a division).
+__device__ __forceinline__ float tile_rcp(int tile) { return tile == 8 ? 0.125f : 0.0625f; }
+
 __device__ __forceinline__ int clamp_tile(float t, int nt) {
   // t is a (possibly huge) tile coordinate; clamp in float first
   t = fminf(fmaxf(t, -1.0f), (float)nt);
@@ -97,7 +100,7 @@ struct PlaneBox {
 
 __device__ __forceinline__ PlaneBox plane_box(const SliceArgs& a, const SliceRec& r, int j) {
   PlaneBox b;
-  const float inv_tile = 1.0f / (float)a.tile;
+  const float inv_tile = tile_rcp(a.tile);
   const float d = __fsub_rn(r.r0.z, a.zs[j]);
   b.k2e = a.k2;
   b.rxe = r.r2.w;
@@ -141,7 +144,7 @@ __device__ __forceinline__ bool row_tiles(const SliceArgs& a, const SliceRec& r,
   const float wm = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(k2, __fmul_rn(D, __fmul_rn(dm, dm))), inv00), 0.0f));
   const float xmax = __fadd_rn(__fsub_rn(b.mx, __fmul_rn(s, dM)), wM);
   const float xmin = __fsub_rn(__fsub_rn(b.mx, __fmul_rn(s, dm)), wm);
-  const float inv_tile = 1.0f / (float)a.tile;
+  const float inv_tile = tile_rcp(a.tile);
   // tile tx spans pixel centres [tx T + 0.5, (tx + 1) T - 0.5] (the last one ends at W - 0.5)
   int l = max(0, clamp_tile(__fmul_rn(__fadd_rn(xmin, 0.5f), inv_tile), a.TX + 1) - 1);
   const float lf = __fsub_rn(__fmul_rn(__fadd_rn(xmin, 0.5f), inv_tile), 1.0f);

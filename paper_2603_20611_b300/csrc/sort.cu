@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "gp_check.cuh"
 #include "gp_internal.h"
 
@@ -312,27 +314,36 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(
     key[r] = i < n ? kin[i] : 0u;
     val[r] = i < n ? (vin ? vin[i] : i) : 0u;  // no input values: the identity
   }
+  // NB = 8 on a tile whose keys are all valid; NB = 9 on the last, partial
+  // tile, where the ninth ballot sets the invalid lanes apart
+  auto rank_keys = [&](auto nb_tag) {
+    constexpr int NB = decltype(nb_tag)::value;
 #pragma unroll
-  for (int r = 0; r < RS_ROUNDS_W; ++r) {
-    const uint32_t i = base + r * 32 + lane;
-    const bool valid = i < n;
-    const uint32_t d = valid ? ((key[r] >> shift) & 0xffu) : (RS_BINS + lane);
-    // lanes holding the same digit: one ballot per digit bit (and one for
-    // validity; an invalid lane's low bits are its lane number, so it is alone)
-    uint32_t peers = 0xffffffffu;
+    for (int r = 0; r < RS_ROUNDS_W; ++r) {
+      const uint32_t i = base + r * 32 + lane;
+      const bool valid = NB == 8 || i < n;
+      const uint32_t d = valid ? ((key[r] >> shift) & 0xffu) : (RS_BINS + lane);
+      // lanes holding the same digit: one ballot per digit bit (and one for
+      // validity; an invalid lane's low bits are its lane number, so it is alone)
+      uint32_t peers = 0xffffffffu;
 #pragma unroll
-    for (int b = 0; b < 9; ++b) {
-      const bool bit = (d >> b) & 1u;
-      const uint32_t m = __ballot_sync(0xffffffffu, bit);
-      peers &= bit ? m : ~m;
+      for (int b = 0; b < NB; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+      }
+      uint32_t c = 0u;
+      if (valid) c = wcnt[warp][d];
+      rank[r] = valid ? c + __popc(peers & lt_mask) : 0xffffffffu;
+      __syncwarp();
+      if (valid && __popc(peers & lt_mask) == 0) wcnt[warp][d] = c + __popc(peers);
+      __syncwarp();
     }
-    uint32_t c = 0u;
-    if (valid) c = wcnt[warp][d];
-    rank[r] = valid ? c + __popc(peers & lt_mask) : 0xffffffffu;
-    __syncwarp();
-    if (valid && __popc(peers & lt_mask) == 0) wcnt[warp][d] = c + __popc(peers);
-    __syncwarp();
-  }
+  };
+  if (tile0 + (uint32_t)RS_TILE <= n)  // uniform across the block
+    rank_keys(std::integral_constant<int, 8>{});
+  else
+    rank_keys(std::integral_constant<int, 9>{});
   __syncthreads();
   // thread t owns digit t: per-warp offsets inside the digit, the digit's tile total
   uint32_t tot = 0;
