@@ -32,8 +32,15 @@
  *   - Images are [S][H][W] fp32 row-major, volumes [Z][Y][X] fp32.
  *   - Every call is asynchronous on the caller's CUDA stream (`stream` is a
  *     cudaStream_t, NULL = the legacy default stream), except where noted.
- *     Plain render / backward / voxelize calls read back one pair count (a
- *     short stream synchronisation) to size their sort buffers.
+ *     Plain render / backward / voxelize calls read back one pair count to
+ *     size their sort buffers: on a context's first binning the host waits for
+ *     it between the count and the emission; once the context holds pair
+ *     buffers, the pairs are emitted and sorted into their capacity (at most a
+ *     quarter above the context's last count) while the count is copied back
+ *     on a context-owned side stream, and the call waits for that copy after
+ *     queueing its rasteriser (a count that did not fit bins the call again
+ *     and repeats the rasteriser before returning).  Either way the host
+ *     returns once the binning's count is known; the rasteriser may still run.
  *   - Contributions are culled where they are provably below eps relative to
  *     their Gaussian: slices with opacity_r < eps are skipped, and only screen
  *     tiles that the ellipse d^T Sigma_2d^-1 d <= 2 ln(1/eps) touches are
