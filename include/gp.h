@@ -538,6 +538,10 @@ GP_API gp_status gp_adam_step(gp_ctx* ctx, const gp_adam_cfg* cfg, int64_t t, in
 #define GP_PHASE_OPT 7        /* gp_adam_step */
 #define GP_NUM_PHASES 8
 GP_API gp_status gp_timing_enable(gp_ctx* ctx, int enable);
+/* Times only the phases whose bit (1 << GP_PHASE_*) is set in mask (0 = none);
+ * each timed phase records two events per call, which cost the stream a few
+ * microseconds.  GP_ERR_ARG for bits past GP_NUM_PHASES. */
+GP_API gp_status gp_timing_enable_phases(gp_ctx* ctx, unsigned mask);
 GP_API gp_status gp_timing_read(gp_ctx* ctx, double* ms /* [GP_NUM_PHASES] */,
                                 int64_t* launches /* [GP_NUM_PHASES] */,
                                 int64_t* calls /* [GP_NUM_PHASES], may be NULL */);

@@ -38,7 +38,8 @@ GP_EXP_POLY_ROW = 3
 EXPORTS = (
     "gp_config_default", "gp_create", "gp_destroy", "gp_last_error", "gp_workspace_bytes",
     "gp_render_slices", "gp_render_backward", "gp_mse_grad", "gp_voxelize", "gp_voxelize_backward",
-    "gp_last_counts", "gp_count_evals", "gp_exp2_eval", "gp_timing_enable", "gp_timing_read",
+    "gp_last_counts", "gp_count_evals", "gp_exp2_eval", "gp_timing_enable", "gp_timing_enable_phases",
+    "gp_timing_read",
     "gp_launch_count", "gp_fma_probe_threads", "gp_fma_probe", "gp_mse_grad_noalloc",
     "gp_batch_plan", "gp_batch_run", "gp_batch_wait", "gp_batch_info", "gp_batch_destroy",
     "gp_serve_open", "gp_serve_load_set", "gp_serve_submit", "gp_serve_poll", "gp_serve_cancel", "gp_serve_stats_get",
@@ -158,6 +159,7 @@ def _load():
         "gp_count_evals": [P, SP, P, I, I, I, F, I, ctypes.POINTER(I64)],
         "gp_exp2_eval": [P, P, P, I64, I, P],
         "gp_timing_enable": [P, I],
+        "gp_timing_enable_phases": [P, ctypes.c_uint],
         "gp_timing_read": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), ctypes.POINTER(I64)],
         "gp_launch_count": [],
         "gp_fma_probe_threads": [P],
@@ -272,8 +274,15 @@ class Context:
     def workspace_bytes(self):
         return int(lib.gp_workspace_bytes(self.h))
 
-    def timing(self, enable=True):
-        self.check(lib.gp_timing_enable(self.h, int(bool(enable))), "gp_timing_enable")
+    def timing(self, enable=True, phases=None):
+        """Phase timing on (all phases, or only the named ones) or off."""
+        if phases is None or not enable:
+            self.check(lib.gp_timing_enable(self.h, int(bool(enable))), "gp_timing_enable")
+        else:
+            mask = 0
+            for p in phases:
+                mask |= 1 << PHASES.index(p)
+            self.check(lib.gp_timing_enable_phases(self.h, mask), "gp_timing_enable_phases")
 
     def timing_read(self):
         """{phase: (ms, launches, calls)} since the last read."""

@@ -103,7 +103,7 @@ struct Ctx {
   const uint32_t* bin_vals = nullptr;
   bool bin_gid_vals = false;  // the sorted values are Gaussian ids (else emission indices)
   char bin_args[256];      // the SliceArgs of that binning (opaque here)
-  bool timing = false;
+  unsigned timing = 0u;     // phases (bit GP_PHASE_*) whose calls record event pairs
   std::vector<PhaseEvent> events;
   std::vector<cudaEvent_t> event_pool;
   gp_config cfg{};

@@ -51,7 +51,7 @@ static cudaEvent_t pooled_event(Ctx* c) {
 
 PhaseTimer::PhaseTimer(Ctx* c, int phase, cudaStream_t st)
     : range_(phase_range_name(phase)), c_(c), phase_(phase), st_(st) {
-  if (!c->timing) return;
+  if (!((c->timing >> phase) & 1u)) return;
   start_ = pooled_event(c);
   if (start_ && cudaEventRecord(start_, st) != cudaSuccess) {
     cudaGetLastError();
@@ -877,7 +877,13 @@ gp_status gp_voxelize_backward(gp_ctx* ctx, const gp_set* set, int X, int Y, int
 
 gp_status gp_timing_enable(gp_ctx* ctx, int enable) {
   if (!ctx) return GP_ERR_ARG;
-  ctx->impl.timing = enable != 0;
+  ctx->impl.timing = enable != 0 ? (1u << GP_NUM_PHASES) - 1u : 0u;
+  return GP_OK;
+}
+
+gp_status gp_timing_enable_phases(gp_ctx* ctx, unsigned mask) {
+  if (!ctx || (mask >> GP_NUM_PHASES) != 0u) return GP_ERR_ARG;
+  ctx->impl.timing = mask;
   return GP_OK;
 }
 

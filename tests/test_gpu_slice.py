@@ -331,3 +331,31 @@ def test_backward_reuses_forward_bins_only_for_identical_calls():
     got2 = B.gp_render_backward(reuse, gs, z2, 40, 48, 2.0, G)
     for a, b in zip(got2, ref2):
         assert torch.equal(a, b)
+
+
+def test_phase_timing_selects_phases():
+    """gp_timing_enable_phases times only the chosen phases; gp_timing_enable
+    times all of them; bits past the last phase are rejected."""
+    c = B.Context(0)
+    g = synth.small(seed=77, n=300, extent=(32, 32, 8))
+    gs = dev_set(g)
+    z = np.array([2.5, 5.5], np.float32)
+    G = torch.ones(2, 32, 32, device="cuda")
+
+    def run():
+        B.gp_render_slices(c, gs, z, 32, 32, 2.0)
+        B.gp_render_backward(c, gs, z, 32, 32, 2.0, G)
+        torch.cuda.synchronize()
+        return c.timing_read()
+
+    c.timing(True, phases=("fwd",))
+    ph = run()
+    assert ph["fwd"][2] == 1 and ph["fwd"][0] > 0.0
+    assert ph["bin"][2] == 0 and ph["bwd"][2] == 0 and ph["bwd_pre"][2] == 0
+    c.timing(True)
+    ph = run()
+    assert all(ph[p][2] >= 1 for p in ("bin", "fwd", "bwd", "bwd_pre"))
+    c.timing(False)
+    ph = run()
+    assert all(v[2] == 0 for v in ph.values())
+    assert B.lib.gp_timing_enable_phases(c.h, 1 << B.GP_NUM_PHASES) == B.GP_ERR_ARG
