@@ -662,8 +662,10 @@ static gp_status backward_impl(gp_ctx* ctx, const gp_set* set, const View& view,
     {
       PhaseTimer timer(c, vox ? GP_PHASE_VOX_BWD : GP_PHASE_BWD_PRE, st);
       if (det)
-        launch_det_reduce(n, (const unsigned long long*)b.offsets.ptr, (const unsigned long long*)b.counts.ptr,
-                          (const float4*)b.partial.ptr, (float*)b.accum.ptr, st);
+        // bounded by the pairs the partials hold: a speculative binning whose
+        // count overflowed them is redone, but its reduce must stay in bounds
+        launch_det_reduce_n(n, (const unsigned long long*)b.offsets.ptr, (const unsigned long long*)b.counts.ptr,
+                            (const float4*)b.partial.ptr, (float*)b.accum.ptr, (unsigned long long)P, st);
       launch_slice_bwd_pre(a, (const float*)b.accum.ptr, d_mu, d_scale, d_quat, d_alpha, st);
     }
     GP_TRY(cuda_err(c, cudaGetLastError(), "backward kernels"));

@@ -968,13 +968,6 @@ void launch_det_reduce_n(int n, const unsigned long long* offsets, const unsigne
   note_launch();
 }
 
-void launch_det_reduce(int n, const unsigned long long* offsets, const unsigned long long* counts,
-                       const float4* partial, float* accum, cudaStream_t st) {
-  if (n <= 0) return;
-  k_det_reduce<<<ceil_div(n, 256), 256, 0, st>>>(n, offsets, counts, partial, accum, ~0ull);
-  note_launch();
-}
-
 // ------------------------------------------------------------ K-bwd-pre
 // Closed-form chain from the ten accumulators to the parameters:
 //   dL/dmu_p = S1,  dL/da = -S2,  dL/dmu_c = -a.S1 - A T1 / v,

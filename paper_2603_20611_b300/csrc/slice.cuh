@@ -111,9 +111,6 @@ cudaError_t launch_raster_bwd(const SliceArgs& a, int px, int raster, int exp_mo
                               const SliceRec* rec, const uint32_t* vals, const uint32_t* emit_gid,
                               const uint2* ranges, const float* dL_dI, float* accum, float4* partial,
                               cudaStream_t st);
-// K-det: per-Gaussian ordered reduction of partials into accum.
-void launch_det_reduce(int n, const unsigned long long* offsets, const unsigned long long* counts,
-                       const float4* partial, float* accum, cudaStream_t st);
 // K-bwd-pre: accumulators -> parameter gradients.
 void launch_slice_bwd_pre(const SliceArgs& a, const float* accum, float* d_mu, float* d_scale,
                           float* d_quat, float* d_alpha, cudaStream_t st);
