@@ -612,7 +612,14 @@ namespace gp {
 
 // ------------------------------------------------------------ plain kernels
 // Row-unit kernels (the default for per-pixel exponentials): one warp per tile.
+// The forward runs one warp per CTA (69 registers, 24 CTAs per SM: fewer
+// registers for more resident warps slowed it, 1.01 -> 1.05 ms at 63 and 1.09 ms
+// at 48).  The backward runs two tiles per CTA, each warp with its own shared
+// memory and no barrier between them: 62 registers and 32 resident warps per SM
+// (one warp per CTA reached fewer, limited by the CTAs an SM holds; voxelizer
+// planes' backward 1.44 -> 1.25 ms).
 constexpr int kRowCtasPerSm = 24;
+constexpr int kRowBwdWarps = 2, kRowBwdCtasPerSm = 16;
 
 template <int TILE, int EXPM>
 __global__ void __launch_bounds__(32, kRowCtasPerSm) k_raster_fwd_rows(SliceArgs a, const SliceRec* __restrict__ rec,
@@ -629,14 +636,14 @@ __global__ void __launch_bounds__(32, kRowCtasPerSm) k_raster_fwd_rows(SliceArgs
 }
 
 template <int TILE, int EXPM, bool DET>
-__global__ void __launch_bounds__(32, kRowCtasPerSm) k_raster_bwd_rows(SliceArgs a, const SliceRec* __restrict__ rec,
-                                                                       const uint32_t* __restrict__ vals,
-                                                                       const uint32_t* __restrict__ emit_gid,
-                                                                       const uint2* __restrict__ ranges,
-                                                                       float* __restrict__ accum,
-                                                                       float4* __restrict__ partial) {
-  __shared__ RowBwdSmem<TILE> sm;
-  bwd_tile_rows<TILE, EXPM, DET>(a, blockIdx.x, rec, vals, emit_gid, ranges, accum, partial, sm);
+__global__ void __launch_bounds__(32 * kRowBwdWarps, kRowBwdCtasPerSm) k_raster_bwd_rows(
+    SliceArgs a, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, float* __restrict__ accum,
+    float4* __restrict__ partial) {
+  const int w = threadIdx.x >> 5, key = blockIdx.x * kRowBwdWarps + w;
+  if ((int64_t)key >= (int64_t)a.S * a.TX * a.TY) return;  // the last CTA's spare warp
+  __shared__ RowBwdSmem<TILE> sm[kRowBwdWarps];
+  bwd_tile_rows<TILE, EXPM, DET>(a, key, rec, vals, emit_gid, ranges, accum, partial, sm[w]);
 }
 
 // Block-culled kernels (the row-factored exponential's): four warps per 16 x 16 tile.
@@ -711,7 +718,7 @@ __global__ void __launch_bounds__((TILE / 8) * (TILE / 8) * 32, TILE == 16 ? (ro
   }
 }
 
-// Persistent row-unit kernels: one warp per CTA takes chunks of keys.
+// Persistent row-unit kernels: each warp takes chunks of keys.
 template <int TILE, int EXPM>
 __global__ void __launch_bounds__(32, kRowCtasPerSm) k_raster_fwd_rows_persist(
     BatchItems b, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
@@ -738,15 +745,17 @@ __global__ void __launch_bounds__(32, kRowCtasPerSm) k_raster_fwd_rows_persist(
   }
 }
 
+// The backward's CTAs hold kRowBwdWarps warps, each taking its own chunks.
 template <int TILE, int EXPM, bool DET>
-__global__ void __launch_bounds__(32, kRowCtasPerSm) k_raster_bwd_rows_persist(
+__global__ void __launch_bounds__(32 * kRowBwdWarps, kRowBwdCtasPerSm) k_raster_bwd_rows_persist(
     BatchItems b, const SliceRec* __restrict__ rec, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ emit_gid, const uint2* __restrict__ ranges, float* __restrict__ accum,
     float4* __restrict__ partial, unsigned* __restrict__ work) {
-  __shared__ RowBwdSmem<TILE> sm;
+  __shared__ RowBwdSmem<TILE> smw[kRowBwdWarps];
+  RowBwdSmem<TILE>& sm = smw[threadIdx.x >> 5];
   for (;;) {
     uint32_t k0 = 0;
-    if (threadIdx.x == 0) k0 = atomicAdd(work, (unsigned)KEY_CHUNK);
+    if ((threadIdx.x & 31) == 0) k0 = atomicAdd(work, (unsigned)KEY_CHUNK);
     k0 = __shfl_sync(0xffffffffu, k0, 0);
     if (k0 >= b.n_keys) break;
     const uint32_t k1 = min(k0 + (uint32_t)KEY_CHUNK, b.n_keys);
@@ -777,13 +786,15 @@ template <int TILE>
 static cudaError_t bwd_rows(const SliceArgs& a, int exp_mode, bool det, const SliceRec* rec, const uint32_t* vals,
                             const uint32_t* emit_gid, const uint2* ranges, float* accum, float4* partial,
                             cudaStream_t st) {
-  const unsigned g = (unsigned)((int64_t)a.S * a.TX * a.TY);
+  const unsigned tiles = (unsigned)((int64_t)a.S * a.TX * a.TY);
+  const unsigned g = (tiles + kRowBwdWarps - 1) / kRowBwdWarps;
+  constexpr int NT = 32 * kRowBwdWarps;
   if (exp_mode == GP_EXP_HW) {
-    if (det) k_raster_bwd_rows<TILE, GP_EXP_HW, true><<<g, 32, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
-    else k_raster_bwd_rows<TILE, GP_EXP_HW, false><<<g, 32, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+    if (det) k_raster_bwd_rows<TILE, GP_EXP_HW, true><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+    else k_raster_bwd_rows<TILE, GP_EXP_HW, false><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
   } else {
-    if (det) k_raster_bwd_rows<TILE, GP_EXP_POLY, true><<<g, 32, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
-    else k_raster_bwd_rows<TILE, GP_EXP_POLY, false><<<g, 32, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+    if (det) k_raster_bwd_rows<TILE, GP_EXP_POLY, true><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
+    else k_raster_bwd_rows<TILE, GP_EXP_POLY, false><<<g, NT, 0, st>>>(a, rec, vals, emit_gid, ranges, accum, partial);
   }
   note_launch();
   return cudaGetLastError();
@@ -931,9 +942,11 @@ cudaError_t launch_raster_bwd_batch(const BatchItems& b, bool rows, int tile, in
 #define GP_BWD_R(T, E)                                                                                         \
   if (tile == T && exp_mode == E) {                                                                            \
     if (det)                                                                                                   \
-      k_raster_bwd_rows_persist<T, E, true><<<ctas, 32, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work);  \
+      k_raster_bwd_rows_persist<T, E, true><<<ctas, 32 * kRowBwdWarps, 0, st>>>(b, rec, vals, emit_gid, ranges,  \
+                                                                                accum, partial, work);           \
     else                                                                                                       \
-      k_raster_bwd_rows_persist<T, E, false><<<ctas, 32, 0, st>>>(b, rec, vals, emit_gid, ranges, accum, partial, work); \
+      k_raster_bwd_rows_persist<T, E, false><<<ctas, 32 * kRowBwdWarps, 0, st>>>(b, rec, vals, emit_gid, ranges, \
+                                                                                 accum, partial, work);          \
     note_launch();                                                                                             \
     return cudaGetLastError();                                                                                 \
   }
@@ -954,12 +967,13 @@ int raster_batch_ctas_per_sm(bool rows, int tile, int chunk, bool backward, int 
   int n = 0;
   cudaError_t e = cudaErrorInvalidValue;
   const bool row = exp_mode == GP_EXP_POLY_ROW;
-  if (rows && !row) {  // the row-unit kernels (one warp per CTA; the chunk is fixed at 32 Gaussians)
+  if (rows && !row) {  // the row-unit kernels (warps of their own; the chunk is fixed at 32 Gaussians)
+    constexpr int NB = 32 * kRowBwdWarps;
     if (tile == 16)
-      e = backward ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_bwd_rows_persist<16, GP_EXP_POLY, false>, 32, 0)
+      e = backward ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_bwd_rows_persist<16, GP_EXP_POLY, false>, NB, 0)
                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd_rows_persist<16, GP_EXP_POLY>, 32, 0);
     else if (tile == 8)
-      e = backward ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_bwd_rows_persist<8, GP_EXP_POLY, false>, 32, 0)
+      e = backward ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_bwd_rows_persist<8, GP_EXP_POLY, false>, NB, 0)
                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd_rows_persist<8, GP_EXP_POLY>, 32, 0);
     if (e != cudaSuccess) {
       cudaGetLastError();
