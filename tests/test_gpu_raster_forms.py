@@ -42,6 +42,9 @@ def _oblique():
 @pytest.mark.parametrize("view", [0, 1, 2, "oblique"])
 @pytest.mark.parametrize("tile", [16, 8])
 def test_forms_against_oracle(form, view, tile):
+    """Five planes of 37 x 43: with 16 x 16 tiles that is 45 (plane, tile)
+    keys, an odd count, so the row backward's last CTA (two tiles per CTA)
+    has a warp without a tile."""
     c = B.Context(0, tile=tile, raster=form)
     g = synth.small(seed=404, n=400, extent=(41, 35, 27))
     gs = dev_set(g, 1.15)
