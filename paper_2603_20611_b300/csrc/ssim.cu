@@ -15,8 +15,12 @@
 //   K-ssim-stats  the five moments -> S, the three derivatives dS/dm_* (global),
 //                 per-block sums of S and |I - T| (double, fixed-order final sum)
 //   K-ssim-grad   the window sums of the three derivatives -> dL/dI
-// About 44 bytes of HBM traffic per pixel in all: a memory-bound loss, ~1 % of
-// a fit step.
+// The window sums take two maps per packed fp32x2 instruction ((m_I, m_T) and
+// (m_II, m_TT) in the stats pass, (dS/dm_I, dS/dm_II) in the gradient pass),
+// rows of the halo are staged as aligned float4 when the width allows, and the
+// loss sums stay in fp32 per thread and warp (the SM's FP64 rate is a small
+// fraction of its FP32 rate), in double across the warps and blocks.
+// About 44 bytes of HBM traffic per pixel in all.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -33,6 +37,7 @@ constexpr int kTS = 32;              // output tile side
 constexpr int kHalo = 5;             // window radius
 constexpr int kWS = kTS + 2 * kHalo; // staged window side (42)
 constexpr int kThreads = 256;
+static_assert(kTS * (kTS / 4) == kThreads, "one vertical output group of 4 pixels per thread");
 
 struct SsimArgs {
   float w[11];  // 1-D window, normalised to sum 1
@@ -44,103 +49,181 @@ __device__ __forceinline__ bool in_img(const SsimArgs& p, int y, int x) {
   return y >= 0 && y < p.H && x >= 0 && x < p.W;
 }
 
+// Stages the kWS x kWS window of N planes around the tile at (x0, y0), zero
+// outside the image: store(r, c, v) with window row r and column c (pixel
+// (y0 - kHalo + r, x0 - kHalo + c)) and v[n] the pixel of plane n.  With vec
+// (W a multiple of 4 and every plane 16-byte aligned) a row is read as 12
+// aligned float4 from x0 - 8, which cover the window's columns x0 - 5 ..
+// x0 + 36 (a float4 lies wholly inside or wholly outside the image);
+// otherwise pixel by pixel.
+template <int N, typename Store>
+__device__ __forceinline__ void stage_window(const SsimArgs& p, const float* const (&src)[N], int x0, int y0,
+                                             bool vec, Store store) {
+  if (vec) {
+    for (int i = threadIdx.x; i < kWS * 12; i += kThreads) {
+      const int r = i / 12, q = i - r * 12;
+      const int y = y0 - kHalo + r, xq = x0 - 8 + 4 * q;
+      const bool in = y >= 0 && y < p.H && xq >= 0 && xq < p.W;
+      float4 v[N];
+#pragma unroll
+      for (int n = 0; n < N; ++n)
+        v[n] = in ? *reinterpret_cast<const float4*>(src[n] + (int64_t)y * p.W + xq) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int c = 4 * q + k - 3;  // x = xq + k = x0 - kHalo + c
+        if (c < 0 || c >= kWS) continue;
+        float e[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) e[n] = k == 0 ? v[n].x : k == 1 ? v[n].y : k == 2 ? v[n].z : v[n].w;
+        store(r, c, e);
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < kWS * kWS; i += kThreads) {
+      const int r = i / kWS, c = i - r * kWS;
+      const int y = y0 - kHalo + r, x = x0 - kHalo + c;
+      const bool in = in_img(p, y, x);
+      float e[N];
+#pragma unroll
+      for (int n = 0; n < N; ++n) e[n] = in ? src[n][(int64_t)y * p.W + x] : 0.0f;
+      store(r, c, e);
+    }
+  }
+}
+
+// 16-byte alignment of every plane a vectorised staging reads.
+template <int N>
+__device__ __forceinline__ bool planes_aligned(const SsimArgs& p, const float* const (&src)[N]) {
+  uintptr_t a = 0;
+#pragma unroll
+  for (int n = 0; n < N; ++n) a |= reinterpret_cast<uintptr_t>(src[n]);
+  return (p.W & 3) == 0 && (a & 15u) == 0;
+}
+
+__device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+
 __global__ void __launch_bounds__(kThreads) k_ssim_stats(SsimArgs p, const float* __restrict__ I,
                                                         const float* __restrict__ T, const int* __restrict__ tidx,
                                                         float* __restrict__ dS, double* __restrict__ part) {
-  __shared__ float sI[kWS][kWS + 1], sT[kWS][kWS + 1];
-  __shared__ float hs[5][kWS][kTS + 1];
+  __shared__ float2 win[kWS][kWS + 1];   // (I, T) of the window
+  __shared__ float2 h01[kWS][kTS + 1];   // row sums (m_I, m_T)
+  __shared__ float2 h23[kWS][kTS + 1];   // row sums (m_II, m_TT)
+  __shared__ float h4[kWS][kTS + 1];     // row sums m_IT
   __shared__ double red[2][kThreads / 32];
   const int s = blockIdx.z;
   const int x0 = blockIdx.x * kTS, y0 = blockIdx.y * kTS;
   const int64_t HW = (int64_t)p.H * p.W;
   const float* Ip = I + (int64_t)s * HW;
   const float* Tp = T + (int64_t)(tidx ? tidx[s] : s) * HW;
-  for (int i = threadIdx.x; i < kWS * kWS; i += kThreads) {
-    const int r = i / kWS, c = i - r * kWS;
-    const int y = y0 - kHalo + r, x = x0 - kHalo + c;
-    const bool in = in_img(p, y, x);
-    sI[r][c] = in ? Ip[(int64_t)y * p.W + x] : 0.0f;
-    sT[r][c] = in ? Tp[(int64_t)y * p.W + x] : 0.0f;
-  }
+  const float* const src[2] = {Ip, Tp};
+  stage_window<2>(p, src, x0, y0, planes_aligned<2>(p, src),
+                  [&](int r, int c, const float (&v)[2]) { win[r][c] = make_float2(v[0], v[1]); });
   __syncthreads();
   // horizontal window sums: a thread takes 8 consecutive outputs of one row from
-  // 18 staged values of each image (a sliding window held in registers)
+  // 18 staged (I, T) pairs held in registers, the moments of I and T side by
+  // side in packed fp32x2 instructions (each lane rounds as the scalar form)
   for (int i = threadIdx.x; i < kWS * (kTS / 8); i += kThreads) {
-    const int r = i / (kTS / 8), c0 = (i - r * (kTS / 8)) * 8;
-    float u[18], v[18];
+    const int c0 = (i / kWS) * 8, r = i - (i / kWS) * kWS;  // consecutive lanes: consecutive rows
+    float2 u[18];
 #pragma unroll
-    for (int k = 0; k < 18; ++k) {
-      u[k] = sI[r][c0 + k];
-      v[k] = sT[r][c0 + k];
-    }
+    for (int k = 0; k < 18; ++k) u[k] = win[r][c0 + k];
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+      float2 a01 = splat(0.f), a23 = splat(0.f);
+      float a4 = 0.f;
 #pragma unroll
       for (int k = 0; k < 11; ++k) {
-        const float wk = p.w[k], uu = u[o + k], vv = v[o + k];
-        a0 = fmaf(wk, uu, a0);
-        a1 = fmaf(wk, vv, a1);
-        a2 = fmaf(wk * uu, uu, a2);
-        a3 = fmaf(wk * vv, vv, a3);
-        a4 = fmaf(wk * uu, vv, a4);
+        const float2 w2 = splat(p.w[k]), uv = u[o + k];
+        a01 = __ffma2_rn(w2, uv, a01);
+        const float2 wuv = __fmul2_rn(w2, uv);
+        a23 = __ffma2_rn(wuv, uv, a23);
+        a4 = fmaf(wuv.x, uv.y, a4);
       }
-      hs[0][r][c0 + o] = a0; hs[1][r][c0 + o] = a1; hs[2][r][c0 + o] = a2; hs[3][r][c0 + o] = a3;
-      hs[4][r][c0 + o] = a4;
+      h01[r][c0 + o] = a01;
+      h23[r][c0 + o] = a23;
+      h4[r][c0 + o] = a4;
     }
   }
   __syncthreads();
-  double ssim_acc = 0.0, l1_acc = 0.0;
-  // vertical window sums: a thread takes 4 consecutive outputs of one column
-  for (int i = threadIdx.x; i < kTS * (kTS / 4); i += kThreads) {
+  // vertical window sums: a thread takes 4 consecutive outputs of one column,
+  // then the SSIM term and its derivatives for each (one division per pixel:
+  // 1/C and 1/D come from 1/(C D))
+  float ssim_f = 0.f, l1_f = 0.f;  // this thread's four pixels, then a fixed xor tree per warp
+  {
+    const int i = threadIdx.x;  // kTS * (kTS / 4) == kThreads outputs groups
     const int x = i % kTS, yb = (i / kTS) * 4;
-    float mm[4][5];
+    float2 m01[4], m23[4];
+    float m4[4];
+    {
+      float2 col[14];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
+      for (int k = 0; k < 14; ++k) col[k] = h01[yb + k][x];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        float2 acc = splat(0.f);
+#pragma unroll
+        for (int k = 0; k < 11; ++k) acc = __ffma2_rn(splat(p.w[k]), col[o + k], acc);
+        m01[o] = acc;
+      }
+    }
+    {
+      float2 col[14];
+#pragma unroll
+      for (int k = 0; k < 14; ++k) col[k] = h23[yb + k][x];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        float2 acc = splat(0.f);
+#pragma unroll
+        for (int k = 0; k < 11; ++k) acc = __ffma2_rn(splat(p.w[k]), col[o + k], acc);
+        m23[o] = acc;
+      }
+    }
+    {
       float col[14];
 #pragma unroll
-      for (int k = 0; k < 14; ++k) col[k] = hs[q][yb + k][x];
+      for (int k = 0; k < 14; ++k) col[k] = h4[yb + k][x];
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
         float acc = 0.f;
 #pragma unroll
         for (int k = 0; k < 11; ++k) acc = fmaf(p.w[k], col[o + k], acc);
-        mm[o][q] = acc;
+        m4[o] = acc;
       }
     }
+    const int64_t plane = (int64_t)p.S * HW;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
-    const int y = yb + o;
-    const int gy = y0 + y, gx = x0 + x;
-    if (!in_img(p, gy, gx)) continue;
-    const float* m = mm[o];
-    const float mI = m[0], mT = m[1];
-    const float sII = m[2] - mI * mI, sTT = m[3] - mT * mT, sIT = m[4] - mI * mT;
-    const float A = fmaf(2.0f * mI, mT, p.c1), Bv = fmaf(2.0f, sIT, p.c2);
-    const float Cv = fmaf(mI, mI, fmaf(mT, mT, p.c1)), D = sII + sTT + p.c2;
-    const float inv_CD = 1.0f / (Cv * D);
-    const float Sv = A * Bv * inv_CD;
-    const float dS_dmI = 2.0f * mT * Bv * inv_CD - Sv * 2.0f * mI / Cv;
-    const float dS_dsII = -Sv / D;
-    const float dS_dsIT = 2.0f * A * inv_CD;
-    const int64_t off = (int64_t)s * HW + (int64_t)gy * p.W + gx;
-    const int64_t plane = (int64_t)p.S * HW;
-    dS[off] = dS_dmI - 2.0f * mI * dS_dsII - mT * dS_dsIT;  // dS/dm_I (all paths)
-    dS[plane + off] = dS_dsII;                              // dS/dm_II
-    dS[2 * plane + off] = dS_dsIT;                          // dS/dm_IT
-    ssim_acc += (double)Sv;
-    l1_acc += (double)fabsf(sI[y + kHalo][x + kHalo] - sT[y + kHalo][x + kHalo]);
+      const int y = yb + o;
+      const int gy = y0 + y, gx = x0 + x;
+      if (!in_img(p, gy, gx)) continue;
+      const float mI = m01[o].x, mT = m01[o].y;
+      const float sII = m23[o].x - mI * mI, sTT = m23[o].y - mT * mT, sIT = m4[o] - mI * mT;
+      const float A = fmaf(2.0f * mI, mT, p.c1), Bv = fmaf(2.0f, sIT, p.c2);
+      const float Cv = fmaf(mI, mI, fmaf(mT, mT, p.c1)), D = sII + sTT + p.c2;
+      const float inv_CD = 1.0f / (Cv * D);
+      const float Sv = A * Bv * inv_CD;
+      const float dS_dmI = 2.0f * mT * Bv * inv_CD - 2.0f * mI * Sv * (D * inv_CD);  // S 2 m_I / C
+      const float dS_dsII = -Sv * (Cv * inv_CD);                                     // -S / D
+      const float dS_dsIT = 2.0f * A * inv_CD;
+      const int64_t off = (int64_t)s * HW + (int64_t)gy * p.W + gx;
+      dS[off] = dS_dmI - 2.0f * mI * dS_dsII - mT * dS_dsIT;  // dS/dm_I (all paths)
+      dS[plane + off] = dS_dsII;                              // dS/dm_II
+      dS[2 * plane + off] = dS_dsIT;                          // dS/dm_IT
+      const float2 it = win[y + kHalo][x + kHalo];
+      ssim_f += Sv;
+      l1_f += fabsf(it.x - it.y);
     }
   }
-  // block sums in a fixed order
+  // block sums in a fixed order: fp32 xor trees over the warp's 128 pixels,
+  // then the eight warps in double
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    ssim_acc += __shfl_xor_sync(0xffffffffu, ssim_acc, o);
-    l1_acc += __shfl_xor_sync(0xffffffffu, l1_acc, o);
+    ssim_f += __shfl_xor_sync(0xffffffffu, ssim_f, o);
+    l1_f += __shfl_xor_sync(0xffffffffu, l1_f, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = ssim_acc;
-    red[1][threadIdx.x >> 5] = l1_acc;
+    red[0][threadIdx.x >> 5] = (double)ssim_f;
+    red[1][threadIdx.x >> 5] = (double)l1_f;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -158,67 +241,85 @@ __global__ void __launch_bounds__(kThreads) k_ssim_stats(SsimArgs p, const float
 __global__ void __launch_bounds__(kThreads) k_ssim_grad(SsimArgs p, const float* __restrict__ I,
                                                        const float* __restrict__ T, const int* __restrict__ tidx,
                                                        const float* __restrict__ dS, float* __restrict__ dL_dI) {
-  __shared__ float sA[3][kWS][kWS + 1];
-  __shared__ float hs[3][kWS][kTS + 1];
+  __shared__ float2 sA01[kWS][kWS + 1];  // (dS/dm_I, dS/dm_II) of the window
+  __shared__ float sA2[kWS][kWS + 1];    // dS/dm_IT
+  __shared__ float2 h01[kWS][kTS + 1];   // their row sums
+  __shared__ float h2[kWS][kTS + 1];
   const int s = blockIdx.z;
   const int x0 = blockIdx.x * kTS, y0 = blockIdx.y * kTS;
   const int64_t HW = (int64_t)p.H * p.W;
   const int64_t plane = (int64_t)p.S * HW;
-  for (int i = threadIdx.x; i < kWS * kWS; i += kThreads) {
-    const int r = i / kWS, c = i - r * kWS;
-    const int y = y0 - kHalo + r, x = x0 - kHalo + c;
-    const bool in = in_img(p, y, x);
-    const int64_t o = (int64_t)s * HW + (int64_t)y * p.W + x;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) sA[q][r][c] = in ? dS[q * plane + o] : 0.0f;
-  }
+  const float* d0 = dS + (int64_t)s * HW;
+  const float* const src[3] = {d0, d0 + plane, d0 + 2 * plane};
+  stage_window<3>(p, src, x0, y0, planes_aligned<3>(p, src), [&](int r, int c, const float (&v)[3]) {
+    sA01[r][c] = make_float2(v[0], v[1]);
+    sA2[r][c] = v[2];
+  });
   __syncthreads();
-  for (int i = threadIdx.x; i < 3 * kWS * (kTS / 8); i += kThreads) {
-    const int q = i / (kWS * (kTS / 8));
-    const int rr = i - q * (kWS * (kTS / 8));
-    const int r = rr / (kTS / 8), c0 = (rr - r * (kTS / 8)) * 8;
-    float u[18];
+  for (int i = threadIdx.x; i < kWS * (kTS / 8); i += kThreads) {
+    const int c0 = (i / kWS) * 8, r = i - (i / kWS) * kWS;  // consecutive lanes: consecutive rows
+    float2 u[18];
+    float v[18];
 #pragma unroll
-    for (int k = 0; k < 18; ++k) u[k] = sA[q][r][c0 + k];
+    for (int k = 0; k < 18; ++k) {
+      u[k] = sA01[r][c0 + k];
+      v[k] = sA2[r][c0 + k];
+    }
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
-      float acc = 0.f;
+      float2 a = splat(0.f);
+      float b = 0.f;
 #pragma unroll
-      for (int k = 0; k < 11; ++k) acc = fmaf(p.w[k], u[o + k], acc);
-      hs[q][r][c0 + o] = acc;
+      for (int k = 0; k < 11; ++k) {
+        a = __ffma2_rn(splat(p.w[k]), u[o + k], a);
+        b = fmaf(p.w[k], v[o + k], b);
+      }
+      h01[r][c0 + o] = a;
+      h2[r][c0 + o] = b;
     }
   }
   __syncthreads();
   const float* Ip = I + (int64_t)s * HW;
   const float* Tp = T + (int64_t)(tidx ? tidx[s] : s) * HW;
-  for (int i = threadIdx.x; i < kTS * (kTS / 4); i += kThreads) {
+  {
+    const int i = threadIdx.x;  // kTS * (kTS / 4) == kThreads output groups
     const int x = i % kTS, yb = (i / kTS) * 4;
-    float cc[4][3];
+    float2 c01[4];
+    float c2[4];
+    {
+      float2 col[14];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
+      for (int k = 0; k < 14; ++k) col[k] = h01[yb + k][x];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        float2 acc = splat(0.f);
+#pragma unroll
+        for (int k = 0; k < 11; ++k) acc = __ffma2_rn(splat(p.w[k]), col[o + k], acc);
+        c01[o] = acc;
+      }
+    }
+    {
       float col[14];
 #pragma unroll
-      for (int k = 0; k < 14; ++k) col[k] = hs[q][yb + k][x];
+      for (int k = 0; k < 14; ++k) col[k] = h2[yb + k][x];
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
         float acc = 0.f;
 #pragma unroll
         for (int k = 0; k < 11; ++k) acc = fmaf(p.w[k], col[o + k], acc);
-        cc[o][q] = acc;
+        c2[o] = acc;
       }
     }
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
-    const int y = yb + o;
-    const int gy = y0 + y, gx = x0 + x;
-    if (!in_img(p, gy, gx)) continue;
-    const float* c = cc[o];
-    const int64_t off = (int64_t)gy * p.W + gx;
-    const float iv = Ip[off], tv = Tp[off];
-    const float d = iv - tv;
-    const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
-    const float dssim = fmaf(2.0f * iv, c[1], fmaf(tv, c[2], c[0]));
-    dL_dI[(int64_t)s * HW + off] = p.inv_n * fmaf(-p.lam, dssim, sgn);
+      const int gy = y0 + yb + o, gx = x0 + x;
+      if (!in_img(p, gy, gx)) continue;
+      const int64_t off = (int64_t)gy * p.W + gx;
+      const float iv = Ip[off], tv = Tp[off];
+      const float d = iv - tv;
+      const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
+      const float dssim = fmaf(2.0f * iv, c01[o].y, fmaf(tv, c2[o], c01[o].x));
+      dL_dI[(int64_t)s * HW + off] = p.inv_n * fmaf(-p.lam, dssim, sgn);
     }
   }
 }
