@@ -59,34 +59,54 @@ __device__ __forceinline__ bool in_img(const SsimArgs& p, int y, int x) {
 template <int N, typename Store>
 __device__ __forceinline__ void stage_window(const SsimArgs& p, const float* const (&src)[N], int x0, int y0,
                                              bool vec, Store store) {
+  // every load of the thread first, then the stores (a store between two
+  // loads would hold the second back until the first has landed)
   if (vec) {
-    for (int i = threadIdx.x; i < kWS * 12; i += kThreads) {
+    constexpr int NI = (kWS * 12 + kThreads - 1) / kThreads;
+    float4 v[NI][N];
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+      const int i = threadIdx.x + j * kThreads;
       const int r = i / 12, q = i - r * 12;
       const int y = y0 - kHalo + r, xq = x0 - 8 + 4 * q;
-      const bool in = y >= 0 && y < p.H && xq >= 0 && xq < p.W;
-      float4 v[N];
+      const bool in = i < kWS * 12 && y >= 0 && y < p.H && xq >= 0 && xq < p.W;
 #pragma unroll
       for (int n = 0; n < N; ++n)
-        v[n] = in ? *reinterpret_cast<const float4*>(src[n] + (int64_t)y * p.W + xq) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[j][n] = in ? *reinterpret_cast<const float4*>(src[n] + (int64_t)y * p.W + xq) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+      const int i = threadIdx.x + j * kThreads;
+      if (i >= kWS * 12) break;
+      const int r = i / 12, q = i - r * 12;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int c = 4 * q + k - 3;  // x = xq + k = x0 - kHalo + c
         if (c < 0 || c >= kWS) continue;
         float e[N];
 #pragma unroll
-        for (int n = 0; n < N; ++n) e[n] = k == 0 ? v[n].x : k == 1 ? v[n].y : k == 2 ? v[n].z : v[n].w;
+        for (int n = 0; n < N; ++n) e[n] = k == 0 ? v[j][n].x : k == 1 ? v[j][n].y : k == 2 ? v[j][n].z : v[j][n].w;
         store(r, c, e);
       }
     }
   } else {
-    for (int i = threadIdx.x; i < kWS * kWS; i += kThreads) {
+    constexpr int NI = (kWS * kWS + kThreads - 1) / kThreads;
+    float e[NI][N];
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+      const int i = threadIdx.x + j * kThreads;
       const int r = i / kWS, c = i - r * kWS;
       const int y = y0 - kHalo + r, x = x0 - kHalo + c;
-      const bool in = in_img(p, y, x);
-      float e[N];
+      const bool in = i < kWS * kWS && in_img(p, y, x);
 #pragma unroll
-      for (int n = 0; n < N; ++n) e[n] = in ? src[n][(int64_t)y * p.W + x] : 0.0f;
-      store(r, c, e);
+      for (int n = 0; n < N; ++n) e[j][n] = in ? src[n][(int64_t)y * p.W + x] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+      const int i = threadIdx.x + j * kThreads;
+      if (i >= kWS * kWS) break;
+      const int r = i / kWS, c = i - r * kWS;
+      store(r, c, e[j]);
     }
   }
 }
@@ -102,7 +122,7 @@ __device__ __forceinline__ bool planes_aligned(const SsimArgs& p, const float* c
 
 __device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
 
-__global__ void __launch_bounds__(kThreads) k_ssim_stats(SsimArgs p, const float* __restrict__ I,
+__global__ void __launch_bounds__(kThreads, 5) k_ssim_stats(SsimArgs p, const float* __restrict__ I,
                                                         const float* __restrict__ T, const int* __restrict__ tidx,
                                                         float* __restrict__ dS, double* __restrict__ part) {
   __shared__ float2 win[kWS][kWS + 1];   // (I, T) of the window
@@ -238,7 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_ssim_stats(SsimArgs p, const float
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_ssim_grad(SsimArgs p, const float* __restrict__ I,
+__global__ void __launch_bounds__(kThreads, 5) k_ssim_grad(SsimArgs p, const float* __restrict__ I,
                                                        const float* __restrict__ T, const int* __restrict__ tidx,
                                                        const float* __restrict__ dS, float* __restrict__ dL_dI) {
   __shared__ float2 sA01[kWS][kWS + 1];  // (dS/dm_I, dS/dm_II) of the window
@@ -251,6 +271,20 @@ __global__ void __launch_bounds__(kThreads) k_ssim_grad(SsimArgs p, const float*
   const int64_t plane = (int64_t)p.S * HW;
   const float* d0 = dS + (int64_t)s * HW;
   const float* const src[3] = {d0, d0 + plane, d0 + 2 * plane};
+  // the thread's four output pixels (column x, rows yb .. yb + 3): their I and T
+  // are loaded first, so the epilogue does not wait on them
+  const int ox = threadIdx.x % kTS, oyb = (threadIdx.x / kTS) * 4;
+  const float* Ip = I + (int64_t)s * HW;
+  const float* Tp = T + (int64_t)(tidx ? tidx[s] : s) * HW;
+  float iv[4], tv[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const int gy = y0 + oyb + o, gx = x0 + ox;
+    const bool in = in_img(p, gy, gx);
+    const int64_t off = (int64_t)gy * p.W + gx;
+    iv[o] = in ? Ip[off] : 0.0f;
+    tv[o] = in ? Tp[off] : 0.0f;
+  }
   stage_window<3>(p, src, x0, y0, planes_aligned<3>(p, src), [&](int r, int c, const float (&v)[3]) {
     sA01[r][c] = make_float2(v[0], v[1]);
     sA2[r][c] = v[2];
@@ -279,11 +313,8 @@ __global__ void __launch_bounds__(kThreads) k_ssim_grad(SsimArgs p, const float*
     }
   }
   __syncthreads();
-  const float* Ip = I + (int64_t)s * HW;
-  const float* Tp = T + (int64_t)(tidx ? tidx[s] : s) * HW;
   {
-    const int i = threadIdx.x;  // kTS * (kTS / 4) == kThreads output groups
-    const int x = i % kTS, yb = (i / kTS) * 4;
+    const int x = ox, yb = oyb;  // kTS * (kTS / 4) == kThreads output groups
     float2 c01[4];
     float c2[4];
     {
@@ -315,10 +346,9 @@ __global__ void __launch_bounds__(kThreads) k_ssim_grad(SsimArgs p, const float*
       const int gy = y0 + yb + o, gx = x0 + x;
       if (!in_img(p, gy, gx)) continue;
       const int64_t off = (int64_t)gy * p.W + gx;
-      const float iv = Ip[off], tv = Tp[off];
-      const float d = iv - tv;
+      const float d = iv[o] - tv[o];
       const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
-      const float dssim = fmaf(2.0f * iv, c01[o].y, fmaf(tv, c2[o], c01[o].x));
+      const float dssim = fmaf(2.0f * iv[o], c01[o].y, fmaf(tv[o], c2[o], c01[o].x));
       dL_dI[(int64_t)s * HW + off] = p.inv_n * fmaf(-p.lam, dssim, sgn);
     }
   }
