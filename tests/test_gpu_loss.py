@@ -86,6 +86,26 @@ def test_identical_images_have_zero_loss_and_gradient(ctx):
     assert g.abs().max().item() < 1e-9
 
 
+def test_staging_paths_agree_bitwise(ctx):
+    """The stencil passes stage their halo rows as aligned float4 when the width
+    is a multiple of 4 and every plane is 16-byte aligned, else pixel by pixel.
+    Planes offset by one float take the second path; both must give the same
+    bits (the arithmetic after staging is the same)."""
+    I, T = _pair(15, (3, 40, 64))
+    Ia, Ta = torch.from_numpy(I).cuda(), torch.from_numpy(T).cuda()
+    bufI = torch.empty(I.size + 1, device="cuda")
+    bufT = torch.empty(T.size + 1, device="cuda")
+    Im, Tm = bufI[1:].view(I.shape), bufT[1:].view(T.shape)  # 4 bytes past a 16-byte boundary
+    Im.copy_(Ia)
+    Tm.copy_(Ta)
+    assert Im.data_ptr() % 16 == 4 and Im.is_contiguous()
+    la, lm = torch.zeros(3, device="cuda"), torch.zeros(3, device="cuda")
+    ga, _ = B.gp_l1_dssim_grad(ctx, Ia, Ta, loss=la)
+    gm, _ = B.gp_l1_dssim_grad(ctx, Im, Tm, loss=lm)
+    assert torch.equal(ga, gm) and torch.equal(la, lm)
+    _check(ctx, I, T)  # and the aligned path against the oracle
+
+
 def test_bad_arguments(ctx):
     I = torch.zeros(1, 8, 8, device="cuda")
     with pytest.raises(B.GPError):
