@@ -68,10 +68,11 @@ def microscopy_set(synth, seed):
 
 # Lane instructions of the FP32/INT pipes per ALGORITHMIC evaluation, counted from
 # the method's arithmetic with the project-written exp2 (range reduction 3 FADD,
-# degree-6 Horner 6 FFMA, exponent insert 2 INT): forward = offset 1 + quadratic
-# form 2 + clamp 1 + exp2 11 + accumulate 1; backward = the same 15 up to the
-# exponential + 5 moment updates (g = G E, 2 sums, 1 product, 1 FMA).
-OPS_PER_EVAL = {"fwd": 16, "bwd": 20}
+# Horner 6 FFMA for the forward's degree-6 polynomial and 4 for the backward's
+# degree-4 one, exponent insert 2 INT): forward = offset 1 + quadratic form 2 +
+# clamp 1 + exp2 11 + accumulate 1; backward = offset 1 + quadratic form 2 +
+# clamp 1 + exp2 9 + 5 moment updates (g = G E, 2 sums, 1 product, 1 FMA).
+OPS_PER_EVAL = {"fwd": 16, "bwd": 18}
 # The row-factored form (GP_EXP_POLY_ROW) does its exponentials per row of 8
 # pixels: per row 2 exp2 (22) + 2 clamps + the larger end's exponent 1 + powers
 # r^2..r^7 6 + row coefficients 4, then forward 7 scalings by L + 8 accumulates

@@ -79,7 +79,9 @@ typedef struct gp_ctx gp_ctx;
 
 /* Exponential used by the rasterisers. */
 #define GP_EXP_POLY 0  /* project-written exp2: range reduction + degree-6 polynomial on
-                          the FP32 pipe (no ex2.approx); the default */
+                          the FP32 pipe (no ex2.approx); the default.  The backward
+                          recomputes its per-pixel exponentials with a degree-4 polynomial
+                          (relative error 3.6e-6; its gradients are held to 1e-3) */
 #define GP_EXP_HW 1    /* the SFU ex2.approx instruction (benchmarked alternative) */
 #define GP_EXP_POLY_PACKED 2  /* gp_exp2_eval only: GP_EXP_POLY in the packed two-value form
                                  the rasterisers use (bitwise equal to GP_EXP_POLY) */
@@ -91,6 +93,9 @@ typedef struct gp_ctx gp_ctx;
                                  ulp per pixel instead of about 2).  Block-culled rasterisers
                                  only (fwd_px = bwd_px = 0); Gaussians narrower than about 0.3
                                  pixel fall back to one exp2 per pixel. */
+#define GP_EXP_POLY_GRAD 4    /* gp_exp2_eval only: the backward's degree-4 exp2 */
+#define GP_EXP_POLY_GRAD_PACKED 5  /* gp_exp2_eval only: GP_EXP_POLY_GRAD in the packed form the
+                                      backward uses (bitwise equal to GP_EXP_POLY_GRAD) */
 
 /* Form of the default rasterisers (fwd_px = bwd_px = 0), GP_EXP_POLY / GP_EXP_HW. */
 #define GP_RASTER_AUTO 0   /* row units for the forward, and for the backward on voxelizer planes;
@@ -308,8 +313,8 @@ GP_API gp_status gp_count_evals(gp_ctx* ctx, const gp_set* set, const float* z, 
                          int W, float sigma_z, int axis, int64_t* evals);
 
 /* Test hook for the rasterisers' exponential: y[i] = 2^x[i] for n DEVICE floats
- * with the given mode (GP_EXP_POLY, GP_EXP_HW or GP_EXP_POLY_PACKED).  Inputs
- * below -125 clamp. */
+ * with the given mode (GP_EXP_POLY, GP_EXP_HW, GP_EXP_POLY_PACKED, GP_EXP_POLY_GRAD or
+ * GP_EXP_POLY_GRAD_PACKED).  Inputs below -125 clamp. */
 GP_API gp_status gp_exp2_eval(gp_ctx* ctx, const float* x, float* y, int64_t n, int mode,
                        void* stream);
 

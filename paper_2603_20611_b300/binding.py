@@ -33,6 +33,8 @@ GP_EXP_POLY = 0
 GP_EXP_HW = 1
 GP_EXP_POLY_PACKED = 2
 GP_EXP_POLY_ROW = 3
+GP_EXP_POLY_GRAD = 4
+GP_EXP_POLY_GRAD_PACKED = 5
 
 # Every symbol include/gp.h declares (checked by the CPU ABI test).
 EXPORTS = (

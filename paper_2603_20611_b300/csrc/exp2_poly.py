@@ -1,12 +1,16 @@
-"""Derives the coefficients of the rasterisers' exp2 polynomial.
+"""Derives the coefficients of the rasterisers' exp2 polynomials.
 
 2^x = 2^n * 2^f with n = round(x) and f = x - n in [-1/2, 1/2]; 2^f is
-approximated by a degree-6 polynomial p(f) with p(0) = 1 exactly, chosen to
-minimise the maximum RELATIVE error |p(f) / 2^f - 1| on [-1/2, 1/2] by the
-Remez exchange algorithm (equioscillation at deg + 1 points once the constant
-term is fixed).  The coefficients are then rounded to fp32 and the error of
-the rounded polynomial, evaluated by Horner's rule in fp32 arithmetic
-(emulated with numpy float32, separate multiply and add roundings), is reported.
+approximated by a polynomial p(f) with p(0) = 1 exactly, chosen to minimise
+the maximum RELATIVE error |p(f) / 2^f - 1| on [-1/2, 1/2] by the Remez
+exchange algorithm (equioscillation at deg + 1 points once the constant term
+is fixed).  The coefficients are then rounded to fp32 and the error of the
+rounded polynomial, evaluated by Horner's rule in fp32 arithmetic (emulated
+with numpy float32, separate multiply and add roundings), is reported.
+
+Two degrees: 6 (GP_EXP2_C*, about 2 ulp: the forward's pixels, which the
+images need to fp32 accuracy) and 4 (GP_EXP2G_C*, 3.6e-6 relative: the
+exponentials the backward recomputes, whose gradients are held to 1e-3).
 
 Run: python exp2_poly.py   (prints the C initialisers used in gp_common.cuh)
 """
@@ -64,11 +68,12 @@ def horner_f32(c32, f):
 
 
 if __name__ == "__main__":
-    c, e = remez()
-    c32 = c.astype(np.float32)
-    g = np.linspace(LO, HI, 2000001)
-    rel = horner_f32(c32, g).astype(np.float64) / np.exp2(g) - 1.0
-    print(f"// degree {DEG}, levelled relative error {e:.3e}, fp32 Horner max rel err "
-          f"{np.max(np.abs(rel)):.3e} ({np.max(np.abs(rel)) / 2**-24:.2f} ulp of 2^-24)")
-    for i, ck in enumerate(c32, start=1):
-        print(f"#define GP_EXP2_C{i} {float(ck)!r}f")
+    for deg, name in ((DEG, "GP_EXP2_C"), (4, "GP_EXP2G_C")):
+        c, e = remez(deg)
+        c32 = c.astype(np.float32)
+        g = np.linspace(LO, HI, 2000001)
+        rel = horner_f32(c32, g).astype(np.float64) / np.exp2(g) - 1.0
+        print(f"// degree {deg}, levelled relative error {e:.3e}, fp32 Horner max rel err "
+              f"{np.max(np.abs(rel)):.3e} ({np.max(np.abs(rel)) / 2**-24:.2f} ulp of 2^-24)")
+        for i, ck in enumerate(c32, start=1):
+            print(f"#define {name}{i} {float(ck)!r}f")

@@ -61,6 +61,44 @@ __device__ __forceinline__ float2 exp2_poly2(float2 x) {
                      __int_as_float(__float_as_int(p.y) + (__float_as_int(t.y) << 23)));
 }
 
+// The backward's exponential: the same range reduction and exponent insert
+// with a degree-4 polynomial (Remez, p(0) = 1, csrc/exp2_poly.py; max
+// relative error 3.6e-6 on the reduced range with fp32 Horner).  The backward
+// recomputes every pixel's exponential only to weight dL/dI in the gradient
+// sums, which are held to 1e-3 relative; the images keep the degree-6 form.
+#define GP_EXP2G_C1 0.6931136250495911f
+#define GP_EXP2G_C2 0.24020710587501526f
+#define GP_EXP2G_C3 0.055976882576942444f
+#define GP_EXP2G_C4 0.009782912209630013f
+
+__device__ __forceinline__ float exp2_grad(float x) {
+  const float kShift = 12582912.0f;  // 1.5 * 2^23
+  float t = __fadd_rn(x, kShift);
+  float n = __fsub_rn(t, kShift);
+  float f = __fsub_rn(x, n);
+  float p = GP_EXP2G_C4;
+  p = fmaf(p, f, GP_EXP2G_C3);
+  p = fmaf(p, f, GP_EXP2G_C2);
+  p = fmaf(p, f, GP_EXP2G_C1);
+  p = fmaf(p, f, 1.0f);
+  return __int_as_float(__float_as_int(p) + (__float_as_int(t) << 23));
+}
+
+// exp2_grad on two values per packed instruction, bitwise the scalar form.
+__device__ __forceinline__ float2 exp2_grad2(float2 x) {
+  const float kShift = 12582912.0f;  // 1.5 * 2^23
+  const float2 t = __fadd2_rn(x, make_float2(kShift, kShift));
+  const float2 n = __fadd2_rn(t, make_float2(-kShift, -kShift));
+  const float2 f = __ffma2_rn(n, make_float2(-1.0f, -1.0f), x);  // x - n, rounded once
+  float2 p = make_float2(GP_EXP2G_C4, GP_EXP2G_C4);
+  p = __ffma2_rn(p, f, make_float2(GP_EXP2G_C3, GP_EXP2G_C3));
+  p = __ffma2_rn(p, f, make_float2(GP_EXP2G_C2, GP_EXP2G_C2));
+  p = __ffma2_rn(p, f, make_float2(GP_EXP2G_C1, GP_EXP2G_C1));
+  p = __ffma2_rn(p, f, make_float2(1.0f, 1.0f));
+  return make_float2(__int_as_float(__float_as_int(p.x) + (__float_as_int(t.x) << 23)),
+                     __int_as_float(__float_as_int(p.y) + (__float_as_int(t.y) << 23)));
+}
+
 // The SFU instruction, as a benchmarked alternative (GP_EXP_HW).
 __device__ __forceinline__ float exp2_hw(float x) {
   float y;
@@ -78,6 +116,19 @@ template <int MODE>
 __device__ __forceinline__ float2 exp2_sel2(float2 x) {
   if constexpr (MODE == GP_EXP_HW) return make_float2(exp2_hw(x.x), exp2_hw(x.y));
   else return exp2_poly2(x);
+}
+
+// The backward's per-pixel exponentials: exp2_grad for the polynomial modes.
+template <int MODE>
+__device__ __forceinline__ float exp2_sel_grad(float x) {
+  if constexpr (MODE == GP_EXP_HW) return exp2_hw(x);
+  else return exp2_grad(x);
+}
+
+template <int MODE>
+__device__ __forceinline__ float2 exp2_sel2_grad(float2 x) {
+  if constexpr (MODE == GP_EXP_HW) return make_float2(exp2_hw(x.x), exp2_hw(x.y));
+  else return exp2_grad2(x);
 }
 
 // Exponentials of two consecutive samples (2p, 2p + 1) of a row: e = A + B q +
@@ -218,14 +269,16 @@ __device__ __forceinline__ unsigned plane_cells(float4 r0, float4 r2, float4 r3,
 // finishes each exponent.
 // FLOOR = false drops the floor where the caller knows every exponent is above
 // kExpUnfloored.
-template <int EXPM, bool FLOOR = true>
+// GRAD selects the backward's exponential (exp2_grad in the polynomial modes).
+template <int EXPM, bool FLOOR = true, bool GRAD = false>
 __device__ __forceinline__ float2 couple_exp2(float2 B2, float2 q, float2 base) {
   float2 e = __ffma2_rn(B2, q, base);
   if constexpr (FLOOR) {
     e.x = fmaxf(e.x, kExpFloor);
     e.y = fmaxf(e.y, kExpFloor);
   }
-  return exp2_sel2<EXPM>(e);
+  if constexpr (GRAD) return exp2_sel2_grad<EXPM>(e);
+  else return exp2_sel2<EXPM>(e);
 }
 
 // Exponents at or above this need no floor in exp2_poly (a margin of one over

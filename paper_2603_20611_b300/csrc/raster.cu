@@ -498,8 +498,8 @@ __device__ __forceinline__ void bwd_tile(const SliceArgs& a, int local_key, cons
                 const float2 GY = k == 0 ? make_float2(gy.x, gy.y) : make_float2(gy.z, gy.w);
                 // e(+-q) = (A + C q^2) +- B q
                 const float2 base = __ffma2_rn(C2, q2, A2);
-                const float2 Y = __fmul2_rn(GY, couple_exp2<EXPM, FL>(Bn2, q, base));
-                const float2 XY = __ffma2_rn(GX, couple_exp2<EXPM, FL>(B2, q, base), Y);
+                const float2 Y = __fmul2_rn(GY, couple_exp2<EXPM, FL, true>(Bn2, q, base));
+                const float2 XY = __ffma2_rn(GX, couple_exp2<EXPM, FL, true>(B2, q, base), Y);
                 if (r == 3 && k == 0) {
                   P0 = XY;
                   P1 = __fmul2_rn(q, XY);

@@ -537,10 +537,10 @@ __device__ __forceinline__ void bwd_tile_rows(const SliceArgs& a, int local_key,
           const float2 bA = __ffma2_rn(C2, make_float2(12.25f, 6.25f), A2);
           const float2 bB = __ffma2_rn(C2, make_float2(2.25f, 0.25f), A2);
           const float2 qA = make_float2(-3.5f, -2.5f), qB = make_float2(-1.5f, -0.5f);
-          const float2 YA = __fmul2_rn(make_float2(gy.x, gy.y), couple_exp2<EXPM>(B2, make_float2(3.5f, 2.5f), bA));
-          const float2 XA = __ffma2_rn(make_float2(gx.x, gx.y), couple_exp2<EXPM>(B2, qA, bA), YA);
-          const float2 YB = __fmul2_rn(make_float2(gy.z, gy.w), couple_exp2<EXPM>(B2, make_float2(1.5f, 0.5f), bB));
-          const float2 XB = __ffma2_rn(make_float2(gx.z, gx.w), couple_exp2<EXPM>(B2, qB, bB), YB);
+          const float2 YA = __fmul2_rn(make_float2(gy.x, gy.y), couple_exp2<EXPM, true, true>(B2, make_float2(3.5f, 2.5f), bA));
+          const float2 XA = __ffma2_rn(make_float2(gx.x, gx.y), couple_exp2<EXPM, true, true>(B2, qA, bA), YA);
+          const float2 YB = __fmul2_rn(make_float2(gy.z, gy.w), couple_exp2<EXPM, true, true>(B2, make_float2(1.5f, 0.5f), bB));
+          const float2 XB = __ffma2_rn(make_float2(gx.z, gx.w), couple_exp2<EXPM, true, true>(B2, qB, bB), YB);
           const float2 P0 = __fadd2_rn(XA, XB);
           float2 P1 = __ffma2_rn(qB, XB, __fmul2_rn(qA, XA));
           P1 = __ffma2_rn(make_float2(7.0f, 5.0f), YA, P1);

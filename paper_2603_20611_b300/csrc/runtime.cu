@@ -811,7 +811,8 @@ gp_status gp_exp2_eval(gp_ctx* ctx, const float* x, float* y, int64_t n, int mod
   if (!ctx) return GP_ERR_ARG;
   Ctx* c = &ctx->impl;
   if (n < 0 || (n > 0 && (!x || !y))) return set_err(c, GP_ERR_ARG, "bad exp2 arguments");
-  if (mode != GP_EXP_POLY && mode != GP_EXP_HW && mode != GP_EXP_POLY_PACKED)
+  if (mode != GP_EXP_POLY && mode != GP_EXP_HW && mode != GP_EXP_POLY_PACKED && mode != GP_EXP_POLY_GRAD &&
+      mode != GP_EXP_POLY_GRAD_PACKED)
     return set_err(c, GP_ERR_ARG, "bad exp mode");
   GP_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   launch_exp2_eval(x, y, n, mode, (cudaStream_t)stream);

@@ -781,7 +781,7 @@ __device__ __forceinline__ void bwd_tile_px(const SliceArgs& a, int local_key, c
         float dx = (px0 + (float)p) - g0.x;
         float e = fmaf(dx, fmaf(g1.x, dx, u), wy);
         e = fmaxf(e, kExpFloor);
-        float gE = G[p] * exp2_sel<EXPM>(e);
+        float gE = G[p] * exp2_sel_grad<EXPM>(e);
         m0 += gE;
         float tdx = gE * dx;
         mx += tdx;
@@ -1250,15 +1250,16 @@ __global__ void k_exp2_eval(const float* __restrict__ x, float* __restrict__ y, 
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float v = fmaxf(x[i], kExpFloor);
-  if (mode == GP_EXP_POLY_PACKED) {
+  if (mode == GP_EXP_POLY_PACKED || mode == GP_EXP_POLY_GRAD_PACKED) {
     // the packed two-value form, paired with the neighbouring element
     const int64_t j = i ^ 1;
     const float w = j < n ? fmaxf(x[j], kExpFloor) : 0.0f;
-    const float2 r = exp2_poly2((i & 1) ? make_float2(w, v) : make_float2(v, w));
+    const float2 xv = (i & 1) ? make_float2(w, v) : make_float2(v, w);
+    const float2 r = mode == GP_EXP_POLY_PACKED ? exp2_poly2(xv) : exp2_grad2(xv);
     y[i] = (i & 1) ? r.y : r.x;
     return;
   }
-  y[i] = mode == GP_EXP_HW ? exp2_hw(v) : exp2_poly(v);
+  y[i] = mode == GP_EXP_HW ? exp2_hw(v) : mode == GP_EXP_POLY_GRAD ? exp2_grad(v) : exp2_poly(v);
 }
 
 void launch_exp2_eval(const float* x, float* y, int64_t n, int mode, cudaStream_t st) {
