@@ -81,6 +81,11 @@ OPS_PER_EVAL = {"fwd": 16, "bwd": 18}
 # (84 per row), i.e. 50/8 and 84/8 lane instructions per evaluation.
 OPS_PER_EVAL_ROW = {"fwd": 6.25, "bwd": 10.5}
 EXP_MODES = {"poly": 0, "hw": 1, "row": 3}
+# What each --exp choice computes, for the JSON line's config.
+EXP_NOTE = {"poly": "project-written exp2, no ex2.approx: degree-6 polynomial (about 2 ulp) in the forward, "
+                    "degree-4 (3.6e-6 relative) for the exponentials the backward recomputes",
+            "hw": "the SFU ex2.approx instruction in both passes",
+            "row": "row-factored exponentials (two exp2 per row of 8 pixels), per-pixel exp2 for narrow Gaussians"}
 RASTER_FORMS = {"auto": 0, "block": 1, "rows": 2}
 
 
@@ -580,7 +585,8 @@ def run_native(args, rank, world):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": dict(WORKLOAD, exp=args.exp, deterministic=bool(args.det), tile=args.tile, loss=args.loss,
+                "config": dict(WORKLOAD, exp=args.exp, exp_note=EXP_NOTE[args.exp], deterministic=bool(args.det),
+                               tile=args.tile, loss=args.loss,
                                view=args.view,
                                backward_bins="re-binned" if args.rebin else "reused from the step's forward",
                                parallelism="replicas" if world > 1 else "single"),
@@ -998,7 +1004,8 @@ def run_ultrasound(args):
             "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": name, "n_gaussians": g.n, "l2": "flushed between steps (256 MiB write)",
-                       "exp": args.exp if args.workload == "ultrasound" else "poly"},
+                       "exp": args.exp if args.workload == "ultrasound" else "poly",
+                       "exp_note": EXP_NOTE[args.exp if args.workload == "ultrasound" else "poly"]},
             "evals_fwd_per_step": evals, "rasteriser": args.raster,
             "phase_ms_per_step": {k: v[0] / n_ph for k, v in phases_all.items() if v[2]},
             "phase_timing": f"a separate pass of {n_ph} steps with every phase timed; the timed steps record "
