@@ -25,6 +25,7 @@
 // the grid, so the same launches serve a preplanned (graph-captured) binning.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -101,6 +102,37 @@ __global__ void __launch_bounds__(1024) k_scan_partials(unsigned long long* __re
   if (threadIdx.x == 0 && total) *total = carry;
 }
 
+// The SCAN_ITEMS consecutive items of one thread (blocked arrangement): as
+// 16-byte loads / stores when they are all in range and the address is
+// 16-byte aligned, item by item otherwise.
+template <typename T>
+__device__ __forceinline__ void load_items(const T* __restrict__ in, int64_t base, int64_t n, T (&v)[SCAN_ITEMS]) {
+  static_assert((SCAN_ITEMS * sizeof(T)) % 16 == 0, "whole 16-byte vectors");
+  if (base + SCAN_ITEMS <= n && (reinterpret_cast<uintptr_t>(in + base) & 15u) == 0) {
+    uint4 w[SCAN_ITEMS * sizeof(T) / 16];
+#pragma unroll
+    for (int k = 0; k < (int)(SCAN_ITEMS * sizeof(T) / 16); ++k) w[k] = reinterpret_cast<const uint4*>(in + base)[k];
+    memcpy(v, w, sizeof(w));
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) v[k] = base + k < n ? in[base + k] : T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_items(T* __restrict__ out, int64_t base, int64_t n, const T (&v)[SCAN_ITEMS]) {
+  if (base + SCAN_ITEMS <= n && (reinterpret_cast<uintptr_t>(out + base) & 15u) == 0) {
+    uint4 w[SCAN_ITEMS * sizeof(T) / 16];
+    memcpy(w, v, sizeof(w));
+#pragma unroll
+    for (int k = 0; k < (int)(SCAN_ITEMS * sizeof(T) / 16); ++k) reinterpret_cast<uint4*>(out + base)[k] = w[k];
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k)
+    if (base + k < n) out[base + k] = v[k];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const T* __restrict__ in, T* __restrict__ out,
                                                              int64_t n,
@@ -110,21 +142,19 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const T* __restrict_
   T v[SCAN_ITEMS];
   unsigned long long s = 0;
   // blocked arrangement: thread t owns SCAN_ITEMS consecutive items
+  load_items(in, base, n, v);
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    int64_t i = base + k;
-    v[k] = i < n ? in[i] : T(0);
-    s += (unsigned long long)v[k];
-  }
+  for (int k = 0; k < SCAN_ITEMS; ++k) s += (unsigned long long)v[k];
   unsigned long long tot;
   unsigned long long ex = block_exclusive_scan<unsigned long long, SCAN_THREADS>(s, sw, &tot);
   unsigned long long run = part[blockIdx.x] + ex;
+  T o[SCAN_ITEMS];
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
-    int64_t i = base + k;
-    if (i < n) out[i] = (T)run;
+    o[k] = (T)run;
     run += (unsigned long long)v[k];
   }
+  store_items(out, base, n, o);
 }
 
 int64_t scan_temp_bytes(int64_t n) {
@@ -149,20 +179,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_small(const T* __restrict
   const int64_t base = tile0 + (int64_t)threadIdx.x * SCAN_ITEMS;
   T v[SCAN_ITEMS];
   unsigned long long s = 0;
+  load_items(in, base, n, v);
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    const int64_t i = base + k;
-    v[k] = i < n ? in[i] : T(0);
-    s += (unsigned long long)v[k];
-  }
+  for (int k = 0; k < SCAN_ITEMS; ++k) s += (unsigned long long)v[k];
   unsigned long long tot;
   unsigned long long run = carry + block_exclusive_scan<unsigned long long, SCAN_THREADS>(s, sw, &tot);
+  T o[SCAN_ITEMS];
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
-    const int64_t i = base + k;
-    if (i < n) out[i] = (T)run;
+    o[k] = (T)run;
     run += (unsigned long long)v[k];
   }
+  store_items(out, base, n, o);
   if (total && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) *total = carry + tot;
 }
 
