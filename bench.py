@@ -934,10 +934,14 @@ def run_ultrasound(args):
     # rasterisers' exponential (the voxelizer always evaluates exp2 per voxel)
     ctx = B.Context(0, reuse_bins=True, exp_mode=EXP_MODES[args.exp], tile=args.tile,
                     raster=RASTER_FORMS[args.raster])
-    g = synth.ultrasound()
+    # --case small (for kernel profiles): 50k Gaussians in 320^3 (the same density; a
+    # 131 MB volume, just above L2) against a two-blob target, so that few launches come
+    # before the rasterisers
+    small = args.case == "small"
+    D = 320 if small else 512
+    g = synth.ultrasound(n=50_000, extent=(D, D, D)) if small else synth.ultrasound()
     gs = B.GaussianSet.from_numpy(g, dev)
-    D = 512
-    target = speckle_blob_volume(torch, dev, (D, D, D))
+    target = speckle_blob_volume(torch, dev, (D, D, D), n_blobs=2 if small else 16)
     stream = torch.cuda.current_stream()
     grads = (torch.empty(g.n, 3, device=dev), torch.empty(g.n, 3, device=dev), torch.empty(g.n, 4, device=dev),
              torch.empty(g.n, device=dev))
@@ -955,7 +959,8 @@ def run_ultrasound(args):
             B.gp_render_backward(ctx, gs, z, D, D, 5.0, G, grads=grads)
         fwd_phase, bwd_phase = "fwd", "bwd"
         ops = (OPS_PER_EVAL_ROW if args.exp == "row" else OPS_PER_EVAL)["bwd"]
-        name = "ultrasound slice stack: 200k Gaussians, 512^3, sigma_z = 5, all 512 slices, fwd + MSE + bwd"
+        name = (f"ultrasound slice stack: {g.n // 1000}k Gaussians, {D}^3, sigma_z = 5, all {D} slices, "
+                "fwd + MSE + bwd")
     else:
         evals = B.gp_count_vox_evals(ctx, gs, D, D, D)
         evaluated = B.gp_count_vox_evaluated(ctx, gs, D, D, D)
@@ -966,7 +971,7 @@ def run_ultrasound(args):
             B.gp_voxelize_backward(ctx, gs, D, D, D, G, grads=grads)
         fwd_phase, bwd_phase = "vox_fwd", "vox_bwd"
         ops = OPS_PER_EVAL["bwd"]  # the voxelizer planes run the slice rasterisers with per-pixel exp2
-        name = "ultrasound voxelize: 200k Gaussians, 512^3 grid, Eq. 12 fwd + MSE + bwd"
+        name = f"ultrasound voxelize: {g.n // 1000}k Gaussians, {D}^3 grid, Eq. 12 fwd + MSE + bwd"
     flush = torch.empty(64 * 1024 * 1024, device=dev)
     for _ in range(args.warmup):
         flush.zero_()
