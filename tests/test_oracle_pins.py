@@ -192,8 +192,9 @@ def test_slice_mass():
 
 def test_stack_mass_conservation():
     """P6: over slices one voxel apart, sum_s sum_p I_s = (2 pi)^(3/2) sum_i alpha_i
-    sqrt(Sigma_zz,i + sigma_z^2) (north star "mass conservation", in the paper's
-    Eq. 9 amplitude)."""
+    sqrt(Sigma_zz,i + sigma_z^2) (mass conservation: the slice sums times the
+    slice spacing give the total integrated intensity, in the paper's Eq. 9
+    amplitude)."""
     rng = np.random.Generator(np.random.PCG64(11))
     n = 5
     mu = np.column_stack([rng.uniform(18, 30, n), rng.uniform(18, 30, n), rng.uniform(28, 36, n)])
